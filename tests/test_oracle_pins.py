@@ -1,0 +1,300 @@
+"""Pins for the CPU oracle: it is checked against facts fixed by the paper and by
+mathematics, never against itself or the CUDA path.
+
+Each test names what it pins. Together they are chosen so that a plausible slip
+in the oracle (a dropped pair swap X, a wrong sign (-1)^{h-|S|}, a 1/k instead of
+1/(2k), a transposed U, a missing s_j!, a wrong cosh normalisation) fails one.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def dfact(k):  # (k)!! for odd k, 1 for k <= 0
+    return math.prod(range(k, 0, -2)) if k > 0 else 1
+
+
+def rand_sym(n, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    return (A + A.T) / 2
+
+
+# --- Hafnian tiers -----------------------------------------------------------
+
+@pytest.mark.parametrize("k", range(0, 9))
+def test_haf_all_ones_double_factorial(orc, k):
+    """Haf(J_2k) = (2k-1)!!, the number of perfect matchings (Eq. HafMatch)."""
+    J = np.ones((2 * k, 2 * k))
+    assert orc.haf_pm(J) == dfact(2 * k - 1)
+    assert orc.haf_subset(J) == dfact(2 * k - 1)
+
+
+@pytest.mark.parametrize("k", [9, 10])
+def test_haf_all_ones_subset_large(orc, k):
+    """(2k-1)!! through the subset sum at n = 18, 20 (kappa ~1e6: dd is needed)."""
+    J = np.ones((2 * k, 2 * k))
+    assert orc.haf_subset(J) == dfact(2 * k - 1)
+
+
+def test_haf_odd_and_empty(orc):
+    """Odd n has no perfect matching (Haf = 0); the empty matrix has Haf = 1."""
+    assert orc.haf_pm(np.ones((3, 3))) == 0
+    assert orc.haf_subset(np.ones((5, 5))) == 0
+    assert orc.haf_pm(np.zeros((0, 0))) == 1
+    assert orc.haf_subset(np.zeros((0, 0))) == 1
+
+
+def test_haf_n4_paper_expansion(orc):
+    """The n = 4 expansion printed in Sec. 2.3, read from the golden fixture."""
+    lines = [l.split() for l in open(os.path.join(GOLDEN, "ws_example.txt")) if not l.startswith("#")]
+    matchings = [l for l in lines if l[0] == "matchings"][0][1:]
+    V = rand_sym(4, 1)
+    expect = 0
+    for mt in matchings:
+        term = 1
+        for pair in mt.split(","):
+            a, b = (int(v) - 1 for v in pair.split("-"))
+            term *= V[a, b]
+        expect += term
+    assert abs(orc.haf_pm(V) - expect) < 1e-14 * abs(expect)
+    assert abs(orc.haf_subset(V) - expect) < 1e-14 * abs(expect)
+
+
+@pytest.mark.parametrize("n", [2, 4, 6, 8, 10, 12, 14])
+def test_subset_equals_matchings_dd(orc, n):
+    """The two independent Hafnian tiers agree to dd accuracy (~1e-20)."""
+    A = rand_sym(n, 100 + n)
+    a = orc.haf_pm(A)
+    b = orc.haf_subset(A)
+    assert abs(a - b) <= 1e-20 * abs(a) + 1e-300
+
+
+def test_subset_equals_matchings_n16(orc):
+    A = rand_sym(16, 7)
+    a = orc.haf_pm(A)
+    b = orc.haf_subset(A)
+    assert abs(a - b) <= 1e-20 * abs(a)
+
+
+def test_haf_bipartite_equals_permanent(orc):
+    """Haf([[0, C], [C^T, 0]]) = Per(C) (textbook), Per by Ryser (O3)."""
+    rng = np.random.default_rng(3)
+    for k in (1, 2, 3, 5, 7):
+        C = rng.standard_normal((k, k)) + 1j * rng.standard_normal((k, k))
+        Z = np.zeros((2 * k, 2 * k), complex)
+        Z[:k, k:] = C
+        Z[k:, :k] = C.T
+        per = orc.per_ryser(C)
+        assert abs(orc.haf_pm(Z) - per) <= 1e-13 * abs(per)
+        assert abs(orc.haf_subset(Z) - per) <= 1e-13 * abs(per)
+
+
+def test_ryser_pins(orc):
+    """Ryser against the permutation sum (k <= 6), Per(J_k) = k!, Per(I) = 1."""
+    rng = np.random.default_rng(4)
+    for k in range(1, 7):
+        C = rng.standard_normal((k, k)) + 1j * rng.standard_normal((k, k))
+        bf = sum(np.prod([C[i, s[i]] for i in range(k)]) for s in itertools.permutations(range(k)))
+        assert abs(orc.per_ryser(C) - bf) <= 1e-13 * abs(bf)
+        assert orc.per_ryser(np.ones((k, k))) == math.factorial(k)
+        assert orc.per_ryser(np.eye(k)) == 1
+
+
+def test_haf_permutation_invariance_and_homogeneity(orc):
+    """Haf(P A P^T) = Haf(A) (Sec. 2.3, Appendix B); Haf(cA) = c^{n/2} Haf(A)."""
+    n = 12
+    A = rand_sym(n, 11)
+    h = orc.haf_subset(A)
+    perm = np.random.default_rng(12).permutation(n)
+    assert abs(orc.haf_subset(A[np.ix_(perm, perm)]) - h) <= 1e-24 * abs(h) * 1e4
+    c = 0.7 - 0.4j
+    assert abs(orc.haf_subset(c * A) - c ** (n // 2) * h) <= 1e-13 * abs(h)
+
+
+def test_haf_diagonal_independent(orc):
+    """No perfect matching uses V(i, i) (Eq. HafMatch): the diagonal is irrelevant."""
+    A = rand_sym(10, 5)
+    B = A.copy()
+    np.fill_diagonal(B, np.arange(10) * (1 + 2j))
+    assert abs(orc.haf_subset(A) - orc.haf_subset(B)) <= 1e-20 * abs(orc.haf_subset(A))
+
+
+def test_haf_laplace_expansion(orc):
+    """Haf(V) = sum_u V(n,u) Haf(V without rows/cols n,u) (Appendix A)."""
+    n = 10
+    V = rand_sym(n, 21)
+    total = 0
+    for u in range(n - 1):
+        keep = [i for i in range(n - 1) if i != u]
+        total += V[n - 1, u] * orc.haf_subset(V[np.ix_(keep, keep)])
+    h = orc.haf_subset(V)
+    assert abs(total - h) <= 1e-13 * abs(h)
+
+
+def test_f64_twin_error_within_kappa_bound(orc):
+    """The double-precision twin stays within a small multiple of kappa*u."""
+    for n, seed in ((8, 1), (12, 2), (16, 3)):
+        A = rand_sym(n, seed)
+        h, K = orc.haf_subset(A, return_kappa=True)
+        f = orc.haf_subset_f64(A)
+        assert abs(f - h) <= 4 * n * K * 2.0 ** -53
+
+
+# --- kernel matrix and probabilities -----------------------------------------
+
+def test_build_B_definition(orc):
+    """B = U diag(tanh r) U^T is symmetric; with t = 1 it is unitary (Sec. 2.3)."""
+    U = W.haar_unitary(12, 5)
+    r = W.squeezing(12, "uniform", seed=5)
+    B = orc.build_B(U, r)
+    ref = np.einsum("ik,k,jk->ij", U, np.tanh(r), U)
+    assert np.abs(B - ref).max() < 1e-14
+    assert np.abs(B - B.T).max() < 1e-15
+    Wm = orc.build_B_dd(U, np.ones(12))
+    Wc = Wm[..., 0] + 1j * Wm[..., 2]
+    assert np.abs(Wc @ Wc.conj().T - np.eye(12)).max() < 1e-13
+
+
+def test_prob_two_photons(orc):
+    """n = 2: p(1_i 1_j) = |B_ij|^2 / prod cosh r; p(2_j) = |B_jj|^2 / (2! prod cosh r)."""
+    m = 6
+    U = W.haar_unitary(m, 9)
+    r = W.squeezing(m, "uniform", seed=9)
+    B = orc.build_B(U, r)
+    L = np.sum(np.log(np.cosh(r)))
+    pats = [np.array([1, 4]), np.array([3, 3])]
+    out = orc.prob(U, r, pats)
+    assert abs(out["p"][0] - abs(B[1, 4]) ** 2 * np.exp(-L)) < 1e-14 * out["p"][0]
+    assert abs(out["p"][1] - abs(B[3, 3]) ** 2 * np.exp(-L) / 2) < 1e-14 * out["p"][1]
+
+
+def test_single_mode_collision(orc):
+    """n photons in one mode: B_x = b J_n, Haf = b^{n/2} (n-1)!!."""
+    m = 5
+    U = W.haar_unitary(m, 2)
+    r = W.squeezing(m, "const", value=0.8)
+    B = orc.build_B(U, r)
+    for n in (2, 4, 6, 8):
+        out = orc.prob(U, r, [np.full(n, 2, dtype=np.int32)])
+        expect = B[2, 2] ** (n // 2) * dfact(n - 1)
+        assert abs(out["haf"][0] - expect) <= 1e-13 * abs(expect)
+        lp = 2 * np.log(abs(expect)) - math.lgamma(n + 1) - np.sum(np.log(np.cosh(r)))
+        assert abs(out["logp"][0] - lp) < 1e-12
+
+
+def smss_c2(s, r):
+    """|c_s(r)|^2 of a single-mode squeezed state (Sec. 2.1), 0 for odd s."""
+    if s % 2:
+        return 0.0
+    return (1 / np.cosh(r)) * (np.tanh(r) / 2) ** s * math.factorial(s) / math.factorial(s // 2) ** 2
+
+
+def test_identity_network_product_state(orc):
+    """U = I (and a permutation): p(s) = prod_j |c_{s_j}(r_j)|^2 (Sec. 2.1)."""
+    m = 5
+    r = W.squeezing(m, "uniform", seed=1, lo=0.3, hi=1.1)
+    for U, rr in ((np.eye(m), r), (np.eye(m)[[2, 0, 4, 1, 3]], r)):
+        # output mode i of U receives input mode perm^{-1}(i): r seen at output i
+        r_out = np.array([rr[np.argmax(np.abs(U[i]))] for i in range(m)])
+        for pat in ([0, 0], [1, 1, 3, 3], [2, 2, 2, 2], [0, 0, 1, 1, 4, 4], [0, 1], [1, 1, 2]):
+            x = np.array(pat, dtype=np.int32)
+            s = W.pattern_to_counts(x, m)
+            expect = np.prod([smss_c2(int(s[j]), r_out[j]) for j in range(m)])
+            got = orc.prob(U, rr, [x])["p"][0]
+            assert abs(got - expect) <= 1e-14 * max(expect, 1e-300) + (1e-300 if expect == 0 else 0)
+
+
+def neg_binomial(m, n, r):
+    """P_n = C((m+n)/2 - 1, n/2) tanh^n r / cosh^m r (Eq. Eqdistribution)."""
+    return math.comb((m + n) // 2 - 1, n // 2) * np.tanh(r) ** n / np.cosh(r) ** m
+
+
+def per_mode_Pn(r, n):
+    """[z^n] prod_i sech r_i (1 - tanh^2 r_i z^2)^{-1/2}: P_n for unequal r."""
+    series = np.zeros(n + 1)
+    series[0] = 1.0
+    for ri in r:
+        t2 = np.tanh(ri) ** 2
+        f = np.zeros(n + 1)
+        for k in range(0, n // 2 + 1):  # (1 - a z^2)^{-1/2} = sum C(2k,k)/4^k a^k z^{2k}
+            f[2 * k] = math.comb(2 * k, k) / 4 ** k * t2 ** k
+        series = np.convolve(series, f)[: n + 1] / np.cosh(ri)
+    return series[n]
+
+
+@pytest.mark.parametrize("n", [0, 2, 4, 6])
+def test_total_probability_negative_binomial(orc, n):
+    """sum_{|s| = n} p(s) = P_n, identical r (Eq. Eqdistribution), m = 8."""
+    m = 8
+    U = W.haar_unitary(m, 0)
+    r = W.squeezing(m, "const", value=0.5)
+    pats = W.all_patterns(m, n)
+    tot = orc.prob(U, r, pats, method="pm")["p"].sum()
+    assert abs(tot - neg_binomial(m, n, 0.5)) <= 1e-12 * neg_binomial(m, n, 0.5)
+
+
+def test_total_probability_per_mode_r(orc):
+    """The same sum with unequal r_i against the product generating function."""
+    m, n = 6, 6
+    U = W.haar_unitary(m, 3)
+    r = W.squeezing(m, "uniform", seed=3)
+    pats = W.all_patterns(m, n)
+    tot = orc.prob(U, r, pats)["p"].sum()
+    ref = per_mode_Pn(r, n)
+    assert abs(tot - ref) <= 1e-12 * ref
+
+
+@pytest.mark.parametrize("m,n", [(4, 4), (3, 6), (5, 2)])
+def test_position_basis_normalisation(orc, m, n):
+    """sum_{x in [m]^n} |Haf(W_x)|^2 = f_n = n! C((m+n)/2 - 1, n/2), W = U U^T
+    (Appendix A). Summed over configurations s with multiplicity n!/prod s_j!."""
+    U = W.haar_unitary(m, 40 + m)
+    Wdd = orc.build_B_dd(U, np.ones(m))
+    pats = W.all_patterns(m, n)
+    out = orc.prob(U, np.zeros(m), pats, Bdd=Wdd)  # r = 0: no cosh factor
+    total = math.factorial(n) * out["p"].sum()  # p = |Haf|^2 / prod s_j!
+    f_n = 1  # recurrence f_n = (n-1)(m+n-2) f_{n-2}, f_0 = 1 (Eq. Eqf)
+    for k in range(2, n + 1, 2):
+        f_n *= (k - 1) * (m + k - 2)
+    # closed form n! C((m+n)/2 - 1, n/2), a generalised binomial when m is odd
+    a = (m + n) / 2 - 1
+    closed = math.factorial(n) * math.exp(math.lgamma(a + 1) - math.lgamma(n // 2 + 1) - math.lgamma(a - n // 2 + 1))
+    assert abs(closed - f_n) <= 1e-12 * f_n
+    assert abs(total - f_n) <= 1e-12 * f_n
+
+
+def test_ws_example_paper(orc):
+    """Sec. 2.3's W_s example: s = (1,1,0,2,0,0) selects rows/cols (1,2,4,4) of W;
+    its Hafnian by the n = 4 expansion equals the oracle's for x = (0,1,3,3)."""
+    lines = {l.split()[0]: l.split()[1:] for l in open(os.path.join(GOLDEN, "ws_example.txt"))
+             if not l.startswith("#") and l.strip()}
+    s = np.array([int(v) for v in lines["s"]])
+    rows = [int(v) - 1 for v in lines["rows"]]
+    x = np.repeat(np.arange(len(s)), s).astype(np.int32)
+    assert list(x) == rows
+    m = len(s)
+    U = W.haar_unitary(m, 17)
+    Wdd = orc.build_B_dd(U, np.ones(m))
+    Wc = (Wdd[..., 0] + Wdd[..., 1]) + 1j * (Wdd[..., 2] + Wdd[..., 3])
+    Ws = Wc[np.ix_(rows, rows)]
+    expect = Ws[0, 1] * Ws[2, 3] + Ws[0, 2] * Ws[1, 3] + Ws[0, 3] * Ws[1, 2]
+    out = orc.prob(U, np.zeros(m), [x], Bdd=Wdd)
+    assert abs(out["haf"][0] - expect) <= 1e-14 * abs(expect)
+    assert abs(out["p"][0] - abs(expect) ** 2 / 2) <= 1e-13 * out["p"][0]
+
+
+def test_prob_methods_agree_tiny_workload(orc):
+    """Tiny workload (m = 8, 4- and 2-photon patterns): subset sum vs matchings."""
+    U, r, pats = W.workload("tiny_m8")
+    a = orc.prob(U, r, pats, method="subset")
+    b = orc.prob(U, r, pats, method="pm")
+    assert np.all(np.abs(a["haf"] - b["haf"]) <= 1e-15 * np.abs(b["haf"]) + 1e-300)
+    assert np.all(np.abs(a["p"] - b["p"]) <= 1e-14 * b["p"])
