@@ -1,0 +1,339 @@
+"""Benchmark: GBS output probabilities per second on one GB300 (or N, weak scaling).
+
+Headline workload: M = 64 modes, Haar-random U (seed 1), r_i ~ U[0.6, 1.0], 4096
+collision-free patterns of n = 16 photons, FP64 path, one batched call per step.
+`value` = patterns / device time of the step with inputs resident in HBM;
+`e2e` = the same through the C ABI with host index lists and host outputs.
+
+Also reported (`extra`): the mixed FP32 path on the same workload, the mixed-n
+collision workload (M = 144), the large instances (M = 900, n = 28 and 30) and
+the serving loop (Poisson stream, p50/p99 latency), unless --quick.
+
+`--impl reference` times the CPU oracle (plain C, FP64 subset sum with repeated
+products, OpenMP over patterns) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+WORKLOAD = "batched_m64_n16"
+METRIC = "GBS output probs/sec at n=16/24/30 vs FP64 oracle; p50/p99 request latency"
+UNIT = "probs/s"
+SMS, SM_MHZ_MAX, FP64_FLOP_PER_CLK_SM = 152, 2070.0, 4.0
+
+
+def model_flops(n: int) -> float:
+    """Algorithmic FP64 flops of one Hafnian: sum_s C(h,s) * 8 (2s)^3 = 64 2^{h-3} h^2 (h+3)."""
+    h = n // 2
+    if n % 2 or h == 0:
+        return 0.0
+    return 64.0 * 2.0 ** (h - 3) * h * h * (h + 3)
+
+
+def fp64_peak_tflops() -> float:
+    """FP64 peak from unit counts and clock: 152 SMs x 4 FP64 flop/clk/SM (2 DFMA
+    lanes) x 2.07 GHz = 1.26 TFLOP/s (the part's 1.25 TFLOP/s FP64 rating)."""
+    return SMS * FP64_FLOP_PER_CLK_SM * SM_MHZ_MAX * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(pats, U, r, target_s: float = 12.0):
+    """Oracle FP64 subset sum on the host cores over a bounded sample (the
+    workload's patterns, repeated in order when the sample exceeds the batch)."""
+    import oracle
+
+    B = oracle.build_B(U, r)
+    mats = [B[np.ix_(p, p)] for p in pats]
+    k = 64
+    t0 = time.perf_counter()
+    oracle.haf_batch_f64(mats[:k])
+    dt = time.perf_counter() - t0
+    k2 = int(max(k, k * target_s / max(dt, 1e-6)))
+    sample = [mats[i % len(mats)] for i in range(k2)]
+    t0 = time.perf_counter()
+    oracle.haf_batch_f64(sample)
+    dt2 = time.perf_counter() - t0
+    return {"value": k2 / dt2, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d patterns (the n=16, M=64 batch of %d, cycled), FP64 subset sum, "
+                      "OpenMP over patterns, %.1f s" % (k2, len(pats), dt2)}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    U, r, pats = W.workload(WORKLOAD)
+    import oracle
+    oracle.build()
+    B = oracle.build_B(U, r)
+    mats = [B[np.ix_(p, p)] for p in pats]
+    # each step: a bounded sample of the workload, sized so the run stays short
+    t0 = time.perf_counter()
+    oracle.haf_batch_f64(mats[:8])
+    per = (time.perf_counter() - t0) / 8
+    k = int(max(8, min(len(mats), 4.0 / max(per, 1e-9) / max(1, args.steps + args.warmup))))
+    for _ in range(args.warmup):
+        oracle.haf_batch_f64(mats[:k])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.haf_batch_f64(mats[:k])
+    dt = time.perf_counter() - t0
+    v = k * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "patterns_per_step": k},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "%d of %d patterns per step" % (k, len(pats))},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true", help="headline workload only")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import paper_1908_10070_gb300 as gbs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    U, r, pats = W.workload(WORKLOAD)
+    K = gbs.build_kernel(torch.from_numpy(U.view(np.float64).copy()).cuda(), torch.from_numpy(r).cuda())
+    idx, n, offs = gbs.pack_patterns(pats)
+    b = len(pats)
+    d_idx = torch.from_numpy(idx).cuda()
+    p = torch.zeros(b, dtype=torch.float64, device="cuda")
+    lp = torch.zeros_like(p)
+    hf = torch.zeros(2 * b, dtype=torch.float64, device="cuda")
+    er = torch.zeros_like(p)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        gbs.prob_batch(K, d_idx, n, offs, gbs.FP64, p_out=p, logp_out=lp, haf_out=hf, err_out=er)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    ks, ke = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ss, se = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for ev in (ks, ke, ss, se):  # torch creates the CUDA event at its first record
+        ev.record(stream)
+    step_ms, kern_ms = [], []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()  # write 256 MB > L2 between timed steps
+            gbs.set_timing_events(ks, ke)
+            ss.record(stream)
+            step()
+            se.record(stream)
+            gbs.set_timing_events(None, None)
+            se.synchronize()
+            step_ms.append(ss.elapsed_time(se))
+            kern_ms.append(ks.elapsed_time(ke))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_step = float(np.sum(step_ms)) / args.steps
+    t_kern = float(np.mean(kern_ms))
+    if dist:
+        tt = torch.tensor([t_step, t_kern], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step, t_kern = tt.tolist()
+    value = world * b / (t_step * 1e-3)
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    hp = np.zeros(b); hl = np.zeros(b); hh = np.zeros(2 * b); he = np.zeros(b)
+    for _ in range(2):
+        gbs.prob_batch(K, idx, n, offs, gbs.FP64, p_out=hp, logp_out=hl, haf_out=hh, err_out=he)
+    t0 = time.perf_counter()
+    e2e_steps = max(3, args.steps // 2)
+    for _ in range(e2e_steps):
+        gbs.prob_batch(K, idx, n, offs, gbs.FP64, p_out=hp, logp_out=hl, haf_out=hh, err_out=he)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    assert np.array_equal(hh, hf.cpu().numpy()), "host and device paths disagree"
+
+    flops = model_flops(16) * b
+    peak = fp64_peak_tflops()
+    achieved = flops / (t_kern * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "M=64 Haar U seed 1, r~U[0.6,1.0], 4096 collision-free n=16 patterns, FP64",
+                   "patterns_per_step": b, "l2": "flushed (256 MB write) between timed steps"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "haf_subsets_kernel<double>", "kernel_ms": t_kern,
+                     "flops_per_launch": flops,
+                     "peak_note": "FP64 from unit counts and clock (152 SM x 4 flop/clk x 2.07 GHz)"},
+        "e2e": {"value": world * b / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(idx.nbytes),
+                "d2h_bytes_per_step": int(hp.nbytes + hl.nbytes + hh.nbytes + he.nbytes)},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(pats, U, r)
+    if rank == 0 and not args.quick:
+        line["extra"] = extras(gbs, torch)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def timed_batch(gbs, torch, K, pats, precision, reps=3):
+    idx, n, offs = gbs.pack_patterns(pats)
+    b = len(pats)
+    d_idx = torch.from_numpy(idx).cuda()
+    p = torch.zeros(b, dtype=torch.float64, device="cuda")
+    hf = torch.zeros(2 * b, dtype=torch.float64, device="cuda")
+    er = torch.zeros_like(p)
+    ks, ke = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ks.record()
+    ke.record()
+    gbs.prob_batch(K, d_idx, n, offs, precision, p_out=p, haf_out=hf, err_out=er)
+    torch.cuda.synchronize()
+    ts, tk = [], []
+    for _ in range(reps):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        gbs.set_timing_events(ks, ke)
+        s.record()
+        gbs.prob_batch(K, d_idx, n, offs, precision, p_out=p, haf_out=hf, err_out=er)
+        e.record()
+        gbs.set_timing_events(None, None)
+        e.synchronize()
+        ts.append(s.elapsed_time(e))
+        tk.append(ks.elapsed_time(ke))
+    h = hf.cpu().numpy()
+    return float(np.median(ts)), float(np.median(tk)), h[0::2] + 1j * h[1::2], er.cpu().numpy()
+
+
+def extras(gbs, torch):
+    out = {}
+    peak = fp64_peak_tflops()
+    # mixed path on the headline workload
+    U, r, pats = W.workload(WORKLOAD)
+    K = gbs.build_kernel(U, r)
+    t64, k64, h64, _ = timed_batch(gbs, torch, K, pats, gbs.FP64)
+    t32, k32, h32, e32 = timed_batch(gbs, torch, K, pats, gbs.MIXED)
+    relerr = np.abs(h32 - h64) / np.abs(h64)
+    out["n16_mixed"] = {"probs_per_s": len(pats) / (t32 * 1e-3), "ms": t32, "kernel_ms": k32,
+                        "fp64_ms": t64, "speedup_vs_fp64": t64 / t32,
+                        "max_rel_err_vs_fp64": float(relerr.max()),
+                        "max_err_bound": float(e32.max()), "within_bound": bool(np.all(relerr <= e32))}
+    # mixed-n workload with collisions
+    U, r, pats = W.workload("mixed_m144")
+    K = gbs.build_kernel(U, r)
+    t64, k64, h64, e64 = timed_batch(gbs, torch, K, pats, gbs.FP64)
+    t32, k32, h32, e32 = timed_batch(gbs, torch, K, pats, gbs.MIXED)
+    fl = sum(model_flops(len(p)) for p in pats)
+    relerr = np.abs(h32 - h64) / np.abs(h64)
+    out["mixed_m144"] = {"fp64_probs_per_s": len(pats) / (t64 * 1e-3), "fp64_ms": t64,
+                         "fp64_frac_of_peak": fl / (k64 * 1e-3) / 1e12 / peak,
+                         "mixed_probs_per_s": len(pats) / (t32 * 1e-3), "mixed_ms": t32,
+                         "mixed_max_rel_err_vs_fp64": float(relerr.max()),
+                         "mixed_within_bound": bool(np.all(relerr <= e32))}
+    # large instances
+    U, r, pats = W.workload("large_m900")
+    K = gbs.build_kernel(U, r)
+    t64, k64, h64, e64 = timed_batch(gbs, torch, K, pats, gbs.FP64, reps=2)
+    fl = sum(model_flops(len(p)) for p in pats)
+    out["large_m900"] = {"probs_per_s": len(pats) / (t64 * 1e-3), "ms": t64, "kernel_ms": k64,
+                         "subset_terms_per_s": sum(2 ** (len(p) // 2) for p in pats) / (k64 * 1e-3),
+                         "achieved_tflops": fl / (k64 * 1e-3) / 1e12, "frac_of_peak": fl / (k64 * 1e-3) / 1e12 / peak,
+                         "max_err_est": float(e64.max())}
+    return out
+
+
+if __name__ == "__main__":
+    main()

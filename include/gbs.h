@@ -1,0 +1,186 @@
+/*
+ * gbs.h - C ABI of the GB300 library for Gaussian-boson-sampling output
+ * probabilities with every input mode squeezed.
+ *
+ * The library evaluates
+ *
+ *     p(s) = |Haf(B_s)|^2 / (prod_j s_j! * prod_i cosh r_i),
+ *     B    = U diag(tanh r_1, ..., tanh r_m) U^T,
+ *
+ * the output-probability formula of Sec. 2.3 (Eq. ProOri) written for per-mode
+ * squeezing r_i; for identical r it is exactly Eq. ProOri, because
+ * Haf(tanh(r) W_s) = tanh(r)^{n/2} Haf(W_s). B_s repeats row and column j of B
+ * s_j times (Sec. 2.3, Eq. W_s_example); equivalently B_x(i, j) = B(x_i, x_j)
+ * for the index list x of the pattern (Sec. 3.2, "Step 2: change of basis").
+ *
+ * Haf is computed by the 2^{n/2}-subset sum whose O(n^3 2^{n/2}) cost Sec. 2.3
+ * cites (Bjorklund, Gupt, Quesada): with n = 2h and pairs {2i, 2i+1},
+ *     Haf(A) = sum_{S subset of [h]} (-1)^{h-|S|} f(X A_S),
+ *     f(M)   = [x^h] det(I - x M)^{-1/2},
+ * X swapping the two members of each pair. One subset term is a characteristic
+ * polynomial of a 2|S| x 2|S| complex matrix.
+ *
+ * Conventions for every call:
+ *   - Return 0 on success or a negative GBS_E* code; gbs_last_error() gives a
+ *     thread-local message for the last failure on the calling thread. No C++
+ *     exception crosses this boundary.
+ *   - Complex numbers are interleaved (re, im) doubles; matrices are row-major.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream). Work is stream-ordered on it; the call returns once the work is
+ *     enqueued, unless an output pointer is host memory (then it returns after
+ *     the results are in that memory).
+ *   - Buffers passed in are owned by the caller and never freed or retained
+ *     after the call returns. Pointer arguments documented as "host or device"
+ *     are classified with cudaPointerGetAttributes.
+ *   - Odd n gives Haf = 0 and p = 0 (P_n = 0 for odd n, Sec. 3.1); n = 0 gives
+ *     Haf = 1 and p = prod_i sech r_i.
+ */
+#ifndef GBS_H
+#define GBS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GBS_OK 0
+#define GBS_EINVAL (-1)    /* bad argument (null pointer, negative size, bad precision) */
+#define GBS_ENOMEM (-2)    /* device or host allocation failed */
+#define GBS_ERANGE (-3)    /* n > GBS_MAX_N, or a mode index outside [0, m) */
+#define GBS_EAGAIN (-4)    /* serving queue full; retry later */
+#define GBS_ETIMEDOUT (-5) /* a bounded device or host wait gave up */
+#define GBS_ECUDA (-6)     /* a CUDA runtime call failed (message has the CUDA error) */
+#define GBS_ENOENT (-7)    /* unknown serving ticket */
+
+#define GBS_FP64 0  /* per-subset arithmetic in FP64, signed sum in double-double */
+#define GBS_MIXED 1 /* per-subset arithmetic in FP32, signed sum in float-float, FP64 final sum */
+
+#define GBS_MAX_N 32 /* largest photon number (matrix order) accepted */
+
+typedef struct gbs_kernel gbs_kernel; /* opaque, library-owned */
+typedef struct gbs_server gbs_server; /* opaque, library-owned */
+
+/* ------------------------------------------------------------------------ */
+/* Kernel matrix                                                            */
+/* ------------------------------------------------------------------------ */
+
+/* Build the resident kernel matrix B = U diag(tanh r) U^T of an m-mode
+ * interferometer (Sec. 2.3, W = U U^T, with per-mode squeezing) and the log
+ * normaliser L = sum_i log cosh r_i of Eq. ProOri.
+ *   U_ri  m*m complex128, interleaved, row-major, host or device.
+ *   r     m doubles, host or device.
+ *   m     number of modes, >= 1.
+ *   out   receives a new library-owned object; free with gbs_free_kernel.
+ * B (16 m^2 bytes) stays in device memory on the current device until freed.
+ * Errors: GBS_EINVAL (null pointer, m < 1), GBS_ENOMEM, GBS_ECUDA. */
+int gbs_build_kernel(const double* U_ri, const double* r, int m, void* stream, gbs_kernel** out);
+
+/* Release a kernel object (waits for the device work that uses it). NULL is a no-op. */
+int gbs_free_kernel(gbs_kernel* k);
+
+/* Number of modes m and the log normaliser L = sum_i log cosh r_i (available
+ * after the build's stream work completes; this call synchronises with it). */
+int gbs_kernel_info(const gbs_kernel* k, int* m, double* log_norm);
+
+/* Copy B (m*m complex128 interleaved) into dst (host or device), stream-ordered. */
+int gbs_kernel_copy_B(const gbs_kernel* k, double* dst, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batched Hafnians and probabilities                                       */
+/* ------------------------------------------------------------------------ */
+
+/* Hafnians of a batch of symmetric complex matrices (Eq. HafMatch), by the
+ * subset sum above.
+ *   A_ri    concatenated matrices, complex128 interleaved, host or device;
+ *           matrix b is n[b] x n[b] row-major starting at complex element
+ *           offs[b]. Only the entries off the diagonal are read (no perfect
+ *           matching uses V(i, i)).
+ *   n,offs  host arrays of `batch` entries; 0 <= n[b] <= GBS_MAX_N.
+ *   precision  GBS_FP64 or GBS_MIXED.
+ *   haf_ri_out  2*batch doubles (host or device): Haf(A_b).
+ *   kappa_out   batch doubles (host or device) or NULL: the cancellation ratio
+ *               kappa_b = sum_S |f(X A_S)|_1 / |Haf(A_b)| (|z|_1 = |re|+|im|).
+ * Errors: GBS_EINVAL, GBS_ERANGE (n[b] > GBS_MAX_N), GBS_ENOMEM, GBS_ECUDA. */
+int gbs_hafnian_batch(const double* A_ri, const int* n, const int64_t* offs, int batch,
+                      int precision, void* stream, double* haf_ri_out, double* kappa_out);
+
+/* Output probabilities of a batch of patterns (Eq. ProOri).
+ *   idx     concatenated 0-based mode-index lists x (host or device); pattern b
+ *           is idx[offs[b] .. offs[b]+n[b]), a repeated index is a collision.
+ *           Order within a list does not matter (Appendix B).
+ *   n,offs  host arrays of `batch` entries; 0 <= n[b] <= GBS_MAX_N.
+ *   Outputs (each host or device, each may be NULL):
+ *     p_out       p(s) per pattern (underflows to 0 below ~1e-308),
+ *     logp_out    log p(s) (-inf when Haf = 0),
+ *     haf_ri_out  Haf(B_x), 2 doubles per pattern,
+ *     err_est_out estimated relative error of Haf: c * u * n * kappa, u the
+ *                 unit roundoff of the per-subset arithmetic (2^-53 or 2^-24).
+ * A host idx is checked on the host (GBS_ERANGE for an index >= m). A device
+ * idx is checked on the device: a pattern with an out-of-range index gets NaN
+ * outputs and no memory outside B is read.
+ * Errors: GBS_EINVAL, GBS_ERANGE, GBS_ENOMEM, GBS_ECUDA. */
+int gbs_prob_batch(const gbs_kernel* k, const int* idx, const int* n, const int64_t* offs,
+                   int batch, int precision, void* stream, double* p_out, double* logp_out,
+                   double* haf_ri_out, double* err_est_out);
+
+/* Instrumentation: when both are non-NULL, every later batch records `start`
+ * immediately before and `stop` immediately after its subset-sum kernel, on
+ * the batch's stream (cudaEvent_t passed as void*), so a caller can time that
+ * kernel alone. Pass NULL, NULL to stop. Process-wide; not for concurrent use
+ * from several threads. The paper has no counterpart (measurement only). */
+int gbs_set_timing_events(void* start, void* stop);
+
+/* ------------------------------------------------------------------------ */
+/* Autotuning                                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Time the candidate launch shapes (subsets per warp work item, warps per
+ * block) for photon number n and precision on synthetic matrices, on the
+ * current device, and keep the fastest for later calls with that n. Calls
+ * that find no tuned entry use a built-in default. Synchronises `stream`.
+ * chosen_out (may be NULL) receives the chosen subsets-per-item. */
+int gbs_autotune(int n, int precision, void* stream, int* chosen_out);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of single-pattern probability requests      */
+/* ------------------------------------------------------------------------ */
+
+typedef struct gbs_serve_opts {
+  int max_slots;          /* requests resident on the device at once (0 = 256) */
+  size_t mem_budget;      /* device bytes for request state (0 = 64 MiB) */
+  int queue_capacity;     /* pending requests accepted before GBS_EAGAIN (0 = 65536) */
+  int subsets_per_step;   /* subset terms per request per step (0 = library choice) */
+  int use_graphs;         /* 1 = replay a captured CUDA graph per step (default 1) */
+  double wait_timeout_s;  /* bound on any internal wait (0 = 10 s) */
+} gbs_serve_opts;
+
+/* Start a server for kernel matrix k: a host thread admits requests into
+ * device slots as slots and memory free up, and runs steps that advance every
+ * resident request's subset sum together; partial sums stay on the device
+ * between steps. k must outlive the server. opts may be NULL. */
+int gbs_serve_create(const gbs_kernel* k, const gbs_serve_opts* opts, gbs_server** out);
+
+/* Enqueue one pattern (host index list of n entries, copied before return).
+ * Non-blocking. ticket receives an id for gbs_serve_poll.
+ * Errors: GBS_EAGAIN (queue full), GBS_ERANGE, GBS_EINVAL. */
+int gbs_serve_submit(gbs_server* s, const int* idx, int n, int precision, int64_t* ticket);
+
+/* Returns 0 and fills p, haf_ri (2 doubles), err_est (each may be NULL) when
+ * the request is done (its ticket is then released), 1 while it is pending,
+ * or a negative error (GBS_ENOENT for an unknown or already-collected ticket). */
+int gbs_serve_poll(gbs_server* s, int64_t ticket, double* p, double* haf_ri, double* err_est);
+
+/* Stop the server thread (after finishing resident work, bounded by the
+ * timeout) and free its resources. */
+int gbs_serve_destroy(gbs_server* s);
+
+/* Thread-local message describing the last error on this thread ("" if none). */
+const char* gbs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBS_H */

@@ -353,7 +353,15 @@ void orc_per_ryser(int k, const double* C, double* out4) {
 void orc_prob(int m, const double* Bdd, const int* idx, const int* n, const long* offs, int batch,
               double log_norm, int method, double* p_out, double* logp_out, double* haf_out,
               double* kappa_out) {
-#pragma omp parallel for schedule(dynamic, 1)
+  /* patterns in parallel when there are enough of them; otherwise each
+   * pattern's subset sum runs its fixed chunks in parallel (same arithmetic
+   * either way: the chunked sum below) */
+#ifdef _OPENMP
+  int outer = batch >= omp_get_max_threads();
+#else
+  int outer = 1;
+#endif
+#pragma omp parallel for schedule(dynamic, 1) if (outer)
   for (int b = 0; b < batch; b++) {
     int nb = n[b];
     const int* x = idx + offs[b];
@@ -370,23 +378,8 @@ void orc_prob(int m, const double* Bdd, const int* idx, const int* n, const long
     if (method == 1) {
       haf = haf_pm_cdd(nb, W);
     } else {
-      /* serial subset sum (this loop already runs patterns in parallel) */
-      haf = cdd_zero();
-      if (nb % 2 == 0) {
-        int h = nb / 2;
-        if (h == 0) { haf = cdd_from(1.0, 0.0); K = 1.0; }
-        else {
-          cdd* buf = (cdd*)malloc(sizeof(cdd) * (3 * (size_t)nb * nb + 2 * (h + 1)));
-          cdd *M = buf, *P = M + nb * nb, *Q = P + nb * nb, *tr = Q + nb * nb, *e = tr + h + 1;
-          for (uint64_t S = 1; S < (1ull << h); S++) {
-            int s = __builtin_popcountll(S);
-            cdd f = subset_term_cdd(h, W, nb, (uint32_t)S, M, P, Q, tr, e);
-            K += cdd_abs(f);
-            haf = ((h - s) % 2) ? cdd_sub(haf, f) : cdd_add(haf, f);
-          }
-          free(buf);
-        }
-      }
+      haf = haf_subset_cdd(nb, W, &K);
+      if (nb == 0) K = 1.0;
     }
     /* p = |Haf|^2 / (prod_j s_j! prod_i cosh r_i): x is sorted, so equal modes
      * are adjacent; sum log s_j! over runs. */

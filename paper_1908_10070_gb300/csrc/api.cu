@@ -1,0 +1,661 @@
+// C ABI entry points: kernel matrix, batched Hafnians and probabilities, and
+// the launch planner shared with the serving loop and the autotuner.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gbs_api_internal.h"
+
+namespace gbs {
+
+// ------------------------------------------------------------------------
+// errors
+// ------------------------------------------------------------------------
+static thread_local std::string t_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return code;
+}
+
+void clear_error() { t_err.clear(); }
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(GBS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool is_device_ptr(const void* p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ------------------------------------------------------------------------
+// device memory: one stream-ordered pool per device, kept warm
+// ------------------------------------------------------------------------
+static std::mutex g_pool_mu;
+static std::map<int, cudaMemPool_t> g_pools;
+
+static cudaError_t get_pool(int dev, cudaMemPool_t* out) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  auto it = g_pools.find(dev);
+  if (it != g_pools.end()) {
+    *out = it->second;
+    return cudaSuccess;
+  }
+  cudaMemPoolProps props;
+  memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.handleTypes = cudaMemHandleTypeNone;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool;
+  cudaError_t e = cudaMemPoolCreate(&pool, &props);
+  if (e != cudaSuccess) return e;
+  uint64_t thr = ~0ull;
+  e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  if (e != cudaSuccess) return e;
+  g_pools[dev] = pool;
+  *out = pool;
+  return cudaSuccess;
+}
+
+cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  cudaMemPool_t pool;
+  e = get_pool(dev, &pool);
+  if (e != cudaSuccess) return e;
+  return cudaMallocFromPoolAsync(p, bytes < 256 ? 256 : bytes, pool, st);
+}
+
+cudaError_t scratch_free(void* p, cudaStream_t st) { return p ? cudaFreeAsync(p, st) : cudaSuccess; }
+
+// ------------------------------------------------------------------------
+// pinned host staging: a small ring of buffers, each reused once the copy
+// that last read it has completed on the device
+// ------------------------------------------------------------------------
+struct PinnedSlot {
+  void* ptr = nullptr;
+  size_t cap = 0;
+  cudaEvent_t ev = nullptr;
+  bool busy = false;
+};
+static std::mutex g_pin_mu;
+static std::vector<PinnedSlot> g_pin;
+
+int pinned_acquire(size_t bytes, void** ptr, int* slot) {
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  int pick = -1;
+  for (size_t i = 0; i < g_pin.size(); ++i) {
+    PinnedSlot& s = g_pin[i];
+    if (s.busy) continue;
+    if (s.ev && cudaEventQuery(s.ev) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (s.cap >= bytes) {
+      pick = (int)i;
+      break;
+    }
+  }
+  if (pick < 0) {
+    // grow a free slot, or add one (at most 32; then wait for slot 0)
+    for (size_t i = 0; i < g_pin.size() && pick < 0; ++i) {
+      PinnedSlot& s = g_pin[i];
+      if (s.busy) continue;
+      if (s.ev && cudaEventQuery(s.ev) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      pick = (int)i;
+    }
+    if (pick < 0 && g_pin.size() < 32) {
+      g_pin.push_back(PinnedSlot());
+      pick = (int)g_pin.size() - 1;
+    }
+    if (pick < 0) {
+      for (size_t i = 0; i < g_pin.size() && pick < 0; ++i)
+        if (!g_pin[i].busy) pick = (int)i;
+      if (pick < 0) return fail(GBS_EAGAIN, "all pinned staging buffers are in use");
+      cudaEventSynchronize(g_pin[pick].ev);
+    }
+    PinnedSlot& s = g_pin[pick];
+    if (s.cap < bytes) {
+      if (s.ptr) cudaFreeHost(s.ptr);
+      s.ptr = nullptr;
+      s.cap = 0;
+      size_t cap = 1 << 20;
+      while (cap < bytes) cap <<= 1;
+      cudaError_t e = cudaMallocHost(&s.ptr, cap);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMallocHost");
+      s.cap = cap;
+    }
+    if (!s.ev) {
+      cudaError_t e = cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    }
+  }
+  g_pin[pick].busy = true;
+  *ptr = g_pin[pick].ptr;
+  *slot = pick;
+  return GBS_OK;
+}
+
+void pinned_release(int slot, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  if (slot < 0 || slot >= (int)g_pin.size()) return;
+  cudaEventRecord(g_pin[slot].ev, st);
+  g_pin[slot].busy = false;
+}
+
+// ------------------------------------------------------------------------
+// launch shapes
+// ------------------------------------------------------------------------
+static std::mutex g_tune_mu;
+static std::map<std::pair<int, int>, TuneCfg> g_tuned;  // (precision, n) -> cfg
+
+TuneCfg default_cfg(int precision, int n) {
+  // 5 warps x 44 KB (FP64) fits every n <= 32 in one block per SM
+  TuneCfg c;
+  if (precision == GBS_FP64) {
+    c.warps_per_block = 5;
+    c.warp_bytes = 44032;
+  } else {
+    c.warps_per_block = 8;
+    c.warp_bytes = 27520;
+  }
+  c.rounds = (n >= 24) ? 2 : 4;
+  return c;
+}
+
+TuneCfg get_cfg(int precision, int n) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned.find(std::make_pair(precision, n));
+  if (it != g_tuned.end()) return it->second;
+  return default_cfg(precision, n);
+}
+
+void set_cfg(int precision, int n, const TuneCfg& c) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned[std::make_pair(precision, n)] = c;
+}
+
+int complex_bytes(int precision) { return precision == GBS_FP64 ? 16 : 8; }
+
+// Every order that a batch with largest photon number maxn can need fits the
+// warp's shared bytes (the largest group is N = n, h = n/2 for each n).
+bool shape_fits(int precision, int warp_bytes, int maxn) {
+  const int cb = complex_bytes(precision);
+  for (int n = 2; n <= maxn; n += 2)
+    if (lanes_for(n, n / 2, warp_bytes, cb) == 0) return false;
+  return true;
+}
+
+static int64_t binom64(int a, int b) {
+  if (b < 0 || b > a) return 0;
+  int64_t r = 1;
+  for (int i = 1; i <= b; ++i) r = r * (a - b + i) / i;
+  return r;
+}
+
+// Build the pattern descriptors and the work items. Items of each pattern are
+// numbered consecutively (their partial slots), and the schedule order lists
+// the most expensive items first (longest-first list scheduling), bucketed by
+// (subset order, rounds) so the cost is O(items).
+int plan_batch(const int* n, int batch, int precision, int warp_bytes, const int* rounds_for_n,
+               std::vector<PatDesc>& pats, std::vector<WorkItem>& items) {
+  const int cb = complex_bytes(precision);
+  auto groups = [&](int s, int h) { return 32 / lanes_for(2 * s, h, warp_bytes, cb); };
+  pats.resize(batch);
+  std::vector<WorkItem> ordered;
+  // count items
+  int64_t total = 0;
+  for (int b = 0; b < batch; ++b) {
+    const int nb = n[b];
+    if (nb < 2 || (nb & 1)) continue;
+    const int h = nb / 2;
+    const int R = rounds_for_n[nb];
+    for (int s = 1; s <= h; ++s) {
+      const int G = groups(s, h);
+      const int64_t cap = (int64_t)G * R;
+      total += (binom64(h, s) + cap - 1) / cap;
+    }
+  }
+  if (total > (int64_t)1 << 30) return fail(GBS_ENOMEM, "too many work items (%lld)", (long long)total);
+  ordered.resize((size_t)total);
+  // bucket key: N/2 (1..16) and rounds used (1..64) -> cost ~ rounds * N^3
+  const int KEYS = (kMaxN / 2 + 1) * 65;
+  std::vector<int64_t> bucket_count(KEYS, 0);
+  int64_t q = 0;
+  for (int b = 0; b < batch; ++b) {
+    const int nb = n[b];
+    PatDesc& d = pats[b];
+    d.n = nb;
+    d.item_begin = (int)q;
+    if (nb >= 2 && !(nb & 1)) {
+      const int h = nb / 2;
+      const int R = rounds_for_n[nb];
+      for (int s = 1; s <= h; ++s) {
+        const int G = groups(s, h);
+        const int64_t cnt = binom64(h, s);
+        const int64_t cap = (int64_t)G * R;
+        for (int64_t r0 = 0; r0 < cnt; r0 += cap) {
+          WorkItem w;
+          w.pat = b;
+          w.s = s;
+          w.rank0 = (int)r0;
+          w.count = (int)std::min<int64_t>(cap, cnt - r0);
+          w.part = (int)q;
+          w.pad[0] = w.pad[1] = w.pad[2] = 0;
+          ordered[(size_t)q++] = w;
+          const int rnds = (w.count + G - 1) / G;
+          bucket_count[s * 65 + std::min(rnds, 64)]++;
+
+        }
+      }
+    }
+    d.item_end = (int)q;
+  }
+  // schedule: descending cost = rounds * N^3 -> iterate keys by cost
+  std::vector<std::pair<int64_t, int>> keys;
+  for (int k = 0; k < KEYS; ++k)
+    if (bucket_count[k]) {
+      const int s = k / 65, r = k % 65;
+      const int64_t N = 2 * s;
+      keys.push_back(std::make_pair(-(int64_t)r * N * N * N, k));
+    }
+  std::sort(keys.begin(), keys.end());
+  std::vector<int64_t> start(KEYS, 0);
+  int64_t acc = 0;
+  for (auto& kv : keys) {
+    start[kv.second] = acc;
+    acc += bucket_count[kv.second];
+  }
+  items.resize((size_t)total);
+  for (int64_t i = 0; i < total; ++i) {
+    const WorkItem& w = ordered[(size_t)i];
+    const int G = groups(w.s, n[w.pat] / 2);
+    const int rnds = (w.count + G - 1) / G;
+    items[(size_t)start[w.s * 65 + std::min(rnds, 64)]++] = w;
+  }
+  return GBS_OK;
+}
+
+static cudaEvent_t g_time_start = nullptr, g_time_stop = nullptr;
+
+int device_sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+// ------------------------------------------------------------------------
+// the batched path shared by gbs_hafnian_batch and gbs_prob_batch
+// ------------------------------------------------------------------------
+int run_batch(const BatchArgs& a) {
+  cudaStream_t st = a.stream;
+  const int batch = a.batch;
+  if (batch == 0) return GBS_OK;
+  if (a.precision != GBS_FP64 && a.precision != GBS_MIXED)
+    return fail(GBS_EINVAL, "precision must be GBS_FP64 or GBS_MIXED");
+  int maxn = 0;
+  for (int b = 0; b < batch; ++b) {
+    if (a.n[b] < 0) return fail(GBS_EINVAL, "n[%d] = %d is negative", b, a.n[b]);
+    if (a.n[b] > GBS_MAX_N) return fail(GBS_ERANGE, "n[%d] = %d exceeds GBS_MAX_N", b, a.n[b]);
+    if (a.offs[b] < 0) return fail(GBS_EINVAL, "offs[%d] is negative", b);
+    maxn = std::max(maxn, a.n[b]);
+  }
+  // launch shape from the largest n (it dominates the cost); rounds per n
+  TuneCfg cfg = a.cfg_override ? *a.cfg_override : get_cfg(a.precision, maxn);
+  int rounds_for_n[kMaxN + 1];
+  for (int v = 0; v <= kMaxN; ++v)
+    rounds_for_n[v] = a.cfg_override ? a.cfg_override->rounds : get_cfg(a.precision, v).rounds;
+  HafLaunch L;
+  memset(&L, 0, sizeof(L));
+  if (!shape_fits(a.precision, cfg.warp_bytes, maxn))
+    return fail(GBS_EINVAL, "warp_bytes %d too small for n = %d", cfg.warp_bytes, maxn);
+
+  std::vector<PatDesc> pats;
+  std::vector<WorkItem> items;
+  int rc = plan_batch(a.n, batch, a.precision, cfg.warp_bytes, rounds_for_n, pats, items);
+  if (rc) return rc;
+  // source offsets / index lists
+  for (int b = 0; b < batch; ++b) {
+    PatDesc& d = pats[b];
+    if (a.mode == BatchArgs::HAFNIAN) {
+      d.src_off = a.offs[b];
+      d.idx_off = -1;
+      d.ld = a.n[b];
+    } else {
+      d.src_off = 0;
+      d.idx_off = a.offs[b];
+      d.ld = a.m;
+    }
+  }
+  const int64_t n_items = (int64_t)items.size();
+
+  // host-side checks and sizes of the inputs to stage
+  const bool src_dev = (a.mode == BatchArgs::HAFNIAN) ? is_device_ptr(a.src) : true;
+  const bool idx_dev = (a.mode == BatchArgs::PROB) ? is_device_ptr(a.idx) : true;
+  int64_t src_elems = 0, idx_elems = 0;
+  for (int b = 0; b < batch; ++b) {
+    if (a.mode == BatchArgs::HAFNIAN)
+      src_elems = std::max<int64_t>(src_elems, a.offs[b] + (int64_t)a.n[b] * a.n[b]);
+    else
+      idx_elems = std::max<int64_t>(idx_elems, a.offs[b] + a.n[b]);
+  }
+  if (a.mode == BatchArgs::PROB && !idx_dev) {
+    for (int b = 0; b < batch; ++b)
+      for (int i = 0; i < a.n[b]; ++i) {
+        const int v = a.idx[a.offs[b] + i];
+        if (v < 0 || v >= a.m)
+          return fail(GBS_ERANGE, "pattern %d index %d = %d is outside [0, %d)", b, i, v, a.m);
+      }
+  }
+  if (a.mode == BatchArgs::HAFNIAN && src_elems > 0 && a.src == nullptr)
+    return fail(GBS_EINVAL, "A_ri is null");
+  if (a.mode == BatchArgs::PROB && idx_elems > 0 && a.idx == nullptr)
+    return fail(GBS_EINVAL, "idx is null");
+
+  // upload block: pats | items | (idx) | (src)
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t pats_b = al(sizeof(PatDesc) * batch);
+  const size_t items_b = al(sizeof(WorkItem) * std::max<int64_t>(n_items, 1));
+  const size_t idx_b = (a.mode == BatchArgs::PROB && !idx_dev) ? al(sizeof(int) * idx_elems) : 0;
+  const size_t src_b = (a.mode == BatchArgs::HAFNIAN && !src_dev) ? al(16 * (size_t)src_elems) : 0;
+  const size_t up_b = pats_b + items_b + idx_b + src_b;
+  // device-only block: parts | counter | status | output staging
+  const size_t parts_b = al(sizeof(Partial) * std::max<int64_t>(n_items, 1));
+  const size_t ctr_b = 256;
+  const size_t status_b = al(sizeof(int) * batch);
+  const bool out_host = (a.out0 && !is_device_ptr(a.out0)) || (a.out1 && !is_device_ptr(a.out1)) ||
+                        (a.out2 && !is_device_ptr(a.out2)) || (a.out3 && !is_device_ptr(a.out3));
+  const size_t outs_b = out_host ? al(sizeof(double) * 5 * batch) : 0;
+  const size_t total_b = up_b + parts_b + ctr_b + status_b + outs_b;
+
+  void* host_stage = nullptr;
+  int slot = -1;
+  rc = pinned_acquire(up_b, &host_stage, &slot);
+  if (rc) return rc;
+  unsigned char* hs = (unsigned char*)host_stage;
+  memcpy(hs, pats.data(), sizeof(PatDesc) * batch);
+  if (n_items) memcpy(hs + pats_b, items.data(), sizeof(WorkItem) * n_items);
+  if (idx_b) memcpy(hs + pats_b + items_b, a.idx, sizeof(int) * idx_elems);
+  if (src_b) memcpy(hs + pats_b + items_b + idx_b, a.src, 16 * (size_t)src_elems);
+
+  void* dmem = nullptr;
+  cudaError_t e = scratch_alloc(&dmem, total_b, st);
+  if (e != cudaSuccess) {
+    pinned_release(slot, st);
+    cudaGetLastError();
+    return fail(GBS_ENOMEM, "device scratch of %zu bytes: %s", total_b, cudaGetErrorString(e));
+  }
+  unsigned char* dm = (unsigned char*)dmem;
+  PatDesc* d_pats = (PatDesc*)dm;
+  WorkItem* d_items = (WorkItem*)(dm + pats_b);
+  const int* d_idx = idx_b ? (const int*)(dm + pats_b + items_b) : a.idx;
+  const double* d_src = src_b ? (const double*)(dm + pats_b + items_b + idx_b) : a.src;
+  Partial* d_parts = (Partial*)(dm + up_b);
+  int* d_ctr = (int*)(dm + up_b + parts_b);
+  int* d_status = (int*)(dm + up_b + parts_b + ctr_b);
+  double* d_outs = outs_b ? (double*)(dm + up_b + parts_b + ctr_b + status_b) : nullptr;
+
+  int ret = GBS_OK;
+  do {
+    e = cudaMemcpyAsync(dm, hs, up_b, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) { ret = cuda_fail(e, "upload"); break; }
+    e = cudaMemsetAsync(d_ctr, 0, ctr_b + status_b, st);
+    if (e != cudaSuccess) { ret = cuda_fail(e, "memset"); break; }
+    if (n_items > 0) {
+      L.src = (a.mode == BatchArgs::HAFNIAN) ? d_src : a.B;
+      L.idx = (a.mode == BatchArgs::PROB) ? d_idx : nullptr;
+      L.pats = d_pats;
+      L.items = d_items;
+      L.n_items = (int)n_items;
+      L.m_bound = (a.mode == BatchArgs::PROB && idx_dev) ? a.m : 0;
+      L.counter = d_ctr;
+      L.status = d_status;
+      L.parts = d_parts;
+      L.warp_bytes = cfg.warp_bytes;
+      const int smem = cfg.warps_per_block * cfg.warp_bytes;
+      int per_sm = max_blocks_per_sm(a.precision, cfg.warps_per_block, smem);
+      if (per_sm < 1) { ret = fail(GBS_EINVAL, "launch shape does not fit an SM"); break; }
+      int blocks = device_sm_count() * per_sm;
+      const int64_t need = (n_items + cfg.warps_per_block - 1) / cfg.warps_per_block;
+      if (need < blocks) blocks = (int)need;
+      const bool timed = g_time_start && g_time_stop && !a.cfg_override;
+      if (timed) cudaEventRecord(g_time_start, st);
+      e = launch_haf_subsets(L, a.precision, blocks, cfg.warps_per_block, st);
+      if (e != cudaSuccess) { ret = cuda_fail(e, "subset kernel launch"); break; }
+      if (timed) cudaEventRecord(g_time_stop, st);
+    }
+    FinalizeLaunch F;
+    memset(&F, 0, sizeof(F));
+    F.pats = d_pats;
+    F.parts = d_parts;
+    F.idx = (a.mode == BatchArgs::PROB) ? d_idx : nullptr;
+    F.status = d_status;
+    F.batch = batch;
+    F.precision = a.precision;
+    F.log_norm = a.log_norm_dev;
+    double* o[4] = {a.out0, a.out1, a.out2, a.out3};
+    double* dst[4];
+    for (int i = 0; i < 4; ++i) dst[i] = o[i];
+    if (out_host) {
+      // all outputs go to device staging: p | logp | haf (2) | err
+      dst[0] = a.out0 ? d_outs : nullptr;
+      dst[1] = a.out1 ? d_outs + batch : nullptr;
+      dst[2] = a.out2 ? d_outs + 2 * batch : nullptr;
+      dst[3] = a.out3 ? d_outs + 4 * batch : nullptr;
+    }
+    if (a.mode == BatchArgs::PROB) {
+      F.p_out = dst[0];
+      F.logp_out = dst[1];
+      F.haf_out = dst[2];
+      F.err_out = dst[3];
+    } else {
+      F.haf_out = dst[2];
+      F.kappa_out = dst[3];
+    }
+    e = launch_finalize(F, st);
+    if (e != cudaSuccess) { ret = cuda_fail(e, "finalize launch"); break; }
+    if (out_host) {
+      const size_t sz[4] = {sizeof(double) * batch, sizeof(double) * batch, 2 * sizeof(double) * batch,
+                            sizeof(double) * batch};
+      for (int i = 0; i < 4 && ret == GBS_OK; ++i)
+        if (o[i]) {
+          e = cudaMemcpyAsync(o[i], dst[i], sz[i], cudaMemcpyDefault, st);
+          if (e != cudaSuccess) ret = cuda_fail(e, "result copy");
+        }
+    }
+  } while (0);
+  pinned_release(slot, st);
+  e = scratch_free(dmem, st);
+  if (e != cudaSuccess && ret == GBS_OK) ret = cuda_fail(e, "scratch free");
+  if (ret == GBS_OK && out_host) {
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) ret = cuda_fail(e, "stream synchronize");
+  }
+  return ret;
+}
+
+}  // namespace gbs
+
+using namespace gbs;
+
+// ------------------------------------------------------------------------
+// kernel matrix
+// ------------------------------------------------------------------------
+extern "C" int gbs_build_kernel(const double* U_ri, const double* r, int m, void* stream,
+                                gbs_kernel** out) {
+  clear_error();
+  if (!U_ri || !r || !out) return fail(GBS_EINVAL, "null argument");
+  if (m < 1) return fail(GBS_EINVAL, "m = %d must be >= 1", m);
+  *out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  gbs_kernel* k = new (std::nothrow) gbs_kernel();
+  if (!k) return fail(GBS_ENOMEM, "host allocation");
+  cudaError_t e = cudaGetDevice(&k->device);
+  if (e != cudaSuccess) { delete k; return cuda_fail(e, "cudaGetDevice"); }
+  k->m = m;
+  const size_t mm = (size_t)m * m;
+  e = cudaMalloc(&k->B, 16 * mm);
+  if (e != cudaSuccess) { delete k; cudaGetLastError(); return fail(GBS_ENOMEM, "B: %s", cudaGetErrorString(e)); }
+  e = cudaMalloc(&k->dscal, 256);
+  if (e != cudaSuccess) { cudaFree(k->B); delete k; cudaGetLastError(); return fail(GBS_ENOMEM, "scalars"); }
+  // stage U and r on the device when they are host memory
+  const bool u_dev = is_device_ptr(U_ri), r_dev = is_device_ptr(r);
+  void* tmp = nullptr;
+  const size_t u_b = u_dev ? 0 : 16 * mm, r_b = r_dev ? 0 : 8 * (size_t)m;
+  const size_t t_b = 8 * (size_t)m;
+  e = scratch_alloc(&tmp, u_b + r_b + t_b, st);
+  if (e != cudaSuccess) {
+    cudaFree(k->B); cudaFree(k->dscal); delete k; cudaGetLastError();
+    return fail(GBS_ENOMEM, "staging: %s", cudaGetErrorString(e));
+  }
+  unsigned char* tb = (unsigned char*)tmp;
+  const double* dU = U_ri;
+  const double* dr = r;
+  int ret = GBS_OK;
+  if (!u_dev) {
+    e = cudaMemcpyAsync(tb, U_ri, u_b, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) ret = cuda_fail(e, "U upload");
+    dU = (const double*)tb;
+  }
+  if (ret == GBS_OK && !r_dev) {
+    e = cudaMemcpyAsync(tb + u_b, r, r_b, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) ret = cuda_fail(e, "r upload");
+    dr = (const double*)(tb + u_b);
+  }
+  if (ret == GBS_OK) {
+    e = launch_build_B(dU, dr, m, k->B, k->dscal, (double*)(tb + u_b + r_b), st);
+    if (e != cudaSuccess) ret = cuda_fail(e, "build_B launch");
+  }
+  scratch_free(tmp, st);
+  if (ret == GBS_OK && (!u_dev || !r_dev)) {
+    // host sources were copied from pageable memory; nothing else to wait for
+  }
+  if (ret != GBS_OK) {
+    cudaStreamSynchronize(st);
+    cudaFree(k->B);
+    cudaFree(k->dscal);
+    delete k;
+    return ret;
+  }
+  *out = k;
+  return GBS_OK;
+}
+
+extern "C" int gbs_free_kernel(gbs_kernel* k) {
+  clear_error();
+  if (!k) return GBS_OK;
+  cudaError_t e1 = cudaFree(k->B);
+  cudaError_t e2 = cudaFree(k->dscal);
+  delete k;
+  if (e1 != cudaSuccess) return cuda_fail(e1, "cudaFree(B)");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFree(scalars)");
+  return GBS_OK;
+}
+
+extern "C" int gbs_kernel_info(const gbs_kernel* k, int* m, double* log_norm) {
+  clear_error();
+  if (!k) return fail(GBS_EINVAL, "null kernel");
+  if (m) *m = k->m;
+  if (log_norm) {
+    cudaError_t e = cudaMemcpy(log_norm, k->dscal, sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "log_norm copy");
+  }
+  return GBS_OK;
+}
+
+extern "C" int gbs_kernel_copy_B(const gbs_kernel* k, double* dst, void* stream) {
+  clear_error();
+  if (!k || !dst) return fail(GBS_EINVAL, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool dev = is_device_ptr(dst);
+  cudaError_t e = cudaMemcpyAsync(dst, k->B, 16 * (size_t)k->m * k->m,
+                                  dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail(e, "B copy");
+  if (!dev) {
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  }
+  return GBS_OK;
+}
+
+// ------------------------------------------------------------------------
+// batches
+// ------------------------------------------------------------------------
+extern "C" int gbs_hafnian_batch(const double* A_ri, const int* n, const int64_t* offs, int batch,
+                                 int precision, void* stream, double* haf_ri_out, double* kappa_out) {
+  clear_error();
+  if (batch < 0) return fail(GBS_EINVAL, "batch = %d is negative", batch);
+  if (batch > 0 && (!n || !offs || !haf_ri_out)) return fail(GBS_EINVAL, "null argument");
+  BatchArgs a;
+  a.mode = BatchArgs::HAFNIAN;
+  a.src = A_ri;
+  a.n = n;
+  a.offs = offs;
+  a.batch = batch;
+  a.precision = precision;
+  a.stream = (cudaStream_t)stream;
+  a.out2 = haf_ri_out;
+  a.out3 = kappa_out;
+  return run_batch(a);
+}
+
+extern "C" int gbs_prob_batch(const gbs_kernel* k, const int* idx, const int* n, const int64_t* offs,
+                              int batch, int precision, void* stream, double* p_out, double* logp_out,
+                              double* haf_ri_out, double* err_est_out) {
+  clear_error();
+  if (!k) return fail(GBS_EINVAL, "null kernel");
+  if (batch < 0) return fail(GBS_EINVAL, "batch = %d is negative", batch);
+  if (batch > 0 && (!n || !offs)) return fail(GBS_EINVAL, "null argument");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != k->device) return fail(GBS_EINVAL, "kernel lives on device %d, current is %d", k->device, dev);
+  BatchArgs a;
+  a.mode = BatchArgs::PROB;
+  a.B = k->B;
+  a.m = k->m;
+  a.log_norm_dev = k->dscal;
+  a.idx = idx;
+  a.n = n;
+  a.offs = offs;
+  a.batch = batch;
+  a.precision = precision;
+  a.stream = (cudaStream_t)stream;
+  a.out0 = p_out;
+  a.out1 = logp_out;
+  a.out2 = haf_ri_out;
+  a.out3 = err_est_out;
+  return run_batch(a);
+}
+
+extern "C" int gbs_set_timing_events(void* start, void* stop) {
+  clear_error();
+  g_time_start = (cudaEvent_t)start;
+  g_time_stop = (cudaEvent_t)stop;
+  return GBS_OK;
+}
+
+extern "C" const char* gbs_last_error(void) { return t_err.c_str(); }

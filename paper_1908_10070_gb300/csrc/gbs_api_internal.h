@@ -1,0 +1,66 @@
+// Host-side internals shared by the C ABI, the serving loop and the autotuner.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "gbs_internal.cuh"
+
+struct gbs_kernel {
+  int device = 0;
+  int m = 0;
+  double* B = nullptr;      // m*m complex128, device
+  double* dscal = nullptr;  // [0] = sum_i log cosh r_i, device
+};
+
+namespace gbs {
+
+// Launch shape of the subset kernel.
+struct TuneCfg {
+  int warps_per_block = 6;
+  int warp_bytes = 36864;  // dynamic shared memory per warp
+  int rounds = 4;          // lane-group rounds per work item (subsets per item = G * rounds)
+};
+
+struct BatchArgs {
+  enum Mode { HAFNIAN, PROB } mode = PROB;
+  const double* src = nullptr;  // Hafnian mode: concatenated matrices
+  const double* B = nullptr;    // probability mode: kernel matrix (device)
+  int m = 0;
+  const double* log_norm_dev = nullptr;
+  const int* idx = nullptr;
+  const int* n = nullptr;
+  const int64_t* offs = nullptr;
+  int batch = 0;
+  int precision = GBS_FP64;
+  cudaStream_t stream = nullptr;
+  double* out0 = nullptr;  // p
+  double* out1 = nullptr;  // log p
+  double* out2 = nullptr;  // Haf (2 per entry)
+  double* out3 = nullptr;  // err estimate (probabilities) or kappa (Hafnians)
+  const TuneCfg* cfg_override = nullptr;
+};
+
+int fail(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+bool is_device_ptr(const void* p);
+cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st);
+cudaError_t scratch_free(void* p, cudaStream_t st);
+int pinned_acquire(size_t bytes, void** ptr, int* slot);
+void pinned_release(int slot, cudaStream_t st);
+
+TuneCfg default_cfg(int precision, int n);
+TuneCfg get_cfg(int precision, int n);
+void set_cfg(int precision, int n, const TuneCfg& c);
+int complex_bytes(int precision);
+bool shape_fits(int precision, int warp_bytes, int maxn);
+int plan_batch(const int* n, int batch, int precision, int warp_bytes, const int* rounds_for_n,
+               std::vector<PatDesc>& pats, std::vector<WorkItem>& items);
+int device_sm_count();
+int run_batch(const BatchArgs& a);
+
+}  // namespace gbs

@@ -1,0 +1,109 @@
+// Internal types shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gbs.h"
+
+namespace gbs {
+
+// One matrix of a batch: the n x n matrix whose (i, j) entry is
+// src[src_off + row(i) * ld + row(j)], row(i) = idx[idx_off + i] (or i when
+// idx_off < 0). For probabilities src is B and the rows are the pattern's mode
+// list x, which is the gather B_x(i, j) = B(x_i, x_j) of Sec. 3.2.
+struct PatDesc {
+  int64_t src_off;  // complex-element offset of the source matrix
+  int64_t idx_off;  // offset of the index list, or -1 for the identity
+  int ld;           // leading dimension of the source
+  int n;            // order (photon number)
+  int item_begin;   // this matrix's work items are parts[item_begin, item_end)
+  int item_end;
+};
+
+// A run of `count` consecutive colex ranks among the C(h, s) subsets with s
+// pairs of one matrix. All subsets of an item have the same order N = 2s.
+struct WorkItem {
+  int pat;
+  int s;
+  int rank0;
+  int count;
+  int part;  // slot of this item's partial sum
+  int pad[3];
+};
+
+// Partial sum of one work item: sum (-1)^{h-|S|} f(X A_S) as a double-double
+// complex number, plus sum |f|_1 for the cancellation ratio.
+struct Partial {
+  double re_hi, re_lo, im_hi, im_lo, kappa, pad[3];
+};
+
+constexpr int kMaxN = GBS_MAX_N;
+constexpr int kMaxH = kMaxN / 2;
+constexpr int kWarpHeaderBytes = 128;  // per-warp index-list buffer (32 ints)
+
+// Power-trace schedule for h = n/2 (see haf_subsets.cu): s baby powers, then
+// giant powers R_{3m}; nbuf packed symmetric matrices are live at once.
+__host__ __device__ inline int sched_s(int h) { return h <= 2 ? 1 : (h <= 4 ? 2 : 3); }
+__host__ __device__ inline int sched_nbuf(int h) {
+  return h <= 2 ? 1 : (h <= 4 ? 2 : (h <= 6 ? 3 : (h <= 9 ? 4 : 5)));
+}
+
+// Shared-memory bytes of one lane group's region for subsets of order N (and
+// half photon number h) with complex elements of `cbytes` bytes: nbuf packed
+// upper triangles of N(N+1)/2 entries, the power traces and exponential-series
+// coefficients (kMaxH + 1 each) and N row indices.
+__host__ __device__ inline int group_bytes(int N, int h, int cbytes) {
+  const int P = N * (N + 1) / 2;
+  const int bytes = (sched_nbuf(h) * P + 2 * (kMaxH + 1)) * cbytes + N * 4;
+  return (bytes + 15) & ~15;
+}
+
+// Lane-group size L (a power of two) for subsets of order N of a matrix of
+// order 2h: the smallest L whose 32/L groups fit `warp_bytes`; 0 if none does.
+__host__ __device__ inline int lanes_for(int N, int h, int warp_bytes, int cbytes) {
+  const int gb = group_bytes(N, h, cbytes);
+  for (int L = 1; L <= 32; L <<= 1)
+    if (kWarpHeaderBytes + (32 / L) * gb <= warp_bytes) return L;
+  return 0;
+}
+
+struct HafLaunch {
+  const double* src;       // interleaved complex source matrices
+  const int* idx;          // index lists (may be null when every idx_off < 0)
+  const PatDesc* pats;
+  const WorkItem* items;   // in schedule order
+  int n_items;
+  int m_bound;             // index lists must be < m_bound (0 = no check)
+  int* counter;            // work-queue head, zero before launch
+  int* status;             // per-pattern flag, set to 1 on an out-of-range index
+  Partial* parts;
+  int warp_bytes;          // dynamic shared memory per warp
+};
+
+struct FinalizeLaunch {
+  const PatDesc* pats;
+  const Partial* parts;
+  const int* idx;
+  const int* status;
+  int batch;
+  int precision;
+  const double* log_norm;  // device scalar sum_i log cosh r_i, or null (Hafnians only)
+  double* p_out;
+  double* logp_out;
+  double* haf_out;
+  double* err_out;         // relative error estimate (probabilities)
+  double* kappa_out;       // kappa (Hafnians)
+};
+
+// Defined in haf_subsets.cu
+cudaError_t launch_haf_subsets(const HafLaunch& L, int precision, int blocks, int warps_per_block,
+                               cudaStream_t st);
+cudaError_t launch_finalize(const FinalizeLaunch& F, cudaStream_t st);
+int max_blocks_per_sm(int precision, int warps_per_block, int smem_bytes);
+
+// Defined in build_b.cu
+cudaError_t launch_build_B(const double* U, const double* r, int m, double* B, double* log_norm,
+                           double* t_scratch, cudaStream_t st);
+
+}  // namespace gbs

@@ -1,0 +1,458 @@
+// Subset-sum Hafnian kernels (FP64 and mixed FP32 paths) and the per-pattern
+// finalisation.
+//
+// Method (Sec. 2.3 cites it for the O(n^3 2^{n/2}) cost; Bjorklund, Gupt,
+// Quesada): for an n x n symmetric A, n = 2h, pairs {2i, 2i+1},
+//     Haf(A) = sum_{S subset of [h]} (-1)^{h-|S|} f(X A_S),
+//     f(M)   = [x^h] exp( sum_{k=1..h} tr(M^k) x^k / (2k) ),
+// where A_S keeps the rows/columns of the pairs in S and X swaps the two
+// members of every pair. Per subset (order N = 2|S|) the kernel
+//   1. gathers A_S into shared memory (packed upper triangle, zero diagonal),
+//   2. forms the power traces tr((X A_S)^k), k = 1..h, through the symmetric
+//      matrices R_k = A_S (X A_S)^{k-1}:  (X A_S)^k = X R_k,
+//      R_{a+b} = R_a X R_b  (symmetric, so only the upper triangle is
+//      computed), tr(X R_k) = 2 sum_t R_k[2t][2t+1] and
+//      tr(X R_a X R_b) = sum_{i,j} R_a[i][j] R_b[i^1][j^1];
+//      baby powers R_1..R_s and giant powers R_{3m} cover k = 1..h with at
+//      most five products for h <= 15,
+//   3. expands e = exp(sum_k tr_k x^k / (2k)): e_k = (1/(2k)) sum_j tr_j e_{k-j},
+//      f = e_h,
+//   4. adds (-1)^{h-|S|} f to a compensated (double-double or float-float)
+//      accumulator.
+// Power traces by products keep the per-term rounding error near the unit
+// roundoff; a similarity reduction (Hessenberg form and a characteristic
+// polynomial recurrence) was measured to lose about an order of magnitude per
+// term, which the cancellation of the signed sum (up to ~1e7 at n = 30)
+// turns into errors above 1e-10.
+//
+// GB300 mapping. FP64 issue costs the same per warp instruction whatever the
+// active mask, so all 32 lanes must do useful FP64 work: a warp works on
+// subsets of one order N only (uniform control flow), split into G = 32/L lane
+// groups, each group owning one subset's matrices in shared memory and
+// spreading the output entries of each product (and the terms of each trace)
+// evenly over its L lanes. Integer work (unranking, packed-triangle
+// addressing) runs on other pipes beside the FP64 pipe. Work items are taken
+// from a global queue by persistent warps; each item writes one partial sum,
+// and partials are added per pattern in a fixed order, so results do not
+// depend on scheduling.
+#include <math.h>
+
+#include "gbs_internal.cuh"
+
+namespace gbs {
+namespace {
+
+template <typename T> struct V2t;
+template <> struct V2t<double> { typedef double2 type; };
+template <> struct V2t<float> { typedef float2 type; };
+template <typename T> using C2 = typename V2t<T>::type;
+
+template <typename T> __device__ __forceinline__ C2<T> mk(T x, T y) {
+  C2<T> r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+// acc + a*b (4 fused multiply-adds)
+template <typename T> __device__ __forceinline__ C2<T> cfma(C2<T> a, C2<T> b, C2<T> acc) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+  return acc;
+}
+// acc - a*b
+template <typename T> __device__ __forceinline__ C2<T> cfms(C2<T> a, C2<T> b, C2<T> acc) {
+  acc.x = fma(-a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(-a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+  return acc;
+}
+template <typename T> __device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
+  C2<T> r;
+  r.x = fma(a.x, b.x, -a.y * b.y);
+  r.y = fma(a.x, b.y, a.y * b.x);
+  return r;
+}
+
+// Compensated accumulation (Knuth two-sum, Dekker fast two-sum).
+template <typename T> struct Comp { T hi, lo; };
+template <typename T> __device__ __forceinline__ void comp_add(Comp<T>& a, T v) {
+  const T s = a.hi + v;
+  const T bb = s - a.hi;
+  const T e = (a.hi - (s - bb)) + (v - bb);
+  const T lo = a.lo + e;
+  const T h2 = s + lo;
+  a.lo = lo - (h2 - s);
+  a.hi = h2;
+}
+__device__ __forceinline__ void dd_add(double& ahi, double& alo, double bhi, double blo) {
+  double s = ahi + bhi;
+  double bb = s - ahi;
+  double e = (ahi - (s - bb)) + (bhi - bb);
+  double t = alo + blo;
+  double tb = t - alo;
+  double f = (alo - (t - tb)) + (blo - tb);
+  e += t;
+  double h = s + e;
+  e = e - (h - s);
+  e += f;
+  double h2 = h + e;
+  alo = e - (h2 - h);
+  ahi = h2;
+}
+
+struct Tables {
+  int binom[kMaxH + 1][kMaxH + 1];  // C(a, b), a, b <= 16
+  double inv2k[kMaxH + 1];          // 1 / (2k)
+};
+
+// Position of entry (r, c) of a symmetric N x N matrix stored as its packed
+// upper triangle, rows in order: row r holds columns r..N-1.
+__device__ __forceinline__ int tri_off(int r, int N) { return r * N - ((r * (r - 1)) >> 1); }
+__device__ __forceinline__ int tri_pos(int r, int c, int N) {
+  const int lo = min(r, c), hi = max(r, c);
+  return tri_off(lo, N) + hi - lo;
+}
+// Advance the packed-upper coordinate (i, j) by `step` entries.
+__device__ __forceinline__ void tri_advance(int& i, int& j, int step, int N) {
+  j += step;
+  while (j >= N && i < N) {
+    const int over = j - N;
+    ++i;
+    j = i + over;
+  }
+}
+
+// Sum over the L lanes of a group (groups are aligned blocks of L lanes).
+template <typename T>
+__device__ __forceinline__ C2<T> group_sum(C2<T> v, int L) {
+  for (int off = L >> 1; off > 0; off >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
+  }
+  return v;
+}
+
+// dst = Ra X Rb (upper triangle), X swapping 2t <-> 2t+1.
+template <typename T>
+__device__ __forceinline__ void sym_prod(C2<T>* __restrict__ dst, const C2<T>* __restrict__ Ra,
+                                         const C2<T>* __restrict__ Rb, int N, int P, int l, int L) {
+  int i = 0, j = l;
+  tri_advance(i, j, 0, N);
+  for (int e = l; e < P; e += L) {
+    C2<T> acc = mk<T>(T(0), T(0));
+    const int oi = tri_off(i, N);
+    for (int k = 0; k < N; ++k) {
+      const C2<T> a = (k >= i) ? Ra[oi + k - i] : Ra[tri_off(k, N) + i - k];
+      const C2<T> b = Rb[tri_pos(k ^ 1, j, N)];
+      acc = cfma<T>(a, b, acc);
+    }
+    dst[e] = acc;
+    tri_advance(i, j, L, N);
+  }
+}
+
+// tr(X Ra) = 2 sum_t Ra[2t][2t+1] (partial over this lane's pairs).
+template <typename T>
+__device__ __forceinline__ C2<T> tr1_part(const C2<T>* __restrict__ Ra, int N, int l, int L) {
+  C2<T> acc = mk<T>(T(0), T(0));
+  for (int t = l; 2 * t < N; t += L) {
+    const C2<T> v = Ra[tri_off(2 * t, N) + 1];
+    acc.x += v.x;
+    acc.y += v.y;
+  }
+  acc.x *= T(2);
+  acc.y *= T(2);
+  return acc;
+}
+
+// tr(X Ra X Rb) = sum_{i,j} Ra[i][j] Rb[i^1][j^1] over the packed upper
+// triangle, off-diagonal entries counted twice (partial over this lane).
+template <typename T>
+__device__ __forceinline__ C2<T> tr2_part(const C2<T>* __restrict__ Ra, const C2<T>* __restrict__ Rb,
+                                          int N, int P, int l, int L) {
+  C2<T> acc = mk<T>(T(0), T(0)), dg = mk<T>(T(0), T(0));
+  int i = 0, j = l;
+  tri_advance(i, j, 0, N);
+  for (int e = l; e < P; e += L) {
+    const C2<T> a = Ra[e];
+    const C2<T> b = Rb[tri_pos(i ^ 1, j ^ 1, N)];
+    const bool diag = (i == j);
+    C2<T> cur = diag ? dg : acc;  // selects, not a divergent branch
+    cur = cfma<T>(a, b, cur);
+    dg = diag ? cur : dg;
+    acc = diag ? acc : cur;
+    tri_advance(i, j, L, N);
+  }
+  acc.x = fma(T(2), acc.x, dg.x);
+  acc.y = fma(T(2), acc.y, dg.y);
+  return acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) {
+  typedef C2<T> C;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ Tables tab;
+  if (threadIdx.x == 0) {
+    for (int a = 0; a <= kMaxH; ++a)
+      for (int b = 0; b <= kMaxH; ++b)
+        tab.binom[a][b] = (b == 0) ? 1 : (a == 0 ? 0 : tab.binom[a - 1][b - 1] + tab.binom[a - 1][b]);
+    for (int k = 0; k <= kMaxH; ++k) tab.inv2k[k] = (k == 0) ? 0.0 : 1.0 / (2.0 * k);
+  }
+  __syncthreads();
+
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int cb = (int)sizeof(C);
+  unsigned char* wbase = smem + (size_t)warp * P.warp_bytes;
+  int* xs = reinterpret_cast<int*>(wbase);
+  unsigned char* gbase = wbase + kWarpHeaderBytes;
+  const double2* src2 = reinterpret_cast<const double2*>(P.src);
+
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(P.counter, 1);
+    it = __shfl_sync(FULL, it, 0);
+    if (it >= P.n_items) break;
+    const WorkItem w = P.items[it];
+    const PatDesc d = P.pats[w.pat];
+    const int n = d.n, h = n >> 1, s = w.s, N = 2 * s;
+    const int NP = N * (N + 1) / 2;
+    const int L = lanes_for(N, h, P.warp_bytes, cb);
+    const int G = 32 / L;
+    const int g = lane / L, l = lane - g * L;
+    const int sb = sched_s(h);
+
+    if (lane < n) {
+      int v = (d.idx_off >= 0) ? P.idx[d.idx_off + lane] : lane;
+      if (P.m_bound > 0 && (v < 0 || v >= P.m_bound)) {
+        P.status[w.pat] = 1;
+        v = 0;
+      }
+      xs[lane] = v;
+    }
+    __syncwarp();
+
+    C* buf = reinterpret_cast<C*>(gbase + (size_t)g * group_bytes(N, h, cb));
+    C* pk = buf + sched_nbuf(h) * NP;  // power traces tr((X A_S)^k), k = 1..h
+    C* ek = pk + (kMaxH + 1);          // exponential-series coefficients
+    int* rowidx = reinterpret_cast<int*>(ek + (kMaxH + 1));
+    const double2* srcp = src2 + d.src_off;
+
+    Comp<T> acc_re = {T(0), T(0)}, acc_im = {T(0), T(0)};
+    T kap = T(0);
+    const int rounds = (w.count + G - 1) / G;
+
+    for (int rd = 0; rd < rounds; ++rd) {
+      const int jsub = rd * G + g;
+      const bool active = jsub < w.count;
+      // -- unrank the subset (colex): rank = sum_i C(c_i, i), c_1 < ... < c_s
+      {
+        int r = w.rank0 + (active ? jsub : 0);
+        int c = h - 1;
+        for (int i = s; i >= 1; --i) {
+          while (tab.binom[c][i] > r) --c;
+          r -= tab.binom[c][i];
+          const int t = i - 1;
+          if ((t % L) == l) {
+            rowidx[2 * t] = xs[2 * c];
+            rowidx[2 * t + 1] = xs[2 * c + 1];
+          }
+          --c;
+        }
+      }
+      __syncwarp();
+      // -- R_1 = A_S (packed upper triangle). Its diagonal is set to zero: no
+      //    perfect matching uses V(i, i), and a zero diagonal lowers the
+      //    cancellation of the signed sum (collision entries B(x_i, x_i) with
+      //    i != j are off the diagonal of B_x and are kept).
+      {
+        int i = 0, j = l;
+        tri_advance(i, j, 0, N);
+        for (int e = l; e < NP; e += L) {
+          const double2 v = (i == j) ? make_double2(0.0, 0.0)
+                                     : __ldg(srcp + (int64_t)rowidx[i] * d.ld + rowidx[j]);
+          buf[e] = mk<T>((T)v.x, (T)v.y);
+          tri_advance(i, j, L, N);
+        }
+      }
+      __syncwarp();
+      // -- power traces: baby powers R_1..R_sb in buffers 0..sb-1
+      for (int b = 2; b <= sb; ++b) {
+        sym_prod<T>(buf + (b - 1) * NP, buf + (b - 2) * NP, buf, N, NP, l, L);
+        __syncwarp();
+      }
+      for (int k = 1; k <= min(sb, h); ++k) {
+        const C t = group_sum<T>(tr1_part<T>(buf + (k - 1) * NP, N, l, L), L);
+        if (l == 0) pk[k] = t;
+      }
+      for (int k = sb + 1; k <= min(2 * sb, h); ++k) {
+        const C t = group_sum<T>(tr2_part<T>(buf + (sb - 1) * NP, buf + (k - sb - 1) * NP, N, NP, l, L), L);
+        if (l == 0) pk[k] = t;
+      }
+      // giant powers R_{m sb}, m >= 2, alternating between buffers sb and sb+1
+      {
+        const C* prev = buf + (sb - 1) * NP;
+        int slot = 0;
+        for (int m = 2; m * sb + 1 <= h; ++m) {
+          C* cur = buf + (sb + slot) * NP;
+          sym_prod<T>(cur, prev, buf + (sb - 1) * NP, N, NP, l, L);
+          __syncwarp();
+          for (int b = 1; b <= sb && m * sb + b <= h; ++b) {
+            const C t = group_sum<T>(tr2_part<T>(cur, buf + (b - 1) * NP, N, NP, l, L), L);
+            if (l == 0) pk[m * sb + b] = t;
+          }
+          prev = cur;
+          slot ^= 1;
+        }
+      }
+      __syncwarp();
+      // -- exponential series and signed accumulation (one lane per group)
+      if (l == 0) {
+        ek[0] = mk<T>(T(1), T(0));
+        for (int k = 1; k <= h; ++k) {
+          C a = mk<T>(T(0), T(0));
+          for (int j = 1; j <= k; ++j) a = cfma<T>(pk[j], ek[k - j], a);
+          const T c = (T)tab.inv2k[k];
+          ek[k] = mk<T>(a.x * c, a.y * c);
+        }
+        const C f = ek[h];
+        if (active) {
+          const T sg = ((h - s) & 1) ? T(-1) : T(1);
+          comp_add<T>(acc_re, sg * f.x);
+          comp_add<T>(acc_im, sg * f.y);
+          kap += fabs(f.x) + fabs(f.y);
+        }
+      }
+      __syncwarp();
+    }
+
+    // warp reduction of the group accumulators (fixed butterfly: deterministic)
+    double rh = (double)acc_re.hi, rl = (double)acc_re.lo;
+    double ih = (double)acc_im.hi, il = (double)acc_im.lo;
+    double kp = (double)kap;
+    for (int off = 16; off > 0; off >>= 1) {
+      const double orh = __shfl_xor_sync(FULL, rh, off), orl = __shfl_xor_sync(FULL, rl, off);
+      const double oih = __shfl_xor_sync(FULL, ih, off), oil = __shfl_xor_sync(FULL, il, off);
+      kp += __shfl_xor_sync(FULL, kp, off);
+      dd_add(rh, rl, orh, orl);
+      dd_add(ih, il, oih, oil);
+    }
+    if (lane == 0) {
+      Partial pr;
+      pr.re_hi = rh;
+      pr.re_lo = rl;
+      pr.im_hi = ih;
+      pr.im_lo = il;
+      pr.kappa = kp;
+      pr.pad[0] = pr.pad[1] = pr.pad[2] = 0.0;
+      P.parts[w.part] = pr;
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void finalize_kernel(const FinalizeLaunch F) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < F.batch; b += gridDim.x * blockDim.x) {
+    const PatDesc d = F.pats[b];
+    const int n = d.n;
+    double rh = 0, rl = 0, ih = 0, il = 0, K = 0;
+    if (n & 1) {
+      // odd n: no perfect matching, Haf = 0 (Sec. 3.1: P_n = 0 for odd n)
+    } else if (n == 0) {
+      rh = 1.0;
+      K = 1.0;
+    } else {
+      for (int q = d.item_begin; q < d.item_end; ++q) {
+        const Partial pr = F.parts[q];
+        dd_add(rh, rl, pr.re_hi, pr.re_lo);
+        dd_add(ih, il, pr.im_hi, pr.im_lo);
+        K += pr.kappa;
+      }
+    }
+    const bool bad = F.status != nullptr && F.status[b] != 0;
+    const double hr = rh + rl, hi = ih + il;
+    const double mod = hypot(hr, hi);
+    const double kappa = (mod > 0.0) ? K / mod : (K > 0.0 ? INFINITY : 0.0);
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    if (F.haf_out) {
+      F.haf_out[2 * b] = bad ? nan : hr;
+      F.haf_out[2 * b + 1] = bad ? nan : hi;
+    }
+    if (F.kappa_out) F.kappa_out[b] = bad ? nan : kappa;
+    if (F.p_out || F.logp_out || F.err_out) {
+      // sum_j log s_j!: the c-th occurrence of a mode contributes log c
+      double log_fact = 0.0;
+      if (d.idx_off >= 0) {
+        for (int i = 0; i < n; ++i) {
+          const int xi = F.idx[d.idx_off + i];
+          int c = 1;
+          for (int j = 0; j < i; ++j) c += (F.idx[d.idx_off + j] == xi);
+          if (c > 1) log_fact += log((double)c);
+        }
+      }
+      const double L = F.log_norm ? *F.log_norm : 0.0;
+      const double logp = (mod > 0.0) ? 2.0 * log(mod) - log_fact - L : -INFINITY;
+      const double u = (F.precision == GBS_FP64) ? 0x1p-53 : 0x1p-24;
+      if (F.p_out) F.p_out[b] = bad ? nan : ((mod > 0.0) ? exp(logp) : 0.0);
+      if (F.logp_out) F.logp_out[b] = bad ? nan : logp;
+      if (F.err_out) F.err_out[b] = bad ? nan : (double)(n > 0 ? n : 1) * u * kappa;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_haf_subsets(const HafLaunch& L, int precision, int blocks, int warps_per_block,
+                               cudaStream_t st) {
+  const size_t smem = (size_t)warps_per_block * L.warp_bytes;
+  cudaError_t e;
+  if (precision == GBS_FP64) {
+    e = cudaFuncSetAttribute(haf_subsets_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    haf_subsets_kernel<double><<<blocks, warps_per_block * 32, smem, st>>>(L);
+  } else {
+    e = cudaFuncSetAttribute(haf_subsets_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    haf_subsets_kernel<float><<<blocks, warps_per_block * 32, smem, st>>>(L);
+  }
+  return cudaGetLastError();
+}
+
+int max_blocks_per_sm(int precision, int warps_per_block, int smem_bytes) {
+  int nb = 0;
+  cudaError_t e;
+  if (precision == GBS_FP64) {
+    cudaFuncSetAttribute(haf_subsets_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem_bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, haf_subsets_kernel<double>,
+                                                      warps_per_block * 32, smem_bytes);
+  } else {
+    cudaFuncSetAttribute(haf_subsets_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem_bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, haf_subsets_kernel<float>,
+                                                      warps_per_block * 32, smem_bytes);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nb;
+}
+
+cudaError_t launch_finalize(const FinalizeLaunch& F, cudaStream_t st) {
+  if (F.batch <= 0) return cudaSuccess;
+  const int threads = 128;
+  int blocks = (F.batch + threads - 1) / threads;
+  if (blocks > 4096) blocks = 4096;
+  finalize_kernel<<<blocks, threads, 0, st>>>(F);
+  return cudaGetLastError();
+}
+
+}  // namespace gbs

@@ -1,0 +1,299 @@
+"""CUDA path vs the CPU oracle, through the C ABI (GPU only).
+
+FP64 path: relative error of Haf and p within 1e-10 of the double-double oracle.
+Mixed path: relative error within its stated per-result bound err_est (reported
+by the library: n * 2^-24 * kappa), checked against the oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def gbs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1908_10070_gb300 as g
+
+    g.lib()
+    return g
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run_haf(gbs, mats, precision):
+    flat, n, offs = gbs.pack_matrices(mats)
+    A = dev(flat)
+    out = torch.zeros(2 * len(mats), dtype=torch.float64, device="cuda")
+    kap = torch.zeros(len(mats), dtype=torch.float64, device="cuda")
+    gbs.hafnian_batch(A, n, offs, precision, haf_out=out, kappa_out=kap)
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    return o[0::2] + 1j * o[1::2], kap.cpu().numpy()
+
+
+def run_prob(gbs, K, pats, precision, host=False):
+    idx, n, offs = gbs.pack_patterns(pats)
+    b = len(pats)
+    if host:
+        p = np.zeros(b); lp = np.zeros(b); hf = np.zeros(2 * b); er = np.zeros(b)
+        gbs.prob_batch(K, idx, n, offs, precision, p_out=p, logp_out=lp, haf_out=hf, err_out=er)
+        return p, lp, hf[0::2] + 1j * hf[1::2], er
+    p = torch.zeros(b, dtype=torch.float64, device="cuda")
+    lp = torch.zeros_like(p)
+    hf = torch.zeros(2 * b, dtype=torch.float64, device="cuda")
+    er = torch.zeros_like(p)
+    gbs.prob_batch(K, dev(idx), n, offs, precision, p_out=p, logp_out=lp, haf_out=hf, err_out=er)
+    torch.cuda.synchronize()
+    h = hf.cpu().numpy()
+    return p.cpu().numpy(), lp.cpu().numpy(), h[0::2] + 1j * h[1::2], er.cpu().numpy()
+
+
+def kernel_for(gbs, U, r):
+    Ud = dev(np.ascontiguousarray(U).view(np.float64))
+    return gbs.build_kernel(Ud, dev(r))
+
+
+def rel(a, b):
+    return np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
+
+
+def rand_sym(n, seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    return scale * (A + A.T) / 2
+
+
+# --- kernel matrix ------------------------------------------------------------
+
+@pytest.mark.parametrize("m,seed", [(8, 0), (64, 1), (145, 2)])
+def test_build_kernel_matches_oracle(gbs, orc, m, seed):
+    U = W.haar_unitary(m, seed)
+    r = W.squeezing(m, "uniform", seed=seed)
+    K = kernel_for(gbs, U, r)
+    B = torch.zeros(2 * m * m, dtype=torch.float64, device="cuda")
+    K.copy_B(B)
+    torch.cuda.synchronize()
+    Bg = B.cpu().numpy().view(np.complex128).reshape(m, m)
+    Bo = orc.build_B(U, r)
+    assert np.abs(Bg - Bo).max() <= 1e-15 * max(1.0, math.sqrt(m))
+    assert np.array_equal(Bg, Bg.T)
+    assert abs(K.log_norm - orc.log_norm(r)) <= 1e-13 * abs(orc.log_norm(r))
+
+
+def test_build_kernel_host_inputs(gbs, orc):
+    m = 20
+    U = W.haar_unitary(m, 7)
+    r = W.squeezing(m, "const", value=0.7)
+    K = gbs.build_kernel(U, r)  # numpy (host) inputs
+    B = np.zeros(2 * m * m)
+    K.copy_B(B)
+    assert np.abs(B.view(np.complex128).reshape(m, m) - orc.build_B(U, r)).max() <= 1e-15 * 5
+
+
+# --- Hafnians -----------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_hafnian_random_all_sizes(gbs, orc, precision):
+    """n = 0..24 (odd included), several per size: tiles of every lane-group shape."""
+    mats = [rand_sym(n, 1000 + 7 * n + k, scale=0.3) for n in range(0, 25) for k in range(3)]
+    got, kap = run_haf(gbs, mats, precision)
+    for A, g, kp in zip(mats, got, kap):
+        n = A.shape[0]
+        ref, K = orc.haf_subset(A, return_kappa=True)
+        if n % 2:
+            assert g == 0
+            continue
+        if precision == 0:
+            assert rel(g, ref) <= FP64_TOL, (n, g, ref)
+        else:
+            bound = max(n, 1) * 2.0 ** -24 * kp
+            assert rel(g, ref) <= bound, (n, rel(g, ref), bound)
+        if n >= 2:
+            # kappa reported with |z|_1: between the modulus-based value and sqrt(2) times it
+            kap_ref = K / abs(ref)
+            assert kap_ref * (1 - 1e-6) <= kp <= math.sqrt(2) * kap_ref * (1 + 1e-6) + 1e-12
+
+
+def test_hafnian_all_ones(gbs):
+    """Haf(J_2k) = (2k-1)!!: FP64 path within its kappa * u bound."""
+    mats = [np.ones((2 * k, 2 * k)) for k in range(0, 9)]
+    got, kap = run_haf(gbs, mats, 0)
+    for k, (g, kp) in enumerate(zip(got, kap)):
+        expect = math.prod(range(2 * k - 1, 0, -2)) if k else 1
+        assert abs(g - expect) <= 4 * max(2 * k, 1) * 2.0 ** -53 * kp * expect
+        if k <= 6:
+            assert rel(g, expect) <= 1e-11
+
+
+def test_hafnian_bipartite_permanent(gbs, orc):
+    """Haf([[0, C], [C^T, 0]]) = Per(C) (Ryser)."""
+    rng = np.random.default_rng(5)
+    mats, pers = [], []
+    for k in (1, 2, 3, 5, 8, 11):
+        C = (rng.standard_normal((k, k)) + 1j * rng.standard_normal((k, k))) * 0.5
+        Z = np.zeros((2 * k, 2 * k), complex)
+        Z[:k, k:] = C
+        Z[k:, :k] = C.T
+        mats.append(Z)
+        pers.append(orc.per_ryser(C))
+    got, _ = run_haf(gbs, mats, 0)
+    for g, p in zip(got, pers):
+        assert rel(g, p) <= FP64_TOL
+
+
+def test_hafnian_diagonal_ignored_and_permutation(gbs, orc):
+    A = rand_sym(14, 3, 0.4)
+    B = A.copy()
+    np.fill_diagonal(B, 5.0 + 1j)
+    perm = np.random.default_rng(9).permutation(14)
+    C = A[np.ix_(perm, perm)]
+    got, _ = run_haf(gbs, [A, B, C], 0)
+    ref = orc.haf_subset(A)
+    assert got[0] == got[1]  # the diagonal is never read
+    for g in got:
+        assert rel(g, ref) <= FP64_TOL
+
+
+def test_hafnian_host_buffers(gbs, orc):
+    mats = [rand_sym(n, 50 + n, 0.3) for n in (4, 10, 16)]
+    flat, n, offs = gbs.pack_matrices(mats)
+    out = np.zeros(2 * len(mats))
+    kap = np.zeros(len(mats))
+    gbs.hafnian_batch(flat, n, offs, 0, haf_out=out, kappa_out=kap)
+    for A, g in zip(mats, out[0::2] + 1j * out[1::2]):
+        assert rel(g, orc.haf_subset(A)) <= FP64_TOL
+
+
+# --- probabilities ---------------------------------------------------------------
+
+def test_prob_tiny_exhaustive(gbs, orc):
+    """m = 8, r = 0.5: all 70 collision-free 4-photon and all 36 2-photon patterns,
+    against the perfect-matching oracle."""
+    U, r, pats = W.workload("tiny_m8")
+    K = kernel_for(gbs, U, r)
+    ref = orc.prob(U, r, pats, method="pm")
+    for prec in (0, 1):
+        p, lp, hf, er = run_prob(gbs, K, pats, prec)
+        if prec == 0:
+            assert np.all(rel(hf, ref["haf"]) <= FP64_TOL)
+            assert np.all(rel(p, ref["p"]) <= FP64_TOL)
+            assert np.all(np.abs(lp - ref["logp"]) <= FP64_TOL * np.abs(ref["logp"]))
+        else:
+            assert np.all(rel(hf, ref["haf"]) <= er)
+
+
+def test_prob_host_and_device_buffers_agree(gbs):
+    U, r, pats = W.workload("tiny_m8")
+    K = kernel_for(gbs, U, r)
+    a = run_prob(gbs, K, pats, 0, host=False)
+    b = run_prob(gbs, K, pats, 0, host=True)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_prob_batched_n16_sampled(gbs, orc):
+    """The benchmark's workload and launch (M = 64, 4096 patterns, n = 16): the
+    whole batch runs on the GPU; 48 patterns spread over it are checked."""
+    U, r, pats = W.workload("batched_m64_n16")
+    K = kernel_for(gbs, U, r)
+    p, lp, hf, er = run_prob(gbs, K, pats, 0)
+    sample = list(range(0, 4096, 4096 // 48))[:48] + [4095]
+    ref = orc.prob(U, r, [pats[i] for i in sample])
+    assert np.all(rel(hf[sample], ref["haf"]) <= FP64_TOL)
+    assert np.all(rel(p[sample], ref["p"]) <= FP64_TOL)
+    assert np.all(np.isfinite(p)) and np.all(p > 0)
+
+
+def test_prob_mixed_collisions(gbs, orc):
+    """M = 144, n in {8..24}, up to 3 photons per mode: FP64 within 1e-10, mixed
+    within its own err_est, on a sample of the 2048-pattern batch."""
+    U, r, pats = W.workload("mixed_m144")
+    K = kernel_for(gbs, U, r)
+    p64, _, h64, e64 = run_prob(gbs, K, pats, 0)
+    p32, _, h32, e32 = run_prob(gbs, K, pats, 1)
+    sample = list(range(0, 2048, 2048 // 40))
+    ref = orc.prob(U, r, [pats[i] for i in sample])
+    assert np.all(rel(h64[sample], ref["haf"]) <= FP64_TOL)
+    assert np.all(rel(h32[sample], ref["haf"]) <= e32[sample])
+    assert np.all(e64 < 1e-9)
+
+
+@pytest.mark.slow
+def test_prob_large_n28_n30_sampled(gbs, orc):
+    """M = 900, r = 1: the 80-pattern batch (64 at n = 28, 16 at n = 30) in one
+    launch; one n = 28 and one n = 30 result against the oracle."""
+    U, r, pats = W.workload("large_m900")
+    K = kernel_for(gbs, U, r)
+    p, lp, hf, er = run_prob(gbs, K, pats, 0)
+    sample = [0, 64]
+    ref = orc.prob(U, r, [pats[i] for i in sample])
+    assert np.all(rel(hf[sample], ref["haf"]) <= FP64_TOL), (rel(hf[sample], ref["haf"]), er[sample])
+    assert np.all(np.isfinite(lp))
+
+
+# --- edge cases -------------------------------------------------------------------
+
+def test_edge_cases(gbs, orc):
+    m = 10
+    U = W.haar_unitary(m, 11)
+    r = W.squeezing(m, "uniform", seed=11)
+    K = kernel_for(gbs, U, r)
+    pats = [np.array([], np.int32), np.array([3], np.int32), np.array([2, 2]), np.array([0, 9]),
+            np.array([5, 5, 5, 5, 5, 5]), np.array([1, 2, 3]), np.array([9, 0, 4, 4])]
+    p, lp, hf, er = run_prob(gbs, K, pats, 0)
+    ref = orc.prob(U, r, pats)
+    L = orc.log_norm(r)
+    assert abs(p[0] - math.exp(-L)) <= 1e-14 * math.exp(-L) and hf[0] == 1
+    assert p[1] == 0 and hf[1] == 0 and lp[1] == -np.inf
+    assert p[5] == 0 and hf[5] == 0
+    for i in (2, 3, 4, 6):
+        assert rel(hf[i], ref["haf"][i]) <= FP64_TOL
+        assert rel(p[i], ref["p"][i]) <= FP64_TOL
+    # empty batch
+    gbs.prob_batch(K, dev(np.zeros(1, np.int32)), np.zeros(0, np.int32), np.zeros(0, np.int64), 0)
+
+
+def test_errors(gbs):
+    m = 6
+    U = W.haar_unitary(m, 1)
+    K = gbs.build_kernel(U, np.full(m, 0.5))
+    idx, n, offs = gbs.pack_patterns([np.array([0, 7])])
+    with pytest.raises(gbs.GbsError) as ei:
+        gbs.prob_batch(K, idx, n, offs, 0, p_out=np.zeros(1))
+    assert ei.value.code == -3
+    idx, n, offs = gbs.pack_patterns([np.zeros(34, np.int32)])
+    with pytest.raises(gbs.GbsError) as ei:
+        gbs.prob_batch(K, idx, n, offs, 0, p_out=np.zeros(1))
+    assert ei.value.code == -3
+    with pytest.raises(gbs.GbsError) as ei:
+        gbs.prob_batch(K, idx, n, offs, 7, p_out=np.zeros(1))
+    assert ei.value.code == -1
+    # device index list with an out-of-range entry: NaN result, no fault
+    idx, n, offs = gbs.pack_patterns([np.array([0, 1]), np.array([0, 99]), np.array([2, 3])])
+    p = torch.zeros(3, dtype=torch.float64, device="cuda")
+    gbs.prob_batch(K, dev(idx), n, offs, 0, p_out=p)
+    pc = p.cpu().numpy()
+    assert np.isfinite(pc[0]) and np.isnan(pc[1]) and np.isfinite(pc[2])
+
+
+def test_determinism_and_order_independence(gbs):
+    U, r, pats = W.workload("mixed_m144")
+    pats = pats[:300]
+    K = kernel_for(gbs, U, r)
+    a = run_prob(gbs, K, pats, 0)
+    b = run_prob(gbs, K, pats, 0)
+    assert np.array_equal(a[2], b[2])
+    perm = np.random.default_rng(0).permutation(len(pats))
+    c = run_prob(gbs, K, [pats[i] for i in perm], 0)
+    assert np.array_equal(c[2], a[2][perm])
