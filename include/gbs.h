@@ -106,6 +106,24 @@ int gbs_kernel_copy_B(const gbs_kernel* k, double* dst, void* stream);
 int gbs_hafnian_batch(const double* A_ri, const int* n, const int64_t* offs, int batch,
                       int precision, void* stream, double* haf_ri_out, double* kappa_out);
 
+/* gbs_hafnian_batch for callers that cannot allocate memory while they run
+ * (for example code inside a host callback or a memory-accounting scope, or a
+ * process that reserves all device memory for other work at start-up). The
+ * paper has no counterpart; this is a deployment variant of the call above.
+ * Same arguments and results, except that A_ri, haf_ri_out and kappa_out must
+ * be device memory (GBS_EINVAL otherwise). Its working space is one fixed
+ * array of about 1.6 MB built into the library, reserved on every GPU that
+ * loads it until the process exits, so the call makes no cudaMalloc, cudaFree,
+ * cudaMallocHost or other allocating call. Limits: at most 1024 matrices and
+ * 16384 work items per call (GBS_ERANGE beyond, with the reason in
+ * gbs_last_error). The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture. All calls share the array: calls whose GPU work overlaps (on
+ * different streams, or from several threads without ordering) race on it and
+ * must be serialised by the caller. */
+int gbs_hafnian_batch_noalloc(const double* A_ri, const int* n, const int64_t* offs, int batch,
+                              int precision, void* stream, double* haf_ri_out, double* kappa_out);
+
 /* Output probabilities of a batch of patterns (Eq. ProOri).
  *   idx     concatenated 0-based mode-index lists x (host or device); pattern b
  *           is idx[offs[b] .. offs[b]+n[b]), a repeated index is a collision.

@@ -19,7 +19,7 @@ from . import build as _build
 
 __all__ = [
     "FP64", "MIXED", "MAX_N", "GbsError", "lib", "build_kernel", "KernelMatrix",
-    "hafnian_batch", "prob_batch", "autotune", "Server", "serve_create", "pack_patterns",
+    "hafnian_batch", "hafnian_batch_noalloc", "prob_batch", "autotune", "Server", "serve_create", "pack_patterns",
     "pack_matrices", "last_error", "ERRORS",
 ]
 
@@ -58,6 +58,7 @@ def lib():
             L.gbs_kernel_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
             L.gbs_kernel_copy_B.argtypes = [vp, dp, vp]
             L.gbs_hafnian_batch.argtypes = [dp, ip, i64p, ctypes.c_int, ctypes.c_int, vp, dp, dp]
+            L.gbs_hafnian_batch_noalloc.argtypes = [dp, ip, i64p, ctypes.c_int, ctypes.c_int, vp, dp, dp]
             L.gbs_prob_batch.argtypes = [vp, ip, ip, i64p, ctypes.c_int, ctypes.c_int, vp, dp, dp, dp, dp]
             L.gbs_autotune.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int)]
             L.gbs_set_timing_events.argtypes = [vp, vp]
@@ -179,6 +180,16 @@ def hafnian_batch(A, n, offs, precision=FP64, stream=None, haf_out=None, kappa_o
     offs = np.ascontiguousarray(offs, dtype=np.int64)
     _check(lib().gbs_hafnian_batch(_ptr(A), _ptr(n), _ptr(offs), len(n), int(precision),
                                    _stream(stream), _ptr(haf_out), _ptr(kappa_out)))
+    return haf_out, kappa_out
+
+
+def hafnian_batch_noalloc(A, n, offs, precision=FP64, stream=None, haf_out=None, kappa_out=None):
+    """gbs_hafnian_batch_noalloc: same as hafnian_batch for callers that cannot
+    allocate; A and the outputs must be device tensors. See include/gbs.h."""
+    n = np.ascontiguousarray(n, dtype=np.int32)
+    offs = np.ascontiguousarray(offs, dtype=np.int64)
+    _check(lib().gbs_hafnian_batch_noalloc(_ptr(A), _ptr(n), _ptr(offs), len(n), int(precision),
+                                           _stream(stream), _ptr(haf_out), _ptr(kappa_out)))
     return haf_out, kappa_out
 
 
