@@ -332,6 +332,68 @@ def extras(gbs, torch):
                          "subset_terms_per_s": sum(2 ** (len(p) // 2) for p in pats) / (k64 * 1e-3),
                          "achieved_tflops": fl / (k64 * 1e-3) / 1e12, "frac_of_peak": fl / (k64 * 1e-3) / 1e12 / peak,
                          "max_err_est": float(e64.max())}
+    out["serving"] = serving(gbs, torch)
+    return out
+
+
+def serve_stream(gbs, K, reqs, precision):
+    """Poisson client: submit at the scheduled arrival times, poll until done.
+    Latency = completion seen by the client - scheduled arrival."""
+    srv = gbs.Server(K)
+    try:
+        warm = [srv.submit(x, precision) for _, x in reqs[:64]]
+        for t in warm:
+            while srv.poll(t) is None:
+                pass
+        lat, outstanding, i = [], {}, 0
+        t0 = time.perf_counter()
+        while i < len(reqs) or outstanding:
+            now = time.perf_counter() - t0
+            while i < len(reqs) and reqs[i][0] <= now:
+                tk = srv.submit(reqs[i][1], precision)
+                if tk < 0:
+                    break
+                outstanding[tk] = reqs[i][0]
+                i += 1
+            for tk in list(outstanding):
+                if srv.poll(tk) is not None:
+                    lat.append(time.perf_counter() - t0 - outstanding.pop(tk))
+        total = time.perf_counter() - t0
+    finally:
+        srv.destroy()
+    lat = np.array(lat) * 1e3
+    return {"requests": len(reqs), "throughput_req_s": len(reqs) / total, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean())}
+
+
+def per_pattern_stream(gbs, K, reqs):
+    """Plain FP64 per-pattern method: one synchronous gbs_prob_batch call per
+    request, in arrival order (host buffers)."""
+    p = np.zeros(1)
+    lat = []
+    t0 = time.perf_counter()
+    for arr, x in reqs:
+        now = time.perf_counter() - t0
+        if now < arr:
+            time.sleep(arr - now)
+        idx, n, offs = gbs.pack_patterns([x])
+        gbs.prob_batch(K, idx, n, offs, gbs.FP64, p_out=p)
+        lat.append(time.perf_counter() - t0 - arr)
+    total = time.perf_counter() - t0
+    lat = np.array(lat) * 1e3
+    return {"requests": len(reqs), "throughput_req_s": len(reqs) / total, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean())}
+
+
+def serving(gbs, torch, count: int = 20000):
+    """M = 256, r = 0.88; Poisson 2000 req/s; n ~ U{12..26} collision-free."""
+    U, r, _ = W.workload("serving_m256")
+    K = gbs.build_kernel(U, r)
+    reqs = W.serving_requests(count)
+    out = {"workload": "M=256 Haar U seed 3, r=0.88, Poisson 2000 req/s, n~U{12..26} collision-free",
+           "fp64": serve_stream(gbs, K, reqs, gbs.FP64),
+           "mixed": serve_stream(gbs, K, reqs, gbs.MIXED),
+           "per_pattern_fp64": per_pattern_stream(gbs, K, reqs[: max(1, count // 4)])}
     return out
 
 

@@ -170,7 +170,8 @@ typedef struct gbs_serve_opts {
   size_t mem_budget;      /* device bytes for request state (0 = 64 MiB) */
   int queue_capacity;     /* pending requests accepted before GBS_EAGAIN (0 = 65536) */
   int subsets_per_step;   /* subset terms per request per step (0 = library choice) */
-  int use_graphs;         /* 1 = replay a captured CUDA graph per step (default 1) */
+  int use_graphs;         /* 0 or 1: replay an instantiated CUDA graph per step (default);
+                             -1: launch each step's copies and kernels directly */
   double wait_timeout_s;  /* bound on any internal wait (0 = 10 s) */
 } gbs_serve_opts;
 

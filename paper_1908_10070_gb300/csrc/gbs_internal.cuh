@@ -82,6 +82,7 @@ struct HafLaunch {
 };
 
 struct FinalizeLaunch {
+  const int* sel;          // if non-null, entry b finalises pattern sel[b] (outputs at b)
   const PatDesc* pats;
   const Partial* parts;
   const int* idx;
@@ -101,6 +102,10 @@ cudaError_t launch_haf_subsets(const HafLaunch& L, int precision, int blocks, in
                                cudaStream_t st);
 cudaError_t launch_finalize(const FinalizeLaunch& F, cudaStream_t st);
 int max_blocks_per_sm(int precision, int warps_per_block, int smem_bytes);
+// Kernel entry points, for CUDA graph kernel nodes (the serving loop).
+const void* haf_kernel_fn(int precision);
+const void* finalize_kernel_fn();
+cudaError_t prepare_haf_kernel(int precision, int smem_bytes);
 
 // Defined in build_b.cu
 cudaError_t launch_build_B(const double* U, const double* r, int m, double* B, double* log_norm,

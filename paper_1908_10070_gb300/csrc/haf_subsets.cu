@@ -358,7 +358,8 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
 
 __global__ void finalize_kernel(const FinalizeLaunch F) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < F.batch; b += gridDim.x * blockDim.x) {
-    const PatDesc d = F.pats[b];
+    const int pb = F.sel ? F.sel[b] : b;
+    const PatDesc d = F.pats[pb];
     const int n = d.n;
     double rh = 0, rl = 0, ih = 0, il = 0, K = 0;
     if (n & 1) {
@@ -374,7 +375,7 @@ __global__ void finalize_kernel(const FinalizeLaunch F) {
         K += pr.kappa;
       }
     }
-    const bool bad = F.status != nullptr && F.status[b] != 0;
+    const bool bad = F.status != nullptr && F.status[pb] != 0;
     const double hr = rh + rl, hi = ih + il;
     const double mod = hypot(hr, hi);
     const double kappa = (mod > 0.0) ? K / mod : (K > 0.0 ? INFINITY : 0.0);
@@ -407,43 +408,68 @@ __global__ void finalize_kernel(const FinalizeLaunch F) {
 
 }  // namespace
 
+// Raise the kernel's dynamic shared-memory limit to the device maximum once
+// (per device and precision); it is never lowered, so every launch shape, and
+// any CUDA graph instantiated with one, stays valid.
+static cudaError_t ensure_smem_limit(int precision) {
+  static int done[2][64] = {{0}};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  const int p = precision == GBS_FP64 ? 0 : 1;
+  if (done[p][dev]) return cudaSuccess;
+  const void* fn = p == 0 ? (const void*)haf_subsets_kernel<double> : (const void*)haf_subsets_kernel<float>;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, fn);
+  if (e != cudaSuccess) return e;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  if (e != cudaSuccess) return e;
+  done[p][dev] = 1;
+  return cudaSuccess;
+}
+
 cudaError_t launch_haf_subsets(const HafLaunch& L, int precision, int blocks, int warps_per_block,
                                cudaStream_t st) {
   const size_t smem = (size_t)warps_per_block * L.warp_bytes;
-  cudaError_t e;
-  if (precision == GBS_FP64) {
-    e = cudaFuncSetAttribute(haf_subsets_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
+  cudaError_t e = ensure_smem_limit(precision);
+  if (e != cudaSuccess) return e;
+  if (precision == GBS_FP64)
     haf_subsets_kernel<double><<<blocks, warps_per_block * 32, smem, st>>>(L);
-  } else {
-    e = cudaFuncSetAttribute(haf_subsets_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-    if (e != cudaSuccess) return e;
+  else
     haf_subsets_kernel<float><<<blocks, warps_per_block * 32, smem, st>>>(L);
-  }
   return cudaGetLastError();
 }
 
 int max_blocks_per_sm(int precision, int warps_per_block, int smem_bytes) {
   int nb = 0;
-  cudaError_t e;
-  if (precision == GBS_FP64) {
-    cudaFuncSetAttribute(haf_subsets_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         smem_bytes);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, haf_subsets_kernel<double>,
-                                                      warps_per_block * 32, smem_bytes);
-  } else {
-    cudaFuncSetAttribute(haf_subsets_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         smem_bytes);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, haf_subsets_kernel<float>,
-                                                      warps_per_block * 32, smem_bytes);
+  if (ensure_smem_limit(precision) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
   }
+  const void* fn = precision == GBS_FP64 ? (const void*)haf_subsets_kernel<double>
+                                         : (const void*)haf_subsets_kernel<float>;
+  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, warps_per_block * 32, smem_bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   return nb;
+}
+
+const void* haf_kernel_fn(int precision) {
+  return precision == GBS_FP64 ? (const void*)haf_subsets_kernel<double>
+                               : (const void*)haf_subsets_kernel<float>;
+}
+
+const void* finalize_kernel_fn() { return (const void*)finalize_kernel; }
+
+cudaError_t prepare_haf_kernel(int precision, int smem_bytes) {
+  (void)smem_bytes;
+  return ensure_smem_limit(precision);
 }
 
 cudaError_t launch_finalize(const FinalizeLaunch& F, cudaStream_t st) {

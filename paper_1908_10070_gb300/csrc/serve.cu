@@ -1,0 +1,756 @@
+// Serving: continuous batching of single-pattern probability requests.
+//
+// A host thread owns the device state. Requests wait in a bounded queue and
+// are admitted into resident slots while a slot is free and the partial-sum
+// arena (the device memory budget) has room for the request's work items.
+// Every step takes a quota of work items from each resident request (round
+// robin), runs them in one subset-kernel launch per precision, and finalises
+// the requests whose last items are in that step; their results come back in
+// the same step. Partial sums stay on the device between steps, so a large
+// request is spread over several steps while small ones that arrive meanwhile
+// are admitted, run beside it and finish first.
+//
+// A request's work items, their partial-sum slots and the order in which its
+// partials are added depend only on its own n and precision, so its result is
+// bit-for-bit the same whether it runs alone or among others.
+//
+// Steps are double-buffered (the host builds step k+1 while step k runs) and,
+// by default, replayed as one instantiated CUDA graph per buffer whose node
+// parameters (item counts, copy sizes, grid sizes) are updated before each
+// launch. Every wait on the device is a bounded poll: past wait_timeout_s the
+// server fails the outstanding requests with GBS_ETIMEDOUT and stops.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "gbs_api_internal.h"
+
+using namespace gbs;
+
+namespace {
+
+struct Request {
+  int64_t ticket;
+  int n;
+  int prec;
+  int idx[GBS_MAX_N];
+};
+
+struct Result {
+  int rc;
+  double p, hr, hi, err;
+};
+
+// First-fit allocator over the partial-sum arena [0, cap).
+class Arena {
+ public:
+  void init(int cap) {
+    free_.clear();
+    free_.push_back({0, cap});
+  }
+  int alloc(int len) {
+    for (size_t i = 0; i < free_.size(); ++i)
+      if (free_[i].len >= len) {
+        const int s = free_[i].start;
+        free_[i].start += len;
+        free_[i].len -= len;
+        if (free_[i].len == 0) free_.erase(free_.begin() + i);
+        return s;
+      }
+    return -1;
+  }
+  void release(int start, int len) {
+    size_t i = 0;
+    while (i < free_.size() && free_[i].start < start) ++i;
+    free_.insert(free_.begin() + i, {start, len});
+    // coalesce neighbours
+    if (i + 1 < free_.size() && free_[i].start + free_[i].len == free_[i + 1].start) {
+      free_[i].len += free_[i + 1].len;
+      free_.erase(free_.begin() + i + 1);
+    }
+    if (i > 0 && free_[i - 1].start + free_[i - 1].len == free_[i].start) {
+      free_[i - 1].len += free_[i].len;
+      free_.erase(free_.begin() + i);
+    }
+  }
+
+ private:
+  struct R {
+    int start, len;
+  };
+  std::vector<R> free_;
+};
+
+struct Slot {
+  bool used = false;
+  int64_t ticket = 0;
+  int n = 0, prec = 0;
+  std::vector<WorkItem> items;  // part = arena base + i, pat = slot index
+  size_t next = 0;              // next item to dispatch
+  int part_base = 0;
+  bool finalize_sent = false;
+};
+
+constexpr int kStepCap = 65536;  // work items per precision per step
+
+struct Stage {
+  // pinned host: slot tables, items (2 precisions), selection list; results
+  unsigned char* h_up = nullptr;
+  double* h_res = nullptr;
+  // device
+  WorkItem* d_items[2] = {nullptr, nullptr};
+  int* d_sel = nullptr;
+  int* d_ctr = nullptr;
+  double* d_res = nullptr;
+  cudaEvent_t ev = nullptr;
+  bool busy = false;
+  int64_t id = 0;
+  int n_items[2] = {0, 0};
+  std::vector<int> fin;  // slots finalised in this step, in selection order
+  // graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t nd_pats = nullptr, nd_idx = nullptr, nd_items[2] = {nullptr, nullptr},
+                  nd_ctr = nullptr, nd_k[2] = {nullptr, nullptr}, nd_sel = nullptr, nd_fin = nullptr,
+                  nd_res = nullptr;
+};
+
+}  // namespace
+
+struct gbs_server {
+  const gbs_kernel* k = nullptr;
+  int device = 0;
+  gbs_serve_opts o;
+  double log_norm = 0.0;
+  cudaStream_t st = nullptr;
+  TuneCfg cfg[2];
+  int blocks_max[2] = {0, 0};
+  // host state
+  std::mutex mu;
+  std::condition_variable cv;
+  bool stop = false;
+  bool failed = false;
+  std::deque<Request> queue;
+  std::unordered_set<int64_t> pending;
+  std::unordered_map<int64_t, Result> done;
+  int64_t next_ticket = 1;
+  std::vector<Slot> slots;
+  Arena arena;
+  int rr = 0;  // round-robin start
+  int64_t step_id = 0;
+  // device tables
+  PatDesc* d_pats = nullptr;
+  int* d_idx = nullptr;
+  Partial* d_parts = nullptr;
+  std::vector<PatDesc> h_pats;
+  std::vector<int> h_idx;
+  size_t off_pats = 0, off_idx = 0, off_items[2] = {0, 0}, off_sel = 0, up_bytes = 0;
+  Stage stage[2];
+  std::thread th;
+};
+
+namespace {
+
+int64_t binom64(int a, int b) {
+  if (b < 0 || b > a) return 0;
+  int64_t r = 1;
+  for (int i = 1; i <= b; ++i) r = r * (a - b + i) / i;
+  return r;
+}
+
+// Work items of one request (slot index `si`) with rounds-per-item R: the same
+// decomposition as the batched path for this launch shape.
+void request_items(const gbs_server* s, int si, int n, int prec, std::vector<WorkItem>& out) {
+  out.clear();
+  const int h = n / 2;
+  const int cb = complex_bytes(prec);
+  const int R = 1;
+  for (int sz = 1; sz <= h; ++sz) {
+    const int G = 32 / lanes_for(2 * sz, h, s->cfg[prec].warp_bytes, cb);
+    const int64_t cnt = binom64(h, sz), cap = (int64_t)G * R;
+    for (int64_t r0 = 0; r0 < cnt; r0 += cap) {
+      WorkItem w;
+      w.pat = si;
+      w.s = sz;
+      w.rank0 = (int)r0;
+      w.count = (int)std::min<int64_t>(cap, cnt - r0);
+      w.part = 0;
+      w.pad[0] = w.pad[1] = w.pad[2] = 0;
+      out.push_back(w);
+    }
+  }
+}
+
+HafLaunch make_launch(gbs_server* s, Stage& g, int prec) {
+  HafLaunch L;
+  memset(&L, 0, sizeof(L));
+  L.src = s->k->B;
+  L.idx = s->d_idx;
+  L.pats = s->d_pats;
+  L.items = g.d_items[prec];
+  L.n_items = g.n_items[prec];
+  L.m_bound = 0;  // indices are checked on submit
+  L.counter = g.d_ctr + prec;
+  L.status = nullptr;
+  L.parts = s->d_parts;
+  L.warp_bytes = s->cfg[prec].warp_bytes;
+  return L;
+}
+
+FinalizeLaunch make_finalize(gbs_server* s, Stage& g) {
+  const int S = s->o.max_slots;
+  FinalizeLaunch F;
+  memset(&F, 0, sizeof(F));
+  F.sel = g.d_sel;
+  F.pats = s->d_pats;
+  F.parts = s->d_parts;
+  F.idx = s->d_idx;
+  F.status = nullptr;
+  F.batch = (int)g.fin.size();
+  F.precision = GBS_FP64;
+  F.log_norm = s->k->dscal;
+  F.p_out = g.d_res;
+  F.logp_out = g.d_res + S;
+  F.haf_out = g.d_res + 2 * S;
+  F.kappa_out = g.d_res + 4 * S;
+  F.err_out = nullptr;
+  return F;
+}
+
+int grid_for(gbs_server* s, int prec, int n_items) {
+  const int wpb = s->cfg[prec].warps_per_block;
+  int b = (n_items + wpb - 1) / wpb;
+  if (b > s->blocks_max[prec]) b = s->blocks_max[prec];
+  return b < 1 ? 1 : b;
+}
+
+// Build the graph of one stage (all nodes present; counts are set per step).
+cudaError_t build_graph(gbs_server* s, Stage& g) {
+  cudaError_t e = cudaGraphCreate(&g.graph, 0);
+  if (e != cudaSuccess) return e;
+  const int S = s->o.max_slots;
+  cudaGraphNode_t prev = nullptr;
+  auto dep = [&](cudaGraphNode_t* deps) -> size_t {
+    if (prev) {
+      deps[0] = prev;
+      return 1;
+    }
+    return 0;
+  };
+  cudaGraphNode_t deps[1];
+  size_t nd;
+  nd = dep(deps);
+  e = cudaGraphAddMemcpyNode1D(&g.nd_pats, g.graph, deps, nd, s->d_pats, g.h_up + s->off_pats,
+                               sizeof(PatDesc) * S, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  prev = g.nd_pats;
+  nd = dep(deps);
+  e = cudaGraphAddMemcpyNode1D(&g.nd_idx, g.graph, deps, nd, s->d_idx, g.h_up + s->off_idx,
+                               sizeof(int) * GBS_MAX_N * S, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  prev = g.nd_idx;
+  cudaMemsetParams mp;
+  memset(&mp, 0, sizeof(mp));
+  mp.dst = g.d_ctr;
+  mp.value = 0;
+  mp.elementSize = 4;
+  mp.width = 2;
+  mp.height = 1;
+  nd = dep(deps);
+  e = cudaGraphAddMemsetNode(&g.nd_ctr, g.graph, deps, nd, &mp);
+  if (e != cudaSuccess) return e;
+  prev = g.nd_ctr;
+  for (int p = 0; p < 2; ++p) {
+    nd = dep(deps);
+    e = cudaGraphAddMemcpyNode1D(&g.nd_items[p], g.graph, deps, nd, g.d_items[p],
+                                 g.h_up + s->off_items[p], sizeof(WorkItem), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    prev = g.nd_items[p];
+    g.n_items[p] = 1;
+    HafLaunch L = make_launch(s, g, p);
+    void* args[1] = {&L};
+    cudaKernelNodeParams kp;
+    memset(&kp, 0, sizeof(kp));
+    kp.func = (void*)haf_kernel_fn(p);
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(s->cfg[p].warps_per_block * 32);
+    kp.sharedMemBytes = s->cfg[p].warps_per_block * s->cfg[p].warp_bytes;
+    kp.kernelParams = args;
+    nd = dep(deps);
+    e = cudaGraphAddKernelNode(&g.nd_k[p], g.graph, deps, nd, &kp);
+    if (e != cudaSuccess) return e;
+    prev = g.nd_k[p];
+  }
+  nd = dep(deps);
+  e = cudaGraphAddMemcpyNode1D(&g.nd_sel, g.graph, deps, nd, g.d_sel, g.h_up + s->off_sel,
+                               sizeof(int) * S, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  prev = g.nd_sel;
+  {
+    g.fin.assign(1, 0);
+    FinalizeLaunch F = make_finalize(s, g);
+    void* args[1] = {&F};
+    cudaKernelNodeParams kp;
+    memset(&kp, 0, sizeof(kp));
+    kp.func = (void*)finalize_kernel_fn();
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(128);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    nd = dep(deps);
+    e = cudaGraphAddKernelNode(&g.nd_fin, g.graph, deps, nd, &kp);
+    if (e != cudaSuccess) return e;
+    prev = g.nd_fin;
+    g.fin.clear();
+  }
+  nd = dep(deps);
+  e = cudaGraphAddMemcpyNode1D(&g.nd_res, g.graph, deps, nd, g.h_res, g.d_res, sizeof(double) * 5 * S,
+                               cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return e;
+  return cudaGraphInstantiate(&g.exec, g.graph, 0);
+}
+
+// Launch one prepared stage, with the graph (parameters updated) or directly.
+cudaError_t launch_stage(gbs_server* s, Stage& g) {
+  const int S = s->o.max_slots;
+  cudaError_t e;
+  if (s->o.use_graphs) {
+    for (int p = 0; p < 2; ++p) {
+      const bool on = g.n_items[p] > 0;
+      e = cudaGraphNodeSetEnabled(g.exec, g.nd_items[p], on);
+      if (e != cudaSuccess) return e;
+      e = cudaGraphNodeSetEnabled(g.exec, g.nd_k[p], on);
+      if (e != cudaSuccess) return e;
+      if (!on) continue;
+      e = cudaGraphExecMemcpyNodeSetParams1D(g.exec, g.nd_items[p], g.d_items[p], g.h_up + s->off_items[p],
+                                             sizeof(WorkItem) * g.n_items[p], cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return e;
+      HafLaunch L = make_launch(s, g, p);
+      void* args[1] = {&L};
+      cudaKernelNodeParams kp;
+      memset(&kp, 0, sizeof(kp));
+      kp.func = (void*)haf_kernel_fn(p);
+      kp.gridDim = dim3(grid_for(s, p, g.n_items[p]));
+      kp.blockDim = dim3(s->cfg[p].warps_per_block * 32);
+      kp.sharedMemBytes = s->cfg[p].warps_per_block * s->cfg[p].warp_bytes;
+      kp.kernelParams = args;
+      e = cudaGraphExecKernelNodeSetParams(g.exec, g.nd_k[p], &kp);
+      if (e != cudaSuccess) return e;
+    }
+    const bool fon = !g.fin.empty();
+    e = cudaGraphNodeSetEnabled(g.exec, g.nd_sel, fon);
+    if (e != cudaSuccess) return e;
+    e = cudaGraphNodeSetEnabled(g.exec, g.nd_fin, fon);
+    if (e != cudaSuccess) return e;
+    e = cudaGraphNodeSetEnabled(g.exec, g.nd_res, fon);
+    if (e != cudaSuccess) return e;
+    if (fon) {
+      FinalizeLaunch F = make_finalize(s, g);
+      void* args[1] = {&F};
+      cudaKernelNodeParams kp;
+      memset(&kp, 0, sizeof(kp));
+      kp.func = (void*)finalize_kernel_fn();
+      kp.gridDim = dim3((unsigned)((g.fin.size() + 127) / 128));
+      kp.blockDim = dim3(128);
+      kp.kernelParams = args;
+      e = cudaGraphExecKernelNodeSetParams(g.exec, g.nd_fin, &kp);
+      if (e != cudaSuccess) return e;
+    }
+    e = cudaGraphLaunch(g.exec, s->st);
+    if (e != cudaSuccess) return e;
+  } else {
+    e = cudaMemcpyAsync(s->d_pats, g.h_up + s->off_pats, sizeof(PatDesc) * S, cudaMemcpyHostToDevice, s->st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(s->d_idx, g.h_up + s->off_idx, sizeof(int) * GBS_MAX_N * S, cudaMemcpyHostToDevice,
+                        s->st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(g.d_ctr, 0, 2 * sizeof(int), s->st);
+    if (e != cudaSuccess) return e;
+    for (int p = 0; p < 2; ++p) {
+      if (g.n_items[p] == 0) continue;
+      e = cudaMemcpyAsync(g.d_items[p], g.h_up + s->off_items[p], sizeof(WorkItem) * g.n_items[p],
+                          cudaMemcpyHostToDevice, s->st);
+      if (e != cudaSuccess) return e;
+      e = launch_haf_subsets(make_launch(s, g, p), p, grid_for(s, p, g.n_items[p]),
+                             s->cfg[p].warps_per_block, s->st);
+      if (e != cudaSuccess) return e;
+    }
+    if (!g.fin.empty()) {
+      e = cudaMemcpyAsync(g.d_sel, g.h_up + s->off_sel, sizeof(int) * g.fin.size(), cudaMemcpyHostToDevice,
+                          s->st);
+      if (e != cudaSuccess) return e;
+      e = launch_finalize(make_finalize(s, g), s->st);
+      if (e != cudaSuccess) return e;
+      e = cudaMemcpyAsync(g.h_res, g.d_res, sizeof(double) * 5 * S, cudaMemcpyDeviceToHost, s->st);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaEventRecord(g.ev, s->st);
+}
+
+// Admit queued requests into free slots while the arena has room (lock held).
+void admit(gbs_server* s) {
+  while (!s->queue.empty()) {
+    int si = -1;
+    for (int i = 0; i < s->o.max_slots; ++i)
+      if (!s->slots[i].used) {
+        si = i;
+        break;
+      }
+    if (si < 0) return;
+    const Request& r = s->queue.front();
+    Slot& sl = s->slots[si];
+    request_items(s, si, r.n, r.prec, sl.items);
+    const int base = s->arena.alloc((int)sl.items.size());
+    if (base < 0) return;  // wait for memory to free up
+    for (size_t i = 0; i < sl.items.size(); ++i) sl.items[i].part = base + (int)i;
+    sl.used = true;
+    sl.ticket = r.ticket;
+    sl.n = r.n;
+    sl.prec = r.prec;
+    sl.next = 0;
+    sl.part_base = base;
+    sl.finalize_sent = false;
+    PatDesc& d = s->h_pats[si];
+    d.src_off = 0;
+    d.idx_off = (int64_t)si * GBS_MAX_N;
+    d.ld = s->k->m;
+    d.n = r.n;
+    d.item_begin = base;
+    d.item_end = base + (int)sl.items.size();
+    memcpy(&s->h_idx[(size_t)si * GBS_MAX_N], r.idx, sizeof(int) * r.n);
+    s->queue.pop_front();
+  }
+}
+
+// Fill a stage with this step's work (lock held). Returns true if it has work.
+bool build_step(gbs_server* s, Stage& g) {
+  const int S = s->o.max_slots;
+  g.n_items[0] = g.n_items[1] = 0;
+  g.fin.clear();
+  memcpy(g.h_up + s->off_pats, s->h_pats.data(), sizeof(PatDesc) * S);
+  memcpy(g.h_up + s->off_idx, s->h_idx.data(), sizeof(int) * GBS_MAX_N * S);
+  WorkItem* it[2] = {(WorkItem*)(g.h_up + s->off_items[0]), (WorkItem*)(g.h_up + s->off_items[1])};
+  int* sel = (int*)(g.h_up + s->off_sel);
+  const int quota = s->o.subsets_per_step;
+  for (int q = 0; q < S; ++q) {
+    const int si = (s->rr + q) % S;
+    Slot& sl = s->slots[si];
+    if (!sl.used || sl.finalize_sent) continue;
+    int taken = 0;
+    int& cnt = g.n_items[sl.prec];
+    while (sl.next < sl.items.size() && taken < quota && cnt < kStepCap) {
+      it[sl.prec][cnt++] = sl.items[sl.next];
+      taken += sl.items[sl.next].count;
+      ++sl.next;
+    }
+    if (sl.next == sl.items.size()) {
+      sel[g.fin.size()] = si;
+      g.fin.push_back(si);
+      sl.finalize_sent = true;
+    }
+  }
+  s->rr = (s->rr + 1) % S;
+  g.id = ++s->step_id;
+  return g.n_items[0] > 0 || g.n_items[1] > 0 || !g.fin.empty();
+}
+
+// Publish the results of a completed stage and free its finished slots (lock held).
+void complete(gbs_server* s, Stage& g) {
+  const int S = s->o.max_slots;
+  for (size_t b = 0; b < g.fin.size(); ++b) {
+    Slot& sl = s->slots[g.fin[b]];
+    Result r;
+    r.rc = GBS_OK;
+    r.p = g.h_res[b];
+    r.hr = g.h_res[2 * S + 2 * b];
+    r.hi = g.h_res[2 * S + 2 * b + 1];
+    const double kappa = g.h_res[4 * S + b];
+    r.err = (double)sl.n * (sl.prec == GBS_FP64 ? 0x1p-53 : 0x1p-24) * kappa;
+    s->done[sl.ticket] = r;
+    s->pending.erase(sl.ticket);
+    s->arena.release(sl.part_base, (int)sl.items.size());
+    sl.used = false;
+    sl.items.clear();
+  }
+  g.fin.clear();
+  g.busy = false;
+}
+
+void fail_all(gbs_server* s, int rc) {
+  for (int64_t t : s->pending) {
+    Result r;
+    r.rc = rc;
+    r.p = r.hr = r.hi = r.err = NAN;
+    s->done[t] = r;
+  }
+  s->pending.clear();
+  s->queue.clear();
+  for (auto& sl : s->slots) sl.used = false;
+}
+
+// Bounded wait for a stage's event; false on timeout or error.
+bool wait_stage(gbs_server* s, Stage& g, bool block) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaEventQuery(g.ev);
+    if (e == cudaSuccess) return true;
+    if (e != cudaErrorNotReady) return false;
+    if (!block) return false;
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el > s->o.wait_timeout_s) return false;
+    std::this_thread::sleep_for(std::chrono::microseconds(5));
+  }
+}
+
+void serve_loop(gbs_server* s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (;;) {
+    admit(s);
+    bool any_work = false;
+    for (const Slot& sl : s->slots)
+      if (sl.used && !sl.finalize_sent) any_work = true;
+    Stage* free_stage = !s->stage[0].busy ? &s->stage[0] : (!s->stage[1].busy ? &s->stage[1] : nullptr);
+    if (s->stop && !any_work && !s->stage[0].busy && !s->stage[1].busy && s->queue.empty()) break;
+    bool launched = false;
+    if (any_work && free_stage && build_step(s, *free_stage)) {
+      const cudaError_t e = launch_stage(s, *free_stage);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail_all(s, GBS_ECUDA);
+        s->failed = true;
+        break;
+      }
+      free_stage->busy = true;
+      launched = true;
+    }
+    Stage* old = nullptr;
+    for (int i = 0; i < 2; ++i)
+      if (s->stage[i].busy && (!old || s->stage[i].id < old->id)) old = &s->stage[i];
+    if (old) {
+      // block on the oldest step when nothing new could be launched
+      const bool block = !launched || (s->stage[0].busy && s->stage[1].busy);
+      lk.unlock();
+      const bool ok = wait_stage(s, *old, block);
+      lk.lock();
+      if (ok) {
+        complete(s, *old);
+        s->cv.notify_all();
+      } else if (block) {
+        const cudaError_t e = cudaEventQuery(old->ev);
+        cudaGetLastError();
+        fail_all(s, e == cudaErrorNotReady ? GBS_ETIMEDOUT : GBS_ECUDA);
+        s->failed = true;
+        break;
+      }
+    } else if (!launched) {
+      s->cv.wait_for(lk, std::chrono::milliseconds(1));
+    }
+  }
+  s->cv.notify_all();
+}
+
+void destroy_resources(gbs_server* s) {
+  for (int i = 0; i < 2; ++i) {
+    Stage& g = s->stage[i];
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    if (g.ev) cudaEventDestroy(g.ev);
+    if (g.h_up) cudaFreeHost(g.h_up);
+    if (g.h_res) cudaFreeHost(g.h_res);
+    if (g.d_items[0]) cudaFree(g.d_items[0]);
+    if (g.d_sel) cudaFree(g.d_sel);
+    if (g.d_ctr) cudaFree(g.d_ctr);
+    if (g.d_res) cudaFree(g.d_res);
+  }
+  if (s->d_pats) cudaFree(s->d_pats);
+  if (s->d_idx) cudaFree(s->d_idx);
+  if (s->d_parts) cudaFree(s->d_parts);
+  if (s->st) cudaStreamDestroy(s->st);
+}
+
+}  // namespace
+
+extern "C" int gbs_serve_create(const gbs_kernel* k, const gbs_serve_opts* opts, gbs_server** out) {
+  clear_error();
+  if (!k || !out) return fail(GBS_EINVAL, "null argument");
+  *out = nullptr;
+  gbs_server* s = new (std::nothrow) gbs_server();
+  if (!s) return fail(GBS_ENOMEM, "host allocation");
+  memset(&s->o, 0, sizeof(s->o));
+  if (opts) s->o = *opts;
+  if (s->o.max_slots <= 0) s->o.max_slots = 256;
+  if (s->o.mem_budget == 0) s->o.mem_budget = (size_t)64 << 20;
+  if (s->o.queue_capacity <= 0) s->o.queue_capacity = 65536;
+  if (s->o.subsets_per_step <= 0) s->o.subsets_per_step = 8192;
+  if (s->o.wait_timeout_s <= 0) s->o.wait_timeout_s = 10.0;
+  s->o.use_graphs = (s->o.use_graphs >= 0) ? 1 : 0;
+  s->k = k;
+  s->device = k->device;
+  int ret = GBS_OK;
+  cudaError_t e = cudaSetDevice(s->device);
+  if (e != cudaSuccess) {
+    delete s;
+    return cuda_fail(e, "cudaSetDevice");
+  }
+  const int S = s->o.max_slots;
+  do {
+    e = cudaMemcpy(&s->log_norm, k->dscal, sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { ret = cuda_fail(e, "log_norm"); break; }
+    e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { ret = cuda_fail(e, "stream"); break; }
+    for (int p = 0; p < 2; ++p) {
+      s->cfg[p] = default_cfg(p, GBS_MAX_N);
+      const int smem = s->cfg[p].warps_per_block * s->cfg[p].warp_bytes;
+      e = prepare_haf_kernel(p, smem);
+      if (e != cudaSuccess) { ret = cuda_fail(e, "kernel attribute"); break; }
+      s->blocks_max[p] = device_sm_count() * std::max(1, max_blocks_per_sm(p, s->cfg[p].warps_per_block, smem));
+    }
+    if (ret) break;
+    // memory budget: slot tables, per-stage buffers, then the partial arena
+    const size_t tables = sizeof(PatDesc) * S + sizeof(int) * GBS_MAX_N * S;
+    const size_t stage_b = 2 * (2 * sizeof(WorkItem) * kStepCap + sizeof(int) * S + 256 + 5 * sizeof(double) * S);
+    if (s->o.mem_budget <= tables + stage_b + 1024 * sizeof(Partial)) {
+      ret = fail(GBS_EINVAL, "mem_budget %zu bytes is too small", s->o.mem_budget);
+      break;
+    }
+    const size_t arena_items = std::min<size_t>((s->o.mem_budget - tables - stage_b) / sizeof(Partial),
+                                                (size_t)1 << 30);
+    s->arena.init((int)arena_items);
+    if ((e = cudaMalloc(&s->d_pats, sizeof(PatDesc) * S)) != cudaSuccess ||
+        (e = cudaMalloc(&s->d_idx, sizeof(int) * GBS_MAX_N * S)) != cudaSuccess ||
+        (e = cudaMalloc(&s->d_parts, sizeof(Partial) * arena_items)) != cudaSuccess) {
+      cudaGetLastError();
+      ret = fail(GBS_ENOMEM, "device buffers: %s", cudaGetErrorString(e));
+      break;
+    }
+    s->h_pats.assign(S, PatDesc());
+    memset(s->h_pats.data(), 0, sizeof(PatDesc) * S);
+    s->h_idx.assign((size_t)GBS_MAX_N * S, 0);
+    s->slots.assign(S, Slot());
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    s->off_pats = 0;
+    s->off_idx = al(sizeof(PatDesc) * S);
+    s->off_items[0] = s->off_idx + al(sizeof(int) * GBS_MAX_N * S);
+    s->off_items[1] = s->off_items[0] + al(sizeof(WorkItem) * kStepCap);
+    s->off_sel = s->off_items[1] + al(sizeof(WorkItem) * kStepCap);
+    s->up_bytes = s->off_sel + al(sizeof(int) * S);
+    for (int i = 0; i < 2 && ret == GBS_OK; ++i) {
+      Stage& g = s->stage[i];
+      if ((e = cudaMallocHost(&g.h_up, s->up_bytes)) != cudaSuccess ||
+          (e = cudaMallocHost(&g.h_res, 5 * sizeof(double) * S)) != cudaSuccess ||
+          (e = cudaMalloc(&g.d_items[0], 2 * al(sizeof(WorkItem) * kStepCap))) != cudaSuccess ||
+          (e = cudaMalloc(&g.d_sel, sizeof(int) * S)) != cudaSuccess ||
+          (e = cudaMalloc(&g.d_ctr, 256)) != cudaSuccess ||
+          (e = cudaMalloc(&g.d_res, 5 * sizeof(double) * S)) != cudaSuccess ||
+          (e = cudaEventCreateWithFlags(&g.ev, cudaEventDisableTiming)) != cudaSuccess) {
+        cudaGetLastError();
+        ret = fail(GBS_ENOMEM, "stage buffers: %s", cudaGetErrorString(e));
+        break;
+      }
+      memset(g.h_up, 0, s->up_bytes);
+      g.d_items[1] = (WorkItem*)((unsigned char*)g.d_items[0] + al(sizeof(WorkItem) * kStepCap));
+      if (s->o.use_graphs) {
+        e = build_graph(s, g);
+        if (e != cudaSuccess) {
+          cudaGetLastError();
+          ret = cuda_fail(e, "step graph");
+          break;
+        }
+      }
+    }
+  } while (0);
+  if (ret != GBS_OK) {
+    destroy_resources(s);
+    delete s;
+    return ret;
+  }
+  s->th = std::thread(serve_loop, s);
+  *out = s;
+  return GBS_OK;
+}
+
+extern "C" int gbs_serve_submit(gbs_server* s, const int* idx, int n, int precision, int64_t* ticket) {
+  clear_error();
+  if (!s || !ticket || (n > 0 && !idx)) return fail(GBS_EINVAL, "null argument");
+  if (precision != GBS_FP64 && precision != GBS_MIXED) return fail(GBS_EINVAL, "bad precision");
+  if (n < 0 || n > GBS_MAX_N) return fail(GBS_ERANGE, "n = %d outside [0, %d]", n, GBS_MAX_N);
+  for (int i = 0; i < n; ++i)
+    if (idx[i] < 0 || idx[i] >= s->k->m)
+      return fail(GBS_ERANGE, "index %d = %d is outside [0, %d)", i, idx[i], s->k->m);
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->failed) return fail(GBS_ECUDA, "server stopped after an error");
+  if (s->stop) return fail(GBS_EINVAL, "server is stopping");
+  if ((int)s->queue.size() >= s->o.queue_capacity) return fail(GBS_EAGAIN, "queue full");
+  const int64_t t = s->next_ticket++;
+  *ticket = t;
+  if (n == 0 || (n & 1)) {
+    // answered without device work: n = 0 is the vacuum (Haf = 1); odd n has
+    // no perfect matching (Haf = 0)
+    Result r;
+    r.rc = GBS_OK;
+    r.hr = (n == 0) ? 1.0 : 0.0;
+    r.hi = 0.0;
+    r.p = (n == 0) ? exp(-s->log_norm) : 0.0;
+    r.err = 0.0;
+    s->done[t] = r;
+    return GBS_OK;
+  }
+  Request r;
+  r.ticket = t;
+  r.n = n;
+  r.prec = precision;
+  memcpy(r.idx, idx, sizeof(int) * n);
+  s->queue.push_back(r);
+  s->pending.insert(t);
+  s->cv.notify_all();
+  return GBS_OK;
+}
+
+extern "C" int gbs_serve_poll(gbs_server* s, int64_t ticket, double* p, double* haf_ri, double* err_est) {
+  clear_error();
+  if (!s) return fail(GBS_EINVAL, "null server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->done.find(ticket);
+  if (it == s->done.end()) {
+    if (s->pending.count(ticket)) return 1;
+    return fail(GBS_ENOENT, "unknown or already collected ticket %lld", (long long)ticket);
+  }
+  const Result r = it->second;
+  s->done.erase(it);
+  if (r.rc != GBS_OK) return fail(r.rc, "request failed (%s)", r.rc == GBS_ETIMEDOUT ? "device wait timed out" : "CUDA error");
+  if (p) *p = r.p;
+  if (haf_ri) {
+    haf_ri[0] = r.hr;
+    haf_ri[1] = r.hi;
+  }
+  if (err_est) *err_est = r.err;
+  return 0;
+}
+
+extern "C" int gbs_serve_destroy(gbs_server* s) {
+  clear_error();
+  if (!s) return GBS_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_all();
+  if (s->th.joinable()) s->th.join();
+  cudaSetDevice(s->device);
+  cudaStreamSynchronize(s->st);
+  const bool failed = s->failed;
+  destroy_resources(s);
+  delete s;
+  return failed ? fail(GBS_ECUDA, "server had stopped after an error") : GBS_OK;
+}

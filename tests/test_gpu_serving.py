@@ -1,0 +1,154 @@
+"""Serving loop (gbs_serve_*) on the GPU: continuous batching of single-pattern
+requests. Results match gbs_prob_batch, are bit-identical alone and in a mix,
+and the host-side failure paths (queue full, unknown ticket) return codes."""
+import time
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def gbs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1908_10070_gb300 as g
+
+    g.lib()
+    return g
+
+
+@pytest.fixture(scope="module")
+def kern(gbs):
+    m = 96
+    U = W.haar_unitary(m, 31)
+    r = W.squeezing(m, "const", value=0.88)
+    return gbs.build_kernel(U, r), m
+
+
+def requests(m, count, seed, n_values=range(2, 21)):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(rng.choice(list(n_values)))
+        out.append(np.sort(rng.choice(m, size=n, replace=False)).astype(np.int32))
+    return out
+
+
+def wait_all(srv, tickets, timeout=60.0):
+    res = {}
+    t0 = time.time()
+    while len(res) < len(tickets):
+        for t in tickets:
+            if t in res:
+                continue
+            r = srv.poll(t)
+            if r is not None:
+                res[t] = r
+        assert time.time() - t0 < timeout, "serving did not finish"
+    return [res[t] for t in tickets]
+
+
+def batch_ref(gbs, K, pats, prec):
+    idx, n, offs = gbs.pack_patterns(pats)
+    b = len(pats)
+    p = np.zeros(b); hf = np.zeros(2 * b)
+    gbs.prob_batch(K, idx, n, offs, prec, p_out=p, haf_out=hf)
+    return p, hf[0::2] + 1j * hf[1::2]
+
+
+@pytest.mark.parametrize("use_graphs", [1, -1])
+def test_serving_matches_batch(gbs, kern, use_graphs):
+    K, m = kern
+    pats = requests(m, 120, 5)
+    srv = gbs.Server(K, use_graphs=use_graphs, subsets_per_step=256)
+    try:
+        tickets = [srv.submit(x) for x in pats]
+        res = wait_all(srv, tickets)
+    finally:
+        srv.destroy()
+    p_ref, h_ref = batch_ref(gbs, K, pats, gbs.FP64)
+    for (p, h, e), pr, hr, x in zip(res, p_ref, h_ref, pats):
+        if len(x) % 2:
+            assert p == 0 and h == 0
+        else:
+            assert abs(h - hr) <= FP64_TOL * abs(hr), (len(x), h, hr)
+            assert abs(p - pr) <= FP64_TOL * pr
+
+
+def test_serving_alone_equals_in_mix(gbs, kern):
+    """A request's result does not depend on what else is resident."""
+    K, m = kern
+    probe = [np.sort(np.random.default_rng(s).choice(m, size=n, replace=False)).astype(np.int32)
+             for s, n in ((1, 18), (2, 12), (3, 20))]
+    srv = gbs.Server(K, subsets_per_step=128)
+    try:
+        alone = [wait_all(srv, [srv.submit(x)])[0] for x in probe]
+        mix = requests(m, 200, 9, n_values=range(10, 23, 2))
+        order = []  # (ticket, probe index or None)
+        for i, x in enumerate(mix):
+            order.append((srv.submit(x), None))
+            if i in (20, 60, 120):
+                j = {20: 0, 60: 1, 120: 2}[i]
+                order.append((srv.submit(probe[j]), j))
+        res = wait_all(srv, [t for t, _ in order])
+    finally:
+        srv.destroy()
+    seen = 0
+    for (t, j), r in zip(order, res):
+        if j is not None:
+            assert r[0] == alone[j][0] and r[1] == alone[j][1], (j, r, alone[j])
+            seen += 1
+    assert seen == 3
+
+
+def test_serving_mixed_precision_bound(gbs, kern):
+    K, m = kern
+    pats = requests(m, 60, 13, n_values=range(8, 21, 2))
+    srv = gbs.Server(K)
+    try:
+        t64 = [srv.submit(x, gbs.FP64) for x in pats]
+        t32 = [srv.submit(x, gbs.MIXED) for x in pats]
+        r64 = wait_all(srv, t64)
+        r32 = wait_all(srv, t32)
+    finally:
+        srv.destroy()
+    for a, b in zip(r64, r32):
+        assert abs(b[1] - a[1]) <= b[2] * abs(a[1])
+
+
+def test_serving_host_failures(gbs, kern):
+    K, m = kern
+    srv = gbs.Server(K, max_slots=1, queue_capacity=3, subsets_per_step=64)
+    try:
+        big = np.arange(24, dtype=np.int32)
+        tickets, refused = [], 0
+        for _ in range(50):
+            t = srv.submit(big)
+            if t < 0:
+                refused += 1
+            else:
+                tickets.append(t)
+        assert refused > 0  # GBS_EAGAIN once the queue is full
+        with pytest.raises(gbs.GbsError) as ei:
+            srv.submit(np.array([0, m + 5], np.int32))
+        assert ei.value.code == -3
+        # odd n and n = 0 are answered without device work
+        t_odd = srv.submit(np.array([1, 2, 3], np.int32))
+        t_vac = srv.submit(np.array([], np.int32))
+        r_odd = srv.poll(t_odd)
+        r_vac = srv.poll(t_vac)
+        assert r_odd[0] == 0 and r_odd[1] == 0
+        assert abs(r_vac[0] - np.exp(-K.log_norm)) <= 1e-15 and r_vac[1] == 1
+        wait_all(srv, tickets)
+        with pytest.raises(gbs.GbsError) as ei:
+            srv.poll(tickets[0])  # already collected
+        assert ei.value.code == -7
+    finally:
+        srv.destroy()
