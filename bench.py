@@ -197,6 +197,9 @@ def main():
     def step():
         gbs.prob_batch(K, d_idx, n, offs, gbs.FP64, p_out=p, logp_out=lp, haf_out=hf, err_out=er)
 
+    # launch shape for n = 16 from the library's autotuner (untimed)
+    tuned_rounds = gbs.autotune(16, gbs.FP64)
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -250,7 +253,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "M=64 Haar U seed 1, r~U[0.6,1.0], 4096 collision-free n=16 patterns, FP64",
-                   "patterns_per_step": b, "l2": "flushed (256 MB write) between timed steps"},
+                   "patterns_per_step": b, "l2": "flushed (256 MB write) between timed steps",
+                   "autotuned_rounds_per_item": tuned_rounds},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "haf_subsets_kernel<double>", "kernel_ms": t_kern,
@@ -304,6 +308,7 @@ def extras(gbs, torch):
     # mixed path on the headline workload
     U, r, pats = W.workload(WORKLOAD)
     K = gbs.build_kernel(U, r)
+    gbs.autotune(16, gbs.MIXED)
     t64, k64, h64, _ = timed_batch(gbs, torch, K, pats, gbs.FP64)
     t32, k32, h32, e32 = timed_batch(gbs, torch, K, pats, gbs.MIXED)
     relerr = np.abs(h32 - h64) / np.abs(h64)
@@ -314,6 +319,9 @@ def extras(gbs, torch):
     # mixed-n workload with collisions
     U, r, pats = W.workload("mixed_m144")
     K = gbs.build_kernel(U, r)
+    for nn in range(8, 25, 2):
+        gbs.autotune(nn, gbs.FP64)
+        gbs.autotune(nn, gbs.MIXED)
     t64, k64, h64, e64 = timed_batch(gbs, torch, K, pats, gbs.FP64)
     t32, k32, h32, e32 = timed_batch(gbs, torch, K, pats, gbs.MIXED)
     fl = sum(model_flops(len(p)) for p in pats)
@@ -326,6 +334,8 @@ def extras(gbs, torch):
     # large instances
     U, r, pats = W.workload("large_m900")
     K = gbs.build_kernel(U, r)
+    gbs.autotune(28, gbs.FP64)
+    gbs.autotune(30, gbs.FP64)
     t64, k64, h64, e64 = timed_batch(gbs, torch, K, pats, gbs.FP64, reps=2)
     fl = sum(model_flops(len(p)) for p in pats)
     out["large_m900"] = {"probs_per_s": len(pats) / (t64 * 1e-3), "ms": t64, "kernel_ms": k64,

@@ -191,6 +191,19 @@ int gbs_serve_submit(gbs_server* s, const int* idx, int n, int precision, int64_
  * or a negative error (GBS_ENOENT for an unknown or already-collected ticket). */
 int gbs_serve_poll(gbs_server* s, int64_t ticket, double* p, double* haf_ri, double* err_est);
 
+/* Counters of a server since creation (for monitoring; the paper has no
+ * counterpart). Step wall time runs from a step's launch to the host seeing
+ * its completion event. */
+typedef struct gbs_serve_stats_t {
+  int64_t steps;          /* steps launched */
+  int64_t items;          /* work items dispatched */
+  int64_t subsets;        /* subset terms dispatched */
+  int64_t completed;      /* requests finished on the device */
+  double step_wall_s;     /* summed step wall time */
+  double step_wall_max_s; /* longest step */
+} gbs_serve_stats_t;
+int gbs_serve_stats(gbs_server* s, gbs_serve_stats_t* out);
+
 /* Stop the server thread (after finishing resident work, bounded by the
  * timeout) and free its resources. */
 int gbs_serve_destroy(gbs_server* s);

@@ -39,6 +39,12 @@ class GbsError(RuntimeError):
         self.code = code
 
 
+class ServeStats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("items", ctypes.c_int64), ("subsets", ctypes.c_int64),
+                ("completed", ctypes.c_int64), ("step_wall_s", ctypes.c_double),
+                ("step_wall_max_s", ctypes.c_double)]
+
+
 class ServeOpts(ctypes.Structure):
     _fields_ = [("max_slots", ctypes.c_int), ("mem_budget", ctypes.c_size_t),
                 ("queue_capacity", ctypes.c_int), ("subsets_per_step", ctypes.c_int),
@@ -62,11 +68,11 @@ def lib():
             L.gbs_prob_batch.argtypes = [vp, ip, ip, i64p, ctypes.c_int, ctypes.c_int, vp, dp, dp, dp, dp]
             L.gbs_autotune.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int)]
             L.gbs_set_timing_events.argtypes = [vp, vp]
-            if hasattr(L, "gbs_serve_create"):
-                L.gbs_serve_create.argtypes = [vp, ctypes.POINTER(ServeOpts), ctypes.POINTER(ctypes.c_void_p)]
-                L.gbs_serve_submit.argtypes = [vp, ip, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
-                L.gbs_serve_poll.argtypes = [vp, ctypes.c_int64, dp, dp, dp]
-                L.gbs_serve_destroy.argtypes = [vp]
+            L.gbs_serve_create.argtypes = [vp, ctypes.POINTER(ServeOpts), ctypes.POINTER(ctypes.c_void_p)]
+            L.gbs_serve_submit.argtypes = [vp, ip, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
+            L.gbs_serve_poll.argtypes = [vp, ctypes.c_int64, dp, dp, dp]
+            L.gbs_serve_destroy.argtypes = [vp]
+            L.gbs_serve_stats.argtypes = [vp, ctypes.POINTER(ServeStats)]
             L.gbs_last_error.restype = ctypes.c_char_p
             _lib = L
     return _lib
@@ -249,6 +255,11 @@ class Server:
             return None
         _check(rc)
         return p.value, complex(hf[0], hf[1]), e.value
+
+    def stats(self) -> dict:
+        st = ServeStats()
+        _check(lib().gbs_serve_stats(self.handle, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServeStats._fields_}
 
     def destroy(self):
         if self.handle:

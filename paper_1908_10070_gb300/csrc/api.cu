@@ -209,94 +209,87 @@ bool shape_fits(int precision, int warp_bytes, int maxn) {
   return true;
 }
 
-static int64_t binom64(int a, int b) {
+int64_t binom64(int a, int b) {
   if (b < 0 || b > a) return 0;
   int64_t r = 1;
   for (int i = 1; i <= b; ++i) r = r * (a - b + i) / i;
   return r;
 }
 
-// Build the pattern descriptors and the work items. Items of each pattern are
-// numbered consecutively (their partial slots), and the schedule order lists
-// the most expensive items first (longest-first list scheduling), bucketed by
-// (subset order, rounds) so the cost is O(items).
-int plan_batch(const int* n, int batch, int precision, int warp_bytes, const int* rounds_for_n,
-               std::vector<PatDesc>& pats, std::vector<WorkItem>& items) {
+// Work-item planning in two passes over per-n templates. Every matrix of order
+// n gets the same list of items (subset size s, first colex rank, count); items
+// of one matrix take consecutive partial slots (pattern order), and the
+// schedule lists the most expensive items first (longest-first list
+// scheduling) by bucketing on (s, rounds), whose cost is rounds * (2s)^3.
+void Planner::init(const int* n, int batch, int precision, int warp_bytes, const int* rounds_for_n) {
+  n_ = n;
+  batch_ = batch;
   const int cb = complex_bytes(precision);
-  auto groups = [&](int s, int h) { return 32 / lanes_for(2 * s, h, warp_bytes, cb); };
-  pats.resize(batch);
-  std::vector<WorkItem> ordered;
-  // count items
-  int64_t total = 0;
-  for (int b = 0; b < batch; ++b) {
-    const int nb = n[b];
-    if (nb < 2 || (nb & 1)) continue;
-    const int h = nb / 2;
-    const int R = rounds_for_n[nb];
-    for (int s = 1; s <= h; ++s) {
-      const int G = groups(s, h);
-      const int64_t cap = (int64_t)G * R;
-      total += (binom64(h, s) + cap - 1) / cap;
-    }
+  for (int v = 0; v <= kMaxN; ++v) {
+    tmpl_[v].clear();
+    npat_[v] = 0;
   }
-  if (total > (int64_t)1 << 30) return fail(GBS_ENOMEM, "too many work items (%lld)", (long long)total);
-  ordered.resize((size_t)total);
-  // bucket key: N/2 (1..16) and rounds used (1..64) -> cost ~ rounds * N^3
-  const int KEYS = (kMaxN / 2 + 1) * 65;
-  std::vector<int64_t> bucket_count(KEYS, 0);
-  int64_t q = 0;
-  for (int b = 0; b < batch; ++b) {
-    const int nb = n[b];
-    PatDesc& d = pats[b];
-    d.n = nb;
-    d.item_begin = (int)q;
-    if (nb >= 2 && !(nb & 1)) {
-      const int h = nb / 2;
-      const int R = rounds_for_n[nb];
-      for (int s = 1; s <= h; ++s) {
-        const int G = groups(s, h);
-        const int64_t cnt = binom64(h, s);
-        const int64_t cap = (int64_t)G * R;
-        for (int64_t r0 = 0; r0 < cnt; r0 += cap) {
-          WorkItem w;
-          w.pat = b;
-          w.s = s;
-          w.rank0 = (int)r0;
-          w.count = (int)std::min<int64_t>(cap, cnt - r0);
-          w.part = (int)q;
-          w.pad[0] = w.pad[1] = w.pad[2] = 0;
-          ordered[(size_t)q++] = w;
-          const int rnds = (w.count + G - 1) / G;
-          bucket_count[s * 65 + std::min(rnds, 64)]++;
-
-        }
+  for (int b = 0; b < batch; ++b) npat_[n[b]]++;
+  std::fill(bucket_, bucket_ + kKeys, 0);
+  total_ = 0;
+  for (int v = 2; v <= kMaxN; v += 2) {
+    if (!npat_[v]) continue;
+    const int h = v / 2, R = rounds_for_n[v];
+    for (int sz = 1; sz <= h; ++sz) {
+      const int G = 32 / lanes_for(2 * sz, h, warp_bytes, cb);
+      const int64_t cnt = binom64(h, sz), cap = (int64_t)G * R;
+      for (int64_t r0 = 0; r0 < cnt; r0 += cap) {
+        ItemTemplate t;
+        t.s = sz;
+        t.rank0 = (int)r0;
+        t.count = (int)std::min<int64_t>(cap, cnt - r0);
+        const int rnds = std::min((t.count + G - 1) / G, 64);
+        t.key = sz * 65 + rnds;
+        tmpl_[v].push_back(t);
+        bucket_[t.key] += npat_[v];
       }
     }
-    d.item_end = (int)q;
+    total_ += (int64_t)tmpl_[v].size() * npat_[v];
   }
-  // schedule: descending cost = rounds * N^3 -> iterate keys by cost
-  std::vector<std::pair<int64_t, int>> keys;
-  for (int k = 0; k < KEYS; ++k)
-    if (bucket_count[k]) {
-      const int s = k / 65, r = k % 65;
-      const int64_t N = 2 * s;
-      keys.push_back(std::make_pair(-(int64_t)r * N * N * N, k));
-    }
-  std::sort(keys.begin(), keys.end());
-  std::vector<int64_t> start(KEYS, 0);
+  // bucket start offsets, most expensive key first
+  int order[kKeys];
+  int nk = 0;
+  for (int k = 0; k < kKeys; ++k)
+    if (bucket_[k]) order[nk++] = k;
+  std::sort(order, order + nk, [](int x, int y) {
+    const int64_t sx = x / 65, rx = x % 65, sy = y / 65, ry = y % 65;
+    const int64_t cx = rx * sx * sx * sx, cy = ry * sy * sy * sy;
+    return cx != cy ? cx > cy : x < y;
+  });
   int64_t acc = 0;
-  for (auto& kv : keys) {
-    start[kv.second] = acc;
-    acc += bucket_count[kv.second];
+  for (int q = 0; q < nk; ++q) {
+    start_[order[q]] = acc;
+    acc += bucket_[order[q]];
   }
-  items.resize((size_t)total);
-  for (int64_t i = 0; i < total; ++i) {
-    const WorkItem& w = ordered[(size_t)i];
-    const int G = groups(w.s, n[w.pat] / 2);
-    const int rnds = (w.count + G - 1) / G;
-    items[(size_t)start[w.s * 65 + std::min(rnds, 64)]++] = w;
+}
+
+void Planner::fill(PatDesc* pats, WorkItem* items) {
+  int64_t next[kKeys];
+  std::copy(start_, start_ + kKeys, next);
+  int q = 0;
+  for (int b = 0; b < batch_; ++b) {
+    PatDesc& d = pats[b];
+    const int v = n_[b];
+    d.n = v;
+    d.item_begin = q;
+    if (v >= 2 && !(v & 1)) {
+      for (const ItemTemplate& t : tmpl_[v]) {
+        WorkItem& w = items[next[t.key]++];
+        w.pat = b;
+        w.s = t.s;
+        w.rank0 = t.rank0;
+        w.count = t.count;
+        w.part = q++;
+        w.pad[0] = w.pad[1] = w.pad[2] = 0;
+      }
+    }
+    d.item_end = q;
   }
-  return GBS_OK;
 }
 
 static cudaEvent_t g_time_start = nullptr, g_time_stop = nullptr;
@@ -334,24 +327,25 @@ int run_batch(const BatchArgs& a) {
   if (!shape_fits(a.precision, cfg.warp_bytes, maxn))
     return fail(GBS_EINVAL, "warp_bytes %d too small for n = %d", cfg.warp_bytes, maxn);
 
-  std::vector<PatDesc> pats;
-  std::vector<WorkItem> items;
-  int rc = plan_batch(a.n, batch, a.precision, cfg.warp_bytes, rounds_for_n, pats, items);
-  if (rc) return rc;
-  // source offsets / index lists
-  for (int b = 0; b < batch; ++b) {
-    PatDesc& d = pats[b];
-    if (a.mode == BatchArgs::HAFNIAN) {
-      d.src_off = a.offs[b];
-      d.idx_off = -1;
-      d.ld = a.n[b];
-    } else {
-      d.src_off = 0;
-      d.idx_off = a.offs[b];
-      d.ld = a.m;
+  Planner plan;
+  plan.init(a.n, batch, a.precision, cfg.warp_bytes, rounds_for_n);
+  if (!a.cfg_override) {
+    // A small batch gets smaller work items (fewer rounds each), so that there
+    // are a few items per resident warp to balance the load over all SMs.
+    const int64_t want = 4LL * device_sm_count() * cfg.warps_per_block;
+    for (int iter = 0; iter < 6 && plan.total() < want; ++iter) {
+      bool shrunk = false;
+      for (int v = 0; v <= kMaxN; ++v)
+        if (rounds_for_n[v] > 1) {
+          rounds_for_n[v] /= 2;
+          shrunk = true;
+        }
+      if (!shrunk) break;
+      plan.init(a.n, batch, a.precision, cfg.warp_bytes, rounds_for_n);
     }
   }
-  const int64_t n_items = (int64_t)items.size();
+  const int64_t n_items = plan.total();
+  if (n_items > ((int64_t)1 << 30)) return fail(GBS_ENOMEM, "too many work items (%lld)", (long long)n_items);
 
   // host-side checks and sizes of the inputs to stage
   const bool src_dev = (a.mode == BatchArgs::HAFNIAN) ? is_device_ptr(a.src) : true;
@@ -394,11 +388,23 @@ int run_batch(const BatchArgs& a) {
 
   void* host_stage = nullptr;
   int slot = -1;
-  rc = pinned_acquire(up_b, &host_stage, &slot);
+  int rc = pinned_acquire(up_b, &host_stage, &slot);
   if (rc) return rc;
   unsigned char* hs = (unsigned char*)host_stage;
-  memcpy(hs, pats.data(), sizeof(PatDesc) * batch);
-  if (n_items) memcpy(hs + pats_b, items.data(), sizeof(WorkItem) * n_items);
+  PatDesc* h_pats = (PatDesc*)hs;
+  plan.fill(h_pats, (WorkItem*)(hs + pats_b));
+  for (int b = 0; b < batch; ++b) {
+    PatDesc& d = h_pats[b];
+    if (a.mode == BatchArgs::HAFNIAN) {
+      d.src_off = a.offs[b];
+      d.idx_off = -1;
+      d.ld = a.n[b];
+    } else {
+      d.src_off = 0;
+      d.idx_off = a.offs[b];
+      d.ld = a.m;
+    }
+  }
   if (idx_b) memcpy(hs + pats_b + items_b, a.idx, sizeof(int) * idx_elems);
   if (src_b) memcpy(hs + pats_b + items_b + idx_b, a.src, 16 * (size_t)src_elems);
 

@@ -9,6 +9,12 @@
 
 #include "gbs_internal.cuh"
 
+namespace gbs {
+struct ItemTemplate {
+  int s, rank0, count, key;
+};
+}  // namespace gbs
+
 struct gbs_kernel {
   int device = 0;
   int m = 0;
@@ -58,8 +64,27 @@ TuneCfg get_cfg(int precision, int n);
 void set_cfg(int precision, int n, const TuneCfg& c);
 int complex_bytes(int precision);
 bool shape_fits(int precision, int warp_bytes, int maxn);
-int plan_batch(const int* n, int batch, int precision, int warp_bytes, const int* rounds_for_n,
-               std::vector<PatDesc>& pats, std::vector<WorkItem>& items);
+int64_t binom64(int a, int b);
+
+struct ItemTemplate;
+// Work items of a batch: init() counts them, fill() writes the descriptors'
+// item ranges and the items (in schedule order) into caller memory.
+class Planner {
+ public:
+  void init(const int* n, int batch, int precision, int warp_bytes, const int* rounds_for_n);
+  void fill(PatDesc* pats, WorkItem* items);
+  int64_t total() const { return total_; }
+
+ private:
+  static constexpr int kKeys = (kMaxN / 2 + 1) * 65;
+  const int* n_ = nullptr;
+  int batch_ = 0;
+  int64_t total_ = 0;
+  int npat_[kMaxN + 1];
+  std::vector<ItemTemplate> tmpl_[kMaxN + 1];
+  int64_t bucket_[kKeys];
+  int64_t start_[kKeys];
+};
 int device_sm_count();
 int run_batch(const BatchArgs& a);
 

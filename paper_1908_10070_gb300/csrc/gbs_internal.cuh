@@ -42,11 +42,10 @@ constexpr int kMaxN = GBS_MAX_N;
 constexpr int kMaxH = kMaxN / 2;
 constexpr int kWarpHeaderBytes = 128;  // per-warp index-list buffer (32 ints)
 
-// Power-trace schedule for h = n/2 (see haf_subsets.cu): s baby powers, then
-// giant powers R_{3m}; nbuf packed symmetric matrices are live at once.
-__host__ __device__ inline int sched_s(int h) { return h <= 2 ? 1 : (h <= 4 ? 2 : 3); }
+// Packed symmetric matrices live at once in the power-trace schedule for
+// h = n/2 (see haf_subsets.cu).
 __host__ __device__ inline int sched_nbuf(int h) {
-  return h <= 2 ? 1 : (h <= 4 ? 2 : (h <= 6 ? 3 : (h <= 9 ? 4 : 5)));
+  return h <= 2 ? 1 : (h <= 4 ? 2 : (h <= 6 ? 3 : (h <= 10 ? 4 : 5)));
 }
 
 // Shared-memory bytes of one lane group's region for subsets of order N (and

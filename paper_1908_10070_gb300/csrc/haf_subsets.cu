@@ -13,8 +13,8 @@
 //      R_{a+b} = R_a X R_b  (symmetric, so only the upper triangle is
 //      computed), tr(X R_k) = 2 sum_t R_k[2t][2t+1] and
 //      tr(X R_a X R_b) = sum_{i,j} R_a[i][j] R_b[i^1][j^1];
-//      baby powers R_1..R_s and giant powers R_{3m} cover k = 1..h with at
-//      most five products for h <= 15,
+//      a fixed schedule per h picks the fewest such products that cover
+//      k = 1..h (at most five for h <= 15),
 //   3. expands e = exp(sum_k tr_k x^k / (2k)): e_k = (1/(2k)) sum_j tr_j e_{k-j},
 //      f = e_h,
 //   4. adds (-1)^{h-|S|} f to a compensated (double-double or float-float)
@@ -108,6 +108,37 @@ struct Tables {
   double inv2k[kMaxH + 1];          // 1 / (2k)
 };
 
+// Power-trace schedule per h: the fewest products R_{a+b} = R_a X R_b whose
+// index set F (with R_1 = A_S) satisfies F + F >= {1..h}, each trace k taken
+// as tr(X R_k) when k is in F, else tr(X R_a X R_b) with a + b = k, and each
+// R kept in one of sched_nbuf(h) buffers (a buffer is reused once its traces
+// are taken). Products per h = 1..16: 0 0 1 1 2 2 3 3 3 3 4 4 4 4 5 6.
+enum { kEnd = -1, kProd = 0, kTr1 = 1, kTr2 = 2 };
+struct SchedOp {
+  signed char kind;  // kProd: buf[k] = buf[a] X buf[b]; kTr1: p_k = tr(X buf[a]); kTr2: p_k = tr(X buf[a] X buf[b])
+  signed char k, a, b;
+};
+constexpr int kMaxOps = 24;
+__constant__ SchedOp c_sched[kMaxH + 1][kMaxOps] = {
+    {{kEnd, 0, 0, 0}},  // h = 0
+    {{kTr1, 1, 0, 0}, {kEnd, 0, 0, 0}},  // h = 1
+    {{kTr1, 1, 0, 0}, {kTr2, 2, 0, 0}, {kEnd, 0, 0, 0}},  // h = 2
+    {{kProd, 1, 0, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr2, 3, 1, 0}, {kEnd, 0, 0, 0}},  // h = 3
+    {{kProd, 1, 0, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr2, 3, 1, 0}, {kTr2, 4, 1, 1}, {kEnd, 0, 0, 0}},  // h = 4
+    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 2, 0}, {kTr2, 5, 2, 1}, {kEnd, 0, 0, 0}},  // h = 5
+    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 2, 0}, {kTr2, 5, 2, 1}, {kTr2, 6, 2, 2}, {kEnd, 0, 0, 0}},  // h = 6
+    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kProd, 3, 2, 1}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 2, 0}, {kTr1, 5, 3, 0}, {kTr2, 6, 3, 0}, {kTr2, 7, 3, 1}, {kEnd, 0, 0, 0}},  // h = 7
+    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kProd, 3, 2, 1}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 2, 0}, {kTr1, 5, 3, 0}, {kTr2, 6, 3, 0}, {kTr2, 7, 3, 1}, {kTr2, 8, 3, 2}, {kEnd, 0, 0, 0}},  // h = 8
+    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kProd, 3, 2, 2}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 2, 0}, {kTr2, 5, 2, 1}, {kTr1, 6, 3, 0}, {kTr2, 7, 3, 0}, {kTr2, 8, 3, 1}, {kTr2, 9, 3, 2}, {kEnd, 0, 0, 0}},  // h = 9
+    {{kProd, 1, 0, 0}, {kProd, 2, 1, 1}, {kProd, 3, 2, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr2, 3, 1, 0}, {kTr1, 4, 2, 0}, {kTr1, 5, 3, 0}, {kTr2, 6, 2, 1}, {kTr2, 7, 3, 1}, {kTr2, 8, 2, 2}, {kTr2, 9, 3, 2}, {kTr2, 10, 3, 3}, {kEnd, 0, 0, 0}},  // h = 10
+    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kProd, 3, 2, 1}, {kProd, 4, 3, 2}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 2, 0}, {kTr1, 5, 3, 0}, {kTr2, 6, 3, 0}, {kTr2, 7, 3, 1}, {kTr1, 8, 4, 0}, {kTr2, 9, 4, 0}, {kTr2, 10, 4, 1}, {kTr2, 11, 4, 2}, {kEnd, 0, 0, 0}},  // h = 11
+    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kProd, 3, 2, 2}, {kProd, 4, 3, 2}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 2, 0}, {kTr2, 5, 2, 1}, {kTr1, 6, 3, 0}, {kTr2, 7, 3, 0}, {kTr2, 8, 3, 1}, {kTr1, 9, 4, 0}, {kTr2, 10, 4, 0}, {kTr2, 11, 4, 1}, {kTr2, 12, 4, 2}, {kEnd, 0, 0, 0}},  // h = 12
+    {{kProd, 1, 0, 0}, {kProd, 2, 1, 1}, {kProd, 3, 2, 1}, {kProd, 4, 3, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr2, 3, 1, 0}, {kTr1, 4, 2, 0}, {kTr2, 5, 2, 0}, {kTr1, 6, 3, 0}, {kTr1, 7, 4, 0}, {kTr2, 8, 2, 2}, {kTr2, 9, 4, 1}, {kTr2, 10, 3, 2}, {kTr2, 11, 4, 2}, {kTr2, 12, 3, 3}, {kTr2, 13, 4, 3}, {kEnd, 0, 0, 0}},  // h = 13
+    {{kProd, 1, 0, 0}, {kProd, 2, 1, 1}, {kProd, 3, 2, 1}, {kProd, 4, 3, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr2, 3, 1, 0}, {kTr1, 4, 2, 0}, {kTr2, 5, 2, 0}, {kTr1, 6, 3, 0}, {kTr1, 7, 4, 0}, {kTr2, 8, 2, 2}, {kTr2, 9, 4, 1}, {kTr2, 10, 3, 2}, {kTr2, 11, 4, 2}, {kTr2, 12, 3, 3}, {kTr2, 13, 4, 3}, {kTr2, 14, 4, 4}, {kEnd, 0, 0, 0}},  // h = 14
+    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 2, 0}, {kTr2, 5, 2, 1}, {kProd, 3, 2, 2}, {kTr1, 6, 3, 0}, {kTr2, 7, 3, 0}, {kTr2, 8, 3, 1}, {kProd, 4, 3, 2}, {kTr1, 9, 4, 0}, {kTr2, 10, 4, 0}, {kTr2, 11, 4, 1}, {kProd, 3, 4, 2}, {kTr1, 12, 3, 0}, {kTr2, 13, 3, 0}, {kTr2, 14, 3, 1}, {kTr2, 15, 3, 2}, {kEnd, 0, 0, 0}},  // h = 15
+    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 2, 0}, {kTr2, 5, 2, 1}, {kProd, 3, 2, 2}, {kTr1, 6, 3, 0}, {kTr2, 7, 3, 0}, {kTr2, 8, 3, 1}, {kProd, 4, 3, 2}, {kTr1, 9, 4, 0}, {kTr2, 10, 4, 0}, {kTr2, 11, 4, 1}, {kProd, 3, 4, 2}, {kTr1, 12, 3, 0}, {kTr2, 13, 3, 0}, {kTr2, 14, 3, 1}, {kTr2, 15, 3, 2}, {kProd, 4, 3, 2}, {kTr2, 16, 4, 0}, {kEnd, 0, 0, 0}},  // h = 16
+};
+
 // Position of entry (r, c) of a symmetric N x N matrix stored as its packed
 // upper triangle, rows in order: row r holds columns r..N-1.
 __device__ __forceinline__ int tri_off(int r, int N) { return r * N - ((r * (r - 1)) >> 1); }
@@ -135,22 +166,37 @@ __device__ __forceinline__ C2<T> group_sum(C2<T> v, int L) {
   return v;
 }
 
-// dst = Ra X Rb (upper triangle), X swapping 2t <-> 2t+1.
+// dst = Ra X Rb (upper triangle), X swapping 2t <-> 2t+1. Each lane takes
+// two output entries at a time (e and e + L) so that four independent FMA
+// chains are in flight.
 template <typename T>
 __device__ __forceinline__ void sym_prod(C2<T>* __restrict__ dst, const C2<T>* __restrict__ Ra,
                                          const C2<T>* __restrict__ Rb, int N, int P, int l, int L) {
-  int i = 0, j = l;
-  tri_advance(i, j, 0, N);
-  for (int e = l; e < P; e += L) {
-    C2<T> acc = mk<T>(T(0), T(0));
-    const int oi = tri_off(i, N);
-    for (int k = 0; k < N; ++k) {
-      const C2<T> a = (k >= i) ? Ra[oi + k - i] : Ra[tri_off(k, N) + i - k];
-      const C2<T> b = Rb[tri_pos(k ^ 1, j, N)];
-      acc = cfma<T>(a, b, acc);
+  int i1 = 0, j1 = l;
+  tri_advance(i1, j1, 0, N);
+  for (int e = l; e < P; e += 2 * L) {
+    int i2 = i1, j2 = j1;
+    tri_advance(i2, j2, L, N);
+    const bool two = (e + L < P);
+    if (!two) {  // keep the second entry's loads in range; its result is dropped
+      i2 = i1;
+      j2 = j1;
     }
-    dst[e] = acc;
-    tri_advance(i, j, L, N);
+    C2<T> acc1 = mk<T>(T(0), T(0)), acc2 = mk<T>(T(0), T(0));
+    const int o1 = tri_off(i1, N), o2 = tri_off(i2, N);
+    for (int k = 0; k < N; ++k) {
+      const int ok = tri_off(k, N);
+      const C2<T> a1 = (k >= i1) ? Ra[o1 + k - i1] : Ra[ok + i1 - k];
+      const C2<T> a2 = (k >= i2) ? Ra[o2 + k - i2] : Ra[ok + i2 - k];
+      const int r = k ^ 1;
+      const C2<T> b1 = Rb[tri_pos(r, j1, N)];
+      const C2<T> b2 = Rb[tri_pos(r, j2, N)];
+      acc1 = cfma<T>(a1, b1, acc1);
+      acc2 = cfma<T>(a2, b2, acc2);
+    }
+    dst[e] = acc1;
+    if (two) dst[e + L] = acc2;
+    tri_advance(i1, j1, 2 * L, N);
   }
 }
 
@@ -225,7 +271,6 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
     const int L = lanes_for(N, h, P.warp_bytes, cb);
     const int G = 32 / L;
     const int g = lane / L, l = lane - g * L;
-    const int sb = sched_s(h);
 
     if (lane < n) {
       int v = (d.idx_off >= 0) ? P.idx[d.idx_off + lane] : lane;
@@ -281,36 +326,20 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
         }
       }
       __syncwarp();
-      // -- power traces: baby powers R_1..R_sb in buffers 0..sb-1
-      for (int b = 2; b <= sb; ++b) {
-        sym_prod<T>(buf + (b - 1) * NP, buf + (b - 2) * NP, buf, N, NP, l, L);
+      // -- power traces tr((X A_S)^k), k = 1..h, by the schedule for h
+      for (int o = 0; o < kMaxOps; ++o) {
+        const SchedOp op = c_sched[h][o];
+        if (op.kind == kEnd) break;
+        if (op.kind == kProd) {
+          sym_prod<T>(buf + op.k * NP, buf + op.a * NP, buf + op.b * NP, N, NP, l, L);
+        } else {
+          const C part = (op.kind == kTr1) ? tr1_part<T>(buf + op.a * NP, N, l, L)
+                                           : tr2_part<T>(buf + op.a * NP, buf + op.b * NP, N, NP, l, L);
+          const C t = group_sum<T>(part, L);
+          if (l == 0) pk[op.k] = t;
+        }
         __syncwarp();
       }
-      for (int k = 1; k <= min(sb, h); ++k) {
-        const C t = group_sum<T>(tr1_part<T>(buf + (k - 1) * NP, N, l, L), L);
-        if (l == 0) pk[k] = t;
-      }
-      for (int k = sb + 1; k <= min(2 * sb, h); ++k) {
-        const C t = group_sum<T>(tr2_part<T>(buf + (sb - 1) * NP, buf + (k - sb - 1) * NP, N, NP, l, L), L);
-        if (l == 0) pk[k] = t;
-      }
-      // giant powers R_{m sb}, m >= 2, alternating between buffers sb and sb+1
-      {
-        const C* prev = buf + (sb - 1) * NP;
-        int slot = 0;
-        for (int m = 2; m * sb + 1 <= h; ++m) {
-          C* cur = buf + (sb + slot) * NP;
-          sym_prod<T>(cur, prev, buf + (sb - 1) * NP, N, NP, l, L);
-          __syncwarp();
-          for (int b = 1; b <= sb && m * sb + b <= h; ++b) {
-            const C t = group_sum<T>(tr2_part<T>(cur, buf + (b - 1) * NP, N, NP, l, L), L);
-            if (l == 0) pk[m * sb + b] = t;
-          }
-          prev = cur;
-          slot ^= 1;
-        }
-      }
-      __syncwarp();
       // -- exponential series and signed accumulation (one lane per group)
       if (l == 0) {
         ek[0] = mk<T>(T(1), T(0));
@@ -356,52 +385,65 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
   }
 }
 
+// One warp per pattern: lane j adds the item partials j, j+32, ... in order,
+// the lanes' sums meet in a fixed butterfly (deterministic for a given item
+// count), and lane 0 writes the outputs.
 __global__ void finalize_kernel(const FinalizeLaunch F) {
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < F.batch; b += gridDim.x * blockDim.x) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  for (int b = blockIdx.x * wpb + (threadIdx.x >> 5); b < F.batch; b += gridDim.x * wpb) {
     const int pb = F.sel ? F.sel[b] : b;
     const PatDesc d = F.pats[pb];
     const int n = d.n;
     double rh = 0, rl = 0, ih = 0, il = 0, K = 0;
-    if (n & 1) {
-      // odd n: no perfect matching, Haf = 0 (Sec. 3.1: P_n = 0 for odd n)
-    } else if (n == 0) {
-      rh = 1.0;
-      K = 1.0;
-    } else {
-      for (int q = d.item_begin; q < d.item_end; ++q) {
+    if (!(n & 1) && n > 0) {
+      for (int q = d.item_begin + lane; q < d.item_end; q += 32) {
         const Partial pr = F.parts[q];
         dd_add(rh, rl, pr.re_hi, pr.re_lo);
         dd_add(ih, il, pr.im_hi, pr.im_lo);
         K += pr.kappa;
       }
-    }
-    const bool bad = F.status != nullptr && F.status[pb] != 0;
-    const double hr = rh + rl, hi = ih + il;
-    const double mod = hypot(hr, hi);
-    const double kappa = (mod > 0.0) ? K / mod : (K > 0.0 ? INFINITY : 0.0);
-    const double nan = __longlong_as_double(0x7ff8000000000000ll);
-    if (F.haf_out) {
-      F.haf_out[2 * b] = bad ? nan : hr;
-      F.haf_out[2 * b + 1] = bad ? nan : hi;
-    }
-    if (F.kappa_out) F.kappa_out[b] = bad ? nan : kappa;
-    if (F.p_out || F.logp_out || F.err_out) {
-      // sum_j log s_j!: the c-th occurrence of a mode contributes log c
-      double log_fact = 0.0;
-      if (d.idx_off >= 0) {
-        for (int i = 0; i < n; ++i) {
-          const int xi = F.idx[d.idx_off + i];
-          int c = 1;
-          for (int j = 0; j < i; ++j) c += (F.idx[d.idx_off + j] == xi);
-          if (c > 1) log_fact += log((double)c);
-        }
+      for (int off = 16; off > 0; off >>= 1) {
+        const double orh = __shfl_xor_sync(FULL, rh, off), orl = __shfl_xor_sync(FULL, rl, off);
+        const double oih = __shfl_xor_sync(FULL, ih, off), oil = __shfl_xor_sync(FULL, il, off);
+        K += __shfl_xor_sync(FULL, K, off);
+        dd_add(rh, rl, orh, orl);
+        dd_add(ih, il, oih, oil);
       }
-      const double L = F.log_norm ? *F.log_norm : 0.0;
-      const double logp = (mod > 0.0) ? 2.0 * log(mod) - log_fact - L : -INFINITY;
-      const double u = (F.precision == GBS_FP64) ? 0x1p-53 : 0x1p-24;
-      if (F.p_out) F.p_out[b] = bad ? nan : ((mod > 0.0) ? exp(logp) : 0.0);
-      if (F.logp_out) F.logp_out[b] = bad ? nan : logp;
-      if (F.err_out) F.err_out[b] = bad ? nan : (double)(n > 0 ? n : 1) * u * kappa;
+    } else if (n == 0) {
+      rh = 1.0;  // the empty matrix has one (empty) perfect matching
+      K = 1.0;
+    }
+    // odd n: no perfect matching, Haf = 0 (Sec. 3.1: P_n = 0 for odd n)
+    // sum_j log s_j!: the c-th occurrence of a mode contributes log c
+    double lf = 0.0;
+    if (d.idx_off >= 0 && lane < n && (F.p_out || F.logp_out || F.err_out)) {
+      const int xi = F.idx[d.idx_off + lane];
+      int c = 1;
+      for (int j = 0; j < lane; ++j) c += (F.idx[d.idx_off + j] == xi);
+      if (c > 1) lf = log((double)c);
+    }
+    for (int off = 16; off > 0; off >>= 1) lf += __shfl_xor_sync(FULL, lf, off);
+    if (lane == 0) {
+      const bool bad = F.status != nullptr && F.status[pb] != 0;
+      const double hr = rh + rl, hi = ih + il;
+      const double mod = hypot(hr, hi);
+      const double kappa = (mod > 0.0) ? K / mod : (K > 0.0 ? INFINITY : 0.0);
+      const double nan = __longlong_as_double(0x7ff8000000000000ll);
+      if (F.haf_out) {
+        F.haf_out[2 * b] = bad ? nan : hr;
+        F.haf_out[2 * b + 1] = bad ? nan : hi;
+      }
+      if (F.kappa_out) F.kappa_out[b] = bad ? nan : kappa;
+      if (F.p_out || F.logp_out || F.err_out) {
+        const double L = F.log_norm ? *F.log_norm : 0.0;
+        const double logp = (mod > 0.0) ? 2.0 * log(mod) - lf - L : -INFINITY;
+        const double u = (F.precision == GBS_FP64) ? 0x1p-53 : 0x1p-24;
+        if (F.p_out) F.p_out[b] = bad ? nan : ((mod > 0.0) ? exp(logp) : 0.0);
+        if (F.logp_out) F.logp_out[b] = bad ? nan : logp;
+        if (F.err_out) F.err_out[b] = bad ? nan : (double)(n > 0 ? n : 1) * u * kappa;
+      }
     }
   }
 }
@@ -474,9 +516,9 @@ cudaError_t prepare_haf_kernel(int precision, int smem_bytes) {
 
 cudaError_t launch_finalize(const FinalizeLaunch& F, cudaStream_t st) {
   if (F.batch <= 0) return cudaSuccess;
-  const int threads = 128;
-  int blocks = (F.batch + threads - 1) / threads;
-  if (blocks > 4096) blocks = 4096;
+  const int threads = 128;  // four patterns per block, one warp each
+  int blocks = (F.batch + 3) / 4;
+  if (blocks > 8192) blocks = 8192;
   finalize_kernel<<<blocks, threads, 0, st>>>(F);
   return cudaGetLastError();
 }

@@ -116,6 +116,7 @@ struct Stage {
   int64_t id = 0;
   int n_items[2] = {0, 0};
   std::vector<int> fin;  // slots finalised in this step, in selection order
+  std::chrono::steady_clock::time_point t_launch;
   // graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -156,6 +157,7 @@ struct gbs_server {
   size_t off_pats = 0, off_idx = 0, off_items[2] = {0, 0}, off_sel = 0, up_bytes = 0;
   Stage stage[2];
   std::thread th;
+  gbs_serve_stats_t stats;
 };
 
 namespace {
@@ -167,14 +169,14 @@ int64_t binom64(int a, int b) {
   return r;
 }
 
-// Work items of one request (slot index `si`) with rounds-per-item R: the same
-// decomposition as the batched path for this launch shape.
+// Work items of one request (slot index `si`), one lane-group round each,
+// largest subsets first so the longest items start earliest.
 void request_items(const gbs_server* s, int si, int n, int prec, std::vector<WorkItem>& out) {
   out.clear();
   const int h = n / 2;
   const int cb = complex_bytes(prec);
   const int R = 1;
-  for (int sz = 1; sz <= h; ++sz) {
+  for (int sz = h; sz >= 1; --sz) {
     const int G = 32 / lanes_for(2 * sz, h, s->cfg[prec].warp_bytes, cb);
     const int64_t cnt = binom64(h, sz), cap = (int64_t)G * R;
     for (int64_t r0 = 0; r0 < cnt; r0 += cap) {
@@ -359,7 +361,7 @@ cudaError_t launch_stage(gbs_server* s, Stage& g) {
       cudaKernelNodeParams kp;
       memset(&kp, 0, sizeof(kp));
       kp.func = (void*)finalize_kernel_fn();
-      kp.gridDim = dim3((unsigned)((g.fin.size() + 127) / 128));
+      kp.gridDim = dim3((unsigned)((g.fin.size() + 3) / 4));
       kp.blockDim = dim3(128);
       kp.kernelParams = args;
       e = cudaGraphExecKernelNodeSetParams(g.exec, g.nd_fin, &kp);
@@ -532,6 +534,13 @@ void serve_loop(gbs_server* s) {
         break;
       }
       free_stage->busy = true;
+      free_stage->t_launch = std::chrono::steady_clock::now();
+      s->stats.steps++;
+      for (int p = 0; p < 2; ++p) {
+        s->stats.items += free_stage->n_items[p];
+        const WorkItem* it = (const WorkItem*)(free_stage->h_up + s->off_items[p]);
+        for (int q = 0; q < free_stage->n_items[p]; ++q) s->stats.subsets += it[q].count;
+      }
       launched = true;
     }
     Stage* old = nullptr;
@@ -544,6 +553,10 @@ void serve_loop(gbs_server* s) {
       const bool ok = wait_stage(s, *old, block);
       lk.lock();
       if (ok) {
+        const double w = std::chrono::duration<double>(std::chrono::steady_clock::now() - old->t_launch).count();
+        s->stats.step_wall_s += w;
+        if (w > s->stats.step_wall_max_s) s->stats.step_wall_max_s = w;
+        s->stats.completed += (int64_t)old->fin.size();
         complete(s, *old);
         s->cv.notify_all();
       } else if (block) {
@@ -588,6 +601,7 @@ extern "C" int gbs_serve_create(const gbs_kernel* k, const gbs_serve_opts* opts,
   gbs_server* s = new (std::nothrow) gbs_server();
   if (!s) return fail(GBS_ENOMEM, "host allocation");
   memset(&s->o, 0, sizeof(s->o));
+  memset(&s->stats, 0, sizeof(s->stats));
   if (opts) s->o = *opts;
   if (s->o.max_slots <= 0) s->o.max_slots = 256;
   if (s->o.mem_budget == 0) s->o.mem_budget = (size_t)64 << 20;
@@ -691,10 +705,9 @@ extern "C" int gbs_serve_submit(gbs_server* s, const int* idx, int n, int precis
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->failed) return fail(GBS_ECUDA, "server stopped after an error");
   if (s->stop) return fail(GBS_EINVAL, "server is stopping");
-  if ((int)s->queue.size() >= s->o.queue_capacity) return fail(GBS_EAGAIN, "queue full");
-  const int64_t t = s->next_ticket++;
-  *ticket = t;
   if (n == 0 || (n & 1)) {
+    const int64_t t = s->next_ticket++;
+    *ticket = t;
     // answered without device work: n = 0 is the vacuum (Haf = 1); odd n has
     // no perfect matching (Haf = 0)
     Result r;
@@ -706,6 +719,9 @@ extern "C" int gbs_serve_submit(gbs_server* s, const int* idx, int n, int precis
     s->done[t] = r;
     return GBS_OK;
   }
+  if ((int)s->queue.size() >= s->o.queue_capacity) return fail(GBS_EAGAIN, "queue full");
+  const int64_t t = s->next_ticket++;
+  *ticket = t;
   Request r;
   r.ticket = t;
   r.n = n;
@@ -736,6 +752,14 @@ extern "C" int gbs_serve_poll(gbs_server* s, int64_t ticket, double* p, double* 
   }
   if (err_est) *err_est = r.err;
   return 0;
+}
+
+extern "C" int gbs_serve_stats(gbs_server* s, gbs_serve_stats_t* out) {
+  clear_error();
+  if (!s || !out) return fail(GBS_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  *out = s->stats;
+  return GBS_OK;
 }
 
 extern "C" int gbs_serve_destroy(gbs_server* s) {
