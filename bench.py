@@ -49,6 +49,11 @@ def fp64_peak_tflops() -> float:
     return SMS * FP64_FLOP_PER_CLK_SM * SM_MHZ_MAX * 1e6 / 1e12
 
 
+def fp32_peak_tflops() -> float:
+    """FP32 peak from unit counts and clock: 152 SMs x 128 FFMA lanes (256 flop)/clk x 2.07 GHz."""
+    return SMS * 256.0 * SM_MHZ_MAX * 1e6 / 1e12
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled during the timed region."""
 
@@ -166,6 +171,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="headline workload only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="arithmetic of the headline line (mixed: FP32 terms, compensated sums)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -194,11 +201,13 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
+    prec = gbs.FP64 if args.precision == "fp64" else gbs.MIXED
+
     def step():
-        gbs.prob_batch(K, d_idx, n, offs, gbs.FP64, p_out=p, logp_out=lp, haf_out=hf, err_out=er)
+        gbs.prob_batch(K, d_idx, n, offs, prec, p_out=p, logp_out=lp, haf_out=hf, err_out=er)
 
     # launch shape for n = 16 from the library's autotuner (untimed)
-    tuned_rounds = gbs.autotune(16, gbs.FP64)
+    tuned_rounds = gbs.autotune(16, prec)
 
     for _ in range(args.warmup):
         step()
@@ -237,35 +246,40 @@ def main():
     # end to end through the C ABI with host buffers (copies inside the timed region)
     hp = np.zeros(b); hl = np.zeros(b); hh = np.zeros(2 * b); he = np.zeros(b)
     for _ in range(2):
-        gbs.prob_batch(K, idx, n, offs, gbs.FP64, p_out=hp, logp_out=hl, haf_out=hh, err_out=he)
+        gbs.prob_batch(K, idx, n, offs, prec, p_out=hp, logp_out=hl, haf_out=hh, err_out=he)
     t0 = time.perf_counter()
     e2e_steps = max(3, args.steps // 2)
     for _ in range(e2e_steps):
-        gbs.prob_batch(K, idx, n, offs, gbs.FP64, p_out=hp, logp_out=hl, haf_out=hh, err_out=he)
+        gbs.prob_batch(K, idx, n, offs, prec, p_out=hp, logp_out=hl, haf_out=hh, err_out=he)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     assert np.array_equal(hh, hf.cpu().numpy()), "host and device paths disagree"
 
     flops = model_flops(16) * b
-    peak = fp64_peak_tflops()
+    peak = fp64_peak_tflops() if prec == gbs.FP64 else fp32_peak_tflops()
     achieved = flops / (t_kern * 1e-3) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "M=64 Haar U seed 1, r~U[0.6,1.0], 4096 collision-free n=16 patterns, FP64",
+        "vs_baseline": None, "dtype": "f64" if prec == gbs.FP64 else "f32 terms, f32x2/f64 sums",
+        "data": "synthetic",
+        "config": {"workload": "M=64 Haar U seed 1, r~U[0.6,1.0], 4096 collision-free n=16 patterns, "
+                               + ("FP64" if prec == gbs.FP64 else "mixed precision"),
                    "patterns_per_step": b, "l2": "flushed (256 MB write) between timed steps",
                    "autotuned_rounds_per_item": tuned_rounds},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "haf_subsets_kernel<double>", "kernel_ms": t_kern,
+                     "kernel": "haf_subsets_kernel<%s>" % ("double" if prec == gbs.FP64 else "float"),
+                     "kernel_ms": t_kern,
                      "flops_per_launch": flops,
-                     "peak_note": "FP64 from unit counts and clock (152 SM x 4 flop/clk x 2.07 GHz)"},
+                     "peak_note": ("FP64 from unit counts and clock (152 SM x 4 flop/clk x 2.07 GHz)"
+                                   if prec == gbs.FP64 else
+                                   "FP32 from unit counts and clock (152 SM x 256 flop/clk x 2.07 GHz)")},
         "e2e": {"value": world * b / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(idx.nbytes),
                 "d2h_bytes_per_step": int(hp.nbytes + hl.nbytes + hh.nbytes + he.nbytes)},
         "gpu_launches": 2 * args.steps,
         "clocks": clk.summary(),
     }
-    if rank == 0 and not args.no_cpu_baseline and world == 1:
+    if rank == 0 and not args.no_cpu_baseline and world == 1 and prec == gbs.FP64:
         line["cpu_baseline"] = cpu_baseline(pats, U, r)
     if rank == 0 and not args.quick:
         line["extra"] = extras(gbs, torch)

@@ -244,6 +244,30 @@ def test_prob_large_n28_n30_sampled(gbs, orc):
     assert np.all(np.isfinite(lp))
 
 
+def test_prob_large_all_patterns_golden(gbs):
+    """All 80 large instances (M = 900, r = 1, n = 28 and 30) against stored
+    double-double oracle values (tests/golden/large_m900_oracle.json, written
+    by tests/golden/make_large_golden.py from the oracle alone)."""
+    import json
+    import os
+
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "large_m900_oracle.json")))
+    U, r, pats = W.workload("large_m900")
+    assert [list(map(int, x)) for x in pats] == [q["x"] for q in g["patterns"]]
+    K = kernel_for(gbs, U, r)
+    B = torch.zeros(2 * 900 * 900, dtype=torch.float64, device="cuda")
+    K.copy_B(B)
+    Bc = B.cpu().numpy().view(np.complex128)
+    # the box's Haar draw must match the one the values were computed from
+    assert abs(np.abs(Bc).sum() - g["B_checksum"][0]) <= 1e-9 * g["B_checksum"][0]
+    p, lp, hf, er = run_prob(gbs, K, pats, 0)
+    ref = np.array([complex(q["haf_dd"][0] + q["haf_dd"][1], q["haf_dd"][2] + q["haf_dd"][3])
+                    for q in g["patterns"]])
+    err = rel(hf, ref)
+    assert np.all(err <= FP64_TOL), (err.max(), int(np.argmax(err)))
+    assert np.all(np.abs(lp - np.array([q["logp"] for q in g["patterns"]])) <= 1e-9)
+
+
 # --- edge cases -------------------------------------------------------------------
 
 def test_edge_cases(gbs, orc):
