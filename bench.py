@@ -111,6 +111,26 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def rank_patterns(world: int, rank: int):
+    """Weak scaling: each rank owns its own 4096 patterns, the rank-th slice of a
+    world * 4096 draw from the workload's seeded stream (rank 0 of a one-GPU run
+    gets exactly the headline batch). No data moves between ranks."""
+    w = W.WORKLOADS[WORKLOAD]
+    pats = W.collision_free_patterns(w["m"], w["n"], w["count"] * world, w["seed"] + 100)
+    return list(pats[rank * w["count"]:(rank + 1) * w["count"]])
+
+
+def max_over_ranks(dist, device, *vals):
+    """Largest value of each entry over all ranks (the step time of the job)."""
+    if dist is None:
+        return list(vals)
+    import torch
+
+    t = torch.tensor(vals, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
 def cpu_baseline(pats, U, r, target_s: float = 12.0):
     """Oracle FP64 subset sum on the host cores over a bounded sample (the
     workload's patterns, repeated in order when the sample exceeds the batch)."""
@@ -189,7 +209,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
-    U, r, pats = W.workload(WORKLOAD)
+    U, r, _ = W.workload(WORKLOAD)
+    pats = rank_patterns(world, rank)
     K = gbs.build_kernel(torch.from_numpy(U.view(np.float64).copy()).cuda(), torch.from_numpy(r).cuda())
     idx, n, offs = gbs.pack_patterns(pats)
     b = len(pats)
@@ -237,10 +258,7 @@ def main():
         dist.barrier()
     t_step = float(np.sum(step_ms)) / args.steps
     t_kern = float(np.mean(kern_ms))
-    if dist:
-        tt = torch.tensor([t_step, t_kern], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step, t_kern = tt.tolist()
+    t_step, t_kern = max_over_ranks(dist, "cuda", t_step, t_kern)
     value = world * b / (t_step * 1e-3)
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
