@@ -179,8 +179,8 @@ TuneCfg default_cfg(int precision, int n) {
     c.warps_per_block = 5;
     c.warp_bytes = 44032;
   } else {
-    c.warps_per_block = 8;
-    c.warp_bytes = 27520;
+    c.warps_per_block = 5;  // full 32 x 32 FP32 tiles need ~42 KB per lane group
+    c.warp_bytes = 44032;
   }
   c.rounds = (n >= 24) ? 2 : 4;
   return c;

@@ -49,11 +49,12 @@ __host__ __device__ inline int sched_nbuf(int h) {
 }
 
 // Shared-memory bytes of one lane group's region for subsets of order N (and
-// half photon number h) with complex elements of `cbytes` bytes: nbuf packed
-// upper triangles of N(N+1)/2 entries, the power traces and exponential-series
-// coefficients (kMaxH + 1 each) and N row indices.
+// half photon number h) with complex elements of `cbytes` bytes: nbuf matrices
+// (FP64: packed upper triangles of N(N+1)/2 entries; FP32: full N x N tiles,
+// whose rows the products read as float4 pairs), the power traces and
+// exponential-series coefficients (kMaxH + 1 each) and N row indices.
 __host__ __device__ inline int group_bytes(int N, int h, int cbytes) {
-  const int P = N * (N + 1) / 2;
+  const int P = (cbytes == 16) ? N * (N + 1) / 2 : N * N;
   const int bytes = (sched_nbuf(h) * P + 2 * (kMaxH + 1)) * cbytes + N * 4;
   return (bytes + 15) & ~15;
 }

@@ -103,9 +103,27 @@ __device__ __forceinline__ void dd_add(double& ahi, double& alo, double bhi, dou
   ahi = h2;
 }
 
+// float-float addition (same steps as dd_add, in single precision)
+__device__ __forceinline__ void ff_add(float& ahi, float& alo, float bhi, float blo) {
+  float s = ahi + bhi;
+  float bb = s - ahi;
+  float e = (ahi - (s - bb)) + (bhi - bb);
+  float t = alo + blo;
+  float tb = t - alo;
+  float f = (alo - (t - tb)) + (blo - tb);
+  e += t;
+  float h = s + e;
+  e = e - (h - s);
+  e += f;
+  float h2 = h + e;
+  alo = e - (h2 - h);
+  ahi = h2;
+}
+
 struct Tables {
   int binom[kMaxH + 1][kMaxH + 1];  // C(a, b), a, b <= 16
   double inv2k[kMaxH + 1];          // 1 / (2k)
+  float inv2kf[kMaxH + 1];          // the same, rounded to float (no conversions on the FP64 pipe)
 };
 
 // Power-trace schedule per h: the fewest products R_{a+b} = R_a X R_b whose
@@ -237,6 +255,90 @@ __device__ __forceinline__ C2<T> tr2_part(const C2<T>* __restrict__ Ra, const C2
   return acc;
 }
 
+// ---- FP32 path: full N x N tiles (row stride N), rows read as float4 pairs.
+// C[i][j] = sum_k Ra[i][k] Rb[k^1][j] = sum_t Ra[i][2t] Rb[j][2t+1] + Ra[i][2t+1] Rb[j][2t]
+// (Rb symmetric), computed for i <= j and stored to both (i, j) and (j, i).
+__device__ __forceinline__ float2 pair_dot(const float4* __restrict__ ra, const float4* __restrict__ rb,
+                                           int half, float2 acc) {
+  for (int t = 0; t < half; ++t) {
+    const float4 a = ra[t], b = rb[t];
+    // (a.x + i a.y)(b.z + i b.w) + (a.z + i a.w)(b.x + i b.y)
+    acc.x = fmaf(a.x, b.z, acc.x);
+    acc.x = fmaf(-a.y, b.w, acc.x);
+    acc.y = fmaf(a.x, b.w, acc.y);
+    acc.y = fmaf(a.y, b.z, acc.y);
+    acc.x = fmaf(a.z, b.x, acc.x);
+    acc.x = fmaf(-a.w, b.y, acc.x);
+    acc.y = fmaf(a.z, b.y, acc.y);
+    acc.y = fmaf(a.w, b.x, acc.y);
+  }
+  return acc;
+}
+
+__device__ __forceinline__ void sym_prod_full(float2* __restrict__ dst, const float2* __restrict__ Ra,
+                                              const float2* __restrict__ Rb, int N, int l, int L) {
+  const int P = N * (N + 1) / 2;
+  const int half = N >> 1;
+  int i1 = 0, j1 = l;
+  tri_advance(i1, j1, 0, N);
+  for (int e = l; e < P; e += 2 * L) {
+    int i2 = i1, j2 = j1;
+    tri_advance(i2, j2, L, N);
+    const bool two = (e + L < P);
+    if (!two) {
+      i2 = i1;
+      j2 = j1;
+    }
+    const float4* a1 = reinterpret_cast<const float4*>(Ra + i1 * N);
+    const float4* b1 = reinterpret_cast<const float4*>(Rb + j1 * N);
+    const float4* a2 = reinterpret_cast<const float4*>(Ra + i2 * N);
+    const float4* b2 = reinterpret_cast<const float4*>(Rb + j2 * N);
+    float2 c1 = make_float2(0.f, 0.f), c2 = make_float2(0.f, 0.f);
+    for (int t = 0; t < half; ++t) {
+      const float4 x1 = a1[t], y1 = b1[t], x2 = a2[t], y2 = b2[t];
+      c1.x = fmaf(x1.x, y1.z, c1.x); c1.x = fmaf(-x1.y, y1.w, c1.x);
+      c1.y = fmaf(x1.x, y1.w, c1.y); c1.y = fmaf(x1.y, y1.z, c1.y);
+      c2.x = fmaf(x2.x, y2.z, c2.x); c2.x = fmaf(-x2.y, y2.w, c2.x);
+      c2.y = fmaf(x2.x, y2.w, c2.y); c2.y = fmaf(x2.y, y2.z, c2.y);
+      c1.x = fmaf(x1.z, y1.x, c1.x); c1.x = fmaf(-x1.w, y1.y, c1.x);
+      c1.y = fmaf(x1.z, y1.y, c1.y); c1.y = fmaf(x1.w, y1.x, c1.y);
+      c2.x = fmaf(x2.z, y2.x, c2.x); c2.x = fmaf(-x2.w, y2.y, c2.x);
+      c2.y = fmaf(x2.z, y2.y, c2.y); c2.y = fmaf(x2.w, y2.x, c2.y);
+    }
+    dst[i1 * N + j1] = c1;
+    dst[j1 * N + i1] = c1;
+    if (two) {
+      dst[i2 * N + j2] = c2;
+      dst[j2 * N + i2] = c2;
+    }
+    tri_advance(i1, j1, 2 * L, N);
+  }
+}
+
+// tr(X Ra) = 2 sum_t Ra[2t][2t+1] (partial over this lane's pairs).
+__device__ __forceinline__ float2 tr1_full(const float2* __restrict__ Ra, int N, int l, int L) {
+  float2 acc = make_float2(0.f, 0.f);
+  for (int t = l; 2 * t < N; t += L) {
+    const float2 v = Ra[2 * t * N + 2 * t + 1];
+    acc.x += v.x;
+    acc.y += v.y;
+  }
+  acc.x *= 2.f;
+  acc.y *= 2.f;
+  return acc;
+}
+
+// tr(X Ra X Rb) = sum_i sum_t Ra[i][2t] Rb[i^1][2t+1] + Ra[i][2t+1] Rb[i^1][2t]
+// (partial over this lane's rows).
+__device__ __forceinline__ float2 tr2_full(const float2* __restrict__ Ra, const float2* __restrict__ Rb,
+                                           int N, int l, int L) {
+  float2 acc = make_float2(0.f, 0.f);
+  for (int i = l; i < N; i += L)
+    acc = pair_dot(reinterpret_cast<const float4*>(Ra + i * N),
+                   reinterpret_cast<const float4*>(Rb + (i ^ 1) * N), N >> 1, acc);
+  return acc;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) {
   typedef C2<T> C;
@@ -246,7 +348,10 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
     for (int a = 0; a <= kMaxH; ++a)
       for (int b = 0; b <= kMaxH; ++b)
         tab.binom[a][b] = (b == 0) ? 1 : (a == 0 ? 0 : tab.binom[a - 1][b - 1] + tab.binom[a - 1][b]);
-    for (int k = 0; k <= kMaxH; ++k) tab.inv2k[k] = (k == 0) ? 0.0 : 1.0 / (2.0 * k);
+    for (int k = 0; k <= kMaxH; ++k) {
+      tab.inv2k[k] = (k == 0) ? 0.0 : 1.0 / (2.0 * k);
+      tab.inv2kf[k] = (float)tab.inv2k[k];
+    }
   }
   __syncthreads();
 
@@ -267,7 +372,7 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
     const WorkItem w = P.items[it];
     const PatDesc d = P.pats[w.pat];
     const int n = d.n, h = n >> 1, s = w.s, N = 2 * s;
-    const int NP = N * (N + 1) / 2;
+    const int NP = (sizeof(T) == 8) ? N * (N + 1) / 2 : N * N;  // entries per matrix
     const int L = lanes_for(N, h, P.warp_bytes, cb);
     const int G = 32 / L;
     const int g = lane / L, l = lane - g * L;
@@ -315,7 +420,7 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
       //    perfect matching uses V(i, i), and a zero diagonal lowers the
       //    cancellation of the signed sum (collision entries B(x_i, x_i) with
       //    i != j are off the diagonal of B_x and are kept).
-      {
+      if (sizeof(T) == 8) {
         int i = 0, j = l;
         tri_advance(i, j, 0, N);
         for (int e = l; e < NP; e += L) {
@@ -324,6 +429,13 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
           buf[e] = mk<T>((T)v.x, (T)v.y);
           tri_advance(i, j, L, N);
         }
+      } else {
+        for (int e = l; e < NP; e += L) {
+          const int i = e / N, j = e - i * N;
+          const double2 v = (i == j) ? make_double2(0.0, 0.0)
+                                     : __ldg(srcp + (int64_t)rowidx[i] * d.ld + rowidx[j]);
+          buf[e] = mk<T>((T)v.x, (T)v.y);
+        }
       }
       __syncwarp();
       // -- power traces tr((X A_S)^k), k = 1..h, by the schedule for h
@@ -331,10 +443,18 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
         const SchedOp op = c_sched[h][o];
         if (op.kind == kEnd) break;
         if (op.kind == kProd) {
-          sym_prod<T>(buf + op.k * NP, buf + op.a * NP, buf + op.b * NP, N, NP, l, L);
+          if constexpr (sizeof(T) == 8)
+            sym_prod<T>(buf + op.k * NP, buf + op.a * NP, buf + op.b * NP, N, NP, l, L);
+          else
+            sym_prod_full(buf + op.k * NP, buf + op.a * NP, buf + op.b * NP, N, l, L);
         } else {
-          const C part = (op.kind == kTr1) ? tr1_part<T>(buf + op.a * NP, N, l, L)
-                                           : tr2_part<T>(buf + op.a * NP, buf + op.b * NP, N, NP, l, L);
+          C part;
+          if constexpr (sizeof(T) == 8)
+            part = (op.kind == kTr1) ? tr1_part<T>(buf + op.a * NP, N, l, L)
+                                     : tr2_part<T>(buf + op.a * NP, buf + op.b * NP, N, NP, l, L);
+          else
+            part = (op.kind == kTr1) ? tr1_full(buf + op.a * NP, N, l, L)
+                                     : tr2_full(buf + op.a * NP, buf + op.b * NP, N, l, L);
           const C t = group_sum<T>(part, L);
           if (l == 0) pk[op.k] = t;
         }
@@ -346,7 +466,9 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
         for (int k = 1; k <= h; ++k) {
           C a = mk<T>(T(0), T(0));
           for (int j = 1; j <= k; ++j) a = cfma<T>(pk[j], ek[k - j], a);
-          const T c = (T)tab.inv2k[k];
+          T c;
+          if constexpr (sizeof(T) == 8) c = tab.inv2k[k];
+          else c = tab.inv2kf[k];
           ek[k] = mk<T>(a.x * c, a.y * c);
         }
         const C f = ek[h];
@@ -360,16 +482,29 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
       __syncwarp();
     }
 
-    // warp reduction of the group accumulators (fixed butterfly: deterministic)
-    double rh = (double)acc_re.hi, rl = (double)acc_re.lo;
-    double ih = (double)acc_im.hi, il = (double)acc_im.lo;
-    double kp = (double)kap;
-    for (int off = 16; off > 0; off >>= 1) {
-      const double orh = __shfl_xor_sync(FULL, rh, off), orl = __shfl_xor_sync(FULL, rl, off);
-      const double oih = __shfl_xor_sync(FULL, ih, off), oil = __shfl_xor_sync(FULL, il, off);
-      kp += __shfl_xor_sync(FULL, kp, off);
-      dd_add(rh, rl, orh, orl);
-      dd_add(ih, il, oih, oil);
+    // warp reduction of the group accumulators (fixed butterfly: deterministic),
+    // in the path's own compensated arithmetic: double-double for FP64,
+    // float-float for FP32 (keeping the slow FP64 pipe out of the FP32 path)
+    double rh, rl, ih, il, kp;
+    if constexpr (sizeof(T) == 8) {
+      rh = acc_re.hi; rl = acc_re.lo; ih = acc_im.hi; il = acc_im.lo; kp = kap;
+      for (int off = 16; off > 0; off >>= 1) {
+        const double orh = __shfl_xor_sync(FULL, rh, off), orl = __shfl_xor_sync(FULL, rl, off);
+        const double oih = __shfl_xor_sync(FULL, ih, off), oil = __shfl_xor_sync(FULL, il, off);
+        kp += __shfl_xor_sync(FULL, kp, off);
+        dd_add(rh, rl, orh, orl);
+        dd_add(ih, il, oih, oil);
+      }
+    } else {
+      float frh = acc_re.hi, frl = acc_re.lo, fih = acc_im.hi, fil = acc_im.lo, fkp = kap;
+      for (int off = 16; off > 0; off >>= 1) {
+        const float orh = __shfl_xor_sync(FULL, frh, off), orl = __shfl_xor_sync(FULL, frl, off);
+        const float oih = __shfl_xor_sync(FULL, fih, off), oil = __shfl_xor_sync(FULL, fil, off);
+        fkp += __shfl_xor_sync(FULL, fkp, off);
+        ff_add(frh, frl, orh, orl);
+        ff_add(fih, fil, oih, oil);
+      }
+      rh = frh; rl = frl; ih = fih; il = fil; kp = fkp;
     }
     if (lane == 0) {
       Partial pr;

@@ -177,6 +177,44 @@ def test_hafnian_host_buffers(gbs, orc):
         assert rel(g, orc.haf_subset(A)) <= FP64_TOL
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_hafnian_max_size_n32(gbs, orc, precision):
+    """n = 32 (GBS_MAX_N), two pins the oracle can afford at that size:
+    Haf(A (+) B) = Haf(A) Haf(B) for a block-diagonal matrix of two n = 16
+    blocks, and Haf([[0, C], [C^T, 0]]) = Per(C) for a 16 x 16 C (Ryser)."""
+    rng = np.random.default_rng(32)
+    A1, A2 = rand_sym(16, 321, 0.4), rand_sym(16, 322, 0.4)
+    D = np.zeros((32, 32), complex)
+    D[:16, :16], D[16:, 16:] = A1, A2
+    perm = rng.permutation(32)  # hide the block structure from the pairing
+    D = D[np.ix_(perm, perm)]
+    C = (rng.standard_normal((16, 16)) + 1j * rng.standard_normal((16, 16))) * 0.35
+    Z = np.zeros((32, 32), complex)
+    Z[:16, 16:], Z[16:, :16] = C, C.T
+    got, kap = run_haf(gbs, [D, Z], precision)
+    ref = [orc.haf_subset(A1) * orc.haf_subset(A2), orc.per_ryser(C)]
+    for g, k, r_ in zip(got, kap, ref):
+        if precision == 0:
+            assert rel(g, r_) <= FP64_TOL, rel(g, r_)
+        else:
+            assert rel(g, r_) <= 32 * 2.0 ** -24 * k
+
+
+def test_hafnian_ragged_batch_every_order(gbs, orc):
+    """A ragged batch mixing every n in 0..26 (odd included), in shuffled order."""
+    rng = np.random.default_rng(77)
+    sizes = list(range(0, 27)) * 2
+    rng.shuffle(sizes)
+    mats = [rand_sym(n, 500 + i, 0.3) for i, n in enumerate(sizes)]
+    got, _ = run_haf(gbs, mats, 0)
+    for A, g in zip(mats, got):
+        n = A.shape[0]
+        if n % 2:
+            assert g == 0
+        elif n <= 22:
+            assert rel(g, orc.haf_subset(A)) <= FP64_TOL
+
+
 # --- probabilities ---------------------------------------------------------------
 
 def test_prob_tiny_exhaustive(gbs, orc):
@@ -266,6 +304,36 @@ def test_prob_large_all_patterns_golden(gbs):
     err = rel(hf, ref)
     assert np.all(err <= FP64_TOL), (err.max(), int(np.argmax(err)))
     assert np.all(np.abs(lp - np.array([q["logp"] for q in g["patterns"]])) <= 1e-9)
+
+
+def test_prob_heavy_collisions(gbs, orc):
+    """Patterns with many photons in few modes (up to 8 in one mode), n <= 16."""
+    m = 12
+    U = W.haar_unitary(m, 61)
+    r = W.squeezing(m, "uniform", seed=61)
+    K = kernel_for(gbs, U, r)
+    pats = [np.array([3] * 8 + [5] * 8), np.array([0] * 6 + [1] * 6 + [2, 2, 7, 7]),
+            np.array([4] * 4 + [9] * 4 + [11] * 2), np.array([1] * 10 + [2] * 2 + [6] * 2),
+            np.array([0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3])]
+    p, lp, hf, er = run_prob(gbs, K, pats, 0)
+    ref = orc.prob(U, r, pats, method="pm")
+    assert np.all(rel(hf, ref["haf"]) <= FP64_TOL), rel(hf, ref["haf"])
+    assert np.all(rel(p, ref["p"]) <= FP64_TOL)
+
+
+def test_prob_mixed_bound_large_golden(gbs):
+    """The mixed path's stated per-result bound holds on the n = 28, 30 instances."""
+    import json
+    import os
+
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "large_m900_oracle.json")))
+    U, r, pats = W.workload("large_m900")
+    K = kernel_for(gbs, U, r)
+    sel = [0, 1, 2, 64, 65]
+    p, lp, hf, er = run_prob(gbs, K, [pats[i] for i in sel], 1)
+    ref = np.array([complex(g["patterns"][i]["haf_dd"][0] + g["patterns"][i]["haf_dd"][1],
+                            g["patterns"][i]["haf_dd"][2] + g["patterns"][i]["haf_dd"][3]) for i in sel])
+    assert np.all(rel(hf, ref) <= er), (rel(hf, ref), er)
 
 
 # --- edge cases -------------------------------------------------------------------
