@@ -375,7 +375,28 @@ def extras(gbs, torch):
                          "achieved_tflops": fl / (k64 * 1e-3) / 1e12, "frac_of_peak": fl / (k64 * 1e-3) / 1e12 / peak,
                          "max_err_est": float(e64.max())}
     out["serving"] = serving(gbs, torch)
+    out["sampler"] = sampler(gbs)
     return out
+
+
+def sampler(gbs):
+    """Appendix I brute-force sampler at the paper's check size (n = 4, m = 16,
+    400,000 draws) and Step 1 (P_n) at m = 36: wall time through the C ABI."""
+    m, n = 16, 4
+    K = gbs.build_kernel(W.haar_unitary(m, 16), np.full(m, 0.5))
+    u = np.random.default_rng(2019).random(400000)
+    gbs.sample_bruteforce(K, n, u[:1000])
+    t0 = time.perf_counter()
+    pats, total = gbs.sample_bruteforce(K, n, u)
+    t_bf = time.perf_counter() - t0
+    K36 = gbs.build_kernel(W.haar_unitary(36, 3), np.full(36, 0.8814))
+    gbs.photon_number_dist(K36, 200)
+    t0 = time.perf_counter()
+    gbs.photon_number_dist(K36, 200)
+    t_pn = time.perf_counter() - t0
+    return {"bruteforce_n4_m16": {"configurations": 3876, "draws": len(u), "wall_ms": 1e3 * t_bf,
+                                  "draws_per_s": len(u) / t_bf, "P_n": total},
+            "photon_number_m36_nmax200_wall_ms": 1e3 * t_pn}
 
 
 def serve_stream(gbs, K, reqs, precision):

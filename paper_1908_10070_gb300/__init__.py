@@ -20,7 +20,7 @@ from . import build as _build
 __all__ = [
     "FP64", "MIXED", "MAX_N", "GbsError", "lib", "build_kernel", "KernelMatrix",
     "hafnian_batch", "hafnian_batch_noalloc", "prob_batch", "autotune", "Server", "serve_create", "pack_patterns",
-    "pack_matrices", "last_error", "ERRORS",
+    "pack_matrices", "last_error", "ERRORS", "photon_number_dist", "sample_bruteforce",
 ]
 
 FP64 = 0
@@ -66,6 +66,8 @@ def lib():
             L.gbs_hafnian_batch.argtypes = [dp, ip, i64p, ctypes.c_int, ctypes.c_int, vp, dp, dp]
             L.gbs_hafnian_batch_noalloc.argtypes = [dp, ip, i64p, ctypes.c_int, ctypes.c_int, vp, dp, dp]
             L.gbs_prob_batch.argtypes = [vp, ip, ip, i64p, ctypes.c_int, ctypes.c_int, vp, dp, dp, dp, dp]
+            L.gbs_photon_number_dist.argtypes = [vp, ctypes.c_int, vp, dp]
+            L.gbs_sample_bruteforce.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, vp, ip, dp]
             L.gbs_autotune.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int)]
             L.gbs_set_timing_events.argtypes = [vp, vp]
             L.gbs_serve_create.argtypes = [vp, ctypes.POINTER(ServeOpts), ctypes.POINTER(ctypes.c_void_p)]
@@ -215,6 +217,24 @@ def set_timing_events(start, stop):
     sp = ctypes.c_void_p(start.cuda_event) if start is not None else None
     tp = ctypes.c_void_p(stop.cuda_event) if stop is not None else None
     _check(lib().gbs_set_timing_events(sp, tp))
+
+
+def photon_number_dist(kernel: KernelMatrix, n_max: int, stream=None) -> np.ndarray:
+    """P_n for n = 0..n_max (gbs_photon_number_dist), as a host array."""
+    out = np.zeros(n_max + 1)
+    _check(lib().gbs_photon_number_dist(kernel.handle, int(n_max), _stream(stream), _ptr(out)))
+    return out
+
+
+def sample_bruteforce(kernel: KernelMatrix, n: int, uniforms, precision=FP64, stream=None):
+    """Configurations with n photons drawn by gbs_sample_bruteforce from the given
+    uniform numbers. Returns (patterns as a draws x n int32 array, total = P_n)."""
+    u = np.ascontiguousarray(uniforms, dtype=np.float64)
+    out = np.zeros((len(u), max(n, 1)), dtype=np.int32)
+    tot = np.zeros(1)
+    _check(lib().gbs_sample_bruteforce(kernel.handle, int(n), _ptr(u) if len(u) else None, len(u),
+                                       int(precision), _stream(stream), _ptr(out), _ptr(tot)))
+    return out[:, :n], float(tot[0])
 
 
 def autotune(n, precision=FP64, stream=None) -> int:

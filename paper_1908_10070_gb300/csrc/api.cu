@@ -384,7 +384,9 @@ int run_batch(const BatchArgs& a) {
   const bool out_host = (a.out0 && !is_device_ptr(a.out0)) || (a.out1 && !is_device_ptr(a.out1)) ||
                         (a.out2 && !is_device_ptr(a.out2)) || (a.out3 && !is_device_ptr(a.out3));
   const size_t outs_b = out_host ? al(sizeof(double) * 5 * batch) : 0;
-  const size_t total_b = up_b + parts_b + ctr_b + status_b + outs_b;
+  // FP32 path on explicit matrices: one rounded copy per call, gathered by the kernel
+  const size_t a32_b = (a.mode == BatchArgs::HAFNIAN && a.precision == GBS_MIXED) ? al(8 * (size_t)src_elems) : 0;
+  const size_t total_b = up_b + parts_b + ctr_b + status_b + outs_b + a32_b;
 
   void* host_stage = nullptr;
   int slot = -1;
@@ -424,6 +426,7 @@ int run_batch(const BatchArgs& a) {
   int* d_ctr = (int*)(dm + up_b + parts_b);
   int* d_status = (int*)(dm + up_b + parts_b + ctr_b);
   double* d_outs = outs_b ? (double*)(dm + up_b + parts_b + ctr_b + status_b) : nullptr;
+  float* d_a32 = a32_b ? (float*)(dm + up_b + parts_b + ctr_b + status_b + outs_b) : nullptr;
 
   int ret = GBS_OK;
   do {
@@ -431,8 +434,13 @@ int run_batch(const BatchArgs& a) {
     if (e != cudaSuccess) { ret = cuda_fail(e, "upload"); break; }
     e = cudaMemsetAsync(d_ctr, 0, ctr_b + status_b, st);
     if (e != cudaSuccess) { ret = cuda_fail(e, "memset"); break; }
+    if (d_a32) {
+      e = launch_to_float(d_src, d_a32, 2 * src_elems, st);
+      if (e != cudaSuccess) { ret = cuda_fail(e, "float copy"); break; }
+    }
     if (n_items > 0) {
       L.src = (a.mode == BatchArgs::HAFNIAN) ? d_src : a.B;
+      L.src32 = (a.precision == GBS_MIXED) ? ((a.mode == BatchArgs::HAFNIAN) ? d_a32 : a.B32) : nullptr;
       L.idx = (a.mode == BatchArgs::PROB) ? d_idx : nullptr;
       L.pats = d_pats;
       L.items = d_items;
@@ -528,12 +536,17 @@ extern "C" int gbs_build_kernel(const double* U_ri, const double* r, int m, void
   if (e != cudaSuccess) { delete k; cudaGetLastError(); return fail(GBS_ENOMEM, "B: %s", cudaGetErrorString(e)); }
   e = cudaMalloc(&k->dscal, 256);
   if (e != cudaSuccess) { cudaFree(k->B); delete k; cudaGetLastError(); return fail(GBS_ENOMEM, "scalars"); }
+  e = cudaMalloc(&k->B32, 8 * mm);
+  if (e == cudaSuccess) e = cudaMalloc(&k->t, 8 * (size_t)m);
+  if (e != cudaSuccess) {
+    cudaFree(k->B); cudaFree(k->B32); cudaFree(k->dscal); delete k; cudaGetLastError();
+    return fail(GBS_ENOMEM, "B32: %s", cudaGetErrorString(e));
+  }
   // stage U and r on the device when they are host memory
   const bool u_dev = is_device_ptr(U_ri), r_dev = is_device_ptr(r);
   void* tmp = nullptr;
   const size_t u_b = u_dev ? 0 : 16 * mm, r_b = r_dev ? 0 : 8 * (size_t)m;
-  const size_t t_b = 8 * (size_t)m;
-  e = scratch_alloc(&tmp, u_b + r_b + t_b, st);
+  e = scratch_alloc(&tmp, u_b + r_b + 256, st);
   if (e != cudaSuccess) {
     cudaFree(k->B); cudaFree(k->dscal); delete k; cudaGetLastError();
     return fail(GBS_ENOMEM, "staging: %s", cudaGetErrorString(e));
@@ -553,8 +566,12 @@ extern "C" int gbs_build_kernel(const double* U_ri, const double* r, int m, void
     dr = (const double*)(tb + u_b);
   }
   if (ret == GBS_OK) {
-    e = launch_build_B(dU, dr, m, k->B, k->dscal, (double*)(tb + u_b + r_b), st);
+    e = launch_build_B(dU, dr, m, k->B, k->dscal, k->t, st);
     if (e != cudaSuccess) ret = cuda_fail(e, "build_B launch");
+  }
+  if (ret == GBS_OK) {
+    e = launch_to_float(k->B, k->B32, 2 * (int64_t)mm, st);
+    if (e != cudaSuccess) ret = cuda_fail(e, "B32 launch");
   }
   scratch_free(tmp, st);
   if (ret == GBS_OK && (!u_dev || !r_dev)) {
@@ -563,6 +580,8 @@ extern "C" int gbs_build_kernel(const double* U_ri, const double* r, int m, void
   if (ret != GBS_OK) {
     cudaStreamSynchronize(st);
     cudaFree(k->B);
+    cudaFree(k->B32);
+    cudaFree(k->t);
     cudaFree(k->dscal);
     delete k;
     return ret;
@@ -576,6 +595,8 @@ extern "C" int gbs_free_kernel(gbs_kernel* k) {
   if (!k) return GBS_OK;
   cudaError_t e1 = cudaFree(k->B);
   cudaError_t e2 = cudaFree(k->dscal);
+  cudaFree(k->B32);
+  cudaFree(k->t);
   delete k;
   if (e1 != cudaSuccess) return cuda_fail(e1, "cudaFree(B)");
   if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFree(scalars)");
@@ -642,6 +663,7 @@ extern "C" int gbs_prob_batch(const gbs_kernel* k, const int* idx, const int* n,
   BatchArgs a;
   a.mode = BatchArgs::PROB;
   a.B = k->B;
+  a.B32 = k->B32;
   a.m = k->m;
   a.log_norm_dev = k->dscal;
   a.idx = idx;

@@ -80,7 +80,20 @@ __global__ void build_B_kernel(const double2* __restrict__ U, const double* __re
   }
 }
 
+__global__ void to_float_kernel(const double* __restrict__ src, float* __restrict__ dst, int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
 }  // namespace
+
+cudaError_t launch_to_float(const double* src, float* dst, int64_t count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  to_float_kernel<<<(int)blocks, 256, 0, st>>>(src, dst, count);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_build_B(const double* U, const double* r, int m, double* B, double* log_norm,
                            double* t_scratch, cudaStream_t st) {

@@ -19,6 +19,8 @@ struct gbs_kernel {
   int device = 0;
   int m = 0;
   double* B = nullptr;      // m*m complex128, device
+  float* B32 = nullptr;     // the same rounded to complex64 (gathered by the FP32 path)
+  double* t = nullptr;      // tanh r_i, m doubles, device
   double* dscal = nullptr;  // [0] = sum_i log cosh r_i, device
 };
 
@@ -35,6 +37,7 @@ struct BatchArgs {
   enum Mode { HAFNIAN, PROB } mode = PROB;
   const double* src = nullptr;  // Hafnian mode: concatenated matrices
   const double* B = nullptr;    // probability mode: kernel matrix (device)
+  const float* B32 = nullptr;   // probability mode: kernel matrix as complex64
   int m = 0;
   const double* log_norm_dev = nullptr;
   const int* idx = nullptr;

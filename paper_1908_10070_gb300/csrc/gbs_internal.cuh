@@ -70,6 +70,7 @@ __host__ __device__ inline int lanes_for(int N, int h, int warp_bytes, int cbyte
 
 struct HafLaunch {
   const double* src;       // interleaved complex source matrices
+  const float* src32;      // the same rounded to float (FP32 path; may be null)
   const int* idx;          // index lists (may be null when every idx_off < 0)
   const PatDesc* pats;
   const WorkItem* items;   // in schedule order
@@ -110,5 +111,7 @@ cudaError_t prepare_haf_kernel(int precision, int smem_bytes);
 // Defined in build_b.cu
 cudaError_t launch_build_B(const double* U, const double* r, int m, double* B, double* log_norm,
                            double* t_scratch, cudaStream_t st);
+// dst[i] = (float)src[i], i < count
+cudaError_t launch_to_float(const double* src, float* dst, int64_t count, cudaStream_t st);
 
 }  // namespace gbs

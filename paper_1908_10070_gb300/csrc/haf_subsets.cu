@@ -392,6 +392,7 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
     C* ek = pk + (kMaxH + 1);          // exponential-series coefficients
     int* rowidx = reinterpret_cast<int*>(ek + (kMaxH + 1));
     const double2* srcp = src2 + d.src_off;
+    const float2* src32p = P.src32 ? reinterpret_cast<const float2*>(P.src32) + d.src_off : nullptr;
 
     Comp<T> acc_re = {T(0), T(0)}, acc_im = {T(0), T(0)};
     T kap = T(0);
@@ -428,6 +429,13 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
                                      : __ldg(srcp + (int64_t)rowidx[i] * d.ld + rowidx[j]);
           buf[e] = mk<T>((T)v.x, (T)v.y);
           tri_advance(i, j, L, N);
+        }
+      } else if (src32p) {
+        for (int e = l; e < NP; e += L) {
+          const int i = e / N, j = e - i * N;
+          const float2 v = (i == j) ? make_float2(0.f, 0.f)
+                                    : __ldg(src32p + (int64_t)rowidx[i] * d.ld + rowidx[j]);
+          buf[e] = mk<T>((T)v.x, (T)v.y);
         }
       } else {
         for (int e = l; e < NP; e += L) {

@@ -196,6 +196,7 @@ HafLaunch make_launch(gbs_server* s, Stage& g, int prec) {
   HafLaunch L;
   memset(&L, 0, sizeof(L));
   L.src = s->k->B;
+  L.src32 = (prec == GBS_MIXED) ? s->k->B32 : nullptr;
   L.idx = s->d_idx;
   L.pats = s->d_pats;
   L.items = g.d_items[prec];
