@@ -170,19 +170,30 @@ void pinned_release(int slot, cudaStream_t st) {
 // launch shapes
 // ------------------------------------------------------------------------
 static std::mutex g_tune_mu;
+bool shape_fits(int precision, int warp_bytes, int maxn);
 static std::map<std::pair<int, int>, TuneCfg> g_tuned;  // (precision, n) -> cfg
 
+// Default launch shape for photon number n: the most warps per block (6 down
+// to 2, one block per SM) whose per-warp shared memory still holds every lane
+// group that n can need.
 TuneCfg default_cfg(int precision, int n) {
-  // 5 warps x 44 KB (FP64) fits every n <= 32 in one block per SM
-  TuneCfg c;
-  if (precision == GBS_FP64) {
-    c.warps_per_block = 5;
-    c.warp_bytes = 44032;
-  } else {
-    c.warps_per_block = 5;  // full 32 x 32 FP32 tiles need ~42 KB per lane group
-    c.warp_bytes = 44032;
+  static int optin = 0;
+  if (optin == 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0) {
+      cudaGetLastError();
+      v = 232448;  // 227 KB, the GB300 opt-in limit
+    }
+    optin = v;
   }
+  TuneCfg c;
   c.rounds = (n >= 24) ? 2 : 4;
+  for (int wpb = 6; wpb >= 2; --wpb) {
+    c.warps_per_block = wpb;
+    c.warp_bytes = ((optin - 4096) / wpb) & ~127;
+    if (shape_fits(precision, c.warp_bytes, n < 2 ? 2 : n)) break;
+  }
   return c;
 }
 
@@ -205,7 +216,7 @@ int complex_bytes(int precision) { return precision == GBS_FP64 ? 16 : 8; }
 bool shape_fits(int precision, int warp_bytes, int maxn) {
   const int cb = complex_bytes(precision);
   for (int n = 2; n <= maxn; n += 2)
-    if (lanes_for(n, n / 2, warp_bytes, cb) == 0) return false;
+    if (lanes_for(n, n / 2, warp_bytes, maxn / 2, cb) == 0) return false;
   return true;
 }
 
@@ -225,6 +236,9 @@ void Planner::init(const int* n, int batch, int precision, int warp_bytes, const
   n_ = n;
   batch_ = batch;
   const int cb = complex_bytes(precision);
+  int maxn = 0;
+  for (int b = 0; b < batch; ++b) maxn = std::max(maxn, n[b]);
+  const int stage_h = maxn / 2;
   for (int v = 0; v <= kMaxN; ++v) {
     tmpl_[v].clear();
     npat_[v] = 0;
@@ -236,7 +250,7 @@ void Planner::init(const int* n, int batch, int precision, int warp_bytes, const
     if (!npat_[v]) continue;
     const int h = v / 2, R = rounds_for_n[v];
     for (int sz = 1; sz <= h; ++sz) {
-      const int G = 32 / lanes_for(2 * sz, h, warp_bytes, cb);
+      const int G = 32 / lanes_for(2 * sz, h, warp_bytes, stage_h, cb);
       const int64_t cnt = binom64(h, sz), cap = (int64_t)G * R;
       for (int64_t r0 = 0; r0 < cnt; r0 += cap) {
         ItemTemplate t;
@@ -450,6 +464,7 @@ int run_batch(const BatchArgs& a) {
       L.status = d_status;
       L.parts = d_parts;
       L.warp_bytes = cfg.warp_bytes;
+      L.stage_h = maxn / 2;
       const int smem = cfg.warps_per_block * cfg.warp_bytes;
       int per_sm = max_blocks_per_sm(a.precision, cfg.warps_per_block, smem);
       if (per_sm < 1) { ret = fail(GBS_EINVAL, "launch shape does not fit an SM"); break; }

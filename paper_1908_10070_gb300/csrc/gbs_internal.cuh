@@ -51,20 +51,28 @@ __host__ __device__ inline int sched_nbuf(int h) {
 // Shared-memory bytes of one lane group's region for subsets of order N (and
 // half photon number h) with complex elements of `cbytes` bytes: nbuf matrices
 // (FP64: packed upper triangles of N(N+1)/2 entries; FP32: full N x N tiles,
-// whose rows the products read as float4 pairs), the power traces and
-// exponential-series coefficients (kMaxH + 1 each) and N row indices.
+// whose rows the products read as float4 pairs) and N row indices.
 __host__ __device__ inline int group_bytes(int N, int h, int cbytes) {
   const int P = (cbytes == 16) ? N * (N + 1) / 2 : N * N;
-  const int bytes = (sched_nbuf(h) * P + 2 * (kMaxH + 1)) * cbytes + N * 4;
+  const int bytes = sched_nbuf(h) * P * cbytes + N * 4;
   return (bytes + 15) & ~15;
 }
 
+// Per-warp staging of finished subsets' power traces (32 slots of stage_h
+// complex values plus 32 sign flags); the exponential series then runs with
+// one subset per lane.
+__host__ __device__ inline int stage_bytes(int stage_h, int cbytes) {
+  return (32 * stage_h * cbytes + 32 * 4 + 15) & ~15;
+}
+
 // Lane-group size L (a power of two) for subsets of order N of a matrix of
-// order 2h: the smallest L whose 32/L groups fit `warp_bytes`; 0 if none does.
-__host__ __device__ inline int lanes_for(int N, int h, int warp_bytes, int cbytes) {
+// order 2h: the smallest L whose 32/L groups fit the warp's bytes left after
+// the header and the staging area; 0 if none does.
+__host__ __device__ inline int lanes_for(int N, int h, int warp_bytes, int stage_h, int cbytes) {
+  const int avail = warp_bytes - kWarpHeaderBytes - stage_bytes(stage_h, cbytes);
   const int gb = group_bytes(N, h, cbytes);
   for (int L = 1; L <= 32; L <<= 1)
-    if (kWarpHeaderBytes + (32 / L) * gb <= warp_bytes) return L;
+    if ((32 / L) * gb <= avail) return L;
   return 0;
 }
 
@@ -80,6 +88,7 @@ struct HafLaunch {
   int* status;             // per-pattern flag, set to 1 on an out-of-range index
   Partial* parts;
   int warp_bytes;          // dynamic shared memory per warp
+  int stage_h;             // power traces staged per subset (>= the batch's largest n/2)
 };
 
 struct FinalizeLaunch {

@@ -361,7 +361,10 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
   const int cb = (int)sizeof(C);
   unsigned char* wbase = smem + (size_t)warp * P.warp_bytes;
   int* xs = reinterpret_cast<int*>(wbase);
-  unsigned char* gbase = wbase + kWarpHeaderBytes;
+  // staging: the power traces of up to 32 finished subsets and their signs
+  C* stP = reinterpret_cast<C*>(wbase + kWarpHeaderBytes);
+  int* stF = reinterpret_cast<int*>(stP + 32 * P.stage_h);
+  unsigned char* gbase = wbase + kWarpHeaderBytes + stage_bytes(P.stage_h, cb);
   const double2* src2 = reinterpret_cast<const double2*>(P.src);
 
   for (;;) {
@@ -373,7 +376,7 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
     const PatDesc d = P.pats[w.pat];
     const int n = d.n, h = n >> 1, s = w.s, N = 2 * s;
     const int NP = (sizeof(T) == 8) ? N * (N + 1) / 2 : N * N;  // entries per matrix
-    const int L = lanes_for(N, h, P.warp_bytes, cb);
+    const int L = lanes_for(N, h, P.warp_bytes, P.stage_h, cb);
     const int G = 32 / L;
     const int g = lane / L, l = lane - g * L;
 
@@ -388,9 +391,8 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
     __syncwarp();
 
     C* buf = reinterpret_cast<C*>(gbase + (size_t)g * group_bytes(N, h, cb));
-    C* pk = buf + sched_nbuf(h) * NP;  // power traces tr((X A_S)^k), k = 1..h
-    C* ek = pk + (kMaxH + 1);          // exponential-series coefficients
-    int* rowidx = reinterpret_cast<int*>(ek + (kMaxH + 1));
+    int* rowidx = reinterpret_cast<int*>(buf + sched_nbuf(h) * NP);
+    int staged = 0;  // subsets whose traces wait in the staging area
     const double2* srcp = src2 + d.src_off;
     const float2* src32p = P.src32 ? reinterpret_cast<const float2*>(P.src32) + d.src_off : nullptr;
 
@@ -464,30 +466,49 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
             part = (op.kind == kTr1) ? tr1_full(buf + op.a * NP, N, l, L)
                                      : tr2_full(buf + op.a * NP, buf + op.b * NP, N, l, L);
           const C t = group_sum<T>(part, L);
-          if (l == 0) pk[op.k] = t;
+          if (l == 0) stP[(staged + g) * P.stage_h + (op.k - 1)] = t;
         }
         __syncwarp();
       }
-      // -- exponential series and signed accumulation (one lane per group)
-      if (l == 0) {
-        ek[0] = mk<T>(T(1), T(0));
-        for (int k = 1; k <= h; ++k) {
-          C a = mk<T>(T(0), T(0));
-          for (int j = 1; j <= k; ++j) a = cfma<T>(pk[j], ek[k - j], a);
-          T c;
-          if constexpr (sizeof(T) == 8) c = tab.inv2k[k];
-          else c = tab.inv2kf[k];
-          ek[k] = mk<T>(a.x * c, a.y * c);
-        }
-        const C f = ek[h];
-        if (active) {
-          const T sg = ((h - s) & 1) ? T(-1) : T(1);
-          comp_add<T>(acc_re, sg * f.x);
-          comp_add<T>(acc_im, sg * f.y);
-          kap += fabs(f.x) + fabs(f.y);
-        }
-      }
+      if (l == 0) stF[staged + g] = active ? (((h - s) & 1) ? -1 : 1) : 0;
+      staged += G;
       __syncwarp();
+      // -- once 32 subsets are staged (or the item ends): the exponential
+      //    series e_k = (1/(2k)) sum_j tr_j e_{k-j}, f = e_h, one subset per
+      //    lane, and the signed compensated accumulation
+      if (staged == 32 || rd == rounds - 1) {
+        if (lane < staged) {
+          const C* pq = stP + lane * P.stage_h;
+          C e[kMaxH + 1];
+          e[0] = mk<T>(T(1), T(0));
+#pragma unroll
+          for (int k = 1; k <= kMaxH; ++k) {
+            C a = mk<T>(T(0), T(0));
+            if (k <= h) {
+#pragma unroll
+              for (int j = 1; j <= k; ++j) a = cfma<T>(pq[j - 1], e[k - j], a);
+              T c;
+              if constexpr (sizeof(T) == 8) c = tab.inv2k[k];
+              else c = tab.inv2kf[k];
+              a.x *= c;
+              a.y *= c;
+            }
+            e[k] = a;
+          }
+          C f = e[1];
+#pragma unroll
+          for (int k = 2; k <= kMaxH; ++k)
+            if (k == h) f = e[k];
+          const int sg = stF[lane];
+          if (sg != 0) {
+            comp_add<T>(acc_re, sg > 0 ? f.x : -f.x);
+            comp_add<T>(acc_im, sg > 0 ? f.y : -f.y);
+            kap += fabs(f.x) + fabs(f.y);
+          }
+        }
+        staged = 0;
+        __syncwarp();
+      }
     }
 
     // warp reduction of the group accumulators (fixed butterfly: deterministic),

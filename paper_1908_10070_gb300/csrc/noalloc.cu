@@ -113,7 +113,7 @@ extern "C" int gbs_hafnian_batch_noalloc(const double* A_ri, const int* n, const
       const int h = n[b] / 2;
       const int R = get_cfg(precision, n[b]).rounds;
       for (int s = 1; s <= h; ++s) {
-        const int G = 32 / lanes_for(2 * s, h, cfg.warp_bytes, cb);
+        const int G = 32 / lanes_for(2 * s, h, cfg.warp_bytes, maxn / 2, cb);
         const int64_t cnt = binom(h, s);
         const int64_t cap = (int64_t)G * R;
         for (int64_t r0 = 0; r0 < cnt; r0 += cap) {
@@ -164,6 +164,7 @@ extern "C" int gbs_hafnian_batch_noalloc(const double* A_ri, const int* n, const
     L.status = d_status;
     L.parts = d_parts;
     L.warp_bytes = cfg.warp_bytes;
+    L.stage_h = maxn / 2;
     const int smem = cfg.warps_per_block * cfg.warp_bytes;
     const int per_sm = max_blocks_per_sm(precision, cfg.warps_per_block, smem);
     if (per_sm < 1) return fail(GBS_EINVAL, "launch shape does not fit an SM");

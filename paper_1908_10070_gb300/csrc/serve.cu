@@ -177,7 +177,7 @@ void request_items(const gbs_server* s, int si, int n, int prec, std::vector<Wor
   const int cb = complex_bytes(prec);
   const int R = 1;
   for (int sz = h; sz >= 1; --sz) {
-    const int G = 32 / lanes_for(2 * sz, h, s->cfg[prec].warp_bytes, cb);
+    const int G = 32 / lanes_for(2 * sz, h, s->cfg[prec].warp_bytes, kMaxH, cb);
     const int64_t cnt = binom64(h, sz), cap = (int64_t)G * R;
     for (int64_t r0 = 0; r0 < cnt; r0 += cap) {
       WorkItem w;
@@ -206,6 +206,7 @@ HafLaunch make_launch(gbs_server* s, Stage& g, int prec) {
   L.status = nullptr;
   L.parts = s->d_parts;
   L.warp_bytes = s->cfg[prec].warp_bytes;
+  L.stage_h = kMaxH;
   return L;
 }
 
