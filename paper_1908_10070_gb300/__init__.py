@@ -20,7 +20,7 @@ from . import build as _build
 __all__ = [
     "FP64", "MIXED", "MAX_N", "GbsError", "lib", "build_kernel", "KernelMatrix",
     "hafnian_batch", "hafnian_batch_noalloc", "prob_batch", "autotune", "Server", "serve_create", "pack_patterns",
-    "pack_matrices", "last_error", "ERRORS", "photon_number_dist", "sample_bruteforce",
+    "pack_matrices", "last_error", "ERRORS", "photon_number_dist", "sample_bruteforce", "marginal_batch", "sample_chain",
 ]
 
 FP64 = 0
@@ -68,6 +68,8 @@ def lib():
             L.gbs_prob_batch.argtypes = [vp, ip, ip, i64p, ctypes.c_int, ctypes.c_int, vp, dp, dp, dp, dp]
             L.gbs_photon_number_dist.argtypes = [vp, ctypes.c_int, vp, dp]
             L.gbs_sample_bruteforce.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, vp, ip, dp]
+            L.gbs_marginal_batch.argtypes = [vp, ip, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, dp]
+            L.gbs_sample_chain.argtypes = [vp, ctypes.c_int, dp, vp, ip]
             L.gbs_autotune.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int)]
             L.gbs_set_timing_events.argtypes = [vp, vp]
             L.gbs_serve_create.argtypes = [vp, ctypes.POINTER(ServeOpts), ctypes.POINTER(ctypes.c_void_p)]
@@ -235,6 +237,23 @@ def sample_bruteforce(kernel: KernelMatrix, n: int, uniforms, precision=FP64, st
     _check(lib().gbs_sample_bruteforce(kernel.handle, int(n), _ptr(u) if len(u) else None, len(u),
                                        int(precision), _stream(stream), _ptr(out), _ptr(tot)))
     return out[:, :n], float(tot[0])
+
+
+def marginal_batch(kernel: KernelMatrix, prefixes, n: int, stream=None) -> np.ndarray:
+    """q_n(x_1..x_k) for each row of `prefixes` (batch x k mode indices)."""
+    x = np.ascontiguousarray(np.asarray(prefixes, dtype=np.int32).reshape(len(prefixes), -1))
+    out = np.zeros(x.shape[0])
+    _check(lib().gbs_marginal_batch(kernel.handle, _ptr(x) if x.size else None, int(x.shape[1]),
+                                    int(x.shape[0]), int(n), _stream(stream), _ptr(out)))
+    return out
+
+
+def sample_chain(kernel: KernelMatrix, n: int, uniforms, stream=None) -> np.ndarray:
+    """One position-basis sample x_1..x_n by Algorithm 1 (gbs_sample_chain)."""
+    u = np.ascontiguousarray(uniforms, dtype=np.float64)
+    x = np.zeros(max(n, 1), dtype=np.int32)
+    _check(lib().gbs_sample_chain(kernel.handle, int(n), _ptr(u), _stream(stream), _ptr(x)))
+    return x[:n]
 
 
 def autotune(n, precision=FP64, stream=None) -> int:

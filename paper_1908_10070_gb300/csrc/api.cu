@@ -570,6 +570,18 @@ extern "C" int gbs_build_kernel(const double* U_ri, const double* r, int m, void
   const double* dU = U_ri;
   const double* dr = r;
   int ret = GBS_OK;
+  {
+    // identical squeezing (needed by the marginals of the chain-rule sampler)
+    std::vector<double> hr(m);
+    if (cudaMemcpy(hr.data(), r, 8 * (size_t)m, cudaMemcpyDefault) == cudaSuccess) {
+      k->r_uniform = 1;
+      for (int i = 1; i < m; ++i)
+        if (hr[i] != hr[0]) k->r_uniform = 0;
+      k->t_uniform = tanh(hr[0]);
+    } else {
+      cudaGetLastError();
+    }
+  }
   if (!u_dev) {
     e = cudaMemcpyAsync(tb, U_ri, u_b, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) ret = cuda_fail(e, "U upload");

@@ -21,6 +21,8 @@ struct gbs_kernel {
   double* B = nullptr;      // m*m complex128, device
   float* B32 = nullptr;     // the same rounded to complex64 (gathered by the FP32 path)
   double* t = nullptr;      // tanh r_i, m doubles, device
+  int r_uniform = 0;        // 1 if every r_i is the same
+  double t_uniform = 0.0;   // tanh r when r_uniform
   double* dscal = nullptr;  // [0] = sum_i log cosh r_i, device
 };
 

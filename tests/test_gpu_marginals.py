@@ -1,0 +1,107 @@
+"""Theorem 1 marginals and the chain-rule sampler (Sec. 3.3-3.4, Algorithm 1)
+on the GPU, against the plain definition q_n(x_1..x_k) = sum over completions
+of |Haf(W_x)|^2 / f_n computed by the oracle."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gbs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1908_10070_gb300 as g
+
+    g.lib()
+    return g
+
+
+def f_n(m, n):
+    a = (m + n) / 2 - 1
+    return math.factorial(n) * math.exp(math.lgamma(a + 1) - math.lgamma(n / 2 + 1) - math.lgamma(a - n / 2 + 1))
+
+
+def brute_marginals(orc, U, prefixes, n):
+    """sum over x_{k+1..n} of |Haf(W_x)|^2 / f_n, W = U U^T (oracle, double-double)."""
+    m = U.shape[0]
+    Wdd = orc.build_B_dd(U, np.ones(m))
+    out = []
+    for x in prefixes:
+        comps = [np.array(list(x) + list(c), dtype=np.int32) for c in itertools.product(range(m), repeat=n - len(x))]
+        h = orc.prob(U, np.zeros(m), comps, method="pm", Bdd=Wdd)["haf"]
+        out.append(np.sum(np.abs(h) ** 2) / f_n(m, n))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("m,n,r", [(4, 4, 0.7), (6, 4, 0.5), (4, 6, 0.9), (5, 4, 0.6)])
+def test_marginals_vs_definition(gbs, orc, m, n, r):
+    U = W.haar_unitary(m, 50 + m + n)
+    K = gbs.build_kernel(U, np.full(m, r))
+    rng = np.random.default_rng(m * 7 + n)
+    for k in range(0, n + 1):
+        prefixes = [rng.integers(0, m, size=k) for _ in range(3)]
+        if k >= 2:
+            prefixes.append(np.full(k, 1))  # all photons in one mode
+        got = gbs.marginal_batch(K, np.array(prefixes).reshape(len(prefixes), k), n)
+        ref = brute_marginals(orc, U, prefixes, n)
+        assert np.all(np.abs(got - ref) <= 1e-10 * np.abs(ref) + 1e-300), (k, got, ref)
+
+
+def test_marginal_limits_and_consistency(gbs, orc):
+    """k = 0 gives 1; k = n gives q_n(x) = |Haf(W_x)|^2 / f_n (Eq. EqDisE); summing
+    over the last position recovers the shorter prefix (Eq. marginal_definition)."""
+    m, n = 12, 6
+    U = W.haar_unitary(m, 12)
+    K = gbs.build_kernel(U, np.full(m, 0.8814))
+    assert abs(gbs.marginal_batch(K, np.zeros((1, 0), np.int32), n)[0] - 1.0) <= 1e-12
+    x = np.array([[3, 7, 7, 0, 11, 2]], np.int32)
+    Wm = U @ U.T
+    ref = abs(orc.haf_pm(Wm[np.ix_(x[0], x[0])])) ** 2 / f_n(m, n)
+    assert abs(gbs.marginal_batch(K, x, n)[0] - ref) <= 1e-10 * ref
+    for pre in ([5], [5, 9], [5, 9, 9], [4, 1, 8, 10]):
+        whole = gbs.marginal_batch(K, np.array([pre], np.int32), n)[0]
+        ext = gbs.marginal_batch(K, np.array([pre + [l] for l in range(m)], np.int32), n)
+        assert abs(ext.sum() - whole) <= 1e-11 * whole, (pre, ext.sum(), whole)
+
+
+def test_marginals_reject_unequal_squeezing(gbs):
+    K = gbs.build_kernel(W.haar_unitary(6, 1), np.linspace(0.3, 0.8, 6))
+    with pytest.raises(gbs.GbsError) as ei:
+        gbs.marginal_batch(K, np.array([[1, 2]], np.int32), 4)
+    assert ei.value.code == -1
+
+
+def test_chain_sampler_distribution(gbs, orc):
+    """Algorithm 1 samples follow p_n(s) = N_p q_n(x) (Sec. 3.2): the configuration
+    frequencies of 1500 chain samples against the oracle's p_n(s)."""
+    m, n = 5, 4
+    U = W.haar_unitary(m, 77)
+    K = gbs.build_kernel(U, np.full(m, 0.6))
+    rng = np.random.default_rng(4)
+    draws = 1500
+    counts = {}
+    for _ in range(draws):
+        x = gbs.sample_chain(K, n, rng.random(n))
+        key = tuple(sorted(int(v) for v in x))
+        counts[key] = counts.get(key, 0) + 1
+    configs = W.all_patterns(m, n)
+    Wdd = orc.build_B_dd(U, np.ones(m))
+    h = orc.prob(U, np.zeros(m), configs, method="pm", Bdd=Wdd)["haf"]
+    pn = []
+    for c, hv in zip(configs, h):
+        s = W.pattern_to_counts(c, m)
+        Np = math.factorial(n) / np.prod([math.factorial(int(v)) for v in s])
+        pn.append(Np * abs(hv) ** 2 / f_n(m, n))
+    pn = np.array(pn)
+    assert abs(pn.sum() - 1.0) < 1e-10  # the p_n(s) form a distribution
+    freq = np.array([counts.get(tuple(int(v) for v in c), 0) for c in configs]) / draws
+    tv = 0.5 * np.abs(freq - pn).sum()
+    expected = 0.5 * np.sqrt(2 / (np.pi * draws)) * np.sum(np.sqrt(pn * (1 - pn)))
+    assert tv <= 1.5 * expected, (tv, expected)
