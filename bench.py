@@ -402,7 +402,7 @@ def sampler(gbs):
 def serve_stream(gbs, K, reqs, precision):
     """Poisson client: submit at the scheduled arrival times, poll until done.
     Latency = completion seen by the client - scheduled arrival."""
-    srv = gbs.Server(K)
+    srv = gbs.Server(K, max_n=26)
     try:
         warm = [srv.submit(x, precision) for _, x in reqs[:64]]
         for t in warm:

@@ -173,6 +173,8 @@ typedef struct gbs_serve_opts {
   int use_graphs;         /* 0 or 1: replay an instantiated CUDA graph per step (default);
                              -1: launch each step's copies and kernels directly */
   double wait_timeout_s;  /* bound on any internal wait (0 = 10 s) */
+  int max_n;              /* largest photon number accepted (0 = GBS_MAX_N); a smaller
+                             bound lets steps run more warps per SM */
 } gbs_serve_opts;
 
 /* Start a server for kernel matrix k: a host thread admits requests into
@@ -183,7 +185,8 @@ int gbs_serve_create(const gbs_kernel* k, const gbs_serve_opts* opts, gbs_server
 
 /* Enqueue one pattern (host index list of n entries, copied before return).
  * Non-blocking. ticket receives an id for gbs_serve_poll.
- * Errors: GBS_EAGAIN (queue full), GBS_ERANGE, GBS_EINVAL. */
+ * Errors: GBS_EAGAIN (queue full), GBS_ERANGE (n above the server's max_n, or
+ * an index outside [0, m)), GBS_EINVAL. */
 int gbs_serve_submit(gbs_server* s, const int* idx, int n, int precision, int64_t* ticket);
 
 /* Returns 0 and fills p, haf_ri (2 doubles), err_est (each may be NULL) when

@@ -48,7 +48,8 @@ class ServeStats(ctypes.Structure):
 class ServeOpts(ctypes.Structure):
     _fields_ = [("max_slots", ctypes.c_int), ("mem_budget", ctypes.c_size_t),
                 ("queue_capacity", ctypes.c_int), ("subsets_per_step", ctypes.c_int),
-                ("use_graphs", ctypes.c_int), ("wait_timeout_s", ctypes.c_double)]
+                ("use_graphs", ctypes.c_int), ("wait_timeout_s", ctypes.c_double),
+                ("max_n", ctypes.c_int)]
 
 
 def lib():
@@ -266,9 +267,10 @@ class Server:
     """Continuous-batching server (gbs_serve_*)."""
 
     def __init__(self, kernel: KernelMatrix, max_slots=0, mem_budget=0, queue_capacity=0,
-                 subsets_per_step=0, use_graphs=1, wait_timeout_s=0.0):
+                 subsets_per_step=0, use_graphs=1, wait_timeout_s=0.0, max_n=0):
         self.kernel = kernel
-        o = ServeOpts(max_slots, mem_budget, queue_capacity, subsets_per_step, use_graphs, wait_timeout_s)
+        o = ServeOpts(max_slots, mem_budget, queue_capacity, subsets_per_step, use_graphs, wait_timeout_s,
+                      max_n)
         h = ctypes.c_void_p()
         _check(lib().gbs_serve_create(kernel.handle, ctypes.byref(o), ctypes.byref(h)))
         self.handle = h

@@ -177,7 +177,7 @@ void request_items(const gbs_server* s, int si, int n, int prec, std::vector<Wor
   const int cb = complex_bytes(prec);
   const int R = 1;
   for (int sz = h; sz >= 1; --sz) {
-    const int G = 32 / lanes_for(2 * sz, h, s->cfg[prec].warp_bytes, kMaxH, cb);
+    const int G = 32 / lanes_for(2 * sz, h, s->cfg[prec].warp_bytes, s->o.max_n / 2, cb);
     const int64_t cnt = binom64(h, sz), cap = (int64_t)G * R;
     for (int64_t r0 = 0; r0 < cnt; r0 += cap) {
       WorkItem w;
@@ -206,7 +206,7 @@ HafLaunch make_launch(gbs_server* s, Stage& g, int prec) {
   L.status = nullptr;
   L.parts = s->d_parts;
   L.warp_bytes = s->cfg[prec].warp_bytes;
-  L.stage_h = kMaxH;
+  L.stage_h = s->o.max_n / 2;
   return L;
 }
 
@@ -610,6 +610,7 @@ extern "C" int gbs_serve_create(const gbs_kernel* k, const gbs_serve_opts* opts,
   if (s->o.queue_capacity <= 0) s->o.queue_capacity = 65536;
   if (s->o.subsets_per_step <= 0) s->o.subsets_per_step = 8192;
   if (s->o.wait_timeout_s <= 0) s->o.wait_timeout_s = 10.0;
+  if (s->o.max_n <= 0 || s->o.max_n > GBS_MAX_N) s->o.max_n = GBS_MAX_N;
   s->o.use_graphs = (s->o.use_graphs >= 0) ? 1 : 0;
   s->k = k;
   s->device = k->device;
@@ -626,7 +627,7 @@ extern "C" int gbs_serve_create(const gbs_kernel* k, const gbs_serve_opts* opts,
     e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
     if (e != cudaSuccess) { ret = cuda_fail(e, "stream"); break; }
     for (int p = 0; p < 2; ++p) {
-      s->cfg[p] = default_cfg(p, GBS_MAX_N);
+      s->cfg[p] = default_cfg(p, s->o.max_n);
       const int smem = s->cfg[p].warps_per_block * s->cfg[p].warp_bytes;
       e = prepare_haf_kernel(p, smem);
       if (e != cudaSuccess) { ret = cuda_fail(e, "kernel attribute"); break; }
@@ -700,7 +701,7 @@ extern "C" int gbs_serve_submit(gbs_server* s, const int* idx, int n, int precis
   clear_error();
   if (!s || !ticket || (n > 0 && !idx)) return fail(GBS_EINVAL, "null argument");
   if (precision != GBS_FP64 && precision != GBS_MIXED) return fail(GBS_EINVAL, "bad precision");
-  if (n < 0 || n > GBS_MAX_N) return fail(GBS_ERANGE, "n = %d outside [0, %d]", n, GBS_MAX_N);
+  if (n < 0 || n > s->o.max_n) return fail(GBS_ERANGE, "n = %d outside [0, %d]", n, s->o.max_n);
   for (int i = 0; i < n; ++i)
     if (idx[i] < 0 || idx[i] >= s->k->m)
       return fail(GBS_ERANGE, "index %d = %d is outside [0, %d)", i, idx[i], s->k->m);

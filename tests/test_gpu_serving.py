@@ -152,3 +152,22 @@ def test_serving_host_failures(gbs, kern):
         assert ei.value.code == -7
     finally:
         srv.destroy()
+
+
+def test_serving_max_n(gbs, kern):
+    """A server built with a smaller photon-number bound refuses larger n and
+    gives the same probabilities as the default server (different launch shape,
+    so equal within the FP64 tolerance, not bit for bit)."""
+    K, m = kern
+    pats = requests(m, 40, 17, n_values=range(2, 21, 2))
+    ref_p, _ = batch_ref(gbs, K, pats, gbs.FP64)
+    srv = gbs.Server(K, max_n=20)
+    try:
+        with pytest.raises(gbs.GbsError) as ei:
+            srv.submit(np.arange(22, dtype=np.int32))
+        assert ei.value.code == -3
+        res = wait_all(srv, [srv.submit(x) for x in pats])
+    finally:
+        srv.destroy()
+    for r, p in zip(res, ref_p):
+        assert abs(r[0] - p) <= FP64_TOL * p, (r[0], p)
