@@ -299,10 +299,100 @@ void Planner::fill(PatDesc* pats, WorkItem* items) {
         w.rank0 = t.rank0;
         w.count = t.count;
         w.part = q++;
-        w.pad[0] = w.pad[1] = w.pad[2] = 0;
+        w.stride = 1;
+        w.pad[0] = w.pad[1] = 0;
       }
     }
     d.item_end = q;
+  }
+}
+
+// ------------------------------------------------------------------------
+// pairing probe
+// ------------------------------------------------------------------------
+// The subset sum pairs positions (2t, 2t+1) of each matrix; the Hafnian does
+// not depend on that choice, but the size of the signed terms does, and with
+// it the rounding error of the sum, which grows with sum |f| / |Haf|. For
+// matrices with n >= kPairingMinN the library tries kPairingCands orderings
+// (the identity and seeded random ones, the same for every matrix of an
+// order) on a systematic sample of kProbePerSize subsets of each size from
+// ceil(h/2) to h-3 (where most of sum |f| lies), and runs the full sum in the
+// ordering with the smallest estimate. The sample costs a few per cent of
+// the full sum at these orders.
+constexpr int kPairingMinN = 26;
+constexpr int kPairingCands = 8;
+constexpr int kProbePerSize = 8;
+static_assert(kProbePerSize < kMaxProbeSample, "probe sample count must index the reciprocal table");
+
+struct PairingPlan {
+  std::vector<int> sel;             // probed matrices (batch indices)
+  std::vector<int> perm;            // candidate orderings, per order n
+  std::vector<PatDesc> pats;        // probe matrices (source fields filled later)
+  std::vector<WorkItem> items;      // their sampled items, part slot = index
+  std::vector<int> perm_off;        // ordering of each probe matrix
+};
+
+static uint64_t splitmix64(uint64_t& x) {
+  uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Probe items hold one round of lane groups each (G subsets of one size), so
+// that the samples of one matrix run in parallel warps.
+static void plan_pairing(const int* n, int batch, int precision, int warp_bytes, int stage_h,
+                         PairingPlan* pp) {
+  const int cb = complex_bytes(precision);
+  int base[kMaxN + 1];
+  for (int v = 0; v <= kMaxN; ++v) base[v] = -1;
+  for (int b = 0; b < batch; ++b)
+    if (n[b] >= kPairingMinN && !(n[b] & 1)) pp->sel.push_back(b);
+  if (pp->sel.empty()) return;
+  for (int b : pp->sel) {
+    const int v = n[b];
+    if (base[v] >= 0) continue;
+    base[v] = (int)pp->perm.size();
+    for (int c = 0; c < kPairingCands; ++c) {
+      const size_t o = pp->perm.size();
+      for (int i = 0; i < v; ++i) pp->perm.push_back(i);
+      uint64_t state = 0x5eedull * 1000003ull + (uint64_t)v * 1009ull + (uint64_t)c;
+      for (int i = v - 1; c > 0 && i > 0; --i) {  // Fisher-Yates; candidate 0 stays the identity
+        const int j = (int)(splitmix64(state) % (uint64_t)(i + 1));
+        std::swap(pp->perm[o + i], pp->perm[o + j]);
+      }
+    }
+  }
+  for (size_t k = 0; k < pp->sel.size(); ++k) {
+    const int v = n[pp->sel[k]], h = v / 2;
+    for (int c = 0; c < kPairingCands; ++c) {
+      PatDesc d;
+      memset(&d, 0, sizeof(d));
+      d.n = v;
+      d.item_begin = (int)pp->items.size();
+      const int q = (int)pp->pats.size();
+      for (int sz = (h + 1) / 2; sz <= h - 3; ++sz) {
+        const int64_t cs = binom64(h, sz);
+        const int K = (int)std::min<int64_t>(cs, kProbePerSize);
+        const int stride = (int)(cs / K);
+        const int G = 32 / lanes_for(2 * sz, h, warp_bytes, stage_h, cb);
+        for (int j = 0; j < K; j += G) {
+          WorkItem w;
+          w.pat = q;
+          w.s = sz;
+          w.rank0 = stride / 2 + j * stride;
+          w.count = std::min(G, K - j);
+          w.part = (int)pp->items.size();
+          w.stride = stride;
+          w.pad[0] = (int)cs;  // the sample's weight C(h, s) / K, read by the choice
+          w.pad[1] = K;
+          pp->items.push_back(w);
+        }
+      }
+      d.item_end = (int)pp->items.size();
+      pp->pats.push_back(d);
+      pp->perm_off.push_back(base[v] + c * v);
+    }
   }
 }
 
@@ -390,7 +480,45 @@ int run_batch(const BatchArgs& a) {
   const size_t items_b = al(sizeof(WorkItem) * std::max<int64_t>(n_items, 1));
   const size_t idx_b = (a.mode == BatchArgs::PROB && !idx_dev) ? al(sizeof(int) * idx_elems) : 0;
   const size_t src_b = (a.mode == BatchArgs::HAFNIAN && !src_dev) ? al(16 * (size_t)src_elems) : 0;
-  const size_t up_b = pats_b + items_b + idx_b + src_b;
+  // FP64: pair terms of each matrix with n >= 6, up to kPairTermBudget bytes
+  // (later matrices form A_S X A_S by the product)
+  constexpr int64_t kPairTermBudget = (int64_t)2 << 30;
+  const bool use_pt = (a.precision == GBS_FP64);
+  int64_t pt_elems = 0;
+  if (use_pt)
+    for (int b = 0; b < batch; ++b) {
+      const int64_t q = pair_terms_elems(a.n[b]);
+      if (q > 0 && 16 * (pt_elems + q) <= kPairTermBudget) pt_elems += q;
+    }
+  const size_t ptoff_b = (use_pt && pt_elems > 0) ? al(sizeof(int64_t) * batch) : 0;
+  // pairing probe of the largest matrices
+  PairingPlan pp;
+  if (n_items > 0) plan_pairing(a.n, batch, a.precision, cfg.warp_bytes, maxn / 2, &pp);
+  const int n_sel = (int)pp.sel.size();
+  const int n_probe = (int)pp.pats.size();
+  const int n_pitems = (int)pp.items.size();
+  const size_t perm_b = n_sel ? al(sizeof(int) * pp.perm.size()) : 0;
+  const size_t ppats_b = n_sel ? al(sizeof(PatDesc) * n_probe) : 0;
+  const size_t pitems_b = n_sel ? al(sizeof(WorkItem) * n_pitems) : 0;
+  const size_t pperm_b = n_sel ? al(sizeof(int) * n_probe) : 0;
+  const size_t mperm_b = n_sel ? al(sizeof(int) * batch) : 0;
+  const size_t selpat_b = n_sel ? al(sizeof(int) * n_sel) : 0;
+  const size_t probe_up_b = perm_b + ppats_b + pitems_b + pperm_b + mperm_b + selpat_b;
+  // two-stage finalisation when some matrix has more than kChunkItems items
+  std::vector<int> chunk_off, chunk_pat;
+  if (plan.max_items_per_pattern() > kChunkItems) {
+    chunk_off.resize(batch + 1);
+    for (int b = 0; b < batch; ++b) {
+      chunk_off[b] = (int)chunk_pat.size();
+      const int cnt = plan.items_of(a.n[b]);
+      for (int c = 0; c * kChunkItems < cnt; ++c) chunk_pat.push_back(b);
+    }
+    chunk_off[batch] = (int)chunk_pat.size();
+  }
+  const int n_chunks = (int)chunk_pat.size();
+  const size_t choff_b = n_chunks ? al(sizeof(int) * (batch + 1)) : 0;
+  const size_t chpat_b = n_chunks ? al(sizeof(int) * n_chunks) : 0;
+  const size_t up_b = pats_b + items_b + idx_b + src_b + ptoff_b + probe_up_b + choff_b + chpat_b;
   // device-only block: parts | counter | status | output staging
   const size_t parts_b = al(sizeof(Partial) * std::max<int64_t>(n_items, 1));
   const size_t ctr_b = 256;
@@ -400,7 +528,12 @@ int run_batch(const BatchArgs& a) {
   const size_t outs_b = out_host ? al(sizeof(double) * 5 * batch) : 0;
   // FP32 path on explicit matrices: one rounded copy per call, gathered by the kernel
   const size_t a32_b = (a.mode == BatchArgs::HAFNIAN && a.precision == GBS_MIXED) ? al(8 * (size_t)src_elems) : 0;
-  const size_t total_b = up_b + parts_b + ctr_b + status_b + outs_b + a32_b;
+  const size_t pt_b = ptoff_b ? al(16 * (size_t)pt_elems) : 0;
+  const size_t pstatus_b = n_sel ? al(sizeof(int) * n_probe) : 0;  // zeroed with ctr and status
+  const size_t pparts_b = n_sel ? al(sizeof(Partial) * n_pitems) : 0;
+  const size_t chparts_b = n_chunks ? al(sizeof(Partial) * n_chunks) : 0;
+  const size_t total_b =
+      up_b + parts_b + ctr_b + status_b + pstatus_b + outs_b + a32_b + pt_b + pparts_b + chparts_b;
 
   void* host_stage = nullptr;
   int slot = -1;
@@ -423,6 +556,50 @@ int run_batch(const BatchArgs& a) {
   }
   if (idx_b) memcpy(hs + pats_b + items_b, a.idx, sizeof(int) * idx_elems);
   if (src_b) memcpy(hs + pats_b + items_b + idx_b, a.src, 16 * (size_t)src_elems);
+  if (ptoff_b) {
+    int64_t* h_ptoff = (int64_t*)(hs + pats_b + items_b + idx_b + src_b);
+    int64_t off = 0;
+    for (int b = 0; b < batch; ++b) {
+      const int64_t q = pair_terms_elems(a.n[b]);
+      if (q > 0 && 16 * (off + q) <= kPairTermBudget) {
+        h_ptoff[b] = off;
+        off += q;
+      } else {
+        h_ptoff[b] = -1;
+      }
+    }
+  }
+
+  const size_t probe_at = pats_b + items_b + idx_b + src_b + ptoff_b;
+  if (n_sel) {
+    unsigned char* q = hs + probe_at;
+    memcpy(q, pp.perm.data(), sizeof(int) * pp.perm.size());
+    q += perm_b;
+    PatDesc* h_ppats = (PatDesc*)q;
+    for (int k = 0; k < n_sel; ++k)
+      for (int c = 0; c < kPairingCands; ++c) {
+        PatDesc d = pp.pats[k * kPairingCands + c];
+        const PatDesc& m = h_pats[pp.sel[k]];
+        d.src_off = m.src_off;
+        d.idx_off = m.idx_off;
+        d.ld = m.ld;
+        h_ppats[k * kPairingCands + c] = d;
+      }
+    q += ppats_b;
+    memcpy(q, pp.items.data(), sizeof(WorkItem) * n_pitems);
+    q += pitems_b;
+    memcpy(q, pp.perm_off.data(), sizeof(int) * n_probe);
+    q += pperm_b;
+    int* h_mperm = (int*)q;
+    for (int b = 0; b < batch; ++b) h_mperm[b] = -1;  // the probe's choice replaces these on the device
+    q += mperm_b;
+    memcpy(q, pp.sel.data(), sizeof(int) * n_sel);
+  }
+  const size_t chunk_at = probe_at + probe_up_b;
+  if (n_chunks) {
+    memcpy(hs + chunk_at, chunk_off.data(), sizeof(int) * (batch + 1));
+    memcpy(hs + chunk_at + choff_b, chunk_pat.data(), sizeof(int) * n_chunks);
+  }
 
   void* dmem = nullptr;
   cudaError_t e = scratch_alloc(&dmem, total_b, st);
@@ -439,14 +616,30 @@ int run_batch(const BatchArgs& a) {
   Partial* d_parts = (Partial*)(dm + up_b);
   int* d_ctr = (int*)(dm + up_b + parts_b);
   int* d_status = (int*)(dm + up_b + parts_b + ctr_b);
-  double* d_outs = outs_b ? (double*)(dm + up_b + parts_b + ctr_b + status_b) : nullptr;
-  float* d_a32 = a32_b ? (float*)(dm + up_b + parts_b + ctr_b + status_b + outs_b) : nullptr;
+  double* d_outs = outs_b ? (double*)(dm + up_b + parts_b + ctr_b + status_b + pstatus_b) : nullptr;
+  float* d_a32 = a32_b ? (float*)(dm + up_b + parts_b + ctr_b + status_b + pstatus_b + outs_b) : nullptr;
+  const int64_t* d_ptoff = ptoff_b ? (const int64_t*)(dm + pats_b + items_b + idx_b + src_b) : nullptr;
+  // device-only block: parts | ctr | status | pstatus | outs | a32 | pt | pparts
+  double* d_pt = pt_b ? (double*)(dm + up_b + parts_b + ctr_b + status_b + pstatus_b + outs_b + a32_b) : nullptr;
+  const int* d_perm = n_sel ? (const int*)(dm + probe_at) : nullptr;
+  const PatDesc* d_ppats = n_sel ? (const PatDesc*)(dm + probe_at + perm_b) : nullptr;
+  const WorkItem* d_pitems = n_sel ? (const WorkItem*)(dm + probe_at + perm_b + ppats_b) : nullptr;
+  const int* d_pperm = n_sel ? (const int*)(dm + probe_at + perm_b + ppats_b + pitems_b) : nullptr;
+  int* d_mperm = n_sel ? (int*)(dm + probe_at + perm_b + ppats_b + pitems_b + pperm_b) : nullptr;
+  const int* d_selpat = n_sel ? (const int*)(dm + probe_at + perm_b + ppats_b + pitems_b + pperm_b + mperm_b) : nullptr;
+  int* d_pstatus = n_sel ? (int*)(dm + up_b + parts_b + ctr_b + status_b) : nullptr;
+  Partial* d_pparts = n_sel ? (Partial*)(dm + up_b + parts_b + ctr_b + status_b + pstatus_b + outs_b + a32_b + pt_b) : nullptr;
+  const int* d_choff = n_chunks ? (const int*)(dm + chunk_at) : nullptr;
+  const int* d_chpat = n_chunks ? (const int*)(dm + chunk_at + choff_b) : nullptr;
+  Partial* d_chparts =
+      n_chunks ? (Partial*)(dm + up_b + parts_b + ctr_b + status_b + pstatus_b + outs_b + a32_b + pt_b + pparts_b)
+               : nullptr;
 
   int ret = GBS_OK;
   do {
     e = cudaMemcpyAsync(dm, hs, up_b, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) { ret = cuda_fail(e, "upload"); break; }
-    e = cudaMemsetAsync(d_ctr, 0, ctr_b + status_b, st);
+    e = cudaMemsetAsync(d_ctr, 0, ctr_b + status_b + pstatus_b, st);
     if (e != cudaSuccess) { ret = cuda_fail(e, "memset"); break; }
     if (d_a32) {
       e = launch_to_float(d_src, d_a32, 2 * src_elems, st);
@@ -465,6 +658,11 @@ int run_batch(const BatchArgs& a) {
       L.parts = d_parts;
       L.warp_bytes = cfg.warp_bytes;
       L.stage_h = maxn / 2;
+      L.pt = d_pt;
+      L.pt_off = d_ptoff;
+      L.batch = batch;
+      L.perm = d_perm;
+      L.perm_off = d_mperm;
       const int smem = cfg.warps_per_block * cfg.warp_bytes;
       int per_sm = max_blocks_per_sm(a.precision, cfg.warps_per_block, smem);
       if (per_sm < 1) { ret = fail(GBS_EINVAL, "launch shape does not fit an SM"); break; }
@@ -473,14 +671,68 @@ int run_batch(const BatchArgs& a) {
       if (need < blocks) blocks = (int)need;
       const bool timed = g_time_start && g_time_stop && !a.cfg_override;
       if (timed) cudaEventRecord(g_time_start, st);
+      if (n_sel) {
+        // probe launch over the candidate orderings, then the choice per matrix
+        HafLaunch Lp = L;
+        Lp.pats = d_ppats;
+        Lp.items = d_pitems;
+        Lp.n_items = n_pitems;
+        Lp.counter = d_ctr + 32;
+        Lp.status = d_pstatus;
+        Lp.parts = d_pparts;
+        Lp.pt = nullptr;
+        Lp.pt_off = nullptr;
+        Lp.batch = n_probe;
+        Lp.perm_off = d_pperm;
+        // few items (one or a few matrices): fewer warps per block, so that
+        // the samples spread over every SM instead of sharing FP64 units
+        const int sms = device_sm_count();
+        int pwpb = (n_pitems + sms - 1) / sms;
+        pwpb = std::max(1, std::min(pwpb, cfg.warps_per_block));
+        const int pper_sm = max_blocks_per_sm(a.precision, pwpb, pwpb * cfg.warp_bytes);
+        if (pper_sm < 1) { ret = fail(GBS_EINVAL, "probe shape does not fit an SM"); break; }
+        int pblocks = sms * pper_sm;
+        const int pneed = (n_pitems + pwpb - 1) / pwpb;
+        if (pneed < pblocks) pblocks = pneed;
+        e = launch_haf_subsets(Lp, a.precision, pblocks, pwpb, st);
+        if (e != cudaSuccess) { ret = cuda_fail(e, "probe launch"); break; }
+        PairingSelect S;
+        S.probe_pats = d_ppats;
+        S.probe_items = d_pitems;
+        S.probe_parts = d_pparts;
+        S.probe_perm_off = d_pperm;
+        S.sel_pat = d_selpat;
+        S.n_sel = n_sel;
+        S.n_cand = kPairingCands;
+        S.main_perm_off = d_mperm;
+        e = launch_pairing_select(S, st);
+        if (e != cudaSuccess) { ret = cuda_fail(e, "pairing choice launch"); break; }
+      }
+      e = launch_pair_terms(L, st);
+      if (e != cudaSuccess) { ret = cuda_fail(e, "pair-term kernel launch"); break; }
       e = launch_haf_subsets(L, a.precision, blocks, cfg.warps_per_block, st);
       if (e != cudaSuccess) { ret = cuda_fail(e, "subset kernel launch"); break; }
       if (timed) cudaEventRecord(g_time_stop, st);
+    }
+    if (n_chunks && n_items > 0) {
+      ChunkLaunch C;
+      C.pats = d_pats;
+      C.parts = d_parts;
+      C.chunk_pat = d_chpat;
+      C.chunk_off = d_choff;
+      C.n_chunks = n_chunks;
+      C.out = d_chparts;
+      e = launch_chunk_sums(C, st);
+      if (e != cudaSuccess) { ret = cuda_fail(e, "chunk-sum launch"); break; }
     }
     FinalizeLaunch F;
     memset(&F, 0, sizeof(F));
     F.pats = d_pats;
     F.parts = d_parts;
+    if (n_chunks && n_items > 0) {
+      F.chunk_parts = d_chparts;
+      F.chunk_off = d_choff;
+    }
     F.idx = (a.mode == BatchArgs::PROB) ? d_idx : nullptr;
     F.status = d_status;
     F.batch = batch;

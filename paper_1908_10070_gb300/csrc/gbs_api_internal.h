@@ -5,6 +5,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "gbs_internal.cuh"
@@ -79,6 +80,14 @@ class Planner {
   void init(const int* n, int batch, int precision, int warp_bytes, const int* rounds_for_n);
   void fill(PatDesc* pats, WorkItem* items);
   int64_t total() const { return total_; }
+  // work items of one matrix of order v (0 for odd v or v < 2)
+  int items_of(int v) const { return (v >= 2 && !(v & 1)) ? (int)tmpl_[v].size() : 0; }
+  int max_items_per_pattern() const {
+    int m = 0;
+    for (int v = 2; v <= kMaxN; v += 2)
+      if (npat_[v]) m = std::max(m, (int)tmpl_[v].size());
+    return m;
+  }
 
  private:
   static constexpr int kKeys = (kMaxN / 2 + 1) * 65;

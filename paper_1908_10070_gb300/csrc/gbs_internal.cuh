@@ -21,15 +21,18 @@ struct PatDesc {
   int item_end;
 };
 
-// A run of `count` consecutive colex ranks among the C(h, s) subsets with s
-// pairs of one matrix. All subsets of an item have the same order N = 2s.
+// `count` colex ranks rank0, rank0 + stride, ... among the C(h, s) subsets
+// with s pairs of one matrix (stride 1: a consecutive run; larger strides make
+// the systematic samples of the pairing probe). All subsets of an item have
+// the same order N = 2s.
 struct WorkItem {
   int pat;
   int s;
   int rank0;
   int count;
   int part;  // slot of this item's partial sum
-  int pad[3];
+  int stride;
+  int pad[2];
 };
 
 // Partial sum of one work item: sum (-1)^{h-|S|} f(X A_S) as a double-double
@@ -51,11 +54,21 @@ __host__ __device__ inline int sched_nbuf(int h) {
 // Shared-memory bytes of one lane group's region for subsets of order N (and
 // half photon number h) with complex elements of `cbytes` bytes: nbuf matrices
 // (FP64: packed upper triangles of N(N+1)/2 entries; FP32: full N x N tiles,
-// whose rows the products read as float4 pairs) and N row indices.
+// whose rows the products read as float4 pairs), N row indices and, for FP64,
+// the N/2 pair numbers of the subset.
 __host__ __device__ inline int group_bytes(int N, int h, int cbytes) {
   const int P = (cbytes == 16) ? N * (N + 1) / 2 : N * N;
-  const int bytes = sched_nbuf(h) * P * cbytes + N * 4;
+  const int bytes = sched_nbuf(h) * P * cbytes + N * 4 + (cbytes == 16 ? N * 2 : 0);
   return (bytes + 15) & ~15;
+}
+
+// Complex elements of one matrix's pair terms (order n = 2h): for every entry
+// (i, j), i <= j, of the packed upper triangle and every pair p < h,
+// Q_p(i, j) = A(i, 2p) A(2p+1, j) + A(i, 2p+1) A(2p, j), pairs innermost.
+// Summed over the pairs of a subset S they give A_S X A_S (used for h >= 3).
+__host__ __device__ inline int64_t pair_terms_elems(int n) {
+  const int h = n / 2;
+  return (n >= 6 && !(n & 1)) ? (int64_t)(n * (n + 1) / 2) * h : 0;
 }
 
 // Per-warp staging of finished subsets' power traces (32 slots of stage_h
@@ -89,10 +102,38 @@ struct HafLaunch {
   Partial* parts;
   int warp_bytes;          // dynamic shared memory per warp
   int stage_h;             // power traces staged per subset (>= the batch's largest n/2)
+  // May be null: a reordering of each matrix's rows and columns. Position i of
+  // matrix b reads source position perm[perm_off[b] + i] (perm_off < 0: the
+  // identity). The Hafnian does not depend on the order; the pairing of
+  // positions (2t, 2t+1) that the subset sum uses does, and with it the
+  // cancellation of the signed sum.
+  const int* perm;
+  const int* perm_off;
+  // FP64 only, may be null: per-matrix pair terms (layout of pair_terms_elems)
+  // at pt + pt_off[pattern]; pt_off < 0 means that matrix forms A_S X A_S by
+  // the product instead
+  double* pt;
+  const int64_t* pt_off;
+  int batch;               // matrices in pats (read by the pair-term kernel)
+};
+
+// Two-stage finalisation: chunk g (of matrix chunk_pat[g]) sums up to
+// kChunkItems consecutive item partials of that matrix; matrix b's chunks are
+// [chunk_off[b], chunk_off[b + 1]).
+constexpr int kChunkItems = 128;
+struct ChunkLaunch {
+  const PatDesc* pats;
+  const Partial* parts;
+  const int* chunk_pat;
+  const int* chunk_off;
+  int n_chunks;
+  Partial* out;
 };
 
 struct FinalizeLaunch {
   const int* sel;          // if non-null, entry b finalises pattern sel[b] (outputs at b)
+  const Partial* chunk_parts;  // if non-null, sum these chunk sums (chunk_off ranges) instead
+  const int* chunk_off;
   const PatDesc* pats;
   const Partial* parts;
   const int* idx;
@@ -107,10 +148,31 @@ struct FinalizeLaunch {
   double* kappa_out;       // kappa (Hafnians)
 };
 
+// Choice of each large matrix's ordering from a probe launch: probe matrix
+// k * n_cand + c is matrix sel_pat[k] in candidate ordering c, its items
+// (part slot = item index) a systematic sample of K subsets of each sampled
+// size s; each probe item carries C(h, s) in pad[0] and K (<= kMaxProbeSample)
+// in pad[1].
+constexpr int kMaxProbeSample = 32;
+struct PairingSelect {
+  const PatDesc* probe_pats;
+  const WorkItem* probe_items;
+  const Partial* probe_parts;
+  const int* probe_perm_off;  // ordering of each probe matrix (offset into perm)
+  const int* sel_pat;
+  int n_sel;
+  int n_cand;
+  int* main_perm_off;         // written: the chosen ordering of each probed matrix
+};
+
 // Defined in haf_subsets.cu
 cudaError_t launch_haf_subsets(const HafLaunch& L, int precision, int blocks, int warps_per_block,
                                cudaStream_t st);
 cudaError_t launch_finalize(const FinalizeLaunch& F, cudaStream_t st);
+cudaError_t launch_chunk_sums(const ChunkLaunch& C, cudaStream_t st);
+cudaError_t launch_pairing_select(const PairingSelect& S, cudaStream_t st);
+// Fill L.pt for every matrix whose pt_off is >= 0 (one block per matrix).
+cudaError_t launch_pair_terms(const HafLaunch& L, cudaStream_t st);
 int max_blocks_per_sm(int precision, int warps_per_block, int smem_bytes);
 // Kernel entry points, for CUDA graph kernel nodes (the serving loop).
 const void* haf_kernel_fn(int precision);

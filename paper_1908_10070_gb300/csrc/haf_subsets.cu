@@ -255,6 +255,33 @@ __device__ __forceinline__ C2<T> tr2_part(const C2<T>* __restrict__ Ra, const C2
   return acc;
 }
 
+// R_2 = A_S X A_S (upper triangle) from the matrix's pair terms: entry (i, j)
+// is sum_{p in S} Q_p(I_i, I_j), I_i = 2 pairs[i/2] + (i mod 2) the position of
+// subset row i in the matrix. Since (A_S X A_S)(i, j) = sum_k A_S(i, k)
+// A_S(k^1, j) and the k of S come in whole pairs, this adds the same products,
+// grouped by pair, with s complex additions per entry instead of 2s complex
+// multiply-adds. pairs[] increases, so I_i <= I_j whenever i <= j.
+__device__ __forceinline__ void pair_sum(double2* __restrict__ dst, const double2* __restrict__ q,
+                                         const int* __restrict__ pairs, int N, int P, int h, int n,
+                                         int l, int L) {
+  const int s = N >> 1;
+  int i = 0, j = l;
+  tri_advance(i, j, 0, N);
+  for (int e = l; e < P; e += L) {
+    const int Ii = 2 * pairs[i >> 1] + (i & 1), Ij = 2 * pairs[j >> 1] + (j & 1);
+    const double2* qe = q + (int64_t)(tri_off(Ii, n) + Ij - Ii) * h;
+    double2 acc = make_double2(0.0, 0.0);
+#pragma unroll 4
+    for (int t = 0; t < s; ++t) {
+      const double2 v = __ldg(qe + pairs[t]);
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    dst[e] = acc;
+    tri_advance(i, j, L, N);
+  }
+}
+
 // ---- FP32 path: full N x N tiles (row stride N), rows read as float4 pairs.
 // C[i][j] = sum_k Ra[i][k] Rb[k^1][j] = sum_t Ra[i][2t] Rb[j][2t+1] + Ra[i][2t+1] Rb[j][2t]
 // (Rb symmetric), computed for i <= j and stored to both (i, j) and (j, i).
@@ -381,7 +408,12 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
     const int g = lane / L, l = lane - g * L;
 
     if (lane < n) {
-      int v = (d.idx_off >= 0) ? P.idx[d.idx_off + lane] : lane;
+      int pos = lane;
+      if (P.perm != nullptr) {
+        const int po = P.perm_off[w.pat];
+        if (po >= 0) pos = P.perm[po + lane];
+      }
+      int v = (d.idx_off >= 0) ? P.idx[d.idx_off + pos] : pos;
       if (P.m_bound > 0 && (v < 0 || v >= P.m_bound)) {
         P.status[w.pat] = 1;
         v = 0;
@@ -392,6 +424,12 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
 
     C* buf = reinterpret_cast<C*>(gbase + (size_t)g * group_bytes(N, h, cb));
     int* rowidx = reinterpret_cast<int*>(buf + sched_nbuf(h) * NP);
+    int* pairs = rowidx + N;  // FP64: the subset's pair numbers, increasing
+    const double2* ptp = nullptr;
+    if (sizeof(T) == 8 && P.pt != nullptr) {
+      const int64_t po = P.pt_off[w.pat];
+      if (po >= 0) ptp = reinterpret_cast<const double2*>(P.pt) + po;
+    }
     int staged = 0;  // subsets whose traces wait in the staging area
     const double2* srcp = src2 + d.src_off;
     const float2* src32p = P.src32 ? reinterpret_cast<const float2*>(P.src32) + d.src_off : nullptr;
@@ -405,7 +443,7 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
       const bool active = jsub < w.count;
       // -- unrank the subset (colex): rank = sum_i C(c_i, i), c_1 < ... < c_s
       {
-        int r = w.rank0 + (active ? jsub : 0);
+        int r = w.rank0 + (active ? jsub : 0) * (w.stride > 1 ? w.stride : 1);
         int c = h - 1;
         for (int i = s; i >= 1; --i) {
           while (tab.binom[c][i] > r) --c;
@@ -414,6 +452,7 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
           if ((t % L) == l) {
             rowidx[2 * t] = xs[2 * c];
             rowidx[2 * t + 1] = xs[2 * c + 1];
+            if (sizeof(T) == 8) pairs[t] = c;
           }
           --c;
         }
@@ -453,9 +492,12 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
         const SchedOp op = c_sched[h][o];
         if (op.kind == kEnd) break;
         if (op.kind == kProd) {
-          if constexpr (sizeof(T) == 8)
-            sym_prod<T>(buf + op.k * NP, buf + op.a * NP, buf + op.b * NP, N, NP, l, L);
-          else
+          if constexpr (sizeof(T) == 8) {
+            if (ptp != nullptr && op.k == 1 && op.a == 0 && op.b == 0)
+              pair_sum(buf + NP, ptp, pairs, N, NP, h, n, l, L);
+            else
+              sym_prod<T>(buf + op.k * NP, buf + op.a * NP, buf + op.b * NP, N, NP, l, L);
+          } else
             sym_prod_full(buf + op.k * NP, buf + op.a * NP, buf + op.b * NP, N, l, L);
         } else {
           C part;
@@ -549,9 +591,70 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
   }
 }
 
-// One warp per pattern: lane j adds the item partials j, j+32, ... in order,
-// the lanes' sums meet in a fixed butterfly (deterministic for a given item
-// count), and lane 0 writes the outputs.
+// Warp sum of parts[begin, end): lane j adds j, j+32, ... in that order (four
+// loads issued ahead of their additions), the lanes meet in a fixed
+// butterfly; every lane ends with the total (deterministic for a given range).
+__device__ __forceinline__ void sum_partials(const Partial* __restrict__ parts, int begin, int end,
+                                             int lane, double& rh, double& rl, double& ih, double& il,
+                                             double& K) {
+  const unsigned FULL = 0xffffffffu;
+  int q = begin + lane;
+  for (; q + 96 < end; q += 128) {
+    Partial pr[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) pr[u] = parts[q + 32 * u];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      dd_add(rh, rl, pr[u].re_hi, pr[u].re_lo);
+      dd_add(ih, il, pr[u].im_hi, pr[u].im_lo);
+      K += pr[u].kappa;
+    }
+  }
+  for (; q < end; q += 32) {
+    const Partial pr = parts[q];
+    dd_add(rh, rl, pr.re_hi, pr.re_lo);
+    dd_add(ih, il, pr.im_hi, pr.im_lo);
+    K += pr.kappa;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const double orh = __shfl_xor_sync(FULL, rh, off), orl = __shfl_xor_sync(FULL, rl, off);
+    const double oih = __shfl_xor_sync(FULL, ih, off), oil = __shfl_xor_sync(FULL, il, off);
+    K += __shfl_xor_sync(FULL, K, off);
+    dd_add(rh, rl, orh, orl);
+    dd_add(ih, il, oih, oil);
+  }
+}
+
+// First stage of the two-stage finalisation (matrices with many items): one
+// warp per chunk of up to kChunkItems consecutive item partials of a matrix.
+// A lone warp's FP64 additions are slow on this part, so the long per-matrix
+// sums are spread over many warps; the chunking is fixed by the item counts,
+// which keeps the result deterministic.
+__global__ void chunk_sum_kernel(const ChunkLaunch C) {
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  for (int g = blockIdx.x * wpb + (threadIdx.x >> 5); g < C.n_chunks; g += gridDim.x * wpb) {
+    const int b = C.chunk_pat[g];
+    const PatDesc d = C.pats[b];
+    const int begin = d.item_begin + (g - C.chunk_off[b]) * kChunkItems;
+    const int end = min(begin + kChunkItems, d.item_end);
+    double rh = 0, rl = 0, ih = 0, il = 0, K = 0;
+    sum_partials(C.parts, begin, end, lane, rh, rl, ih, il, K);
+    if (lane == 0) {
+      Partial pr;
+      pr.re_hi = rh;
+      pr.re_lo = rl;
+      pr.im_hi = ih;
+      pr.im_lo = il;
+      pr.kappa = K;
+      pr.pad[0] = pr.pad[1] = pr.pad[2] = 0.0;
+      C.out[g] = pr;
+    }
+  }
+}
+
+// One warp per pattern: the item partials (or, after chunk_sum_kernel, the
+// chunk sums) are added by sum_partials, and lane 0 writes the outputs.
 __global__ void finalize_kernel(const FinalizeLaunch F) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -562,19 +665,10 @@ __global__ void finalize_kernel(const FinalizeLaunch F) {
     const int n = d.n;
     double rh = 0, rl = 0, ih = 0, il = 0, K = 0;
     if (!(n & 1) && n > 0) {
-      for (int q = d.item_begin + lane; q < d.item_end; q += 32) {
-        const Partial pr = F.parts[q];
-        dd_add(rh, rl, pr.re_hi, pr.re_lo);
-        dd_add(ih, il, pr.im_hi, pr.im_lo);
-        K += pr.kappa;
-      }
-      for (int off = 16; off > 0; off >>= 1) {
-        const double orh = __shfl_xor_sync(FULL, rh, off), orl = __shfl_xor_sync(FULL, rl, off);
-        const double oih = __shfl_xor_sync(FULL, ih, off), oil = __shfl_xor_sync(FULL, il, off);
-        K += __shfl_xor_sync(FULL, K, off);
-        dd_add(rh, rl, orh, orl);
-        dd_add(ih, il, oih, oil);
-      }
+      if (F.chunk_parts)
+        sum_partials(F.chunk_parts, F.chunk_off[pb], F.chunk_off[pb + 1], lane, rh, rl, ih, il, K);
+      else
+        sum_partials(F.parts, d.item_begin, d.item_end, lane, rh, rl, ih, il, K);
     } else if (n == 0) {
       rh = 1.0;  // the empty matrix has one (empty) perfect matching
       K = 1.0;
@@ -612,7 +706,107 @@ __global__ void finalize_kernel(const FinalizeLaunch F) {
   }
 }
 
+// Pair terms of one matrix per block: the zero-diagonal matrix is staged in
+// shared memory, then Q_p(i, j) = A(i, 2p) A(2p+1, j) + A(i, 2p+1) A(2p, j) is
+// written for the packed upper triangle, pairs innermost (coalesced stores).
+__global__ void __launch_bounds__(256) pair_terms_kernel(const HafLaunch P) {
+  __shared__ double2 A[kMaxN * kMaxN];
+  __shared__ int rows[kMaxN];
+  __shared__ int tri[kMaxN + 1];
+  const double2* src2 = reinterpret_cast<const double2*>(P.src);
+  double2* pt2 = reinterpret_cast<double2*>(P.pt);
+  for (int b = blockIdx.x; b < P.batch; b += gridDim.x) {
+    const int64_t po = P.pt_off[b];
+    const PatDesc d = P.pats[b];
+    const int n = d.n, h = n >> 1;
+    if (po < 0 || pair_terms_elems(n) == 0) continue;  // uniform over the block
+    if (threadIdx.x < n) {
+      int pos = threadIdx.x;
+      if (P.perm != nullptr && P.perm_off[b] >= 0) pos = P.perm[P.perm_off[b] + threadIdx.x];
+      int v = (d.idx_off >= 0) ? P.idx[d.idx_off + pos] : pos;
+      if (P.m_bound > 0 && (v < 0 || v >= P.m_bound)) v = 0;  // flagged by the subset kernel
+      rows[threadIdx.x] = v;
+    }
+    if (threadIdx.x <= n) tri[threadIdx.x] = threadIdx.x * n - ((threadIdx.x * (threadIdx.x - 1)) >> 1);
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int i = e / n, j = e - i * n;
+      A[e] = (i == j) ? make_double2(0.0, 0.0) : __ldg(src2 + d.src_off + (int64_t)rows[i] * d.ld + rows[j]);
+    }
+    __syncthreads();
+    const int total = (n * (n + 1) / 2) * h;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+      const int e = t / h, p = t - e * h;
+      int i = 0;
+      while (tri[i + 1] <= e) ++i;
+      const int j = i + (e - tri[i]);
+      const double2 a1 = A[i * n + 2 * p], b1 = A[(2 * p + 1) * n + j];
+      const double2 a2 = A[i * n + 2 * p + 1], b2 = A[2 * p * n + j];
+      double2 q = make_double2(0.0, 0.0);
+      q = cfma<double>(a1, b1, q);
+      q = cfma<double>(a2, b2, q);
+      pt2[po + t] = q;
+    }
+    __syncthreads();
+  }
+}
+
+// 1/K for the probe's sample counts K = 1..kMaxProbeSample - 1
+__constant__ double c_recip[kMaxProbeSample] = {
+    0.0,        1.0,        1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,  1.0 / 6,  1.0 / 7,
+    1.0 / 8,    1.0 / 9,    1.0 / 10, 1.0 / 11, 1.0 / 12, 1.0 / 13, 1.0 / 14, 1.0 / 15,
+    1.0 / 16,   1.0 / 17,   1.0 / 18, 1.0 / 19, 1.0 / 20, 1.0 / 21, 1.0 / 22, 1.0 / 23,
+    1.0 / 24,   1.0 / 25,   1.0 / 26, 1.0 / 27, 1.0 / 28, 1.0 / 29, 1.0 / 30, 1.0 / 31};
+
+// One warp per probed matrix, lane c < n_cand for candidate ordering c: the
+// candidate's sum of |f| over the whole subset sum is estimated from its
+// sampled items (the K sampled subsets of size s stand for all C(h, s), so
+// each item's kappa counts C(h, s) / K times), and the candidate with the
+// smallest estimate (the lowest c on a tie) becomes the matrix's ordering.
+__global__ void pairing_select_kernel(const PairingSelect S) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (k >= S.n_sel) return;  // uniform over the warp
+  double est = INFINITY;
+  if (lane < S.n_cand) {
+    const int q = k * S.n_cand + lane;
+    const PatDesc d = S.probe_pats[q];
+    est = 0.0;
+#pragma unroll 4
+    for (int it = d.item_begin; it < d.item_end; ++it) {
+      const WorkItem w = S.probe_items[it];
+      const double kp = S.probe_parts[it].kappa;
+      est = fma((double)w.pad[0] * c_recip[w.pad[1] & (kMaxProbeSample - 1)], kp, est);
+    }
+    if (!(est == est)) est = INFINITY;  // a NaN estimate never wins
+  }
+  int c = lane;
+  for (int off = 16; off > 0; off >>= 1) {
+    const double oe = __shfl_xor_sync(FULL, est, off);
+    const int oc = __shfl_xor_sync(FULL, c, off);
+    if (oe < est || (oe == est && oc < c)) {
+      est = oe;
+      c = oc;
+    }
+  }
+  if (lane == 0) S.main_perm_off[S.sel_pat[k]] = S.probe_perm_off[k * S.n_cand + (c < S.n_cand ? c : 0)];
+}
+
 }  // namespace
+
+cudaError_t launch_pairing_select(const PairingSelect& S, cudaStream_t st) {
+  if (S.n_sel <= 0 || S.n_cand > 32) return S.n_sel <= 0 ? cudaSuccess : cudaErrorInvalidValue;
+  pairing_select_kernel<<<(S.n_sel + 3) / 4, 128, 0, st>>>(S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_terms(const HafLaunch& L, cudaStream_t st) {
+  if (L.pt == nullptr || L.batch <= 0) return cudaSuccess;
+  int blocks = L.batch < 4096 ? L.batch : 4096;
+  pair_terms_kernel<<<blocks, 256, 0, st>>>(L);
+  return cudaGetLastError();
+}
 
 // Raise the kernel's dynamic shared-memory limit to the device maximum once
 // (per device and precision); it is never lowered, so every launch shape, and
@@ -676,6 +870,14 @@ const void* finalize_kernel_fn() { return (const void*)finalize_kernel; }
 cudaError_t prepare_haf_kernel(int precision, int smem_bytes) {
   (void)smem_bytes;
   return ensure_smem_limit(precision);
+}
+
+cudaError_t launch_chunk_sums(const ChunkLaunch& C, cudaStream_t st) {
+  if (C.n_chunks <= 0) return cudaSuccess;
+  int blocks = (C.n_chunks + 3) / 4;
+  if (blocks > 8192) blocks = 8192;
+  chunk_sum_kernel<<<blocks, 128, 0, st>>>(C);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(const FinalizeLaunch& F, cudaStream_t st) {

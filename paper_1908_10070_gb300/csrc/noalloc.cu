@@ -126,7 +126,8 @@ extern "C" int gbs_hafnian_batch_noalloc(const double* A_ri, const int* n, const
           w.rank0 = (int)r0;
           w.count = (int)((cnt - r0) < cap ? (cnt - r0) : cap);
           w.part = q;
-          w.pad[0] = w.pad[1] = w.pad[2] = 0;
+          w.stride = 1;
+          w.pad[0] = w.pad[1] = 0;
           ++q;
         }
       }

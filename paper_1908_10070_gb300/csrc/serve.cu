@@ -186,7 +186,8 @@ void request_items(const gbs_server* s, int si, int n, int prec, std::vector<Wor
       w.rank0 = (int)r0;
       w.count = (int)std::min<int64_t>(cap, cnt - r0);
       w.part = 0;
-      w.pad[0] = w.pad[1] = w.pad[2] = 0;
+      w.stride = 1;
+      w.pad[0] = w.pad[1] = 0;
       out.push_back(w);
     }
   }

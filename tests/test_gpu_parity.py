@@ -391,3 +391,43 @@ def test_determinism_and_order_independence(gbs):
     perm = np.random.default_rng(0).permutation(len(pats))
     c = run_prob(gbs, K, [pats[i] for i in perm], 0)
     assert np.array_equal(c[2], a[2][perm])
+
+
+def test_pairing_choice_lowers_cancellation(gbs):
+    """For n >= 26 the batched path runs the subset sum in the candidate ordering
+    of rows and columns whose sampled sum |f| is smallest. The Hafnian is the
+    same in every ordering; the cancellation ratio kappa = sum |f| / |Haf| falls
+    (the no-alloc entry point keeps the given ordering), and both results agree
+    with the stored oracle values."""
+    import json
+    import os
+
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "large_m900_oracle.json")))
+    U, r, pats = W.workload("large_m900")
+    pats = pats[:16]
+    K = kernel_for(gbs, U, r)
+    B = torch.zeros(2 * 900 * 900, dtype=torch.float64, device="cuda")
+    K.copy_B(B)
+    Bc = B.cpu().numpy().view(np.complex128).reshape(900, 900)
+    flat, n, offs = gbs.pack_matrices([Bc[np.ix_(x, x)] for x in pats])
+    A = dev(flat)
+    b = len(pats)
+    h1 = torch.zeros(2 * b, dtype=torch.float64, device="cuda")
+    k1 = torch.zeros(b, dtype=torch.float64, device="cuda")
+    gbs.hafnian_batch(A, n, offs, gbs.FP64, haf_out=h1, kappa_out=k1)
+    h0 = torch.zeros(2 * b, dtype=torch.float64, device="cuda")
+    k0 = torch.zeros(b, dtype=torch.float64, device="cuda")
+    for c in range(0, b, 2):
+        out = torch.zeros(4, dtype=torch.float64, device="cuda")
+        ko = torch.zeros(2, dtype=torch.float64, device="cuda")
+        gbs.hafnian_batch_noalloc(A, n[c:c + 2], offs[c:c + 2], gbs.FP64, haf_out=out, kappa_out=ko)
+        h0[2 * c:2 * c + 4] = out
+        k0[c:c + 2] = ko
+    ref = np.array([complex(q["haf_dd"][0] + q["haf_dd"][1], q["haf_dd"][2] + q["haf_dd"][3])
+                    for q in g["patterns"][:16]])
+    for h in (h1, h0):
+        a = h.cpu().numpy()
+        assert np.all(rel(a[0::2] + 1j * a[1::2], ref) <= FP64_TOL)
+    ratio = k1.cpu().numpy() / k0.cpu().numpy()
+    assert np.all(np.isfinite(ratio))
+    assert np.exp(np.mean(np.log(ratio))) < 0.8, ratio
