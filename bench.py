@@ -15,6 +15,7 @@ products, OpenMP over patterns) on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -28,6 +29,21 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
+
+# DRAM bytes (read + write) per launch of haf_subsets_kernel<double> on the
+# headline workload, from one ncu capture (profiles/haf_subsets_fp64_m64_n16.md).
+# Reported only while the kernel's sources are the ones the capture was taken
+# from; any change to them makes the figure stale and the bench reports null.
+NCU_TRAFFIC = {"sources_sha256": "a534bf9369cdfa996fed10fa83b62c1464d3e03e562a3422ca2cfec92e9946d6", "bytes_per_launch": 93250816.0}
+KERNEL_SOURCES = ("paper_1908_10070_gb300/csrc/haf_subsets.cu", "paper_1908_10070_gb300/csrc/gbs_internal.cuh")
+
+
+def measured_traffic():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return NCU_TRAFFIC["bytes_per_launch"] if h.hexdigest() == NCU_TRAFFIC["sources_sha256"] else None
 
 WORKLOAD = "batched_m64_n16"
 METRIC = "GBS output probs/sec at n=16/24/30 vs FP64 oracle; p50/p99 request latency"
@@ -285,7 +301,8 @@ def main():
                    "patterns_per_step": b, "l2": "flushed (256 MB write) between timed steps",
                    "autotuned_rounds_per_item": tuned_rounds},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": measured_traffic() if prec == gbs.FP64 else None,
                      "kernel": "haf_subsets_kernel<%s>" % ("double" if prec == gbs.FP64 else "float"),
                      "kernel_ms": t_kern,
                      "flops_per_launch": flops,
