@@ -144,10 +144,12 @@ int gbs_prob_batch(const gbs_kernel* k, const int* idx, const int* n, const int6
                    double* haf_ri_out, double* err_est_out);
 
 /* Instrumentation: when both are non-NULL, every later batch records `start`
- * immediately before and `stop` immediately after its subset-sum kernel, on
- * the batch's stream (cudaEvent_t passed as void*), so a caller can time that
- * kernel alone. Pass NULL, NULL to stop. Process-wide; not for concurrent use
- * from several threads. The paper has no counterpart (measurement only). */
+ * immediately before and `stop` immediately after the kernels of its subset
+ * sum (the pair terms, for n >= 26 the ordering probe and choice, and the
+ * subset kernel), on the batch's stream (cudaEvent_t passed as void*), so a
+ * caller can time that work alone. Pass NULL, NULL to stop. Process-wide; not
+ * for concurrent use from several threads. The paper has no counterpart
+ * (measurement only). */
 int gbs_set_timing_events(void* start, void* stop);
 
 /* ------------------------------------------------------------------------ */
@@ -160,6 +162,72 @@ int gbs_set_timing_events(void* start, void* stop);
  * that find no tuned entry use a built-in default. Synchronises `stream`.
  * chosen_out (may be NULL) receives the chosen subsets-per-item. */
 int gbs_autotune(int n, int precision, void* stream, int* chosen_out);
+
+/* ------------------------------------------------------------------------ */
+/* Sampling (Sec. 3)                                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Step 1 of the sampler (Sec. 3.1, Eq. Eqdistribution): the total photon-number
+ * distribution P_n = sum over |s| = n of p(s), for n = 0..n_max, computed on the
+ * device as the power series prod_i sech r_i (1 - tanh^2 r_i z^2)^(-1/2) (the
+ * negative binomial of Eq. Eqdistribution when every r_i is equal).
+ *   n_max   0..2048.
+ *   Pn_out  n_max + 1 doubles, host or device (caller-owned). P_n = 0 for odd n.
+ * Errors: GBS_EINVAL, GBS_ERANGE, GBS_ENOMEM, GBS_ECUDA. */
+int gbs_photon_number_dist(const gbs_kernel* k, int n_max, void* stream, double* Pn_out);
+
+/* Brute-force sampler (Appendix I): p(s) of every one of the C(m+n-1, n)
+ * configurations with n photons (enumerated on the device in colex order of
+ * their index lists x_1 <= ... <= x_n), a fixed-order prefix sum, and for each
+ * uniform u the configuration whose interval contains u * (sum of all p).
+ *   n             0..GBS_MAX_N; C(m+n-1, n) must not exceed 2^26.
+ *   uniforms      `draws` numbers in [0, 1), host or device.
+ *   precision     GBS_FP64 or GBS_MIXED (the probability path used).
+ *   patterns_out  draws * n ints, host or device: draw d's sorted mode list at
+ *                 [d * n, (d + 1) * n).
+ *   total_out     may be NULL; receives sum of p over all configurations
+ *                 (= P_n of Eq. Eqdistribution up to rounding), host or device.
+ * Errors: GBS_EINVAL, GBS_ERANGE, GBS_ENOMEM, GBS_ECUDA. */
+int gbs_sample_bruteforce(const gbs_kernel* k, int n, const double* uniforms, int draws, int precision,
+                          void* stream, int* patterns_out, double* total_out);
+
+/* Theorem 1 (Sec. 3.3, Algorithm 2): marginal probabilities
+ * q_n(x_1..x_k) = sum over x_{k+1..n} of |Haf(W_x)|^2 / f_n, W = U U^T, of
+ * `batch` ordered prefixes of length k, for n-photon samples with identical
+ * squeezing on every mode (the kernel's r must all be equal and > 0). The
+ * sub-Hafnians of every even subset of each prefix come from the batched FP64
+ * path; the sums over A, B, mu of Theorem 1 run one block per prefix.
+ *   x      batch * k mode indices in [0, m), prefix b at [b * k, (b + 1) * k),
+ *          host or device (read before return).
+ *   k      0..min(n, 10).  n  even, <= GBS_MAX_N.
+ *   q_out  batch doubles, host or device. k = 0 gives 1; k = n gives
+ *          |Haf(W_x)|^2 / f_n (Eq. EqDisE).
+ * Errors: GBS_EINVAL (also unequal squeezing), GBS_ERANGE, GBS_ENOMEM, GBS_ECUDA. */
+int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int batch, int n, void* stream,
+                       double* q_out);
+
+/* Algorithm 1 (Sec. 3.2): one ordered n-photon sample x_1..x_n by the chain
+ * rule, x_k drawn from the m conditional weights q_n(x_1..x_{k-1}, l),
+ * l = 0..m-1 (gbs_marginal_batch), by the inverse CDF in mode order with the
+ * caller's uniform u_k. Identical squeezing only.
+ *   n         even, 0..10.
+ *   uniforms  n numbers in [0, 1), HOST memory.
+ *   x_out     n ints, HOST memory: the mode of each photon in draw order.
+ * Errors: GBS_EINVAL, GBS_ERANGE, GBS_ENOMEM, GBS_ECUDA. */
+int gbs_sample_chain(const gbs_kernel* k, int n, const double* uniforms, void* stream, int* x_out);
+
+/* One complete sample (Sec. 3, Steps 1-3): the photon number n drawn from
+ * P_n of Eq. Eqdistribution restricted to n <= n_max and renormalised (inverse
+ * CDF with uniforms[0]), then the n photons placed by gbs_sample_chain with
+ * uniforms[1..n]. Identical squeezing only.
+ *   n_max     0..10 (the chain sampler's limit); the mass above n_max is
+ *             left out, so choose n_max where P_n has become negligible.
+ *   uniforms  n_max + 1 numbers in [0, 1), HOST memory.
+ *   n_out     HOST int: the drawn photon number (even).
+ *   x_out     HOST, room for n_max ints: x_1..x_n in draw order.
+ * Errors: GBS_EINVAL, GBS_ERANGE, GBS_ENOMEM, GBS_ECUDA. */
+int gbs_sample(const gbs_kernel* k, int n_max, const double* uniforms, void* stream, int* n_out,
+               int* x_out);
 
 /* ------------------------------------------------------------------------ */
 /* Serving: continuous batching of single-pattern probability requests      */

@@ -71,6 +71,7 @@ def lib():
             L.gbs_sample_bruteforce.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, vp, ip, dp]
             L.gbs_marginal_batch.argtypes = [vp, ip, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, dp]
             L.gbs_sample_chain.argtypes = [vp, ctypes.c_int, dp, vp, ip]
+            L.gbs_sample.argtypes = [vp, ctypes.c_int, dp, vp, ctypes.POINTER(ctypes.c_int), ip]
             L.gbs_autotune.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int)]
             L.gbs_set_timing_events.argtypes = [vp, vp]
             L.gbs_serve_create.argtypes = [vp, ctypes.POINTER(ServeOpts), ctypes.POINTER(ctypes.c_void_p)]
@@ -255,6 +256,18 @@ def sample_chain(kernel: KernelMatrix, n: int, uniforms, stream=None) -> np.ndar
     x = np.zeros(max(n, 1), dtype=np.int32)
     _check(lib().gbs_sample_chain(kernel.handle, int(n), _ptr(u), _stream(stream), _ptr(x)))
     return x[:n]
+
+
+def sample(kernel: KernelMatrix, n_max: int, uniforms, stream=None) -> np.ndarray:
+    """One complete sample (gbs_sample): n from P_n truncated at n_max, then
+    Algorithm 1. uniforms: n_max + 1 numbers in [0, 1). Returns x_1..x_n."""
+    u = np.ascontiguousarray(uniforms, dtype=np.float64)
+    if u.size < n_max + 1:
+        raise ValueError("need n_max + 1 uniform numbers")
+    x = np.zeros(max(n_max, 1), dtype=np.int32)
+    n = ctypes.c_int()
+    _check(lib().gbs_sample(kernel.handle, int(n_max), _ptr(u), _stream(stream), ctypes.byref(n), _ptr(x)))
+    return x[:n.value]
 
 
 def autotune(n, precision=FP64, stream=None) -> int:

@@ -294,3 +294,32 @@ extern "C" int gbs_sample_chain(const gbs_kernel* k, int n, const double* unifor
   for (int i = 0; i < n; ++i) x_out[i] = x[i];
   return GBS_OK;
 }
+
+// Steps 1-3 of Sec. 3: n from P_n (truncated at n_max, renormalised) by the
+// inverse CDF with uniforms[0], then the chain rule for the n photons.
+extern "C" int gbs_sample(const gbs_kernel* k, int n_max, const double* uniforms, void* stream, int* n_out,
+                          int* x_out) {
+  clear_error();
+  if (!k || !uniforms || !n_out || (n_max > 0 && !x_out)) return fail(GBS_EINVAL, "null argument");
+  if (n_max < 0 || n_max > kMaxK) return fail(GBS_ERANGE, "n_max = %d outside [0, %d]", n_max, kMaxK);
+  if (!k->r_uniform) return fail(GBS_EINVAL, "sampling needs identical squeezing on every mode");
+  std::vector<double> Pn((size_t)n_max + 1);
+  int rc = gbs_photon_number_dist(k, n_max, stream, Pn.data());
+  if (rc) return rc;
+  double tot = 0.0;
+  for (int v = 0; v <= n_max; v += 2) tot += std::max(Pn[v], 0.0);
+  if (!(tot > 0.0)) return fail(GBS_EINVAL, "P_n vanishes for every n <= n_max");
+  const double target = uniforms[0] * tot;
+  double run = 0.0;
+  int n = n_max & ~1;
+  for (int v = 0; v <= n_max; v += 2) {
+    run += std::max(Pn[v], 0.0);
+    if (run > target) {
+      n = v;
+      break;
+    }
+  }
+  *n_out = n;
+  if (n == 0) return GBS_OK;
+  return gbs_sample_chain(k, n, uniforms + 1, stream, x_out);
+}

@@ -29,11 +29,19 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_last_error_starts_empty():
+    """The last-error message is per thread: a thread that has made no call
+    reads an empty string, whatever other threads (or tests) did before."""
+    import threading
+
     from paper_1908_10070_gb300 import build
 
     lib = ctypes.CDLL(build.build())
     lib.gbs_last_error.restype = ctypes.c_char_p
-    assert lib.gbs_last_error() == b""
+    seen = []
+    t = threading.Thread(target=lambda: seen.append(lib.gbs_last_error()))
+    t.start()
+    t.join()
+    assert seen == [b""]
 
 
 def test_argument_errors_without_device():

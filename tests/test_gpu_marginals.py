@@ -105,3 +105,38 @@ def test_chain_sampler_distribution(gbs, orc):
     tv = 0.5 * np.abs(freq - pn).sum()
     expected = 0.5 * np.sqrt(2 / (np.pi * draws)) * np.sum(np.sqrt(pn * (1 - pn)))
     assert tv <= 1.5 * expected, (tv, expected)
+
+
+def test_end_to_end_sample(gbs):
+    """gbs_sample (Sec. 3, Steps 1-3): the photon number of every draw is the
+    inverse-CDF pick of P_n restricted to n <= n_max (Eq. Eqdistribution), the
+    photons are then placed by Algorithm 1, the same uniforms give the same
+    sample, and the frequencies of n follow the truncated P_n."""
+    m, r, n_max = 5, 0.6, 4
+    U = W.haar_unitary(m, 91)
+    K = gbs.build_kernel(U, np.full(m, r))
+    P = gbs.photon_number_dist(K, n_max)
+    Pe = np.array([P[v] if v % 2 == 0 else 0.0 for v in range(n_max + 1)])
+    cum = np.cumsum(Pe)
+    rng = np.random.default_rng(11)
+    draws = 600
+    counts = np.zeros(n_max + 1)
+    for _ in range(draws):
+        u = rng.random(n_max + 1)
+        x = gbs.sample(K, n_max, u)
+        n = len(x)
+        assert n == int(np.searchsorted(cum, u[0] * cum[-1], side="right"))
+        assert n % 2 == 0 and np.all((x >= 0) & (x < m))
+        if n:
+            assert np.array_equal(x, gbs.sample_chain(K, n, u[1:n + 1]))
+        counts[n] += 1
+    pt = Pe / Pe.sum()
+    tv = 0.5 * np.abs(counts / draws - pt).sum()
+    expected = 0.5 * np.sqrt(2 / (np.pi * draws)) * np.sum(np.sqrt(pt * (1 - pt)))
+    assert tv <= 2.0 * expected, (tv, expected, counts, pt)
+    u = np.full(n_max + 1, 0.3)
+    assert np.array_equal(gbs.sample(K, n_max, u), gbs.sample(K, n_max, u))
+    assert len(gbs.sample(K, n_max, np.zeros(n_max + 1))) == 0  # u_0 = 0 picks n = 0 (P_0 > 0)
+    with pytest.raises(gbs.GbsError) as ei:
+        gbs.sample(gbs.build_kernel(U, np.linspace(0.3, 0.8, m)), n_max, u)
+    assert ei.value.code == -1
