@@ -17,6 +17,14 @@ What each function computes, and the passage it follows:
   matrix products; also returns kappa = sum_S |f(X A_S)|.
 * ``haf_subset_f64(A)``: the same sum in plain double precision.
 * ``per_ryser(C)``: permanent by Ryser's formula.
+* ``haf_repeated(B, reps)``: Hafnian of the matrix that repeats row and column j
+  of B reps[j] times, as a sum over 0 <= nu_j <= reps[j] of
+  prod_j (-1)^nu_j C(reps[j], nu_j) (x^T B x / 2)^{n/2}, x_j = reps[j] - 2 nu_j,
+  divided by 2^n (n/2)! (the moment-extraction identity of Kan, 2008, "From
+  moments of sum to moments of product", derived in the docstring below). Not
+  in the paper: it is the collision path of the library (cost prod (reps+1)
+  instead of 2^{n/2}). Plain Python, double-precision terms, exactly rounded
+  sums (math.fsum); small cases only.
 * ``prob(U, r, patterns)``: p(s) = |Haf(B_x)|^2 / (prod_j s_j! prod_i cosh r_i)
   (Eq. ProOri with per-mode r; W_x gather of Sec. 3.2).
 
@@ -26,6 +34,8 @@ force and textbook special cases; see that file for the list.
 from __future__ import annotations
 
 import ctypes
+import itertools
+import math
 import os
 import platform
 import subprocess
@@ -169,6 +179,41 @@ def per_ryser(C) -> complex:
     out = np.zeros(4)
     _load().orc_per_ryser(k, _dp(_cplx(C)), _dp(out))
     return _dd_complex(out)
+
+
+def haf_repeated(B, reps):
+    """Hafnian of B with row/column j repeated reps[j] times (n = sum reps).
+
+    Derivation. With Q(z) = z^T A z / 2 for the n x n repeated matrix A, the
+    coefficient of z_1 z_2 ... z_n in Q(z)^{n/2} / (n/2)! is Haf(A): each way of
+    picking one entry A_ij z_i z_j (i != j) from each of the n/2 factors so that
+    every variable appears once is a perfect matching, counted (n/2)! times over
+    the factor order and once per orientation (the 1/2 of Q cancels the two
+    orientations); diagonal entries give z_i^2 and never reach that monomial.
+    For a homogeneous polynomial P of degree n, sum over s in {+1, -1}^n of
+    (prod s_i) P(s) keeps exactly the monomials odd in every variable, i.e.
+    2^n times the coefficient of z_1 ... z_n. At a sign vector, Q depends only on
+    x_j = (sum of the signs of mode j's copies) = reps[j] - 2 nu_j, nu_j the
+    number of minus signs among them, which C(reps[j], nu_j) sign vectors share,
+    each with prod s_i = (-1)^nu_j.
+    """
+    B = np.asarray(B, dtype=np.complex128)
+    reps = [int(v) for v in reps]
+    n = sum(reps)
+    if n % 2:
+        return 0j
+    h = n // 2
+    re, im = [], []
+    for nu in itertools.product(*[range(v + 1) for v in reps]):
+        x = np.array([reps[j] - 2 * nu[j] for j in range(len(reps))], dtype=np.float64)
+        w = 1
+        for j, v in enumerate(reps):
+            w *= (-1) ** nu[j] * math.comb(v, nu[j])
+        t = w * (0.5 * (x @ B @ x)) ** h
+        re.append(t.real)
+        im.append(t.imag)
+    scale = 2.0 ** n * math.factorial(h)
+    return complex(math.fsum(re) / scale, math.fsum(im) / scale)
 
 
 def log_norm(r) -> float:

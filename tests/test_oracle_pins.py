@@ -298,3 +298,53 @@ def test_prob_methods_agree_tiny_workload(orc):
     b = orc.prob(U, r, pats, method="pm")
     assert np.all(np.abs(a["haf"] - b["haf"]) <= 1e-15 * np.abs(b["haf"]) + 1e-300)
     assert np.all(np.abs(a["p"] - b["p"]) <= 1e-14 * b["p"])
+
+
+# --- repeated-row Hafnian (collision path; Kan's moment identity) ---------------
+
+def expand(B, reps):
+    idx = np.repeat(np.arange(len(reps)), reps)
+    return np.asarray(B)[np.ix_(idx, idx)]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_haf_repeated_brute_force(orc, seed):
+    """haf_repeated equals the perfect-matching sum of the explicitly repeated
+    matrix (brute force, Eq. HafMatch) for random complex symmetric B and
+    random multiplicities with n <= 10."""
+    rng = np.random.default_rng(100 + seed)
+    mp = int(rng.integers(1, 5))
+    reps = [int(v) for v in rng.integers(0, 4, size=mp)]
+    if sum(reps) % 2:
+        reps[0] += 1
+    if sum(reps) > 10:
+        reps = [min(v, 2) for v in reps]
+        if sum(reps) % 2:
+            reps[0] += 1
+    B = rand_sym(mp, 200 + seed)
+    ref = orc.haf_pm(expand(B, reps))
+    got = orc.haf_repeated(B, reps)
+    assert abs(got - ref) <= 1e-12 * max(1.0, abs(ref)), (reps, got, ref)
+
+
+@pytest.mark.parametrize("k", range(1, 7))
+def test_haf_repeated_single_mode(orc, k):
+    """One mode repeated 2k times: the repeated matrix is b J_2k, so
+    Haf = b^k (2k-1)!!."""
+    b = 0.7 - 0.4j
+    got = orc.haf_repeated(np.array([[b]]), [2 * k])
+    ref = b ** k * dfact(2 * k - 1)
+    assert abs(got - ref) <= 1e-13 * abs(ref)
+
+
+def test_haf_repeated_collision_free_and_edges(orc):
+    """All multiplicities 1: the plain Hafnian (double-double subset sum); odd n
+    gives 0; a mode with multiplicity 0 is the same as leaving it out."""
+    B = rand_sym(8, 31)
+    ref = orc.haf_subset(B)
+    assert abs(orc.haf_repeated(B, [1] * 8) - ref) <= 1e-12 * abs(ref)
+    assert orc.haf_repeated(B[:3, :3], [1, 1, 1]) == 0
+    B4 = rand_sym(4, 32)
+    a = orc.haf_repeated(B4, [2, 0, 1, 1])
+    b = orc.haf_repeated(B4[np.ix_([0, 2, 3], [0, 2, 3])], [2, 1, 1])
+    assert abs(a - b) <= 1e-14 * abs(b)
