@@ -232,9 +232,15 @@ int64_t binom64(int a, int b) {
 // of one matrix take consecutive partial slots (pattern order), and the
 // schedule lists the most expensive items first (longest-first list
 // scheduling) by bucketing on (s, rounds), whose cost is rounds * (2s)^3.
-void Planner::init(const int* n, int batch, int precision, int warp_bytes, const int* rounds_for_n) {
+void Planner::init(const int* n, int batch, int precision, int warp_bytes, const int* rounds_for_n,
+                   const int* rep_half) {
   n_ = n;
+  rep_half_ = rep_half;
   batch_ = batch;
+  rep_total_ = 0;
+  if (rep_half)
+    for (int b = 0; b < batch; ++b)
+      rep_total_ += (rep_half[b] + kRepTermsPerItem - 1) / kRepTermsPerItem;
   const int cb = complex_bytes(precision);
   int maxn = 0;
   for (int b = 0; b < batch; ++b) maxn = std::max(maxn, n[b]);
@@ -243,7 +249,8 @@ void Planner::init(const int* n, int batch, int precision, int warp_bytes, const
     tmpl_[v].clear();
     npat_[v] = 0;
   }
-  for (int b = 0; b < batch; ++b) npat_[n[b]]++;
+  for (int b = 0; b < batch; ++b)
+    if (!rep_half || rep_half[b] == 0) npat_[n[b]]++;
   std::fill(bucket_, bucket_ + kKeys, 0);
   total_ = 0;
   for (int v = 2; v <= kMaxN; v += 2) {
@@ -282,16 +289,27 @@ void Planner::init(const int* n, int batch, int precision, int warp_bytes, const
   }
 }
 
-void Planner::fill(PatDesc* pats, WorkItem* items) {
+void Planner::fill(PatDesc* pats, WorkItem* items, WorkItem* rep_items) {
   int64_t next[kKeys];
   std::copy(start_, start_ + kKeys, next);
-  int q = 0;
+  int q = 0, rq = 0;
   for (int b = 0; b < batch_; ++b) {
     PatDesc& d = pats[b];
     const int v = n_[b];
     d.n = v;
     d.item_begin = q;
-    if (v >= 2 && !(v & 1)) {
+    if (rep_half_ && rep_half_[b] > 0) {
+      for (int t0 = 0; t0 < rep_half_[b]; t0 += kRepTermsPerItem) {
+        WorkItem& w = rep_items[rq++];
+        w.pat = b;
+        w.s = 0;
+        w.rank0 = t0;
+        w.count = std::min(kRepTermsPerItem, rep_half_[b] - t0);
+        w.part = q++;
+        w.stride = 1;
+        w.pad[0] = w.pad[1] = 0;
+      }
+    } else if (v >= 2 && !(v & 1)) {
       for (const ItemTemplate& t : tmpl_[v]) {
         WorkItem& w = items[next[t.key]++];
         w.pat = b;
@@ -342,12 +360,12 @@ static uint64_t splitmix64(uint64_t& x) {
 // Probe items hold one round of lane groups each (G subsets of one size), so
 // that the samples of one matrix run in parallel warps.
 static void plan_pairing(const int* n, int batch, int precision, int warp_bytes, int stage_h,
-                         PairingPlan* pp) {
+                         const int* skip, PairingPlan* pp) {
   const int cb = complex_bytes(precision);
   int base[kMaxN + 1];
   for (int v = 0; v <= kMaxN; ++v) base[v] = -1;
   for (int b = 0; b < batch; ++b)
-    if (n[b] >= kPairingMinN && !(n[b] & 1)) pp->sel.push_back(b);
+    if (n[b] >= kPairingMinN && !(n[b] & 1) && !(skip && skip[b])) pp->sel.push_back(b);
   if (pp->sel.empty()) return;
   for (int b : pp->sel) {
     const int v = n[b];
@@ -396,6 +414,63 @@ static void plan_pairing(const int* n, int batch, int precision, int warp_bytes,
   }
 }
 
+// ------------------------------------------------------------------------
+// route choice: subset sum or repeated-row terms
+// ------------------------------------------------------------------------
+// FP64 operations of the subset sum for order n (products and traces of every
+// subset, the schedule's product count per h).
+static double subset_cost(int n) {
+  static const int kProducts[kMaxH + 1] = {0, 0, 0, 1, 1, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4, 5, 6};
+  const int h = n / 2;
+  double c = 0.0;
+  for (int s = 1; s <= h; ++s) {
+    const double N = 2.0 * s;
+    c += (double)binom64(h, s) * (kProducts[h] + 1) * 2.0 * N * N * (N + 1);
+  }
+  return c;
+}
+
+// Terms (ceil(T / 2)) that the repeated-row route sums for index list x of
+// length n, or 0 when the subset sum is the cheaper route: the route needs a
+// repeated mode, at most kRepMaxDistinct distinct modes and T <= 2^30, and its
+// terms (about d^2 + 3d + 60 FP64 operations each) must cost under a quarter
+// of the subset sum (the margin covers its lower efficiency).
+static int rep_half_terms(const int* x, int n) {
+  if (n < 4 || (n & 1)) return 0;
+  // T >= 2^d, so beyond d_max(n) the route can never win: stop scanning there
+  // (collision-free lists, the common case, stop after about n/2 entries)
+  static const std::vector<int> d_max = [] {  // thread-safe one-time initialisation
+    std::vector<int> t(kMaxN + 1, 0);
+    for (int v = 4; v <= kMaxN; v += 2) {
+      const double pc = subset_cost(v);
+      for (int d = 1; d <= kRepMaxDistinct; ++d)
+        if (4.0 * std::ldexp(1.0, d - 1) * (double)(d * d + 3 * d + 60) < pc) t[v] = d;
+    }
+    return t;
+  }();
+  const int dmx = d_max[n];
+  int vals[kMaxN], cnt[kMaxN], d = 0;
+  for (int i = 0; i < n; ++i) {
+    int j = 0;
+    while (j < d && vals[j] != x[i]) ++j;
+    if (j == d) {
+      if (d == dmx) return 0;
+      vals[d] = x[i];
+      cnt[d++] = 0;
+    }
+    cnt[j]++;
+  }
+  if (d == n) return 0;
+  int64_t T = 1;
+  for (int j = 0; j < d; ++j) {
+    T *= cnt[j] + 1;
+    if (T > ((int64_t)1 << 30)) return 0;
+  }
+  const int64_t half = (T + 1) / 2;
+  const double rep_cost = (double)half * (double)(d * d + 3 * d + 60);
+  return (4.0 * rep_cost < subset_cost(n)) ? (int)half : 0;
+}
+
 static cudaEvent_t g_time_start = nullptr, g_time_stop = nullptr;
 
 int device_sm_count() {
@@ -431,8 +506,21 @@ int run_batch(const BatchArgs& a) {
   if (!shape_fits(a.precision, cfg.warp_bytes, maxn))
     return fail(GBS_EINVAL, "warp_bytes %d too small for n = %d", cfg.warp_bytes, maxn);
 
+  // FP64 index lists held on the host: matrices with repeated modes whose
+  // repeated-row terms are cheaper than the subset sum take that route
+  std::vector<int> rep_half;
+  int n_rep_pat = 0;
+  if (a.mode == BatchArgs::PROB && a.precision == GBS_FP64 && a.idx && !is_device_ptr(a.idx)) {
+    rep_half.assign(batch, 0);
+    for (int b = 0; b < batch; ++b) {
+      rep_half[b] = rep_half_terms(a.idx + a.offs[b], a.n[b]);
+      n_rep_pat += rep_half[b] > 0;
+    }
+  }
+  const int* rep_ptr = n_rep_pat ? rep_half.data() : nullptr;
+
   Planner plan;
-  plan.init(a.n, batch, a.precision, cfg.warp_bytes, rounds_for_n);
+  plan.init(a.n, batch, a.precision, cfg.warp_bytes, rounds_for_n, rep_ptr);
   if (!a.cfg_override) {
     // A small batch gets smaller work items (fewer rounds each), so that there
     // are a few items per resident warp to balance the load over all SMs.
@@ -445,11 +533,13 @@ int run_batch(const BatchArgs& a) {
           shrunk = true;
         }
       if (!shrunk) break;
-      plan.init(a.n, batch, a.precision, cfg.warp_bytes, rounds_for_n);
+      plan.init(a.n, batch, a.precision, cfg.warp_bytes, rounds_for_n, rep_ptr);
     }
   }
   const int64_t n_items = plan.total();
-  if (n_items > ((int64_t)1 << 30)) return fail(GBS_ENOMEM, "too many work items (%lld)", (long long)n_items);
+  const int64_t n_rep = plan.rep_total();
+  if (n_items + n_rep > ((int64_t)1 << 30))
+    return fail(GBS_ENOMEM, "too many work items (%lld)", (long long)(n_items + n_rep));
 
   // host-side checks and sizes of the inputs to stage
   const bool src_dev = (a.mode == BatchArgs::HAFNIAN) ? is_device_ptr(a.src) : true;
@@ -487,13 +577,14 @@ int run_batch(const BatchArgs& a) {
   int64_t pt_elems = 0;
   if (use_pt)
     for (int b = 0; b < batch; ++b) {
+      if (rep_ptr && rep_ptr[b]) continue;  // repeated-row route: no subsets
       const int64_t q = pair_terms_elems(a.n[b]);
       if (q > 0 && 16 * (pt_elems + q) <= kPairTermBudget) pt_elems += q;
     }
   const size_t ptoff_b = (use_pt && pt_elems > 0) ? al(sizeof(int64_t) * batch) : 0;
   // pairing probe of the largest matrices
   PairingPlan pp;
-  if (n_items > 0) plan_pairing(a.n, batch, a.precision, cfg.warp_bytes, maxn / 2, &pp);
+  if (n_items > 0) plan_pairing(a.n, batch, a.precision, cfg.warp_bytes, maxn / 2, rep_ptr, &pp);
   const int n_sel = (int)pp.sel.size();
   const int n_probe = (int)pp.pats.size();
   const int n_pitems = (int)pp.items.size();
@@ -506,11 +597,13 @@ int run_batch(const BatchArgs& a) {
   const size_t probe_up_b = perm_b + ppats_b + pitems_b + pperm_b + mperm_b + selpat_b;
   // two-stage finalisation when some matrix has more than kChunkItems items
   std::vector<int> chunk_off, chunk_pat;
-  if (plan.max_items_per_pattern() > kChunkItems) {
+  int max_items = 0;
+  for (int b = 0; b < batch; ++b) max_items = std::max(max_items, plan.items_for(b));
+  if (max_items > kChunkItems) {
     chunk_off.resize(batch + 1);
     for (int b = 0; b < batch; ++b) {
       chunk_off[b] = (int)chunk_pat.size();
-      const int cnt = plan.items_of(a.n[b]);
+      const int cnt = plan.items_for(b);
       for (int c = 0; c * kChunkItems < cnt; ++c) chunk_pat.push_back(b);
     }
     chunk_off[batch] = (int)chunk_pat.size();
@@ -518,9 +611,10 @@ int run_batch(const BatchArgs& a) {
   const int n_chunks = (int)chunk_pat.size();
   const size_t choff_b = n_chunks ? al(sizeof(int) * (batch + 1)) : 0;
   const size_t chpat_b = n_chunks ? al(sizeof(int) * n_chunks) : 0;
-  const size_t up_b = pats_b + items_b + idx_b + src_b + ptoff_b + probe_up_b + choff_b + chpat_b;
+  const size_t rep_b = n_rep ? al(sizeof(WorkItem) * n_rep) : 0;  // repeated-row items
+  const size_t up_b = pats_b + items_b + idx_b + src_b + ptoff_b + probe_up_b + choff_b + chpat_b + rep_b;
   // device-only block: parts | counter | status | output staging
-  const size_t parts_b = al(sizeof(Partial) * std::max<int64_t>(n_items, 1));
+  const size_t parts_b = al(sizeof(Partial) * std::max<int64_t>(n_items + n_rep, 1));
   const size_t ctr_b = 256;
   const size_t status_b = al(sizeof(int) * batch);
   const bool out_host = (a.out0 && !is_device_ptr(a.out0)) || (a.out1 && !is_device_ptr(a.out1)) ||
@@ -541,7 +635,8 @@ int run_batch(const BatchArgs& a) {
   if (rc) return rc;
   unsigned char* hs = (unsigned char*)host_stage;
   PatDesc* h_pats = (PatDesc*)hs;
-  plan.fill(h_pats, (WorkItem*)(hs + pats_b));
+  const size_t rep_at = up_b - rep_b;
+  plan.fill(h_pats, (WorkItem*)(hs + pats_b), n_rep ? (WorkItem*)(hs + rep_at) : nullptr);
   for (int b = 0; b < batch; ++b) {
     PatDesc& d = h_pats[b];
     if (a.mode == BatchArgs::HAFNIAN) {
@@ -560,7 +655,7 @@ int run_batch(const BatchArgs& a) {
     int64_t* h_ptoff = (int64_t*)(hs + pats_b + items_b + idx_b + src_b);
     int64_t off = 0;
     for (int b = 0; b < batch; ++b) {
-      const int64_t q = pair_terms_elems(a.n[b]);
+      const int64_t q = (rep_ptr && rep_ptr[b]) ? 0 : pair_terms_elems(a.n[b]);
       if (q > 0 && 16 * (off + q) <= kPairTermBudget) {
         h_ptoff[b] = off;
         off += q;
@@ -645,7 +740,7 @@ int run_batch(const BatchArgs& a) {
       e = launch_to_float(d_src, d_a32, 2 * src_elems, st);
       if (e != cudaSuccess) { ret = cuda_fail(e, "float copy"); break; }
     }
-    if (n_items > 0) {
+    if (n_items > 0 || n_rep > 0) {
       L.src = (a.mode == BatchArgs::HAFNIAN) ? d_src : a.B;
       L.src32 = (a.precision == GBS_MIXED) ? ((a.mode == BatchArgs::HAFNIAN) ? d_a32 : a.B32) : nullptr;
       L.idx = (a.mode == BatchArgs::PROB) ? d_idx : nullptr;
@@ -710,11 +805,27 @@ int run_batch(const BatchArgs& a) {
       }
       e = launch_pair_terms(L, st);
       if (e != cudaSuccess) { ret = cuda_fail(e, "pair-term kernel launch"); break; }
-      e = launch_haf_subsets(L, a.precision, blocks, cfg.warps_per_block, st);
-      if (e != cudaSuccess) { ret = cuda_fail(e, "subset kernel launch"); break; }
+      if (n_items > 0) {
+        e = launch_haf_subsets(L, a.precision, blocks, cfg.warps_per_block, st);
+        if (e != cudaSuccess) { ret = cuda_fail(e, "subset kernel launch"); break; }
+      }
+      if (n_rep > 0) {
+        RepLaunch R;
+        R.B = a.B;
+        R.idx = d_idx;
+        R.pats = d_pats;
+        R.items = (const WorkItem*)(dm + rep_at);
+        R.n_items = (int)n_rep;
+        R.m_bound = L.m_bound;
+        R.counter = d_ctr + 48;
+        R.status = d_status;
+        R.parts = d_parts;
+        e = launch_haf_repeated(R, st);
+        if (e != cudaSuccess) { ret = cuda_fail(e, "repeated-row kernel launch"); break; }
+      }
       if (timed) cudaEventRecord(g_time_stop, st);
     }
-    if (n_chunks && n_items > 0) {
+    if (n_chunks && n_items + n_rep > 0) {
       ChunkLaunch C;
       C.pats = d_pats;
       C.parts = d_parts;
@@ -729,7 +840,7 @@ int run_batch(const BatchArgs& a) {
     memset(&F, 0, sizeof(F));
     F.pats = d_pats;
     F.parts = d_parts;
-    if (n_chunks && n_items > 0) {
+    if (n_chunks && n_items + n_rep > 0) {
       F.chunk_parts = d_chparts;
       F.chunk_off = d_choff;
     }

@@ -77,23 +77,29 @@ struct ItemTemplate;
 // item ranges and the items (in schedule order) into caller memory.
 class Planner {
  public:
-  void init(const int* n, int batch, int precision, int warp_bytes, const int* rounds_for_n);
-  void fill(PatDesc* pats, WorkItem* items);
+  // rep_half (may be null): per matrix, the number of repeated-row terms it
+  // sums (ceil(T / 2)), or 0 for the subset-sum route; those matrices get
+  // repeated-row items (kRepTermsPerItem terms each) instead of subset items.
+  void init(const int* n, int batch, int precision, int warp_bytes, const int* rounds_for_n,
+            const int* rep_half = nullptr);
+  void fill(PatDesc* pats, WorkItem* items, WorkItem* rep_items = nullptr);
+  int64_t rep_total() const { return rep_total_; }
   int64_t total() const { return total_; }
   // work items of one matrix of order v (0 for odd v or v < 2)
-  int items_of(int v) const { return (v >= 2 && !(v & 1)) ? (int)tmpl_[v].size() : 0; }
-  int max_items_per_pattern() const {
-    int m = 0;
-    for (int v = 2; v <= kMaxN; v += 2)
-      if (npat_[v]) m = std::max(m, (int)tmpl_[v].size());
-    return m;
+  // work items (= partial slots) of matrix b
+  int items_for(int b) const {
+    if (rep_half_ && rep_half_[b] > 0) return (rep_half_[b] + kRepTermsPerItem - 1) / kRepTermsPerItem;
+    const int v = n_[b];
+    return (v >= 2 && !(v & 1)) ? (int)tmpl_[v].size() : 0;
   }
 
  private:
   static constexpr int kKeys = (kMaxN / 2 + 1) * 65;
   const int* n_ = nullptr;
+  const int* rep_half_ = nullptr;
   int batch_ = 0;
   int64_t total_ = 0;
+  int64_t rep_total_ = 0;
   int npat_[kMaxN + 1];
   std::vector<ItemTemplate> tmpl_[kMaxN + 1];
   int64_t bucket_[kKeys];

@@ -165,7 +165,32 @@ struct PairingSelect {
   int* main_perm_off;         // written: the chosen ordering of each probed matrix
 };
 
+// Repeated-row route (index-list matrices with collisions, FP64): with
+// distinct modes v_1..v_d of multiplicities c_j (sum c_j = n, h = n/2),
+//   Haf(B_x) = (1 / (2^n h!)) sum_{0 <= nu_j <= c_j}
+//              prod_j (-1)^nu_j C(c_j, nu_j) (x^T B_v x / 2)^h,  x_j = c_j - 2 nu_j,
+// B_v the d x d submatrix of B on the distinct modes (the moment-extraction
+// identity of Kan, 2008). Terms are numbered in mixed radix (digit j = nu_j,
+// radix c_j + 1); term t and T - 1 - t (nu and c - nu) are equal, so only
+// t < ceil(T / 2) is summed, T = prod (c_j + 1). A work item is a run
+// [rank0, rank0 + count) of term numbers of one matrix; its partial sum goes to
+// parts[part] like a subset-sum item's.
+constexpr int kRepMaxDistinct = 16;
+constexpr int kRepTermsPerItem = 1024;
+struct RepLaunch {
+  const double* B;         // interleaved complex, m x m, row stride ld (the PatDesc's)
+  const int* idx;
+  const PatDesc* pats;
+  const WorkItem* items;
+  int n_items;
+  int m_bound;             // index lists must be < m_bound (0 = no check)
+  int* counter;            // work-queue head, zero before launch
+  int* status;             // per-pattern flag, set to 1 on an out-of-range index
+  Partial* parts;
+};
+
 // Defined in haf_subsets.cu
+cudaError_t launch_haf_repeated(const RepLaunch& R, cudaStream_t st);
 cudaError_t launch_haf_subsets(const HafLaunch& L, int precision, int blocks, int warps_per_block,
                                cudaStream_t st);
 cudaError_t launch_finalize(const FinalizeLaunch& F, cudaStream_t st);

@@ -793,7 +793,178 @@ __global__ void pairing_select_kernel(const PairingSelect S) {
   if (lane == 0) S.main_perm_off[S.sel_pat[k]] = S.probe_perm_off[k * S.n_cand + (c < S.n_cand ? c : 0)];
 }
 
+// ---- repeated-row route (Kan's moment identity; see RepLaunch) ----------
+
+struct RepWarp {
+  double2 B[kRepMaxDistinct * kRepMaxDistinct];  // B_v, row stride kRepMaxDistinct
+  double x[kRepMaxDistinct][32];                  // x_j of each lane's current term (column = lane)
+  int c[kRepMaxDistinct];                         // multiplicities c_j
+  int mode[kRepMaxDistinct];                      // distinct modes v_j
+};
+
+// Warp sum of compensated accumulators (fixed butterfly, double-double) into
+// one item partial.
+__device__ __forceinline__ void store_warp_partial(Comp<double> re, Comp<double> im, double kap, int lane,
+                                                   Partial* out) {
+  const unsigned FULL = 0xffffffffu;
+  double rh = re.hi, rl = re.lo, ih = im.hi, il = im.lo;
+  for (int off = 16; off > 0; off >>= 1) {
+    const double orh = __shfl_xor_sync(FULL, rh, off), orl = __shfl_xor_sync(FULL, rl, off);
+    const double oih = __shfl_xor_sync(FULL, ih, off), oil = __shfl_xor_sync(FULL, il, off);
+    kap += __shfl_xor_sync(FULL, kap, off);
+    dd_add(rh, rl, orh, orl);
+    dd_add(ih, il, oih, oil);
+  }
+  if (lane == 0) {
+    Partial pr;
+    pr.re_hi = rh;
+    pr.re_lo = rl;
+    pr.im_hi = ih;
+    pr.im_lo = il;
+    pr.kappa = kap;
+    pr.pad[0] = pr.pad[1] = pr.pad[2] = 0.0;
+    *out = pr;
+  }
+}
+
+// Terms t0 + q, q = lane, lane + 32, ... < count, for D distinct modes: digits
+// nu_j of t (mixed radix c_j + 1, j = 0 fastest), x_j = c_j - 2 nu_j (kept in
+// the lane's own column of W.x), the weight prod (-1)^nu_j C(c_j, nu_j),
+// Q = x^T B_v x / 2 evaluated as sum_j x_j (B_jj x_j / 2 + sum_{k>j} B_jk x_k)
+// (x integer, so every product with x is one rounding), Q^h by squaring, and
+// the term times 2 / (2^n h!) (1 / (2^n h!) for the middle term
+// t = (T - 1) / 2, which is its own mirror).
+__device__ __forceinline__ void rep_terms(RepWarp& W, const int (*binom)[kMaxN + 1], int D, int h, int t0,
+                                          int count, int T, double scale, int lane, Comp<double>& re,
+                                          Comp<double>& im, double& kap) {
+  for (int q = lane; q < count; q += 32) {
+    const int t = t0 + q;
+    int rem = t;
+    double w = 1.0;
+    for (int j = 0; j < D; ++j) {
+      const int cj = W.c[j];
+      const int nu = rem % (cj + 1);
+      rem /= (cj + 1);
+      W.x[j][lane] = (double)(cj - 2 * nu);
+      const double bw = (double)binom[cj][nu];
+      w *= (nu & 1) ? -bw : bw;
+    }
+    double qr = 0.0, qi = 0.0;
+    for (int j = 0; j < D; ++j) {
+      const double xj = W.x[j][lane];
+      const double2 bjj = W.B[j * kRepMaxDistinct + j];
+      const double hx = 0.5 * xj;
+      double sr = bjj.x * hx, si = bjj.y * hx;
+      for (int k = j + 1; k < D; ++k) {
+        const double2 b = W.B[j * kRepMaxDistinct + k];
+        const double xk = W.x[k][lane];
+        sr = fma(b.x, xk, sr);
+        si = fma(b.y, xk, si);
+      }
+      qr = fma(xj, sr, qr);
+      qi = fma(xj, si, qi);
+    }
+    double pr = 1.0, pi = 0.0, br = qr, bi = qi;
+    for (int e = h; e > 0; e >>= 1) {
+      if (e & 1) {
+        const double tr = fma(pr, br, -pi * bi);
+        pi = fma(pr, bi, pi * br);
+        pr = tr;
+      }
+      if (e > 1) {
+        const double tr = fma(br, br, -bi * bi);
+        bi = 2.0 * br * bi;
+        br = tr;
+      }
+    }
+    const double f = w * ((2 * t + 1 == T) ? scale : 2.0 * scale);
+    const double vr = f * pr, vi = f * pi;
+    comp_add<double>(re, vr);
+    comp_add<double>(im, vi);
+    kap += fabs(vr) + fabs(vi);
+  }
+}
+
+// Persistent warps over repeated-row work items. Per item: the matrix's index
+// list (lane i holds x_i), its distinct modes and multiplicities by
+// __match_any_sync (order of first occurrence), B_v gathered into the warp's
+// shared slot, then the item's terms.
+__global__ void __launch_bounds__(128) haf_repeated_kernel(const RepLaunch R) {
+  __shared__ RepWarp ws[4];
+  __shared__ int binom[kMaxN + 1][kMaxN + 1];
+  if (threadIdx.x == 0)
+    for (int a = 0; a <= kMaxN; ++a)
+      for (int b = 0; b <= kMaxN; ++b)
+        binom[a][b] = (b == 0) ? 1 : (a == 0 ? 0 : binom[a - 1][b - 1] + binom[a - 1][b]);
+  __syncthreads();
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  RepWarp& W = ws[threadIdx.x >> 5];
+  const double2* src2 = reinterpret_cast<const double2*>(R.B);
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(R.counter, 1);
+    it = __shfl_sync(FULL, it, 0);
+    if (it >= R.n_items) break;
+    const WorkItem w = R.items[it];
+    const PatDesc d = R.pats[w.pat];
+    const int n = d.n, h = n >> 1;
+    int v = -1 - lane;  // lanes past n: values no index takes
+    bool bad = false;
+    if (lane < n) {
+      v = (d.idx_off >= 0) ? R.idx[d.idx_off + lane] : lane;
+      if (R.m_bound > 0 && (v < 0 || v >= R.m_bound)) bad = true;
+    }
+    const unsigned same = __match_any_sync(FULL, v);
+    const bool leader = (lane < n) && ((__ffs(same) - 1) == lane);
+    const unsigned leaders = __ballot_sync(FULL, leader);
+    const int D = __popc(leaders);
+    if (__any_sync(FULL, bad) || D > kRepMaxDistinct) {
+      // an out-of-range index (NaN output) or a matrix this route was not
+      // planned for: flag it, leave a zero partial, read nothing
+      if (lane == 0) R.status[w.pat] = 1;
+      const Comp<double> z = {0.0, 0.0};
+      store_warp_partial(z, z, 0.0, lane, R.parts + w.part);
+      __syncwarp();
+      continue;
+    }
+    if (leader) {
+      const int j = __popc(leaders & ((1u << lane) - 1u));
+      W.mode[j] = v;
+      W.c[j] = __popc(same);
+    }
+    __syncwarp();
+    for (int e = lane; e < D * D; e += 32) {
+      const int j = e / D, k = e - j * D;
+      W.B[j * kRepMaxDistinct + k] = __ldg(src2 + d.src_off + (int64_t)W.mode[j] * d.ld + W.mode[k]);
+    }
+    __syncwarp();
+    int T = 1;
+    for (int j = 0; j < D; ++j) T *= W.c[j] + 1;
+    double hf = 1.0;
+    for (int i = 2; i <= h; ++i) hf *= (double)i;  // exact: h! < 2^53 for h <= 16
+    const double scale = ldexp(1.0 / hf, -n);
+    Comp<double> re = {0.0, 0.0}, im = {0.0, 0.0};
+    double kap = 0.0;
+    rep_terms(W, binom, D, h, w.rank0, w.count, T, scale, lane, re, im, kap);
+    store_warp_partial(re, im, kap, lane, R.parts + w.part);
+    __syncwarp();
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_haf_repeated(const RepLaunch& R, cudaStream_t st) {
+  if (R.n_items <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int blocks = (R.n_items + 3) / 4;
+  const int cap = (sms > 0 ? sms : 1) * 8;
+  if (blocks > cap) blocks = cap;
+  haf_repeated_kernel<<<blocks, 128, 0, st>>>(R);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_pairing_select(const PairingSelect& S, cudaStream_t st) {
   if (S.n_sel <= 0 || S.n_cand > 32) return S.n_sel <= 0 ? cudaSuccess : cudaErrorInvalidValue;

@@ -321,6 +321,68 @@ def test_prob_heavy_collisions(gbs, orc):
     assert np.all(rel(p, ref["p"]) <= FP64_TOL)
 
 
+def bunched_patterns(m, n_values, per_n, seed):
+    """Multisets of n modes drawn with replacement from m: many photons per mode."""
+    rng = np.random.default_rng(seed)
+    return [np.sort(rng.choice(m, n, replace=True)).astype(np.int32) for n in n_values for _ in range(per_n)]
+
+
+def test_prob_repeated_row_route(gbs, orc):
+    """Host index lists with many repeated modes take the repeated-row route
+    (terms of the moment-extraction identity) when it is cheaper than the
+    subset sum; device index lists and explicit matrices take the subset sum.
+    All three agree with the double-double oracle within 1e-10."""
+    m = 8
+    U = W.haar_unitary(m, 5)
+    r = np.full(m, 1.0)
+    K = kernel_for(gbs, U, r)
+    pats = bunched_patterns(m, (8, 12, 16, 20), 3, 71) + bunched_patterns(m, (24, 28), 1, 72)
+    ref = orc.prob(U, r, pats)
+    p_h, lp_h, hf_h, er_h = run_prob(gbs, K, pats, 0, host=True)
+    p_d, lp_d, hf_d, er_d = run_prob(gbs, K, pats, 0)
+    assert np.all(rel(hf_h, ref["haf"]) <= FP64_TOL), rel(hf_h, ref["haf"])
+    assert np.all(rel(p_h, ref["p"]) <= FP64_TOL)
+    assert np.all(rel(hf_d, ref["haf"]) <= FP64_TOL), rel(hf_d, ref["haf"])
+    assert np.all(np.abs(lp_h - lp_d) <= 1e-9)
+    B = torch.zeros(2 * m * m, dtype=torch.float64, device="cuda")
+    K.copy_B(B)
+    Bc = B.cpu().numpy().view(np.complex128).reshape(m, m)
+    flat, n, offs = gbs.pack_matrices([Bc[np.ix_(x, x)] for x in pats])
+    hm = np.zeros(2 * len(pats))
+    gbs.hafnian_batch(flat, n, offs, gbs.FP64, haf_out=hm)
+    assert np.all(rel(hm[0::2] + 1j * hm[1::2], ref["haf"]) <= FP64_TOL)
+
+
+def test_repeated_row_route_extreme_bunching(gbs, orc):
+    """32 photons in 2 modes (289 terms): the repeated-row route against the
+    oracle's repeated-row formula, and much faster than the subset sum that a
+    device index list takes for the same pattern (2^16 subsets of order <= 32)."""
+    import time
+
+    m = 6
+    U = W.haar_unitary(m, 8)
+    r = np.full(m, 0.9)
+    K = kernel_for(gbs, U, r)
+    x = np.array([1] * 16 + [4] * 16, np.int32)
+    Bdd = orc.build_B_dd(U, np.tanh(r))
+    B = (Bdd[..., 0] + Bdd[..., 1]) + 1j * (Bdd[..., 2] + Bdd[..., 3])
+    ref = orc.haf_repeated(B[np.ix_([1, 4], [1, 4])], [16, 16])
+    _, _, hf_h, _ = run_prob(gbs, K, [x], 0, host=True)
+    _, _, hf_d, _ = run_prob(gbs, K, [x], 0)
+    assert rel(hf_h, np.array([ref]))[0] <= FP64_TOL, (hf_h, ref)
+    assert rel(hf_d, np.array([ref]))[0] <= FP64_TOL, (hf_d, ref)
+
+    def best(host, reps=3):
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            run_prob(gbs, K, [x], 0, host=host)
+            ts.append(time.perf_counter() - t0)
+        return min(ts)
+
+    assert best(True) * 3 < best(False)
+
+
 def test_prob_mixed_bound_large_golden(gbs):
     """The mixed path's stated per-result bound holds on the n = 28, 30 instances."""
     import json
