@@ -391,9 +391,55 @@ def extras(gbs, torch):
                          "subset_terms_per_s": sum(2 ** (len(p) // 2) for p in pats) / (k64 * 1e-3),
                          "achieved_tflops": fl / (k64 * 1e-3) / 1e12, "frac_of_peak": fl / (k64 * 1e-3) / 1e12 / peak,
                          "max_err_est": float(e64.max())}
+    out["bunched_m8"] = bunched(gbs, torch)
     out["serving"] = serving(gbs, torch)
     out["sampler"] = sampler(gbs)
     return out
+
+
+def bunched(gbs, torch, reps=3):
+    """M = 8, r = 1, 512 patterns of 24 photons drawn with replacement: host
+    index lists take the repeated-row route (cost prod (c_j + 1)), device index
+    lists the subset sum (cost 2^12 subsets); wall time per batch, both through
+    gbs_prob_batch, their largest relative deviation and each route's largest
+    error estimate (the subset sum cancels far more on bunched patterns)."""
+    U, r, pats = W.workload("bunched_m8")
+    K = gbs.build_kernel(U, r)
+    idx, n, offs = gbs.pack_patterns(pats)
+    b = len(pats)
+    hh = np.zeros(2 * b)
+    eh = np.zeros(b)
+    d_idx = torch.from_numpy(idx).cuda()
+    hd = torch.zeros(2 * b, dtype=torch.float64, device="cuda")
+    ed = torch.zeros(b, dtype=torch.float64, device="cuda")
+
+    def rep_route():
+        gbs.prob_batch(K, idx, n, offs, gbs.FP64, haf_out=hh, err_out=eh)
+
+    def subset_route():
+        gbs.prob_batch(K, d_idx, n, offs, gbs.FP64, haf_out=hd, err_out=ed)
+        torch.cuda.synchronize()
+
+    gbs.autotune(24, gbs.FP64)
+    ts = {}
+    for name, fn in (("repeated_row", rep_route), ("subset_sum", subset_route)):
+        fn()
+        t = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            t.append(time.perf_counter() - t0)
+        ts[name] = float(np.median(t))
+    a = hh[0::2] + 1j * hh[1::2]
+    h = hd.cpu().numpy()
+    c = h[0::2] + 1j * h[1::2]
+    return {"workload": "M=8 Haar U seed 5, r=1.0, 512 patterns of n=24 drawn with replacement, FP64",
+            "repeated_row_probs_per_s": b / ts["repeated_row"], "repeated_row_ms": 1e3 * ts["repeated_row"],
+            "subset_sum_probs_per_s": b / ts["subset_sum"], "subset_sum_ms": 1e3 * ts["subset_sum"],
+            "speedup": ts["subset_sum"] / ts["repeated_row"],
+            "max_rel_dev_between_routes": float(np.max(np.abs(a - c) / np.abs(c))),
+            "repeated_row_max_err_est": float(eh.max()),
+            "subset_sum_max_err_est": float(ed.cpu().numpy().max())}
 
 
 def sampler(gbs):

@@ -107,7 +107,7 @@ def poisson_arrivals(rate_hz: float, count: int, seed: int) -> np.ndarray:
     return np.cumsum(rng.exponential(1.0 / rate_hz, size=count))
 
 
-# The five workloads the library is measured and checked on. Sizes follow the
+# The workloads the library is measured and checked on. Sizes follow the
 # paper's setting of Haar-random interferometers with every mode squeezed
 # (Sec. 2); the paper itself ran m = n^2 with identical r (Sec. 3.5).
 WORKLOADS = {
@@ -118,6 +118,9 @@ WORKLOADS = {
     "serving_m256": dict(m=256, seed=3, r=("const", 0.88), n_values=tuple(range(12, 27)),
                          rate_hz=2000.0),
     "large_m900": dict(m=900, seed=4, r=("const", 1.0), n28=64, n30=16),
+    # photons bunched into few modes (a small interferometer, many photons):
+    # the regime of the repeated-row route
+    "bunched_m8": dict(m=8, seed=5, r=("const", 1.0), n=24, count=512),
 }
 
 
@@ -142,6 +145,9 @@ def workload(name: str):
     elif name == "large_m900":
         pats = list(collision_free_patterns(m, 28, w["n28"], seed + 100))
         pats += list(collision_free_patterns(m, 30, w["n30"], seed + 200))
+    elif name == "bunched_m8":
+        rng = np.random.default_rng(seed + 100)
+        pats = [np.sort(rng.choice(m, w["n"], replace=True)).astype(np.int32) for _ in range(w["count"])]
     else:
         raise KeyError(name)
     return U, r, pats
