@@ -177,16 +177,15 @@ static std::map<std::pair<int, int>, TuneCfg> g_tuned;  // (precision, n) -> cfg
 // to 2, one block per SM) whose per-warp shared memory still holds every lane
 // group that n can need.
 TuneCfg default_cfg(int precision, int n) {
-  static int optin = 0;
-  if (optin == 0) {
+  static const int optin = [] {  // thread-safe one-time initialisation
     int dev = 0, v = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0) {
       cudaGetLastError();
       v = 232448;  // 227 KB, the GB300 opt-in limit
     }
-    optin = v;
-  }
+    return v;
+  }();
   TuneCfg c;
   c.rounds = (n >= 24) ? 2 : 4;
   for (int wpb = 6; wpb >= 2; --wpb) {

@@ -37,6 +37,8 @@
 // depend on scheduling.
 #include <math.h>
 
+#include <atomic>
+
 #include "gbs_internal.cuh"
 
 namespace gbs {
@@ -983,13 +985,13 @@ cudaError_t launch_pair_terms(const HafLaunch& L, cudaStream_t st) {
 // (per device and precision); it is never lowered, so every launch shape, and
 // any CUDA graph instantiated with one, stays valid.
 static cudaError_t ensure_smem_limit(int precision) {
-  static int done[2][64] = {{0}};
+  static std::atomic<int> done[2][64];  // zero-initialised (static storage)
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   const int p = precision == GBS_FP64 ? 0 : 1;
-  if (done[p][dev]) return cudaSuccess;
+  if (done[p][dev].load(std::memory_order_acquire)) return cudaSuccess;
   const void* fn = p == 0 ? (const void*)haf_subsets_kernel<double> : (const void*)haf_subsets_kernel<float>;
   cudaFuncAttributes fa;
   e = cudaFuncGetAttributes(&fa, fn);
@@ -999,7 +1001,7 @@ static cudaError_t ensure_smem_limit(int precision) {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
   if (e != cudaSuccess) return e;
-  done[p][dev] = 1;
+  done[p][dev].store(1, std::memory_order_release);
   return cudaSuccess;
 }
 

@@ -88,7 +88,16 @@ __global__ void marginal_kernel(int k, int n, const double2* __restrict__ H, con
       const int mu = __popc(A);
       if (mu >= mu_lo && mu <= mu_hi && !((k - ja - mu) & 1)) {
         const double f = F[((ja >> 1) * K2 + (jb >> 1)) * (k + 1) + mu];
-        if (f != 0.0) {
+        if (f != 0.0 && nvals == k) {
+          // Proposition (collision-free prefix): Per(S_{A,B}) is 1 for B = A
+          // and 0 for every other B, so only B = A contributes
+          if ((A & ~csp) == 0) {
+            const double2 he = Hb[cs & ~A], hep = Hb[csp & ~A];
+            const double er = he.x * hep.x + he.y * hep.y, ei = he.y * hep.x - he.x * hep.y;
+            t_re = fma(f, er, t_re);
+            t_im = fma(f, ei, t_im);
+          }
+        } else if (f != 0.0) {
           const double2 he = Hb[cs & ~A];
           for (int B = csp;; B = (B - 1) & csp) {
             if (__popc(B) == mu) {
@@ -145,6 +154,30 @@ __global__ void rescale_kernel(const double* __restrict__ hafB, const int* __res
       const double sc = pow(t, -0.5 * c);
       v.x = hafB[2 * j] * sc;
       v.y = hafB[2 * j + 1] * sc;
+    }
+    H[q] = v;
+  }
+}
+
+// Exponential-space variant (Appendix D) for the chain sampler: the sampled
+// prefix's sub-Hafnians Haf(B_T) are kept in `cache` (index = position mask
+// over the prefix). For candidate l of step k (prefix x_1..x_{k-1}, l), T with
+// position k-1 reads the step's new value newv[l][T minus that position], the
+// rest the cache; H holds Haf(W_T) = Haf(B_T) / t^{|T|/2} (0 for odd |T|).
+__global__ void chain_table_kernel(const double2* __restrict__ cache, const double2* __restrict__ newv, int k,
+                                   double t, int m, double2* __restrict__ H) {
+  const int64_t total = (int64_t)m << k;
+  const int half = 1 << (k - 1);
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int l = (int)(q >> k);
+    const int T = (int)(q & ((1 << k) - 1));
+    const int c = __popc(T);
+    double2 v = make_double2(0.0, 0.0);
+    if (!(c & 1)) {
+      const double2 h = (T & half) ? newv[(int64_t)l * half + (T & (half - 1))] : cache[T];
+      const double sc = pow(t, -0.5 * c);
+      v.x = h.x * sc;
+      v.y = h.y * sc;
     }
     H[q] = v;
   }
@@ -262,37 +295,136 @@ extern "C" int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int
 
 // Algorithm 1: x_k drawn from the m conditional weights q_n(x_1..x_{k-1}, l),
 // l = 0..m-1, with the caller's uniform number u_k (inverse CDF in mode order).
+// The exponential-space variant of Appendix D: the sub-Hafnians of the sampled
+// prefix are kept on the device across steps, so step k computes only those
+// of subsets that hold the new photon (for each candidate l, the odd subsets
+// T' of positions 0..k-2 plus l), half of the step's table; the marginal
+// kernel then reads the cache for the rest.
 extern "C" int gbs_sample_chain(const gbs_kernel* k, int n, const double* uniforms, void* stream, int* x_out) {
   clear_error();
   if (!k || (n > 0 && (!uniforms || !x_out))) return fail(GBS_EINVAL, "null argument");
   if (n < 0 || n > kMaxK || (n & 1)) return fail(GBS_ERANGE, "n = %d must be even and <= %d", n, kMaxK);
+  if (n == 0) return GBS_OK;
+  if (!k->r_uniform) return fail(GBS_EINVAL, "marginals need identical squeezing on every mode");
+  if (!(k->t_uniform > 0.0)) return fail(GBS_EINVAL, "marginals need r > 0");
+  cudaStream_t st = (cudaStream_t)stream;
   const int m = k->m;
-  std::vector<int> prefix((size_t)m * n);
-  std::vector<double> w(m);
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const size_t cache_b = al(16 * ((size_t)1 << n)), new_b = al(16 * ((size_t)m << (n - 1)));
+  const size_t H_b = al(16 * ((size_t)m << n)), F_b = al(8 * (size_t)(n / 2 + 1) * (n / 2 + 1) * (n + 1));
+  const size_t vm_b = al(4 * (size_t)m * kMaxK), nv_b = al(4 * (size_t)m), q_b = al(8 * (size_t)m);
+  void* tmp = nullptr;
+  cudaError_t e = scratch_alloc(&tmp, cache_b + new_b + H_b + F_b + vm_b + nv_b + q_b, st);
+  if (e != cudaSuccess) return fail(GBS_ENOMEM, "chain scratch: %s", cudaGetErrorString(e));
+  unsigned char* t = (unsigned char*)tmp;
+  double2* d_cache = (double2*)t;
+  double2* d_new = (double2*)(t + cache_b);
+  double2* d_H = (double2*)(t + cache_b + new_b);
+  double* d_F = (double*)(t + cache_b + new_b + H_b);
+  int* d_vm = (int*)(t + cache_b + new_b + H_b + F_b);
+  int* d_nv = (int*)(t + cache_b + new_b + H_b + F_b + vm_b);
+  double* d_q = (double*)(t + cache_b + new_b + H_b + F_b + vm_b + nv_b);
   std::vector<int> x;
-  for (int kk = 1; kk <= n; ++kk) {
-    for (int l = 0; l < m; ++l) {
-      for (int i = 0; i < kk - 1; ++i) prefix[(size_t)l * kk + i] = x[i];
-      prefix[(size_t)l * kk + kk - 1] = l;
+  std::vector<double> w(m);
+  std::vector<int> idx, nvl, vmask((size_t)m * kMaxK), nvals(m);
+  std::vector<int64_t> offs;
+  int ret = GBS_OK;
+  do {
+    const double2 one = make_double2(1.0, 0.0);  // Haf of the empty matrix
+    if ((e = cudaMemcpyAsync(d_cache, &one, 16, cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+      ret = cuda_fail(e, "cache init");
+      break;
     }
-    const int rc = gbs_marginal_batch(k, prefix.data(), kk, m, n, stream, w.data());
-    if (rc) return rc;
-    double tot = 0.0;
-    for (int l = 0; l < m; ++l) tot += std::max(w[l], 0.0);
-    const double target = uniforms[kk - 1] * tot;
-    double run = 0.0;
-    int pick = m - 1;
-    for (int l = 0; l < m; ++l) {
-      run += std::max(w[l], 0.0);
-      if (run > target) {
-        pick = l;
+    for (int kk = 1; kk <= n && ret == GBS_OK; ++kk) {
+      const int half = 1 << (kk - 1);
+      // new sub-Hafnians: candidate l, mask T' over positions 0..kk-2 (odd
+      // |T'| gives an even list; even |T'| an odd one, whose Hafnian is 0 and
+      // costs no work), list = x_{T'} followed by l
+      idx.clear();
+      nvl.clear();
+      offs.clear();
+      for (int l = 0; l < m; ++l)
+        for (int T = 0; T < half; ++T) {
+          offs.push_back((int64_t)idx.size());
+          for (int i = 0; i < kk - 1; ++i)
+            if (T >> i & 1) idx.push_back(x[i]);
+          idx.push_back(l);
+          nvl.push_back(__builtin_popcount(T) + 1);
+        }
+      BatchArgs a;
+      a.mode = BatchArgs::PROB;
+      a.B = k->B;
+      a.B32 = k->B32;
+      a.m = m;
+      a.log_norm_dev = k->dscal;
+      a.idx = idx.data();
+      a.n = nvl.data();
+      a.offs = offs.data();
+      a.batch = m * half;
+      a.precision = GBS_FP64;
+      a.stream = st;
+      a.out2 = (double*)d_new;
+      if ((ret = run_batch(a)) != GBS_OK) break;
+      // per candidate: position masks of the distinct values (for Per(S_{A,B}))
+      std::fill(vmask.begin(), vmask.end(), 0);
+      for (int l = 0; l < m; ++l) {
+        int nvv = 0;
+        for (int i = 0; i < kk; ++i) {
+          const int xi = (i < kk - 1) ? x[i] : l;
+          int v = 0;
+          while (v < nvv) {
+            const int p0 = __builtin_ctz(vmask[(size_t)l * kMaxK + v]);
+            if (((p0 < kk - 1) ? x[p0] : l) == xi) break;
+            ++v;
+          }
+          if (v == nvv) nvv++;
+          vmask[(size_t)l * kMaxK + v] |= 1 << i;
+        }
+        nvals[l] = nvv;
+      }
+      if ((e = cudaMemcpyAsync(d_vm, vmask.data(), 4 * vmask.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+          (e = cudaMemcpyAsync(d_nv, nvals.data(), 4 * (size_t)m, cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+        ret = cuda_fail(e, "chain upload");
+        break;
+      }
+      chain_table_kernel<<<std::min(4096, (int)((((int64_t)m << kk) + 255) / 256)), 256, 0, st>>>(
+          d_cache, d_new, kk, k->t_uniform, m, d_H);
+      fcoef_kernel<<<1, 256, 0, st>>>(kk, n, m, d_F);
+      marginal_kernel<<<m, 256, 0, st>>>(kk, n, d_H, d_F, d_vm, d_nv, d_q);
+      if ((e = cudaGetLastError()) != cudaSuccess) {
+        ret = cuda_fail(e, "chain kernels");
+        break;
+      }
+      if ((e = cudaMemcpyAsync(w.data(), d_q, 8 * (size_t)m, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+          (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+        ret = cuda_fail(e, "chain weights");
+        break;
+      }
+      double tot = 0.0;
+      for (int l = 0; l < m; ++l) tot += std::max(w[l], 0.0);
+      const double target = uniforms[kk - 1] * tot;
+      double run = 0.0;
+      int pick = m - 1;
+      for (int l = 0; l < m; ++l) {
+        run += std::max(w[l], 0.0);
+        if (run > target) {
+          pick = l;
+          break;
+        }
+      }
+      x.push_back(pick);
+      // keep the chosen candidate's new sub-Hafnians: masks with bit kk-1
+      if (kk < n && (e = cudaMemcpyAsync(d_cache + half, d_new + (size_t)pick * half, 16 * (size_t)half,
+                                         cudaMemcpyDeviceToDevice, st)) != cudaSuccess) {
+        ret = cuda_fail(e, "cache update");
         break;
       }
     }
-    x.push_back(pick);
-  }
-  for (int i = 0; i < n; ++i) x_out[i] = x[i];
-  return GBS_OK;
+  } while (0);
+  scratch_free(tmp, st);
+  if (ret == GBS_OK)
+    for (int i = 0; i < n; ++i) x_out[i] = x[i];
+  return ret;
 }
 
 // Steps 1-3 of Sec. 3: n from P_n (truncated at n_max, renormalised) by the

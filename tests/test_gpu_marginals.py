@@ -140,3 +140,24 @@ def test_end_to_end_sample(gbs):
     with pytest.raises(gbs.GbsError) as ei:
         gbs.sample(gbs.build_kernel(U, np.linspace(0.3, 0.8, m)), n_max, u)
     assert ei.value.code == -1
+
+
+def test_chain_sampler_cache_matches_plain_chain(gbs):
+    """The chain sampler keeps the sampled prefix's sub-Hafnians across steps
+    (the exponential-space variant, Appendix D) and computes only the new
+    ones; its samples equal a plain chain whose every step recomputes all
+    conditional weights with gbs_marginal_batch (inverse CDF in mode order)."""
+    m, n = 7, 8
+    U = W.haar_unitary(m, 123)
+    K = gbs.build_kernel(U, np.full(m, 0.7))
+    rng = np.random.default_rng(5)
+    for _ in range(12):
+        u = rng.random(n)
+        got = gbs.sample_chain(K, n, u)
+        x = []
+        for k in range(1, n + 1):
+            pre = np.array([x + [l] for l in range(m)], np.int32)
+            w = np.maximum(gbs.marginal_batch(K, pre, n), 0.0)
+            c = np.cumsum(w)
+            x.append(int(min(np.searchsorted(c, u[k - 1] * c[-1], side="right"), m - 1)))
+        assert list(got) == x, (list(got), x)
