@@ -493,3 +493,29 @@ def test_pairing_choice_lowers_cancellation(gbs):
     ratio = k1.cpu().numpy() / k0.cpu().numpy()
     assert np.all(np.isfinite(ratio))
     assert np.exp(np.mean(np.log(ratio))) < 0.8, ratio
+
+
+def test_repeated_row_route_largest_orders(gbs, orc):
+    """n = 30 and 32 through the repeated-row route: all photons in one mode
+    (Haf = B_vv^16 (31)!!, the closed form of J_32 scaled) and photons spread
+    over 5 to 6 modes (the oracle's repeated-row formula); each result is also
+    within its own error estimate."""
+    m = 6
+    U = W.haar_unitary(m, 9)
+    r = np.full(m, 0.6)
+    K = kernel_for(gbs, U, r)
+    Bdd = orc.build_B_dd(U, np.tanh(r))
+    B = (Bdd[..., 0] + Bdd[..., 1]) + 1j * (Bdd[..., 2] + Bdd[..., 3])
+    one = np.full(32, 3, np.int32)
+    _, _, hf, er = run_prob(gbs, K, [one], 0, host=True)
+    ref = B[3, 3] ** 16 * math.prod(range(31, 0, -2))
+    # the 33 alternating terms cancel strongly here (measured 3.6e-11)
+    err = abs(hf[0] - ref) / abs(ref)
+    assert err <= FP64_TOL and err <= er[0], (hf[0], ref, er[0])
+    pats = [np.array([0] * 7 + [1] * 5 + [2] * 6 + [4] * 6 + [5] * 6, np.int32),
+            np.array([0] * 4 + [1] * 6 + [2] * 6 + [3] * 6 + [4] * 4 + [5] * 6, np.int32)]
+    _, _, hf, er = run_prob(gbs, K, pats, 0, host=True)
+    for x, h, e in zip(pats, hf, er):
+        modes, reps = np.unique(x, return_counts=True)
+        ref = orc.haf_repeated(B[np.ix_(modes, modes)], reps)
+        assert abs(h - ref) <= FP64_TOL * abs(ref) and abs(h - ref) <= e * abs(ref), (reps, h, ref, e)
