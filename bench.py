@@ -34,16 +34,22 @@ import workloads as W  # noqa: E402
 # headline workload, from one ncu capture (profiles/haf_subsets_fp64_m64_n16.md).
 # Reported only while the kernel's sources are the ones the capture was taken
 # from; any change to them makes the figure stale and the bench reports null.
-NCU_TRAFFIC = {"sources_sha256": "a534bf9369cdfa996fed10fa83b62c1464d3e03e562a3422ca2cfec92e9946d6", "bytes_per_launch": 93250816.0}
+NCU_TRAFFIC = {"sources_sha256": "a534bf9369cdfa996fed10fa83b62c1464d3e03e562a3422ca2cfec92e9946d6", "bytes_per_launch": 93250816.0,
+               # executed FP64 flops per cycle (DFMA x 2 + DADD + DMUL) over the 608 peak
+               "executed_fp64_frac": 0.798}
 KERNEL_SOURCES = ("paper_1908_10070_gb300/csrc/haf_subsets.cu", "paper_1908_10070_gb300/csrc/gbs_internal.cuh")
 
 
-def measured_traffic():
+def capture_current():
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
-    return NCU_TRAFFIC["bytes_per_launch"] if h.hexdigest() == NCU_TRAFFIC["sources_sha256"] else None
+    return h.hexdigest() == NCU_TRAFFIC["sources_sha256"]
+
+
+def measured_traffic():
+    return NCU_TRAFFIC["bytes_per_launch"] if capture_current() else None
 
 WORKLOAD = "batched_m64_n16"
 METRIC = "GBS output probs/sec at n=16/24/30 vs FP64 oracle; p50/p99 request latency"
@@ -303,6 +309,11 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "traffic": measured_traffic() if prec == gbs.FP64 else None,
+                     # the same capture's executed FP64 rate (the flop model above counts
+                     # one N x N complex product per subset; the route executes more)
+                     "ncu_executed_fp64_frac": (NCU_TRAFFIC["executed_fp64_frac"]
+                                                if prec == gbs.FP64 and capture_current() else None),
+                     "hafnian_terms_per_s": b * (2 ** 8 - 1) / (t_kern * 1e-3),
                      "kernel": "haf_subsets_kernel<%s>" % ("double" if prec == gbs.FP64 else "float"),
                      "kernel_ms": t_kern,
                      "flops_per_launch": flops,
