@@ -103,6 +103,13 @@ int gbs_kernel_copy_B(const gbs_kernel* k, double* dst, void* stream);
  *   kappa_out   batch doubles (host or device) or NULL: the cancellation ratio
  *               kappa_b = sum_S |f(X A_S)|_1 / |Haf(A_b)| (|z|_1 = |re|+|im|).
  * Errors: GBS_EINVAL, GBS_ERANGE (n[b] > GBS_MAX_N), GBS_ENOMEM, GBS_ECUDA. */
+/* Ordering: the subset sum pairs positions (t, t + n/2) of each matrix by
+ * default (which keeps copies of a repeated row apart); for n >= 26 this call
+ * and gbs_prob_batch first try 16 orderings on a sample of subsets and run the
+ * sum in the one with the smallest sampled sum |f|. The Hafnian does not depend
+ * on the ordering; the cancellation, and so the rounding error, does (measured
+ * on 80 matrices at n = 28 and 30: largest error 3.5e-11 with the choice,
+ * 3.1e-10 in the default order). */
 int gbs_hafnian_batch(const double* A_ri, const int* n, const int64_t* offs, int batch,
                       int precision, void* stream, double* haf_ri_out, double* kappa_out);
 
@@ -120,7 +127,9 @@ int gbs_hafnian_batch(const double* A_ri, const int* n, const int64_t* offs, int
  * address (cudaGetSymbolAddress); make that first call before any stream
  * capture. All calls share the array: calls whose GPU work overlaps (on
  * different streams, or from several threads without ordering) race on it and
- * must be serialised by the caller. */
+ * must be serialised by the caller. Matrices keep the default ordering at
+ * every n (no ordering probe), so at n >= 28 an ill-conditioned matrix can
+ * exceed 1e-10 relative error where gbs_hafnian_batch does not. */
 int gbs_hafnian_batch_noalloc(const double* A_ri, const int* n, const int64_t* offs, int batch,
                               int precision, void* stream, double* haf_ri_out, double* kappa_out);
 
@@ -253,7 +262,9 @@ typedef struct gbs_serve_opts {
                              bound lets steps run more warps per SM */
 } gbs_serve_opts;
 
-/* Start a server for kernel matrix k: a host thread admits requests into
+/* Start a server for kernel matrix k (requests keep the default ordering of
+ * the subset sum, as in gbs_hafnian_batch_noalloc: for n >= 28 the batched
+ * calls are the more accurate route): a host thread admits requests into
  * device slots as slots and memory free up, and runs steps that advance every
  * resident request's subset sum together; partial sums stay on the device
  * between steps. k must outlive the server. opts may be NULL. */

@@ -331,13 +331,13 @@ void Planner::fill(PatDesc* pats, WorkItem* items, WorkItem* rep_items) {
 // not depend on that choice, but the size of the signed terms does, and with
 // it the rounding error of the sum, which grows with sum |f| / |Haf|. For
 // matrices with n >= kPairingMinN the library tries kPairingCands orderings
-// (the identity and seeded random ones, the same for every matrix of an
+// (the default one and seeded random ones, the same for every matrix of an
 // order) on a systematic sample of kProbePerSize subsets of each size from
 // ceil(h/2) to h-3 (where most of sum |f| lies), and runs the full sum in the
 // ordering with the smallest estimate. The sample costs a few per cent of
 // the full sum at these orders.
 constexpr int kPairingMinN = 26;
-constexpr int kPairingCands = 8;
+constexpr int kPairingCands = 16;
 constexpr int kProbePerSize = 8;
 static_assert(kProbePerSize < kMaxProbeSample, "probe sample count must index the reciprocal table");
 
@@ -372,9 +372,9 @@ static void plan_pairing(const int* n, int batch, int precision, int warp_bytes,
     base[v] = (int)pp->perm.size();
     for (int c = 0; c < kPairingCands; ++c) {
       const size_t o = pp->perm.size();
-      for (int i = 0; i < v; ++i) pp->perm.push_back(i);
+      for (int i = 0; i < v; ++i) pp->perm.push_back(default_pos(i, v / 2));
       uint64_t state = 0x5eedull * 1000003ull + (uint64_t)v * 1009ull + (uint64_t)c;
-      for (int i = v - 1; c > 0 && i > 0; --i) {  // Fisher-Yates; candidate 0 stays the identity
+      for (int i = v - 1; c > 0 && i > 0; --i) {  // Fisher-Yates; candidate 0 stays the default order
         const int j = (int)(splitmix64(state) % (uint64_t)(i + 1));
         std::swap(pp->perm[o + i], pp->perm[o + j]);
       }

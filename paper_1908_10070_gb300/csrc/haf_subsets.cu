@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
     const int g = lane / L, l = lane - g * L;
 
     if (lane < n) {
-      int pos = lane;
+      int pos = default_pos(lane, h);
       if (P.perm != nullptr) {
         const int po = P.perm_off[w.pat];
         if (po >= 0) pos = P.perm[po + lane];
@@ -723,7 +723,7 @@ __global__ void __launch_bounds__(256) pair_terms_kernel(const HafLaunch P) {
     const int n = d.n, h = n >> 1;
     if (po < 0 || pair_terms_elems(n) == 0) continue;  // uniform over the block
     if (threadIdx.x < n) {
-      int pos = threadIdx.x;
+      int pos = default_pos(threadIdx.x, h);
       if (P.perm != nullptr && P.perm_off[b] >= 0) pos = P.perm[P.perm_off[b] + threadIdx.x];
       int v = (d.idx_off >= 0) ? P.idx[d.idx_off + pos] : pos;
       if (P.m_bound > 0 && (v < 0 || v >= P.m_bound)) v = 0;  // flagged by the subset kernel
