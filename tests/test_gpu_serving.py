@@ -171,3 +171,24 @@ def test_serving_max_n(gbs, kern):
         srv.destroy()
     for r, p in zip(res, ref_p):
         assert abs(r[0] - p) <= FP64_TOL * p, (r[0], p)
+
+
+def test_serving_bunched_requests(gbs, orc):
+    """Requests with many photons per mode (multisets drawn with replacement
+    from 10 modes, n <= 16) through the serving loop: FP64 results within 1e-10
+    of the double-double oracle."""
+    m = 10
+    U = W.haar_unitary(m, 44)
+    r = np.full(m, 0.9)
+    K = gbs.build_kernel(U, r)
+    rng = np.random.default_rng(45)
+    pats = [np.sort(rng.choice(m, n, replace=True)).astype(np.int32) for n in (8, 10, 12, 14, 16) for _ in range(4)]
+    srv = gbs.Server(K, max_n=16)
+    try:
+        res = wait_all(srv, [srv.submit(x) for x in pats])
+    finally:
+        srv.destroy()
+    ref = orc.prob(U, r, pats)
+    for (p, hf, e), rp, rh in zip(res, ref["p"], ref["haf"]):
+        assert abs(hf - rh) <= FP64_TOL * abs(rh), (hf, rh, e)
+        assert abs(p - rp) <= FP64_TOL * rp
