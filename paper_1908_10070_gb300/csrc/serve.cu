@@ -503,7 +503,10 @@ void fail_all(gbs_server* s, int rc) {
   for (auto& sl : s->slots) sl.used = false;
 }
 
-// Bounded wait for a stage's event; false on timeout or error.
+// Bounded wait for a stage's event; false on timeout or error. The first
+// half millisecond polls with yields only (a step takes ~0.1-1 ms, and a short
+// sleep lasts tens of microseconds on Linux, which would add to every
+// request's latency); after that it sleeps between polls.
 bool wait_stage(gbs_server* s, Stage& g, bool block) {
   const auto t0 = std::chrono::steady_clock::now();
   for (;;) {
@@ -513,7 +516,10 @@ bool wait_stage(gbs_server* s, Stage& g, bool block) {
     if (!block) return false;
     const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (el > s->o.wait_timeout_s) return false;
-    std::this_thread::sleep_for(std::chrono::microseconds(5));
+    if (el < 5e-4)
+      std::this_thread::yield();
+    else
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
 }
 
