@@ -52,6 +52,7 @@ def measured_traffic():
     return NCU_TRAFFIC["bytes_per_launch"] if capture_current() else None
 
 WORKLOAD = "batched_m64_n16"
+WORKLOAD_DESC = "M=64 Haar U seed 1, r~U[0.6,1.0], 4096 collision-free n=16 patterns, "
 METRIC = "GBS output probs/sec at n=16/24/30 vs FP64 oracle; p50/p99 request latency"
 UNIT = "probs/s"
 SMS, SM_MHZ_MAX, FP64_FLOP_PER_CLK_SM = 152, 2070.0, 4.0
@@ -198,7 +199,7 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "patterns_per_step": k},
+            "data": "synthetic", "config": {"workload": WORKLOAD_DESC + "FP64", "patterns_per_step": k},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": "%d of %d patterns per step" % (k, len(pats))},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -302,8 +303,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == gbs.FP64 else "f32 terms, f32x2/f64 sums",
         "data": "synthetic",
-        "config": {"workload": "M=64 Haar U seed 1, r~U[0.6,1.0], 4096 collision-free n=16 patterns, "
-                               + ("FP64" if prec == gbs.FP64 else "mixed precision"),
+        "config": {"workload": WORKLOAD_DESC + ("FP64" if prec == gbs.FP64 else "mixed precision"),
                    "patterns_per_step": b, "l2": "flushed (256 MB write) between timed steps",
                    "autotuned_rounds_per_item": tuned_rounds},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
