@@ -34,7 +34,7 @@ import workloads as W  # noqa: E402
 # headline workload, from one ncu capture (profiles/haf_subsets_fp64_m64_n16.md).
 # Reported only while the kernel's sources are the ones the capture was taken
 # from; any change to them makes the figure stale and the bench reports null.
-NCU_TRAFFIC = {"sources_sha256": "9568b721ea1ee65a2000fd0c11dbcc13c30e0c37c1259fb5ffde03b3ded300f3", "bytes_per_launch": 95652608.0,
+NCU_TRAFFIC = {"sources_sha256": "a33b184f51f4620e93b660b087a745e863308b7cfed3625f7f68e8521daed697", "bytes_per_launch": 93914624.0,
                # executed FP64 flops per cycle (DFMA x 2 + DADD + DMUL) over the 608 peak
                "executed_fp64_frac": 0.795}
 KERNEL_SOURCES = ("paper_1908_10070_gb300/csrc/haf_subsets.cu", "paper_1908_10070_gb300/csrc/gbs_internal.cuh")

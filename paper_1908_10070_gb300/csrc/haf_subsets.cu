@@ -195,6 +195,19 @@ __device__ __forceinline__ void sym_prod(C2<T>* __restrict__ dst, const C2<T>* _
   int i1 = 0, j1 = l;
   tri_advance(i1, j1, 0, N);
   for (int e = l; e < P; e += 2 * L) {
+    if (e - l + L >= P) {
+      // no lane has a second entry in this (last) pass: one chain only; the
+      // condition is the same for every lane of the warp
+      C2<T> acc = mk<T>(T(0), T(0));
+      const int o1 = tri_off(i1, N);
+      for (int k = 0; k < N; ++k) {
+        const int ok = tri_off(k, N);
+        const C2<T> a1 = (k >= i1) ? Ra[o1 + k - i1] : Ra[ok + i1 - k];
+        acc = cfma<T>(a1, Rb[tri_pos(k ^ 1, j1, N)], acc);
+      }
+      dst[e] = acc;
+      break;
+    }
     int i2 = i1, j2 = j1;
     tri_advance(i2, j2, L, N);
     const bool two = (e + L < P);
@@ -311,6 +324,21 @@ __device__ __forceinline__ void sym_prod_full(float2* __restrict__ dst, const fl
   int i1 = 0, j1 = l;
   tri_advance(i1, j1, 0, N);
   for (int e = l; e < P; e += 2 * L) {
+    if (e - l + L >= P) {  // last pass without second entries (warp-uniform)
+      const float4* a1 = reinterpret_cast<const float4*>(Ra + i1 * N);
+      const float4* b1 = reinterpret_cast<const float4*>(Rb + j1 * N);
+      float2 c1 = make_float2(0.f, 0.f);
+      for (int t = 0; t < half; ++t) {
+        const float4 x1 = a1[t], y1 = b1[t];
+        c1.x = fmaf(x1.x, y1.z, c1.x); c1.x = fmaf(-x1.y, y1.w, c1.x);
+        c1.y = fmaf(x1.x, y1.w, c1.y); c1.y = fmaf(x1.y, y1.z, c1.y);
+        c1.x = fmaf(x1.z, y1.x, c1.x); c1.x = fmaf(-x1.w, y1.y, c1.x);
+        c1.y = fmaf(x1.z, y1.y, c1.y); c1.y = fmaf(x1.w, y1.x, c1.y);
+      }
+      dst[i1 * N + j1] = c1;
+      dst[j1 * N + i1] = c1;
+      break;
+    }
     int i2 = i1, j2 = j1;
     tri_advance(i2, j2, L, N);
     const bool two = (e + L < P);
