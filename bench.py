@@ -15,6 +15,7 @@ products, OpenMP over patterns) on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -483,6 +484,11 @@ def serve_stream(gbs, K, reqs, precision):
             while srv.poll(t) is None:
                 pass
         lat, outstanding, i = [], {}, 0
+        # the client is Python: keep its cyclic garbage collector from pausing
+        # it mid-stream (a pause would count as latency of every request due
+        # in it); the server is native code and unaffected either way
+        gc.collect()
+        gc.disable()
         t0 = time.perf_counter()
         while i < len(reqs) or outstanding:
             now = time.perf_counter() - t0
@@ -496,11 +502,17 @@ def serve_stream(gbs, K, reqs, precision):
                 if srv.poll(tk) is not None:
                     lat.append(time.perf_counter() - t0 - outstanding.pop(tk))
         total = time.perf_counter() - t0
+        st = srv.stats()
     finally:
+        gc.enable()
         srv.destroy()
     lat = np.array(lat) * 1e3
     return {"requests": len(reqs), "throughput_req_s": len(reqs) / total, "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean())}
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            # the server's own view: device steps, their mean and longest wall time
+            # (a long tail with short steps points at the host side)
+            "steps": int(st["steps"]), "step_mean_ms": 1e3 * st["step_wall_s"] / max(1, st["steps"]),
+            "step_max_ms": 1e3 * st["step_wall_max_s"]}
 
 
 def per_pattern_stream(gbs, K, reqs):
@@ -508,15 +520,20 @@ def per_pattern_stream(gbs, K, reqs):
     request, in arrival order (host buffers)."""
     p = np.zeros(1)
     lat = []
-    t0 = time.perf_counter()
-    for arr, x in reqs:
-        now = time.perf_counter() - t0
-        if now < arr:
-            time.sleep(arr - now)
-        idx, n, offs = gbs.pack_patterns([x])
-        gbs.prob_batch(K, idx, n, offs, gbs.FP64, p_out=p)
-        lat.append(time.perf_counter() - t0 - arr)
-    total = time.perf_counter() - t0
+    gc.collect()
+    gc.disable()  # as in serve_stream: no collector pauses inside the client loop
+    try:
+        t0 = time.perf_counter()
+        for arr, x in reqs:
+            now = time.perf_counter() - t0
+            if now < arr:
+                time.sleep(arr - now)
+            idx, n, offs = gbs.pack_patterns([x])
+            gbs.prob_batch(K, idx, n, offs, gbs.FP64, p_out=p)
+            lat.append(time.perf_counter() - t0 - arr)
+        total = time.perf_counter() - t0
+    finally:
+        gc.enable()
     lat = np.array(lat) * 1e3
     return {"requests": len(reqs), "throughput_req_s": len(reqs) / total, "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean())}
