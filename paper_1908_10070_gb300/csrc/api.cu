@@ -231,8 +231,20 @@ int64_t binom64(int a, int b) {
 // of one matrix take consecutive partial slots (pattern order), and the
 // schedule lists the most expensive items first (longest-first list
 // scheduling) by bucketing on (s, rounds), whose cost is rounds * (2s)^3.
+
+
+// Estimated cost of a bucket key: size s * 65 + rounds for per-size items
+// (rounds * s^3), 0 * 65 + h for whole-matrix items (sum_s C(h, s) s^3).
+static int64_t key_cost(int key) {
+  const int64_t sz = key / 65, r = key % 65;
+  if (sz > 0) return r * sz * sz * sz;
+  int64_t c = 0;
+  for (int s = 1; s <= r; ++s) c += binom64((int)r, s) * s * s * s;
+  return c;
+}
+
 void Planner::init(const int* n, int batch, int precision, int warp_bytes, const int* rounds_for_n,
-                   const int* rep_half) {
+                   const int* rep_half, int64_t whole_reserve) {
   n_ = n;
   rep_half_ = rep_half;
   batch_ = batch;
@@ -247,6 +259,7 @@ void Planner::init(const int* n, int batch, int precision, int warp_bytes, const
   for (int v = 0; v <= kMaxN; ++v) {
     tmpl_[v].clear();
     npat_[v] = 0;
+    nwhole_[v] = 0;
   }
   for (int b = 0; b < batch; ++b)
     if (!rep_half || rep_half[b] == 0) npat_[n[b]]++;
@@ -255,21 +268,36 @@ void Planner::init(const int* n, int batch, int precision, int warp_bytes, const
   for (int v = 2; v <= kMaxN; v += 2) {
     if (!npat_[v]) continue;
     const int h = v / 2, R = rounds_for_n[v];
+    if (whole_reserve > 0 && v >= 4 && v <= kWholeMaxN && npat_[v] >= 2 * whole_reserve)
+      nwhole_[v] = npat_[v] - whole_reserve;
+    const int64_t nsplit = npat_[v] - nwhole_[v];
+    if (nwhole_[v]) {
+      bucket_[h] += nwhole_[v];  // size 0 row of the key table: whole-matrix items of half order h
+      total_ += nwhole_[v];
+    }
     for (int sz = 1; sz <= h; ++sz) {
       const int G = 32 / lanes_for(2 * sz, h, warp_bytes, stage_h, cb);
       const int64_t cnt = binom64(h, sz), cap = (int64_t)G * R;
       for (int64_t r0 = 0; r0 < cnt; r0 += cap) {
         ItemTemplate t;
         t.s = sz;
+        t.s_last = sz;
         t.rank0 = (int)r0;
         t.count = (int)std::min<int64_t>(cap, cnt - r0);
         const int rnds = std::min((t.count + G - 1) / G, 64);
         t.key = sz * 65 + rnds;
         tmpl_[v].push_back(t);
-        bucket_[t.key] += npat_[v];
+        bucket_[t.key] += nsplit;
       }
     }
-    total_ += (int64_t)tmpl_[v].size() * npat_[v];
+    total_ += (int64_t)tmpl_[v].size() * nsplit;
+  }
+  whole_.assign(batch, 0);
+  int64_t seen[kMaxN + 1] = {0};
+  for (int b = 0; b < batch; ++b) {
+    const int v = n[b];
+    if ((rep_half && rep_half[b] > 0) || v < 4 || (v & 1)) continue;
+    whole_[b] = (seen[v]++ < nwhole_[v]) ? 1 : 0;
   }
   // bucket start offsets, most expensive key first
   int order[kKeys];
@@ -277,8 +305,7 @@ void Planner::init(const int* n, int batch, int precision, int warp_bytes, const
   for (int k = 0; k < kKeys; ++k)
     if (bucket_[k]) order[nk++] = k;
   std::sort(order, order + nk, [](int x, int y) {
-    const int64_t sx = x / 65, rx = x % 65, sy = y / 65, ry = y % 65;
-    const int64_t cx = rx * sx * sx * sx, cy = ry * sy * sy * sy;
+    const int64_t cx = key_cost(x), cy = key_cost(y);
     return cx != cy ? cx > cy : x < y;
   });
   int64_t acc = 0;
@@ -306,8 +333,20 @@ void Planner::fill(PatDesc* pats, WorkItem* items, WorkItem* rep_items) {
         w.count = std::min(kRepTermsPerItem, rep_half_[b] - t0);
         w.part = q++;
         w.stride = 1;
-        w.pad[0] = w.pad[1] = 0;
+        w.s_last = 0;
+        w.aux = 0;
       }
+    } else if (whole_[b]) {
+      const int h = v / 2;
+      WorkItem& w = items[next[h]++];
+      w.pat = b;
+      w.s = 1;
+      w.rank0 = 0;
+      w.count = (1 << h) - 1;
+      w.part = q++;
+      w.stride = 1;
+      w.s_last = h;  // every subset of the matrix
+      w.aux = 0;
     } else if (v >= 2 && !(v & 1)) {
       for (const ItemTemplate& t : tmpl_[v]) {
         WorkItem& w = items[next[t.key]++];
@@ -317,7 +356,8 @@ void Planner::fill(PatDesc* pats, WorkItem* items, WorkItem* rep_items) {
         w.count = t.count;
         w.part = q++;
         w.stride = 1;
-        w.pad[0] = w.pad[1] = 0;
+        w.s_last = 0;
+        w.aux = 0;
       }
     }
     d.item_end = q;
@@ -401,8 +441,8 @@ static void plan_pairing(const int* n, int batch, int precision, int warp_bytes,
           w.count = std::min(G, K - j);
           w.part = (int)pp->items.size();
           w.stride = stride;
-          w.pad[0] = (int)cs;  // the sample's weight C(h, s) / K, read by the choice
-          w.pad[1] = K;
+          w.s_last = 0;
+          w.aux = K;  // the sample stands for C(h, s) / K times its kappa
           pp->items.push_back(w);
         }
       }
@@ -519,11 +559,14 @@ int run_batch(const BatchArgs& a) {
   const int* rep_ptr = n_rep_pat ? rep_half.data() : nullptr;
 
   Planner plan;
-  plan.init(a.n, batch, a.precision, cfg.warp_bytes, rounds_for_n, rep_ptr);
+  // a few items per resident warp balance the load over all SMs; whole-matrix
+  // items for all but one matrix per resident warp of an order (tuning runs
+  // keep per-size items, whose rounds they choose)
+  const int64_t want = 4LL * device_sm_count() * cfg.warps_per_block;
+  const int64_t reserve = a.cfg_override ? 0 : (int64_t)device_sm_count() * cfg.warps_per_block;
+  plan.init(a.n, batch, a.precision, cfg.warp_bytes, rounds_for_n, rep_ptr, reserve);
   if (!a.cfg_override) {
-    // A small batch gets smaller work items (fewer rounds each), so that there
-    // are a few items per resident warp to balance the load over all SMs.
-    const int64_t want = 4LL * device_sm_count() * cfg.warps_per_block;
+    // A small batch gets smaller work items (fewer rounds each) for the same reason.
     for (int iter = 0; iter < 6 && plan.total() < want; ++iter) {
       bool shrunk = false;
       for (int v = 0; v <= kMaxN; ++v)
@@ -532,7 +575,7 @@ int run_batch(const BatchArgs& a) {
           shrunk = true;
         }
       if (!shrunk) break;
-      plan.init(a.n, batch, a.precision, cfg.warp_bytes, rounds_for_n, rep_ptr);
+      plan.init(a.n, batch, a.precision, cfg.warp_bytes, rounds_for_n, rep_ptr, reserve);
     }
   }
   const int64_t n_items = plan.total();

@@ -13,6 +13,7 @@
 namespace gbs {
 struct ItemTemplate {
   int s, rank0, count, key;
+  int s_last;  // > s: the item covers every subset of sizes s..s_last (whole matrix)
 };
 }  // namespace gbs
 
@@ -73,6 +74,9 @@ bool shape_fits(int precision, int warp_bytes, int maxn);
 int64_t binom64(int a, int b);
 
 struct ItemTemplate;
+// Largest order whose matrices may be one whole-matrix work item each
+// (2^12 - 1 subsets at n = 24).
+constexpr int kWholeMaxN = 24;
 // Work items of a batch: init() counts them, fill() writes the descriptors'
 // item ranges and the items (in schedule order) into caller memory.
 class Planner {
@@ -80,8 +84,13 @@ class Planner {
   // rep_half (may be null): per matrix, the number of repeated-row terms it
   // sums (ceil(T / 2)), or 0 for the subset-sum route; those matrices get
   // repeated-row items (kRepTermsPerItem terms each) instead of subset items.
+  // whole_reserve (0 = never): of an order n <= kWholeMaxN with at least
+  // 2 * whole_reserve matrices, all but whole_reserve get one item each that
+  // covers all their subsets (sizes staged and reduced together); the
+  // remaining ones keep one item per size and rank range, which fill the tail
+  // of the schedule (whole items go first, as the largest).
   void init(const int* n, int batch, int precision, int warp_bytes, const int* rounds_for_n,
-            const int* rep_half = nullptr);
+            const int* rep_half = nullptr, int64_t whole_reserve = 0);
   void fill(PatDesc* pats, WorkItem* items, WorkItem* rep_items = nullptr);
   int64_t rep_total() const { return rep_total_; }
   int64_t total() const { return total_; }
@@ -89,6 +98,7 @@ class Planner {
   // work items (= partial slots) of matrix b
   int items_for(int b) const {
     if (rep_half_ && rep_half_[b] > 0) return (rep_half_[b] + kRepTermsPerItem - 1) / kRepTermsPerItem;
+    if (!whole_.empty() && whole_[b]) return 1;
     const int v = n_[b];
     return (v >= 2 && !(v & 1)) ? (int)tmpl_[v].size() : 0;
   }
@@ -101,6 +111,8 @@ class Planner {
   int64_t total_ = 0;
   int64_t rep_total_ = 0;
   int npat_[kMaxN + 1];
+  int64_t nwhole_[kMaxN + 1];
+  std::vector<char> whole_;  // per matrix: one whole-matrix item
   std::vector<ItemTemplate> tmpl_[kMaxN + 1];
   int64_t bucket_[kKeys];
   int64_t start_[kKeys];

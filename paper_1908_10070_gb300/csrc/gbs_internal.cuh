@@ -23,16 +23,19 @@ struct PatDesc {
 
 // `count` colex ranks rank0, rank0 + stride, ... among the C(h, s) subsets
 // with s pairs of one matrix (stride 1: a consecutive run; larger strides make
-// the systematic samples of the pairing probe). All subsets of an item have
-// the same order N = 2s.
+// the systematic samples of the pairing probe); or, when s_last > s, every
+// subset of every size s..s_last of the matrix (rank0, count and stride unused).
+// The subset kernel checks 1 <= s, s_last <= h and that the last rank is below
+// C(h, s) before it uses an item, and flags the matrix otherwise.
 struct WorkItem {
   int pat;
   int s;
   int rank0;
   int count;
-  int part;  // slot of this item's partial sum
+  int part;    // slot of this item's partial sum
   int stride;
-  int pad[2];
+  int s_last;  // 0 (or <= s): a single size
+  int aux;     // probe items: the number K of subsets sampled of size s
 };
 
 // Partial sum of one work item: sum (-1)^{h-|S|} f(X A_S) as a double-double
@@ -159,8 +162,7 @@ struct FinalizeLaunch {
 // Choice of each large matrix's ordering from a probe launch: probe matrix
 // k * n_cand + c is matrix sel_pat[k] in candidate ordering c, its items
 // (part slot = item index) a systematic sample of K subsets of each sampled
-// size s; each probe item carries C(h, s) in pad[0] and K (<= kMaxProbeSample)
-// in pad[1].
+// size s; each probe item carries K (< kMaxProbeSample) in aux.
 constexpr int kMaxProbeSample = 32;
 struct PairingSelect {
   const PatDesc* probe_pats;

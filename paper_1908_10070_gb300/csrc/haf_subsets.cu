@@ -431,11 +431,32 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
     if (it >= P.n_items) break;
     const WorkItem w = P.items[it];
     const PatDesc d = P.pats[w.pat];
-    const int n = d.n, h = n >> 1, s = w.s, N = 2 * s;
-    const int NP = (sizeof(T) == 8) ? N * (N + 1) / 2 : N * N;  // entries per matrix
-    const int L = lanes_for(N, h, P.warp_bytes, P.stage_h, cb);
-    const int G = 32 / L;
-    const int g = lane / L, l = lane - g * L;
+    const int n = d.n, h = n >> 1;
+    // sizes s_first..s_last: one size (a rank range of it), or every subset of
+    // every size of the matrix (s_last > s), staged and reduced together
+    const int s_first = w.s, s_last = (w.s_last > w.s) ? w.s_last : w.s;
+    const bool whole = s_last > s_first;
+    {
+      // the item must name sizes and ranks that exist for this matrix: a
+      // malformed one flags the matrix (status, NaN partial) and is skipped
+      bool ok = s_first >= 1 && s_last <= h && h <= kMaxH && w.count >= 1 && w.rank0 >= 0;
+      if (ok && !whole) {
+        const int64_t last = (int64_t)w.rank0 + (int64_t)(w.count - 1) * (w.stride > 1 ? w.stride : 1);
+        ok = last < (int64_t)tab.binom[h][s_first];
+      }
+      if (!ok) {
+        if (lane == 0) {
+          if (P.status) P.status[w.pat] = 1;
+          Partial pr;
+          pr.re_hi = pr.im_hi = __longlong_as_double(0x7ff8000000000000ll);
+          pr.re_lo = pr.im_lo = pr.kappa = 0.0;
+          pr.pad[0] = pr.pad[1] = pr.pad[2] = 0.0;
+          P.parts[w.part] = pr;
+        }
+        __syncwarp();
+        continue;
+      }
+    }
 
     if (lane < n) {
       int pos = default_pos(lane, h);
@@ -452,9 +473,6 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
     }
     __syncwarp();
 
-    C* buf = reinterpret_cast<C*>(gbase + (size_t)g * group_bytes(N, h, cb));
-    int* rowidx = reinterpret_cast<int*>(buf + sched_nbuf(h) * NP);
-    int* pairs = rowidx + N;  // FP64: the subset's pair numbers, increasing
     const double2* ptp = nullptr;
     if (sizeof(T) == 8 && P.pt != nullptr) {
       const int64_t po = P.pt_off[w.pat];
@@ -466,14 +484,64 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
 
     Comp<T> acc_re = {T(0), T(0)}, acc_im = {T(0), T(0)};
     T kap = T(0);
-    const int rounds = (w.count + G - 1) / G;
+
+    // the exponential series e_k = (1/(2k)) sum_j tr_j e_{k-j}, f = e_h, one
+    // staged subset per lane, and the signed compensated accumulation
+    auto flush = [&]() {
+      if (lane < staged) {
+        const C* pq = stP + lane * P.stage_h;
+        C e[kMaxH + 1];
+        e[0] = mk<T>(T(1), T(0));
+#pragma unroll
+        for (int k = 1; k <= kMaxH; ++k) {
+          C a = mk<T>(T(0), T(0));
+          if (k <= h) {
+#pragma unroll
+            for (int j = 1; j <= k; ++j) a = cfma<T>(pq[j - 1], e[k - j], a);
+            T c;
+            if constexpr (sizeof(T) == 8) c = tab.inv2k[k];
+            else c = tab.inv2kf[k];
+            a.x *= c;
+            a.y *= c;
+          }
+          e[k] = a;
+        }
+        C f = e[1];
+#pragma unroll
+        for (int k = 2; k <= kMaxH; ++k)
+          if (k == h) f = e[k];
+        const int sg = stF[lane];
+        if (sg != 0) {
+          comp_add<T>(acc_re, sg > 0 ? f.x : -f.x);
+          comp_add<T>(acc_im, sg > 0 ? f.y : -f.y);
+          kap += fabs(f.x) + fabs(f.y);
+        }
+      }
+      staged = 0;
+      __syncwarp();
+    };
+
+   for (int s = s_first; s <= s_last; ++s) {
+    const int N = 2 * s;
+    const int NP = (sizeof(T) == 8) ? N * (N + 1) / 2 : N * N;  // entries per matrix
+    const int L = lanes_for(N, h, P.warp_bytes, P.stage_h, cb);
+    const int G = 32 / L;
+    const int g = lane / L, l = lane - g * L;
+    C* buf = reinterpret_cast<C*>(gbase + (size_t)g * group_bytes(N, h, cb));
+    int* rowidx = reinterpret_cast<int*>(buf + sched_nbuf(h) * NP);
+    int* pairs = rowidx + N;  // FP64: the subset's pair numbers, increasing
+    const int count = whole ? tab.binom[h][s] : w.count;
+    const int rank0 = whole ? 0 : w.rank0;
+    const int stride = (!whole && w.stride > 1) ? w.stride : 1;
+    const int rounds = (count + G - 1) / G;
 
     for (int rd = 0; rd < rounds; ++rd) {
+      if (staged + G > 32) flush();  // only when the group count changed between sizes
       const int jsub = rd * G + g;
-      const bool active = jsub < w.count;
+      const bool active = jsub < count;
       // -- unrank the subset (colex): rank = sum_i C(c_i, i), c_1 < ... < c_s
       {
-        int r = w.rank0 + (active ? jsub : 0) * (w.stride > 1 ? w.stride : 1);
+        int r = rank0 + (active ? jsub : 0) * stride;
         int c = h - 1;
         for (int i = s; i >= 1; --i) {
           while (tab.binom[c][i] > r) --c;
@@ -545,43 +613,10 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
       if (l == 0) stF[staged + g] = active ? (((h - s) & 1) ? -1 : 1) : 0;
       staged += G;
       __syncwarp();
-      // -- once 32 subsets are staged (or the item ends): the exponential
-      //    series e_k = (1/(2k)) sum_j tr_j e_{k-j}, f = e_h, one subset per
-      //    lane, and the signed compensated accumulation
-      if (staged == 32 || rd == rounds - 1) {
-        if (lane < staged) {
-          const C* pq = stP + lane * P.stage_h;
-          C e[kMaxH + 1];
-          e[0] = mk<T>(T(1), T(0));
-#pragma unroll
-          for (int k = 1; k <= kMaxH; ++k) {
-            C a = mk<T>(T(0), T(0));
-            if (k <= h) {
-#pragma unroll
-              for (int j = 1; j <= k; ++j) a = cfma<T>(pq[j - 1], e[k - j], a);
-              T c;
-              if constexpr (sizeof(T) == 8) c = tab.inv2k[k];
-              else c = tab.inv2kf[k];
-              a.x *= c;
-              a.y *= c;
-            }
-            e[k] = a;
-          }
-          C f = e[1];
-#pragma unroll
-          for (int k = 2; k <= kMaxH; ++k)
-            if (k == h) f = e[k];
-          const int sg = stF[lane];
-          if (sg != 0) {
-            comp_add<T>(acc_re, sg > 0 ? f.x : -f.x);
-            comp_add<T>(acc_im, sg > 0 ? f.y : -f.y);
-            kap += fabs(f.x) + fabs(f.y);
-          }
-        }
-        staged = 0;
-        __syncwarp();
-      }
+      // -- once 32 subsets are staged, or the item ends
+      if (staged == 32 || (rd == rounds - 1 && s == s_last)) flush();
     }
+   }
 
     // warp reduction of the group accumulators (fixed butterfly: deterministic),
     // in the path's own compensated arithmetic: double-double for FP64,
@@ -781,6 +816,26 @@ __global__ void __launch_bounds__(256) pair_terms_kernel(const HafLaunch P) {
   }
 }
 
+// C(a, b) for a, b <= kMaxH (the probe's weights C(h, s) / K)
+__constant__ int c_binom[kMaxH + 1][kMaxH + 1] = {
+    {1},
+    {1, 1},
+    {1, 2, 1},
+    {1, 3, 3, 1},
+    {1, 4, 6, 4, 1},
+    {1, 5, 10, 10, 5, 1},
+    {1, 6, 15, 20, 15, 6, 1},
+    {1, 7, 21, 35, 35, 21, 7, 1},
+    {1, 8, 28, 56, 70, 56, 28, 8, 1},
+    {1, 9, 36, 84, 126, 126, 84, 36, 9, 1},
+    {1, 10, 45, 120, 210, 252, 210, 120, 45, 10, 1},
+    {1, 11, 55, 165, 330, 462, 462, 330, 165, 55, 11, 1},
+    {1, 12, 66, 220, 495, 792, 924, 792, 495, 220, 66, 12, 1},
+    {1, 13, 78, 286, 715, 1287, 1716, 1716, 1287, 715, 286, 78, 13, 1},
+    {1, 14, 91, 364, 1001, 2002, 3003, 3432, 3003, 2002, 1001, 364, 91, 14, 1},
+    {1, 15, 105, 455, 1365, 3003, 5005, 6435, 6435, 5005, 3003, 1365, 455, 105, 15, 1},
+    {1, 16, 120, 560, 1820, 4368, 8008, 11440, 12870, 11440, 8008, 4368, 1820, 560, 120, 16, 1}};
+
 // 1/K for the probe's sample counts K = 1..kMaxProbeSample - 1
 __constant__ double c_recip[kMaxProbeSample] = {
     0.0,        1.0,        1.0 / 2,  1.0 / 3,  1.0 / 4,  1.0 / 5,  1.0 / 6,  1.0 / 7,
@@ -804,10 +859,13 @@ __global__ void pairing_select_kernel(const PairingSelect S) {
     const PatDesc d = S.probe_pats[q];
     est = 0.0;
 #pragma unroll 4
+    const int h = min(max(d.n >> 1, 0), kMaxH);
     for (int it = d.item_begin; it < d.item_end; ++it) {
       const WorkItem w = S.probe_items[it];
       const double kp = S.probe_parts[it].kappa;
-      est = fma((double)w.pad[0] * c_recip[w.pad[1] & (kMaxProbeSample - 1)], kp, est);
+      const int sz = min(max(w.s, 0), h);
+      const int K = min(max(w.aux, 1), kMaxProbeSample - 1);
+      est = fma((double)c_binom[h][sz] * c_recip[K], kp, est);
     }
     if (!(est == est)) est = INFINITY;  // a NaN estimate never wins
   }

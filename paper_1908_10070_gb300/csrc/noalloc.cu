@@ -127,7 +127,8 @@ extern "C" int gbs_hafnian_batch_noalloc(const double* A_ri, const int* n, const
           w.count = (int)((cnt - r0) < cap ? (cnt - r0) : cap);
           w.part = q;
           w.stride = 1;
-          w.pad[0] = w.pad[1] = 0;
+          w.s_last = 0;
+          w.aux = 0;
           ++q;
         }
       }

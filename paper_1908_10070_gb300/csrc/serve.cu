@@ -187,7 +187,8 @@ void request_items(const gbs_server* s, int si, int n, int prec, std::vector<Wor
       w.count = (int)std::min<int64_t>(cap, cnt - r0);
       w.part = 0;
       w.stride = 1;
-      w.pad[0] = w.pad[1] = 0;
+      w.s_last = 0;
+      w.aux = 0;
       out.push_back(w);
     }
   }
