@@ -522,3 +522,18 @@ def test_repeated_row_route_largest_orders(gbs, orc):
         modes, reps = np.unique(x, return_counts=True)
         ref = orc.haf_repeated(B[np.ix_(modes, modes)], reps)
         assert abs(h - ref) <= FP64_TOL * abs(ref) and abs(h - ref) <= e * abs(ref), (reps, h, ref, e)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_whole_matrix_items_match_per_size_items(gbs, precision):
+    """In a large batch most matrices of an order are one whole-matrix work item
+    (all subset sizes staged and reduced together); a single-pattern call runs
+    per-size items. Both give the same Hafnian: within 1e-11 (FP64) or within
+    the stated bound (mixed)."""
+    U, r, pats = W.workload("batched_m64_n16")
+    K = kernel_for(gbs, U, r)
+    _, _, hb, eb = run_prob(gbs, K, pats, precision)
+    for i in (0, 1, 777, 2048, 3000):
+        _, _, hs, es = run_prob(gbs, K, [pats[i]], precision)
+        tol = 1e-11 if precision == 0 else max(eb[i], es[0])
+        assert rel(hb[i:i + 1], hs)[0] <= tol, (i, hb[i], hs[0], tol)
