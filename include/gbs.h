@@ -289,8 +289,10 @@ typedef struct gbs_serve_stats_t {
   int64_t items;          /* work items dispatched */
   int64_t subsets;        /* subset terms dispatched */
   int64_t completed;      /* requests finished on the device */
-  double step_wall_s;     /* summed step wall time */
+  double step_wall_s;     /* summed step wall time (launch to detected completion) */
   double step_wall_max_s; /* longest step */
+  double step_device_s;   /* summed step device time (CUDA events around the step) */
+  double step_device_max_s; /* longest step on the device */
 } gbs_serve_stats_t;
 int gbs_serve_stats(gbs_server* s, gbs_serve_stats_t* out);
 

@@ -111,7 +111,8 @@ struct Stage {
   int* d_sel = nullptr;
   int* d_ctr = nullptr;
   double* d_res = nullptr;
-  cudaEvent_t ev = nullptr;
+  cudaEvent_t ev = nullptr;   // the step's end
+  cudaEvent_t ev0 = nullptr;  // its start on the stream (device time = ev - ev0)
   bool busy = false;
   int64_t id = 0;
   int n_items[2] = {0, 0};
@@ -328,7 +329,8 @@ cudaError_t build_graph(gbs_server* s, Stage& g) {
 // Launch one prepared stage, with the graph (parameters updated) or directly.
 cudaError_t launch_stage(gbs_server* s, Stage& g) {
   const int S = s->o.max_slots;
-  cudaError_t e;
+  cudaError_t e = cudaEventRecord(g.ev0, s->st);
+  if (e != cudaSuccess) return e;
   if (s->o.use_graphs) {
     for (int p = 0; p < 2; ++p) {
       const bool on = g.n_items[p] > 0;
@@ -566,6 +568,13 @@ void serve_loop(gbs_server* s) {
         const double w = std::chrono::duration<double>(std::chrono::steady_clock::now() - old->t_launch).count();
         s->stats.step_wall_s += w;
         if (w > s->stats.step_wall_max_s) s->stats.step_wall_max_s = w;
+        float dev_ms = 0.f;
+        if (cudaEventElapsedTime(&dev_ms, old->ev0, old->ev) == cudaSuccess) {
+          s->stats.step_device_s += 1e-3 * dev_ms;
+          if (1e-3 * dev_ms > s->stats.step_device_max_s) s->stats.step_device_max_s = 1e-3 * dev_ms;
+        } else {
+          cudaGetLastError();
+        }
         s->stats.completed += (int64_t)old->fin.size();
         complete(s, *old);
         s->cv.notify_all();
@@ -589,6 +598,7 @@ void destroy_resources(gbs_server* s) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
     if (g.graph) cudaGraphDestroy(g.graph);
     if (g.ev) cudaEventDestroy(g.ev);
+    if (g.ev0) cudaEventDestroy(g.ev0);
     if (g.h_up) cudaFreeHost(g.h_up);
     if (g.h_res) cudaFreeHost(g.h_res);
     if (g.d_items[0]) cudaFree(g.d_items[0]);
@@ -678,7 +688,7 @@ extern "C" int gbs_serve_create(const gbs_kernel* k, const gbs_serve_opts* opts,
           (e = cudaMalloc(&g.d_sel, sizeof(int) * S)) != cudaSuccess ||
           (e = cudaMalloc(&g.d_ctr, 256)) != cudaSuccess ||
           (e = cudaMalloc(&g.d_res, 5 * sizeof(double) * S)) != cudaSuccess ||
-          (e = cudaEventCreateWithFlags(&g.ev, cudaEventDisableTiming)) != cudaSuccess) {
+          (e = cudaEventCreate(&g.ev)) != cudaSuccess || (e = cudaEventCreate(&g.ev0)) != cudaSuccess) {
         cudaGetLastError();
         ret = fail(GBS_ENOMEM, "stage buffers: %s", cudaGetErrorString(e));
         break;
