@@ -130,9 +130,10 @@ struct Tables {
 
 // Power-trace schedule per h: the fewest products R_{a+b} = R_a X R_b whose
 // index set F (with R_1 = A_S) satisfies F + F >= {1..h}, each trace k taken
-// as tr(X R_k) when k is in F, else tr(X R_a X R_b) with a + b = k, and each
-// R kept in one of sched_nbuf(h) buffers (a buffer is reused once its traces
-// are taken). Products per h = 1..16: 0 0 1 1 2 2 3 3 3 3 4 4 4 4 5 6.
+// as tr(X R_k) when k is in F, else tr(X R_a X R_b) with a + b = k (a = b
+// where R_{k/2} is kept: that square trace needs about half the terms), and
+// each R kept in one of sched_nbuf(h) buffers (a buffer is reused once its
+// traces are taken). Products per h = 1..16: 0 0 1 1 2 2 3 3 3 3 4 4 4 4 5 6.
 enum { kEnd = -1, kProd = 0, kTr1 = 1, kTr2 = 2 };
 struct SchedOp {
   signed char kind;  // kProd: buf[k] = buf[a] X buf[b]; kTr1: p_k = tr(X buf[a]); kTr2: p_k = tr(X buf[a] X buf[b])
@@ -145,18 +146,18 @@ __constant__ SchedOp c_sched[kMaxH + 1][kMaxOps] = {
     {{kTr1, 1, 0, 0}, {kTr2, 2, 0, 0}, {kEnd, 0, 0, 0}},  // h = 2
     {{kProd, 1, 0, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr2, 3, 1, 0}, {kEnd, 0, 0, 0}},  // h = 3
     {{kProd, 1, 0, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr2, 3, 1, 0}, {kTr2, 4, 1, 1}, {kEnd, 0, 0, 0}},  // h = 4
-    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 2, 0}, {kTr2, 5, 2, 1}, {kEnd, 0, 0, 0}},  // h = 5
-    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 2, 0}, {kTr2, 5, 2, 1}, {kTr2, 6, 2, 2}, {kEnd, 0, 0, 0}},  // h = 6
-    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kProd, 3, 2, 1}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 2, 0}, {kTr1, 5, 3, 0}, {kTr2, 6, 3, 0}, {kTr2, 7, 3, 1}, {kEnd, 0, 0, 0}},  // h = 7
-    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kProd, 3, 2, 1}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 2, 0}, {kTr1, 5, 3, 0}, {kTr2, 6, 3, 0}, {kTr2, 7, 3, 1}, {kTr2, 8, 3, 2}, {kEnd, 0, 0, 0}},  // h = 8
-    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kProd, 3, 2, 2}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 2, 0}, {kTr2, 5, 2, 1}, {kTr1, 6, 3, 0}, {kTr2, 7, 3, 0}, {kTr2, 8, 3, 1}, {kTr2, 9, 3, 2}, {kEnd, 0, 0, 0}},  // h = 9
+    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 1, 1}, {kTr2, 5, 2, 1}, {kEnd, 0, 0, 0}},  // h = 5
+    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 1, 1}, {kTr2, 5, 2, 1}, {kTr2, 6, 2, 2}, {kEnd, 0, 0, 0}},  // h = 6
+    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kProd, 3, 2, 1}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 1, 1}, {kTr1, 5, 3, 0}, {kTr2, 6, 2, 2}, {kTr2, 7, 3, 1}, {kEnd, 0, 0, 0}},  // h = 7
+    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kProd, 3, 2, 1}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 1, 1}, {kTr1, 5, 3, 0}, {kTr2, 6, 2, 2}, {kTr2, 7, 3, 1}, {kTr2, 8, 3, 2}, {kEnd, 0, 0, 0}},  // h = 8
+    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kProd, 3, 2, 2}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 1, 1}, {kTr2, 5, 2, 1}, {kTr1, 6, 3, 0}, {kTr2, 7, 3, 0}, {kTr2, 8, 3, 1}, {kTr2, 9, 3, 2}, {kEnd, 0, 0, 0}},  // h = 9
     {{kProd, 1, 0, 0}, {kProd, 2, 1, 1}, {kProd, 3, 2, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr2, 3, 1, 0}, {kTr1, 4, 2, 0}, {kTr1, 5, 3, 0}, {kTr2, 6, 2, 1}, {kTr2, 7, 3, 1}, {kTr2, 8, 2, 2}, {kTr2, 9, 3, 2}, {kTr2, 10, 3, 3}, {kEnd, 0, 0, 0}},  // h = 10
-    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kProd, 3, 2, 1}, {kProd, 4, 3, 2}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 2, 0}, {kTr1, 5, 3, 0}, {kTr2, 6, 3, 0}, {kTr2, 7, 3, 1}, {kTr1, 8, 4, 0}, {kTr2, 9, 4, 0}, {kTr2, 10, 4, 1}, {kTr2, 11, 4, 2}, {kEnd, 0, 0, 0}},  // h = 11
-    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kProd, 3, 2, 2}, {kProd, 4, 3, 2}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 2, 0}, {kTr2, 5, 2, 1}, {kTr1, 6, 3, 0}, {kTr2, 7, 3, 0}, {kTr2, 8, 3, 1}, {kTr1, 9, 4, 0}, {kTr2, 10, 4, 0}, {kTr2, 11, 4, 1}, {kTr2, 12, 4, 2}, {kEnd, 0, 0, 0}},  // h = 12
+    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kProd, 3, 2, 1}, {kProd, 4, 3, 2}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 1, 1}, {kTr1, 5, 3, 0}, {kTr2, 6, 2, 2}, {kTr2, 7, 3, 1}, {kTr1, 8, 4, 0}, {kTr2, 9, 4, 0}, {kTr2, 10, 3, 3}, {kTr2, 11, 4, 2}, {kEnd, 0, 0, 0}},  // h = 11
+    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kProd, 3, 2, 2}, {kProd, 4, 3, 2}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 1, 1}, {kTr2, 5, 2, 1}, {kTr1, 6, 3, 0}, {kTr2, 7, 3, 0}, {kTr2, 8, 3, 1}, {kTr1, 9, 4, 0}, {kTr2, 10, 4, 0}, {kTr2, 11, 4, 1}, {kTr2, 12, 3, 3}, {kEnd, 0, 0, 0}},  // h = 12
     {{kProd, 1, 0, 0}, {kProd, 2, 1, 1}, {kProd, 3, 2, 1}, {kProd, 4, 3, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr2, 3, 1, 0}, {kTr1, 4, 2, 0}, {kTr2, 5, 2, 0}, {kTr1, 6, 3, 0}, {kTr1, 7, 4, 0}, {kTr2, 8, 2, 2}, {kTr2, 9, 4, 1}, {kTr2, 10, 3, 2}, {kTr2, 11, 4, 2}, {kTr2, 12, 3, 3}, {kTr2, 13, 4, 3}, {kEnd, 0, 0, 0}},  // h = 13
     {{kProd, 1, 0, 0}, {kProd, 2, 1, 1}, {kProd, 3, 2, 1}, {kProd, 4, 3, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr2, 3, 1, 0}, {kTr1, 4, 2, 0}, {kTr2, 5, 2, 0}, {kTr1, 6, 3, 0}, {kTr1, 7, 4, 0}, {kTr2, 8, 2, 2}, {kTr2, 9, 4, 1}, {kTr2, 10, 3, 2}, {kTr2, 11, 4, 2}, {kTr2, 12, 3, 3}, {kTr2, 13, 4, 3}, {kTr2, 14, 4, 4}, {kEnd, 0, 0, 0}},  // h = 14
-    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 2, 0}, {kTr2, 5, 2, 1}, {kProd, 3, 2, 2}, {kTr1, 6, 3, 0}, {kTr2, 7, 3, 0}, {kTr2, 8, 3, 1}, {kProd, 4, 3, 2}, {kTr1, 9, 4, 0}, {kTr2, 10, 4, 0}, {kTr2, 11, 4, 1}, {kProd, 3, 4, 2}, {kTr1, 12, 3, 0}, {kTr2, 13, 3, 0}, {kTr2, 14, 3, 1}, {kTr2, 15, 3, 2}, {kEnd, 0, 0, 0}},  // h = 15
-    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 2, 0}, {kTr2, 5, 2, 1}, {kProd, 3, 2, 2}, {kTr1, 6, 3, 0}, {kTr2, 7, 3, 0}, {kTr2, 8, 3, 1}, {kProd, 4, 3, 2}, {kTr1, 9, 4, 0}, {kTr2, 10, 4, 0}, {kTr2, 11, 4, 1}, {kProd, 3, 4, 2}, {kTr1, 12, 3, 0}, {kTr2, 13, 3, 0}, {kTr2, 14, 3, 1}, {kTr2, 15, 3, 2}, {kProd, 4, 3, 2}, {kTr2, 16, 4, 0}, {kEnd, 0, 0, 0}},  // h = 16
+    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 1, 1}, {kTr2, 5, 2, 1}, {kProd, 3, 2, 2}, {kTr1, 6, 3, 0}, {kTr2, 7, 3, 0}, {kTr2, 8, 3, 1}, {kProd, 4, 3, 2}, {kTr1, 9, 4, 0}, {kTr2, 10, 4, 0}, {kTr2, 11, 4, 1}, {kProd, 3, 4, 2}, {kTr1, 12, 3, 0}, {kTr2, 13, 3, 0}, {kTr2, 14, 3, 1}, {kTr2, 15, 3, 2}, {kEnd, 0, 0, 0}},  // h = 15
+    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 1, 1}, {kTr2, 5, 2, 1}, {kProd, 3, 2, 2}, {kTr1, 6, 3, 0}, {kTr2, 7, 3, 0}, {kTr2, 8, 3, 1}, {kProd, 4, 3, 2}, {kTr1, 9, 4, 0}, {kTr2, 10, 4, 0}, {kTr2, 11, 4, 1}, {kProd, 3, 4, 2}, {kTr1, 12, 3, 0}, {kTr2, 13, 3, 0}, {kTr2, 14, 3, 1}, {kTr2, 15, 3, 2}, {kProd, 4, 3, 2}, {kTr2, 16, 4, 0}, {kEnd, 0, 0, 0}},  // h = 16
 };
 
 // Position of entry (r, c) of a symmetric N x N matrix stored as its packed
@@ -267,6 +268,45 @@ __device__ __forceinline__ C2<T> tr2_part(const C2<T>* __restrict__ Ra, const C2
   }
   acc.x = fma(T(2), acc.x, dg.x);
   acc.y = fma(T(2), acc.y, dg.y);
+  return acc;
+}
+
+// tr(X Ra X Ra): the term Ra[i][j] Ra[i^1][j^1] is unchanged by transposing
+// (i, j) -> (j, i) and by swapping both indices within their pairs
+// (i, j) -> (i^1, j^1), so one entry per orbit is enough: row 2t (columns
+// j >= 2t) against row 2t+1,
+//   T = 2 sum_t sum_{j >= 2t} c_j Ra[2t][j] Ra[2t+1][j^1],
+// c_j = 1 for j in {2t, 2t+1} (orbits of two) and 2 otherwise (orbits of four):
+// N(N+2)/4 terms instead of N(N+1)/2. The even rows are walked in packed order
+// (row 2t holds N - 2t entries).
+template <typename T>
+__device__ __forceinline__ C2<T> tr2sq_part(const C2<T>* __restrict__ Ra, int N, int l, int L) {
+  const int E = (N * N) / 4 + N / 2;
+  C2<T> acc = mk<T>(T(0), T(0)), dg = mk<T>(T(0), T(0));
+  int t = 0, j = l;
+  while (j >= N && 2 * t < N) {
+    const int over = j - N;
+    ++t;
+    j = 2 * t + over;
+  }
+  for (int e = l; e < E; e += L) {
+    const int o = tri_off(2 * t, N), ow = o + (N - 2 * t);  // rows 2t and 2t+1
+    const C2<T> a = Ra[o + j - 2 * t];
+    const C2<T> b = (j == 2 * t + 1) ? a : Ra[ow + (j ^ 1) - 2 * t - 1];
+    const bool w2 = j >= 2 * t + 2;
+    C2<T> cur = w2 ? acc : dg;  // selects, not a divergent branch
+    cur = cfma<T>(a, b, cur);
+    acc = w2 ? cur : acc;
+    dg = w2 ? dg : cur;
+    j += L;
+    while (j >= N && 2 * t < N) {
+      const int over = j - N;
+      ++t;
+      j = 2 * t + over;
+    }
+  }
+  acc.x = T(2) * fma(T(2), acc.x, dg.x);
+  acc.y = T(2) * fma(T(2), acc.y, dg.y);
   return acc;
 }
 
@@ -385,14 +425,57 @@ __device__ __forceinline__ float2 tr1_full(const float2* __restrict__ Ra, int N,
   return acc;
 }
 
-// tr(X Ra X Rb) = sum_i sum_t Ra[i][2t] Rb[i^1][2t+1] + Ra[i][2t+1] Rb[i^1][2t]
-// (partial over this lane's rows).
+// tr(X Ra X Rb) = sum_{p,u} B(p, u), B(p, u) = sum_{i in pair p} (Ra[i][2u]
+// Rb[i^1][2u+1] + Ra[i][2u+1] Rb[i^1][2u]) the block of row pair p and column
+// pair u. Both matrices are symmetric, so B(p, u) = B(u, p) and
+// T = sum_p B(p, p) + 2 sum_{p < u} B(p, u): the upper triangle p <= u of the
+// s x s block grid, s = N/2, walked like a packed triangle (partial over this
+// lane's blocks). Half the products of the plain sum over all rows.
 __device__ __forceinline__ float2 tr2_full(const float2* __restrict__ Ra, const float2* __restrict__ Rb,
                                            int N, int l, int L) {
-  float2 acc = make_float2(0.f, 0.f);
-  for (int i = l; i < N; i += L)
-    acc = pair_dot(reinterpret_cast<const float4*>(Ra + i * N),
-                   reinterpret_cast<const float4*>(Rb + (i ^ 1) * N), N >> 1, acc);
+  const int s = N >> 1, E = s * (s + 1) / 2;
+  float2 acc = make_float2(0.f, 0.f), dg = make_float2(0.f, 0.f);
+  int p = 0, u = l;
+  tri_advance(p, u, 0, s);
+  for (int e = l; e < E; e += L) {
+    const float4* a0 = reinterpret_cast<const float4*>(Ra + 2 * p * N) + u;
+    const float4* a1 = reinterpret_cast<const float4*>(Ra + (2 * p + 1) * N) + u;
+    const float4* b0 = reinterpret_cast<const float4*>(Rb + (2 * p + 1) * N) + u;
+    const float4* b1 = reinterpret_cast<const float4*>(Rb + 2 * p * N) + u;
+    const bool off = u > p;
+    float2 cur = off ? acc : dg;
+    cur = pair_dot(a0, b0, 1, cur);
+    cur = pair_dot(a1, b1, 1, cur);
+    acc = off ? cur : acc;
+    dg = off ? dg : cur;
+    tri_advance(p, u, L, s);
+  }
+  acc.x = fmaf(2.f, acc.x, dg.x);
+  acc.y = fmaf(2.f, acc.y, dg.y);
+  return acc;
+}
+
+// tr(X Ra X Ra): within the block grid, B(p, u) further splits into two equal
+// halves (the pair swap maps row 2p's terms onto row 2p+1's), so
+// T = 2 (sum_p D(p, p) + 2 sum_{p < u} D(p, u)) with D(p, u) the row-2p half
+// alone: a quarter of the products of the plain sum.
+__device__ __forceinline__ float2 tr2sq_full(const float2* __restrict__ Ra, int N, int l, int L) {
+  const int s = N >> 1, E = s * (s + 1) / 2;
+  float2 acc = make_float2(0.f, 0.f), dg = make_float2(0.f, 0.f);
+  int p = 0, u = l;
+  tri_advance(p, u, 0, s);
+  for (int e = l; e < E; e += L) {
+    const float4* a0 = reinterpret_cast<const float4*>(Ra + 2 * p * N) + u;
+    const float4* b0 = reinterpret_cast<const float4*>(Ra + (2 * p + 1) * N) + u;
+    const bool off = u > p;
+    float2 cur = off ? acc : dg;
+    cur = pair_dot(a0, b0, 1, cur);
+    acc = off ? cur : acc;
+    dg = off ? dg : cur;
+    tri_advance(p, u, L, s);
+  }
+  acc.x = 2.f * fmaf(2.f, acc.x, dg.x);
+  acc.y = 2.f * fmaf(2.f, acc.y, dg.y);
   return acc;
 }
 
@@ -600,11 +683,13 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
         } else {
           C part;
           if constexpr (sizeof(T) == 8)
-            part = (op.kind == kTr1) ? tr1_part<T>(buf + op.a * NP, N, l, L)
-                                     : tr2_part<T>(buf + op.a * NP, buf + op.b * NP, N, NP, l, L);
+            part = (op.kind == kTr1)  ? tr1_part<T>(buf + op.a * NP, N, l, L)
+                   : (op.a == op.b) ? tr2sq_part<T>(buf + op.a * NP, N, l, L)
+                                    : tr2_part<T>(buf + op.a * NP, buf + op.b * NP, N, NP, l, L);
           else
-            part = (op.kind == kTr1) ? tr1_full(buf + op.a * NP, N, l, L)
-                                     : tr2_full(buf + op.a * NP, buf + op.b * NP, N, l, L);
+            part = (op.kind == kTr1)  ? tr1_full(buf + op.a * NP, N, l, L)
+                   : (op.a == op.b) ? tr2sq_full(buf + op.a * NP, N, l, L)
+                                    : tr2_full(buf + op.a * NP, buf + op.b * NP, N, l, L);
           const C t = group_sum<T>(part, L);
           if (l == 0) stP[(staged + g) * P.stage_h + (op.k - 1)] = t;
         }
