@@ -501,7 +501,7 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
   const int cb = (int)sizeof(C);
   unsigned char* wbase = smem + (size_t)warp * P.warp_bytes;
   int* xs = reinterpret_cast<int*>(wbase);
-  // staging: the power traces of up to 32 finished subsets and their signs
+  // staging: the power traces of up to 32 finished subsets, their signs and orders
   C* stP = reinterpret_cast<C*>(wbase + kWarpHeaderBytes);
   int* stF = reinterpret_cast<int*>(stP + 32 * P.stage_h);
   unsigned char* gbase = wbase + kWarpHeaderBytes + stage_bytes(P.stage_h, cb);
@@ -572,7 +572,37 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
     // staged subset per lane, and the signed compensated accumulation
     auto flush = [&]() {
       if (lane < staged) {
-        const C* pq = stP + lane * P.stage_h;
+        C* pq = stP + lane * P.stage_h;
+        const int sv = stF[lane];
+        const int Nl = sv < 0 ? -sv : sv;  // the subset's order N
+        if (Nl > 0 && Nl < h) {
+          // an order-N subset has traces 1..N only: det(I - xM) = sum_i d_i x^i
+          // has degree N, so by Newton's identities d_k = -(1/k) sum_{i<=k}
+          // d_{k-i} p_i (d_0 = 1) and, for k > N, p_k = -sum_{i<=N} d_i p_{k-i}
+          C dk[kMaxH];  // d_1..d_{kMaxH-1}
+#pragma unroll
+          for (int k = 1; k < kMaxH; ++k) {
+            C a = mk<T>(T(0), T(0));
+            if (k <= Nl) {
+              a = pq[k - 1];
+#pragma unroll
+              for (int i = 1; i < k; ++i) a = cfma<T>(dk[i], pq[k - i - 1], a);
+              T c;
+              if constexpr (sizeof(T) == 8) c = T(-2) * tab.inv2k[k];
+              else c = T(-2) * tab.inv2kf[k];
+              a.x *= c;
+              a.y *= c;
+            }
+            dk[k] = a;
+          }
+          for (int k = Nl + 1; k <= h; ++k) {
+            C a = mk<T>(T(0), T(0));
+#pragma unroll
+            for (int i = 1; i < kMaxH; ++i)
+              if (i <= Nl) a = cfma<T>(dk[i], pq[k - i - 1], a);
+            pq[k - 1] = mk<T>(-a.x, -a.y);
+          }
+        }
         C e[kMaxH + 1];
         e[0] = mk<T>(T(1), T(0));
 #pragma unroll
@@ -593,7 +623,7 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
 #pragma unroll
         for (int k = 2; k <= kMaxH; ++k)
           if (k == h) f = e[k];
-        const int sg = stF[lane];
+        const int sg = sv;
         if (sg != 0) {
           comp_add<T>(acc_re, sg > 0 ? f.x : -f.x);
           comp_add<T>(acc_im, sg > 0 ? f.y : -f.y);
@@ -607,6 +637,8 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
    for (int s = s_first; s <= s_last; ++s) {
     const int N = 2 * s;
     const int NP = (sizeof(T) == 8) ? N * (N + 1) / 2 : N * N;  // entries per matrix
+    // traces taken directly: 1..min(N, h) (those past N follow in the series step)
+    const int hs = N < h ? N : h;
     const int L = lanes_for(N, h, P.warp_bytes, P.stage_h, cb);
     const int G = 32 / L;
     const int g = lane / L, l = lane - g * L;
@@ -668,9 +700,9 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
         }
       }
       __syncwarp();
-      // -- power traces tr((X A_S)^k), k = 1..h, by the schedule for h
+      // -- power traces tr((X A_S)^k), k = 1..hs, by the schedule for hs
       for (int o = 0; o < kMaxOps; ++o) {
-        const SchedOp op = c_sched[h][o];
+        const SchedOp op = c_sched[hs][o];
         if (op.kind == kEnd) break;
         if (op.kind == kProd) {
           if constexpr (sizeof(T) == 8) {
@@ -695,7 +727,8 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
         }
         __syncwarp();
       }
-      if (l == 0) stF[staged + g] = active ? (((h - s) & 1) ? -1 : 1) : 0;
+      // sign (-1)^{h-s} times the order N (0: no subset in this slot)
+      if (l == 0) stF[staged + g] = active ? (((h - s) & 1) ? -N : N) : 0;
       staged += G;
       __syncwarp();
       // -- once 32 subsets are staged, or the item ends
