@@ -142,8 +142,13 @@ struct gbs_server {
   bool stop = false;
   bool failed = false;
   std::deque<Request> queue;
-  std::unordered_set<int64_t> pending;
-  std::unordered_map<int64_t, Result> done;
+  // Results have their own lock (taken after mu, never before it), so that a
+  // client polling in a tight loop contends only for the result table and
+  // never holds up the server thread, which keeps mu while it admits, builds
+  // and completes steps.
+  std::mutex rmu;
+  std::unordered_set<int64_t> pending;         // under rmu
+  std::unordered_map<int64_t, Result> done;   // under rmu
   int64_t next_ticket = 1;
   std::vector<Slot> slots;
   Arena arena;
@@ -475,6 +480,7 @@ bool build_step(gbs_server* s, Stage& g) {
 // Publish the results of a completed stage and free its finished slots (lock held).
 void complete(gbs_server* s, Stage& g) {
   const int S = s->o.max_slots;
+  std::lock_guard<std::mutex> rl(s->rmu);
   for (size_t b = 0; b < g.fin.size(); ++b) {
     Slot& sl = s->slots[g.fin[b]];
     Result r;
@@ -495,6 +501,7 @@ void complete(gbs_server* s, Stage& g) {
 }
 
 void fail_all(gbs_server* s, int rc) {
+  std::lock_guard<std::mutex> rl(s->rmu);
   for (int64_t t : s->pending) {
     Result r;
     r.rc = rc;
@@ -737,6 +744,7 @@ extern "C" int gbs_serve_submit(gbs_server* s, const int* idx, int n, int precis
     r.hi = 0.0;
     r.p = (n == 0) ? exp(-s->log_norm) : 0.0;
     r.err = 0.0;
+    std::lock_guard<std::mutex> rl(s->rmu);
     s->done[t] = r;
     return GBS_OK;
   }
@@ -749,7 +757,10 @@ extern "C" int gbs_serve_submit(gbs_server* s, const int* idx, int n, int precis
   r.prec = precision;
   memcpy(r.idx, idx, sizeof(int) * n);
   s->queue.push_back(r);
-  s->pending.insert(t);
+  {
+    std::lock_guard<std::mutex> rl(s->rmu);
+    s->pending.insert(t);
+  }
   s->cv.notify_all();
   return GBS_OK;
 }
@@ -757,7 +768,7 @@ extern "C" int gbs_serve_submit(gbs_server* s, const int* idx, int n, int precis
 extern "C" int gbs_serve_poll(gbs_server* s, int64_t ticket, double* p, double* haf_ri, double* err_est) {
   clear_error();
   if (!s) return fail(GBS_EINVAL, "null server");
-  std::lock_guard<std::mutex> lk(s->mu);
+  std::lock_guard<std::mutex> lk(s->rmu);
   auto it = s->done.find(ticket);
   if (it == s->done.end()) {
     if (s->pending.count(ticket)) return 1;

@@ -75,11 +75,14 @@ extern "C" int gbs_autotune(int n, int precision, void* stream, int* chosen_out)
     cudaEventCreate(&e1);
   }
   const int maxdyn = max_dynamic_smem();
-  const int wpbs[] = {4, 6, 8, 12};
+  // 5 warps is the most that holds n = 28 and 30 (whose largest lane groups
+  // take about 45 KB a warp)
+  const int wpbs[] = {4, 5, 6, 8, 10, 12};
+  const int n_wpbs = (int)(sizeof(wpbs) / sizeof(wpbs[0]));
   const int rnds[] = {1, 2, 4, 8, 16};
   TuneCfg best = default_cfg(precision, n);
   float best_ms = 1e30f;
-  for (int wi = 0; wi < 4 && ret == GBS_OK; ++wi) {
+  for (int wi = 0; wi < n_wpbs && ret == GBS_OK; ++wi) {
     TuneCfg c;
     c.warps_per_block = wpbs[wi];
     c.warp_bytes = (maxdyn / c.warps_per_block) & ~127;
