@@ -776,11 +776,35 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
 
 // Warp sum of parts[begin, end): lane j adds j, j+32, ... in that order (four
 // loads issued ahead of their additions), the lanes meet in a fixed
-// butterfly; every lane ends with the total (deterministic for a given range).
+// butterfly; lane 0 ends with the total (deterministic for a given range).
 __device__ __forceinline__ void sum_partials(const Partial* __restrict__ parts, int begin, int end,
                                              int lane, double& rh, double& rl, double& ih, double& il,
                                              double& K) {
   const unsigned FULL = 0xffffffffu;
+  const int count = end - begin;
+  if (count <= 32) {
+    // one partial per lane and only the butterfly levels that reach them: lane
+    // 0 gets the same sum as the full butterfly, whose other levels would add
+    // exact zeros (a single partial is taken as it is)
+    if (lane < count) {
+      const Partial pr = parts[begin + lane];
+      rh = pr.re_hi;
+      rl = pr.re_lo;
+      ih = pr.im_hi;
+      il = pr.im_lo;
+      K = pr.kappa;
+    }
+    int span = 1;
+    while (span < count) span <<= 1;
+    for (int off = span >> 1; off > 0; off >>= 1) {
+      const double orh = __shfl_xor_sync(FULL, rh, off), orl = __shfl_xor_sync(FULL, rl, off);
+      const double oih = __shfl_xor_sync(FULL, ih, off), oil = __shfl_xor_sync(FULL, il, off);
+      K += __shfl_xor_sync(FULL, K, off);
+      dd_add(rh, rl, orh, orl);
+      dd_add(ih, il, oih, oil);
+    }
+    return;
+  }
   int q = begin + lane;
   for (; q + 96 < end; q += 128) {
     Partial pr[4];
@@ -836,56 +860,80 @@ __global__ void chunk_sum_kernel(const ChunkLaunch C) {
   }
 }
 
-// One warp per pattern: the item partials (or, after chunk_sum_kernel, the
-// chunk sums) are added by sum_partials, and lane 0 writes the outputs.
-__global__ void finalize_kernel(const FinalizeLaunch F) {
+// One warp per pattern adds its item partials (or, after chunk_sum_kernel,
+// the chunk sums) and forms prod_j s_j! (each lane counts the earlier
+// occurrences of its index; the c-th occurrence of a mode contributes a
+// factor c). The sums go to shared memory and warp 0 finishes the block's
+// patterns one per lane (hypot, log, exp): that scalar tail costs one warp
+// instruction per block instead of one per pattern.
+constexpr int kFinWarps = 16;  // most warps in a finalisation block
+__global__ void __launch_bounds__(kFinWarps * 32) finalize_kernel(const FinalizeLaunch F) {
+  __shared__ double sv[6][kFinWarps];  // re hi/lo, im hi/lo, sum |f|, prod s_j!
   const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
-  for (int b = blockIdx.x * wpb + (threadIdx.x >> 5); b < F.batch; b += gridDim.x * wpb) {
-    const int pb = F.sel ? F.sel[b] : b;
-    const PatDesc d = F.pats[pb];
-    const int n = d.n;
-    double rh = 0, rl = 0, ih = 0, il = 0, K = 0;
-    if (!(n & 1) && n > 0) {
-      if (F.chunk_parts)
-        sum_partials(F.chunk_parts, F.chunk_off[pb], F.chunk_off[pb + 1], lane, rh, rl, ih, il, K);
-      else
-        sum_partials(F.parts, d.item_begin, d.item_end, lane, rh, rl, ih, il, K);
-    } else if (n == 0) {
-      rh = 1.0;  // the empty matrix has one (empty) perfect matching
-      K = 1.0;
+  const bool want_p = F.p_out || F.logp_out || F.err_out;
+  for (int base = blockIdx.x * wpb; base < F.batch; base += gridDim.x * wpb) {
+    const int b = base + warp;
+    if (b < F.batch) {  // uniform over the warp
+      const int pb = F.sel ? F.sel[b] : b;
+      const PatDesc d = F.pats[pb];
+      const int n = d.n;
+      double rh = 0, rl = 0, ih = 0, il = 0, K = 0;
+      if (!(n & 1) && n > 0) {
+        if (F.chunk_parts)
+          sum_partials(F.chunk_parts, F.chunk_off[pb], F.chunk_off[pb + 1], lane, rh, rl, ih, il, K);
+        else
+          sum_partials(F.parts, d.item_begin, d.item_end, lane, rh, rl, ih, il, K);
+      } else if (n == 0) {
+        rh = 1.0;  // the empty matrix has one (empty) perfect matching
+        K = 1.0;
+      }
+      // odd n: no perfect matching, Haf = 0 (Sec. 3.1: P_n = 0 for odd n)
+      double fac = 1.0;
+      if (want_p && d.idx_off >= 0 && lane < n) {
+        const int xi = F.idx[d.idx_off + lane];
+        int c = 1;
+        for (int q = 0; q < lane; ++q) c += (F.idx[d.idx_off + q] == xi);
+        fac = (double)c;
+      }
+      for (int off = 16; off > 0; off >>= 1) fac *= __shfl_xor_sync(FULL, fac, off);
+      if (lane == 0) {
+        sv[0][warp] = rh;
+        sv[1][warp] = rl;
+        sv[2][warp] = ih;
+        sv[3][warp] = il;
+        sv[4][warp] = K;
+        sv[5][warp] = fac;
+      }
     }
-    // odd n: no perfect matching, Haf = 0 (Sec. 3.1: P_n = 0 for odd n)
-    // sum_j log s_j!: the c-th occurrence of a mode contributes log c
-    double lf = 0.0;
-    if (d.idx_off >= 0 && lane < n && (F.p_out || F.logp_out || F.err_out)) {
-      const int xi = F.idx[d.idx_off + lane];
-      int c = 1;
-      for (int j = 0; j < lane; ++j) c += (F.idx[d.idx_off + j] == xi);
-      if (c > 1) lf = log((double)c);
-    }
-    for (int off = 16; off > 0; off >>= 1) lf += __shfl_xor_sync(FULL, lf, off);
-    if (lane == 0) {
+    __syncthreads();
+    if (warp == 0 && lane < wpb && base + lane < F.batch) {
+      const int bo = base + lane;
+      const int pb = F.sel ? F.sel[bo] : bo;
+      const int n = F.pats[pb].n;
       const bool bad = F.status != nullptr && F.status[pb] != 0;
-      const double hr = rh + rl, hi = ih + il;
+      const double hr = sv[0][lane] + sv[1][lane], hi = sv[2][lane] + sv[3][lane];
+      const double K = sv[4][lane];
       const double mod = hypot(hr, hi);
       const double kappa = (mod > 0.0) ? K / mod : (K > 0.0 ? INFINITY : 0.0);
       const double nan = __longlong_as_double(0x7ff8000000000000ll);
       if (F.haf_out) {
-        F.haf_out[2 * b] = bad ? nan : hr;
-        F.haf_out[2 * b + 1] = bad ? nan : hi;
+        F.haf_out[2 * bo] = bad ? nan : hr;
+        F.haf_out[2 * bo + 1] = bad ? nan : hi;
       }
-      if (F.kappa_out) F.kappa_out[b] = bad ? nan : kappa;
-      if (F.p_out || F.logp_out || F.err_out) {
+      if (F.kappa_out) F.kappa_out[bo] = bad ? nan : kappa;
+      if (want_p) {
         const double L = F.log_norm ? *F.log_norm : 0.0;
+        const double lf = log(sv[5][lane]);  // sum_j log s_j!
         const double logp = (mod > 0.0) ? 2.0 * log(mod) - lf - L : -INFINITY;
         const double u = (F.precision == GBS_FP64) ? 0x1p-53 : 0x1p-24;
-        if (F.p_out) F.p_out[b] = bad ? nan : ((mod > 0.0) ? exp(logp) : 0.0);
-        if (F.logp_out) F.logp_out[b] = bad ? nan : logp;
-        if (F.err_out) F.err_out[b] = bad ? nan : (double)(n > 0 ? n : 1) * u * kappa;
+        if (F.p_out) F.p_out[bo] = bad ? nan : ((mod > 0.0) ? exp(logp) : 0.0);
+        if (F.logp_out) F.logp_out[bo] = bad ? nan : logp;
+        if (F.err_out) F.err_out[bo] = bad ? nan : (double)(n > 0 ? n : 1) * u * kappa;
       }
     }
+    __syncthreads();
   }
 }
 
@@ -1259,8 +1307,8 @@ cudaError_t launch_chunk_sums(const ChunkLaunch& C, cudaStream_t st) {
 
 cudaError_t launch_finalize(const FinalizeLaunch& F, cudaStream_t st) {
   if (F.batch <= 0) return cudaSuccess;
-  const int threads = 128;  // four patterns per block, one warp each
-  int blocks = (F.batch + 3) / 4;
+  const int threads = kFinWarps * 32;  // one warp per pattern
+  int blocks = (F.batch + kFinWarps - 1) / kFinWarps;
   if (blocks > 8192) blocks = 8192;
   finalize_kernel<<<blocks, threads, 0, st>>>(F);
   return cudaGetLastError();

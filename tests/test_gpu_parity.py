@@ -305,6 +305,11 @@ def test_prob_large_all_patterns_golden(gbs):
     ref = np.array([complex(q["haf_dd"][0] + q["haf_dd"][1], q["haf_dd"][2] + q["haf_dd"][3])
                     for q in g["patterns"]])
     err = rel(hf, ref)
+    nn = np.array([len(x) for x in pats])
+    for n_ in (28, 30):  # shown with -s
+        e_ = err[nn == n_]
+        print("n=%d: %d patterns, max rel. error %.2e, median %.2e, largest estimate %.2e, within estimate: %s"
+              % (n_, e_.size, e_.max(), np.median(e_), er[nn == n_].max(), bool(np.all(e_ <= er[nn == n_]))))
     assert np.all(err <= FP64_TOL), (err.max(), int(np.argmax(err)))
     assert np.all(np.abs(lp - np.array([q["logp"] for q in g["patterns"]])) <= 1e-9)
 
