@@ -516,7 +516,10 @@ def serve_stream(gbs, K, reqs, precision):
             "steps": int(st["steps"]), "step_mean_ms": 1e3 * st["step_wall_s"] / max(1, st["steps"]),
             "step_max_ms": 1e3 * st["step_wall_max_s"],
             "step_device_mean_ms": 1e3 * st["step_device_s"] / max(1, st["steps"]),
-            "step_device_max_ms": 1e3 * st["step_device_max_s"]}
+            "step_device_max_ms": 1e3 * st["step_device_max_s"],
+            # the server thread's longest pause between loop iterations or polls,
+            # and its longest step launch call
+            "poll_gap_max_ms": 1e3 * st["poll_gap_max_s"], "launch_max_ms": 1e3 * st["launch_max_s"]}
 
 
 def per_pattern_stream(gbs, K, reqs):

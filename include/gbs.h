@@ -293,6 +293,10 @@ typedef struct gbs_serve_stats_t {
   double step_wall_max_s; /* longest step */
   double step_device_s;   /* summed step device time (CUDA events around the step) */
   double step_device_max_s; /* longest step on the device */
+  double poll_gap_max_s;  /* longest interval, while a step was in flight, between two
+                             runs of the server thread's loop or completion polls
+                             (large: the thread was not running) */
+  double launch_max_s;    /* longest call that launches a step */
 } gbs_serve_stats_t;
 int gbs_serve_stats(gbs_server* s, gbs_serve_stats_t* out);
 

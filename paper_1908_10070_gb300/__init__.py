@@ -43,7 +43,8 @@ class ServeStats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("items", ctypes.c_int64), ("subsets", ctypes.c_int64),
                 ("completed", ctypes.c_int64), ("step_wall_s", ctypes.c_double),
                 ("step_wall_max_s", ctypes.c_double), ("step_device_s", ctypes.c_double),
-                ("step_device_max_s", ctypes.c_double)]
+                ("step_device_max_s", ctypes.c_double), ("poll_gap_max_s", ctypes.c_double),
+                ("launch_max_s", ctypes.c_double)]
 
 
 class ServeOpts(ctypes.Structure):

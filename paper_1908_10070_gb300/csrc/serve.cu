@@ -164,6 +164,10 @@ struct gbs_server {
   Stage stage[2];
   std::thread th;
   gbs_serve_stats_t stats;
+  // server-thread only (no lock): the last time the thread ran its loop or a
+  // completion poll, and the longest interval between two such times
+  std::chrono::steady_clock::time_point last_tick;
+  double tick_gap_max = 0.0;
 };
 
 namespace {
@@ -517,9 +521,21 @@ void fail_all(gbs_server* s, int rc) {
 // half millisecond polls with yields only (a step takes ~0.1-1 ms, and a short
 // sleep lasts tens of microseconds on Linux, which would add to every
 // request's latency); after that it sleeps between polls.
+// The server thread's responsiveness: the longest interval between two of its
+// loop iterations or completion polls while a step is in flight (a
+// descheduled or blocked thread shows here; a step that is slow on the device
+// does not, nor does an idle server waiting for requests).
+void tick(gbs_server* s) {
+  const auto now = std::chrono::steady_clock::now();
+  const double gap = std::chrono::duration<double>(now - s->last_tick).count();
+  if ((s->stage[0].busy || s->stage[1].busy) && gap > s->tick_gap_max) s->tick_gap_max = gap;
+  s->last_tick = now;
+}
+
 bool wait_stage(gbs_server* s, Stage& g, bool block) {
   const auto t0 = std::chrono::steady_clock::now();
   for (;;) {
+    tick(s);
     const cudaError_t e = cudaEventQuery(g.ev);
     if (e == cudaSuccess) return true;
     if (e != cudaErrorNotReady) return false;
@@ -536,7 +552,10 @@ bool wait_stage(gbs_server* s, Stage& g, bool block) {
 void serve_loop(gbs_server* s) {
   cudaSetDevice(s->device);
   std::unique_lock<std::mutex> lk(s->mu);
+  s->last_tick = std::chrono::steady_clock::now();
   for (;;) {
+    tick(s);
+    s->stats.poll_gap_max_s = s->tick_gap_max;
     admit(s);
     bool any_work = false;
     for (const Slot& sl : s->slots)
@@ -545,7 +564,10 @@ void serve_loop(gbs_server* s) {
     if (s->stop && !any_work && !s->stage[0].busy && !s->stage[1].busy && s->queue.empty()) break;
     bool launched = false;
     if (any_work && free_stage && build_step(s, *free_stage)) {
+      const auto tl0 = std::chrono::steady_clock::now();
       const cudaError_t e = launch_stage(s, *free_stage);
+      const double tl = std::chrono::duration<double>(std::chrono::steady_clock::now() - tl0).count();
+      if (tl > s->stats.launch_max_s) s->stats.launch_max_s = tl;
       if (e != cudaSuccess) {
         cudaGetLastError();
         fail_all(s, GBS_ECUDA);
