@@ -46,6 +46,9 @@ struct Partial {
 
 constexpr int kMaxN = GBS_MAX_N;
 constexpr int kMaxH = kMaxN / 2;
+// Most warps in a block of the subset kernel (one block per SM); the kernel's
+// launch bounds allow 65536 / (32 * kMaxWarpsPerBlock) = 170 registers a thread.
+constexpr int kMaxWarpsPerBlock = 12;
 constexpr int kWarpHeaderBytes = 128;  // per-warp index-list buffer (32 ints)
 
 // Default order of a matrix of order n = 2h in the subset sum: position p reads
@@ -73,13 +76,20 @@ __host__ __device__ inline int group_bytes(int N, int h, int cbytes) {
   return (bytes + 15) & ~15;
 }
 
-// Complex elements of one matrix's pair terms (order n = 2h): for every entry
-// (i, j), i <= j, of the packed upper triangle and every pair p < h,
-// Q_p(i, j) = A(i, 2p) A(2p+1, j) + A(i, 2p+1) A(2p, j), pairs innermost.
-// Summed over the pairs of a subset S they give A_S X A_S (used for h >= 3).
+// Pair sums of a matrix of order n = 2h. With the pair terms
+// Q_p(i, j) = A(i, 2p) A(2p+1, j) + A(i, 2p+1) A(2p, j), the pairs split into
+// a low part (p < hl, hl = ceil(h/2)) and a high part (p >= hl). For every
+// entry (i, j), i <= j, of the packed upper triangle the matrix keeps W values:
+// the sum of Q_p over each subset of the low pairs (slot = its bit mask), then
+// over each subset of the high pairs (slot 2^hl + mask >> hl). For a subset S
+// of pairs, A_S X A_S (i, j) = low[S] + high[S]: one complex addition per
+// entry (used for h >= 3).
+__host__ __device__ inline int pair_split_lo(int h) { return (h + 1) >> 1; }
+__host__ __device__ inline int pair_sums_width(int h) { return (1 << ((h + 1) >> 1)) + (1 << (h >> 1)); }
+// Complex elements of one matrix's pair sums (0 where they are not used).
 __host__ __device__ inline int64_t pair_terms_elems(int n) {
   const int h = n / 2;
-  return (n >= 6 && !(n & 1)) ? (int64_t)(n * (n + 1) / 2) * h : 0;
+  return (n >= 6 && !(n & 1)) ? (int64_t)(n * (n + 1) / 2) * pair_sums_width(h) : 0;
 }
 
 // Per-warp staging of finished subsets' power traces (32 slots of stage_h
@@ -120,7 +130,7 @@ struct HafLaunch {
   // the cancellation of the signed sum.
   const int* perm;
   const int* perm_off;
-  // FP64 only, may be null: per-matrix pair terms (layout of pair_terms_elems)
+  // FP64 only, may be null: per-matrix pair sums (layout of pair_terms_elems)
   // at pt + pt_off[pattern]; pt_off < 0 means that matrix forms A_S X A_S by
   // the product instead
   double* pt;

@@ -310,30 +310,34 @@ __device__ __forceinline__ C2<T> tr2sq_part(const C2<T>* __restrict__ Ra, int N,
   return acc;
 }
 
-// R_2 = A_S X A_S (upper triangle) from the matrix's pair terms: entry (i, j)
-// is sum_{p in S} Q_p(I_i, I_j), I_i = 2 pairs[i/2] + (i mod 2) the position of
-// subset row i in the matrix. Since (A_S X A_S)(i, j) = sum_k A_S(i, k)
-// A_S(k^1, j) and the k of S come in whole pairs, this adds the same products,
-// grouped by pair, with s complex additions per entry instead of 2s complex
-// multiply-adds. pairs[] increases, so I_i <= I_j whenever i <= j.
+// R_2 = A_S X A_S (upper triangle) from the matrix's pair sums: entry (i, j)
+// is low[S](I_i, I_j) + high[S](I_i, I_j), I_i = 2 pairs[i/2] + (i mod 2) the
+// position of subset row i in the matrix and klo, khi the slots of S's low and
+// high pairs. Since (A_S X A_S)(i, j) = sum_k A_S(i, k) A_S(k^1, j) and the k
+// of S come in whole pairs, this is the product's sum grouped by pair: one
+// complex addition per entry instead of 2s complex multiply-adds. pairs[]
+// increases, so I_i <= I_j whenever i <= j. The loads of four entries are
+// issued before their sums (the pair sums stream from L2 or memory).
 __device__ __forceinline__ void pair_sum(double2* __restrict__ dst, const double2* __restrict__ q,
-                                         const int* __restrict__ pairs, int N, int P, int h, int n,
-                                         int l, int L) {
-  const int s = N >> 1;
+                                         const int* __restrict__ pairs, int N, int P, int W, int n,
+                                         int klo, int khi, int l, int L) {
   int i = 0, j = l;
   tri_advance(i, j, 0, N);
-  for (int e = l; e < P; e += L) {
-    const int Ii = 2 * pairs[i >> 1] + (i & 1), Ij = 2 * pairs[j >> 1] + (j & 1);
-    const double2* qe = q + (int64_t)(tri_off(Ii, n) + Ij - Ii) * h;
-    double2 acc = make_double2(0.0, 0.0);
-#pragma unroll 4
-    for (int t = 0; t < s; ++t) {
-      const double2 v = __ldg(qe + pairs[t]);
-      acc.x += v.x;
-      acc.y += v.y;
+  for (int e0 = l; e0 < P; e0 += 4 * L) {
+    double2 a[4], b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (e0 + u * L < P) {
+        const int Ii = 2 * pairs[i >> 1] + (i & 1), Ij = 2 * pairs[j >> 1] + (j & 1);
+        const double2* qe = q + (int64_t)(tri_off(Ii, n) + Ij - Ii) * W;
+        a[u] = __ldg(qe + klo);
+        b[u] = __ldg(qe + khi);
+        tri_advance(i, j, L, N);
+      }
     }
-    dst[e] = acc;
-    tri_advance(i, j, L, N);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (e0 + u * L < P) dst[e0 + u * L] = make_double2(a[u].x + b[u].x, a[u].y + b[u].y);
   }
 }
 
@@ -480,7 +484,7 @@ __device__ __forceinline__ float2 tr2sq_full(const float2* __restrict__ Ra, int 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) {
+__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) haf_subsets_kernel(const HafLaunch P) {
   typedef C2<T> C;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Tables tab;
@@ -654,7 +658,9 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
       if (staged + G > 32) flush();  // only when the group count changed between sizes
       const int jsub = rd * G + g;
       const bool active = jsub < count;
-      // -- unrank the subset (colex): rank = sum_i C(c_i, i), c_1 < ... < c_s
+      // -- unrank the subset (colex): rank = sum_i C(c_i, i), c_1 < ... < c_s;
+      //    every lane of the group walks all of it and keeps its pair mask
+      unsigned smask = 0;
       {
         int r = rank0 + (active ? jsub : 0) * stride;
         int c = h - 1;
@@ -667,6 +673,7 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
             rowidx[2 * t + 1] = xs[2 * c + 1];
             if (sizeof(T) == 8) pairs[t] = c;
           }
+          smask |= 1u << c;
           --c;
         }
       }
@@ -706,8 +713,11 @@ __global__ void __launch_bounds__(512, 1) haf_subsets_kernel(const HafLaunch P) 
         if (op.kind == kEnd) break;
         if (op.kind == kProd) {
           if constexpr (sizeof(T) == 8) {
-            if (ptp != nullptr && op.k == 1 && op.a == 0 && op.b == 0)
-              pair_sum(buf + NP, ptp, pairs, N, NP, h, n, l, L);
+            if (ptp != nullptr && op.k == 1 && op.a == 0 && op.b == 0) {
+              const int hl = pair_split_lo(h);
+              pair_sum(buf + NP, ptp, pairs, N, NP, pair_sums_width(h), n, (int)(smask & ((1u << hl) - 1)),
+                       (1 << hl) + (int)(smask >> hl), l, L);
+            }
             else
               sym_prod<T>(buf + op.k * NP, buf + op.a * NP, buf + op.b * NP, N, NP, l, L);
           } else
@@ -937,20 +947,28 @@ __global__ void __launch_bounds__(kFinWarps * 32) finalize_kernel(const Finalize
   }
 }
 
-// Pair terms of one matrix per block: the zero-diagonal matrix is staged in
-// shared memory, then Q_p(i, j) = A(i, 2p) A(2p+1, j) + A(i, 2p+1) A(2p, j) is
-// written for the packed upper triangle, pairs innermost (coalesced stores).
+// Pair sums of one matrix per block. The zero-diagonal matrix is staged in
+// shared memory, then every pair term Q_p(e) = A(i, 2p) A(2p+1, j) +
+// A(i, 2p+1) A(2p, j) of every packed upper entry e = (i, j), and from those
+// the entry's W subset sums (low pairs by mask, then high pairs by mask), each
+// added in increasing pair order and written with the slots innermost
+// (coalesced stores). Dynamic shared memory: the largest matrix of the launch
+// (order 2 stage_h) and its pair terms.
 __global__ void __launch_bounds__(256) pair_terms_kernel(const HafLaunch P) {
-  __shared__ double2 A[kMaxN * kMaxN];
+  extern __shared__ __align__(16) unsigned char psm[];
   __shared__ int rows[kMaxN];
   __shared__ int tri[kMaxN + 1];
+  const int nmax = 2 * P.stage_h;
+  double2* A = reinterpret_cast<double2*>(psm);  // nmax x nmax
+  double2* Q = A + nmax * nmax;                  // entries x pairs, pairs innermost
   const double2* src2 = reinterpret_cast<const double2*>(P.src);
   double2* pt2 = reinterpret_cast<double2*>(P.pt);
   for (int b = blockIdx.x; b < P.batch; b += gridDim.x) {
     const int64_t po = P.pt_off[b];
     const PatDesc d = P.pats[b];
     const int n = d.n, h = n >> 1;
-    if (po < 0 || pair_terms_elems(n) == 0) continue;  // uniform over the block
+    // uniform over the block; a matrix beyond the launch's order is not read
+    if (po < 0 || pair_terms_elems(n) == 0 || n > nmax) continue;
     if (threadIdx.x < n) {
       int pos = default_pos(threadIdx.x, h);
       if (P.perm != nullptr && P.perm_off[b] >= 0) pos = P.perm[P.perm_off[b] + threadIdx.x];
@@ -965,18 +983,36 @@ __global__ void __launch_bounds__(256) pair_terms_kernel(const HafLaunch P) {
       A[e] = (i == j) ? make_double2(0.0, 0.0) : __ldg(src2 + d.src_off + (int64_t)rows[i] * d.ld + rows[j]);
     }
     __syncthreads();
-    const int total = (n * (n + 1) / 2) * h;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int NPn = n * (n + 1) / 2;
+    for (int t = threadIdx.x; t < NPn * h; t += blockDim.x) {
       const int e = t / h, p = t - e * h;
       int i = 0;
       while (tri[i + 1] <= e) ++i;
       const int j = i + (e - tri[i]);
-      const double2 a1 = A[i * n + 2 * p], b1 = A[(2 * p + 1) * n + j];
-      const double2 a2 = A[i * n + 2 * p + 1], b2 = A[2 * p * n + j];
       double2 q = make_double2(0.0, 0.0);
-      q = cfma<double>(a1, b1, q);
-      q = cfma<double>(a2, b2, q);
-      pt2[po + t] = q;
+      q = cfma<double>(A[i * n + 2 * p], A[(2 * p + 1) * n + j], q);
+      q = cfma<double>(A[i * n + 2 * p + 1], A[2 * p * n + j], q);
+      Q[t] = q;
+    }
+    __syncthreads();
+    const int hl = pair_split_lo(h), W = pair_sums_width(h);
+    for (int t = threadIdx.x; t < NPn * W; t += blockDim.x) {
+      const int e = t / W, k = t - e * W;
+      const bool lo = k < (1 << hl);
+      unsigned m = lo ? (unsigned)k : (unsigned)(k - (1 << hl));
+      const double2* qe = Q + e * h + (lo ? 0 : hl);
+      double2 acc = make_double2(0.0, 0.0);
+      if (m) {
+        acc = qe[__ffs(m) - 1];
+        m &= m - 1;
+        while (m) {
+          const double2 v = qe[__ffs(m) - 1];
+          acc.x += v.x;
+          acc.y += v.y;
+          m &= m - 1;
+        }
+      }
+      pt2[po + t] = acc;
     }
     __syncthreads();
   }
@@ -1024,8 +1060,8 @@ __global__ void pairing_select_kernel(const PairingSelect S) {
     const int q = k * S.n_cand + lane;
     const PatDesc d = S.probe_pats[q];
     est = 0.0;
-#pragma unroll 4
     const int h = min(max(d.n >> 1, 0), kMaxH);
+#pragma unroll 4
     for (int it = d.item_begin; it < d.item_end; ++it) {
       const WorkItem w = S.probe_items[it];
       const double kp = S.probe_parts[it].kappa;
@@ -1226,10 +1262,25 @@ cudaError_t launch_pairing_select(const PairingSelect& S, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Dynamic shared memory of the pair-sum kernel for matrices up to order n:
+// the staged matrix and its pair terms.
+static int pair_terms_smem(int n) { return 16 * (n * n + (n * (n + 1) / 2) * (n / 2)); }
+
 cudaError_t launch_pair_terms(const HafLaunch& L, cudaStream_t st) {
   if (L.pt == nullptr || L.batch <= 0) return cudaSuccess;
+  if (2 * L.stage_h > kMaxN) return cudaErrorInvalidValue;
+  // raised once to the largest order's need (per device), never lowered
+  static std::atomic<int> raised[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !raised[dev].load()) {
+    const cudaError_t e = cudaFuncSetAttribute(pair_terms_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               pair_terms_smem(kMaxN));
+    if (e != cudaSuccess) return e;
+    raised[dev].store(1);
+  }
   int blocks = L.batch < 4096 ? L.batch : 4096;
-  pair_terms_kernel<<<blocks, 256, 0, st>>>(L);
+  pair_terms_kernel<<<blocks, 256, pair_terms_smem(2 * L.stage_h), st>>>(L);
   return cudaGetLastError();
 }
 
@@ -1259,6 +1310,7 @@ static cudaError_t ensure_smem_limit(int precision) {
 
 cudaError_t launch_haf_subsets(const HafLaunch& L, int precision, int blocks, int warps_per_block,
                                cudaStream_t st) {
+  if (warps_per_block < 1 || warps_per_block > kMaxWarpsPerBlock) return cudaErrorInvalidValue;
   const size_t smem = (size_t)warps_per_block * L.warp_bytes;
   cudaError_t e = ensure_smem_limit(precision);
   if (e != cudaSuccess) return e;

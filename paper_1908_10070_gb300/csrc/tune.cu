@@ -79,6 +79,7 @@ extern "C" int gbs_autotune(int n, int precision, void* stream, int* chosen_out)
   // take about 45 KB a warp)
   const int wpbs[] = {4, 5, 6, 8, 10, 12};
   const int n_wpbs = (int)(sizeof(wpbs) / sizeof(wpbs[0]));
+  static_assert(12 <= kMaxWarpsPerBlock, "a tuner shape exceeds the kernel's launch bounds");
   const int rnds[] = {1, 2, 4, 8, 16};
   TuneCfg best = default_cfg(precision, n);
   float best_ms = 1e30f;
