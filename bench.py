@@ -519,7 +519,8 @@ def serve_stream(gbs, K, reqs, precision):
             "step_device_max_ms": 1e3 * st["step_device_max_s"],
             # the server thread's longest pause between loop iterations or polls,
             # and its longest step launch call
-            "poll_gap_max_ms": 1e3 * st["poll_gap_max_s"], "launch_max_ms": 1e3 * st["launch_max_s"]}
+            "poll_gap_max_ms": 1e3 * st["poll_gap_max_s"], "launch_max_ms": 1e3 * st["launch_max_s"],
+            "update_max_ms": 1e3 * st["update_max_s"], "submit_max_ms": 1e3 * st["submit_max_s"]}
 
 
 def per_pattern_stream(gbs, K, reqs):

@@ -296,7 +296,10 @@ typedef struct gbs_serve_stats_t {
   double poll_gap_max_s;  /* longest interval, while a step was in flight, between two
                              runs of the server thread's loop or completion polls
                              (large: the thread was not running) */
-  double launch_max_s;    /* longest call that launches a step */
+  double launch_max_s;    /* longest call that launches a step, of which: */
+  double update_max_s;    /* longest update of a step graph's parameters */
+  double submit_max_s;    /* longest submission of a step (graph launch, or the
+                             direct copies and launches without graphs) */
 } gbs_serve_stats_t;
 int gbs_serve_stats(gbs_server* s, gbs_serve_stats_t* out);
 

@@ -44,7 +44,8 @@ class ServeStats(ctypes.Structure):
                 ("completed", ctypes.c_int64), ("step_wall_s", ctypes.c_double),
                 ("step_wall_max_s", ctypes.c_double), ("step_device_s", ctypes.c_double),
                 ("step_device_max_s", ctypes.c_double), ("poll_gap_max_s", ctypes.c_double),
-                ("launch_max_s", ctypes.c_double)]
+                ("launch_max_s", ctypes.c_double), ("update_max_s", ctypes.c_double),
+                ("submit_max_s", ctypes.c_double)]
 
 
 class ServeOpts(ctypes.Structure):

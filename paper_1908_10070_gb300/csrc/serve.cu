@@ -336,8 +336,16 @@ cudaError_t build_graph(gbs_server* s, Stage& g) {
 }
 
 // Launch one prepared stage, with the graph (parameters updated) or directly.
+// The longest parameter update (graph path) and the longest submission are
+// kept in the stats.
+void note_max(double& m, std::chrono::steady_clock::time_point t0) {
+  const double d = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (d > m) m = d;
+}
+
 cudaError_t launch_stage(gbs_server* s, Stage& g) {
   const int S = s->o.max_slots;
+  auto t0 = std::chrono::steady_clock::now();
   cudaError_t e = cudaEventRecord(g.ev0, s->st);
   if (e != cudaSuccess) return e;
   if (s->o.use_graphs) {
@@ -382,7 +390,10 @@ cudaError_t launch_stage(gbs_server* s, Stage& g) {
       e = cudaGraphExecKernelNodeSetParams(g.exec, g.nd_fin, &kp);
       if (e != cudaSuccess) return e;
     }
+    note_max(s->stats.update_max_s, t0);
+    t0 = std::chrono::steady_clock::now();
     e = cudaGraphLaunch(g.exec, s->st);
+    note_max(s->stats.submit_max_s, t0);
     if (e != cudaSuccess) return e;
   } else {
     e = cudaMemcpyAsync(s->d_pats, g.h_up + s->off_pats, sizeof(PatDesc) * S, cudaMemcpyHostToDevice, s->st);
@@ -410,6 +421,7 @@ cudaError_t launch_stage(gbs_server* s, Stage& g) {
       e = cudaMemcpyAsync(g.h_res, g.d_res, sizeof(double) * 5 * S, cudaMemcpyDeviceToHost, s->st);
       if (e != cudaSuccess) return e;
     }
+    note_max(s->stats.submit_max_s, t0);
   }
   return cudaEventRecord(g.ev, s->st);
 }
