@@ -35,7 +35,7 @@ import workloads as W  # noqa: E402
 # headline workload, from one ncu capture (profiles/haf_subsets_fp64_m64_n16.md).
 # Reported only while the kernel's sources are the ones the capture was taken
 # from; any change to them makes the figure stale and the bench reports null.
-NCU_TRAFFIC = {"sources_sha256": "c8c11fef7f5131a831439723f6030a2fc6d8c3b6f88c80ae7076bd34c1423730", "bytes_per_launch": 328511232.0,
+NCU_TRAFFIC = {"sources_sha256": "c83819b914cad9e84c41f07e6d3473c62ba573a3956f41a5da602d45db3d9372", "bytes_per_launch": 326200576.0,
                # executed FP64 flops per cycle (DFMA x 2 + DADD + DMUL) over the 608 peak
                "executed_fp64_frac": 0.817}
 KERNEL_SOURCES = ("paper_1908_10070_gb300/csrc/haf_subsets.cu", "paper_1908_10070_gb300/csrc/gbs_internal.cuh")

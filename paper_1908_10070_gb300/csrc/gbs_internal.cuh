@@ -115,8 +115,9 @@ struct HafLaunch {
   const float* src32;      // the same rounded to float (FP32 path; may be null)
   const int* idx;          // index lists (may be null when every idx_off < 0)
   const PatDesc* pats;
-  const WorkItem* items;   // in schedule order
+  const WorkItem* items;   // in schedule order (device or mapped host memory)
   int n_items;
+  const int* n_items_dev;  // if non-null, the item count is read here (device memory)
   int m_bound;             // index lists must be < m_bound (0 = no check)
   int* counter;            // work-queue head, zero before launch
   int* status;             // per-pattern flag, set to 1 on an out-of-range index
@@ -153,6 +154,7 @@ struct ChunkLaunch {
 
 struct FinalizeLaunch {
   const int* sel;          // if non-null, entry b finalises pattern sel[b] (outputs at b)
+  const int* batch_dev;    // if non-null, the number of entries is read here (device memory)
   const Partial* chunk_parts;  // if non-null, sum these chunk sums (chunk_off ranges) instead
   const int* chunk_off;
   const PatDesc* pats;

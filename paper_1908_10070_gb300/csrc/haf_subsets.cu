@@ -503,6 +503,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) haf_subsets_kernel(
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int cb = (int)sizeof(C);
+  const int n_items = P.n_items_dev ? *P.n_items_dev : P.n_items;
   unsigned char* wbase = smem + (size_t)warp * P.warp_bytes;
   int* xs = reinterpret_cast<int*>(wbase);
   // staging: the power traces of up to 32 finished subsets, their signs and orders
@@ -515,7 +516,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) haf_subsets_kernel(
     int it = 0;
     if (lane == 0) it = atomicAdd(P.counter, 1);
     it = __shfl_sync(FULL, it, 0);
-    if (it >= P.n_items) break;
+    if (it >= n_items) break;
     const WorkItem w = P.items[it];
     const PatDesc d = P.pats[w.pat];
     const int n = d.n, h = n >> 1;
@@ -883,9 +884,10 @@ __global__ void __launch_bounds__(kFinWarps * 32) finalize_kernel(const Finalize
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
   const bool want_p = F.p_out || F.logp_out || F.err_out;
-  for (int base = blockIdx.x * wpb; base < F.batch; base += gridDim.x * wpb) {
+  const int batch = F.batch_dev ? *F.batch_dev : F.batch;
+  for (int base = blockIdx.x * wpb; base < batch; base += gridDim.x * wpb) {
     const int b = base + warp;
-    if (b < F.batch) {  // uniform over the warp
+    if (b < batch) {  // uniform over the warp
       const int pb = F.sel ? F.sel[b] : b;
       const PatDesc d = F.pats[pb];
       const int n = d.n;
@@ -918,7 +920,7 @@ __global__ void __launch_bounds__(kFinWarps * 32) finalize_kernel(const Finalize
       }
     }
     __syncthreads();
-    if (warp == 0 && lane < wpb && base + lane < F.batch) {
+    if (warp == 0 && lane < wpb && base + lane < batch) {
       const int bo = base + lane;
       const int pb = F.sel ? F.sel[bo] : bo;
       const int n = F.pats[pb].n;
@@ -947,28 +949,31 @@ __global__ void __launch_bounds__(kFinWarps * 32) finalize_kernel(const Finalize
   }
 }
 
-// Pair sums of one matrix per block. The zero-diagonal matrix is staged in
-// shared memory, then every pair term Q_p(e) = A(i, 2p) A(2p+1, j) +
-// A(i, 2p+1) A(2p, j) of every packed upper entry e = (i, j), and from those
-// the entry's W subset sums (low pairs by mask, then high pairs by mask), each
-// added in increasing pair order and written with the slots innermost
-// (coalesced stores). Dynamic shared memory: the largest matrix of the launch
-// (order 2 stage_h) and its pair terms.
+// Pair sums, one block per chunk of kPairChunk packed entries of a matrix (a
+// lone matrix spreads over several SMs). The block stages the zero-diagonal
+// matrix in shared memory, then the pair terms Q_p(e) = A(i, 2p) A(2p+1, j) +
+// A(i, 2p+1) A(2p, j) of its entries e = (i, j), and from those each entry's W
+// subset sums (low pairs by mask, then high pairs by mask), each added in
+// increasing pair order and written with the slots innermost (coalesced).
+constexpr int kPairChunk = 32;
 __global__ void __launch_bounds__(256) pair_terms_kernel(const HafLaunch P) {
-  extern __shared__ __align__(16) unsigned char psm[];
+  __shared__ double2 A[kMaxN * kMaxN];
+  __shared__ double2 Q[kPairChunk * kMaxH];  // entries x pairs, pairs innermost
   __shared__ int rows[kMaxN];
   __shared__ int tri[kMaxN + 1];
-  const int nmax = 2 * P.stage_h;
-  double2* A = reinterpret_cast<double2*>(psm);  // nmax x nmax
-  double2* Q = A + nmax * nmax;                  // entries x pairs, pairs innermost
   const double2* src2 = reinterpret_cast<const double2*>(P.src);
   double2* pt2 = reinterpret_cast<double2*>(P.pt);
-  for (int b = blockIdx.x; b < P.batch; b += gridDim.x) {
+  const int nmax = 2 * P.stage_h;
+  const int cpm = (nmax * (nmax + 1) / 2 + kPairChunk - 1) / kPairChunk;  // chunks per matrix
+  const int64_t n_chunks = (int64_t)P.batch * cpm;
+  for (int64_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+    const int b = (int)(c / cpm), e0 = (int)(c - (int64_t)b * cpm) * kPairChunk;
     const int64_t po = P.pt_off[b];
     const PatDesc d = P.pats[b];
-    const int n = d.n, h = n >> 1;
+    const int n = d.n, h = n >> 1, NPn = n * (n + 1) / 2;
     // uniform over the block; a matrix beyond the launch's order is not read
-    if (po < 0 || pair_terms_elems(n) == 0 || n > nmax) continue;
+    if (po < 0 || pair_terms_elems(n) == 0 || n > nmax || e0 >= NPn) continue;
+    const int ne = min(kPairChunk, NPn - e0);
     if (threadIdx.x < n) {
       int pos = default_pos(threadIdx.x, h);
       if (P.perm != nullptr && P.perm_off[b] >= 0) pos = P.perm[P.perm_off[b] + threadIdx.x];
@@ -983,9 +988,8 @@ __global__ void __launch_bounds__(256) pair_terms_kernel(const HafLaunch P) {
       A[e] = (i == j) ? make_double2(0.0, 0.0) : __ldg(src2 + d.src_off + (int64_t)rows[i] * d.ld + rows[j]);
     }
     __syncthreads();
-    const int NPn = n * (n + 1) / 2;
-    for (int t = threadIdx.x; t < NPn * h; t += blockDim.x) {
-      const int e = t / h, p = t - e * h;
+    for (int t = threadIdx.x; t < ne * h; t += blockDim.x) {
+      const int el = t / h, p = t - el * h, e = e0 + el;
       int i = 0;
       while (tri[i + 1] <= e) ++i;
       const int j = i + (e - tri[i]);
@@ -996,11 +1000,12 @@ __global__ void __launch_bounds__(256) pair_terms_kernel(const HafLaunch P) {
     }
     __syncthreads();
     const int hl = pair_split_lo(h), W = pair_sums_width(h);
-    for (int t = threadIdx.x; t < NPn * W; t += blockDim.x) {
-      const int e = t / W, k = t - e * W;
+    double2* out = pt2 + po + (int64_t)e0 * W;
+    for (int t = threadIdx.x; t < ne * W; t += blockDim.x) {
+      const int el = t / W, k = t - el * W;
       const bool lo = k < (1 << hl);
       unsigned m = lo ? (unsigned)k : (unsigned)(k - (1 << hl));
-      const double2* qe = Q + e * h + (lo ? 0 : hl);
+      const double2* qe = Q + el * h + (lo ? 0 : hl);
       double2 acc = make_double2(0.0, 0.0);
       if (m) {
         acc = qe[__ffs(m) - 1];
@@ -1012,7 +1017,7 @@ __global__ void __launch_bounds__(256) pair_terms_kernel(const HafLaunch P) {
           m &= m - 1;
         }
       }
-      pt2[po + t] = acc;
+      out[t] = acc;
     }
     __syncthreads();
   }
@@ -1262,25 +1267,13 @@ cudaError_t launch_pairing_select(const PairingSelect& S, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// Dynamic shared memory of the pair-sum kernel for matrices up to order n:
-// the staged matrix and its pair terms.
-static int pair_terms_smem(int n) { return 16 * (n * n + (n * (n + 1) / 2) * (n / 2)); }
-
 cudaError_t launch_pair_terms(const HafLaunch& L, cudaStream_t st) {
   if (L.pt == nullptr || L.batch <= 0) return cudaSuccess;
   if (2 * L.stage_h > kMaxN) return cudaErrorInvalidValue;
-  // raised once to the largest order's need (per device), never lowered
-  static std::atomic<int> raised[64];
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !raised[dev].load()) {
-    const cudaError_t e = cudaFuncSetAttribute(pair_terms_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               pair_terms_smem(kMaxN));
-    if (e != cudaSuccess) return e;
-    raised[dev].store(1);
-  }
-  int blocks = L.batch < 4096 ? L.batch : 4096;
-  pair_terms_kernel<<<blocks, 256, pair_terms_smem(2 * L.stage_h), st>>>(L);
+  const int nmax = 2 * L.stage_h;
+  const int64_t chunks = (int64_t)L.batch * ((nmax * (nmax + 1) / 2 + kPairChunk - 1) / kPairChunk);
+  const int blocks = (int)std::min<int64_t>(chunks, 16384);
+  pair_terms_kernel<<<blocks, 256, 0, st>>>(L);
   return cudaGetLastError();
 }
 

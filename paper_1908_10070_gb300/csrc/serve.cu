@@ -15,8 +15,11 @@
 // bit-for-bit the same whether it runs alone or among others.
 //
 // Steps are double-buffered (the host builds step k+1 while step k runs) and,
-// by default, replayed as one instantiated CUDA graph per buffer whose node
-// parameters (item counts, copy sizes, grid sizes) are updated before each
+// by default, replayed as one instantiated CUDA graph per buffer. The graphs
+// never change: a step's item and finalisation counts travel in a small header
+// copied by the graph, the kernels read the step's items in place from the
+// buffer's pinned (device-mapped) memory and exit at once when a count is
+// zero, and the grids are the largest a step can use. A step is one graph
 // launch. Every wait on the device is a bounded poll: past wait_timeout_s the
 // server fails the outstanding requests with GBS_ETIMEDOUT and stops.
 #include <math.h>
@@ -103,13 +106,15 @@ struct Slot {
 constexpr int kStepCap = 65536;  // work items per precision per step
 
 struct Stage {
-  // pinned host: slot tables, items (2 precisions), selection list; results
+  // pinned host: slot tables, items (2 precisions), selection list, step
+  // header (item counts, finalisation count); results
   unsigned char* h_up = nullptr;
+  unsigned char* h_up_dev = nullptr;  // the same memory as the device sees it
   double* h_res = nullptr;
   // device
   WorkItem* d_items[2] = {nullptr, nullptr};
   int* d_sel = nullptr;
-  int* d_ctr = nullptr;
+  int* d_ctr = nullptr;  // [0..1] queue heads, [2..4] the step header (graph path)
   double* d_res = nullptr;
   cudaEvent_t ev = nullptr;   // the step's end
   cudaEvent_t ev0 = nullptr;  // its start on the stream (device time = ev - ev0)
@@ -121,9 +126,9 @@ struct Stage {
   // graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  cudaGraphNode_t nd_pats = nullptr, nd_idx = nullptr, nd_items[2] = {nullptr, nullptr},
-                  nd_ctr = nullptr, nd_k[2] = {nullptr, nullptr}, nd_sel = nullptr, nd_fin = nullptr,
-                  nd_res = nullptr;
+  cudaGraphNode_t nd_ev0 = nullptr, nd_pats = nullptr, nd_idx = nullptr, nd_hdr = nullptr, nd_ctr = nullptr,
+                  nd_k[2] = {nullptr, nullptr}, nd_sel = nullptr, nd_fin = nullptr, nd_res = nullptr,
+                  nd_ev = nullptr;
 };
 
 }  // namespace
@@ -160,7 +165,7 @@ struct gbs_server {
   Partial* d_parts = nullptr;
   std::vector<PatDesc> h_pats;
   std::vector<int> h_idx;
-  size_t off_pats = 0, off_idx = 0, off_items[2] = {0, 0}, off_sel = 0, up_bytes = 0;
+  size_t off_pats = 0, off_idx = 0, off_items[2] = {0, 0}, off_sel = 0, off_hdr = 0, up_bytes = 0;
   Stage stage[2];
   std::thread th;
   gbs_serve_stats_t stats;
@@ -204,15 +209,24 @@ void request_items(const gbs_server* s, int si, int n, int prec, std::vector<Wor
   }
 }
 
-HafLaunch make_launch(gbs_server* s, Stage& g, int prec) {
+// Launch arguments of a stage's subset kernel. In the step graph the kernel
+// reads its items in place from the stage's pinned buffer and their count from
+// the step header, so the graph's parameters never change between steps;
+// direct launches pass the uploaded items and the count itself.
+HafLaunch make_launch(gbs_server* s, Stage& g, int prec, bool graph) {
   HafLaunch L;
   memset(&L, 0, sizeof(L));
   L.src = s->k->B;
   L.src32 = (prec == GBS_MIXED) ? s->k->B32 : nullptr;
   L.idx = s->d_idx;
   L.pats = s->d_pats;
-  L.items = g.d_items[prec];
-  L.n_items = g.n_items[prec];
+  if (graph) {
+    L.items = (const WorkItem*)(g.h_up_dev + s->off_items[prec]);
+    L.n_items_dev = g.d_ctr + 2 + prec;
+  } else {
+    L.items = g.d_items[prec];
+    L.n_items = g.n_items[prec];
+  }
   L.m_bound = 0;  // indices are checked on submit
   L.counter = g.d_ctr + prec;
   L.status = nullptr;
@@ -222,7 +236,7 @@ HafLaunch make_launch(gbs_server* s, Stage& g, int prec) {
   return L;
 }
 
-FinalizeLaunch make_finalize(gbs_server* s, Stage& g) {
+FinalizeLaunch make_finalize(gbs_server* s, Stage& g, bool graph) {
   const int S = s->o.max_slots;
   FinalizeLaunch F;
   memset(&F, 0, sizeof(F));
@@ -231,7 +245,10 @@ FinalizeLaunch make_finalize(gbs_server* s, Stage& g) {
   F.parts = s->d_parts;
   F.idx = s->d_idx;
   F.status = nullptr;
-  F.batch = (int)g.fin.size();
+  if (graph)
+    F.batch_dev = g.d_ctr + 4;
+  else
+    F.batch = (int)g.fin.size();
   F.precision = GBS_FP64;
   F.log_norm = s->k->dscal;
   F.p_out = g.d_res;
@@ -249,7 +266,11 @@ int grid_for(gbs_server* s, int prec, int n_items) {
   return b < 1 ? 1 : b;
 }
 
-// Build the graph of one stage (all nodes present; counts are set per step).
+// Build the graph of one stage. Every node is fixed: the per-step counts
+// travel in the step header (copied into d_ctr[2..4]), the kernels read their
+// items from the stage's pinned buffer and exit at once when a count is zero,
+// and the grids are the largest a step can use. A step is then one graph
+// launch, with no parameter update.
 cudaError_t build_graph(gbs_server* s, Stage& g) {
   cudaError_t e = cudaGraphCreate(&g.graph, 0);
   if (e != cudaSuccess) return e;
@@ -264,6 +285,10 @@ cudaError_t build_graph(gbs_server* s, Stage& g) {
   };
   cudaGraphNode_t deps[1];
   size_t nd;
+  // the step's start and end events are nodes of the graph too
+  e = cudaGraphAddEventRecordNode(&g.nd_ev0, g.graph, nullptr, 0, g.ev0);
+  if (e != cudaSuccess) return e;
+  prev = g.nd_ev0;
   nd = dep(deps);
   e = cudaGraphAddMemcpyNode1D(&g.nd_pats, g.graph, deps, nd, s->d_pats, g.h_up + s->off_pats,
                                sizeof(PatDesc) * S, cudaMemcpyHostToDevice);
@@ -285,19 +310,18 @@ cudaError_t build_graph(gbs_server* s, Stage& g) {
   e = cudaGraphAddMemsetNode(&g.nd_ctr, g.graph, deps, nd, &mp);
   if (e != cudaSuccess) return e;
   prev = g.nd_ctr;
+  nd = dep(deps);
+  e = cudaGraphAddMemcpyNode1D(&g.nd_hdr, g.graph, deps, nd, g.d_ctr + 2, g.h_up + s->off_hdr, sizeof(int) * 3,
+                               cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  prev = g.nd_hdr;
   for (int p = 0; p < 2; ++p) {
-    nd = dep(deps);
-    e = cudaGraphAddMemcpyNode1D(&g.nd_items[p], g.graph, deps, nd, g.d_items[p],
-                                 g.h_up + s->off_items[p], sizeof(WorkItem), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return e;
-    prev = g.nd_items[p];
-    g.n_items[p] = 1;
-    HafLaunch L = make_launch(s, g, p);
+    HafLaunch L = make_launch(s, g, p, true);
     void* args[1] = {&L};
     cudaKernelNodeParams kp;
     memset(&kp, 0, sizeof(kp));
     kp.func = (void*)haf_kernel_fn(p);
-    kp.gridDim = dim3(1);
+    kp.gridDim = dim3(s->blocks_max[p]);
     kp.blockDim = dim3(s->cfg[p].warps_per_block * 32);
     kp.sharedMemBytes = s->cfg[p].warps_per_block * s->cfg[p].warp_bytes;
     kp.kernelParams = args;
@@ -312,13 +336,12 @@ cudaError_t build_graph(gbs_server* s, Stage& g) {
   if (e != cudaSuccess) return e;
   prev = g.nd_sel;
   {
-    g.fin.assign(1, 0);
-    FinalizeLaunch F = make_finalize(s, g);
+    FinalizeLaunch F = make_finalize(s, g, true);
     void* args[1] = {&F};
     cudaKernelNodeParams kp;
     memset(&kp, 0, sizeof(kp));
     kp.func = (void*)finalize_kernel_fn();
-    kp.gridDim = dim3(1);
+    kp.gridDim = dim3((unsigned)((S + 3) / 4));
     kp.blockDim = dim3(128);
     kp.sharedMemBytes = 0;
     kp.kernelParams = args;
@@ -326,16 +349,20 @@ cudaError_t build_graph(gbs_server* s, Stage& g) {
     e = cudaGraphAddKernelNode(&g.nd_fin, g.graph, deps, nd, &kp);
     if (e != cudaSuccess) return e;
     prev = g.nd_fin;
-    g.fin.clear();
   }
   nd = dep(deps);
   e = cudaGraphAddMemcpyNode1D(&g.nd_res, g.graph, deps, nd, g.h_res, g.d_res, sizeof(double) * 5 * S,
                                cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return e;
+  prev = g.nd_res;
+  nd = dep(deps);
+  e = cudaGraphAddEventRecordNode(&g.nd_ev, g.graph, deps, nd, g.ev);
+  if (e != cudaSuccess) return e;
   return cudaGraphInstantiate(&g.exec, g.graph, 0);
 }
 
-// Launch one prepared stage, with the graph (parameters updated) or directly.
+// Launch one prepared stage: the step header and one graph launch, or direct
+// copies and launches.
 // The longest parameter update (graph path) and the longest submission are
 // kept in the stats.
 void note_max(double& m, std::chrono::steady_clock::time_point t0) {
@@ -346,56 +373,22 @@ void note_max(double& m, std::chrono::steady_clock::time_point t0) {
 cudaError_t launch_stage(gbs_server* s, Stage& g) {
   const int S = s->o.max_slots;
   auto t0 = std::chrono::steady_clock::now();
-  cudaError_t e = cudaEventRecord(g.ev0, s->st);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
   if (s->o.use_graphs) {
-    for (int p = 0; p < 2; ++p) {
-      const bool on = g.n_items[p] > 0;
-      e = cudaGraphNodeSetEnabled(g.exec, g.nd_items[p], on);
-      if (e != cudaSuccess) return e;
-      e = cudaGraphNodeSetEnabled(g.exec, g.nd_k[p], on);
-      if (e != cudaSuccess) return e;
-      if (!on) continue;
-      e = cudaGraphExecMemcpyNodeSetParams1D(g.exec, g.nd_items[p], g.d_items[p], g.h_up + s->off_items[p],
-                                             sizeof(WorkItem) * g.n_items[p], cudaMemcpyHostToDevice);
-      if (e != cudaSuccess) return e;
-      HafLaunch L = make_launch(s, g, p);
-      void* args[1] = {&L};
-      cudaKernelNodeParams kp;
-      memset(&kp, 0, sizeof(kp));
-      kp.func = (void*)haf_kernel_fn(p);
-      kp.gridDim = dim3(grid_for(s, p, g.n_items[p]));
-      kp.blockDim = dim3(s->cfg[p].warps_per_block * 32);
-      kp.sharedMemBytes = s->cfg[p].warps_per_block * s->cfg[p].warp_bytes;
-      kp.kernelParams = args;
-      e = cudaGraphExecKernelNodeSetParams(g.exec, g.nd_k[p], &kp);
-      if (e != cudaSuccess) return e;
-    }
-    const bool fon = !g.fin.empty();
-    e = cudaGraphNodeSetEnabled(g.exec, g.nd_sel, fon);
-    if (e != cudaSuccess) return e;
-    e = cudaGraphNodeSetEnabled(g.exec, g.nd_fin, fon);
-    if (e != cudaSuccess) return e;
-    e = cudaGraphNodeSetEnabled(g.exec, g.nd_res, fon);
-    if (e != cudaSuccess) return e;
-    if (fon) {
-      FinalizeLaunch F = make_finalize(s, g);
-      void* args[1] = {&F};
-      cudaKernelNodeParams kp;
-      memset(&kp, 0, sizeof(kp));
-      kp.func = (void*)finalize_kernel_fn();
-      kp.gridDim = dim3((unsigned)((g.fin.size() + 3) / 4));
-      kp.blockDim = dim3(128);
-      kp.kernelParams = args;
-      e = cudaGraphExecKernelNodeSetParams(g.exec, g.nd_fin, &kp);
-      if (e != cudaSuccess) return e;
-    }
+    // the whole step, its two events included, is one graph launch
+    int* hdr = (int*)(g.h_up + s->off_hdr);
+    hdr[0] = g.n_items[0];
+    hdr[1] = g.n_items[1];
+    hdr[2] = (int)g.fin.size();
     note_max(s->stats.update_max_s, t0);
     t0 = std::chrono::steady_clock::now();
     e = cudaGraphLaunch(g.exec, s->st);
     note_max(s->stats.submit_max_s, t0);
-    if (e != cudaSuccess) return e;
-  } else {
+    return e;
+  }
+  e = cudaEventRecord(g.ev0, s->st);
+  if (e != cudaSuccess) return e;
+  {
     e = cudaMemcpyAsync(s->d_pats, g.h_up + s->off_pats, sizeof(PatDesc) * S, cudaMemcpyHostToDevice, s->st);
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(s->d_idx, g.h_up + s->off_idx, sizeof(int) * GBS_MAX_N * S, cudaMemcpyHostToDevice,
@@ -408,7 +401,7 @@ cudaError_t launch_stage(gbs_server* s, Stage& g) {
       e = cudaMemcpyAsync(g.d_items[p], g.h_up + s->off_items[p], sizeof(WorkItem) * g.n_items[p],
                           cudaMemcpyHostToDevice, s->st);
       if (e != cudaSuccess) return e;
-      e = launch_haf_subsets(make_launch(s, g, p), p, grid_for(s, p, g.n_items[p]),
+      e = launch_haf_subsets(make_launch(s, g, p, false), p, grid_for(s, p, g.n_items[p]),
                              s->cfg[p].warps_per_block, s->st);
       if (e != cudaSuccess) return e;
     }
@@ -416,7 +409,7 @@ cudaError_t launch_stage(gbs_server* s, Stage& g) {
       e = cudaMemcpyAsync(g.d_sel, g.h_up + s->off_sel, sizeof(int) * g.fin.size(), cudaMemcpyHostToDevice,
                           s->st);
       if (e != cudaSuccess) return e;
-      e = launch_finalize(make_finalize(s, g), s->st);
+      e = launch_finalize(make_finalize(s, g, false), s->st);
       if (e != cudaSuccess) return e;
       e = cudaMemcpyAsync(g.h_res, g.d_res, sizeof(double) * 5 * S, cudaMemcpyDeviceToHost, s->st);
       if (e != cudaSuccess) return e;
@@ -720,7 +713,8 @@ extern "C" int gbs_serve_create(const gbs_kernel* k, const gbs_serve_opts* opts,
     s->off_items[0] = s->off_idx + al(sizeof(int) * GBS_MAX_N * S);
     s->off_items[1] = s->off_items[0] + al(sizeof(WorkItem) * kStepCap);
     s->off_sel = s->off_items[1] + al(sizeof(WorkItem) * kStepCap);
-    s->up_bytes = s->off_sel + al(sizeof(int) * S);
+    s->off_hdr = s->off_sel + al(sizeof(int) * S);
+    s->up_bytes = s->off_hdr + al(sizeof(int) * 3);
     for (int i = 0; i < 2 && ret == GBS_OK; ++i) {
       Stage& g = s->stage[i];
       if ((e = cudaMallocHost(&g.h_up, s->up_bytes)) != cudaSuccess ||
@@ -736,6 +730,11 @@ extern "C" int gbs_serve_create(const gbs_kernel* k, const gbs_serve_opts* opts,
       }
       memset(g.h_up, 0, s->up_bytes);
       g.d_items[1] = (WorkItem*)((unsigned char*)g.d_items[0] + al(sizeof(WorkItem) * kStepCap));
+      if ((e = cudaHostGetDevicePointer((void**)&g.h_up_dev, g.h_up, 0)) != cudaSuccess) {
+        cudaGetLastError();
+        ret = fail(GBS_ECUDA, "pinned step buffer not mapped: %s", cudaGetErrorString(e));
+        break;
+      }
       if (s->o.use_graphs) {
         e = build_graph(s, g);
         if (e != cudaSuccess) {
