@@ -35,9 +35,9 @@ import workloads as W  # noqa: E402
 # headline workload, from one ncu capture (profiles/haf_subsets_fp64_m64_n16.md).
 # Reported only while the kernel's sources are the ones the capture was taken
 # from; any change to them makes the figure stale and the bench reports null.
-NCU_TRAFFIC = {"sources_sha256": "c83819b914cad9e84c41f07e6d3473c62ba573a3956f41a5da602d45db3d9372", "bytes_per_launch": 326200576.0,
+NCU_TRAFFIC = {"sources_sha256": "3541a8da03554ba3638c96b5d418d9c4a70c4d31c6e6c3e1b8caca761bb6b5b6", "bytes_per_launch": 329142016.0,
                # executed FP64 flops per cycle (DFMA x 2 + DADD + DMUL) over the 608 peak
-               "executed_fp64_frac": 0.817}
+               "executed_fp64_frac": 0.816}
 KERNEL_SOURCES = ("paper_1908_10070_gb300/csrc/haf_subsets.cu", "paper_1908_10070_gb300/csrc/gbs_internal.cuh")
 
 

@@ -484,7 +484,11 @@ __device__ __forceinline__ float2 tr2sq_full(const float2* __restrict__ Ra, int 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, 1) haf_subsets_kernel(const HafLaunch P) {
+// Launch bounds: the double instance names its largest block (12 warps), which
+// lets it keep up to 170 registers a thread; the float instance is held to 128
+// (it runs faster with a small spill than with 150 registers and no spill).
+__global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512, 1)
+    haf_subsets_kernel(const HafLaunch P) {
   typedef C2<T> C;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Tables tab;
