@@ -187,6 +187,27 @@ __device__ __forceinline__ C2<T> group_sum(C2<T> v, int L) {
   return v;
 }
 
+// Sums over the L >= 2 lanes of a group of two values at once: at the first
+// level (offset L/2) each lane sends its partner the value the partner keeps,
+// so the lower half of the group carries a's partial sums and the upper half
+// b's; the remaining levels sum each within its half. Lane 0 of the group ends
+// with the total of a, lane L/2 with the total of b: one addition per level
+// for both values instead of one per level for each.
+template <typename T>
+__device__ __forceinline__ C2<T> group_sum2(C2<T> a, C2<T> b, int l, int L) {
+  const int half = L >> 1;
+  const bool up = (l & half) != 0;
+  const C2<T> send = up ? a : b;
+  C2<T> keep = up ? b : a;
+  keep.x += __shfl_xor_sync(0xffffffffu, send.x, half);
+  keep.y += __shfl_xor_sync(0xffffffffu, send.y, half);
+  for (int off = half >> 1; off > 0; off >>= 1) {
+    keep.x += __shfl_xor_sync(0xffffffffu, keep.x, off);
+    keep.y += __shfl_xor_sync(0xffffffffu, keep.y, off);
+  }
+  return keep;
+}
+
 // dst = Ra X Rb (upper triangle), X swapping 2t <-> 2t+1. Each lane takes
 // two output entries at a time (e and e + L) so that four independent FMA
 // chains are in flight.
@@ -712,7 +733,12 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
         }
       }
       __syncwarp();
-      // -- power traces tr((X A_S)^k), k = 1..hs, by the schedule for hs
+      // -- power traces tr((X A_S)^k), k = 1..hs, by the schedule for hs; the
+      //    lanes' partial traces are summed over the group two traces at a
+      //    time (one waits in registers for the next)
+      C pend_v = mk<T>(T(0), T(0));
+      int pend_k = 0;  // 0: none waiting
+      C* const strow = stP + (staged + g) * P.stage_h;
       for (int o = 0; o < kMaxOps; ++o) {
         const SchedOp op = c_sched[hs][o];
         if (op.kind == kEnd) break;
@@ -737,10 +763,23 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
             part = (op.kind == kTr1)  ? tr1_full(buf + op.a * NP, N, l, L)
                    : (op.a == op.b) ? tr2sq_full(buf + op.a * NP, N, l, L)
                                     : tr2_full(buf + op.a * NP, buf + op.b * NP, N, l, L);
-          const C t = group_sum<T>(part, L);
-          if (l == 0) stP[(staged + g) * P.stage_h + (op.k - 1)] = t;
+          if (L == 1) {
+            strow[op.k - 1] = part;
+          } else if (pend_k == 0) {
+            pend_v = part;
+            pend_k = op.k;
+          } else {
+            const C t = group_sum2<T>(pend_v, part, l, L);
+            if (l == 0) strow[pend_k - 1] = t;
+            if (l == (L >> 1)) strow[op.k - 1] = t;
+            pend_k = 0;
+          }
         }
         __syncwarp();
+      }
+      if (pend_k != 0) {  // uniform over the warp
+        const C t = group_sum<T>(pend_v, L);
+        if (l == 0) strow[pend_k - 1] = t;
       }
       // sign (-1)^{h-s} times the order N (0: no subset in this slot)
       if (l == 0) stF[staged + g] = active ? (((h - s) & 1) ? -N : N) : 0;

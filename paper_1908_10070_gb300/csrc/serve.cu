@@ -20,12 +20,15 @@
 // copied by the graph, the kernels read the step's items in place from the
 // buffer's pinned (device-mapped) memory and exit at once when a count is
 // zero, and the grids are the largest a step can use. A step is one graph
-// launch. Every wait on the device is a bounded poll: past wait_timeout_s the
-// server fails the outstanding requests with GBS_ETIMEDOUT and stops.
+// launch, and its last copy writes the step's number into pinned host memory,
+// which the server polls without a driver call. Every wait on the device is a
+// bounded poll: past wait_timeout_s the server fails the outstanding requests
+// with GBS_ETIMEDOUT and stops.
 #include <math.h>
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -110,11 +113,11 @@ struct Stage {
   // header (item counts, finalisation count); results
   unsigned char* h_up = nullptr;
   unsigned char* h_up_dev = nullptr;  // the same memory as the device sees it
-  double* h_res = nullptr;
+  double* h_res = nullptr;  // 5 S results, then the completion word (graph path)
   // device
   WorkItem* d_items[2] = {nullptr, nullptr};
   int* d_sel = nullptr;
-  int* d_ctr = nullptr;  // [0..1] queue heads, [2..4] the step header (graph path)
+  int* d_ctr = nullptr;  // [0..1] queue heads, [2..5] the step header (graph path)
   double* d_res = nullptr;
   cudaEvent_t ev = nullptr;   // the step's end
   cudaEvent_t ev0 = nullptr;  // its start on the stream (device time = ev - ev0)
@@ -128,7 +131,7 @@ struct Stage {
   cudaGraphExec_t exec = nullptr;
   cudaGraphNode_t nd_ev0 = nullptr, nd_pats = nullptr, nd_idx = nullptr, nd_hdr = nullptr, nd_ctr = nullptr,
                   nd_k[2] = {nullptr, nullptr}, nd_sel = nullptr, nd_fin = nullptr, nd_res = nullptr,
-                  nd_ev = nullptr;
+                  nd_done = nullptr, nd_ev = nullptr;
 };
 
 }  // namespace
@@ -311,7 +314,7 @@ cudaError_t build_graph(gbs_server* s, Stage& g) {
   if (e != cudaSuccess) return e;
   prev = g.nd_ctr;
   nd = dep(deps);
-  e = cudaGraphAddMemcpyNode1D(&g.nd_hdr, g.graph, deps, nd, g.d_ctr + 2, g.h_up + s->off_hdr, sizeof(int) * 3,
+  e = cudaGraphAddMemcpyNode1D(&g.nd_hdr, g.graph, deps, nd, g.d_ctr + 2, g.h_up + s->off_hdr, sizeof(int) * 4,
                                cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return e;
   prev = g.nd_hdr;
@@ -358,6 +361,14 @@ cudaError_t build_graph(gbs_server* s, Stage& g) {
   nd = dep(deps);
   e = cudaGraphAddEventRecordNode(&g.nd_ev, g.graph, deps, nd, g.ev);
   if (e != cudaSuccess) return e;
+  prev = g.nd_ev;
+  // the completion word last: the step's number, copied back after its results
+  // and its end event, so that the server sees a finished step without a
+  // driver call
+  nd = dep(deps);
+  e = cudaGraphAddMemcpyNode1D(&g.nd_done, g.graph, deps, nd, g.h_res + 5 * S, g.d_ctr + 5, sizeof(int),
+                               cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return e;
   return cudaGraphInstantiate(&g.exec, g.graph, 0);
 }
 
@@ -380,6 +391,7 @@ cudaError_t launch_stage(gbs_server* s, Stage& g) {
     hdr[0] = g.n_items[0];
     hdr[1] = g.n_items[1];
     hdr[2] = (int)g.fin.size();
+    hdr[3] = (int)(g.id & 0x7fffffff);  // comes back in the completion word
     note_max(s->stats.update_max_s, t0);
     t0 = std::chrono::steady_clock::now();
     e = cudaGraphLaunch(g.exec, s->st);
@@ -539,11 +551,20 @@ void tick(gbs_server* s) {
 
 bool wait_stage(gbs_server* s, Stage& g, bool block) {
   const auto t0 = std::chrono::steady_clock::now();
+  const int S = s->o.max_slots;
   for (;;) {
     tick(s);
-    const cudaError_t e = cudaEventQuery(g.ev);
-    if (e == cudaSuccess) return true;
-    if (e != cudaErrorNotReady) return false;
+    if (s->o.use_graphs) {
+      // the graph's last copy writes the step's number: no driver call here
+      if (*(volatile int*)(g.h_res + 5 * S) == (int)(g.id & 0x7fffffff)) {
+        std::atomic_thread_fence(std::memory_order_acquire);  // results before the word
+        return true;
+      }
+    } else {
+      const cudaError_t e = cudaEventQuery(g.ev);
+      if (e == cudaSuccess) return true;
+      if (e != cudaErrorNotReady) return false;
+    }
     if (!block) return false;
     const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (el > s->o.wait_timeout_s) return false;
@@ -714,11 +735,11 @@ extern "C" int gbs_serve_create(const gbs_kernel* k, const gbs_serve_opts* opts,
     s->off_items[1] = s->off_items[0] + al(sizeof(WorkItem) * kStepCap);
     s->off_sel = s->off_items[1] + al(sizeof(WorkItem) * kStepCap);
     s->off_hdr = s->off_sel + al(sizeof(int) * S);
-    s->up_bytes = s->off_hdr + al(sizeof(int) * 3);
+    s->up_bytes = s->off_hdr + al(sizeof(int) * 4);
     for (int i = 0; i < 2 && ret == GBS_OK; ++i) {
       Stage& g = s->stage[i];
       if ((e = cudaMallocHost(&g.h_up, s->up_bytes)) != cudaSuccess ||
-          (e = cudaMallocHost(&g.h_res, 5 * sizeof(double) * S)) != cudaSuccess ||
+          (e = cudaMallocHost(&g.h_res, 5 * sizeof(double) * S + 16)) != cudaSuccess ||
           (e = cudaMalloc(&g.d_items[0], 2 * al(sizeof(WorkItem) * kStepCap))) != cudaSuccess ||
           (e = cudaMalloc(&g.d_sel, sizeof(int) * S)) != cudaSuccess ||
           (e = cudaMalloc(&g.d_ctr, 256)) != cudaSuccess ||
@@ -729,6 +750,7 @@ extern "C" int gbs_serve_create(const gbs_kernel* k, const gbs_serve_opts* opts,
         break;
       }
       memset(g.h_up, 0, s->up_bytes);
+      memset(g.h_res, 0, 5 * sizeof(double) * S + 16);  // completion word 0: no step has number 0
       g.d_items[1] = (WorkItem*)((unsigned char*)g.d_items[0] + al(sizeof(WorkItem) * kStepCap));
       if ((e = cudaHostGetDevicePointer((void**)&g.h_up_dev, g.h_up, 0)) != cudaSuccess) {
         cudaGetLastError();
