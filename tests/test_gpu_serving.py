@@ -82,6 +82,30 @@ def test_serving_matches_batch(gbs, kern, use_graphs):
             assert abs(p - pr) <= FP64_TOL * pr
 
 
+@pytest.mark.parametrize("use_graphs", [1, -1])
+def test_serving_stats_consistent(gbs, kern, use_graphs):
+    """The server's own counters: every request with device work completes in
+    some step; every step has a positive device time (the step's events are
+    recorded, as graph nodes or on the stream) no longer than its maximum; the
+    launch time is at least its submission part."""
+    K, m = kern
+    pats = [x for x in requests(m, 60, 9, n_values=range(4, 19, 2))]
+    srv = gbs.Server(K, use_graphs=use_graphs, subsets_per_step=512)
+    try:
+        tickets = [srv.submit(x) for x in pats]
+        wait_all(srv, tickets)
+        st = srv.stats()
+    finally:
+        srv.destroy()
+    assert st["completed"] == len(pats)
+    assert st["steps"] >= 1 and st["items"] >= st["steps"] and st["subsets"] >= len(pats)
+    assert 0 < st["step_device_s"] and st["step_device_max_s"] <= st["step_device_s"]
+    assert st["step_device_s"] <= st["steps"] * st["step_device_max_s"] + 1e-12
+    assert 0 < st["step_wall_max_s"] <= st["step_wall_s"]
+    assert st["launch_max_s"] >= st["submit_max_s"] > 0
+    assert st["poll_gap_max_s"] >= 0
+
+
 def test_serving_alone_equals_in_mix(gbs, kern):
     """A request's result does not depend on what else is resident."""
     K, m = kern
