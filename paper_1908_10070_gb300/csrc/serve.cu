@@ -560,6 +560,12 @@ bool wait_stage(gbs_server* s, Stage& g, bool block) {
         std::atomic_thread_fence(std::memory_order_acquire);  // results before the word
         return true;
       }
+      // a step still running after 5 ms (most take well under 1 ms) is also
+      // checked with the driver, so that a failed step is reported at once
+      if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > 5e-3) {
+        const cudaError_t e = cudaEventQuery(g.ev);
+        if (e != cudaSuccess && e != cudaErrorNotReady) return false;
+      }
     } else {
       const cudaError_t e = cudaEventQuery(g.ev);
       if (e == cudaSuccess) return true;
