@@ -155,6 +155,22 @@ def max_over_ranks(dist, device, *vals):
     return t.tolist()
 
 
+def host_cpu() -> str:
+    """Architecture, logical cores and CPU model of the host (from /proc/cpuinfo)."""
+    import platform
+
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                key = ln.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part") and not model:
+                    model = ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "%s, %d logical cores, %s" % (platform.machine(), os.cpu_count() or 0, model or "model unknown")
+
+
 def cpu_baseline(pats, U, r, target_s: float = 12.0):
     """Oracle FP64 subset sum on the host cores over a bounded sample (the
     workload's patterns, repeated in order when the sample exceeds the batch)."""
@@ -171,9 +187,19 @@ def cpu_baseline(pats, U, r, target_s: float = 12.0):
     t0 = time.perf_counter()
     oracle.haf_batch_f64(sample)
     dt2 = time.perf_counter() - t0
-    return {"value": k2 / dt2, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    cores = oracle.num_threads()
+    # one core on the first 64 patterns
+    oracle.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.haf_batch_f64(mats[:k])
+        dt1 = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(cores)
+    return {"value": k2 / dt2, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d patterns (the n=16, M=64 batch of %d, cycled), FP64 subset sum, "
-                      "OpenMP over patterns, %.1f s" % (k2, len(pats), dt2)}
+                      "OpenMP over patterns, %.1f s" % (k2, len(pats), dt2),
+            "single_core_value": k / dt1, "cpu": host_cpu()}
 
 
 def reference_arm(args):
@@ -202,7 +228,7 @@ def reference_arm(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD_DESC + "FP64", "patterns_per_step": k},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": "%d of %d patterns per step" % (k, len(pats))},
+                             "sample": "%d of %d patterns per step" % (k, len(pats)), "cpu": host_cpu()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -87,6 +87,7 @@ def _load():
                                      ctypes.c_int, dp, dp, dp, dp]
             lib.orc_haf_batch_f64.argtypes = [dp, ip, lp, ctypes.c_int, dp]
             lib.orc_num_threads.restype = ctypes.c_int
+            lib.orc_set_num_threads.argtypes = [ctypes.c_int]
             _lib = lib
     return _lib
 
@@ -106,6 +107,11 @@ def _dd_complex(out4) -> complex:
 
 def num_threads() -> int:
     return int(_load().orc_num_threads())
+
+
+def set_num_threads(t: int) -> None:
+    """Threads of the oracle's parallel loops over patterns (timing only)."""
+    _load().orc_set_num_threads(int(t))
 
 
 def build_B_dd(U, t) -> np.ndarray:

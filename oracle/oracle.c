@@ -425,3 +425,13 @@ int orc_num_threads(void) {
   return 1;
 #endif
 }
+
+/* Threads used by later parallel loops (timing only; no effect on results,
+   which are per pattern). */
+void orc_set_num_threads(int t) {
+#ifdef _OPENMP
+  if (t > 0) omp_set_num_threads(t);
+#else
+  (void)t;
+#endif
+}
