@@ -245,6 +245,24 @@ def test_prob_host_and_device_buffers_agree(gbs):
         assert np.array_equal(x, y)
 
 
+def test_prob_pair_sum_budget_overflow(gbs, orc):
+    """A batch whose pair sums exceed their 2 GiB budget: 32768 collision-free
+    n = 16 patterns need about 2.3 GB, so the first matrices form R_2 from their
+    pair sums and the last ones by the product, in the same launch. Matrices
+    from both ends are checked against the oracle."""
+    m = 64
+    U = W.haar_unitary(m, 1)
+    r = W.squeezing(m, "uniform", seed=1)
+    rng = np.random.default_rng(77)
+    pats = [np.sort(rng.choice(m, 16, replace=False)).astype(np.int32) for _ in range(32768)]
+    K = kernel_for(gbs, U, r)
+    p, lp, hf, er = run_prob(gbs, K, pats, 0)
+    sample = list(range(0, 12)) + list(range(32768 - 12, 32768))
+    ref = orc.prob(U, r, [pats[i] for i in sample])
+    assert np.all(rel(hf[sample], ref["haf"]) <= FP64_TOL), rel(hf[sample], ref["haf"])
+    assert np.all(np.isfinite(p)) and np.all(p > 0)
+
+
 def test_prob_batched_n16_sampled(gbs, orc):
     """The benchmark's workload and launch (M = 64, 4096 patterns, n = 16): the
     whole batch runs on the GPU; 48 patterns spread over it are checked."""
