@@ -59,10 +59,11 @@ constexpr int kWarpHeaderBytes = 128;  // per-warp index-list buffer (32 ints)
 // made the signed sum cancel up to ~1e4 times more in measurements.
 __host__ __device__ inline int default_pos(int p, int h) { return (p >> 1) + ((p & 1) ? h : 0); }
 
-// Packed symmetric matrices live at once in the power-trace schedule for
-// h = n/2 (see haf_subsets.cu).
+// Matrix buffers a lane group keeps for a matrix with h = n/2: the most that
+// the power-trace schedule of h, or of any order N < h that its smaller
+// subsets run (see haf_subsets.cu), holds at once.
 __host__ __device__ inline int sched_nbuf(int h) {
-  return h <= 2 ? 1 : (h <= 4 ? 2 : (h <= 6 ? 3 : (h <= 10 ? 4 : 5)));
+  return h <= 2 ? 1 : (h <= 4 ? 2 : (h <= 8 ? 3 : (h <= 12 ? 4 : 5)));
 }
 
 // Shared-memory bytes of one lane group's region for subsets of order N (and

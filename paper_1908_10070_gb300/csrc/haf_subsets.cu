@@ -132,8 +132,11 @@ struct Tables {
 // index set F (with R_1 = A_S) satisfies F + F >= {1..h}, each trace k taken
 // as tr(X R_k) when k is in F, else tr(X R_a X R_b) with a + b = k (a = b
 // where R_{k/2} is kept: that square trace needs about half the terms), and
-// each R kept in one of sched_nbuf(h) buffers (a buffer is reused once its
-// traces are taken). Products per h = 1..16: 0 0 1 1 2 2 3 3 3 3 4 4 4 4 5 6.
+// each R kept in a buffer that is reused once its traces are taken. Among the
+// schedules with the fewest products, the rows for h = 7, 8, 11, 12, 15, 16
+// (found by an exhaustive search) hold the fewest matrices at once (3, 3, 3,
+// 3, 4, 4) and have the cheapest traces. Products per h = 1..16:
+// 0 0 1 1 2 2 3 3 3 3 4 4 4 4 5 5.
 enum { kEnd = -1, kProd = 0, kTr1 = 1, kTr2 = 2 };
 struct SchedOp {
   signed char kind;  // kProd: buf[k] = buf[a] X buf[b]; kTr1: p_k = tr(X buf[a]); kTr2: p_k = tr(X buf[a] X buf[b])
@@ -148,16 +151,16 @@ __constant__ SchedOp c_sched[kMaxH + 1][kMaxOps] = {
     {{kProd, 1, 0, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr2, 3, 1, 0}, {kTr2, 4, 1, 1}, {kEnd, 0, 0, 0}},  // h = 4
     {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 1, 1}, {kTr2, 5, 2, 1}, {kEnd, 0, 0, 0}},  // h = 5
     {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 1, 1}, {kTr2, 5, 2, 1}, {kTr2, 6, 2, 2}, {kEnd, 0, 0, 0}},  // h = 6
-    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kProd, 3, 2, 1}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 1, 1}, {kTr1, 5, 3, 0}, {kTr2, 6, 2, 2}, {kTr2, 7, 3, 1}, {kEnd, 0, 0, 0}},  // h = 7
-    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kProd, 3, 2, 1}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 1, 1}, {kTr1, 5, 3, 0}, {kTr2, 6, 2, 2}, {kTr2, 7, 3, 1}, {kTr2, 8, 3, 2}, {kEnd, 0, 0, 0}},  // h = 8
+    {{kProd, 1, 0, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr2, 4, 1, 1}, {kProd, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 6, 2, 2}, {kProd, 0, 2, 1}, {kTr1, 5, 0, 0}, {kTr2, 7, 0, 1}, {kEnd, 0, 0, 0}},  // h = 7
+    {{kProd, 1, 0, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kProd, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 5, 2, 1}, {kTr2, 6, 2, 2}, {kProd, 1, 2, 0}, {kTr1, 4, 1, 0}, {kTr2, 7, 1, 2}, {kTr2, 8, 1, 1}, {kEnd, 0, 0, 0}},  // h = 8
     {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kProd, 3, 2, 2}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 1, 1}, {kTr2, 5, 2, 1}, {kTr1, 6, 3, 0}, {kTr2, 7, 3, 0}, {kTr2, 8, 3, 1}, {kTr2, 9, 3, 2}, {kEnd, 0, 0, 0}},  // h = 9
     {{kProd, 1, 0, 0}, {kProd, 2, 1, 1}, {kProd, 3, 2, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr2, 3, 1, 0}, {kTr1, 4, 2, 0}, {kTr1, 5, 3, 0}, {kTr2, 6, 2, 1}, {kTr2, 7, 3, 1}, {kTr2, 8, 2, 2}, {kTr2, 9, 3, 2}, {kTr2, 10, 3, 3}, {kEnd, 0, 0, 0}},  // h = 10
-    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kProd, 3, 2, 1}, {kProd, 4, 3, 2}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 1, 1}, {kTr1, 5, 3, 0}, {kTr2, 6, 2, 2}, {kTr2, 7, 3, 1}, {kTr1, 8, 4, 0}, {kTr2, 9, 4, 0}, {kTr2, 10, 3, 3}, {kTr2, 11, 4, 2}, {kEnd, 0, 0, 0}},  // h = 11
-    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kProd, 3, 2, 2}, {kProd, 4, 3, 2}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 1, 1}, {kTr2, 5, 2, 1}, {kTr1, 6, 3, 0}, {kTr2, 7, 3, 0}, {kTr2, 8, 3, 1}, {kTr1, 9, 4, 0}, {kTr2, 10, 4, 0}, {kTr2, 11, 4, 1}, {kTr2, 12, 3, 3}, {kEnd, 0, 0, 0}},  // h = 12
+    {{kProd, 1, 0, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr2, 4, 1, 1}, {kProd, 2, 1, 0}, {kTr1, 3, 2, 0}, {kProd, 0, 2, 1}, {kTr1, 5, 0, 0}, {kTr2, 7, 0, 1}, {kTr2, 8, 0, 2}, {kTr2, 10, 0, 0}, {kProd, 1, 2, 2}, {kTr1, 6, 1, 0}, {kTr2, 9, 1, 2}, {kTr2, 11, 1, 0}, {kEnd, 0, 0, 0}},  // h = 11
+    {{kProd, 1, 0, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr2, 4, 1, 1}, {kProd, 2, 1, 0}, {kTr1, 3, 2, 0}, {kProd, 0, 2, 1}, {kTr1, 5, 0, 0}, {kTr2, 7, 0, 1}, {kTr2, 8, 0, 2}, {kTr2, 10, 0, 0}, {kProd, 1, 2, 2}, {kTr1, 6, 1, 0}, {kTr2, 9, 1, 2}, {kTr2, 11, 1, 0}, {kTr2, 12, 1, 1}, {kEnd, 0, 0, 0}},  // h = 12
     {{kProd, 1, 0, 0}, {kProd, 2, 1, 1}, {kProd, 3, 2, 1}, {kProd, 4, 3, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr2, 3, 1, 0}, {kTr1, 4, 2, 0}, {kTr2, 5, 2, 0}, {kTr1, 6, 3, 0}, {kTr1, 7, 4, 0}, {kTr2, 8, 2, 2}, {kTr2, 9, 4, 1}, {kTr2, 10, 3, 2}, {kTr2, 11, 4, 2}, {kTr2, 12, 3, 3}, {kTr2, 13, 4, 3}, {kEnd, 0, 0, 0}},  // h = 13
     {{kProd, 1, 0, 0}, {kProd, 2, 1, 1}, {kProd, 3, 2, 1}, {kProd, 4, 3, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr2, 3, 1, 0}, {kTr1, 4, 2, 0}, {kTr2, 5, 2, 0}, {kTr1, 6, 3, 0}, {kTr1, 7, 4, 0}, {kTr2, 8, 2, 2}, {kTr2, 9, 4, 1}, {kTr2, 10, 3, 2}, {kTr2, 11, 4, 2}, {kTr2, 12, 3, 3}, {kTr2, 13, 4, 3}, {kTr2, 14, 4, 4}, {kEnd, 0, 0, 0}},  // h = 14
-    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 1, 1}, {kTr2, 5, 2, 1}, {kProd, 3, 2, 2}, {kTr1, 6, 3, 0}, {kTr2, 7, 3, 0}, {kTr2, 8, 3, 1}, {kProd, 4, 3, 2}, {kTr1, 9, 4, 0}, {kTr2, 10, 4, 0}, {kTr2, 11, 4, 1}, {kProd, 3, 4, 2}, {kTr1, 12, 3, 0}, {kTr2, 13, 3, 0}, {kTr2, 14, 3, 1}, {kTr2, 15, 3, 2}, {kEnd, 0, 0, 0}},  // h = 15
-    {{kProd, 1, 0, 0}, {kProd, 2, 1, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 4, 1, 1}, {kTr2, 5, 2, 1}, {kProd, 3, 2, 2}, {kTr1, 6, 3, 0}, {kTr2, 7, 3, 0}, {kTr2, 8, 3, 1}, {kProd, 4, 3, 2}, {kTr1, 9, 4, 0}, {kTr2, 10, 4, 0}, {kTr2, 11, 4, 1}, {kProd, 3, 4, 2}, {kTr1, 12, 3, 0}, {kTr2, 13, 3, 0}, {kTr2, 14, 3, 1}, {kTr2, 15, 3, 2}, {kProd, 4, 3, 2}, {kTr2, 16, 4, 0}, {kEnd, 0, 0, 0}},  // h = 16
+    {{kProd, 1, 0, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr2, 4, 1, 1}, {kProd, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 6, 2, 2}, {kProd, 3, 2, 1}, {kTr1, 5, 3, 0}, {kTr2, 10, 3, 3}, {kProd, 0, 3, 1}, {kTr1, 7, 0, 0}, {kTr2, 9, 0, 1}, {kTr2, 12, 0, 3}, {kTr2, 14, 0, 0}, {kProd, 1, 3, 2}, {kTr1, 8, 1, 0}, {kTr2, 11, 1, 2}, {kTr2, 13, 1, 3}, {kTr2, 15, 1, 0}, {kEnd, 0, 0, 0}},  // h = 15
+    {{kProd, 1, 0, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr2, 4, 1, 1}, {kProd, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 6, 2, 2}, {kProd, 3, 2, 1}, {kTr1, 5, 3, 0}, {kTr2, 10, 3, 3}, {kProd, 0, 3, 1}, {kTr1, 7, 0, 0}, {kTr2, 9, 0, 1}, {kTr2, 12, 0, 3}, {kTr2, 14, 0, 0}, {kProd, 1, 3, 2}, {kTr1, 8, 1, 0}, {kTr2, 11, 1, 2}, {kTr2, 13, 1, 3}, {kTr2, 15, 1, 0}, {kTr2, 16, 1, 1}, {kEnd, 0, 0, 0}},  // h = 16
 };
 
 // Position of entry (r, c) of a symmetric N x N matrix stored as its packed
