@@ -108,12 +108,19 @@ struct Slot {
 
 constexpr int kStepCap = 65536;  // work items per precision per step
 
+// The GPU's global nanosecond timer, for the step graph's start and end stamps.
+__global__ void stamp_kernel(unsigned long long* out) {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  *out = t;
+}
+
 struct Stage {
   // pinned host: slot tables, items (2 precisions), selection list, step
   // header (item counts, finalisation count); results
   unsigned char* h_up = nullptr;
   unsigned char* h_up_dev = nullptr;  // the same memory as the device sees it
-  double* h_res = nullptr;  // 5 S results, then the completion word (graph path)
+  double* h_res = nullptr;  // 5 S results, 2 timer stamps, the completion word (graph path)
   // device
   WorkItem* d_items[2] = {nullptr, nullptr};
   int* d_sel = nullptr;
@@ -129,7 +136,7 @@ struct Stage {
   // graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  cudaGraphNode_t nd_ev0 = nullptr, nd_pats = nullptr, nd_idx = nullptr, nd_hdr = nullptr, nd_ctr = nullptr,
+  cudaGraphNode_t nd_t0 = nullptr, nd_t1 = nullptr, nd_pats = nullptr, nd_idx = nullptr, nd_hdr = nullptr, nd_ctr = nullptr,
                   nd_k[2] = {nullptr, nullptr}, nd_sel = nullptr, nd_fin = nullptr, nd_res = nullptr,
                   nd_done = nullptr, nd_ev = nullptr;
 };
@@ -288,10 +295,24 @@ cudaError_t build_graph(gbs_server* s, Stage& g) {
   };
   cudaGraphNode_t deps[1];
   size_t nd;
-  // the step's start and end events are nodes of the graph too
-  e = cudaGraphAddEventRecordNode(&g.nd_ev0, g.graph, nullptr, 0, g.ev0);
+  // the step's start and end are stamped with the GPU's timer by the graph
+  // itself (device time without a driver call); its end event remains for
+  // the error check of a long wait
+  unsigned long long* d_stamp = (unsigned long long*)(g.d_res + 5 * S);
+  auto add_stamp = [&](cudaGraphNode_t* node, unsigned long long* out) -> cudaError_t {
+    void* args[1] = {&out};
+    cudaKernelNodeParams kp;
+    memset(&kp, 0, sizeof(kp));
+    kp.func = (void*)stamp_kernel;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1);
+    kp.kernelParams = args;
+    nd = dep(deps);
+    return cudaGraphAddKernelNode(node, g.graph, deps, nd, &kp);
+  };
+  e = add_stamp(&g.nd_t0, d_stamp);
   if (e != cudaSuccess) return e;
-  prev = g.nd_ev0;
+  prev = g.nd_t0;
   nd = dep(deps);
   e = cudaGraphAddMemcpyNode1D(&g.nd_pats, g.graph, deps, nd, s->d_pats, g.h_up + s->off_pats,
                                sizeof(PatDesc) * S, cudaMemcpyHostToDevice);
@@ -353,8 +374,11 @@ cudaError_t build_graph(gbs_server* s, Stage& g) {
     if (e != cudaSuccess) return e;
     prev = g.nd_fin;
   }
+  e = add_stamp(&g.nd_t1, d_stamp + 1);
+  if (e != cudaSuccess) return e;
+  prev = g.nd_t1;
   nd = dep(deps);
-  e = cudaGraphAddMemcpyNode1D(&g.nd_res, g.graph, deps, nd, g.h_res, g.d_res, sizeof(double) * 5 * S,
+  e = cudaGraphAddMemcpyNode1D(&g.nd_res, g.graph, deps, nd, g.h_res, g.d_res, sizeof(double) * 5 * S + 16,
                                cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return e;
   prev = g.nd_res;
@@ -366,7 +390,7 @@ cudaError_t build_graph(gbs_server* s, Stage& g) {
   // and its end event, so that the server sees a finished step without a
   // driver call
   nd = dep(deps);
-  e = cudaGraphAddMemcpyNode1D(&g.nd_done, g.graph, deps, nd, g.h_res + 5 * S, g.d_ctr + 5, sizeof(int),
+  e = cudaGraphAddMemcpyNode1D(&g.nd_done, g.graph, deps, nd, g.h_res + 5 * S + 2, g.d_ctr + 5, sizeof(int),
                                cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return e;
   return cudaGraphInstantiate(&g.exec, g.graph, 0);
@@ -556,7 +580,7 @@ bool wait_stage(gbs_server* s, Stage& g, bool block) {
     tick(s);
     if (s->o.use_graphs) {
       // the graph's last copy writes the step's number: no driver call here
-      if (*(volatile int*)(g.h_res + 5 * S) == (int)(g.id & 0x7fffffff)) {
+      if (*(volatile int*)(g.h_res + 5 * S + 2) == (int)(g.id & 0x7fffffff)) {
         std::atomic_thread_fence(std::memory_order_acquire);  // results before the word
         return true;
       }
@@ -629,12 +653,18 @@ void serve_loop(gbs_server* s) {
         const double w = std::chrono::duration<double>(std::chrono::steady_clock::now() - old->t_launch).count();
         s->stats.step_wall_s += w;
         if (w > s->stats.step_wall_max_s) s->stats.step_wall_max_s = w;
-        float dev_ms = 0.f;
-        if (cudaEventElapsedTime(&dev_ms, old->ev0, old->ev) == cudaSuccess) {
-          s->stats.step_device_s += 1e-3 * dev_ms;
-          if (1e-3 * dev_ms > s->stats.step_device_max_s) s->stats.step_device_max_s = 1e-3 * dev_ms;
+        double dev_s = -1.0;
+        if (s->o.use_graphs) {
+          const unsigned long long* st = (const unsigned long long*)(old->h_res + 5 * s->o.max_slots);
+          if (st[1] >= st[0]) dev_s = 1e-9 * (double)(st[1] - st[0]);
         } else {
-          cudaGetLastError();
+          float dev_ms = 0.f;
+          if (cudaEventElapsedTime(&dev_ms, old->ev0, old->ev) == cudaSuccess) dev_s = 1e-3 * dev_ms;
+          else cudaGetLastError();
+        }
+        if (dev_s >= 0.0) {
+          s->stats.step_device_s += dev_s;
+          if (dev_s > s->stats.step_device_max_s) s->stats.step_device_max_s = dev_s;
         }
         s->stats.completed += (int64_t)old->fin.size();
         complete(s, *old);
@@ -745,18 +775,18 @@ extern "C" int gbs_serve_create(const gbs_kernel* k, const gbs_serve_opts* opts,
     for (int i = 0; i < 2 && ret == GBS_OK; ++i) {
       Stage& g = s->stage[i];
       if ((e = cudaMallocHost(&g.h_up, s->up_bytes)) != cudaSuccess ||
-          (e = cudaMallocHost(&g.h_res, 5 * sizeof(double) * S + 16)) != cudaSuccess ||
+          (e = cudaMallocHost(&g.h_res, 5 * sizeof(double) * S + 32)) != cudaSuccess ||
           (e = cudaMalloc(&g.d_items[0], 2 * al(sizeof(WorkItem) * kStepCap))) != cudaSuccess ||
           (e = cudaMalloc(&g.d_sel, sizeof(int) * S)) != cudaSuccess ||
           (e = cudaMalloc(&g.d_ctr, 256)) != cudaSuccess ||
-          (e = cudaMalloc(&g.d_res, 5 * sizeof(double) * S)) != cudaSuccess ||
+          (e = cudaMalloc(&g.d_res, 5 * sizeof(double) * S + 16)) != cudaSuccess ||
           (e = cudaEventCreate(&g.ev)) != cudaSuccess || (e = cudaEventCreate(&g.ev0)) != cudaSuccess) {
         cudaGetLastError();
         ret = fail(GBS_ENOMEM, "stage buffers: %s", cudaGetErrorString(e));
         break;
       }
       memset(g.h_up, 0, s->up_bytes);
-      memset(g.h_res, 0, 5 * sizeof(double) * S + 16);  // completion word 0: no step has number 0
+      memset(g.h_res, 0, 5 * sizeof(double) * S + 32);  // completion word 0: no step has number 0
       g.d_items[1] = (WorkItem*)((unsigned char*)g.d_items[0] + al(sizeof(WorkItem) * kStepCap));
       if ((e = cudaHostGetDevicePointer((void**)&g.h_up_dev, g.h_up, 0)) != cudaSuccess) {
         cudaGetLastError();
