@@ -560,10 +560,14 @@ int run_batch(const BatchArgs& a) {
 
   Planner plan;
   // a few items per resident warp balance the load over all SMs; whole-matrix
-  // items for all but one matrix per resident warp of an order (tuning runs
-  // keep per-size items, whose rounds they choose)
+  // items for all but a reserve of an order, whose per-size items fill the
+  // schedule's tail: one matrix per two resident warps in FP64 (one per warp
+  // was 0.8 % slower at 10 warps per SM, one per four warps 9 % slower), one
+  // per warp for the float kernel (half that was 5 % slower); tuning runs keep
+  // per-size items, whose rounds they choose
   const int64_t want = 4LL * device_sm_count() * cfg.warps_per_block;
-  const int64_t reserve = a.cfg_override ? 0 : (int64_t)device_sm_count() * cfg.warps_per_block;
+  const int64_t reserve = a.cfg_override ? 0
+                        : (int64_t)device_sm_count() * cfg.warps_per_block / (a.precision == GBS_FP64 ? 2 : 1);
   plan.init(a.n, batch, a.precision, cfg.warp_bytes, rounds_for_n, rep_ptr, reserve);
   if (!a.cfg_override) {
     // A small batch gets smaller work items (fewer rounds each) for the same reason.
