@@ -630,7 +630,14 @@ int run_batch(const BatchArgs& a) {
   const size_t ptoff_b = (use_pt && pt_elems > 0) ? al(sizeof(int64_t) * batch) : 0;
   // pairing probe of the largest matrices
   PairingPlan pp;
-  if (n_items > 0) plan_pairing(a.n, batch, a.precision, cfg.warp_bytes, maxn / 2, rep_ptr, &pp);
+  // The probe only ranks candidate orderings by their estimated sum |f|, which
+  // float arithmetic does as well as FP64; so FP64 probability calls run it on
+  // the float kernel over the kernel's float copy of B (about a quarter of the
+  // time), with the float kernel's launch shape.
+  const bool probe32 = (a.precision == GBS_FP64 && a.mode == BatchArgs::PROB && a.B32 != nullptr);
+  const int pprec = probe32 ? GBS_MIXED : a.precision;
+  const TuneCfg pcfg = (probe32 && !a.cfg_override) ? get_cfg(GBS_MIXED, maxn) : cfg;
+  if (n_items > 0) plan_pairing(a.n, batch, pprec, pcfg.warp_bytes, maxn / 2, rep_ptr, &pp);
   const int n_sel = (int)pp.sel.size();
   const int n_probe = (int)pp.pats.size();
   const int n_pitems = (int)pp.items.size();
@@ -825,17 +832,19 @@ int run_batch(const BatchArgs& a) {
         Lp.pt_off = nullptr;
         Lp.batch = n_probe;
         Lp.perm_off = d_pperm;
+        if (probe32) Lp.src32 = a.B32;
+        Lp.warp_bytes = pcfg.warp_bytes;
         // few items (one or a few matrices): fewer warps per block, so that
         // the samples spread over every SM instead of sharing FP64 units
         const int sms = device_sm_count();
         int pwpb = (n_pitems + sms - 1) / sms;
-        pwpb = std::max(1, std::min(pwpb, cfg.warps_per_block));
-        const int pper_sm = max_blocks_per_sm(a.precision, pwpb, pwpb * cfg.warp_bytes);
+        pwpb = std::max(1, std::min(pwpb, pcfg.warps_per_block));
+        const int pper_sm = max_blocks_per_sm(pprec, pwpb, pwpb * pcfg.warp_bytes);
         if (pper_sm < 1) { ret = fail(GBS_EINVAL, "probe shape does not fit an SM"); break; }
         int pblocks = sms * pper_sm;
         const int pneed = (n_pitems + pwpb - 1) / pwpb;
         if (pneed < pblocks) pblocks = pneed;
-        e = launch_haf_subsets(Lp, a.precision, pblocks, pwpb, st);
+        e = launch_haf_subsets(Lp, pprec, pblocks, pwpb, st);
         if (e != cudaSuccess) { ret = cuda_fail(e, "probe launch"); break; }
         PairingSelect S;
         S.probe_pats = d_ppats;
