@@ -84,7 +84,7 @@ def _load():
             lib.orc_haf_subset_f64.argtypes = [ctypes.c_int, dp, dp]
             lib.orc_per_ryser.argtypes = [ctypes.c_int, dp, dp]
             lib.orc_prob.argtypes = [ctypes.c_int, dp, ip, ip, lp, ctypes.c_int, ctypes.c_double,
-                                     ctypes.c_int, dp, dp, dp, dp]
+                                     ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
             lib.orc_haf_batch_f64.argtypes = [dp, ip, lp, ctypes.c_int, dp]
             lib.orc_num_threads.restype = ctypes.c_int
             lib.orc_set_num_threads.argtypes = [ctypes.c_int]
@@ -227,11 +227,15 @@ def log_norm(r) -> float:
     return float(np.sum(np.log(np.cosh(np.asarray(r, dtype=np.float64)))))
 
 
-def prob(U, r, patterns, method: str = "subset", Bdd=None) -> dict:
-    """Output probabilities of index-list patterns.
+def prob(U, r, patterns, method: str = "subset", Bdd=None, zero_diag: bool = False) -> dict:
+    """Output probabilities of index-list patterns (in any order, Appendix B).
 
-    Returns dict with arrays p, logp, haf (complex128, the dd value rounded),
-    haf_dd (batch, 4) and kappa (sum_S |f|; subset method only)."""
+    The subset sum pairs positions (2t, 2t+1) of each list as given; with
+    zero_diag the diagonal of W_x is set to 0 first (no perfect matching uses
+    it, Eq. HafMatch). Neither changes Haf or p; both change the individual
+    subset terms and so kappa. Returns dict with arrays p, logp, haf
+    (complex128, the dd value rounded), haf_dd (batch, 4) and kappa (sum_S |f|;
+    subset method only)."""
     if Bdd is None:
         Bdd = build_B_dd(U, np.tanh(np.asarray(r, dtype=np.float64)))
     m = Bdd.shape[0]
@@ -247,7 +251,8 @@ def prob(U, r, patterns, method: str = "subset", Bdd=None) -> dict:
     _load().orc_prob(m, _dp(B), idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                      ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                      offs.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), nb, log_norm(r),
-                     1 if method == "pm" else 0, _dp(p), _dp(lp), _dp(hd), _dp(kap))
+                     1 if method == "pm" else 0, 1 if zero_diag else 0, _dp(p), _dp(lp), _dp(hd),
+                     _dp(kap))
     hd = hd.reshape(nb, 4)
     return dict(p=p, logp=lp, haf=(hd[:, 0] + hd[:, 1]) + 1j * (hd[:, 2] + hd[:, 3]),
                 haf_dd=hd, kappa=kap)

@@ -345,14 +345,18 @@ void orc_per_ryser(int k, const double* C, double* out4) {
 /* Output probabilities                                                      */
 /* ------------------------------------------------------------------------ */
 /* Bdd: m*m dd-complex kernel matrix from orc_build_B (4 doubles per entry).
- * idx: concatenated 0-based mode lists; n[b], offs[b] (start of pattern b in
- * idx). log_norm = sum_i log cosh r_i. method 0 = subset sum, 1 = perfect
- * matchings. Outputs per pattern: p, log p (-inf when Haf = 0), Haf (dd, 4
- * doubles), kappa_sum (subset method; 0 for matchings). Patterns run in
- * parallel; each pattern's own sum is computed serially inside. */
+ * idx: concatenated 0-based mode lists, in any order (Appendix B: the order
+ * of x does not change Haf(W_x)); n[b], offs[b] (start of pattern b in idx).
+ * log_norm = sum_i log cosh r_i. method 0 = subset sum, 1 = perfect
+ * matchings. zero_diag != 0: W_x(i, i) is set to 0 before the sum (no perfect
+ * matching uses V(i, i), Eq. HafMatch, so Haf is unchanged; the subset sum's
+ * individual terms, and so kappa_sum, are not). Outputs per pattern: p, log p
+ * (-inf when Haf = 0), Haf (dd, 4 doubles), kappa_sum (subset method; 0 for
+ * matchings). Patterns run in parallel; each pattern's own sum is computed
+ * serially inside. */
 void orc_prob(int m, const double* Bdd, const int* idx, const int* n, const long* offs, int batch,
-              double log_norm, int method, double* p_out, double* logp_out, double* haf_out,
-              double* kappa_out) {
+              double log_norm, int method, int zero_diag, double* p_out, double* logp_out,
+              double* haf_out, double* kappa_out) {
   /* patterns in parallel when there are enough of them; otherwise each
    * pattern's subset sum runs its fixed chunks in parallel (same arithmetic
    * either way: the chunked sum below) */
@@ -371,7 +375,7 @@ void orc_prob(int m, const double* Bdd, const int* idx, const int* n, const long
       for (int j = 0; j < nb; j++) {
         const double* e = Bdd + 4 * ((size_t)x[i] * m + x[j]);
         cdd v = {{e[0], e[1]}, {e[2], e[3]}};
-        W[i * nb + j] = v;
+        W[i * nb + j] = (zero_diag && i == j) ? cdd_zero() : v;
       }
     double K = 0.0;
     cdd haf;
@@ -381,12 +385,19 @@ void orc_prob(int m, const double* Bdd, const int* idx, const int* n, const long
       haf = haf_subset_cdd(nb, W, &K);
       if (nb == 0) K = 1.0;
     }
-    /* p = |Haf|^2 / (prod_j s_j! prod_i cosh r_i): x is sorted, so equal modes
-     * are adjacent; sum log s_j! over runs. */
+    /* p = |Haf|^2 / (prod_j s_j! prod_i cosh r_i), s_j the number of times
+     * mode j occurs in x: sort a copy so that equal modes are adjacent, then
+     * sum log s_j! over the runs. */
+    int xs[64];
+    for (int i = 0; i < nb; i++) {
+      int v = x[i], k = i;
+      while (k > 0 && xs[k - 1] > v) { xs[k] = xs[k - 1]; k--; }
+      xs[k] = v;
+    }
     double log_fact = 0.0;
     int run = 1;
     for (int i = 1; i <= nb; i++) {
-      if (i < nb && x[i] == x[i - 1]) { run++; continue; }
+      if (i < nb && xs[i] == xs[i - 1]) { run++; continue; }
       if (nb > 0)
         for (int k = 2; k <= run; k++) log_fact += log((double)k);
       run = 1;

@@ -348,3 +348,27 @@ def test_haf_repeated_collision_free_and_edges(orc):
     a = orc.haf_repeated(B4, [2, 0, 1, 1])
     b = orc.haf_repeated(B4[np.ix_([0, 2, 3], [0, 2, 3])], [2, 1, 1])
     assert abs(a - b) <= 1e-14 * abs(b)
+
+
+def test_prob_order_and_diagonal_free(orc):
+    """p(s) is a function of the configuration s alone: any order of the index
+    list x gives the same Haf(W_x) (Appendix B) and the same prod_j s_j!; and no
+    perfect matching uses a diagonal entry (Eq. HafMatch), so zeroing the
+    diagonal of W_x leaves Haf and p unchanged, while the subset sum's terms
+    (and so kappa) change. Checked against the perfect-matching oracle on
+    patterns with collisions."""
+    m = 7
+    U = W.haar_unitary(m, 41)
+    r = W.squeezing(m, "uniform", seed=41)
+    rng = np.random.default_rng(41)
+    pats = [np.sort(rng.choice(m, n, replace=True)).astype(np.int32) for n in (4, 6, 8, 10) for _ in range(2)]
+    ref = orc.prob(U, r, pats, method="pm")
+    shuffled = [rng.permutation(x).astype(np.int32) for x in pats]
+    for zd in (False, True):
+        out = orc.prob(U, r, shuffled, zero_diag=zd)
+        assert np.all(np.abs(out["haf"] - ref["haf"]) <= 1e-15 * np.abs(ref["haf"]))
+        assert np.all(np.abs(out["p"] - ref["p"]) <= 1e-14 * ref["p"])
+        assert np.all(np.abs(out["logp"] - ref["logp"]) <= 1e-12 * np.abs(ref["logp"]))
+    k0 = orc.prob(U, r, pats)["kappa"]
+    k1 = orc.prob(U, r, pats, zero_diag=True)["kappa"]
+    assert np.all(k0 > 0) and np.all(k1 > 0) and not np.allclose(k0, k1)
