@@ -325,6 +325,11 @@ def main():
     flops = model_flops(16) * b
     peak = fp64_peak_tflops() if prec == gbs.FP64 else fp32_peak_tflops()
     achieved = flops / (t_kern * 1e-3) / 1e12
+    # the FP64 pipe's measured throughput (DFMA microbenchmark in the library),
+    # with the clocks it ran at: the second denominator of the fraction
+    with ClockSampler(local) as pclk:
+        measured_peak = gbs.measure_fp64_peak()
+    pclk_s = pclk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
@@ -346,17 +351,22 @@ def main():
                      "flops_per_launch": flops,
                      "peak_note": ("FP64 from unit counts and clock (152 SM x 4 flop/clk x 2.07 GHz)"
                                    if prec == gbs.FP64 else
-                                   "FP32 from unit counts and clock (152 SM x 256 flop/clk x 2.07 GHz)")},
+                                   "FP32 from unit counts and clock (152 SM x 256 flop/clk x 2.07 GHz)"),
+                     "measured_fp64_peak": measured_peak,
+                     "frac_of_measured_fp64_peak": (achieved / measured_peak) if prec == gbs.FP64 else None,
+                     "measured_peak_note": "gbs_measure_fp64_peak (independent DFMA chains on every SM), "
+                                           "SM clock %s MHz during it" % pclk_s.get("sm_mhz")},
         "e2e": {"value": world * b / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(idx.nbytes),
                 "d2h_bytes_per_step": int(hp.nbytes + hl.nbytes + hh.nbytes + he.nbytes)},
-        # per step: pair terms (FP64 only), the subset kernel, finalisation
-        "gpu_launches": (3 if prec == gbs.FP64 else 2) * args.steps,
+        # per step: the route choice, pair terms and repeated-row kernel (FP64
+        # only), the subset kernel, finalisation
+        "gpu_launches": (5 if prec == gbs.FP64 else 2) * args.steps,
         "clocks": clk.summary(),
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1 and prec == gbs.FP64:
         line["cpu_baseline"] = cpu_baseline(pats, U, r)
     if rank == 0 and not args.quick:
-        line["extra"] = extras(gbs, torch)
+        line["extra"] = extras(gbs, torch, measured_peak)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -390,22 +400,90 @@ def timed_batch(gbs, torch, K, pats, precision, reps=3):
     return float(np.median(ts)), float(np.median(tk)), h[0::2] + 1j * h[1::2], er.cpu().numpy()
 
 
-def extras(gbs, torch):
+def stored_oracle(name):
+    """Stored double-double oracle Hafnians of a workload (tests/golden, written
+    by the oracle alone), or None when they come from another Haar draw."""
+    import hashlib
+
+    U, _, _ = W.workload(name)
+    fname = {"large_m900": "large_m900_oracle.json"}.get(name, name + "_oracle.json")
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", fname)) as f:
+            g = json.load(f)
+    except OSError:
+        return None
+    if g.get("U_sha256") != hashlib.sha256(np.ascontiguousarray(U, dtype=np.complex128).tobytes()).hexdigest():
+        return None
+    if "patterns" in g:
+        return np.array([complex(q["haf_dd"][0] + q["haf_dd"][1], q["haf_dd"][2] + q["haf_dd"][3])
+                         for q in g["patterns"]])
+    return np.array(g["haf_re"]) + 1j * np.array(g["haf_im"])
+
+
+def error_columns(ref, h, e, tag):
+    """Each result's relative error against the oracle and its stated bound."""
+    if ref is None:
+        return {tag + "_vs_oracle": "unavailable (stored values from another Haar draw)"}
+    err = np.abs(h - ref) / np.abs(ref)
+    return {tag + "_max_rel_err_vs_oracle": float(err.max()), tag + "_median_rel_err_vs_oracle": float(np.median(err)),
+            tag + "_max_stated_bound": float(e.max()), tag + "_within_bound": bool(np.all(err <= e)),
+            tag + "_max_err_over_bound": float(np.max(err / e))}
+
+
+def oracle_rate(pats, U, r, target_s=6.0):
+    """CPU baseline of one workload: the oracle's FP64 subset sum on all host
+    cores over a bounded sample (the workload's patterns in order, cycled), and
+    on one core over its first patterns."""
+    import oracle
+
+    B = oracle.build_B(U, r)
+    mats = [B[np.ix_(p, p)] for p in pats]
+    k = min(len(mats), max(1, oracle.num_threads()))
+    t0 = time.perf_counter()
+    oracle.haf_batch_f64(mats[:k])
+    dt = time.perf_counter() - t0
+    k2 = int(max(k, min(len(mats) * 4, k * target_s / max(dt, 1e-6))))
+    sample = [mats[i % len(mats)] for i in range(k2)]
+    t0 = time.perf_counter()
+    oracle.haf_batch_f64(sample)
+    dt2 = time.perf_counter() - t0
+    cores = oracle.num_threads()
+    oracle.set_num_threads(1)
+    try:
+        k1 = min(len(mats), 4)
+        t0 = time.perf_counter()
+        oracle.haf_batch_f64(mats[:k1])
+        dt1 = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(cores)
+    return {"value": k2 / dt2, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d patterns (the workload's %d, in order, cycled), FP64 subset sum, %.1f s"
+                      % (k2, len(pats), dt2),
+            "single_core_value": k1 / dt1, "cpu": host_cpu()}
+
+
+def extras(gbs, torch, measured_peak):
     out = {}
     peak = fp64_peak_tflops()
+
+    def frac(fl, ms):
+        a = fl / (ms * 1e-3) / 1e12
+        return {"achieved_tflops": a, "frac_of_nominal_peak": a / peak,
+                "frac_of_measured_peak": (a / measured_peak) if measured_peak else None}
+
     # mixed path on the headline workload
     U, r, pats = W.workload(WORKLOAD)
+    ref = stored_oracle(WORKLOAD)
     K = gbs.build_kernel(U, r)
     gbs.autotune(16, gbs.MIXED)
-    t64, k64, h64, _ = timed_batch(gbs, torch, K, pats, gbs.FP64)
+    t64, k64, h64, e64 = timed_batch(gbs, torch, K, pats, gbs.FP64)
     t32, k32, h32, e32 = timed_batch(gbs, torch, K, pats, gbs.MIXED)
-    relerr = np.abs(h32 - h64) / np.abs(h64)
     out["n16_mixed"] = {"probs_per_s": len(pats) / (t32 * 1e-3), "ms": t32, "kernel_ms": k32,
                         "fp64_ms": t64, "speedup_vs_fp64": t64 / t32,
-                        "max_rel_err_vs_fp64": float(relerr.max()),
-                        "max_err_bound": float(e32.max()), "within_bound": bool(np.all(relerr <= e32))}
+                        **error_columns(ref, h32, e32, "mixed"), **error_columns(ref, h64, e64, "fp64")}
     # mixed-n workload with collisions
     U, r, pats = W.workload("mixed_m144")
+    ref = stored_oracle("mixed_m144")
     K = gbs.build_kernel(U, r)
     for nn in range(8, 25, 2):
         gbs.autotune(nn, gbs.FP64)
@@ -413,23 +491,27 @@ def extras(gbs, torch):
     t64, k64, h64, e64 = timed_batch(gbs, torch, K, pats, gbs.FP64)
     t32, k32, h32, e32 = timed_batch(gbs, torch, K, pats, gbs.MIXED)
     fl = sum(model_flops(len(p)) for p in pats)
-    relerr = np.abs(h32 - h64) / np.abs(h64)
-    out["mixed_m144"] = {"fp64_probs_per_s": len(pats) / (t64 * 1e-3), "fp64_ms": t64,
-                         "fp64_frac_of_peak": fl / (k64 * 1e-3) / 1e12 / peak,
+    out["mixed_m144"] = {"fp64_probs_per_s": len(pats) / (t64 * 1e-3), "fp64_ms": t64, "fp64_kernel_ms": k64,
+                         "fp64_roofline": frac(fl, k64),
                          "mixed_probs_per_s": len(pats) / (t32 * 1e-3), "mixed_ms": t32,
-                         "mixed_max_rel_err_vs_fp64": float(relerr.max()),
-                         "mixed_within_bound": bool(np.all(relerr <= e32))}
+                         **error_columns(ref, h64, e64, "fp64"), **error_columns(ref, h32, e32, "mixed"),
+                         "cpu_baseline": oracle_rate(pats, U, r)}
     # large instances
     U, r, pats = W.workload("large_m900")
+    ref = stored_oracle("large_m900")
     K = gbs.build_kernel(U, r)
     gbs.autotune(28, gbs.FP64)
     gbs.autotune(30, gbs.FP64)
     t64, k64, h64, e64 = timed_batch(gbs, torch, K, pats, gbs.FP64, reps=2)
+    t32, k32, h32, e32 = timed_batch(gbs, torch, K, pats, gbs.MIXED, reps=2)
     fl = sum(model_flops(len(p)) for p in pats)
     out["large_m900"] = {"probs_per_s": len(pats) / (t64 * 1e-3), "ms": t64, "kernel_ms": k64,
                          "subset_terms_per_s": sum(2 ** (len(p) // 2) for p in pats) / (k64 * 1e-3),
-                         "achieved_tflops": fl / (k64 * 1e-3) / 1e12, "frac_of_peak": fl / (k64 * 1e-3) / 1e12 / peak,
-                         "max_err_est": float(e64.max())}
+                         "roofline": frac(fl, k64),
+                         "mixed_probs_per_s": len(pats) / (t32 * 1e-3), "mixed_ms": t32,
+                         **error_columns(ref, h64, e64, "fp64"), **error_columns(ref, h32, e32, "mixed"),
+                         "cpu_baseline": oracle_rate(pats[:16], U, r, target_s=8.0)}
+    out["large_m900"]["cpu_baseline"]["sample"] += " (16 of the 64 n=28 patterns)"
     out["bunched_m8"] = bunched(gbs, torch)
     out["serving"] = serving(gbs, torch)
     out["sampler"] = sampler(gbs)
@@ -438,10 +520,12 @@ def extras(gbs, torch):
 
 def bunched(gbs, torch, reps=3):
     """M = 8, r = 1, 512 patterns of 24 photons drawn with replacement: host
-    index lists take the repeated-row route (cost prod (c_j + 1)), device index
-    lists the subset sum (cost 2^12 subsets); wall time per batch, both through
-    gbs_prob_batch, their largest relative deviation and each route's largest
-    error estimate (the subset sum cancels far more on bunched patterns)."""
+    index lists take the repeated-row route chosen on the host, device index
+    lists the same route chosen on the device (cost prod (c_j + 1) terms); the
+    explicit matrices B_x through gbs_hafnian_batch take the subset sum (cost
+    2^12 subsets). Wall time per batch, the routes' largest relative deviations
+    and each route's largest error estimate (the subset sum cancels far more on
+    bunched patterns)."""
     U, r, pats = W.workload("bunched_m8")
     K = gbs.build_kernel(U, r)
     idx, n, offs = gbs.pack_patterns(pats)
@@ -451,17 +535,28 @@ def bunched(gbs, torch, reps=3):
     d_idx = torch.from_numpy(idx).cuda()
     hd = torch.zeros(2 * b, dtype=torch.float64, device="cuda")
     ed = torch.zeros(b, dtype=torch.float64, device="cuda")
+    Bd = torch.zeros(2 * 8 * 8, dtype=torch.float64, device="cuda")
+    K.copy_B(Bd)
+    Bc = Bd.cpu().numpy().view(np.complex128).reshape(8, 8)
+    flat, nm, om = gbs.pack_matrices([Bc[np.ix_(x, x)] for x in pats])
+    d_mat = torch.from_numpy(flat).cuda()
+    hm = torch.zeros(2 * b, dtype=torch.float64, device="cuda")
+    km = torch.zeros(b, dtype=torch.float64, device="cuda")
 
-    def rep_route():
+    def host_route():
         gbs.prob_batch(K, idx, n, offs, gbs.FP64, haf_out=hh, err_out=eh)
 
-    def subset_route():
+    def device_route():
         gbs.prob_batch(K, d_idx, n, offs, gbs.FP64, haf_out=hd, err_out=ed)
+        torch.cuda.synchronize()
+
+    def subset_sum():
+        gbs.hafnian_batch(d_mat, nm, om, gbs.FP64, haf_out=hm, kappa_out=km)
         torch.cuda.synchronize()
 
     gbs.autotune(24, gbs.FP64)
     ts = {}
-    for name, fn in (("repeated_row", rep_route), ("subset_sum", subset_route)):
+    for name, fn in (("repeated_row", host_route), ("device_route", device_route), ("subset_sum", subset_sum)):
         fn()
         t = []
         for _ in range(reps):
@@ -472,13 +567,17 @@ def bunched(gbs, torch, reps=3):
     a = hh[0::2] + 1j * hh[1::2]
     h = hd.cpu().numpy()
     c = h[0::2] + 1j * h[1::2]
+    q = hm.cpu().numpy()
+    sub = q[0::2] + 1j * q[1::2]
     return {"workload": "M=8 Haar U seed 5, r=1.0, 512 patterns of n=24 drawn with replacement, FP64",
             "repeated_row_probs_per_s": b / ts["repeated_row"], "repeated_row_ms": 1e3 * ts["repeated_row"],
+            "device_route_probs_per_s": b / ts["device_route"], "device_route_ms": 1e3 * ts["device_route"],
             "subset_sum_probs_per_s": b / ts["subset_sum"], "subset_sum_ms": 1e3 * ts["subset_sum"],
             "speedup": ts["subset_sum"] / ts["repeated_row"],
-            "max_rel_dev_between_routes": float(np.max(np.abs(a - c) / np.abs(c))),
+            "max_rel_dev_between_routes": float(np.max(np.abs(a - c) / np.abs(a))),
+            "subset_sum_max_rel_dev_vs_repeated_row": float(np.max(np.abs(sub - a) / np.abs(a))),
             "repeated_row_max_err_est": float(eh.max()),
-            "subset_sum_max_err_est": float(ed.cpu().numpy().max())}
+            "subset_sum_max_err_est": float(np.max(km.cpu().numpy() * 24 * 2.0 ** -53))}
 
 
 def sampler(gbs):
@@ -496,9 +595,24 @@ def sampler(gbs):
     t0 = time.perf_counter()
     gbs.photon_number_dist(K36, 200)
     t_pn = time.perf_counter() - t0
+    # Algorithm 1 chain samples in the paper's m = n^2 setting (Sec. 3.5)
+    chain = {}
+    for n_, reps in ((12, 3), (16, 1)):
+        m_ = n_ * n_
+        Kc = gbs.build_kernel(W.haar_unitary(m_, 40 + n_), np.full(m_, 0.8814))
+        rng = np.random.default_rng(n_)
+        gbs.sample_chain(Kc, n_, rng.random(n_))  # warm-up
+        ts = []
+        for _ in range(reps):
+            uu = rng.random(n_)
+            t0 = time.perf_counter()
+            gbs.sample_chain(Kc, n_, uu)
+            ts.append(time.perf_counter() - t0)
+        chain["n%d_m%d" % (n_, m_)] = {"s_per_sample": float(np.median(ts)), "samples": reps}
     return {"bruteforce_n4_m16": {"configurations": 3876, "draws": len(u), "wall_ms": 1e3 * t_bf,
                                   "draws_per_s": len(u) / t_bf, "P_n": total},
-            "photon_number_m36_nmax200_wall_ms": 1e3 * t_pn}
+            "photon_number_m36_nmax200_wall_ms": 1e3 * t_pn,
+            "chain_sampler": chain}
 
 
 def serve_stream(gbs, K, reqs, precision):

@@ -53,9 +53,11 @@ extern "C" {
 #define GBS_ETIMEDOUT (-5) /* a bounded device or host wait gave up */
 #define GBS_ECUDA (-6)     /* a CUDA runtime call failed (message has the CUDA error) */
 #define GBS_ENOENT (-7)    /* unknown serving ticket */
+#define GBS_ECANCELED (-8) /* serving request cancelled by gbs_serve_cancel */
 
 #define GBS_FP64 0  /* per-subset arithmetic in FP64, signed sum in double-double */
-#define GBS_MIXED 1 /* per-subset arithmetic in FP32, signed sum in float-float, FP64 final sum */
+#define GBS_MIXED 1 /* power traces in FP32; their exponential series (the characteristic-
+                       polynomial recurrence) in FP64 and the signed sum in double-double */
 
 #define GBS_MAX_N 32 /* largest photon number (matrix order) accepted */
 
@@ -148,13 +150,16 @@ int gbs_hafnian_batch_noalloc(const double* A_ri, const int* n, const int64_t* o
  * idx is checked on the device: a pattern with an out-of-range index gets NaN
  * outputs and no memory outside B is read.
  * Route: every pattern takes the subset sum of Sec. 2.3, except that with
- * GBS_FP64 and a HOST idx, a pattern whose photons are bunched into few modes
- * (at most 16 distinct modes, prod_j (s_j + 1) terms costing well under the
- * subset sum) takes the repeated-row sum instead (the moment-extraction
- * identity of Kan, 2008; not in the paper). On such patterns that route is
- * also the accurate one: the subset sum cancels strongly there (errors up to
- * ~1e-8 measured at n = 24 in 8 modes, flagged by err_est_out), so pass
- * bunched patterns in host memory.
+ * GBS_FP64 a pattern whose photons are bunched into few modes (at most 16
+ * distinct modes, prod_j (s_j + 1) terms costing well under the subset sum)
+ * takes the repeated-row sum instead (the moment-extraction identity of Kan,
+ * 2008; not in the paper). The choice is made on the host for a host idx and
+ * on the device for a device idx, by the same rule and with the same result
+ * bits (a device batch reserves repeated-row partial slots for at most 2^20
+ * term chunks in all; patterns past that, in batch order, keep the subset
+ * sum). On such patterns that route is also the accurate one: the subset sum
+ * cancels strongly there (errors up to ~1e-8 measured at n = 24 in 8 modes,
+ * flagged by err_est_out).
  * Errors: GBS_EINVAL, GBS_ERANGE, GBS_ENOMEM, GBS_ECUDA. */
 int gbs_prob_batch(const gbs_kernel* k, const int* idx, const int* n, const int64_t* offs,
                    int batch, int precision, void* stream, double* p_out, double* logp_out,
@@ -168,6 +173,13 @@ int gbs_prob_batch(const gbs_kernel* k, const int* idx, const int* n, const int6
  * for concurrent use from several threads. The paper has no counterpart
  * (measurement only). */
 int gbs_set_timing_events(void* start, void* stop);
+
+/* Measurement: the FP64 (DFMA) throughput of the current device in TFLOP/s,
+ * from a kernel that fills every SM with independent DFMA chains (best of
+ * three timed runs after a warm-up, CUDA events on `stream`; about 50 ms).
+ * The denominator of the subset sum's roofline fraction; the paper has no
+ * counterpart. Errors: GBS_EINVAL, GBS_ENOMEM, GBS_ECUDA. */
+int gbs_measure_fp64_peak(void* stream, double* tflops_out);
 
 /* ------------------------------------------------------------------------ */
 /* Autotuning                                                               */
@@ -211,12 +223,16 @@ int gbs_sample_bruteforce(const gbs_kernel* k, int n, const double* uniforms, in
 /* Theorem 1 (Sec. 3.3, Algorithm 2): marginal probabilities
  * q_n(x_1..x_k) = sum over x_{k+1..n} of |Haf(W_x)|^2 / f_n, W = U U^T, of
  * `batch` ordered prefixes of length k, for n-photon samples with identical
- * squeezing on every mode (the kernel's r must all be equal and > 0). The
- * sub-Hafnians of every even subset of each prefix come from the batched FP64
- * path; the sums over A, B, mu of Theorem 1 run one block per prefix.
+ * squeezing on every mode (the kernel's r must all be equal and > 0: the
+ * theorem sums out the unsampled photons with the unitarity of W, which
+ * B = U diag(tanh r_i) U^T lacks when the r_i differ). The sub-Hafnians of
+ * every even subset of each prefix come from the batched FP64 path; the sums
+ * over s, s', A, B, mu of Theorem 1 are regrouped by the multisets of modes
+ * they involve (at most 3^k products per prefix) and run one thread per
+ * multiset.
  *   x      batch * k mode indices in [0, m), prefix b at [b * k, (b + 1) * k),
  *          host or device (read before return).
- *   k      0..min(n, 10).  n  even, <= GBS_MAX_N.
+ *   k      0..min(n, 20).  n  even, <= GBS_MAX_N.
  *   q_out  batch doubles, host or device. k = 0 gives 1; k = n gives
  *          |Haf(W_x)|^2 / f_n (Eq. EqDisE).
  * Errors: GBS_EINVAL (also unequal squeezing), GBS_ERANGE, GBS_ENOMEM, GBS_ECUDA. */
@@ -227,7 +243,7 @@ int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int batch, int
  * rule, x_k drawn from the m conditional weights q_n(x_1..x_{k-1}, l),
  * l = 0..m-1 (gbs_marginal_batch), by the inverse CDF in mode order with the
  * caller's uniform u_k. Identical squeezing only.
- *   n         even, 0..10.
+ *   n         even, 0..20.
  *   uniforms  n numbers in [0, 1), HOST memory.
  *   x_out     n ints, HOST memory: the mode of each photon in draw order.
  * Errors: GBS_EINVAL, GBS_ERANGE, GBS_ENOMEM, GBS_ECUDA. */
@@ -237,7 +253,7 @@ int gbs_sample_chain(const gbs_kernel* k, int n, const double* uniforms, void* s
  * P_n of Eq. Eqdistribution restricted to n <= n_max and renormalised (inverse
  * CDF with uniforms[0]), then the n photons placed by gbs_sample_chain with
  * uniforms[1..n]. Identical squeezing only.
- *   n_max     0..10 (the chain sampler's limit); the mass above n_max is
+ *   n_max     0..20 (the chain sampler's limit); the mass above n_max is
  *             left out, so choose n_max where P_n has become negligible.
  *   uniforms  n_max + 1 numbers in [0, 1), HOST memory.
  *   n_out     HOST int: the drawn photon number (even).
@@ -260,14 +276,17 @@ typedef struct gbs_serve_opts {
   double wait_timeout_s;  /* bound on any internal wait (0 = 10 s) */
   int max_n;              /* largest photon number accepted (0 = GBS_MAX_N); a smaller
                              bound lets steps run more warps per SM */
+  int fault_alloc_failures; /* testing: the first N admissions find the memory budget
+                             used up (the request waits and is retried), 0 = none */
 } gbs_serve_opts;
 
-/* Start a server for kernel matrix k (requests keep the default ordering of
- * the subset sum, as in gbs_hafnian_batch_noalloc: for n >= 28 the batched
- * calls are the more accurate route): a host thread admits requests into
+/* Start a server for kernel matrix k: a host thread admits requests into
  * device slots as slots and memory free up, and runs steps that advance every
  * resident request's subset sum together; partial sums stay on the device
- * between steps. k must outlive the server. opts may be NULL. */
+ * between steps. A request with n >= 26 is admitted once the ordering probe
+ * of gbs_prob_batch has chosen its ordering (on a side stream, several
+ * waiting requests per launch), so its subset sum cancels as little as in
+ * the batched call. k must outlive the server. opts may be NULL. */
 int gbs_serve_create(const gbs_kernel* k, const gbs_serve_opts* opts, gbs_server** out);
 
 /* Enqueue one pattern (host index list of n entries, copied before return).
@@ -278,8 +297,18 @@ int gbs_serve_submit(gbs_server* s, const int* idx, int n, int precision, int64_
 
 /* Returns 0 and fills p, haf_ri (2 doubles), err_est (each may be NULL) when
  * the request is done (its ticket is then released), 1 while it is pending,
- * or a negative error (GBS_ENOENT for an unknown or already-collected ticket). */
+ * or a negative error: GBS_ENOENT for an unknown or already-collected ticket;
+ * for a request that ended without a result (its ticket is then released)
+ * GBS_ECANCELED, GBS_ENOMEM (its partial sums exceed the whole memory budget),
+ * GBS_ETIMEDOUT or GBS_ECUDA. */
 int gbs_serve_poll(gbs_server* s, int64_t ticket, double* p, double* haf_ri, double* err_est);
+
+/* Cancel a request: 0 when it was still pending (its ticket then polls
+ * GBS_ECANCELED; device work already in flight for it finishes and is
+ * discarded, and its slot and memory are freed after that), 1 when it had
+ * already finished (poll it as usual), GBS_ENOENT for an unknown or collected
+ * ticket. Host-side only: the paper has no counterpart. */
+int gbs_serve_cancel(gbs_server* s, int64_t ticket);
 
 /* Counters of a server since creation (for monitoring; the paper has no
  * counterpart). Step wall time runs from a step's launch to the host seeing
@@ -300,6 +329,11 @@ typedef struct gbs_serve_stats_t {
   double update_max_s;    /* longest update of a step graph's parameters */
   double submit_max_s;    /* longest submission of a step (graph launch, or the
                              direct copies and launches without graphs) */
+  int64_t probed;         /* requests whose ordering the probe chose (n >= 26) */
+  int64_t cancelled;      /* requests cancelled while pending */
+  int64_t alloc_waits;    /* admissions that found the memory budget used up and waited */
+  int64_t arena_slots;    /* partial sums the memory budget holds (a request needs one
+                             per work item) */
 } gbs_serve_stats_t;
 int gbs_serve_stats(gbs_server* s, gbs_serve_stats_t* out);
 

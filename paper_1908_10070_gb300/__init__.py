@@ -19,7 +19,7 @@ from . import build as _build
 
 __all__ = [
     "FP64", "MIXED", "MAX_N", "GbsError", "lib", "build_kernel", "KernelMatrix",
-    "hafnian_batch", "hafnian_batch_noalloc", "prob_batch", "autotune", "Server", "serve_create", "pack_patterns",
+    "hafnian_batch", "hafnian_batch_noalloc", "prob_batch", "autotune", "measure_fp64_peak", "Server", "serve_create", "pack_patterns",
     "pack_matrices", "last_error", "ERRORS", "photon_number_dist", "sample_bruteforce", "marginal_batch", "sample_chain",
 ]
 
@@ -27,7 +27,7 @@ FP64 = 0
 MIXED = 1
 MAX_N = 32
 ERRORS = {0: "GBS_OK", -1: "GBS_EINVAL", -2: "GBS_ENOMEM", -3: "GBS_ERANGE", -4: "GBS_EAGAIN",
-          -5: "GBS_ETIMEDOUT", -6: "GBS_ECUDA", -7: "GBS_ENOENT"}
+          -5: "GBS_ETIMEDOUT", -6: "GBS_ECUDA", -7: "GBS_ENOENT", -8: "GBS_ECANCELED"}
 
 _lock = threading.Lock()
 _lib = None
@@ -45,14 +45,16 @@ class ServeStats(ctypes.Structure):
                 ("step_wall_max_s", ctypes.c_double), ("step_device_s", ctypes.c_double),
                 ("step_device_max_s", ctypes.c_double), ("poll_gap_max_s", ctypes.c_double),
                 ("launch_max_s", ctypes.c_double), ("update_max_s", ctypes.c_double),
-                ("submit_max_s", ctypes.c_double)]
+                ("submit_max_s", ctypes.c_double), ("probed", ctypes.c_int64),
+                ("cancelled", ctypes.c_int64), ("alloc_waits", ctypes.c_int64),
+                ("arena_slots", ctypes.c_int64)]
 
 
 class ServeOpts(ctypes.Structure):
     _fields_ = [("max_slots", ctypes.c_int), ("mem_budget", ctypes.c_size_t),
                 ("queue_capacity", ctypes.c_int), ("subsets_per_step", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("wait_timeout_s", ctypes.c_double),
-                ("max_n", ctypes.c_int)]
+                ("max_n", ctypes.c_int), ("fault_alloc_failures", ctypes.c_int)]
 
 
 def lib():
@@ -76,10 +78,12 @@ def lib():
             L.gbs_sample_chain.argtypes = [vp, ctypes.c_int, dp, vp, ip]
             L.gbs_sample.argtypes = [vp, ctypes.c_int, dp, vp, ctypes.POINTER(ctypes.c_int), ip]
             L.gbs_autotune.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int)]
+            L.gbs_measure_fp64_peak.argtypes = [vp, dp]
             L.gbs_set_timing_events.argtypes = [vp, vp]
             L.gbs_serve_create.argtypes = [vp, ctypes.POINTER(ServeOpts), ctypes.POINTER(ctypes.c_void_p)]
             L.gbs_serve_submit.argtypes = [vp, ip, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
             L.gbs_serve_poll.argtypes = [vp, ctypes.c_int64, dp, dp, dp]
+            L.gbs_serve_cancel.argtypes = [vp, ctypes.c_int64]
             L.gbs_serve_destroy.argtypes = [vp]
             L.gbs_serve_stats.argtypes = [vp, ctypes.POINTER(ServeStats)]
             L.gbs_last_error.restype = ctypes.c_char_p
@@ -273,6 +277,13 @@ def sample(kernel: KernelMatrix, n_max: int, uniforms, stream=None) -> np.ndarra
     return x[:n.value]
 
 
+def measure_fp64_peak(stream=None) -> float:
+    """gbs_measure_fp64_peak: the device's measured DFMA throughput, TFLOP/s."""
+    v = ctypes.c_double()
+    _check(lib().gbs_measure_fp64_peak(_stream(stream), ctypes.byref(v)))
+    return v.value
+
+
 def autotune(n, precision=FP64, stream=None) -> int:
     c = ctypes.c_int()
     _check(lib().gbs_autotune(int(n), int(precision), _stream(stream), ctypes.byref(c)))
@@ -283,10 +294,10 @@ class Server:
     """Continuous-batching server (gbs_serve_*)."""
 
     def __init__(self, kernel: KernelMatrix, max_slots=0, mem_budget=0, queue_capacity=0,
-                 subsets_per_step=0, use_graphs=1, wait_timeout_s=0.0, max_n=0):
+                 subsets_per_step=0, use_graphs=1, wait_timeout_s=0.0, max_n=0, fault_alloc_failures=0):
         self.kernel = kernel
         o = ServeOpts(max_slots, mem_budget, queue_capacity, subsets_per_step, use_graphs, wait_timeout_s,
-                      max_n)
+                      max_n, fault_alloc_failures)
         h = ctypes.c_void_p()
         _check(lib().gbs_serve_create(kernel.handle, ctypes.byref(o), ctypes.byref(h)))
         self.handle = h
@@ -313,6 +324,12 @@ class Server:
         _check(rc)
         return p.value, complex(hf[0], hf[1]), e.value
 
+    def cancel(self, ticket) -> int:
+        """0: cancelled (its poll raises GBS_ECANCELED); 1: already finished."""
+        rc = lib().gbs_serve_cancel(self.handle, int(ticket))
+        _check(rc)
+        return rc
+
     def stats(self) -> dict:
         st = ServeStats()
         _check(lib().gbs_serve_stats(self.handle, ctypes.byref(st)))
@@ -320,8 +337,8 @@ class Server:
 
     def destroy(self):
         if self.handle:
-            _check(lib().gbs_serve_destroy(self.handle))
-            self.handle = None
+            h, self.handle = self.handle, None  # freed even when destroy reports an error
+            _check(lib().gbs_serve_destroy(h))
 
     def __del__(self):
         try:

@@ -5,6 +5,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <cmath>
 #include <map>
 #include <mutex>
 #include <string>
@@ -376,7 +378,6 @@ void Planner::fill(PatDesc* pats, WorkItem* items, WorkItem* rep_items) {
 // ceil(h/2) to h-3 (where most of sum |f| lies), and runs the full sum in the
 // ordering with the smallest estimate. The sample costs a few per cent of
 // the full sum at these orders.
-constexpr int kPairingMinN = 26;
 constexpr int kPairingCands = 16;
 constexpr int kProbePerSize = 8;
 static_assert(kProbePerSize < kMaxProbeSample, "probe sample count must index the reciprocal table");
@@ -469,15 +470,10 @@ static double subset_cost(int n) {
   return c;
 }
 
-// Terms (ceil(T / 2)) that the repeated-row route sums for index list x of
-// length n, or 0 when the subset sum is the cheaper route: the route needs a
-// repeated mode, at most kRepMaxDistinct distinct modes and T <= 2^30, and its
-// terms (about d^2 + 3d + 60 FP64 operations each) must cost under a quarter
-// of the subset sum (the margin covers its lower efficiency).
-static int rep_half_terms(const int* x, int n) {
-  if (n < 4 || (n & 1)) return 0;
-  // T >= 2^d, so beyond d_max(n) the route can never win: stop scanning there
-  // (collision-free lists, the common case, stop after about n/2 entries)
+// Most distinct modes with which the repeated-row route can still win at
+// order n: T >= 2^d, so beyond it the route never does (collision-free lists,
+// the common case, stop their scan after about n/2 entries).
+static int rep_d_max(int n) {
   static const std::vector<int> d_max = [] {  // thread-safe one-time initialisation
     std::vector<int> t(kMaxN + 1, 0);
     for (int v = 4; v <= kMaxN; v += 2) {
@@ -487,7 +483,40 @@ static int rep_half_terms(const int* x, int n) {
     }
     return t;
   }();
-  const int dmx = d_max[n];
+  return (n >= 0 && n <= kMaxN) ? d_max[n] : 0;
+}
+
+// Largest number of repeated-row partials (term chunks) that a pattern of
+// order n can need under the rule below: T = prod (c_j + 1) is largest for
+// balanced multiplicities, and the cost condition bounds ceil(T / 2) too.
+static int64_t rep_max_chunks(int n) {
+  static const std::vector<int64_t> table = [] {  // thread-safe one-time initialisation
+    std::vector<int64_t> t(kMaxN + 1, 0);
+    for (int v = 4; v <= kMaxN; v += 2) {
+      const double pc = subset_cost(v);
+      int64_t best = 0;
+      for (int d = 1; d <= rep_d_max(v) && d < v; ++d) {
+        const int q = v / d, r = v % d;
+        const double T = std::min(std::pow(q + 2.0, r) * std::pow(q + 1.0, d - r), 0x1p30);
+        const double lim = std::ceil(pc / (4.0 * (double)(d * d + 3 * d + 60)));
+        best = std::max(best, (int64_t)std::min(std::ceil(T / 2), lim));
+      }
+      t[v] = (best + kRepTermsPerItem - 1) / kRepTermsPerItem;
+    }
+    return t;
+  }();
+  return (n >= 0 && n <= kMaxN) ? table[n] : 0;
+}
+
+// Terms (ceil(T / 2)) that the repeated-row route sums for index list x of
+// length n, or 0 when the subset sum is the cheaper route: the route needs a
+// repeated mode, at most kRepMaxDistinct distinct modes and T <= 2^30, and its
+// terms (about d^2 + 3d + 60 FP64 operations each) must cost under a quarter
+// of the subset sum (the margin covers its lower efficiency). The route
+// choice on the device (route_plan_kernel) applies the same rule.
+static int rep_half_terms(const int* x, int n) {
+  if (n < 4 || (n & 1)) return 0;
+  const int dmx = rep_d_max(n);
   int vals[kMaxN], cnt[kMaxN], d = 0;
   for (int i = 0; i < n; ++i) {
     int j = 0;
@@ -607,6 +636,16 @@ int run_batch(const BatchArgs& a) {
   }
   if (a.mode == BatchArgs::HAFNIAN && src_elems > 0 && a.src == nullptr)
     return fail(GBS_EINVAL, "A_ri is null");
+  // FP64 index lists in device memory: the route choice above is made on the
+  // device (route_plan_kernel) before the subset sum; repeated-row partial
+  // slots are reserved for the most each pattern's order can need, up to
+  // kDevRepCap in all (patterns past that in batch order keep the subset sum)
+  constexpr int64_t kDevRepCap = (int64_t)1 << 20;
+  int64_t dev_rep_cap = 0;
+  if (a.mode == BatchArgs::PROB && a.precision == GBS_FP64 && idx_dev && idx_elems > 0) {
+    for (int b = 0; b < batch; ++b) dev_rep_cap += rep_max_chunks(a.n[b]);
+    dev_rep_cap = std::min(dev_rep_cap, kDevRepCap);
+  }
   if (a.mode == BatchArgs::PROB && idx_elems > 0 && a.idx == nullptr)
     return fail(GBS_EINVAL, "idx is null");
 
@@ -679,8 +718,10 @@ int run_batch(const BatchArgs& a) {
   const size_t pstatus_b = n_sel ? al(sizeof(int) * n_probe) : 0;  // zeroed with ctr and status
   const size_t pparts_b = n_sel ? al(sizeof(Partial) * n_pitems) : 0;
   const size_t chparts_b = n_chunks ? al(sizeof(Partial) * n_chunks) : 0;
+  // route choice on the device: rep_half | rep_end | repeated-row partials
+  const size_t droute_b = dev_rep_cap ? 2 * al(sizeof(int) * batch) + al(sizeof(Partial) * dev_rep_cap) : 0;
   const size_t total_b =
-      up_b + parts_b + ctr_b + status_b + pstatus_b + outs_b + a32_b + pt_b + pparts_b + chparts_b;
+      up_b + parts_b + ctr_b + status_b + pstatus_b + outs_b + a32_b + pt_b + pparts_b + chparts_b + droute_b;
 
   void* host_stage = nullptr;
   int slot = -1;
@@ -782,6 +823,10 @@ int run_batch(const BatchArgs& a) {
   Partial* d_chparts =
       n_chunks ? (Partial*)(dm + up_b + parts_b + ctr_b + status_b + pstatus_b + outs_b + a32_b + pt_b + pparts_b)
                : nullptr;
+  unsigned char* droute = dm + (total_b - droute_b);
+  int* d_rephalf = dev_rep_cap ? (int*)droute : nullptr;
+  int* d_repend = dev_rep_cap ? (int*)(droute + al(sizeof(int) * batch)) : nullptr;
+  Partial* d_repparts = dev_rep_cap ? (Partial*)(droute + 2 * al(sizeof(int) * batch)) : nullptr;
 
   int ret = GBS_OK;
   do {
@@ -819,9 +864,30 @@ int run_batch(const BatchArgs& a) {
       if (need < blocks) blocks = (int)need;
       const bool timed = g_time_start && g_time_stop && !a.cfg_override;
       if (timed) cudaEventRecord(g_time_start, st);
+      if (dev_rep_cap) {
+        RoutePlan RP;
+        memset(&RP, 0, sizeof(RP));
+        RP.idx = d_idx;
+        RP.pats = d_pats;
+        RP.batch = batch;
+        RP.m_bound = a.m;
+        RP.cap = (int)dev_rep_cap;
+        for (int v = 0; v <= kMaxN; ++v) {
+          RP.subset_cost[v] = (v >= 4 && !(v & 1)) ? subset_cost(v) : 0.0;
+          RP.d_max[v] = rep_d_max(v);
+        }
+        RP.rep_half = d_rephalf;
+        RP.rep_end = d_repend;
+        RP.rep_total = d_ctr + 56;
+        RP.blocks_done = (unsigned*)(d_ctr + 57);
+        e = launch_route_plan(RP, st);
+        if (e != cudaSuccess) { ret = cuda_fail(e, "route choice launch"); break; }
+        L.skip = d_rephalf;
+      }
       if (n_sel) {
         // probe launch over the candidate orderings, then the choice per matrix
         HafLaunch Lp = L;
+        Lp.skip = nullptr;  // probe matrices are numbered differently
         Lp.pats = d_ppats;
         Lp.items = d_pitems;
         Lp.n_items = n_pitems;
@@ -878,6 +944,26 @@ int run_batch(const BatchArgs& a) {
         e = launch_haf_repeated(R, st);
         if (e != cudaSuccess) { ret = cuda_fail(e, "repeated-row kernel launch"); break; }
       }
+      if (dev_rep_cap) {
+        // the patterns the device chose for the repeated-row sum (the item
+        // count is read on the device; the grid covers the reservation)
+        RepLaunch R;
+        R.B = a.B;
+        R.idx = d_idx;
+        R.pats = d_pats;
+        R.items = nullptr;
+        R.n_items = (int)dev_rep_cap;
+        R.n_items_dev = d_ctr + 56;
+        R.m_bound = L.m_bound;
+        R.counter = d_ctr + 58;
+        R.status = d_status;
+        R.parts = d_repparts;
+        R.rep_half = d_rephalf;
+        R.rep_end = d_repend;
+        R.batch = batch;
+        e = launch_haf_repeated(R, st);
+        if (e != cudaSuccess) { ret = cuda_fail(e, "repeated-row kernel launch"); break; }
+      }
       if (timed) cudaEventRecord(g_time_stop, st);
     }
     if (n_chunks && n_items + n_rep > 0) {
@@ -901,6 +987,11 @@ int run_batch(const BatchArgs& a) {
     }
     F.idx = (a.mode == BatchArgs::PROB) ? d_idx : nullptr;
     F.status = d_status;
+    if (dev_rep_cap && n_items > 0) {
+      F.rep_half = d_rephalf;
+      F.rep_end = d_repend;
+      F.rep_parts = d_repparts;
+    }
     F.batch = batch;
     F.precision = a.precision;
     F.log_norm = a.log_norm_dev;
@@ -943,6 +1034,162 @@ int run_batch(const BatchArgs& a) {
     if (e != cudaSuccess) ret = cuda_fail(e, "stream synchronize");
   }
   return ret;
+}
+
+// ------------------------------------------------------------------------
+// the ordering probe on its own (serving loop)
+// ------------------------------------------------------------------------
+int order_probe_launch(const gbs_kernel* k, const int* const* lists, const int* n, int count, int stage_h,
+                       const TuneCfg& cfg, cudaStream_t st, OrderProbe* out) {
+  out->n_lists = count;
+  out->n.assign(n, n + count);
+  PairingPlan pp;
+  plan_pairing(n, count, GBS_MIXED, cfg.warp_bytes, stage_h, nullptr, &pp);
+  out->perm = pp.perm;
+  out->sel = pp.sel;
+  const int n_sel = (int)pp.sel.size();
+  if (n_sel == 0) return GBS_OK;
+  const int n_probe = (int)pp.pats.size();
+  const int n_pitems = (int)pp.items.size();
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  // upload: idx (kMaxN per list) | probe pats | items | perm | probe perm offsets | sel
+  const size_t idx_b = al(sizeof(int) * kMaxN * count), ppats_b = al(sizeof(PatDesc) * n_probe);
+  const size_t items_b = al(sizeof(WorkItem) * n_pitems), perm_b = al(sizeof(int) * pp.perm.size());
+  const size_t pperm_b = al(sizeof(int) * n_probe), sel_b = al(sizeof(int) * n_sel);
+  const size_t up_b = idx_b + ppats_b + items_b + perm_b + pperm_b + sel_b;
+  // device only: partials | counter, completion word | status | chosen offsets
+  const size_t parts_b = al(sizeof(Partial) * n_pitems), ctr_b = 256, status_b = al(sizeof(int) * n_probe);
+  const size_t mperm_b = al(sizeof(int) * count);
+  const size_t total_b = up_b + parts_b + ctr_b + status_b + mperm_b;
+  void* hv = nullptr;
+  // pinned: the uploads, then the results and the completion word
+  int rc = pinned_acquire(up_b + mperm_b + 256, &hv, &out->pin_slot);
+  if (rc) return rc;
+  unsigned char* hs = (unsigned char*)hv;
+  int* h_idx = (int*)hs;
+  for (int i = 0; i < count; ++i) memcpy(h_idx + (size_t)i * kMaxN, lists[i], sizeof(int) * n[i]);
+  PatDesc* h_ppats = (PatDesc*)(hs + idx_b);
+  for (int q = 0; q < n_probe; ++q) {
+    PatDesc d = pp.pats[q];
+    d.src_off = 0;
+    d.idx_off = (int64_t)pp.sel[q / kPairingCands] * kMaxN;
+    d.ld = k->m;
+    h_ppats[q] = d;
+  }
+  memcpy(hs + idx_b + ppats_b, pp.items.data(), sizeof(WorkItem) * n_pitems);
+  memcpy(hs + idx_b + ppats_b + items_b, pp.perm.data(), sizeof(int) * pp.perm.size());
+  memcpy(hs + idx_b + ppats_b + items_b + perm_b, pp.perm_off.data(), sizeof(int) * n_probe);
+  memcpy(hs + idx_b + ppats_b + items_b + perm_b + pperm_b, pp.sel.data(), sizeof(int) * n_sel);
+  out->res = (int*)(hs + up_b);
+  out->flag = (volatile int*)(hs + up_b + mperm_b);
+  *out->flag = 0;
+  static std::atomic<unsigned> seq{0};
+  const unsigned byte = 1u + seq.fetch_add(1u) % 255u;  // the word's four bytes, never 0
+  out->expect = (int)(byte * 0x01010101u);
+  cudaError_t e = scratch_alloc(&out->dmem, total_b, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    pinned_release(out->pin_slot, st);
+    out->pin_slot = -1;
+    out->dmem = nullptr;
+    return fail(GBS_ENOMEM, "probe scratch of %zu bytes: %s", total_b, cudaGetErrorString(e));
+  }
+  unsigned char* dm = (unsigned char*)out->dmem;
+  int ret = GBS_OK;
+  do {
+    e = cudaMemcpyAsync(dm, hs, up_b, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) { ret = cuda_fail(e, "probe upload"); break; }
+    int* d_ctr = (int*)(dm + up_b + parts_b);
+    e = cudaMemsetAsync(d_ctr, 0, ctr_b + status_b, st);
+    if (e != cudaSuccess) { ret = cuda_fail(e, "probe memset"); break; }
+    HafLaunch Lp;
+    memset(&Lp, 0, sizeof(Lp));
+    Lp.src = k->B;
+    Lp.src32 = k->B32;
+    Lp.idx = (const int*)dm;
+    Lp.pats = (const PatDesc*)(dm + idx_b);
+    Lp.items = (const WorkItem*)(dm + idx_b + ppats_b);
+    Lp.n_items = n_pitems;
+    Lp.counter = d_ctr;
+    Lp.status = (int*)(dm + up_b + parts_b + ctr_b);
+    Lp.parts = (Partial*)(dm + up_b);
+    Lp.warp_bytes = cfg.warp_bytes;
+    Lp.stage_h = stage_h;
+    Lp.perm = (const int*)(dm + idx_b + ppats_b + items_b);
+    Lp.perm_off = (const int*)(dm + idx_b + ppats_b + items_b + perm_b);
+    Lp.batch = n_probe;
+    const int sms = device_sm_count();
+    const int pwpb = std::max(1, std::min((n_pitems + sms - 1) / sms, cfg.warps_per_block));
+    const int per_sm = max_blocks_per_sm(GBS_MIXED, pwpb, pwpb * cfg.warp_bytes);
+    if (per_sm < 1) { ret = fail(GBS_EINVAL, "probe shape does not fit an SM"); break; }
+    const int blocks = std::min(sms * per_sm, (n_pitems + pwpb - 1) / pwpb);
+    e = launch_haf_subsets(Lp, GBS_MIXED, blocks, pwpb, st);
+    if (e != cudaSuccess) { ret = cuda_fail(e, "probe launch"); break; }
+    int* d_mperm = (int*)(dm + up_b + parts_b + ctr_b + status_b);
+    PairingSelect S;
+    S.probe_pats = Lp.pats;
+    S.probe_items = Lp.items;
+    S.probe_parts = Lp.parts;
+    S.probe_perm_off = Lp.perm_off;
+    S.sel_pat = (const int*)(dm + idx_b + ppats_b + items_b + perm_b + pperm_b);
+    S.n_sel = n_sel;
+    S.n_cand = kPairingCands;
+    S.main_perm_off = d_mperm;
+    e = launch_pairing_select(S, st);
+    if (e != cudaSuccess) { ret = cuda_fail(e, "pairing choice launch"); break; }
+    e = cudaMemcpyAsync(out->res, d_mperm, sizeof(int) * count, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) { ret = cuda_fail(e, "probe result copy"); break; }
+    // the completion word after the results (stream order)
+    e = cudaMemsetAsync(d_ctr + 32, (int)byte, sizeof(int), st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync((void*)out->flag, d_ctr + 32, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) { ret = cuda_fail(e, "probe completion word"); break; }
+    if (!out->done) {
+      e = cudaEventCreateWithFlags(&out->done, cudaEventDisableTiming);
+      if (e != cudaSuccess) { ret = cuda_fail(e, "probe event"); break; }
+    }
+    e = cudaEventRecord(out->done, st);
+    if (e != cudaSuccess) { ret = cuda_fail(e, "probe event record"); break; }
+  } while (0);
+  scratch_free(out->dmem, st);
+  out->dmem = nullptr;
+  if (ret != GBS_OK) {
+    cudaStreamSynchronize(st);
+    cudaGetLastError();
+    order_probe_release(out, st);
+  }
+  return ret;
+}
+
+bool order_probe_ready(const OrderProbe& pr) {
+  if (pr.flag == nullptr || *pr.flag != pr.expect) return false;
+  std::atomic_thread_fence(std::memory_order_acquire);  // the results before the word
+  return true;
+}
+
+bool order_probe_result(const OrderProbe& pr, int i, int* positions) {
+  if (i < 0 || i >= pr.n_lists || pr.res == nullptr) return false;
+  if (std::find(pr.sel.begin(), pr.sel.end(), i) == pr.sel.end()) return false;
+  const int off = pr.res[i], v = pr.n[i];
+  if (off < 0 || off + v > (int)pr.perm.size()) return false;
+  memcpy(positions, pr.perm.data() + off, sizeof(int) * v);
+  return true;
+}
+
+void order_probe_release(OrderProbe* pr, cudaStream_t st) {
+  if (pr->pin_slot >= 0) pinned_release(pr->pin_slot, st);
+  pr->pin_slot = -1;
+  pr->res = nullptr;
+  pr->flag = nullptr;
+  pr->sel.clear();
+  pr->perm.clear();
+  pr->n.clear();
+  pr->n_lists = 0;
+}
+
+void order_probe_destroy(OrderProbe* pr) {
+  if (pr->done) cudaEventDestroy(pr->done);
+  pr->done = nullptr;
 }
 
 }  // namespace gbs

@@ -7,8 +7,9 @@
 // (Haf is homogeneous of degree n/2).
 //
 // B is complex symmetric, so only tiles on or above the diagonal are computed
-// and each is written to both (i, j) and (j, i). The product is FP64 (DFMA
-// bound); it runs once per interferometer.
+// and each is written to both (i, j) and (j, i). The product is summed in
+// double-double and rounded once (FP64 bound, about ten times the plain
+// product's work); it runs once per interferometer.
 #include <math.h>
 
 #include "gbs_internal.cuh"
@@ -38,43 +39,72 @@ __global__ void tanh_lognorm_kernel(const double* __restrict__ r, int m, double*
   if (threadIdx.x == 0) *log_norm = part[0];
 }
 
-// One 16x16 tile of B per block: B[i][j] = sum_k U[i][k] t_k U[j][k].
+// Error-free transformations (Knuth's two-sum; the FMA-based exact product).
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+  s = a + b;
+  const double bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void two_prod(double a, double b, double& p, double& e) {
+  p = a * b;
+  e = fma(a, b, -p);
+}
+
+// acc (hi, lo) += (ah + al) * v: the product of a double-double and a double,
+// its leading part exact (two_prod) and the rest added to the low word.
+__device__ __forceinline__ void dot2_add(double& hi, double& lo, double ah, double al, double v) {
+  double p, e, s, f;
+  two_prod(ah, v, p, e);
+  two_sum(hi, p, s, f);
+  hi = s;
+  lo += f + fma(al, v, e);
+}
+
+// One 16x16 tile of B per block: B[i][j] = sum_k U[i][k] t_k U[j][k], summed in
+// double-double (the compensated dot product of Ogita, Rump and Oishi, with
+// U[i][k] t_k kept exact as a double-double), then rounded once: every entry
+// is within about an ulp of the exact sum of the given U and t, however small
+// it is beside its m terms (a plain FP64 sum of m = 144 terms left small entries
+// relative errors near 1e-14, which the Hafnian's cancellation amplifies).
 __global__ void build_B_kernel(const double2* __restrict__ U, const double* __restrict__ t, int m,
                                double2* __restrict__ B) {
   const int bi = blockIdx.y, bj = blockIdx.x;
   if (bj < bi) return;  // upper triangle of tiles; mirrored on store
-  __shared__ double2 Ui[TB][TB + 1];
+  __shared__ double4 Ui[TB][TB + 1];  // U[i][k] t_k: re hi, re lo, im hi, im lo
   __shared__ double2 Uj[TB][TB + 1];
   const int ty = threadIdx.y, tx = threadIdx.x;
   const int i = bi * TB + ty, j = bj * TB + tx;
-  double2 acc = make_double2(0.0, 0.0);
+  double rh = 0.0, rl = 0.0, ih = 0.0, il = 0.0;
   for (int k0 = 0; k0 < m; k0 += TB) {
     const int kk = k0 + tx;
     const int ri = bi * TB + ty, rj = bj * TB + ty;
-    double2 a = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0);
+    double4 a = make_double4(0.0, 0.0, 0.0, 0.0);
+    double2 b = make_double2(0.0, 0.0);
     if (ri < m && kk < m) {
-      a = U[(int64_t)ri * m + kk];
+      const double2 u = U[(int64_t)ri * m + kk];
       const double tk = t[kk];
-      a.x *= tk;
-      a.y *= tk;
+      two_prod(u.x, tk, a.x, a.y);
+      two_prod(u.y, tk, a.z, a.w);
     }
     if (rj < m && kk < m) b = U[(int64_t)rj * m + kk];
     Ui[ty][tx] = a;
     Uj[ty][tx] = b;
     __syncthreads();
-#pragma unroll
+#pragma unroll 4
     for (int q = 0; q < TB; ++q) {
-      const double2 u = Ui[ty][q], v = Uj[tx][q];
-      acc.x = fma(u.x, v.x, acc.x);
-      acc.x = fma(-u.y, v.y, acc.x);
-      acc.y = fma(u.x, v.y, acc.y);
-      acc.y = fma(u.y, v.x, acc.y);
+      const double4 u = Ui[ty][q];
+      const double2 v = Uj[tx][q];
+      dot2_add(rh, rl, u.x, u.y, v.x);    // + re(a) re(v)
+      dot2_add(rh, rl, -u.z, -u.w, v.y);  // - im(a) im(v)
+      dot2_add(ih, il, u.x, u.y, v.y);    // + re(a) im(v)
+      dot2_add(ih, il, u.z, u.w, v.x);    // + im(a) re(v)
     }
     __syncthreads();
   }
   // In a diagonal tile only the thread with i <= j stores the pair, so B is
   // exactly symmetric and every entry has one writer.
   if (i < m && j < m && (bi < bj || ty <= tx)) {
+    const double2 acc = make_double2(rh + rl, ih + il);
     B[(int64_t)i * m + j] = acc;
     B[(int64_t)j * m + i] = acc;
   }

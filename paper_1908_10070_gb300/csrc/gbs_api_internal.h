@@ -120,4 +120,40 @@ class Planner {
 int device_sm_count();
 int run_batch(const BatchArgs& a);
 
+// Smallest order whose subset sum runs in an ordering chosen by the probe.
+constexpr int kPairingMinN = 26;
+
+// The ordering probe of the batched calls, on its own, for index lists held
+// on the host (the serving loop): for every list with n >= kPairingMinN it
+// runs the sampled subset sums of the candidate orderings on the float kernel
+// over k's float copy of B and picks the one with the smallest estimated
+// sum |f|, asynchronously on `st`. Lists never probe each other: a list's
+// choice depends only on the list, the launch shape cfg and stage_h.
+struct OrderProbe {
+  int n_lists = 0;
+  std::vector<int> n;          // order of each list
+  std::vector<int> perm;       // candidate orderings (source positions), per order
+  std::vector<int> sel;        // probed lists
+  void* dmem = nullptr;        // device scratch (freed stream-ordered at launch)
+  int pin_slot = -1;           // pinned staging, holding the results at `res`
+  int* res = nullptr;          // per list: chosen ordering's offset into perm
+  volatile int* flag = nullptr;  // pinned: equals `expect` once res has arrived
+  int expect = 0;
+  cudaEvent_t done = nullptr;  // recorded after the results (for error checks); kept across launches
+};
+// Enqueue the probe of `count` host index lists (lists[i] has n[i] entries,
+// all < k->m). On success the caller waits for order_probe_ready (or
+// out->done) and then calls order_probe_result for each list, then
+// order_probe_release (order_probe_destroy once the object is not reused).
+int order_probe_launch(const gbs_kernel* k, const int* const* lists, const int* n, int count, int stage_h,
+                       const TuneCfg& cfg, cudaStream_t st, OrderProbe* out);
+// After out->done: positions[p] = the source position that position p of list
+// i reads in the chosen ordering, p < n[i]; false if list i was not probed.
+bool order_probe_result(const OrderProbe& pr, int i, int* positions);
+// True once the launch's results are in host memory (reads a pinned word that
+// the stream writes after them; no driver call).
+bool order_probe_ready(const OrderProbe& pr);
+void order_probe_release(OrderProbe* pr, cudaStream_t st);
+void order_probe_destroy(OrderProbe* pr);
+
 }  // namespace gbs

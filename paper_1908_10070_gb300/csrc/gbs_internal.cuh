@@ -94,17 +94,16 @@ __host__ __device__ inline int64_t pair_terms_elems(int n) {
 }
 
 // Per-warp staging of finished subsets' power traces (32 slots of stage_h
-// complex values plus 32 sign flags); the exponential series then runs with
-// one subset per lane.
-__host__ __device__ inline int stage_bytes(int stage_h, int cbytes) {
-  return (32 * stage_h * cbytes + 32 * 4 + 15) & ~15;
-}
+// complex doubles plus 32 sign flags; the FP32 path's traces are staged in
+// double too); the exponential series then runs in FP64 with one subset per
+// lane.
+__host__ __device__ inline int stage_bytes(int stage_h) { return (32 * stage_h * 16 + 32 * 4 + 15) & ~15; }
 
 // Lane-group size L (a power of two) for subsets of order N of a matrix of
 // order 2h: the smallest L whose 32/L groups fit the warp's bytes left after
 // the header and the staging area; 0 if none does.
 __host__ __device__ inline int lanes_for(int N, int h, int warp_bytes, int stage_h, int cbytes) {
-  const int avail = warp_bytes - kWarpHeaderBytes - stage_bytes(stage_h, cbytes);
+  const int avail = warp_bytes - kWarpHeaderBytes - stage_bytes(stage_h);
   const int gb = group_bytes(N, h, cbytes);
   for (int L = 1; L <= 32; L <<= 1)
     if ((32 / L) * gb <= avail) return L;
@@ -138,6 +137,10 @@ struct HafLaunch {
   double* pt;
   const int64_t* pt_off;
   int batch;               // matrices in pats (read by the pair-term kernel)
+  // May be null: per matrix, nonzero when the route choice on the device sent
+  // it to the repeated-row sum; its subset items then leave a zero partial and
+  // the pair-term kernel skips it.
+  const int* skip;
 };
 
 // Two-stage finalisation: chunk g (of matrix chunk_pat[g]) sums up to
@@ -155,6 +158,12 @@ struct ChunkLaunch {
 
 struct FinalizeLaunch {
   const int* sel;          // if non-null, entry b finalises pattern sel[b] (outputs at b)
+  // If non-null (route choice on the device): a pattern with rep_half > 0 sums
+  // its ceil(rep_half / kRepTermsPerItem) repeated-row partials, which end at
+  // rep_parts[rep_end[pattern]], instead of its subset items.
+  const int* rep_half;
+  const int* rep_end;
+  const Partial* rep_parts;
   const int* batch_dev;    // if non-null, the number of entries is read here (device memory)
   const Partial* chunk_parts;  // if non-null, sum these chunk sums (chunk_off ranges) instead
   const int* chunk_off;
@@ -210,10 +219,42 @@ struct RepLaunch {
   int* counter;            // work-queue head, zero before launch
   int* status;             // per-pattern flag, set to 1 on an out-of-range index
   Partial* parts;
+  // Route choice on the device (items null): item v of the *n_items_dev items
+  // is term chunk v - (rep_end[b] - chunks_b) of the pattern b whose partial
+  // range [rep_end[b] - chunks_b, rep_end[b]) holds v, chunks_b =
+  // ceil(rep_half[b] / kRepTermsPerItem); its partial goes to parts[v].
+  const int* rep_half = nullptr;
+  const int* rep_end = nullptr;
+  const int* n_items_dev = nullptr;
+  int batch = 0;
+};
+
+// Route choice on the device, for FP64 probabilities of index lists held in
+// device memory (the host cannot read them without a synchronisation). One
+// warp per pattern finds its distinct modes and multiplicities and applies the
+// host's rule (rep_half_terms in api.cu): the repeated-row sum when the
+// pattern has a repeated mode, at most d_max[n] distinct modes, T <= 2^30 and
+// 4 ceil(T / 2) (d^2 + 3d + 60) < subset_cost[n]. The last block to finish
+// then assigns partial ranges in pattern order: a pattern keeps the route
+// only while the running total of chunks stays within cap (later ones fall
+// back to the subset sum), so the choice is the same for the same batch.
+struct RoutePlan {
+  const int* idx;
+  const PatDesc* pats;
+  int batch;
+  int m_bound;             // index lists must be < m_bound (0 = no check)
+  int cap;                 // repeated-row partial slots available
+  double subset_cost[kMaxN + 1];
+  int d_max[kMaxN + 1];
+  int* rep_half;           // out, per pattern: terms summed (ceil(T / 2)), 0 = subset sum
+  int* rep_end;            // out, per pattern: end of its partial range (non-decreasing)
+  int* rep_total;          // out: partial slots used (the repeated-row item count)
+  unsigned* blocks_done;   // zero before launch
 };
 
 // Defined in haf_subsets.cu
 cudaError_t launch_haf_repeated(const RepLaunch& R, cudaStream_t st);
+cudaError_t launch_route_plan(const RoutePlan& R, cudaStream_t st);
 cudaError_t launch_haf_subsets(const HafLaunch& L, int precision, int blocks, int warps_per_block,
                                cudaStream_t st);
 cudaError_t launch_finalize(const FinalizeLaunch& F, cudaStream_t st);

@@ -105,27 +105,9 @@ __device__ __forceinline__ void dd_add(double& ahi, double& alo, double bhi, dou
   ahi = h2;
 }
 
-// float-float addition (same steps as dd_add, in single precision)
-__device__ __forceinline__ void ff_add(float& ahi, float& alo, float bhi, float blo) {
-  float s = ahi + bhi;
-  float bb = s - ahi;
-  float e = (ahi - (s - bb)) + (bhi - bb);
-  float t = alo + blo;
-  float tb = t - alo;
-  float f = (alo - (t - tb)) + (blo - tb);
-  e += t;
-  float h = s + e;
-  e = e - (h - s);
-  e += f;
-  float h2 = h + e;
-  alo = e - (h2 - h);
-  ahi = h2;
-}
-
 struct Tables {
   int binom[kMaxH + 1][kMaxH + 1];  // C(a, b), a, b <= 16
   double inv2k[kMaxH + 1];          // 1 / (2k)
-  float inv2kf[kMaxH + 1];          // the same, rounded to float (no conversions on the FP64 pipe)
 };
 
 // Power-trace schedule per h: the fewest products R_{a+b} = R_a X R_b whose
@@ -522,7 +504,6 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
         tab.binom[a][b] = (b == 0) ? 1 : (a == 0 ? 0 : tab.binom[a - 1][b - 1] + tab.binom[a - 1][b]);
     for (int k = 0; k <= kMaxH; ++k) {
       tab.inv2k[k] = (k == 0) ? 0.0 : 1.0 / (2.0 * k);
-      tab.inv2kf[k] = (float)tab.inv2k[k];
     }
   }
   __syncthreads();
@@ -535,9 +516,9 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
   unsigned char* wbase = smem + (size_t)warp * P.warp_bytes;
   int* xs = reinterpret_cast<int*>(wbase);
   // staging: the power traces of up to 32 finished subsets, their signs and orders
-  C* stP = reinterpret_cast<C*>(wbase + kWarpHeaderBytes);
+  double2* stP = reinterpret_cast<double2*>(wbase + kWarpHeaderBytes);
   int* stF = reinterpret_cast<int*>(stP + 32 * P.stage_h);
-  unsigned char* gbase = wbase + kWarpHeaderBytes + stage_bytes(P.stage_h, cb);
+  unsigned char* gbase = wbase + kWarpHeaderBytes + stage_bytes(P.stage_h);
   const double2* src2 = reinterpret_cast<const double2*>(P.src);
 
   for (;;) {
@@ -546,6 +527,17 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
     it = __shfl_sync(FULL, it, 0);
     if (it >= n_items) break;
     const WorkItem w = P.items[it];
+    if (P.skip != nullptr && P.skip[w.pat] != 0) {
+      // the repeated-row sum computes this matrix: leave a zero partial
+      if (lane == 0) {
+        Partial pr;
+        pr.re_hi = pr.re_lo = pr.im_hi = pr.im_lo = pr.kappa = 0.0;
+        pr.pad[0] = pr.pad[1] = pr.pad[2] = 0.0;
+        P.parts[w.part] = pr;
+      }
+      __syncwarp();
+      continue;
+    }
     const PatDesc d = P.pats[w.pat];
     const int n = d.n, h = n >> 1;
     // sizes s_first..s_last: one size (a rank range of it), or every subset of
@@ -598,68 +590,66 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
     const double2* srcp = src2 + d.src_off;
     const float2* src32p = P.src32 ? reinterpret_cast<const float2*>(P.src32) + d.src_off : nullptr;
 
-    Comp<T> acc_re = {T(0), T(0)}, acc_im = {T(0), T(0)};
-    T kap = T(0);
+    // the signed sum of the subset terms in double-double (both paths)
+    Comp<double> acc_re = {0.0, 0.0}, acc_im = {0.0, 0.0};
+    double kap = 0.0;
 
-    // the exponential series e_k = (1/(2k)) sum_j tr_j e_{k-j}, f = e_h, one
-    // staged subset per lane, and the signed compensated accumulation
+    // the exponential series e_k = (1/(2k)) sum_j tr_j e_{k-j}, f = e_h, in
+    // FP64 for both paths (one staged subset per lane), and the signed
+    // compensated accumulation
     auto flush = [&]() {
       if (lane < staged) {
-        C* pq = stP + lane * P.stage_h;
+        double2* pq = stP + lane * P.stage_h;
         const int sv = stF[lane];
         const int Nl = sv < 0 ? -sv : sv;  // the subset's order N
         if (Nl > 0 && Nl < h) {
           // an order-N subset has traces 1..N only: det(I - xM) = sum_i d_i x^i
           // has degree N, so by Newton's identities d_k = -(1/k) sum_{i<=k}
           // d_{k-i} p_i (d_0 = 1) and, for k > N, p_k = -sum_{i<=N} d_i p_{k-i}
-          C dk[kMaxH];  // d_1..d_{kMaxH-1}
+          double2 dk[kMaxH];  // d_1..d_{kMaxH-1}
 #pragma unroll
           for (int k = 1; k < kMaxH; ++k) {
-            C a = mk<T>(T(0), T(0));
+            double2 a = mk<double>(0.0, 0.0);
             if (k <= Nl) {
               a = pq[k - 1];
 #pragma unroll
-              for (int i = 1; i < k; ++i) a = cfma<T>(dk[i], pq[k - i - 1], a);
-              T c;
-              if constexpr (sizeof(T) == 8) c = T(-2) * tab.inv2k[k];
-              else c = T(-2) * tab.inv2kf[k];
+              for (int i = 1; i < k; ++i) a = cfma<double>(dk[i], pq[k - i - 1], a);
+              const double c = -2.0 * tab.inv2k[k];
               a.x *= c;
               a.y *= c;
             }
             dk[k] = a;
           }
           for (int k = Nl + 1; k <= h; ++k) {
-            C a = mk<T>(T(0), T(0));
+            double2 a = mk<double>(0.0, 0.0);
 #pragma unroll
             for (int i = 1; i < kMaxH; ++i)
-              if (i <= Nl) a = cfma<T>(dk[i], pq[k - i - 1], a);
-            pq[k - 1] = mk<T>(-a.x, -a.y);
+              if (i <= Nl) a = cfma<double>(dk[i], pq[k - i - 1], a);
+            pq[k - 1] = mk<double>(-a.x, -a.y);
           }
         }
-        C e[kMaxH + 1];
-        e[0] = mk<T>(T(1), T(0));
+        double2 e[kMaxH + 1];
+        e[0] = mk<double>(1.0, 0.0);
 #pragma unroll
         for (int k = 1; k <= kMaxH; ++k) {
-          C a = mk<T>(T(0), T(0));
+          double2 a = mk<double>(0.0, 0.0);
           if (k <= h) {
 #pragma unroll
-            for (int j = 1; j <= k; ++j) a = cfma<T>(pq[j - 1], e[k - j], a);
-            T c;
-            if constexpr (sizeof(T) == 8) c = tab.inv2k[k];
-            else c = tab.inv2kf[k];
+            for (int j = 1; j <= k; ++j) a = cfma<double>(pq[j - 1], e[k - j], a);
+            const double c = tab.inv2k[k];
             a.x *= c;
             a.y *= c;
           }
           e[k] = a;
         }
-        C f = e[1];
+        double2 f = e[1];
 #pragma unroll
         for (int k = 2; k <= kMaxH; ++k)
           if (k == h) f = e[k];
         const int sg = sv;
         if (sg != 0) {
-          comp_add<T>(acc_re, sg > 0 ? f.x : -f.x);
-          comp_add<T>(acc_im, sg > 0 ? f.y : -f.y);
+          comp_add<double>(acc_re, sg > 0 ? f.x : -f.x);
+          comp_add<double>(acc_im, sg > 0 ? f.y : -f.y);
           kap += fabs(f.x) + fabs(f.y);
         }
       }
@@ -741,7 +731,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
       //    time (one waits in registers for the next)
       C pend_v = mk<T>(T(0), T(0));
       int pend_k = 0;  // 0: none waiting
-      C* const strow = stP + (staged + g) * P.stage_h;
+      double2* const strow = stP + (staged + g) * P.stage_h;
       for (int o = 0; o < kMaxOps; ++o) {
         const SchedOp op = c_sched[hs][o];
         if (op.kind == kEnd) break;
@@ -767,14 +757,14 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
                    : (op.a == op.b) ? tr2sq_full(buf + op.a * NP, N, l, L)
                                     : tr2_full(buf + op.a * NP, buf + op.b * NP, N, l, L);
           if (L == 1) {
-            strow[op.k - 1] = part;
+            strow[op.k - 1] = make_double2(part.x, part.y);
           } else if (pend_k == 0) {
             pend_v = part;
             pend_k = op.k;
           } else {
             const C t = group_sum2<T>(pend_v, part, l, L);
-            if (l == 0) strow[pend_k - 1] = t;
-            if (l == (L >> 1)) strow[op.k - 1] = t;
+            if (l == 0) strow[pend_k - 1] = make_double2(t.x, t.y);
+            if (l == (L >> 1)) strow[op.k - 1] = make_double2(t.x, t.y);
             pend_k = 0;
           }
         }
@@ -782,7 +772,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
       }
       if (pend_k != 0) {  // uniform over the warp
         const C t = group_sum<T>(pend_v, L);
-        if (l == 0) strow[pend_k - 1] = t;
+        if (l == 0) strow[pend_k - 1] = make_double2(t.x, t.y);
       }
       // sign (-1)^{h-s} times the order N (0: no subset in this slot)
       if (l == 0) stF[staged + g] = active ? (((h - s) & 1) ? -N : N) : 0;
@@ -793,29 +783,15 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
     }
    }
 
-    // warp reduction of the group accumulators (fixed butterfly: deterministic),
-    // in the path's own compensated arithmetic: double-double for FP64,
-    // float-float for FP32 (keeping the slow FP64 pipe out of the FP32 path)
-    double rh, rl, ih, il, kp;
-    if constexpr (sizeof(T) == 8) {
-      rh = acc_re.hi; rl = acc_re.lo; ih = acc_im.hi; il = acc_im.lo; kp = kap;
-      for (int off = 16; off > 0; off >>= 1) {
-        const double orh = __shfl_xor_sync(FULL, rh, off), orl = __shfl_xor_sync(FULL, rl, off);
-        const double oih = __shfl_xor_sync(FULL, ih, off), oil = __shfl_xor_sync(FULL, il, off);
-        kp += __shfl_xor_sync(FULL, kp, off);
-        dd_add(rh, rl, orh, orl);
-        dd_add(ih, il, oih, oil);
-      }
-    } else {
-      float frh = acc_re.hi, frl = acc_re.lo, fih = acc_im.hi, fil = acc_im.lo, fkp = kap;
-      for (int off = 16; off > 0; off >>= 1) {
-        const float orh = __shfl_xor_sync(FULL, frh, off), orl = __shfl_xor_sync(FULL, frl, off);
-        const float oih = __shfl_xor_sync(FULL, fih, off), oil = __shfl_xor_sync(FULL, fil, off);
-        fkp += __shfl_xor_sync(FULL, fkp, off);
-        ff_add(frh, frl, orh, orl);
-        ff_add(fih, fil, oih, oil);
-      }
-      rh = frh; rl = frl; ih = fih; il = fil; kp = fkp;
+    // warp reduction of the group accumulators (fixed butterfly: deterministic)
+    // in double-double
+    double rh = acc_re.hi, rl = acc_re.lo, ih = acc_im.hi, il = acc_im.lo, kp = kap;
+    for (int off = 16; off > 0; off >>= 1) {
+      const double orh = __shfl_xor_sync(FULL, rh, off), orl = __shfl_xor_sync(FULL, rl, off);
+      const double oih = __shfl_xor_sync(FULL, ih, off), oil = __shfl_xor_sync(FULL, il, off);
+      kp += __shfl_xor_sync(FULL, kp, off);
+      dd_add(rh, rl, orh, orl);
+      dd_add(ih, il, oih, oil);
     }
     if (lane == 0) {
       Partial pr;
@@ -939,7 +915,12 @@ __global__ void __launch_bounds__(kFinWarps * 32) finalize_kernel(const Finalize
       const int n = d.n;
       double rh = 0, rl = 0, ih = 0, il = 0, K = 0;
       if (!(n & 1) && n > 0) {
-        if (F.chunk_parts)
+        const int rep = F.rep_half ? F.rep_half[pb] : 0;
+        if (rep > 0) {
+          const int end = F.rep_end[pb];
+          sum_partials(F.rep_parts, end - (rep + kRepTermsPerItem - 1) / kRepTermsPerItem, end, lane, rh, rl,
+                       ih, il, K);
+        } else if (F.chunk_parts)
           sum_partials(F.chunk_parts, F.chunk_off[pb], F.chunk_off[pb + 1], lane, rh, rl, ih, il, K);
         else
           sum_partials(F.parts, d.item_begin, d.item_end, lane, rh, rl, ih, il, K);
@@ -1017,8 +998,10 @@ __global__ void __launch_bounds__(256) pair_terms_kernel(const HafLaunch P) {
     const int64_t po = P.pt_off[b];
     const PatDesc d = P.pats[b];
     const int n = d.n, h = n >> 1, NPn = n * (n + 1) / 2;
-    // uniform over the block; a matrix beyond the launch's order is not read
+    // uniform over the block; a matrix beyond the launch's order, or one that
+    // the repeated-row sum computes, is not read
     if (po < 0 || pair_terms_elems(n) == 0 || n > nmax || e0 >= NPn) continue;
+    if (P.skip != nullptr && P.skip[b] != 0) continue;
     const int ne = min(kPairChunk, NPn - e0);
     if (threadIdx.x < n) {
       int pos = default_pos(threadIdx.x, h);
@@ -1242,12 +1225,43 @@ __global__ void __launch_bounds__(128) haf_repeated_kernel(const RepLaunch R) {
   const int lane = threadIdx.x & 31;
   RepWarp& W = ws[threadIdx.x >> 5];
   const double2* src2 = reinterpret_cast<const double2*>(R.B);
+  const int n_items = R.n_items_dev ? *R.n_items_dev : R.n_items;
   for (;;) {
     int it = 0;
     if (lane == 0) it = atomicAdd(R.counter, 1);
     it = __shfl_sync(FULL, it, 0);
-    if (it >= R.n_items) break;
-    const WorkItem w = R.items[it];
+    if (it >= n_items) break;
+    WorkItem w;
+    if (R.items != nullptr) {
+      w = R.items[it];
+    } else {
+      // route choice on the device: the pattern whose partial range holds
+      // slot it (the smallest b with rep_end[b] > it), and its chunk
+      int lo = 0, hi = R.batch - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (R.rep_end[mid] > it) hi = mid;
+        else lo = mid + 1;
+      }
+      const int half = R.rep_half[lo];
+      const int chunks = (half + kRepTermsPerItem - 1) / kRepTermsPerItem;
+      const int c = it - (R.rep_end[lo] - chunks);
+      w.pat = lo;
+      w.s = 0;
+      w.rank0 = c * kRepTermsPerItem;
+      w.count = min(kRepTermsPerItem, half - w.rank0);
+      w.part = it;
+      w.stride = 1;
+      w.s_last = 0;
+      w.aux = 0;
+      if (half <= 0 || c < 0 || c >= chunks) {  // never for a consistent plan
+        if (lane == 0) R.status[lo] = 1;
+        const Comp<double> z = {0.0, 0.0};
+        store_warp_partial(z, z, 0.0, lane, R.parts + it);
+        __syncwarp();
+        continue;
+      }
+    }
     const PatDesc d = R.pats[w.pat];
     const int n = d.n, h = n >> 1;
     int v = -1 - lane;  // lanes past n: values no index takes
@@ -1293,9 +1307,98 @@ __global__ void __launch_bounds__(128) haf_repeated_kernel(const RepLaunch R) {
   }
 }
 
+// Route choice on the device (see RoutePlan): one warp per pattern decides
+// between the subset sum and the repeated-row sum by the host's rule, then the
+// last block to finish assigns each repeated-row pattern its partial range in
+// pattern order (a block-wide prefix sum over tiles of the batch).
+__global__ void __launch_bounds__(256) route_plan_kernel(const RoutePlan R) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  for (int b = blockIdx.x * wpb + warp; b < R.batch; b += gridDim.x * wpb) {
+    const PatDesc d = R.pats[b];
+    const int n = d.n;
+    int half = 0;
+    if (n >= 4 && !(n & 1) && n <= kMaxN) {  // uniform over the warp
+      int v = -1 - lane;  // lanes past n: values no index takes
+      bool bad = false;
+      if (lane < n) {
+        v = R.idx[d.idx_off + lane];
+        if (R.m_bound > 0 && (v < 0 || v >= R.m_bound)) bad = true;
+      }
+      const unsigned same = __match_any_sync(FULL, v);
+      const bool leader = lane < n && (__ffs(same) - 1) == lane;
+      const int D = __popc(__ballot_sync(FULL, leader));
+      if (!__any_sync(FULL, bad) && D < n && D <= R.d_max[n]) {
+        // T = prod_j (c_j + 1) over the distinct modes; partial products
+        // above 2^31 are capped there (exact below, and the rule needs only
+        // T <= 2^30)
+        double t = leader ? (double)(__popc(same) + 1) : 1.0;
+        for (int off = 16; off > 0; off >>= 1) t = fmin(t * __shfl_xor_sync(FULL, t, off), 0x1p31);
+        if (t <= 0x1p30) {
+          const int T = (int)t;
+          const int hh = (T + 1) / 2;
+          const double rep_cost = (double)hh * (double)(D * D + 3 * D + 60);
+          if (4.0 * rep_cost < R.subset_cost[n]) half = hh;
+        }
+      }
+    }
+    if (lane == 0) R.rep_half[b] = half;
+  }
+  __shared__ int s_last, s_total;
+  __shared__ long long s_warp[8], s_base;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(R.blocks_done, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x == 0) {
+    s_base = 0;
+    s_total = 0;
+  }
+  __syncthreads();
+  for (int b0 = 0; b0 < R.batch; b0 += blockDim.x) {
+    const int b = b0 + threadIdx.x;
+    const int half = (b < R.batch) ? __ldcg(R.rep_half + b) : 0;
+    const long long c = (half + kRepTermsPerItem - 1) / kRepTermsPerItem;
+    long long x = c;  // inclusive prefix within the warp
+    for (int off = 1; off < 32; off <<= 1) {
+      const long long y = __shfl_up_sync(FULL, x, off);
+      if (lane >= off) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    long long wbase = s_base;
+    for (int q = 0; q < warp; ++q) wbase += s_warp[q];
+    const long long incl = wbase + x;
+    if (b < R.batch) {
+      if (incl <= R.cap) {
+        R.rep_end[b] = (int)incl;
+        if (c > 0) atomicMax(&s_total, (int)incl);
+      } else {  // past the capacity: the subset sum instead
+        R.rep_end[b] = R.cap;
+        if (half > 0) R.rep_half[b] = 0;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) s_base = incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *R.rep_total = s_total;
+}
+
 }  // namespace
 
+cudaError_t launch_route_plan(const RoutePlan& R, cudaStream_t st) {
+  if (R.batch <= 0) return cudaSuccess;
+  int blocks = (R.batch + 7) / 8;
+  if (blocks > 1024) blocks = 1024;
+  route_plan_kernel<<<blocks, 256, 0, st>>>(R);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_haf_repeated(const RepLaunch& R, cudaStream_t st) {
+  // with the item count on the device, n_items is its upper bound (the grid)
   if (R.n_items <= 0) return cudaSuccess;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);

@@ -1,7 +1,11 @@
 // Marginal probabilities q_n(x_1..x_k) of the position-basis distribution and
 // the chain-rule sampler built on them (Sec. 3.3-3.4, Theorem 1, Algorithms 1
-// and 2). Identical squeezing only: the theorem uses the unitarity of
-// W = U U^T (Rule 3), and q_n does not depend on r.
+// and 2). Identical squeezing only: the theorem collapses the sums over the
+// unsampled photons with the unitarity of W = U U^T (Rule 3:
+// sum_i W(i, j) conj(W(i, j')) = delta_jj'); for B = U diag(tanh r_i) U^T with
+// unequal r_i that sum is (U* diag(tanh^2 r) U^T)_{j'j}, not a multiple of
+// delta, so the theorem does not apply (and q_n does not depend on r when the
+// r_i are equal).
 //
 // Theorem 1, as used here (with the index sets of Algorithm 2):
 //   q_n(x_1..x_k) = sum_{ja, jb} sum_{s in C([k], ja), s' in C([k], jb)}
@@ -16,9 +20,25 @@
 // e' uses s; the theorem's B ranges over [k] \ a. Both are read with s', which
 // the brute-force marginal of Eq. marginal_definition confirms.)
 //
+// Evaluation order. The same sum, regrouped: W_T, and so Haf(W_T), depends
+// only on the multiset of modes x_T, and Per(S_{A,B}) only on the multisets
+// of A and B. Write alpha for the multiset of A (per distinct mode v of the
+// prefix, alpha_v of its m_v copies) and rho = prefix - alpha for what is
+// left. For fixed A and B the sums over s and s' separate, and each depends
+// on A (or B) only through alpha, so
+//   q_n = sum_alpha  prod_v alpha_v! (prod_v C(m_v, alpha_v))^2
+//         sum_{ja, jb} F(k, |alpha|, ja, jb) / f_n  G(rho, ja) conj(G(rho, jb)),
+//   G(rho, j) = sum_{sigma <= rho, |sigma| = j} prod_v C(rho_v, sigma_v)
+//               Haf(W_sigma) Haf(W_{rho - sigma})
+// (the binomials count the position sets with a given multiset). That is
+// at most 3^k products per prefix, where the nested sums of the theorem take
+// about 6^k; for a prefix without repeated modes the multisets are the
+// position sets themselves and every count is 1.
+//
 // The sub-Hafnians Haf(W_T) for every even subset T of the prefix come from
-// the batched subset-sum path (Haf(B_T) = tanh(r)^{|T|/2} Haf(W_T)); one block
-// per prefix then adds the terms in a fixed order.
+// the batched subset-sum path (Haf(B_T) = tanh(r)^{|T|/2} Haf(W_T)); the
+// regrouped sum runs one thread per rho, in fixed-order block and prefix
+// reductions.
 #include <math.h>
 #include <string.h>
 
@@ -30,7 +50,8 @@
 namespace gbs {
 namespace {
 
-constexpr int kMaxK = 10;  // prefix length limit (the term count grows like 9^k)
+constexpr int kMaxK = 20;  // prefix length limit (the regrouped sum takes up to 3^k products)
+constexpr int kMargThreads = 256;
 
 __device__ double lgbinom(double x, double y) { return lgamma(x + 1.0) - lgamma(y + 1.0) - lgamma(x - y + 1.0); }
 
@@ -55,90 +76,150 @@ __global__ void fcoef_kernel(int k, int n, int m, double* __restrict__ F) {
   }
 }
 
-// One block per prefix. H: Haf(W_T) for all 2^k subsets T (bitmask order),
-// F: coefficient table, vmask: for each distinct mode value of the prefix the
-// bitmask of its positions (nv values). Terms are split over threads by
-// (s, s') in a fixed order and reduced in a fixed tree.
-__global__ void marginal_kernel(int k, int n, const double2* __restrict__ H, const double* __restrict__ F,
-                                const int* __restrict__ vmask, const int* __restrict__ nv,
-                                double* __restrict__ q_out) {
-  __shared__ double red_re[256], red_im[256];
-  const int b = blockIdx.x;
+__device__ __forceinline__ double binom_d(int a, int b) {
+  double r = 1.0;
+  for (int i = 1; i <= b; ++i) r = r * (double)(a - b + i) / (double)i;
+  return r;
+}
+
+// The regrouped Theorem 1 sum (see the top of this file). Blocks cover the
+// rho of one prefix (blockIdx.y = prefix, blockIdx.x = a run of kMargThreads
+// indices); each thread forms G(rho, .) for its rho and the quadratic form
+// with F, and the block writes the sum of its threads (fixed tree) to
+// part[prefix * gridDim.x + blockIdx.x].
+//   H: Haf(W_T) of every position set T (bitmask order, 0 for odd |T|), 2^k per prefix.
+//   vmask, nv: per prefix, the position mask of each of its nv distinct modes.
+// A prefix without repeated modes (nv == k) indexes rho by position masks; otherwise
+// rho is a mixed-radix number over the distinct modes (digit v in [0, m_v]),
+// and a multiset reads the sub-Hafnian of its representative position set (the
+// first rho_v positions of each mode v).
+__global__ void __launch_bounds__(kMargThreads) marginal_terms_kernel(int k, int n, const double2* __restrict__ H,
+                                                                     const double* __restrict__ F,
+                                                                     const int* __restrict__ vmask,
+                                                                     const int* __restrict__ nv,
+                                                                     double* __restrict__ part) {
+  __shared__ double red[kMargThreads];
+  __shared__ int s_pm[kMaxK][kMaxK + 1];  // first c positions of mode v
+  __shared__ int s_mv[kMaxK], s_stride[kMaxK + 1];
+  const int b = blockIdx.y;
   const double2* Hb = H + ((int64_t)b << k);
-  const int* vm = vmask + b * kMaxK;
   const int nvals = nv[b];
-  const int full = (1 << k) - 1;
+  const int* vm = vmask + (int64_t)b * kMaxK;
+  if (threadIdx.x == 0) {
+    int stride = 1;
+    for (int v = 0; v < nvals; ++v) {
+      const int mk = vm[v];
+      s_mv[v] = __popc(mk);
+      s_stride[v] = stride;
+      stride *= s_mv[v] + 1;
+      int acc = 0, rest = mk;
+      s_pm[v][0] = 0;
+      for (int c = 1; c <= s_mv[v]; ++c) {
+        acc |= rest & -rest;  // the next position of mode v
+        rest &= rest - 1;
+        s_pm[v][c] = acc;
+      }
+    }
+    s_stride[nvals] = stride;
+  }
+  __syncthreads();
   const int K2 = k / 2 + 1;
-  const int lo = max(0, 2 * k - n);
-  double acc_re = 0.0, acc_im = 0.0;
-  const int pairs = 1 << (2 * k);
-  for (int ps = threadIdx.x; ps < pairs; ps += blockDim.x) {
-    const int s = ps & full, sp = ps >> k;
-    const int ja = __popc(s), jb = __popc(sp);
-    if ((ja & 1) || (jb & 1) || ja < lo || jb < lo) continue;
-    const double2 hs = Hb[s], hsp = Hb[sp];
-    // Haf(W_s) conj(Haf(W_s'))
-    const double pr = hs.x * hsp.x + hs.y * hsp.y, pi = hs.y * hsp.x - hs.x * hsp.y;
-    if (pr == 0.0 && pi == 0.0) continue;
-    const int cs = full & ~s, csp = full & ~sp;
-    double t_re = 0.0, t_im = 0.0;
-    const int mu_lo = max(0, 3 * k - ja - jb - n), mu_hi = k - max(ja, jb);
-    // submasks A of cs and B of csp with |A| = |B| = mu
-    for (int A = cs;; A = (A - 1) & cs) {
-      const int mu = __popc(A);
-      if (mu >= mu_lo && mu <= mu_hi && !((k - ja - mu) & 1)) {
-        const double f = F[((ja >> 1) * K2 + (jb >> 1)) * (k + 1) + mu];
-        if (f != 0.0 && nvals == k) {
-          // Proposition (collision-free prefix): Per(S_{A,B}) is 1 for B = A
-          // and 0 for every other B, so only B = A contributes
-          if ((A & ~csp) == 0) {
-            const double2 he = Hb[cs & ~A], hep = Hb[csp & ~A];
-            const double er = he.x * hep.x + he.y * hep.y, ei = he.y * hep.x - he.x * hep.y;
-            t_re = fma(f, er, t_re);
-            t_im = fma(f, ei, t_im);
+  const int full = (1 << k) - 1;
+  const int64_t idx = (int64_t)blockIdx.x * kMargThreads + threadIdx.x;
+  double acc = 0.0;
+  const bool distinct = (nvals == k);
+  if (idx < (distinct ? (int64_t)1 << k : (int64_t)s_stride[nvals])) {
+    double2 G[kMaxK / 2 + 1];
+    for (int j = 0; j < K2; ++j) G[j] = make_double2(0.0, 0.0);
+    int rsize;
+    double w;  // prod alpha_v! (prod C(m_v, alpha_v))^2
+    if (distinct) {
+      const int rho = (int)idx;
+      rsize = __popc(rho);
+      if (!(rsize & 1)) {
+        for (int sub = rho;; sub = (sub - 1) & rho) {
+          const int c = __popc(sub);
+          if (!(c & 1)) {
+            const double2 a = Hb[sub], e = Hb[rho ^ sub];
+            G[c >> 1].x += a.x * e.x - a.y * e.y;
+            G[c >> 1].y += a.x * e.y + a.y * e.x;
           }
-        } else if (f != 0.0) {
-          const double2 he = Hb[cs & ~A];
-          for (int B = csp;; B = (B - 1) & csp) {
-            if (__popc(B) == mu) {
-              // Per(S_{A,B}) = prod_v c_v! when A and B hold each value equally often
-              double per = 1.0;
-              for (int v = 0; v < nvals; ++v) {
-                const int ca = __popc(A & vm[v]), cb = __popc(B & vm[v]);
-                if (ca != cb) {
-                  per = 0.0;
-                  break;
-                }
-                for (int c = 2; c <= ca; ++c) per *= (double)c;
-              }
-              if (per != 0.0) {
-                const double2 hep = Hb[csp & ~B];
-                // Haf(W_e) conj(Haf(W_e'))
-                const double er = he.x * hep.x + he.y * hep.y, ei = he.y * hep.x - he.x * hep.y;
-                t_re = fma(f * per, er, t_re);
-                t_im = fma(f * per, ei, t_im);
-              }
-            }
-            if (B == 0) break;
-          }
+          if (sub == 0) break;
         }
       }
-      if (A == 0) break;
+      w = 1.0;
+      (void)full;
+    } else {
+      int rho_d[kMaxK];
+      int rem = (int)idx;
+      rsize = 0;
+      w = 1.0;
+      for (int v = 0; v < nvals; ++v) {
+        rho_d[v] = rem % (s_mv[v] + 1);
+        rem /= s_mv[v] + 1;
+        rsize += rho_d[v];
+        const int a = s_mv[v] - rho_d[v];
+        const double cm = binom_d(s_mv[v], a);
+        double fa = 1.0;
+        for (int c = 2; c <= a; ++c) fa *= (double)c;
+        w *= fa * cm * cm;
+      }
+      if (!(rsize & 1)) {
+        // sigma <= rho in mixed radix (digit v in [0, rho_v])
+        int sg[kMaxK];
+        for (int v = 0; v < nvals; ++v) sg[v] = 0;
+        for (;;) {
+          int c = 0, ms = 0, mr = 0;
+          double cnt = 1.0;
+          for (int v = 0; v < nvals; ++v) {
+            c += sg[v];
+            ms |= s_pm[v][sg[v]];
+            mr |= s_pm[v][rho_d[v] - sg[v]];
+            cnt *= binom_d(rho_d[v], sg[v]);
+          }
+          if (!(c & 1)) {
+            const double2 a = Hb[ms], e = Hb[mr];
+            G[c >> 1].x = fma(cnt, a.x * e.x - a.y * e.y, G[c >> 1].x);
+            G[c >> 1].y = fma(cnt, a.x * e.y + a.y * e.x, G[c >> 1].y);
+          }
+          int v = 0;
+          while (v < nvals && sg[v] == rho_d[v]) sg[v++] = 0;
+          if (v == nvals) break;
+          ++sg[v];
+        }
+      }
     }
-    acc_re += pr * t_re - pi * t_im;
-    acc_im += pr * t_im + pi * t_re;
+    if (!(rsize & 1)) {
+      // the Hermitian form sum_{ja, jb} F(k, mu, ja, jb) G_ja conj(G_jb), mu = k - |rho|
+      const int mu = k - rsize;
+      double t = 0.0;
+      for (int a = 0; a < K2; ++a)
+        for (int c = 0; c < K2; ++c) {
+          const double f = F[(a * K2 + c) * (k + 1) + mu];
+          if (f != 0.0) t = fma(f, G[a].x * G[c].x + G[a].y * G[c].y, t);
+        }
+      acc = w * t;
+    }
   }
-  red_re[threadIdx.x] = acc_re;
-  red_im[threadIdx.x] = acc_im;
+  red[threadIdx.x] = acc;
   __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) {
-      red_re[threadIdx.x] += red_re[threadIdx.x + w];
-      red_im[threadIdx.x] += red_im[threadIdx.x + w];
-    }
+  for (int s2 = kMargThreads / 2; s2 > 0; s2 >>= 1) {
+    if ((int)threadIdx.x < s2) red[threadIdx.x] += red[threadIdx.x + s2];
     __syncthreads();
   }
-  if (threadIdx.x == 0) q_out[b] = red_re[0];  // the imaginary part cancels
+  if (threadIdx.x == 0) part[(int64_t)b * gridDim.x + blockIdx.x] = red[0];
+}
+
+// q_out[b] = sum of the prefix's block sums, in block order (one warp per
+// prefix: lane-strided, then a fixed butterfly).
+__global__ void marginal_sum_kernel(const double* __restrict__ part, int nblk, int batch, double* __restrict__ q_out) {
+  const int lane = threadIdx.x & 31;
+  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (b >= batch) return;
+  double s = 0.0;
+  for (int i = lane; i < nblk; i += 32) s += part[(int64_t)b * nblk + i];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) q_out[b] = s;
 }
 
 // H_W[b][T] = Haf(B_{x_T}) / t^{|T|/2} for even |T| (0 for odd |T|).
@@ -181,6 +262,23 @@ __global__ void chain_table_kernel(const double2* __restrict__ cache, const doub
     }
     H[q] = v;
   }
+}
+
+// The regrouped sum for `batch` prefixes of length k: block sums into
+// part (batch * blocks doubles), then one total per prefix.
+cudaError_t launch_marginals(int k, int n, const double2* H, const double* F, const int* vmask, const int* nv,
+                             int batch, double* part, double* q_out, cudaStream_t st) {
+  const int nblk = (int)((((int64_t)1 << k) + kMargThreads - 1) / kMargThreads);
+  marginal_terms_kernel<<<dim3(nblk, batch), kMargThreads, 0, st>>>(k, n, H, F, vmask, nv, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  marginal_sum_kernel<<<(batch + 7) / 8, 256, 0, st>>>(part, nblk, batch, q_out);
+  return cudaGetLastError();
+}
+
+size_t marginal_part_bytes(int k, int batch) {
+  const int64_t nblk = (((int64_t)1 << k) + kMargThreads - 1) / kMargThreads;
+  return sizeof(double) * (size_t)(nblk * batch);
 }
 
 }  // namespace
@@ -238,8 +336,9 @@ extern "C" int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int
   const size_t hafB_b = al(16 * (size_t)nh), H_b = al(16 * ((size_t)batch << kk)), slot_b = al(4 * slot.size());
   const size_t F_b = al(8 * (size_t)(kk / 2 + 1) * (kk / 2 + 1) * (kk + 1)), vm_b = al(4 * vmask.size()),
                nv_b = al(4 * (size_t)batch), q_b = al(8 * (size_t)batch);
+  const size_t part_b = al(marginal_part_bytes(kk, batch));
   void* tmp = nullptr;
-  cudaError_t e = scratch_alloc(&tmp, hafB_b + H_b + slot_b + F_b + vm_b + nv_b + q_b, st);
+  cudaError_t e = scratch_alloc(&tmp, hafB_b + H_b + slot_b + F_b + vm_b + nv_b + q_b + part_b, st);
   if (e != cudaSuccess) return fail(GBS_ENOMEM, "marginal scratch: %s", cudaGetErrorString(e));
   unsigned char* t = (unsigned char*)tmp;
   double* d_hafB = (double*)t;
@@ -249,6 +348,7 @@ extern "C" int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int
   int* d_vm = (int*)(t + hafB_b + H_b + slot_b + F_b);
   int* d_nv = (int*)(t + hafB_b + H_b + slot_b + F_b + vm_b);
   double* d_q = (double*)(t + hafB_b + H_b + slot_b + F_b + vm_b + nv_b);
+  double* d_part = (double*)(t + hafB_b + H_b + slot_b + F_b + vm_b + nv_b + q_b);
   const bool q_dev = is_device_ptr(q_out);
   int ret = GBS_OK;
   do {
@@ -275,8 +375,13 @@ extern "C" int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int
     rescale_kernel<<<std::min(4096, (int)((((int64_t)batch << kk) + 255) / 256)), 256, 0, st>>>(
         d_hafB, d_slot, nh, kk, k->t_uniform, d_H, batch);
     fcoef_kernel<<<1, 256, 0, st>>>(kk, n, k->m, d_F);
-    marginal_kernel<<<batch, 256, 0, st>>>(kk, n, d_H, d_F, d_vm, d_nv, q_dev ? q_out : d_q);
-    if ((e = cudaGetLastError()) != cudaSuccess) {
+    double* qd = q_dev ? q_out : d_q;
+    const int nblk = (int)(marginal_part_bytes(kk, 1) / sizeof(double));
+    for (int b0 = 0; b0 < batch && e == cudaSuccess; b0 += 65535)  // the grid's y extent
+      e = launch_marginals(kk, n, d_H + ((int64_t)b0 << kk), d_F, d_vm + (int64_t)b0 * kMaxK, d_nv + b0,
+                           std::min(65535, batch - b0), d_part + (int64_t)b0 * nblk, qd + b0, st);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
       ret = cuda_fail(e, "marginal kernels");
       break;
     }
@@ -299,7 +404,46 @@ extern "C" int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int
 // prefix are kept on the device across steps, so step k computes only those
 // of subsets that hold the new photon (for each candidate l, the odd subsets
 // T' of positions 0..k-2 plus l), half of the step's table; the marginal
-// kernel then reads the cache for the rest.
+// kernels then read the cache for the rest. Candidates are taken in chunks
+// of at most 2^22 new sub-Hafnians, so memory stays bounded at large k; the
+// chosen candidate's new sub-Hafnians are then computed once more for the
+// cache.
+namespace {
+
+// new sub-Hafnians of candidates [l0, l0 + cnt) at step kk into dst
+// (cnt * 2^(kk-1) entries, candidate-major)
+int chain_new_subhafnians(const gbs_kernel* k, const std::vector<int>& x, int kk, int l0, int cnt,
+                          cudaStream_t st, double2* dst) {
+  const int half = 1 << (kk - 1);
+  std::vector<int> idx, nvl;
+  std::vector<int64_t> offs;
+  idx.reserve((size_t)cnt * half * kk / 2 + 1);
+  for (int l = l0; l < l0 + cnt; ++l)
+    for (int T = 0; T < half; ++T) {
+      offs.push_back((int64_t)idx.size());
+      for (int i = 0; i < kk - 1; ++i)
+        if (T >> i & 1) idx.push_back(x[i]);
+      idx.push_back(l);
+      nvl.push_back(__builtin_popcount(T) + 1);
+    }
+  BatchArgs a;
+  a.mode = BatchArgs::PROB;
+  a.B = k->B;
+  a.B32 = k->B32;
+  a.m = k->m;
+  a.log_norm_dev = k->dscal;
+  a.idx = idx.data();
+  a.n = nvl.data();
+  a.offs = offs.data();
+  a.batch = cnt * half;
+  a.precision = GBS_FP64;
+  a.stream = st;
+  a.out2 = (double*)dst;
+  return run_batch(a);
+}
+
+}  // namespace
+
 extern "C" int gbs_sample_chain(const gbs_kernel* k, int n, const double* uniforms, void* stream, int* x_out) {
   clear_error();
   if (!k || (n > 0 && (!uniforms || !x_out))) return fail(GBS_EINVAL, "null argument");
@@ -309,12 +453,19 @@ extern "C" int gbs_sample_chain(const gbs_kernel* k, int n, const double* unifor
   if (!(k->t_uniform > 0.0)) return fail(GBS_EINVAL, "marginals need r > 0");
   cudaStream_t st = (cudaStream_t)stream;
   const int m = k->m;
+  // candidates per pass at the last step (at most 2^22 new sub-Hafnians)
+  const int chunk_max = std::max(1, std::min(m, (1 << 22) >> (n - 1)));
   auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
-  const size_t cache_b = al(16 * ((size_t)1 << n)), new_b = al(16 * ((size_t)m << (n - 1)));
-  const size_t H_b = al(16 * ((size_t)m << n)), F_b = al(8 * (size_t)(n / 2 + 1) * (n / 2 + 1) * (n + 1));
+  const size_t cache_b = al(16 * ((size_t)1 << n)), new_b = al(16 * ((size_t)chunk_max << (n - 1)));
+  const size_t H_b = al(16 * ((size_t)chunk_max << n)), F_b = al(8 * (size_t)(n / 2 + 1) * (n / 2 + 1) * (n + 1));
   const size_t vm_b = al(4 * (size_t)m * kMaxK), nv_b = al(4 * (size_t)m), q_b = al(8 * (size_t)m);
+  size_t part_b = 0;
+  for (int kk = 1; kk <= n; ++kk) {
+    const int ch = std::max(1, std::min(m, (1 << 22) >> (kk - 1)));
+    part_b = std::max(part_b, al(marginal_part_bytes(kk, ch)));
+  }
   void* tmp = nullptr;
-  cudaError_t e = scratch_alloc(&tmp, cache_b + new_b + H_b + F_b + vm_b + nv_b + q_b, st);
+  cudaError_t e = scratch_alloc(&tmp, cache_b + new_b + H_b + F_b + vm_b + nv_b + q_b + part_b, st);
   if (e != cudaSuccess) return fail(GBS_ENOMEM, "chain scratch: %s", cudaGetErrorString(e));
   unsigned char* t = (unsigned char*)tmp;
   double2* d_cache = (double2*)t;
@@ -324,10 +475,10 @@ extern "C" int gbs_sample_chain(const gbs_kernel* k, int n, const double* unifor
   int* d_vm = (int*)(t + cache_b + new_b + H_b + F_b);
   int* d_nv = (int*)(t + cache_b + new_b + H_b + F_b + vm_b);
   double* d_q = (double*)(t + cache_b + new_b + H_b + F_b + vm_b + nv_b);
+  double* d_part = (double*)(t + cache_b + new_b + H_b + F_b + vm_b + nv_b + q_b);
   std::vector<int> x;
   std::vector<double> w(m);
-  std::vector<int> idx, nvl, vmask((size_t)m * kMaxK), nvals(m);
-  std::vector<int64_t> offs;
+  std::vector<int> vmask((size_t)m * kMaxK), nvals(m);
   int ret = GBS_OK;
   do {
     const double2 one = make_double2(1.0, 0.0);  // Haf of the empty matrix
@@ -337,34 +488,7 @@ extern "C" int gbs_sample_chain(const gbs_kernel* k, int n, const double* unifor
     }
     for (int kk = 1; kk <= n && ret == GBS_OK; ++kk) {
       const int half = 1 << (kk - 1);
-      // new sub-Hafnians: candidate l, mask T' over positions 0..kk-2 (odd
-      // |T'| gives an even list; even |T'| an odd one, whose Hafnian is 0 and
-      // costs no work), list = x_{T'} followed by l
-      idx.clear();
-      nvl.clear();
-      offs.clear();
-      for (int l = 0; l < m; ++l)
-        for (int T = 0; T < half; ++T) {
-          offs.push_back((int64_t)idx.size());
-          for (int i = 0; i < kk - 1; ++i)
-            if (T >> i & 1) idx.push_back(x[i]);
-          idx.push_back(l);
-          nvl.push_back(__builtin_popcount(T) + 1);
-        }
-      BatchArgs a;
-      a.mode = BatchArgs::PROB;
-      a.B = k->B;
-      a.B32 = k->B32;
-      a.m = m;
-      a.log_norm_dev = k->dscal;
-      a.idx = idx.data();
-      a.n = nvl.data();
-      a.offs = offs.data();
-      a.batch = m * half;
-      a.precision = GBS_FP64;
-      a.stream = st;
-      a.out2 = (double*)d_new;
-      if ((ret = run_batch(a)) != GBS_OK) break;
+      const int chunk = std::max(1, std::min(m, (1 << 22) >> (kk - 1)));
       // per candidate: position masks of the distinct values (for Per(S_{A,B}))
       std::fill(vmask.begin(), vmask.end(), 0);
       for (int l = 0; l < m; ++l) {
@@ -387,14 +511,21 @@ extern "C" int gbs_sample_chain(const gbs_kernel* k, int n, const double* unifor
         ret = cuda_fail(e, "chain upload");
         break;
       }
-      chain_table_kernel<<<std::min(4096, (int)((((int64_t)m << kk) + 255) / 256)), 256, 0, st>>>(
-          d_cache, d_new, kk, k->t_uniform, m, d_H);
       fcoef_kernel<<<1, 256, 0, st>>>(kk, n, m, d_F);
-      marginal_kernel<<<m, 256, 0, st>>>(kk, n, d_H, d_F, d_vm, d_nv, d_q);
-      if ((e = cudaGetLastError()) != cudaSuccess) {
-        ret = cuda_fail(e, "chain kernels");
-        break;
+      for (int l0 = 0; l0 < m && ret == GBS_OK; l0 += chunk) {
+        const int cnt = std::min(chunk, m - l0);
+        if ((ret = chain_new_subhafnians(k, x, kk, l0, cnt, st, d_new)) != GBS_OK) break;
+        chain_table_kernel<<<std::min(4096, (int)((((int64_t)cnt << kk) + 255) / 256)), 256, 0, st>>>(
+            d_cache, d_new, kk, k->t_uniform, cnt, d_H);
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+          e = launch_marginals(kk, n, d_H, d_F, d_vm + (size_t)l0 * kMaxK, d_nv + l0, cnt, d_part, d_q + l0, st);
+        if (e != cudaSuccess) {
+          ret = cuda_fail(e, "chain kernels");
+          break;
+        }
       }
+      if (ret != GBS_OK) break;
       if ((e = cudaMemcpyAsync(w.data(), d_q, 8 * (size_t)m, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
           (e = cudaStreamSynchronize(st)) != cudaSuccess) {
         ret = cuda_fail(e, "chain weights");
@@ -414,10 +545,18 @@ extern "C" int gbs_sample_chain(const gbs_kernel* k, int n, const double* unifor
       }
       x.push_back(pick);
       // keep the chosen candidate's new sub-Hafnians: masks with bit kk-1
-      if (kk < n && (e = cudaMemcpyAsync(d_cache + half, d_new + (size_t)pick * half, 16 * (size_t)half,
-                                         cudaMemcpyDeviceToDevice, st)) != cudaSuccess) {
-        ret = cuda_fail(e, "cache update");
-        break;
+      if (kk < n) {
+        if (chunk >= m) {
+          e = cudaMemcpyAsync(d_cache + half, d_new + (size_t)pick * half, 16 * (size_t)half,
+                              cudaMemcpyDeviceToDevice, st);
+          if (e != cudaSuccess) {
+            ret = cuda_fail(e, "cache update");
+            break;
+          }
+        } else {
+          std::vector<int> xp(x.begin(), x.end() - 1);
+          if ((ret = chain_new_subhafnians(k, xp, kk, pick, 1, st, d_cache + half)) != GBS_OK) break;
+        }
       }
     }
   } while (0);

@@ -24,6 +24,13 @@
 // which the server polls without a driver call. Every wait on the device is a
 // bounded poll: past wait_timeout_s the server fails the outstanding requests
 // with GBS_ETIMEDOUT and stops.
+//
+// A request with n >= kPairingMinN first waits for the ordering probe of the
+// batched calls (run on a side stream, several waiting requests in one
+// launch): its index list is stored in the chosen ordering, so its subset sum
+// has the same cancellation, and so the same accuracy, as in gbs_prob_batch.
+// The choice depends only on the request, so results stay the same alone and
+// in any mix.
 #include <math.h>
 #include <string.h>
 
@@ -48,8 +55,11 @@ struct Request {
   int64_t ticket;
   int n;
   int prec;
+  bool probed;  // the list is in its chosen ordering (n >= kPairingMinN)
   int idx[GBS_MAX_N];
 };
+
+constexpr int kProbeMax = 64;  // requests in one probe launch
 
 struct Result {
   int rc;
@@ -60,9 +70,11 @@ struct Result {
 class Arena {
  public:
   void init(int cap) {
+    cap_ = cap;
     free_.clear();
     free_.push_back({0, cap});
   }
+  int capacity() const { return cap_; }
   int alloc(int len) {
     for (size_t i = 0; i < free_.size(); ++i)
       if (free_[i].len >= len) {
@@ -94,6 +106,7 @@ class Arena {
     int start, len;
   };
   std::vector<R> free_;
+  int cap_ = 0;
 };
 
 struct Slot {
@@ -104,6 +117,8 @@ struct Slot {
   size_t next = 0;              // next item to dispatch
   int part_base = 0;
   bool finalize_sent = false;
+  bool cancelled = false;  // its ticket is answered; the slot frees once no step in flight uses it
+  int64_t last_step = 0;   // the last step that carried its items or its finalisation
 };
 
 constexpr int kStepCap = 65536;  // work items per precision per step
@@ -156,6 +171,7 @@ struct gbs_server {
   std::condition_variable cv;
   bool stop = false;
   bool failed = false;
+  int fail_rc = GBS_ECUDA;  // why the server stopped (GBS_ETIMEDOUT or GBS_ECUDA)
   std::deque<Request> queue;
   // Results have their own lock (taken after mu, never before it), so that a
   // client polling in a tight loop contends only for the result table and
@@ -177,6 +193,16 @@ struct gbs_server {
   std::vector<int> h_idx;
   size_t off_pats = 0, off_idx = 0, off_items[2] = {0, 0}, off_sel = 0, off_hdr = 0, up_bytes = 0;
   Stage stage[2];
+  // ordering probe of requests with n >= kPairingMinN (side stream)
+  cudaStream_t st_probe = nullptr;
+  std::deque<Request> probe_wait;
+  std::vector<Request> probing;  // in the probe launch in flight
+  OrderProbe probe;
+  bool probe_busy = false;
+  std::chrono::steady_clock::time_point probe_t0;
+  std::unordered_set<int64_t> probe_cancelled;  // cancelled while in the probe launch
+  int64_t last_done_step = 0;  // the newest step whose completion was handled
+  int fault_allocs = 0;        // injected allocation failures still to report
   std::thread th;
   gbs_serve_stats_t stats;
   // server-thread only (no lock): the last time the thread ran its loop or a
@@ -455,9 +481,95 @@ cudaError_t launch_stage(gbs_server* s, Stage& g) {
   return cudaEventRecord(g.ev, s->st);
 }
 
+void fail_all(gbs_server* s, int rc);
+
+// Fail the given tickets with rc (lock held).
+void fail_tickets(gbs_server* s, const std::vector<Request>& reqs, int rc) {
+  std::lock_guard<std::mutex> rl(s->rmu);
+  for (const Request& q : reqs) {
+    Result r;
+    r.rc = rc;
+    r.p = r.hr = r.hi = r.err = NAN;
+    s->done[q.ticket] = r;
+    s->pending.erase(q.ticket);
+  }
+}
+
+// Ordering probe (lock held): collect a finished probe launch, whose requests
+// go back to the front of the queue with their lists in the chosen ordering,
+// and start the next one for the requests waiting. Returns false after a
+// failure that stops the server.
+bool probe_step(gbs_server* s) {
+  if (s->probe_busy) {
+    if (!order_probe_ready(s->probe)) {
+      // no driver call while it runs (a probe takes well under a
+      // millisecond); past 5 ms its event tells a failed launch from a slow one
+      const double el =
+          std::chrono::duration<double>(std::chrono::steady_clock::now() - s->probe_t0).count();
+      if (el < 5e-3) return true;
+      const cudaError_t e = cudaEventQuery(s->probe.done);
+      if (e != cudaSuccess && e != cudaErrorNotReady) {
+        cudaGetLastError();
+        fail_all(s, GBS_ECUDA);
+        s->fail_rc = GBS_ECUDA;
+        return false;
+      }
+      if (el <= s->o.wait_timeout_s) return true;
+      fail_all(s, GBS_ETIMEDOUT);
+      s->fail_rc = GBS_ETIMEDOUT;
+      return false;
+    }
+    int pos[GBS_MAX_N];
+    for (int i = (int)s->probing.size() - 1; i >= 0; --i) {
+      Request& q = s->probing[i];
+      if (s->probe_cancelled.erase(q.ticket)) continue;  // answered already
+      if (order_probe_result(s->probe, i, pos)) {
+        // the kernel reads position p of the list at default_pos(p, h): store
+        // the list so that this gives source position pos[p]
+        int y[GBS_MAX_N];
+        for (int p = 0; p < q.n; ++p) y[default_pos(p, q.n / 2)] = q.idx[pos[p]];
+        memcpy(q.idx, y, sizeof(int) * q.n);
+      }
+      q.probed = true;
+      s->queue.push_front(q);
+    }
+    s->probing.clear();
+    order_probe_release(&s->probe, s->st_probe);
+    s->probe_busy = false;
+  }
+  if (!s->probe_busy && !s->probe_wait.empty()) {
+    const int cnt = (int)std::min<size_t>(s->probe_wait.size(), kProbeMax);
+    s->probing.assign(s->probe_wait.begin(), s->probe_wait.begin() + cnt);
+    s->probe_wait.erase(s->probe_wait.begin(), s->probe_wait.begin() + cnt);
+    const int* lists[kProbeMax];
+    int ns[kProbeMax];
+    for (int i = 0; i < cnt; ++i) {
+      lists[i] = s->probing[i].idx;
+      ns[i] = s->probing[i].n;
+    }
+    const int rc = order_probe_launch(s->k, lists, ns, cnt, s->o.max_n / 2, s->cfg[GBS_MIXED], s->st_probe,
+                                      &s->probe);
+    if (rc != GBS_OK) {
+      fail_tickets(s, s->probing, rc);
+      s->probing.clear();
+      return true;
+    }
+    s->probe_busy = true;
+    s->probe_t0 = std::chrono::steady_clock::now();
+    s->stats.probed += cnt;
+  }
+  return true;
+}
+
 // Admit queued requests into free slots while the arena has room (lock held).
+// A request that still needs the ordering probe moves to its waiting list.
 void admit(gbs_server* s) {
   while (!s->queue.empty()) {
+    if (s->queue.front().n >= kPairingMinN && !s->queue.front().probed) {
+      s->probe_wait.push_back(s->queue.front());
+      s->queue.pop_front();
+      continue;
+    }
     int si = -1;
     for (int i = 0; i < s->o.max_slots; ++i)
       if (!s->slots[i].used) {
@@ -468,8 +580,25 @@ void admit(gbs_server* s) {
     const Request& r = s->queue.front();
     Slot& sl = s->slots[si];
     request_items(s, si, r.n, r.prec, sl.items);
-    const int base = s->arena.alloc((int)sl.items.size());
-    if (base < 0) return;  // wait for memory to free up
+    if ((int64_t)sl.items.size() > s->arena.capacity()) {
+      // more partial sums than the whole memory budget holds: it can never
+      // be admitted, so it fails now instead of waiting forever
+      fail_tickets(s, std::vector<Request>(1, r), GBS_ENOMEM);
+      sl.items.clear();
+      s->queue.pop_front();
+      continue;
+    }
+    int base = -1;
+    if (s->fault_allocs > 0) {
+      --s->fault_allocs;  // injected failure: as if the budget were used up
+    } else {
+      base = s->arena.alloc((int)sl.items.size());
+    }
+    if (base < 0) {  // wait for memory to free up
+      s->stats.alloc_waits++;
+      sl.items.clear();
+      return;
+    }
     for (size_t i = 0; i < sl.items.size(); ++i) sl.items[i].part = base + (int)i;
     sl.used = true;
     sl.ticket = r.ticket;
@@ -478,6 +607,8 @@ void admit(gbs_server* s) {
     sl.next = 0;
     sl.part_base = base;
     sl.finalize_sent = false;
+    sl.cancelled = false;
+    sl.last_step = 0;
     PatDesc& d = s->h_pats[si];
     d.src_off = 0;
     d.idx_off = (int64_t)si * GBS_MAX_N;
@@ -500,10 +631,12 @@ bool build_step(gbs_server* s, Stage& g) {
   WorkItem* it[2] = {(WorkItem*)(g.h_up + s->off_items[0]), (WorkItem*)(g.h_up + s->off_items[1])};
   int* sel = (int*)(g.h_up + s->off_sel);
   const int quota = s->o.subsets_per_step;
+  const int64_t id = s->step_id + 1;
   for (int q = 0; q < S; ++q) {
     const int si = (s->rr + q) % S;
     Slot& sl = s->slots[si];
-    if (!sl.used || sl.finalize_sent) continue;
+    if (!sl.used || sl.finalize_sent || sl.cancelled) continue;
+    sl.last_step = id;
     int taken = 0;
     int& cnt = g.n_items[sl.prec];
     while (sl.next < sl.items.size() && taken < quota && cnt < kStepCap) {
@@ -518,7 +651,7 @@ bool build_step(gbs_server* s, Stage& g) {
     }
   }
   s->rr = (s->rr + 1) % S;
-  g.id = ++s->step_id;
+  g.id = ++s->step_id;  // == id
   return g.n_items[0] > 0 || g.n_items[1] > 0 || !g.fin.empty();
 }
 
@@ -528,6 +661,13 @@ void complete(gbs_server* s, Stage& g) {
   std::lock_guard<std::mutex> rl(s->rmu);
   for (size_t b = 0; b < g.fin.size(); ++b) {
     Slot& sl = s->slots[g.fin[b]];
+    if (sl.cancelled) {  // answered at cancellation: drop the result
+      s->arena.release(sl.part_base, (int)sl.items.size());
+      sl.used = false;
+      sl.cancelled = false;
+      sl.items.clear();
+      continue;
+    }
     Result r;
     r.rc = GBS_OK;
     r.p = g.h_res[b];
@@ -543,6 +683,18 @@ void complete(gbs_server* s, Stage& g) {
   }
   g.fin.clear();
   g.busy = false;
+  s->last_done_step = std::max(s->last_done_step, g.id);
+}
+
+// Free the slots of cancelled requests that no step in flight uses (lock held).
+void reap_cancelled(gbs_server* s) {
+  for (Slot& sl : s->slots)
+    if (sl.used && sl.cancelled && !sl.finalize_sent && sl.last_step <= s->last_done_step) {
+      s->arena.release(sl.part_base, (int)sl.items.size());
+      sl.used = false;
+      sl.cancelled = false;
+      sl.items.clear();
+    }
 }
 
 void fail_all(gbs_server* s, int rc) {
@@ -555,7 +707,13 @@ void fail_all(gbs_server* s, int rc) {
   }
   s->pending.clear();
   s->queue.clear();
-  for (auto& sl : s->slots) sl.used = false;
+  s->probe_wait.clear();
+  s->probing.clear();
+  s->probe_cancelled.clear();
+  for (auto& sl : s->slots) {
+    sl.used = false;
+    sl.cancelled = false;
+  }
 }
 
 // Bounded wait for a stage's event; false on timeout or error. The first
@@ -613,11 +771,19 @@ void serve_loop(gbs_server* s) {
     tick(s);
     s->stats.poll_gap_max_s = s->tick_gap_max;
     admit(s);
+    if (!probe_step(s)) {
+      s->failed = true;
+      break;
+    }
+    reap_cancelled(s);
+    admit(s);  // requests whose probe just finished, or whose slot freed
     bool any_work = false;
     for (const Slot& sl : s->slots)
-      if (sl.used && !sl.finalize_sent) any_work = true;
+      if (sl.used && !sl.finalize_sent && !sl.cancelled) any_work = true;
     Stage* free_stage = !s->stage[0].busy ? &s->stage[0] : (!s->stage[1].busy ? &s->stage[1] : nullptr);
-    if (s->stop && !any_work && !s->stage[0].busy && !s->stage[1].busy && s->queue.empty()) break;
+    if (s->stop && !any_work && !s->stage[0].busy && !s->stage[1].busy && s->queue.empty() && !s->probe_busy &&
+        s->probe_wait.empty())
+      break;
     bool launched = false;
     if (any_work && free_stage && build_step(s, *free_stage)) {
       const auto tl0 = std::chrono::steady_clock::now();
@@ -670,14 +836,23 @@ void serve_loop(gbs_server* s) {
         complete(s, *old);
         s->cv.notify_all();
       } else if (block) {
+        // the wait gave up: a step that has finished meanwhile is taken
+        // normally on the next pass; one still running, or failed, stops the
+        // server
         const cudaError_t e = cudaEventQuery(old->ev);
-        cudaGetLastError();
-        fail_all(s, e == cudaErrorNotReady ? GBS_ETIMEDOUT : GBS_ECUDA);
-        s->failed = true;
-        break;
+        if (e != cudaSuccess) {
+          cudaGetLastError();
+          s->fail_rc = (e == cudaErrorNotReady) ? GBS_ETIMEDOUT : GBS_ECUDA;
+          fail_all(s, s->fail_rc);
+          s->failed = true;
+          break;
+        }
       }
     } else if (!launched) {
-      s->cv.wait_for(lk, std::chrono::milliseconds(1));
+      if (s->probe_busy)  // a probe is in flight: poll it soon
+        s->cv.wait_for(lk, std::chrono::microseconds(20));
+      else
+        s->cv.wait_for(lk, std::chrono::milliseconds(1));
     }
   }
   s->cv.notify_all();
@@ -700,6 +875,12 @@ void destroy_resources(gbs_server* s) {
   if (s->d_pats) cudaFree(s->d_pats);
   if (s->d_idx) cudaFree(s->d_idx);
   if (s->d_parts) cudaFree(s->d_parts);
+  if (s->st_probe) {
+    cudaStreamSynchronize(s->st_probe);
+    order_probe_release(&s->probe, s->st_probe);
+    order_probe_destroy(&s->probe);
+    cudaStreamDestroy(s->st_probe);
+  }
   if (s->st) cudaStreamDestroy(s->st);
 }
 
@@ -720,6 +901,7 @@ extern "C" int gbs_serve_create(const gbs_kernel* k, const gbs_serve_opts* opts,
   if (s->o.subsets_per_step <= 0) s->o.subsets_per_step = 8192;
   if (s->o.wait_timeout_s <= 0) s->o.wait_timeout_s = 10.0;
   if (s->o.max_n <= 0 || s->o.max_n > GBS_MAX_N) s->o.max_n = GBS_MAX_N;
+  s->fault_allocs = s->o.fault_alloc_failures > 0 ? s->o.fault_alloc_failures : 0;
   s->o.use_graphs = (s->o.use_graphs >= 0) ? 1 : 0;
   s->k = k;
   s->device = k->device;
@@ -735,6 +917,8 @@ extern "C" int gbs_serve_create(const gbs_kernel* k, const gbs_serve_opts* opts,
     if (e != cudaSuccess) { ret = cuda_fail(e, "log_norm"); break; }
     e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
     if (e != cudaSuccess) { ret = cuda_fail(e, "stream"); break; }
+    e = cudaStreamCreateWithFlags(&s->st_probe, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { ret = cuda_fail(e, "probe stream"); break; }
     for (int p = 0; p < 2; ++p) {
       s->cfg[p] = default_cfg(p, s->o.max_n);
       const int smem = s->cfg[p].warps_per_block * s->cfg[p].warp_bytes;
@@ -753,6 +937,7 @@ extern "C" int gbs_serve_create(const gbs_kernel* k, const gbs_serve_opts* opts,
     const size_t arena_items = std::min<size_t>((s->o.mem_budget - tables - stage_b) / sizeof(Partial),
                                                 (size_t)1 << 30);
     s->arena.init((int)arena_items);
+    s->stats.arena_slots = (int64_t)arena_items;
     if ((e = cudaMalloc(&s->d_pats, sizeof(PatDesc) * S)) != cudaSuccess ||
         (e = cudaMalloc(&s->d_idx, sizeof(int) * GBS_MAX_N * S)) != cudaSuccess ||
         (e = cudaMalloc(&s->d_parts, sizeof(Partial) * arena_items)) != cudaSuccess) {
@@ -822,7 +1007,9 @@ extern "C" int gbs_serve_submit(gbs_server* s, const int* idx, int n, int precis
     if (idx[i] < 0 || idx[i] >= s->k->m)
       return fail(GBS_ERANGE, "index %d = %d is outside [0, %d)", i, idx[i], s->k->m);
   std::lock_guard<std::mutex> lk(s->mu);
-  if (s->failed) return fail(GBS_ECUDA, "server stopped after an error");
+  if (s->failed)
+    return fail(s->fail_rc, "server stopped after %s",
+                s->fail_rc == GBS_ETIMEDOUT ? "a device wait timed out" : "an error");
   if (s->stop) return fail(GBS_EINVAL, "server is stopping");
   if (n == 0 || (n & 1)) {
     const int64_t t = s->next_ticket++;
@@ -846,12 +1033,59 @@ extern "C" int gbs_serve_submit(gbs_server* s, const int* idx, int n, int precis
   r.ticket = t;
   r.n = n;
   r.prec = precision;
+  r.probed = false;
   memcpy(r.idx, idx, sizeof(int) * n);
   s->queue.push_back(r);
   {
     std::lock_guard<std::mutex> rl(s->rmu);
     s->pending.insert(t);
   }
+  s->cv.notify_all();
+  return GBS_OK;
+}
+
+extern "C" int gbs_serve_cancel(gbs_server* s, int64_t ticket) {
+  clear_error();
+  if (!s) return fail(GBS_EINVAL, "null server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  {
+    std::lock_guard<std::mutex> rl(s->rmu);
+    if (s->done.count(ticket)) return 1;  // finished (or failed): collect it with gbs_serve_poll
+    if (!s->pending.count(ticket))
+      return fail(GBS_ENOENT, "unknown or already collected ticket %lld", (long long)ticket);
+  }
+  bool found = false;
+  for (auto it = s->queue.begin(); it != s->queue.end() && !found; ++it)
+    if (it->ticket == ticket) {
+      s->queue.erase(it);
+      found = true;
+      break;
+    }
+  for (auto it = s->probe_wait.begin(); it != s->probe_wait.end() && !found; ++it)
+    if (it->ticket == ticket) {
+      s->probe_wait.erase(it);
+      found = true;
+      break;
+    }
+  for (const Request& q : s->probing)
+    if (!found && q.ticket == ticket) {
+      s->probe_cancelled.insert(ticket);  // dropped when its probe launch returns
+      found = true;
+    }
+  for (Slot& sl : s->slots)
+    if (!found && sl.used && !sl.cancelled && sl.ticket == ticket) {
+      // its steps in flight finish; no more are built, and the slot frees
+      // once none is left
+      sl.cancelled = true;
+      found = true;
+    }
+  std::lock_guard<std::mutex> rl(s->rmu);
+  Result r;
+  r.rc = GBS_ECANCELED;
+  r.p = r.hr = r.hi = r.err = NAN;
+  s->done[ticket] = r;
+  s->pending.erase(ticket);
+  s->stats.cancelled++;
   s->cv.notify_all();
   return GBS_OK;
 }
@@ -867,7 +1101,12 @@ extern "C" int gbs_serve_poll(gbs_server* s, int64_t ticket, double* p, double* 
   }
   const Result r = it->second;
   s->done.erase(it);
-  if (r.rc != GBS_OK) return fail(r.rc, "request failed (%s)", r.rc == GBS_ETIMEDOUT ? "device wait timed out" : "CUDA error");
+  if (r.rc != GBS_OK)
+    return fail(r.rc, "request failed (%s)",
+                r.rc == GBS_ETIMEDOUT   ? "device wait timed out"
+                : r.rc == GBS_ECANCELED ? "cancelled"
+                : r.rc == GBS_ENOMEM    ? "needs more partial sums than the memory budget holds"
+                                        : "CUDA error");
   if (p) *p = r.p;
   if (haf_ri) {
     haf_ri[0] = r.hr;
@@ -897,7 +1136,10 @@ extern "C" int gbs_serve_destroy(gbs_server* s) {
   cudaSetDevice(s->device);
   cudaStreamSynchronize(s->st);
   const bool failed = s->failed;
+  const int frc = s->fail_rc;
   destroy_resources(s);
   delete s;
-  return failed ? fail(GBS_ECUDA, "server had stopped after an error") : GBS_OK;
+  return failed ? fail(frc, "server had stopped after %s",
+                       frc == GBS_ETIMEDOUT ? "a device wait timed out" : "an error")
+                : GBS_OK;
 }

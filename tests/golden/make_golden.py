@@ -1,6 +1,6 @@
 """Write double-double oracle values for the parity tests at full workload size.
 
-    python tests/golden/make_golden.py [name ...]
+    python tests/golden/make_golden.py [--out DIR] [name ...]
 
 Calls only the oracle and the seeded input generators. Each file holds, per
 pattern (or request), the oracle's Hafnian of B_x rounded to complex128, log p,
@@ -18,8 +18,13 @@ Files (tests/golden/):
   large_m900_default_order.json patterns 0-3 (n = 28) and 64-65 (n = 30) of the
                                 M = 900 batch: kappa in the default order
 
+Each file records a SHA-256 of the Haar draw U's bytes: the draw comes from a
+LAPACK QR, whose last bits differ between platforms, so the values must be
+written on the platform whose GPU tests read them (the tests check the hash).
+
 Takes about ten minutes on eight cores.
 """
+import hashlib
 import json
 import os
 import sys
@@ -51,6 +56,7 @@ def table(U, r, pats, name, extra=None):
     mod = np.abs(haf)
     kappa = np.where(mod > 0, res["kappa"] / np.where(mod > 0, mod, 1.0), 0.0)
     out = {"workload": name, "m": int(U.shape[0]),
+           "U_sha256": u_hash(U),
            "B_checksum": [float(np.abs(B).sum()), float(B.real.sum()), float(B.imag.sum())],
            "order": "pair t = positions (t, t + n/2); zero diagonal",
            "x": [[int(v) for v in p] for p in pats],
@@ -62,8 +68,17 @@ def table(U, r, pats, name, extra=None):
     return out
 
 
+def u_hash(U):
+    """SHA-256 of the Haar draw's bytes (complex128, row-major)."""
+    return hashlib.sha256(np.ascontiguousarray(U, dtype=np.complex128).tobytes()).hexdigest()
+
+
+OUT = HERE
+
+
 def write(fname, obj):
-    with open(os.path.join(HERE, fname), "w") as f:
+    os.makedirs(OUT, exist_ok=True)
+    with open(os.path.join(OUT, fname), "w") as f:
         json.dump(obj, f, separators=(",", ":"))
 
 
@@ -88,4 +103,8 @@ def main(names):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:])
+    args = sys.argv[1:]
+    if args[:1] == ["--out"]:
+        OUT = os.path.abspath(args[1])
+        args = args[2:]
+    main(args)

@@ -2,10 +2,15 @@
 of all 80 patterns of the large workload (M = 900, r = 1, 64 at n = 28 and 16
 at n = 30). Calls only the oracle and the seeded input generators.
 
-    python tests/golden/make_large_golden.py
+    python tests/golden/make_large_golden.py [--out DIR]
+
+The Haar draw comes from a LAPACK QR whose last bits differ between
+platforms; the file records a SHA-256 of U's bytes, and must be written on
+the platform whose GPU tests read it.
 
 Takes tens of minutes on a few cores (the oracle is the plain subset sum with
 repeated products in double-double arithmetic)."""
+import hashlib
 import json
 import os
 import sys
@@ -25,6 +30,7 @@ def main():
     Bdd = oracle.build_B_dd(U, np.tanh(r))
     B = (Bdd[..., 0] + Bdd[..., 1]) + 1j * (Bdd[..., 2] + Bdd[..., 3])
     out = {"workload": "large_m900", "m": 900, "r": 1.0,
+           "U_sha256": hashlib.sha256(np.ascontiguousarray(U, dtype=np.complex128).tobytes()).hexdigest(),
            "B_checksum": [float(np.abs(B).sum()), float(B.real.sum()), float(B.imag.sum())],
            "patterns": []}
     t0 = time.time()
@@ -35,7 +41,9 @@ def main():
                                 "haf_dd": [float(v) for v in hd], "p": float(res["p"][0]),
                                 "logp": float(res["logp"][0]), "kappa": float(res["kappa"][0])})
         print("%d/%d n=%d %.0fs" % (i + 1, len(pats), len(x), time.time() - t0), flush=True)
-    with open(os.path.join(HERE, "large_m900_oracle.json"), "w") as f:
+    out_dir = os.path.abspath(sys.argv[2]) if sys.argv[1:2] == ["--out"] else HERE
+    os.makedirs(out_dir, exist_ok=True)
+    with open(os.path.join(out_dir, "large_m900_oracle.json"), "w") as f:
         json.dump(out, f)
 
 

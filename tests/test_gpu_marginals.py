@@ -161,3 +161,54 @@ def test_chain_sampler_cache_matches_plain_chain(gbs):
             c = np.cumsum(w)
             x.append(int(min(np.searchsorted(c, u[k - 1] * c[-1], side="right"), m - 1)))
         assert list(got) == x, (list(got), x)
+
+
+def brute_marginals_subset(orc, U, prefixes, n):
+    """The plain definition with the oracle's double-double subset sum (pinned
+    against perfect matchings) for the longer lists."""
+    m = U.shape[0]
+    Wdd = orc.build_B_dd(U, np.ones(m))
+    out = []
+    for x in prefixes:
+        comps = [np.array(list(x) + list(c), dtype=np.int32) for c in itertools.product(range(m), repeat=n - len(x))]
+        h = orc.prob(U, np.zeros(m), comps, Bdd=Wdd)["haf"]
+        out.append(np.sum(np.abs(h) ** 2) / f_n(m, n))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("m,n,ks", [(3, 14, (12, 13, 14)), (14, 14, (12, 13)), (4, 16, (13, 14)), (2, 20, (18, 19, 20))])
+def test_marginals_long_prefixes_vs_definition(gbs, orc, m, n, ks):
+    """Prefixes of 12 to 20 photons (beyond the nested sums' reach): with many
+    repeated modes (m = 2..4, the multiset form of the regrouped sum) and
+    without any (m = 14, one prefix of distinct modes), against the brute-force
+    marginal of Eq. marginal_definition."""
+    U = W.haar_unitary(m, 300 + m + n)
+    K = gbs.build_kernel(U, np.full(m, 0.75))
+    rng = np.random.default_rng(m * 31 + n)
+    for k in ks:
+        if m >= k:
+            prefixes = [rng.permutation(m)[:k] for _ in range(2)]
+        else:
+            prefixes = [rng.integers(0, m, size=k) for _ in range(3)]
+        got = gbs.marginal_batch(K, np.array(prefixes).reshape(len(prefixes), k), n)
+        ref = brute_marginals_subset(orc, U, prefixes, n)
+        assert np.all(np.abs(got - ref) <= 1e-10 * np.abs(ref) + 1e-300), (k, got, ref)
+
+
+def test_chain_sampler_n12_matches_plain_chain(gbs):
+    """A 12-photon chain sample (Algorithm 1) with the Appendix D cache equals
+    the chain that recomputes every conditional weight with gbs_marginal_batch."""
+    m, n = 9, 12
+    U = W.haar_unitary(m, 321)
+    K = gbs.build_kernel(U, np.full(m, 0.8))
+    rng = np.random.default_rng(6)
+    for _ in range(3):
+        u = rng.random(n)
+        got = gbs.sample_chain(K, n, u)
+        x = []
+        for k in range(1, n + 1):
+            pre = np.array([x + [l] for l in range(m)], np.int32)
+            w = np.maximum(gbs.marginal_batch(K, pre, n), 0.0)
+            c = np.cumsum(w)
+            x.append(int(min(np.searchsorted(c, u[k - 1] * c[-1], side="right"), m - 1)))
+        assert list(got) == x, (list(got), x)

@@ -59,6 +59,47 @@ def run_prob(gbs, K, pats, precision, host=False):
     return p.cpu().numpy(), lp.cpu().numpy(), h[0::2] + 1j * h[1::2], er.cpu().numpy()
 
 
+def golden(name):
+    """Stored double-double oracle values (tests/golden/make_golden.py)."""
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        g = json.load(f)
+    g["haf"] = np.array(g["haf_re"]) + 1j * np.array(g["haf_im"])
+    g["logp"] = np.array(g["logp"])
+    g["kappa"] = np.array(g["kappa"])
+    return g
+
+
+def check_draw(U, g):
+    """The Haar draw on this machine is byte for byte the one the stored values
+    were computed from (the draw comes from a LAPACK QR, whose last bits differ
+    between platforms; tests/golden/make_golden.py writes the values on the
+    platform that runs these tests)."""
+    import hashlib
+
+    h = hashlib.sha256(np.ascontiguousarray(U, dtype=np.complex128).tobytes()).hexdigest()
+    assert h == g["U_sha256"], "Haar draw differs from the stored values' draw: regenerate tests/golden"
+
+
+def check_B(K, g):
+    """The box's Haar draw and kernel matrix are the ones the values came from."""
+    m = g["m"]
+    B = torch.zeros(2 * m * m, dtype=torch.float64, device="cuda")
+    K.copy_B(B)
+    Bc = B.cpu().numpy().view(np.complex128)
+    assert abs(np.abs(Bc).sum() - g["B_checksum"][0]) <= 1e-9 * g["B_checksum"][0]
+    return Bc.reshape(m, m)
+
+
+def kappa_pin(kp, kref, slack=0.0):
+    """The library reports kappa with |z|_1 = |re| + |im| per term, the oracle
+    with the modulus: the ratio lies in [1, sqrt(2)] (up to the slack of the
+    path's own rounding of the terms)."""
+    return (kref * (1 - 1e-6 - slack) <= kp) & (kp <= math.sqrt(2) * kref * (1 + 1e-6 + slack))
+
+
 def kernel_for(gbs, U, r):
     Ud = dev(np.ascontiguousarray(U).view(np.float64))
     return gbs.build_kernel(Ud, dev(r))
@@ -86,7 +127,12 @@ def test_build_kernel_matches_oracle(gbs, orc, m, seed):
     torch.cuda.synchronize()
     Bg = B.cpu().numpy().view(np.complex128).reshape(m, m)
     Bo = orc.build_B(U, r)
-    assert np.abs(Bg - Bo).max() <= 1e-15 * max(1.0, math.sqrt(m))
+    # entries correctly rounded up to the last bit of tanh r_k (each side
+    # rounds it once; sum_k |U_ik| |U_jk| <= 1, so that moves an entry by at
+    # most ~1e-16) and the final rounding
+    d = np.abs(Bg - Bo)
+    assert np.all(d.real <= 2 * np.spacing(np.abs(Bo.real)) + 2.3e-16), d.real.max()
+    assert np.all(d.imag <= 2 * np.spacing(np.abs(Bo.imag)) + 2.3e-16), d.imag.max()
     assert np.array_equal(Bg, Bg.T)
     assert abs(K.log_norm - orc.log_norm(r)) <= 1e-13 * abs(orc.log_norm(r))
 
@@ -263,31 +309,48 @@ def test_prob_pair_sum_budget_overflow(gbs, orc):
     assert np.all(np.isfinite(p)) and np.all(p > 0)
 
 
-def test_prob_batched_n16_sampled(gbs, orc):
-    """The benchmark's workload and launch (M = 64, 4096 patterns, n = 16): the
-    whole batch runs on the GPU; 48 patterns spread over it are checked."""
-    U, r, pats = W.workload("batched_m64_n16")
+def golden_batch_check(gbs, name):
+    """A whole workload batch in both precisions, as the benchmark launches it
+    (device index lists), against stored oracle values for every pattern:
+    FP64 within 1e-10 and within its own error estimate; the mixed path within
+    its stated bound, whose kappa is first pinned to the oracle's kappa of the
+    same pairing (the library pairs positions (t, t + n/2) and zeroes the
+    diagonal below n = 26, as the stored kappa does)."""
+    U, r, pats = W.workload(name)
+    g = golden(name + "_oracle.json")
+    check_draw(U, g)
+    assert [list(map(int, x)) for x in pats] == g["x"]
     K = kernel_for(gbs, U, r)
-    p, lp, hf, er = run_prob(gbs, K, pats, 0)
-    sample = list(range(0, 4096, 4096 // 48))[:48] + [4095]
-    ref = orc.prob(U, r, [pats[i] for i in sample])
-    assert np.all(rel(hf[sample], ref["haf"]) <= FP64_TOL)
-    assert np.all(rel(p[sample], ref["p"]) <= FP64_TOL)
-    assert np.all(np.isfinite(p)) and np.all(p > 0)
-
-
-def test_prob_mixed_collisions(gbs, orc):
-    """M = 144, n in {8..24}, up to 3 photons per mode: FP64 within 1e-10, mixed
-    within its own err_est, on a sample of the 2048-pattern batch."""
-    U, r, pats = W.workload("mixed_m144")
-    K = kernel_for(gbs, U, r)
-    p64, _, h64, e64 = run_prob(gbs, K, pats, 0)
+    check_B(K, g)
+    nn = np.array([len(x) for x in pats])
+    p64, lp64, h64, e64 = run_prob(gbs, K, pats, 0)
+    err = rel(h64, g["haf"])
+    assert np.all(err <= FP64_TOL), (err.max(), int(np.argmax(err)))
+    assert np.all(err <= e64), int(np.argmax(err / e64))
+    assert np.all(np.abs(lp64 - g["logp"]) <= FP64_TOL * np.abs(g["logp"]))
+    assert np.all(rel(p64, np.exp(g["logp"])) <= FP64_TOL)
+    # FP64 kappa (subset route; no pattern here is bunched enough for the
+    # repeated-row route) against the oracle's
+    k64 = e64 / (nn * 2.0 ** -53)
+    assert np.all(kappa_pin(k64, g["kappa"])), np.min(k64 / g["kappa"])
     p32, _, h32, e32 = run_prob(gbs, K, pats, 1)
-    sample = list(range(0, 2048, 2048 // 40))
-    ref = orc.prob(U, r, [pats[i] for i in sample])
-    assert np.all(rel(h64[sample], ref["haf"]) <= FP64_TOL)
-    assert np.all(rel(h32[sample], ref["haf"]) <= e32[sample])
-    assert np.all(np.isfinite(e64)) and np.all(e64 >= 0)
+    k32 = e32 / (nn * 2.0 ** -24)
+    assert np.all(kappa_pin(k32, g["kappa"], slack=1e-3)), (np.min(k32 / g["kappa"]), np.max(k32 / g["kappa"]))
+    err32 = rel(h32, g["haf"])
+    assert np.all(err32 <= e32), (err32 / e32).max()
+    return err, err32, e32
+
+
+def test_prob_batched_n16_all_patterns_golden(gbs):
+    """The benchmark's workload and launch (M = 64, 4096 patterns, n = 16): every
+    result against the stored oracle values."""
+    golden_batch_check(gbs, "batched_m64_n16")
+
+
+def test_prob_mixed_collisions(gbs):
+    """M = 144, n in {8..24}, up to 3 photons per mode (collisions, Eq.
+    W_s_example): all 2048 results against the stored oracle values."""
+    golden_batch_check(gbs, "mixed_m144")
 
 
 @pytest.mark.slow
@@ -312,6 +375,7 @@ def test_prob_large_all_patterns_golden(gbs):
 
     g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "large_m900_oracle.json")))
     U, r, pats = W.workload("large_m900")
+    check_draw(U, g)
     assert [list(map(int, x)) for x in pats] == [q["x"] for q in g["patterns"]]
     K = kernel_for(gbs, U, r)
     B = torch.zeros(2 * 900 * 900, dtype=torch.float64, device="cuda")
@@ -329,6 +393,7 @@ def test_prob_large_all_patterns_golden(gbs):
         print("n=%d: %d patterns, max rel. error %.2e, median %.2e, largest estimate %.2e, within estimate: %s"
               % (n_, e_.size, e_.max(), np.median(e_), er[nn == n_].max(), bool(np.all(e_ <= er[nn == n_]))))
     assert np.all(err <= FP64_TOL), (err.max(), int(np.argmax(err)))
+    assert np.all(err <= er), (err / er).max()
     assert np.all(np.abs(lp - np.array([q["logp"] for q in g["patterns"]])) <= 1e-9)
 
 
@@ -354,10 +419,11 @@ def bunched_patterns(m, n_values, per_n, seed):
 
 
 def test_prob_repeated_row_route(gbs, orc):
-    """Host index lists with many repeated modes take the repeated-row route
-    (terms of the moment-extraction identity) when it is cheaper than the
-    subset sum; device index lists and explicit matrices take the subset sum.
-    All three agree with the double-double oracle within 1e-10."""
+    """Index lists with many repeated modes take the repeated-row route (terms
+    of the moment-extraction identity) when it is cheaper than the subset sum:
+    chosen on the host for host lists and on the device for device lists, with
+    bit-identical results; explicit matrices take the subset sum. All agree
+    with the double-double oracle within 1e-10."""
     m = 8
     U = W.haar_unitary(m, 5)
     r = np.full(m, 1.0)
@@ -369,6 +435,9 @@ def test_prob_repeated_row_route(gbs, orc):
     assert np.all(rel(hf_h, ref["haf"]) <= FP64_TOL), rel(hf_h, ref["haf"])
     assert np.all(rel(p_h, ref["p"]) <= FP64_TOL)
     assert np.all(rel(hf_d, ref["haf"]) <= FP64_TOL), rel(hf_d, ref["haf"])
+    # the same route on both sides (the planner's item split of subset-sum
+    # patterns may differ, which changes only the rounding)
+    assert np.all(rel(hf_d, hf_h) <= 1e-12) and np.all(np.abs(er_d - er_h) <= 1e-6 * er_h)
     assert np.all(np.abs(lp_h - lp_d) <= 1e-9)
     B = torch.zeros(2 * m * m, dtype=torch.float64, device="cuda")
     K.copy_B(B)
@@ -380,9 +449,10 @@ def test_prob_repeated_row_route(gbs, orc):
 
 
 def test_repeated_row_route_extreme_bunching(gbs, orc):
-    """32 photons in 2 modes (289 terms): the repeated-row route against the
-    oracle's repeated-row formula, and much faster than the subset sum that a
-    device index list takes for the same pattern (2^16 subsets of order <= 32)."""
+    """32 photons in 2 modes (289 terms): the repeated-row route, from a host
+    or a device index list, against the oracle's repeated-row formula, and much
+    faster than the subset sum that the explicit matrix takes (2^16 subsets of
+    order <= 32)."""
     import time
 
     m = 6
@@ -398,30 +468,71 @@ def test_repeated_row_route_extreme_bunching(gbs, orc):
     assert rel(hf_h, np.array([ref]))[0] <= FP64_TOL, (hf_h, ref)
     assert rel(hf_d, np.array([ref]))[0] <= FP64_TOL, (hf_d, ref)
 
-    def best(host, reps=3):
+    Bg = torch.zeros(2 * m * m, dtype=torch.float64, device="cuda")
+    K.copy_B(Bg)
+    Bc = Bg.cpu().numpy().view(np.complex128).reshape(m, m)
+    flat, n, offs = gbs.pack_matrices([Bc[np.ix_(x, x)]])
+    Ad = dev(flat)
+    hm = torch.zeros(2, dtype=torch.float64, device="cuda")
+
+    def best(fn, reps=3):
         ts = []
         for _ in range(reps):
             t0 = time.perf_counter()
-            run_prob(gbs, K, [x], 0, host=host)
+            fn()
+            torch.cuda.synchronize()
             ts.append(time.perf_counter() - t0)
         return min(ts)
 
-    assert best(True) * 3 < best(False)
+    t_rep = best(lambda: run_prob(gbs, K, [x], 0))
+    t_sub = best(lambda: gbs.hafnian_batch(Ad, n, offs, gbs.FP64, haf_out=hm))
+    assert t_rep * 3 < t_sub, (t_rep, t_sub)
 
 
 def test_prob_mixed_bound_large_golden(gbs):
-    """The mixed path's stated per-result bound holds on the n = 28, 30 instances."""
+    """The mixed path's stated per-result bound holds on the n = 28, 30 instances.
+    The kappa behind it is pinned first: the no-allocation entry point keeps
+    the default pairing (positions t and t + n/2), for which the oracle's kappa
+    is stored (tests/golden/large_m900_default_order.json), in both precisions;
+    the batched call then runs the mixed path in its chosen ordering."""
+    U, r, pats = W.workload("large_m900")
+    K = kernel_for(gbs, U, r)
+    gd = golden("large_m900_default_order.json")
+    check_draw(U, gd)
+    Bc = check_B(K, gd)
+    sel = gd["pattern_index"]
+    xs = [pats[i] for i in sel]
+    assert [list(map(int, x)) for x in xs] == gd["x"]
+    nn = np.array([len(x) for x in xs])
+    for prec, slack in ((0, 0.0), (1, 1e-3)):
+        hc = np.zeros(len(xs), complex)
+        kc = np.zeros(len(xs))
+        for q, x in enumerate(xs):  # one matrix per call: within the entry point's item limit
+            flat, n, offs = gbs.pack_matrices([Bc[np.ix_(x, x)]])
+            h = torch.zeros(2, dtype=torch.float64, device="cuda")
+            k = torch.zeros(1, dtype=torch.float64, device="cuda")
+            gbs.hafnian_batch_noalloc(dev(flat), n, offs, prec, haf_out=h, kappa_out=k)
+            torch.cuda.synchronize()
+            hh = h.cpu().numpy()
+            hc[q] = complex(hh[0], hh[1])
+            kc[q] = k.cpu().numpy()[0]
+        assert np.all(kappa_pin(kc, gd["kappa"], slack)), (prec, kc / gd["kappa"])
+        bound = nn * (2.0 ** -53 if prec == 0 else 2.0 ** -24) * kc
+        assert np.all(rel(hc, gd["haf"]) <= bound), (prec, rel(hc, gd["haf"]) / bound)
+    g = golden_large()
+    sel = [0, 1, 2, 64, 65]
+    p, lp, hf, er = run_prob(gbs, K, [pats[i] for i in sel], 1)
+    assert np.all(rel(hf, g[sel]) <= er), (rel(hf, g[sel]), er)
+
+
+def golden_large():
+    """Hafnians of the 80 large instances (tests/golden/large_m900_oracle.json)."""
     import json
     import os
 
     g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "large_m900_oracle.json")))
-    U, r, pats = W.workload("large_m900")
-    K = kernel_for(gbs, U, r)
-    sel = [0, 1, 2, 64, 65]
-    p, lp, hf, er = run_prob(gbs, K, [pats[i] for i in sel], 1)
-    ref = np.array([complex(g["patterns"][i]["haf_dd"][0] + g["patterns"][i]["haf_dd"][1],
-                            g["patterns"][i]["haf_dd"][2] + g["patterns"][i]["haf_dd"][3]) for i in sel])
-    assert np.all(rel(hf, ref) <= er), (rel(hf, ref), er)
+    return np.array([complex(q["haf_dd"][0] + q["haf_dd"][1], q["haf_dd"][2] + q["haf_dd"][3])
+                     for q in g["patterns"]])
 
 
 # --- edge cases -------------------------------------------------------------------
@@ -521,6 +632,28 @@ def test_pairing_choice_lowers_cancellation(gbs):
     assert np.exp(np.mean(np.log(ratio))) < 0.8, ratio
 
 
+def test_prob_bunched_batch_device_index_list(gbs, orc):
+    """The bunched workload (M = 8, r = 1, 512 patterns of n = 24 drawn with
+    replacement, the collision case of Eq. W_s_example) as one batch from a
+    device index list: the route choice on the device sends these patterns to
+    the repeated-row sum, bit-identical to the host list's route; the patterns
+    with the largest error estimates and a spread of others are within 1e-10
+    of the double-double oracle and within their estimates."""
+    U, r, pats = W.workload("bunched_m8")
+    K = kernel_for(gbs, U, r)
+    p_d, lp_d, hf_d, er_d = run_prob(gbs, K, pats, 0)
+    p_h, lp_h, hf_h, er_h = run_prob(gbs, K, pats, 0, host=True)
+    assert np.array_equal(hf_d, hf_h) and np.array_equal(er_d, er_h)
+    assert np.array_equal(p_d, p_h)
+    worst = list(np.argsort(er_d)[-6:])
+    sample = sorted(set(worst + list(range(0, 512, 128))))
+    ref = orc.prob(U, r, [pats[i] for i in sample])
+    err = rel(hf_d[sample], ref["haf"])
+    assert np.all(err <= FP64_TOL), (err, er_d[sample])
+    assert np.all(err <= er_d[sample]), (err, er_d[sample])
+    assert np.all(rel(p_d[sample], ref["p"]) <= FP64_TOL)
+
+
 def test_repeated_row_route_largest_orders(gbs, orc):
     """n = 30 and 32 through the repeated-row route: all photons in one mode
     (Haf = B_vv^16 (31)!!, the closed form of J_32 scaled) and photons spread
@@ -560,3 +693,28 @@ def test_whole_matrix_items_match_per_size_items(gbs, precision):
         _, _, hs, es = run_prob(gbs, K, [pats[i]], precision)
         tol = 1e-11 if precision == 0 else max(eb[i], es[0])
         assert rel(hb[i:i + 1], hs)[0] <= tol, (i, hb[i], hs[0], tol)
+
+
+@pytest.mark.parametrize("n_", [16, 28])
+def test_autotune_shape_fits_and_agrees(gbs, n_):
+    """gbs_autotune times its candidate launch shapes for one photon number and
+    keeps the fastest: a batch then runs in the tuned shape (so it fits) and
+    gives the same Hafnians as before tuning within 1e-10, both within 1e-10
+    of the stored oracle values."""
+    if n_ == 16:
+        U, r, pats = W.workload("batched_m64_n16")
+        ref = golden("batched_m64_n16_oracle.json")["haf"]
+        sel = list(range(0, 4096, 16))
+    else:
+        U, r, pats = W.workload("large_m900")
+        ref = golden_large()
+        sel = list(range(8))
+    K = kernel_for(gbs, U, r)
+    xs = [pats[i] for i in sel]
+    _, _, before, _ = run_prob(gbs, K, xs, 0)
+    chosen = gbs.autotune(n_, gbs.FP64)
+    assert chosen in (1, 2, 4, 8, 16)
+    _, _, after, er = run_prob(gbs, K, xs, 0)
+    assert np.all(rel(after, before) <= FP64_TOL)
+    assert np.all(rel(after, ref[sel]) <= FP64_TOL) and np.all(rel(before, ref[sel]) <= FP64_TOL)
+    assert np.all(rel(after, ref[sel]) <= er)

@@ -216,3 +216,194 @@ def test_serving_bunched_requests(gbs, orc):
     for (p, hf, e), rp, rh in zip(res, ref["p"], ref["haf"]):
         assert abs(hf - rh) <= FP64_TOL * abs(rh), (hf, rh, e)
         assert abs(p - rp) <= FP64_TOL * rp
+
+
+def u_hash(U):
+    import hashlib
+
+    return hashlib.sha256(np.ascontiguousarray(U, dtype=np.complex128).tobytes()).hexdigest()
+
+
+def golden(name):
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        g = json.load(f)
+    g["haf"] = np.array(g["haf_re"]) + 1j * np.array(g["haf_im"])
+    g["kappa"] = np.array(g["kappa"])
+    return g
+
+
+def test_serving_stream_n22_26_against_oracle(gbs):
+    """The serving workload's own interferometer (M = 256, r = 0.88) and its
+    requests of n = 22, 24, 26 (the top of its range): FP64 results within 1e-10
+    of stored double-double oracle values and within their estimates; mixed
+    results within their stated bound, whose kappa is pinned to the oracle's
+    kappa of the same pairing for n < 26 (n = 26 takes the probe's ordering)."""
+    U, r, _ = W.workload("serving_m256")
+    g = golden("serving_m256_oracle.json")
+    assert u_hash(U) == g["U_sha256"], "Haar draw differs from the stored values' draw: regenerate tests/golden"
+    pats = [np.array(x, np.int32) for x in g["x"]]
+    nn = np.array([len(x) for x in pats])
+    K = gbs.build_kernel(U, r)
+    srv = gbs.Server(K, max_n=26)
+    try:
+        r64 = wait_all(srv, [srv.submit(x, gbs.FP64) for x in pats])
+        r32 = wait_all(srv, [srv.submit(x, gbs.MIXED) for x in pats])
+        st = srv.stats()
+    finally:
+        srv.destroy()
+    assert st["probed"] == 2 * int(np.sum(nn >= 26))
+    h64 = np.array([x[1] for x in r64])
+    e64 = np.array([x[2] for x in r64])
+    err = np.abs(h64 - g["haf"]) / np.abs(g["haf"])
+    assert np.all(err <= FP64_TOL), (err.max(), nn[np.argmax(err)])
+    assert np.all(err <= e64)
+    h32 = np.array([x[1] for x in r32])
+    e32 = np.array([x[2] for x in r32])
+    assert np.all(np.abs(h32 - g["haf"]) <= e32 * np.abs(g["haf"]))
+    small = nn < 26
+    for e, u, slack in ((e64, 2.0 ** -53, 0.0), (e32, 2.0 ** -24, 1e-3)):
+        k = e[small] / (nn[small] * u)
+        kr = g["kappa"][small]
+        assert np.all((k >= kr * (1 - 1e-6 - slack)) & (k <= np.sqrt(2) * kr * (1 + 1e-6 + slack)))
+
+
+def test_serving_large_n28_n30_against_oracle(gbs):
+    """All 80 large instances (M = 900, r = 1, n = 28 and 30) as serving
+    requests: each waits for the ordering probe, then runs in the steps; FP64
+    results within 1e-10 of the stored oracle values and within their
+    estimates, and a request's result is the same alone as in the stream."""
+    import json
+    import os
+
+    U, r, pats = W.workload("large_m900")
+    gl = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "large_m900_oracle.json")))
+    assert u_hash(U) == gl["U_sha256"], "Haar draw differs from the stored values' draw: regenerate tests/golden"
+    ref = np.array([complex(q["haf_dd"][0] + q["haf_dd"][1], q["haf_dd"][2] + q["haf_dd"][3])
+                    for q in gl["patterns"]])
+    K = gbs.build_kernel(U, r)
+    srv = gbs.Server(K, max_n=30, mem_budget=512 << 20)
+    try:
+        alone = wait_all(srv, [srv.submit(pats[5])])[0]
+        res = wait_all(srv, [srv.submit(x) for x in pats], timeout=300.0)
+        st = srv.stats()
+    finally:
+        srv.destroy()
+    assert st["probed"] == 81
+    h = np.array([x[1] for x in res])
+    e = np.array([x[2] for x in res])
+    err = np.abs(h - ref) / np.abs(ref)
+    assert np.all(err <= FP64_TOL), (err.max(), int(np.argmax(err)))
+    assert np.all(err <= e)
+    assert res[5][1] == alone[1] and res[5][0] == alone[0]
+
+
+def test_serving_wait_timeout(gbs, kern):
+    """A bounded wait that runs out: with a wait limit far below a step's
+    duration, the server gives up on the step, fails the outstanding requests
+    with GBS_ETIMEDOUT and stops (the GPU work itself finishes normally and is
+    waited for when the server is destroyed)."""
+    K, m = kern
+    srv = gbs.Server(K, wait_timeout_s=1e-6, subsets_per_step=256)
+    try:
+        tickets = []
+        for s in range(8):
+            try:
+                tickets.append(srv.submit(np.sort(np.random.default_rng(s).choice(m, 24, replace=False))
+                                          .astype(np.int32)))
+            except gbs.GbsError as ex:  # the server may already have given up on its first step
+                assert ex.code == -5, ex
+                break
+        assert tickets
+        codes = []
+        t0 = time.time()
+        for t in tickets:
+            while True:
+                try:
+                    r = srv.poll(t)
+                except gbs.GbsError as ex:
+                    codes.append(ex.code)
+                    break
+                assert r is None, "a step finished within a microsecond"
+                assert time.time() - t0 < 30
+        assert codes and all(c == -5 for c in codes), codes
+        with pytest.raises(gbs.GbsError) as ei:
+            srv.submit(np.arange(4, dtype=np.int32))  # the server has stopped
+        assert ei.value.code == -5
+    finally:
+        with pytest.raises(gbs.GbsError) as ei:
+            srv.destroy()  # reports why it had stopped
+    assert ei.value.code == -5
+
+
+def test_serving_cancel(gbs, kern):
+    """Requests cancelled while queued or resident poll GBS_ECANCELED; the rest
+    complete with the batched path's results; the server's memory is returned
+    (a later request still runs)."""
+    K, m = kern
+    pats = requests(m, 60, 21, n_values=range(14, 23, 2))
+    srv = gbs.Server(K, max_slots=8, subsets_per_step=64)
+    try:
+        tickets = [srv.submit(x) for x in pats]
+        cancel = set(range(0, 60, 3))
+        outcome = {i: srv.cancel(tickets[i]) for i in sorted(cancel)}
+        assert all(v in (0, 1) for v in outcome.values()) and sum(v == 0 for v in outcome.values()) >= 10
+        keep = [i for i in range(60) if i not in cancel or outcome[i] == 1]
+        res = wait_all(srv, [tickets[i] for i in keep])
+        for i in cancel:
+            if outcome[i] == 0:
+                with pytest.raises(gbs.GbsError) as ei:
+                    srv.poll(tickets[i])
+                assert ei.value.code == -8
+        with pytest.raises(gbs.GbsError) as ei:
+            srv.cancel(tickets[keep[0]])  # collected
+        assert ei.value.code == -7
+        after = wait_all(srv, [srv.submit(pats[1])])[0]
+        st = srv.stats()
+    finally:
+        srv.destroy()
+    assert st["cancelled"] == sum(v == 0 for v in outcome.values())
+    p_ref, h_ref = batch_ref(gbs, K, [pats[i] for i in keep], gbs.FP64)
+    for (p, h, e), pr, hr in zip(res, p_ref, h_ref):
+        assert abs(h - hr) <= FP64_TOL * abs(hr)
+    assert abs(after[1] - batch_ref(gbs, K, [pats[1]], gbs.FP64)[1][0]) <= FP64_TOL * abs(after[1])
+
+
+def test_serving_memory_budget_failures(gbs, kern):
+    """Admission by memory: a request whose partial sums exceed the whole memory
+    budget fails with GBS_ENOMEM instead of waiting forever; injected
+    allocation failures make requests wait and then complete; requests that
+    fit run normally."""
+    K, m = kern
+    probe = gbs.Server(K, max_slots=8, max_n=30)
+    try:
+        cap = probe.stats()["arena_slots"]
+    finally:
+        probe.destroy()
+    budget0 = 64 << 20
+    overhead = budget0 - 64 * cap  # tables and step buffers (64-byte partial sums)
+    srv = gbs.Server(K, max_slots=8, max_n=30, mem_budget=overhead + 64 * 1100, fault_alloc_failures=5)
+    try:
+        assert srv.stats()["arena_slots"] < 1200
+        small = [np.sort(np.random.default_rng(s).choice(m, 12, replace=False)).astype(np.int32) for s in range(6)]
+        huge = np.sort(np.random.default_rng(99).choice(m, 30, replace=False)).astype(np.int32)
+        t_small = [srv.submit(x) for x in small]
+        t_huge = srv.submit(huge)
+        res = wait_all(srv, t_small)
+        t0 = time.time()
+        while True:
+            try:
+                assert srv.poll(t_huge) is None
+            except gbs.GbsError as ex:
+                assert ex.code == -2
+                break
+            assert time.time() - t0 < 30
+        st = srv.stats()
+    finally:
+        srv.destroy()
+    assert st["alloc_waits"] >= 5
+    _, h_ref = batch_ref(gbs, K, small, gbs.FP64)
+    for (p, h, e), hr in zip(res, h_ref):
+        assert abs(h - hr) <= FP64_TOL * abs(hr)
