@@ -966,10 +966,9 @@ __global__ void __launch_bounds__(kFinWarps * 32) finalize_kernel(const Finalize
         const double L = F.log_norm ? *F.log_norm : 0.0;
         const double lf = log(sv[5][lane]);  // sum_j log s_j!
         const double logp = (mod > 0.0) ? 2.0 * log(mod) - lf - L : -INFINITY;
-        const double u = (F.precision == GBS_FP64) ? 0x1p-53 : 0x1p-24;
         if (F.p_out) F.p_out[bo] = bad ? nan : ((mod > 0.0) ? exp(logp) : 0.0);
         if (F.logp_out) F.logp_out[bo] = bad ? nan : logp;
-        if (F.err_out) F.err_out[bo] = bad ? nan : (double)(n > 0 ? n : 1) * u * kappa;
+        if (F.err_out) F.err_out[bo] = bad ? nan : err_estimate(F.precision, n, kappa);
       }
     }
     __syncthreads();

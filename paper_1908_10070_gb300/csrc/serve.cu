@@ -674,7 +674,7 @@ void complete(gbs_server* s, Stage& g) {
     r.hr = g.h_res[2 * S + 2 * b];
     r.hi = g.h_res[2 * S + 2 * b + 1];
     const double kappa = g.h_res[4 * S + b];
-    r.err = (double)sl.n * (sl.prec == GBS_FP64 ? 0x1p-53 : 0x1p-24) * kappa;
+    r.err = err_estimate(sl.prec, sl.n, kappa);
     s->done[sl.ticket] = r;
     s->pending.erase(sl.ticket);
     s->arena.release(sl.part_base, (int)sl.items.size());

@@ -264,8 +264,8 @@ def test_serving_stream_n22_26_against_oracle(gbs):
     e32 = np.array([x[2] for x in r32])
     assert np.all(np.abs(h32 - g["haf"]) <= e32 * np.abs(g["haf"]))
     small = nn < 26
-    for e, u, slack in ((e64, 2.0 ** -53, 0.0), (e32, 2.0 ** -24, 1e-3)):
-        k = e[small] / (nn[small] * u)
+    for e, c, slack in ((e64, nn * 2.0 ** -53, 0.0), (e32, np.minimum(nn, 4) * 2.0 ** -24, 1e-3)):
+        k = e[small] / c[small]
         kr = g["kappa"][small]
         assert np.all((k >= kr * (1 - 1e-6 - slack)) & (k <= np.sqrt(2) * kr * (1 + 1e-6 + slack)))
 
