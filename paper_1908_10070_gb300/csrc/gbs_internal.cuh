@@ -107,8 +107,14 @@ __host__ __device__ inline int64_t pair_terms_elems(int n) {
 // Per-warp staging of finished subsets' power traces (32 slots of stage_h
 // complex doubles plus 32 sign flags; the FP32 path's traces are staged in
 // double too); the exponential series then runs in FP64 with one subset per
-// lane.
-__host__ __device__ inline int stage_bytes(int stage_h) { return (32 * stage_h * 16 + 32 * 4 + 15) & ~15; }
+// lane. Slots are stage_stride(stage_h) entries apart, an odd number of
+// 16-byte entries, so that the eight lanes of a quarter-warp reading entry k of
+// their own slots touch eight different bank groups (at an even stride such as
+// 8 entries they all hit the same four banks).
+__host__ __device__ inline int stage_stride(int stage_h) { return stage_h | 1; }
+__host__ __device__ inline int stage_bytes(int stage_h) {
+  return (32 * stage_stride(stage_h) * 16 + 32 * 4 + 15) & ~15;
+}
 
 // Lane-group size L (a power of two) for subsets of order N of a matrix of
 // order 2h: the smallest L whose 32/L groups fit the warp's bytes left after

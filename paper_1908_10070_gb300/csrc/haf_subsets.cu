@@ -517,7 +517,8 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
   int* xs = reinterpret_cast<int*>(wbase);
   // staging: the power traces of up to 32 finished subsets, their signs and orders
   double2* stP = reinterpret_cast<double2*>(wbase + kWarpHeaderBytes);
-  int* stF = reinterpret_cast<int*>(stP + 32 * P.stage_h);
+  const int sts = stage_stride(P.stage_h);  // entries between two subsets' slots
+  int* stF = reinterpret_cast<int*>(stP + 32 * sts);
   unsigned char* gbase = wbase + kWarpHeaderBytes + stage_bytes(P.stage_h);
   const double2* src2 = reinterpret_cast<const double2*>(P.src);
 
@@ -599,53 +600,46 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
     // compensated accumulation
     auto flush = [&]() {
       if (lane < staged) {
-        double2* pq = stP + lane * P.stage_h;
+        double2* pq = stP + lane * sts;
         const int sv = stF[lane];
         const int Nl = sv < 0 ? -sv : sv;  // the subset's order N
+        // the loops run exact trip counts (not unrolled to the largest
+        // order): terms past h or N would be issued predicated off and still
+        // hold the FP64 pipe, whose warp instructions occupy it for many
+        // cycles on this part
+        double2 dk[kMaxH];  // d_1..d_N, then e_1..e_{h-1}
         if (Nl > 0 && Nl < h) {
           // an order-N subset has traces 1..N only: det(I - xM) = sum_i d_i x^i
           // has degree N, so by Newton's identities d_k = -(1/k) sum_{i<=k}
           // d_{k-i} p_i (d_0 = 1) and, for k > N, p_k = -sum_{i<=N} d_i p_{k-i}
-          double2 dk[kMaxH];  // d_1..d_{kMaxH-1}
-#pragma unroll
-          for (int k = 1; k < kMaxH; ++k) {
-            double2 a = mk<double>(0.0, 0.0);
-            if (k <= Nl) {
-              a = pq[k - 1];
-#pragma unroll
-              for (int i = 1; i < k; ++i) a = cfma<double>(dk[i], pq[k - i - 1], a);
-              const double c = -2.0 * tab.inv2k[k];
-              a.x *= c;
-              a.y *= c;
-            }
-            dk[k] = a;
+#pragma unroll 1
+          for (int k = 1; k <= Nl; ++k) {
+            double2 a = pq[k - 1];
+#pragma unroll 1
+            for (int i = 1; i < k; ++i) a = cfma<double>(dk[i], pq[k - i - 1], a);
+            const double c = -2.0 * tab.inv2k[k];
+            dk[k] = mk<double>(a.x * c, a.y * c);
           }
+#pragma unroll 1
           for (int k = Nl + 1; k <= h; ++k) {
             double2 a = mk<double>(0.0, 0.0);
-#pragma unroll
-            for (int i = 1; i < kMaxH; ++i)
-              if (i <= Nl) a = cfma<double>(dk[i], pq[k - i - 1], a);
+#pragma unroll 1
+            for (int i = 1; i <= Nl; ++i) a = cfma<double>(dk[i], pq[k - i - 1], a);
             pq[k - 1] = mk<double>(-a.x, -a.y);
           }
         }
-        double2 e[kMaxH + 1];
-        e[0] = mk<double>(1.0, 0.0);
-#pragma unroll
-        for (int k = 1; k <= kMaxH; ++k) {
-          double2 a = mk<double>(0.0, 0.0);
-          if (k <= h) {
-#pragma unroll
-            for (int j = 1; j <= k; ++j) a = cfma<double>(pq[j - 1], e[k - j], a);
-            const double c = tab.inv2k[k];
-            a.x *= c;
-            a.y *= c;
-          }
-          e[k] = a;
+        // e_k = (1/(2k)) (p_k e_0 + sum_{j<k} p_j e_{k-j}), e_0 = 1; f = e_h
+        double2* e = dk;  // the d_k are no longer needed
+        double2 f = mk<double>(1.0, 0.0);
+#pragma unroll 1
+        for (int k = 1; k <= h; ++k) {
+          double2 a = pq[k - 1];
+#pragma unroll 1
+          for (int j = 1; j < k; ++j) a = cfma<double>(pq[j - 1], e[k - j], a);
+          const double c = tab.inv2k[k];
+          f = mk<double>(a.x * c, a.y * c);
+          if (k < h) e[k] = f;
         }
-        double2 f = e[1];
-#pragma unroll
-        for (int k = 2; k <= kMaxH; ++k)
-          if (k == h) f = e[k];
         const int sg = sv;
         if (sg != 0) {
           comp_add<double>(acc_re, sg > 0 ? f.x : -f.x);
@@ -731,7 +725,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
       //    time (one waits in registers for the next)
       C pend_v = mk<T>(T(0), T(0));
       int pend_k = 0;  // 0: none waiting
-      double2* const strow = stP + (staged + g) * P.stage_h;
+      double2* const strow = stP + (staged + g) * sts;
       for (int o = 0; o < kMaxOps; ++o) {
         const SchedOp op = c_sched[hs][o];
         if (op.kind == kEnd) break;
