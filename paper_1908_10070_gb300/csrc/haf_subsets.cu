@@ -367,58 +367,43 @@ __device__ __forceinline__ float2 pair_dot(const float4* __restrict__ ra, const 
   return acc;
 }
 
+// C = Ra X Rb in 2 x 2 register blocks: block (r, c), r <= c, of the
+// (N/2) x (N/2) grid of 2 x 2 blocks holds rows 2r, 2r+1 and columns 2c, 2c+1;
+// per chunk t the lane loads four float4 (two rows of each operand) for 32
+// FMAs. (One output per row pair would take two 16-byte loads per 8 FMAs,
+// which shared-memory bandwidth, not the FP32 pipe, would bound.) Each output
+// adds its t terms in increasing order; a diagonal block stores its
+// (2r+1, 2r) entry from (2r, 2r+1), which keeps C exactly symmetric.
 __device__ __forceinline__ void sym_prod_full(float2* __restrict__ dst, const float2* __restrict__ Ra,
                                               const float2* __restrict__ Rb, int N, int l, int L) {
-  const int P = N * (N + 1) / 2;
-  const int half = N >> 1;
-  int i1 = 0, j1 = l;
-  tri_advance(i1, j1, 0, N);
-  for (int e = l; e < P; e += 2 * L) {
-    if (e - l + L >= P) {  // last pass without second entries (warp-uniform)
-      const float4* a1 = reinterpret_cast<const float4*>(Ra + i1 * N);
-      const float4* b1 = reinterpret_cast<const float4*>(Rb + j1 * N);
-      float2 c1 = make_float2(0.f, 0.f);
-      for (int t = 0; t < half; ++t) {
-        const float4 x1 = a1[t], y1 = b1[t];
-        c1.x = fmaf(x1.x, y1.z, c1.x); c1.x = fmaf(-x1.y, y1.w, c1.x);
-        c1.y = fmaf(x1.x, y1.w, c1.y); c1.y = fmaf(x1.y, y1.z, c1.y);
-        c1.x = fmaf(x1.z, y1.x, c1.x); c1.x = fmaf(-x1.w, y1.y, c1.x);
-        c1.y = fmaf(x1.z, y1.y, c1.y); c1.y = fmaf(x1.w, y1.x, c1.y);
-      }
-      dst[i1 * N + j1] = c1;
-      dst[j1 * N + i1] = c1;
-      break;
-    }
-    int i2 = i1, j2 = j1;
-    tri_advance(i2, j2, L, N);
-    const bool two = (e + L < P);
-    if (!two) {
-      i2 = i1;
-      j2 = j1;
-    }
-    const float4* a1 = reinterpret_cast<const float4*>(Ra + i1 * N);
-    const float4* b1 = reinterpret_cast<const float4*>(Rb + j1 * N);
-    const float4* a2 = reinterpret_cast<const float4*>(Ra + i2 * N);
-    const float4* b2 = reinterpret_cast<const float4*>(Rb + j2 * N);
-    float2 c1 = make_float2(0.f, 0.f), c2 = make_float2(0.f, 0.f);
+  const int half = N >> 1, E = half * (half + 1) / 2;
+  int r = 0, c = l;
+  tri_advance(r, c, 0, half);
+  for (int e = l; e < E; e += L) {
+    const float4* a0 = reinterpret_cast<const float4*>(Ra + 2 * r * N);
+    const float4* a1 = reinterpret_cast<const float4*>(Ra + (2 * r + 1) * N);
+    const float4* b0 = reinterpret_cast<const float4*>(Rb + 2 * c * N);
+    const float4* b1 = reinterpret_cast<const float4*>(Rb + (2 * c + 1) * N);
+    float2 c00 = make_float2(0.f, 0.f), c01 = c00, c10 = c00, c11 = c00;
     for (int t = 0; t < half; ++t) {
-      const float4 x1 = a1[t], y1 = b1[t], x2 = a2[t], y2 = b2[t];
-      c1.x = fmaf(x1.x, y1.z, c1.x); c1.x = fmaf(-x1.y, y1.w, c1.x);
-      c1.y = fmaf(x1.x, y1.w, c1.y); c1.y = fmaf(x1.y, y1.z, c1.y);
-      c2.x = fmaf(x2.x, y2.z, c2.x); c2.x = fmaf(-x2.y, y2.w, c2.x);
-      c2.y = fmaf(x2.x, y2.w, c2.y); c2.y = fmaf(x2.y, y2.z, c2.y);
-      c1.x = fmaf(x1.z, y1.x, c1.x); c1.x = fmaf(-x1.w, y1.y, c1.x);
-      c1.y = fmaf(x1.z, y1.y, c1.y); c1.y = fmaf(x1.w, y1.x, c1.y);
-      c2.x = fmaf(x2.z, y2.x, c2.x); c2.x = fmaf(-x2.w, y2.y, c2.x);
-      c2.y = fmaf(x2.z, y2.y, c2.y); c2.y = fmaf(x2.w, y2.x, c2.y);
+      const float4 x0 = a0[t], x1 = a1[t], y0 = b0[t], y1 = b1[t];
+      c00 = pair_dot(&x0, &y0, 1, c00);
+      c01 = pair_dot(&x0, &y1, 1, c01);
+      c10 = pair_dot(&x1, &y0, 1, c10);
+      c11 = pair_dot(&x1, &y1, 1, c11);
     }
-    dst[i1 * N + j1] = c1;
-    dst[j1 * N + i1] = c1;
-    if (two) {
-      dst[i2 * N + j2] = c2;
-      dst[j2 * N + i2] = c2;
+    const int i0 = 2 * r, j0 = 2 * c;
+    dst[i0 * N + j0] = c00;
+    dst[j0 * N + i0] = c00;
+    dst[i0 * N + j0 + 1] = c01;
+    dst[(j0 + 1) * N + i0] = c01;
+    dst[(i0 + 1) * N + j0 + 1] = c11;
+    dst[(j0 + 1) * N + i0 + 1] = c11;
+    if (r != c) {
+      dst[(i0 + 1) * N + j0] = c10;
+      dst[j0 * N + i0 + 1] = c10;
     }
-    tri_advance(i1, j1, 2 * L, N);
+    tri_advance(r, c, L, half);
   }
 }
 
@@ -602,7 +587,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
       if (lane < staged) {
         double2* pq = stP + lane * sts;
         const int sv = stF[lane];
-        const int Nl = sv < 0 ? -sv : sv;  // the subset's order N
+        const int Nl = sv < 0 ? -sv : sv;  // traces taken directly (the subset's order N when < h)
         // the loops run exact trip counts (not unrolled to the largest
         // order): terms past h or N would be issued predicated off and still
         // hold the FP64 pipe, whose warp instructions occupy it for many
@@ -654,8 +639,11 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
    for (int s = s_first; s <= s_last; ++s) {
     const int N = 2 * s;
     const int NP = (sizeof(T) == 8) ? N * (N + 1) / 2 : N * N;  // entries per matrix
-    // traces taken directly: 1..min(N, h) (those past N follow in the series step)
-    const int hs = N < h ? N : h;
+    // traces taken directly: FP64 1..min(N, h) (those past N follow from
+    // Newton's identities in the series step, which saves products on the
+    // FP64 pipe); FP32 1..h (extra FP32 products are cheaper than the FP64
+    // extension)
+    const int hs = (sizeof(T) == 8 && N < h) ? N : h;
     const int L = lanes_for(N, h, P.warp_bytes, P.stage_h, cb);
     const int G = 32 / L;
     const int g = lane / L, l = lane - g * L;
@@ -768,8 +756,9 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
         const C t = group_sum<T>(pend_v, L);
         if (l == 0) strow[pend_k - 1] = make_double2(t.x, t.y);
       }
-      // sign (-1)^{h-s} times the order N (0: no subset in this slot)
-      if (l == 0) stF[staged + g] = active ? (((h - s) & 1) ? -N : N) : 0;
+      // sign (-1)^{h-s} times the number of traces taken directly (< h: the
+      // series step extends them; 0: no subset in this slot)
+      if (l == 0) stF[staged + g] = active ? (((h - s) & 1) ? -hs : hs) : 0;
       staged += G;
       __syncwarp();
       // -- once 32 subsets are staged, or the item ends
