@@ -70,21 +70,24 @@ __host__ __device__ inline double err_estimate(int precision, int n, double kapp
 // made the signed sum cancel up to ~1e4 times more in measurements.
 __host__ __device__ inline int default_pos(int p, int h) { return (p >> 1) + ((p & 1) ? h : 0); }
 
-// Matrix buffers a lane group keeps for a matrix with h = n/2: the most that
-// the power-trace schedule of h, or of any order N < h that its smaller
-// subsets run (see haf_subsets.cu), holds at once.
-__host__ __device__ inline int sched_nbuf(int h) {
-  return h <= 2 ? 1 : (h <= 4 ? 2 : (h <= 8 ? 3 : (h <= 12 ? 4 : 5)));
-}
+// The row of the power-trace schedule (see haf_subsets.cu) that subsets of
+// order N of a matrix of order 2h run: FP64 takes traces 1..min(N, h) by
+// products (those past N follow from Newton's identities), FP32 all of 1..h.
+__host__ __device__ inline int sched_row(int N, int h, int cbytes) { return (cbytes == 16 && N < h) ? N : h; }
+
+// Matrix buffers schedule row hs holds at once (its largest buffer index plus
+// one; 3 bits per row, rows 0..16: 1 1 1 2 2 3 3 3 3 4 4 3 3 5 5 4 4).
+__host__ __device__ inline int sched_nbuf(int hs) { return (int)((0x496b7236da449ull >> (3 * hs)) & 7u); }
 
 // Shared-memory bytes of one lane group's region for subsets of order N (and
-// half photon number h) with complex elements of `cbytes` bytes: nbuf matrices
-// (FP64: packed upper triangles of N(N+1)/2 entries; FP32: full N x N tiles,
-// whose rows the products read as float4 pairs), N row indices and, for FP64,
-// the N/2 pair numbers of the subset.
+// half photon number h) with complex elements of `cbytes` bytes: the
+// matrices its schedule row holds at once (FP64: packed upper triangles of
+// N(N+1)/2 entries; FP32: full N x N tiles, whose rows the products read as
+// float4 pairs), N row indices and, for FP64, the N/2 pair numbers of the
+// subset.
 __host__ __device__ inline int group_bytes(int N, int h, int cbytes) {
   const int P = (cbytes == 16) ? N * (N + 1) / 2 : N * N;
-  const int bytes = sched_nbuf(h) * P * cbytes + N * 4 + (cbytes == 16 ? N * 2 : 0);
+  const int bytes = sched_nbuf(sched_row(N, h, cbytes)) * P * cbytes + N * 4 + (cbytes == 16 ? N * 2 : 0);
   return (bytes + 15) & ~15;
 }
 

@@ -643,12 +643,12 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
     // Newton's identities in the series step, which saves products on the
     // FP64 pipe); FP32 1..h (extra FP32 products are cheaper than the FP64
     // extension)
-    const int hs = (sizeof(T) == 8 && N < h) ? N : h;
+    const int hs = sched_row(N, h, cb);
     const int L = lanes_for(N, h, P.warp_bytes, P.stage_h, cb);
     const int G = 32 / L;
     const int g = lane / L, l = lane - g * L;
     C* buf = reinterpret_cast<C*>(gbase + (size_t)g * group_bytes(N, h, cb));
-    int* rowidx = reinterpret_cast<int*>(buf + sched_nbuf(h) * NP);
+    int* rowidx = reinterpret_cast<int*>(buf + sched_nbuf(sched_row(N, h, cb)) * NP);
     int* pairs = rowidx + N;  // FP64: the subset's pair numbers, increasing
     const int count = whole ? tab.binom[h][s] : w.count;
     const int rank0 = whole ? 0 : w.rank0;
