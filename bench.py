@@ -663,6 +663,117 @@ def serve_stream(gbs, K, reqs, precision):
             "update_max_ms": 1e3 * st["update_max_s"], "submit_max_ms": 1e3 * st["submit_max_s"]}
 
 
+def serve_load(gbs, K, reqs, precision):
+    """Open-loop Poisson client for the saturation sweep: submits at the
+    scheduled arrival times (a full queue is retried) and collects finished
+    requests through the completion queue (gbs_serve_wait_any), so the client
+    does not poll each ticket. Latency = collection time - scheduled arrival."""
+    srv = gbs.Server(K, max_n=26)
+    try:
+        for _, x in reqs[:64]:
+            srv.submit(x, precision)
+        got = 0
+        while got < 64:
+            got += len(srv.wait_any(0.05)[0])
+        arr = np.array([a for a, _ in reqs])
+        xs = [np.ascontiguousarray(x, dtype=np.int32) for _, x in reqs]
+        lat = np.empty(len(reqs))
+        where = {}
+        i = done = 0
+        gc.collect()
+        gc.disable()
+        t0 = time.perf_counter()
+        while done < len(reqs):
+            now = time.perf_counter() - t0
+            while i < len(reqs) and arr[i] <= now:
+                tk = srv.submit(xs[i], precision)
+                if tk < 0:
+                    break
+                where[tk] = i
+                i += 1
+            wait = 0.0 if i >= len(reqs) else max(0.0, min(arr[i] - now, 0.002))
+            tks = srv.wait_any(wait if i < len(reqs) else 0.002)[0]
+            tnow = time.perf_counter() - t0
+            for tk in tks:
+                lat[done] = tnow - arr[where.pop(int(tk))]
+                done += 1
+        total = time.perf_counter() - t0
+    finally:
+        gc.enable()
+        srv.destroy()
+    return lat, total
+
+
+def saturation_summary(rate, lat, total):
+    lat_ms = lat * 1e3
+    q = len(lat) // 4
+    return {"offered_req_s": rate, "throughput_req_s": len(lat) / total,
+            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+            # latency drift over the run: a queue that grows shows as a rising median
+            "median_first_quarter_ms": float(np.median(lat_ms[:q])),
+            "median_last_quarter_ms": float(np.median(lat_ms[-q:]))}
+
+
+def sustainable(row):
+    """Kept up: 95 % of the offered rate served, and no queue build-up (the
+    last quarter's median latency under twice the first quarter's + 1 ms)."""
+    return (row["throughput_req_s"] >= 0.95 * row["offered_req_s"]
+            and row["median_last_quarter_ms"] <= 2.0 * row["median_first_quarter_ms"] + 1.0)
+
+
+def saturation(gbs, K, dur_s=1.0, max_levels=9):
+    """Rising Poisson rates (x1.5 from 1000 req/s, about dur_s of requests
+    each) until the stream is no longer sustained; the largest sustained rate
+    for the FP64 server, the mixed server and plain per-pattern calls."""
+    out = {"criterion": "served >= 0.95 x offered and last-quarter median latency <= "
+                        "2 x first-quarter median + 1 ms", "levels": {}}
+    for name in ("fp64", "mixed", "per_pattern_fp64"):
+        rows, best = [], None
+        rate = 1000.0
+        for _ in range(max_levels):
+            count = int(rate * dur_s) + 64
+            reqs = W.serving_requests(count, rate_hz=rate)
+            if name == "per_pattern_fp64":
+                lat, total = per_pattern_load(gbs, K, reqs)
+            else:
+                lat, total = serve_load(gbs, K, reqs, gbs.FP64 if name == "fp64" else gbs.MIXED)
+            row = saturation_summary(rate, lat, total)
+            row["sustained"] = sustainable(row)
+            rows.append(row)
+            if not row["sustained"]:
+                break
+            best = row
+            rate *= 1.5
+        out["levels"][name] = rows
+        out[name + "_max_sustained_req_s"] = best["offered_req_s"] if best else None
+        out[name + "_at_max"] = ({"p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"]} if best else None)
+    return out
+
+
+def per_pattern_load(gbs, K, reqs):
+    """per_pattern_stream's client for the sweep: (latencies s, total s)."""
+    p = np.zeros(1)
+    for _, x in reqs[:64]:
+        idx, n, offs = gbs.pack_patterns([x])
+        gbs.prob_batch(K, idx, n, offs, gbs.FP64, p_out=p)
+    lat = np.empty(len(reqs))
+    gc.collect()
+    gc.disable()
+    try:
+        t0 = time.perf_counter()
+        for j, (arr, x) in enumerate(reqs):
+            now = time.perf_counter() - t0
+            if now < arr:
+                time.sleep(arr - now)
+            idx, n, offs = gbs.pack_patterns([x])
+            gbs.prob_batch(K, idx, n, offs, gbs.FP64, p_out=p)
+            lat[j] = time.perf_counter() - t0 - arr
+        total = time.perf_counter() - t0
+    finally:
+        gc.enable()
+    return lat, total
+
+
 def per_pattern_stream(gbs, K, reqs):
     """Plain FP64 per-pattern method: one synchronous gbs_prob_batch call per
     request, in arrival order (host buffers)."""
@@ -698,7 +809,8 @@ def serving(gbs, torch, count: int = 20000):
     out = {"workload": "M=256 Haar U seed 3, r=0.88, Poisson 2000 req/s, n~U{12..26} collision-free",
            "fp64": serve_stream(gbs, K, reqs, gbs.FP64),
            "mixed": serve_stream(gbs, K, reqs, gbs.MIXED),
-           "per_pattern_fp64": per_pattern_stream(gbs, K, reqs[: max(1, count // 4)])}
+           "per_pattern_fp64": per_pattern_stream(gbs, K, reqs[: max(1, count // 4)]),
+           "saturation": saturation(gbs, K)}
     return out
 
 

@@ -157,17 +157,30 @@ int gbs_hafnian_batch_noalloc(const double* A_ri, const int* n, const int64_t* o
  * GBS_FP64 a pattern whose photons are bunched into few modes (at most 16
  * distinct modes, prod_j (s_j + 1) terms costing well under the subset sum)
  * takes the repeated-row sum instead (the moment-extraction identity of Kan,
- * 2008; not in the paper). The choice is made on the host for a host idx and
- * on the device for a device idx, by the same rule and with the same result
- * bits (a device batch reserves repeated-row partial slots for at most 2^20
- * term chunks in all; patterns past that, in batch order, keep the subset
- * sum). On such patterns that route is also the accurate one: the subset sum
+ * 2008; not in the paper). The choice is made on the device (a host idx is
+ * copied there first), so it costs the host nothing and gives the same bits
+ * for host and device lists; a batch reserves repeated-row partial slots for
+ * at most 2^20 term chunks in all (patterns past that, in batch order, keep
+ * the subset sum). On such patterns that route is also the accurate one: the subset sum
  * cancels strongly there (errors up to ~1e-8 measured at n = 24 in 8 modes,
  * flagged by err_est_out).
+ * Kept plans: the host-side plan of a call (work items, per-matrix
+ * descriptors, ordering-probe tables) depends only on n[], offs[], m, the
+ * precision and the launch shape, never on the index lists or matrices, so
+ * the library keeps it in device memory, for up to 8 such shapes and 256 MB in
+ * all (least recently used evicted), and a later call of the same shape on any
+ * stream (this call or gbs_hafnian_batch, host or device inputs) skips the
+ * planning and its upload. gbs_clear_plans frees the kept plans.
  * Errors: GBS_EINVAL, GBS_ERANGE, GBS_ENOMEM, GBS_ECUDA. */
 int gbs_prob_batch(const gbs_kernel* k, const int* idx, const int* n, const int64_t* offs,
                    int batch, int precision, void* stream, double* p_out, double* logp_out,
                    double* haf_ri_out, double* err_est_out);
+
+/* Frees every kept plan that no call is using (see gbs_prob_batch), after the
+ * device has finished the work already issued (a device-wide synchronize).
+ * The paper has no counterpart (memory management only). Returns GBS_OK, or
+ * GBS_ECUDA if that synchronize reports an earlier asynchronous error. */
+int gbs_clear_plans(void);
 
 /* Instrumentation: when both are non-NULL, every later batch records `start`
  * immediately before and `stop` immediately after the kernels of its subset
@@ -306,6 +319,18 @@ int gbs_serve_submit(gbs_server* s, const int* idx, int n, int precision, int64_
  * GBS_ECANCELED, GBS_ENOMEM (its partial sums exceed the whole memory budget),
  * GBS_ETIMEDOUT or GBS_ECUDA. */
 int gbs_serve_poll(gbs_server* s, int64_t ticket, double* p, double* haf_ri, double* err_est);
+
+/* Completion queue: collect up to max finished requests, in any order. When
+ * none is finished and some are pending, waits up to timeout_s seconds (0 =
+ * no wait) for one. Entry i of *count gets tickets[i] and, in each array that
+ * is not NULL, p[i], haf_ri[2i..2i+1], err_est[i] and rc[i] (0, or the
+ * negative code gbs_serve_poll would return for that ticket; its outputs are
+ * then NaN). Collected tickets are released as by gbs_serve_poll. *count = 0
+ * when the wait ran out or nothing is pending. A client serving many requests
+ * collects them here instead of polling each ticket. The paper has no
+ * counterpart (serving only). Errors: GBS_EINVAL. */
+int gbs_serve_wait_any(gbs_server* s, double timeout_s, int max, int64_t* tickets, double* p,
+                       double* haf_ri, double* err_est, int* rc, int* count);
 
 /* Cancel a request: 0 when it was still pending (its ticket then polls
  * GBS_ECANCELED; device work already in flight for it finishes and is

@@ -21,6 +21,7 @@ __all__ = [
     "FP64", "MIXED", "MAX_N", "GbsError", "lib", "build_kernel", "KernelMatrix",
     "hafnian_batch", "hafnian_batch_noalloc", "prob_batch", "autotune", "measure_fp64_peak", "Server", "serve_create", "pack_patterns",
     "pack_matrices", "last_error", "ERRORS", "photon_number_dist", "sample_bruteforce", "marginal_batch", "sample_chain",
+    "clear_plans",
 ]
 
 FP64 = 0
@@ -80,10 +81,13 @@ def lib():
             L.gbs_autotune.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int)]
             L.gbs_measure_fp64_peak.argtypes = [vp, dp]
             L.gbs_set_timing_events.argtypes = [vp, vp]
+            L.gbs_clear_plans.argtypes = []
             L.gbs_serve_create.argtypes = [vp, ctypes.POINTER(ServeOpts), ctypes.POINTER(ctypes.c_void_p)]
             L.gbs_serve_submit.argtypes = [vp, ip, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
             L.gbs_serve_poll.argtypes = [vp, ctypes.c_int64, dp, dp, dp]
             L.gbs_serve_cancel.argtypes = [vp, ctypes.c_int64]
+            L.gbs_serve_wait_any.argtypes = [vp, ctypes.c_double, ctypes.c_int, vp, dp, dp, dp, ip,
+                                             ctypes.POINTER(ctypes.c_int)]
             L.gbs_serve_destroy.argtypes = [vp]
             L.gbs_serve_stats.argtypes = [vp, ctypes.POINTER(ServeStats)]
             L.gbs_last_error.restype = ctypes.c_char_p
@@ -230,6 +234,11 @@ def set_timing_events(start, stop):
     _check(lib().gbs_set_timing_events(sp, tp))
 
 
+def clear_plans():
+    """gbs_clear_plans: free the batch plans kept for repeated shapes."""
+    _check(lib().gbs_clear_plans())
+
+
 def photon_number_dist(kernel: KernelMatrix, n_max: int, stream=None) -> np.ndarray:
     """P_n for n = 0..n_max (gbs_photon_number_dist), as a host array."""
     out = np.zeros(n_max + 1)
@@ -323,6 +332,21 @@ class Server:
             return None
         _check(rc)
         return p.value, complex(hf[0], hf[1]), e.value
+
+    def wait_any(self, timeout_s=0.0, max_results=1024):
+        """gbs_serve_wait_any: finished requests in any order, as numpy arrays
+        (tickets, p, haf complex, err_est, rc); empty when none finished within
+        timeout_s. A failed request has rc < 0 and NaN outputs."""
+        if getattr(self, "_wa_cap", 0) < max_results:
+            self._wa_cap = max_results
+            self._wa = (np.zeros(max_results, np.int64), np.zeros(max_results), np.zeros(2 * max_results),
+                        np.zeros(max_results), np.zeros(max_results, np.int32))
+        t, p, hf, e, rc = self._wa
+        cnt = ctypes.c_int()
+        _check(lib().gbs_serve_wait_any(self.handle, float(timeout_s), int(max_results), _ptr(t), _ptr(p),
+                                        _ptr(hf), _ptr(e), _ptr(rc), ctypes.byref(cnt)))
+        k = cnt.value
+        return t[:k].copy(), p[:k].copy(), hf[0:2 * k:2] + 1j * hf[1:2 * k:2], e[:k].copy(), rc[:k].copy()
 
     def cancel(self, ticket) -> int:
         """0: cancelled (its poll raises GBS_ECANCELED); 1: already finished."""

@@ -246,14 +246,9 @@ static int64_t key_cost(int key) {
 }
 
 void Planner::init(const int* n, int batch, int precision, int warp_bytes, const int* rounds_for_n,
-                   const int* rep_half, int64_t whole_reserve) {
+                   int64_t whole_reserve) {
   n_ = n;
-  rep_half_ = rep_half;
   batch_ = batch;
-  rep_total_ = 0;
-  if (rep_half)
-    for (int b = 0; b < batch; ++b)
-      rep_total_ += (rep_half[b] + kRepTermsPerItem - 1) / kRepTermsPerItem;
   const int cb = complex_bytes(precision);
   int maxn = 0;
   for (int b = 0; b < batch; ++b) maxn = std::max(maxn, n[b]);
@@ -263,8 +258,7 @@ void Planner::init(const int* n, int batch, int precision, int warp_bytes, const
     npat_[v] = 0;
     nwhole_[v] = 0;
   }
-  for (int b = 0; b < batch; ++b)
-    if (!rep_half || rep_half[b] == 0) npat_[n[b]]++;
+  for (int b = 0; b < batch; ++b) npat_[n[b]]++;
   std::fill(bucket_, bucket_ + kKeys, 0);
   total_ = 0;
   for (int v = 2; v <= kMaxN; v += 2) {
@@ -298,7 +292,7 @@ void Planner::init(const int* n, int batch, int precision, int warp_bytes, const
   int64_t seen[kMaxN + 1] = {0};
   for (int b = 0; b < batch; ++b) {
     const int v = n[b];
-    if ((rep_half && rep_half[b] > 0) || v < 4 || (v & 1)) continue;
+    if (v < 4 || (v & 1)) continue;
     whole_[b] = (seen[v]++ < nwhole_[v]) ? 1 : 0;
   }
   // bucket start offsets, most expensive key first
@@ -317,28 +311,16 @@ void Planner::init(const int* n, int batch, int precision, int warp_bytes, const
   }
 }
 
-void Planner::fill(PatDesc* pats, WorkItem* items, WorkItem* rep_items) {
+void Planner::fill(PatDesc* pats, WorkItem* items) {
   int64_t next[kKeys];
   std::copy(start_, start_ + kKeys, next);
-  int q = 0, rq = 0;
+  int q = 0;
   for (int b = 0; b < batch_; ++b) {
     PatDesc& d = pats[b];
     const int v = n_[b];
     d.n = v;
     d.item_begin = q;
-    if (rep_half_ && rep_half_[b] > 0) {
-      for (int t0 = 0; t0 < rep_half_[b]; t0 += kRepTermsPerItem) {
-        WorkItem& w = rep_items[rq++];
-        w.pat = b;
-        w.s = 0;
-        w.rank0 = t0;
-        w.count = std::min(kRepTermsPerItem, rep_half_[b] - t0);
-        w.part = q++;
-        w.stride = 1;
-        w.s_last = 0;
-        w.aux = 0;
-      }
-    } else if (whole_[b]) {
+    if (whole_[b]) {
       const int h = v / 2;
       WorkItem& w = items[next[h]++];
       w.pat = b;
@@ -400,12 +382,12 @@ static uint64_t splitmix64(uint64_t& x) {
 // Probe items hold one round of lane groups each (G subsets of one size), so
 // that the samples of one matrix run in parallel warps.
 static void plan_pairing(const int* n, int batch, int precision, int warp_bytes, int stage_h,
-                         const int* skip, PairingPlan* pp) {
+                         PairingPlan* pp) {
   const int cb = complex_bytes(precision);
   int base[kMaxN + 1];
   for (int v = 0; v <= kMaxN; ++v) base[v] = -1;
   for (int b = 0; b < batch; ++b)
-    if (n[b] >= kPairingMinN && !(n[b] & 1) && !(skip && skip[b])) pp->sel.push_back(b);
+    if (n[b] >= kPairingMinN && !(n[b] & 1)) pp->sel.push_back(b);
   if (pp->sel.empty()) return;
   for (int b : pp->sel) {
     const int v = n[b];
@@ -508,37 +490,6 @@ static int64_t rep_max_chunks(int n) {
   return (n >= 0 && n <= kMaxN) ? table[n] : 0;
 }
 
-// Terms (ceil(T / 2)) that the repeated-row route sums for index list x of
-// length n, or 0 when the subset sum is the cheaper route: the route needs a
-// repeated mode, at most kRepMaxDistinct distinct modes and T <= 2^30, and its
-// terms (about d^2 + 3d + 60 FP64 operations each) must cost under a quarter
-// of the subset sum (the margin covers its lower efficiency). The route
-// choice on the device (route_plan_kernel) applies the same rule.
-static int rep_half_terms(const int* x, int n) {
-  if (n < 4 || (n & 1)) return 0;
-  const int dmx = rep_d_max(n);
-  int vals[kMaxN], cnt[kMaxN], d = 0;
-  for (int i = 0; i < n; ++i) {
-    int j = 0;
-    while (j < d && vals[j] != x[i]) ++j;
-    if (j == d) {
-      if (d == dmx) return 0;
-      vals[d] = x[i];
-      cnt[d++] = 0;
-    }
-    cnt[j]++;
-  }
-  if (d == n) return 0;
-  int64_t T = 1;
-  for (int j = 0; j < d; ++j) {
-    T *= cnt[j] + 1;
-    if (T > ((int64_t)1 << 30)) return 0;
-  }
-  const int64_t half = (T + 1) / 2;
-  const double rep_cost = (double)half * (double)(d * d + 3 * d + 60);
-  return (4.0 * rep_cost < subset_cost(n)) ? (int)half : 0;
-}
-
 static cudaEvent_t g_time_start = nullptr, g_time_stop = nullptr;
 
 int device_sm_count() {
@@ -551,81 +502,171 @@ int device_sm_count() {
 // ------------------------------------------------------------------------
 // the batched path shared by gbs_hafnian_batch and gbs_prob_batch
 // ------------------------------------------------------------------------
+// Sizes and counts of a batch's plan: the plan block (descriptors, work
+// items, pair-sum offsets, probe tables, chunk tables) and what the launches
+// need to know about it. The inputs themselves are not part of it.
+struct BatchLayout {
+  int maxn = 0;
+  TuneCfg cfg, pcfg;
+  int pprec = GBS_FP64;
+  bool probe32 = false;
+  int64_t n_items = 0, src_elems = 0, idx_elems = 0, pt_elems = 0, dev_rep_cap = 0;
+  int n_sel = 0, n_probe = 0, n_pitems = 0, n_chunks = 0;
+  size_t pats_b = 0, items_b = 0, ptoff_b = 0;
+  size_t perm_b = 0, ppats_b = 0, pitems_b = 0, pperm_b = 0, selpat_b = 0, probe_up_b = 0;
+  size_t choff_b = 0, chpat_b = 0, up_b = 0;
+  size_t probe_at = 0, chunk_at = 0;
+};
+
+// Plans of repeated batch shapes. The plan block depends only on the orders,
+// offsets, m and launch shapes (never on the index lists or matrices), so a
+// call whose n[] and offs[] match a kept plan skips the planning and its
+// upload and reads the kept block (read-only on the device; the probe's
+// per-call choice lives in the call's own scratch). Entries are
+// evicted least recently used, never while a call is using them, and only
+// after the device has finished every launch that read them.
+struct PlanKey {
+  int mode, precision, batch, maxn, m, device, sms, probe32;
+  int wpb, warp_bytes, pwpb, pwarp_bytes;
+  int rounds[kMaxN + 1];
+  bool operator==(const PlanKey& o) const { return memcmp(this, &o, sizeof(PlanKey)) == 0; }
+};
+struct PlanEntry {
+  PlanKey key;
+  std::vector<int> n;
+  std::vector<int64_t> offs;
+  BatchLayout lay;
+  void* d_up = nullptr;          // the upload block (cudaMalloc)
+  cudaEvent_t ready = nullptr;   // recorded after its upload
+  bool uploaded = false;         // `ready` recorded: other calls may use it
+  bool bad = false;              // its upload failed: never used again
+  int in_use = 0;
+  uint64_t last_use = 0;
+};
+constexpr int kPlanCacheEntries = 8;
+constexpr size_t kPlanCacheBytes = (size_t)256 << 20;
+static std::mutex g_plan_mu;
+static std::vector<PlanEntry*> g_plans;
+static uint64_t g_plan_clock = 0;
+
+static PlanEntry* plan_lookup(const PlanKey& key, const int* n, const int64_t* offs) {
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  for (PlanEntry* p : g_plans)
+    if (p->uploaded && !p->bad && p->key == key && memcmp(p->n.data(), n, sizeof(int) * key.batch) == 0 &&
+        memcmp(p->offs.data(), offs, sizeof(int64_t) * key.batch) == 0) {
+      p->in_use++;
+      p->last_use = ++g_plan_clock;
+      return p;
+    }
+  return nullptr;
+}
+
+// A new entry (in use by the caller) with room for the layout's upload block,
+// or null when none can be made (the call then uploads into its own scratch).
+static PlanEntry* plan_insert(const PlanKey& key, const int* n, const int64_t* offs, const BatchLayout& lay) {
+  if (lay.up_b > kPlanCacheBytes / 4) return nullptr;
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  size_t used = 0;
+  for (PlanEntry* p : g_plans) used += p->lay.up_b;
+  while ((int)g_plans.size() >= kPlanCacheEntries || used + lay.up_b > kPlanCacheBytes) {
+    int victim = -1;
+    for (int i = 0; i < (int)g_plans.size(); ++i)
+      if (g_plans[i]->in_use == 0 && (victim < 0 || g_plans[i]->last_use < g_plans[victim]->last_use)) victim = i;
+    if (victim < 0) return nullptr;
+    PlanEntry* v = g_plans[victim];
+    used -= v->lay.up_b;
+    // launches of earlier calls may still read it, on any stream
+    cudaDeviceSynchronize();
+    cudaFree(v->d_up);
+    if (v->ready) cudaEventDestroy(v->ready);
+    delete v;
+    g_plans.erase(g_plans.begin() + victim);
+  }
+  PlanEntry* p = new (std::nothrow) PlanEntry();
+  if (!p) return nullptr;
+  if (cudaMalloc(&p->d_up, lay.up_b) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ready, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (p->d_up) cudaFree(p->d_up);
+    delete p;
+    return nullptr;
+  }
+  p->key = key;
+  p->n.assign(n, n + key.batch);
+  p->offs.assign(offs, offs + key.batch);
+  p->lay = lay;
+  p->in_use = 1;
+  p->last_use = ++g_plan_clock;
+  g_plans.push_back(p);
+  return p;
+}
+
+// The upload into a new entry was issued (and `ready` recorded), or failed.
+static void plan_uploaded(PlanEntry* p, bool ok) {
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  p->uploaded = ok;
+  p->bad = !ok;
+}
+
+static void plan_release(PlanEntry* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  p->in_use--;
+}
+
+static int clear_plans() {
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  cudaError_t e = cudaDeviceSynchronize();
+  for (size_t i = 0; i < g_plans.size();) {
+    PlanEntry* v = g_plans[i];
+    if (v->in_use) {
+      ++i;
+      continue;
+    }
+    cudaFree(v->d_up);
+    if (v->ready) cudaEventDestroy(v->ready);
+    delete v;
+    g_plans.erase(g_plans.begin() + i);
+  }
+  return e == cudaSuccess ? GBS_OK : cuda_fail(e, "synchronize before freeing kept plans");
+}
+
+
 int run_batch(const BatchArgs& a) {
   cudaStream_t st = a.stream;
   const int batch = a.batch;
   if (batch == 0) return GBS_OK;
   if (a.precision != GBS_FP64 && a.precision != GBS_MIXED)
     return fail(GBS_EINVAL, "precision must be GBS_FP64 or GBS_MIXED");
-  int maxn = 0;
+  BatchLayout U;
   for (int b = 0; b < batch; ++b) {
     if (a.n[b] < 0) return fail(GBS_EINVAL, "n[%d] = %d is negative", b, a.n[b]);
     if (a.n[b] > GBS_MAX_N) return fail(GBS_ERANGE, "n[%d] = %d exceeds GBS_MAX_N", b, a.n[b]);
     if (a.offs[b] < 0) return fail(GBS_EINVAL, "offs[%d] is negative", b);
-    maxn = std::max(maxn, a.n[b]);
+    U.maxn = std::max(U.maxn, a.n[b]);
   }
+  const int maxn = U.maxn;
   // launch shape from the largest n (it dominates the cost); rounds per n
-  TuneCfg cfg = a.cfg_override ? *a.cfg_override : get_cfg(a.precision, maxn);
+  U.cfg = a.cfg_override ? *a.cfg_override : get_cfg(a.precision, maxn);
+  const TuneCfg& cfg = U.cfg;
   int rounds_for_n[kMaxN + 1];
   for (int v = 0; v <= kMaxN; ++v)
     rounds_for_n[v] = a.cfg_override ? a.cfg_override->rounds : get_cfg(a.precision, v).rounds;
-  HafLaunch L;
-  memset(&L, 0, sizeof(L));
   if (!shape_fits(a.precision, cfg.warp_bytes, maxn))
     return fail(GBS_EINVAL, "warp_bytes %d too small for n = %d", cfg.warp_bytes, maxn);
-
-  // FP64 index lists held on the host: matrices with repeated modes whose
-  // repeated-row terms are cheaper than the subset sum take that route
-  std::vector<int> rep_half;
-  int n_rep_pat = 0;
-  if (a.mode == BatchArgs::PROB && a.precision == GBS_FP64 && a.idx && !is_device_ptr(a.idx)) {
-    rep_half.assign(batch, 0);
-    for (int b = 0; b < batch; ++b) {
-      rep_half[b] = rep_half_terms(a.idx + a.offs[b], a.n[b]);
-      n_rep_pat += rep_half[b] > 0;
-    }
-  }
-  const int* rep_ptr = n_rep_pat ? rep_half.data() : nullptr;
-
-  Planner plan;
-  // a few items per resident warp balance the load over all SMs; whole-matrix
-  // items for all but a reserve of an order, whose per-size items fill the
-  // schedule's tail: one matrix per two resident warps in FP64 (one per warp
-  // was 0.8 % slower at 10 warps per SM, one per four warps 9 % slower), one
-  // per warp for the float kernel (half that was 5 % slower); tuning runs keep
-  // per-size items, whose rounds they choose
-  const int64_t want = 4LL * device_sm_count() * cfg.warps_per_block;
-  const int64_t reserve = a.cfg_override ? 0
-                        : (int64_t)device_sm_count() * cfg.warps_per_block / (a.precision == GBS_FP64 ? 2 : 1);
-  plan.init(a.n, batch, a.precision, cfg.warp_bytes, rounds_for_n, rep_ptr, reserve);
-  if (!a.cfg_override) {
-    // A small batch gets smaller work items (fewer rounds each) for the same reason.
-    for (int iter = 0; iter < 6 && plan.total() < want; ++iter) {
-      bool shrunk = false;
-      for (int v = 0; v <= kMaxN; ++v)
-        if (rounds_for_n[v] > 1) {
-          rounds_for_n[v] /= 2;
-          shrunk = true;
-        }
-      if (!shrunk) break;
-      plan.init(a.n, batch, a.precision, cfg.warp_bytes, rounds_for_n, rep_ptr, reserve);
-    }
-  }
-  const int64_t n_items = plan.total();
-  const int64_t n_rep = plan.rep_total();
-  if (n_items + n_rep > ((int64_t)1 << 30))
-    return fail(GBS_ENOMEM, "too many work items (%lld)", (long long)(n_items + n_rep));
-
-  // host-side checks and sizes of the inputs to stage
   const bool src_dev = (a.mode == BatchArgs::HAFNIAN) ? is_device_ptr(a.src) : true;
   const bool idx_dev = (a.mode == BatchArgs::PROB) ? is_device_ptr(a.idx) : true;
-  int64_t src_elems = 0, idx_elems = 0;
+  // sizes of the inputs; host inputs are checked and staged on every call
   for (int b = 0; b < batch; ++b) {
     if (a.mode == BatchArgs::HAFNIAN)
-      src_elems = std::max<int64_t>(src_elems, a.offs[b] + (int64_t)a.n[b] * a.n[b]);
+      U.src_elems = std::max<int64_t>(U.src_elems, a.offs[b] + (int64_t)a.n[b] * a.n[b]);
     else
-      idx_elems = std::max<int64_t>(idx_elems, a.offs[b] + a.n[b]);
+      U.idx_elems = std::max<int64_t>(U.idx_elems, a.offs[b] + a.n[b]);
   }
+  if (a.mode == BatchArgs::HAFNIAN && U.src_elems > 0 && a.src == nullptr)
+    return fail(GBS_EINVAL, "A_ri is null");
+  if (a.mode == BatchArgs::PROB && U.idx_elems > 0 && a.idx == nullptr)
+    return fail(GBS_EINVAL, "idx is null");
   if (a.mode == BatchArgs::PROB && !idx_dev) {
     for (int b = 0; b < batch; ++b)
       for (int i = 0; i < a.n[b]; ++i) {
@@ -634,218 +675,315 @@ int run_batch(const BatchArgs& a) {
           return fail(GBS_ERANGE, "pattern %d index %d = %d is outside [0, %d)", b, i, v, a.m);
       }
   }
-  if (a.mode == BatchArgs::HAFNIAN && src_elems > 0 && a.src == nullptr)
-    return fail(GBS_EINVAL, "A_ri is null");
-  // FP64 index lists in device memory: the route choice above is made on the
-  // device (route_plan_kernel) before the subset sum; repeated-row partial
-  // slots are reserved for the most each pattern's order can need, up to
-  // kDevRepCap in all (patterns past that in batch order keep the subset sum)
-  constexpr int64_t kDevRepCap = (int64_t)1 << 20;
-  int64_t dev_rep_cap = 0;
-  if (a.mode == BatchArgs::PROB && a.precision == GBS_FP64 && idx_dev && idx_elems > 0) {
-    for (int b = 0; b < batch; ++b) dev_rep_cap += rep_max_chunks(a.n[b]);
-    dev_rep_cap = std::min(dev_rep_cap, kDevRepCap);
-  }
-  if (a.mode == BatchArgs::PROB && idx_elems > 0 && a.idx == nullptr)
-    return fail(GBS_EINVAL, "idx is null");
-
-  // upload block: pats | items | (idx) | (src)
+  const int64_t src_elems = U.src_elems, idx_elems = U.idx_elems;
+  // host inputs: staged per call into the call's own device block
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  const size_t pats_b = al(sizeof(PatDesc) * batch);
-  const size_t items_b = al(sizeof(WorkItem) * std::max<int64_t>(n_items, 1));
-  const size_t idx_b = (a.mode == BatchArgs::PROB && !idx_dev) ? al(sizeof(int) * idx_elems) : 0;
-  const size_t src_b = (a.mode == BatchArgs::HAFNIAN && !src_dev) ? al(16 * (size_t)src_elems) : 0;
-  // FP64: pair terms of each matrix with n >= 6, up to kPairTermBudget bytes
-  // (later matrices form A_S X A_S by the product)
-  constexpr int64_t kPairTermBudget = (int64_t)2 << 30;
-  const bool use_pt = (a.precision == GBS_FP64);
-  int64_t pt_elems = 0;
-  if (use_pt)
-    for (int b = 0; b < batch; ++b) {
-      if (rep_ptr && rep_ptr[b]) continue;  // repeated-row route: no subsets
-      const int64_t q = pair_terms_elems(a.n[b]);
-      if (q > 0 && 16 * (pt_elems + q) <= kPairTermBudget) pt_elems += q;
-    }
-  const size_t ptoff_b = (use_pt && pt_elems > 0) ? al(sizeof(int64_t) * batch) : 0;
-  // pairing probe of the largest matrices
-  PairingPlan pp;
+  const size_t data_b = (a.mode == BatchArgs::PROB && !idx_dev) ? al(sizeof(int) * idx_elems)
+                      : (a.mode == BatchArgs::HAFNIAN && !src_dev) ? al(16 * (size_t)src_elems) : 0;
   // The probe only ranks candidate orderings by their estimated sum |f|, which
   // float arithmetic does as well as FP64; so FP64 probability calls run it on
   // the float kernel over the kernel's float copy of B (about a quarter of the
   // time), with the float kernel's launch shape.
-  const bool probe32 = (a.precision == GBS_FP64 && a.mode == BatchArgs::PROB && a.B32 != nullptr);
-  const int pprec = probe32 ? GBS_MIXED : a.precision;
-  const TuneCfg pcfg = (probe32 && !a.cfg_override) ? get_cfg(GBS_MIXED, maxn) : cfg;
-  if (n_items > 0) plan_pairing(a.n, batch, pprec, pcfg.warp_bytes, maxn / 2, rep_ptr, &pp);
-  const int n_sel = (int)pp.sel.size();
-  const int n_probe = (int)pp.pats.size();
-  const int n_pitems = (int)pp.items.size();
-  const size_t perm_b = n_sel ? al(sizeof(int) * pp.perm.size()) : 0;
-  const size_t ppats_b = n_sel ? al(sizeof(PatDesc) * n_probe) : 0;
-  const size_t pitems_b = n_sel ? al(sizeof(WorkItem) * n_pitems) : 0;
-  const size_t pperm_b = n_sel ? al(sizeof(int) * n_probe) : 0;
-  const size_t mperm_b = n_sel ? al(sizeof(int) * batch) : 0;
-  const size_t selpat_b = n_sel ? al(sizeof(int) * n_sel) : 0;
-  const size_t probe_up_b = perm_b + ppats_b + pitems_b + pperm_b + mperm_b + selpat_b;
-  // two-stage finalisation when some matrix has more than kChunkItems items
-  std::vector<int> chunk_off, chunk_pat;
-  int max_items = 0;
-  for (int b = 0; b < batch; ++b) max_items = std::max(max_items, plan.items_for(b));
-  if (max_items > kChunkItems) {
-    chunk_off.resize(batch + 1);
-    for (int b = 0; b < batch; ++b) {
-      chunk_off[b] = (int)chunk_pat.size();
-      const int cnt = plan.items_for(b);
-      for (int c = 0; c * kChunkItems < cnt; ++c) chunk_pat.push_back(b);
+  U.probe32 = (a.precision == GBS_FP64 && a.mode == BatchArgs::PROB && a.B32 != nullptr);
+  U.pprec = U.probe32 ? GBS_MIXED : a.precision;
+  U.pcfg = (U.probe32 && !a.cfg_override) ? get_cfg(GBS_MIXED, maxn) : cfg;
+
+  // a kept plan of the same shape (untuned calls)
+  const bool cacheable = !a.cfg_override;
+  PlanKey key;
+  memset(&key, 0, sizeof(key));
+  PlanEntry* pe = nullptr;
+  bool hit = false;
+  if (cacheable) {
+    key.mode = (int)a.mode;
+    key.precision = a.precision;
+    key.batch = batch;
+    key.maxn = maxn;
+    key.m = a.m;
+    cudaGetDevice(&key.device);
+    key.sms = device_sm_count();
+    key.probe32 = U.probe32;
+    key.wpb = cfg.warps_per_block;
+    key.warp_bytes = cfg.warp_bytes;
+    key.pwpb = U.pcfg.warps_per_block;
+    key.pwarp_bytes = U.pcfg.warp_bytes;
+    for (int v = 0; v <= kMaxN; ++v) key.rounds[v] = rounds_for_n[v];
+    pe = plan_lookup(key, a.n, a.offs);
+    if (pe) {
+      U = pe->lay;
+      hit = true;
     }
-    chunk_off[batch] = (int)chunk_pat.size();
   }
-  const int n_chunks = (int)chunk_pat.size();
-  const size_t choff_b = n_chunks ? al(sizeof(int) * (batch + 1)) : 0;
-  const size_t chpat_b = n_chunks ? al(sizeof(int) * n_chunks) : 0;
-  const size_t rep_b = n_rep ? al(sizeof(WorkItem) * n_rep) : 0;  // repeated-row items
-  const size_t up_b = pats_b + items_b + idx_b + src_b + ptoff_b + probe_up_b + choff_b + chpat_b + rep_b;
-  // device-only block: parts | counter | status | output staging
-  const size_t parts_b = al(sizeof(Partial) * std::max<int64_t>(n_items + n_rep, 1));
+
+  // FP64: pair terms of each matrix with n >= 6, up to kPairTermBudget bytes
+  // (later matrices form A_S X A_S by the product)
+  constexpr int64_t kPairTermBudget = (int64_t)2 << 30;
+  void* host_stage = nullptr;
+  int slot = -1;
+  unsigned char* hs = nullptr;
+  if (!hit) {
+    Planner plan;
+    // a few items per resident warp balance the load over all SMs; whole-matrix
+    // items for all but a reserve of an order, whose per-size items fill the
+    // schedule's tail: one matrix per two resident warps in FP64 (one per warp
+    // was 0.8 % slower at 10 warps per SM, one per four warps 9 % slower), one
+    // per warp for the float kernel (half that was 5 % slower); tuning runs keep
+    // per-size items, whose rounds they choose
+    const int64_t want = 4LL * device_sm_count() * cfg.warps_per_block;
+    const int64_t reserve = a.cfg_override ? 0
+                          : (int64_t)device_sm_count() * cfg.warps_per_block / (a.precision == GBS_FP64 ? 2 : 1);
+    plan.init(a.n, batch, a.precision, cfg.warp_bytes, rounds_for_n, reserve);
+    if (!a.cfg_override) {
+      // A small batch gets smaller work items (fewer rounds each) for the same reason.
+      for (int iter = 0; iter < 6 && plan.total() < want; ++iter) {
+        bool shrunk = false;
+        for (int v = 0; v <= kMaxN; ++v)
+          if (rounds_for_n[v] > 1) {
+            rounds_for_n[v] /= 2;
+            shrunk = true;
+          }
+        if (!shrunk) break;
+        plan.init(a.n, batch, a.precision, cfg.warp_bytes, rounds_for_n, reserve);
+      }
+    }
+    U.n_items = plan.total();
+    if (U.n_items > ((int64_t)1 << 30))
+      return fail(GBS_ENOMEM, "too many work items (%lld)", (long long)U.n_items);
+
+    // FP64 probabilities: the route choice (repeated-row sum for bunched
+    // patterns) is made on the device (route_plan_kernel) before the subset
+    // sum; repeated-row partial slots are reserved for the most each pattern's
+    // order can need, up to kDevRepCap in all (patterns past that in batch
+    // order keep the subset sum)
+    constexpr int64_t kDevRepCap = (int64_t)1 << 20;
+    if (a.mode == BatchArgs::PROB && a.precision == GBS_FP64 && U.idx_elems > 0) {
+      for (int b = 0; b < batch; ++b) U.dev_rep_cap += rep_max_chunks(a.n[b]);
+      U.dev_rep_cap = std::min(U.dev_rep_cap, kDevRepCap);
+    }
+
+    // plan block: pats | items | (pair-sum offsets) | (probe tables) | (chunk
+    // tables)
+    U.pats_b = al(sizeof(PatDesc) * batch);
+    U.items_b = al(sizeof(WorkItem) * std::max<int64_t>(U.n_items, 1));
+    if (a.precision == GBS_FP64)
+      for (int b = 0; b < batch; ++b) {
+        const int64_t q = pair_terms_elems(a.n[b]);
+        if (q > 0 && 16 * (U.pt_elems + q) <= kPairTermBudget) U.pt_elems += q;
+      }
+    U.ptoff_b = (U.pt_elems > 0) ? al(sizeof(int64_t) * batch) : 0;
+    // pairing probe of the largest matrices
+    PairingPlan pp;
+    if (U.n_items > 0) plan_pairing(a.n, batch, U.pprec, U.pcfg.warp_bytes, maxn / 2, &pp);
+    U.n_sel = (int)pp.sel.size();
+    U.n_probe = (int)pp.pats.size();
+    U.n_pitems = (int)pp.items.size();
+    U.perm_b = U.n_sel ? al(sizeof(int) * pp.perm.size()) : 0;
+    U.ppats_b = U.n_sel ? al(sizeof(PatDesc) * U.n_probe) : 0;
+    U.pitems_b = U.n_sel ? al(sizeof(WorkItem) * U.n_pitems) : 0;
+    U.pperm_b = U.n_sel ? al(sizeof(int) * U.n_probe) : 0;
+    U.selpat_b = U.n_sel ? al(sizeof(int) * U.n_sel) : 0;
+    U.probe_up_b = U.perm_b + U.ppats_b + U.pitems_b + U.pperm_b + U.selpat_b;
+    // two-stage finalisation when some matrix has more than kChunkItems items
+    std::vector<int> chunk_off, chunk_pat;
+    int max_items = 0;
+    for (int b = 0; b < batch; ++b) max_items = std::max(max_items, plan.items_for(b));
+    if (max_items > kChunkItems) {
+      chunk_off.resize(batch + 1);
+      for (int b = 0; b < batch; ++b) {
+        chunk_off[b] = (int)chunk_pat.size();
+        const int cnt = plan.items_for(b);
+        for (int c = 0; c * kChunkItems < cnt; ++c) chunk_pat.push_back(b);
+      }
+      chunk_off[batch] = (int)chunk_pat.size();
+    }
+    U.n_chunks = (int)chunk_pat.size();
+    U.choff_b = U.n_chunks ? al(sizeof(int) * (batch + 1)) : 0;
+    U.chpat_b = U.n_chunks ? al(sizeof(int) * U.n_chunks) : 0;
+    U.up_b = U.pats_b + U.items_b + U.ptoff_b + U.probe_up_b + U.choff_b + U.chpat_b;
+    U.probe_at = U.pats_b + U.items_b + U.ptoff_b;
+    U.chunk_at = U.probe_at + U.probe_up_b;
+
+    int rc = pinned_acquire(U.up_b + data_b, &host_stage, &slot);
+    if (rc) return rc;
+    hs = (unsigned char*)host_stage;
+    PatDesc* h_pats = (PatDesc*)hs;
+    plan.fill(h_pats, (WorkItem*)(hs + U.pats_b));
+    for (int b = 0; b < batch; ++b) {
+      PatDesc& d = h_pats[b];
+      if (a.mode == BatchArgs::HAFNIAN) {
+        d.src_off = a.offs[b];
+        d.idx_off = -1;
+        d.ld = a.n[b];
+      } else {
+        d.src_off = 0;
+        d.idx_off = a.offs[b];
+        d.ld = a.m;
+      }
+    }
+    if (U.ptoff_b) {
+      int64_t* h_ptoff = (int64_t*)(hs + U.pats_b + U.items_b);
+      int64_t off = 0;
+      for (int b = 0; b < batch; ++b) {
+        const int64_t q = pair_terms_elems(a.n[b]);
+        if (q > 0 && 16 * (off + q) <= kPairTermBudget) {
+          h_ptoff[b] = off;
+          off += q;
+        } else {
+          h_ptoff[b] = -1;
+        }
+      }
+    }
+    if (U.n_sel) {
+      unsigned char* q = hs + U.probe_at;
+      memcpy(q, pp.perm.data(), sizeof(int) * pp.perm.size());
+      q += U.perm_b;
+      PatDesc* h_ppats = (PatDesc*)q;
+      for (int k = 0; k < U.n_sel; ++k)
+        for (int c = 0; c < kPairingCands; ++c) {
+          PatDesc d = pp.pats[k * kPairingCands + c];
+          const PatDesc& m = h_pats[pp.sel[k]];
+          d.src_off = m.src_off;
+          d.idx_off = m.idx_off;
+          d.ld = m.ld;
+          h_ppats[k * kPairingCands + c] = d;
+        }
+      q += U.ppats_b;
+      memcpy(q, pp.items.data(), sizeof(WorkItem) * U.n_pitems);
+      q += U.pitems_b;
+      memcpy(q, pp.perm_off.data(), sizeof(int) * U.n_probe);
+      q += U.pperm_b;
+      memcpy(q, pp.sel.data(), sizeof(int) * U.n_sel);
+    }
+    if (U.n_chunks) {
+      memcpy(hs + U.chunk_at, chunk_off.data(), sizeof(int) * (batch + 1));
+      memcpy(hs + U.chunk_at + U.choff_b, chunk_pat.data(), sizeof(int) * U.n_chunks);
+    }
+    if (cacheable) pe = plan_insert(key, a.n, a.offs, U);
+  } else if (data_b) {
+    int rc = pinned_acquire(data_b, &host_stage, &slot);
+    if (rc) {
+      plan_release(pe);
+      return rc;
+    }
+    hs = (unsigned char*)host_stage;
+  }
+  // host inputs after the plan in the staging buffer
+  unsigned char* hdata = data_b ? hs + (hit ? 0 : U.up_b) : nullptr;
+  if (data_b) {
+    if (a.mode == BatchArgs::PROB) memcpy(hdata, a.idx, sizeof(int) * idx_elems);
+    else memcpy(hdata, a.src, 16 * (size_t)src_elems);
+  }
+  const int64_t n_items = U.n_items, dev_rep_cap = U.dev_rep_cap;
+  const int n_sel = U.n_sel, n_probe = U.n_probe, n_pitems = U.n_pitems, n_chunks = U.n_chunks;
+  const TuneCfg& pcfg = U.pcfg;
+  const int pprec = U.pprec;
+  const bool probe32 = U.probe32;
+
+  // the call's device block: (staged inputs) | parts | counter | status |
+  // probe status | output staging | float copy | pair sums | probe partials |
+  // chunk sums | the probe's choice | route choice; preceded by the plan
+  // block unless a kept plan holds it
+  const size_t parts_b = al(sizeof(Partial) * std::max<int64_t>(n_items, 1));
   const size_t ctr_b = 256;
   const size_t status_b = al(sizeof(int) * batch);
+  const size_t pstatus_b = n_sel ? al(sizeof(int) * n_probe) : 0;  // zeroed with ctr and status
   const bool out_host = (a.out0 && !is_device_ptr(a.out0)) || (a.out1 && !is_device_ptr(a.out1)) ||
                         (a.out2 && !is_device_ptr(a.out2)) || (a.out3 && !is_device_ptr(a.out3));
   const size_t outs_b = out_host ? al(sizeof(double) * 5 * batch) : 0;
   // FP32 path on explicit matrices: one rounded copy per call, gathered by the kernel
   const size_t a32_b = (a.mode == BatchArgs::HAFNIAN && a.precision == GBS_MIXED) ? al(8 * (size_t)src_elems) : 0;
-  const size_t pt_b = ptoff_b ? al(16 * (size_t)pt_elems) : 0;
-  const size_t pstatus_b = n_sel ? al(sizeof(int) * n_probe) : 0;  // zeroed with ctr and status
+  const size_t pt_b = U.ptoff_b ? al(16 * (size_t)U.pt_elems) : 0;
   const size_t pparts_b = n_sel ? al(sizeof(Partial) * n_pitems) : 0;
   const size_t chparts_b = n_chunks ? al(sizeof(Partial) * n_chunks) : 0;
+  const size_t mperm_b = n_sel ? al(sizeof(int) * batch) : 0;  // written by the probe's choice
   // route choice on the device: rep_half | rep_end | repeated-row partials
   const size_t droute_b = dev_rep_cap ? 2 * al(sizeof(int) * batch) + al(sizeof(Partial) * dev_rep_cap) : 0;
-  const size_t total_b =
-      up_b + parts_b + ctr_b + status_b + pstatus_b + outs_b + a32_b + pt_b + pparts_b + chparts_b + droute_b;
-
-  void* host_stage = nullptr;
-  int slot = -1;
-  int rc = pinned_acquire(up_b, &host_stage, &slot);
-  if (rc) return rc;
-  unsigned char* hs = (unsigned char*)host_stage;
-  PatDesc* h_pats = (PatDesc*)hs;
-  const size_t rep_at = up_b - rep_b;
-  plan.fill(h_pats, (WorkItem*)(hs + pats_b), n_rep ? (WorkItem*)(hs + rep_at) : nullptr);
-  for (int b = 0; b < batch; ++b) {
-    PatDesc& d = h_pats[b];
-    if (a.mode == BatchArgs::HAFNIAN) {
-      d.src_off = a.offs[b];
-      d.idx_off = -1;
-      d.ld = a.n[b];
-    } else {
-      d.src_off = 0;
-      d.idx_off = a.offs[b];
-      d.ld = a.m;
-    }
-  }
-  if (idx_b) memcpy(hs + pats_b + items_b, a.idx, sizeof(int) * idx_elems);
-  if (src_b) memcpy(hs + pats_b + items_b + idx_b, a.src, 16 * (size_t)src_elems);
-  if (ptoff_b) {
-    int64_t* h_ptoff = (int64_t*)(hs + pats_b + items_b + idx_b + src_b);
-    int64_t off = 0;
-    for (int b = 0; b < batch; ++b) {
-      const int64_t q = (rep_ptr && rep_ptr[b]) ? 0 : pair_terms_elems(a.n[b]);
-      if (q > 0 && 16 * (off + q) <= kPairTermBudget) {
-        h_ptoff[b] = off;
-        off += q;
-      } else {
-        h_ptoff[b] = -1;
-      }
-    }
-  }
-
-  const size_t probe_at = pats_b + items_b + idx_b + src_b + ptoff_b;
-  if (n_sel) {
-    unsigned char* q = hs + probe_at;
-    memcpy(q, pp.perm.data(), sizeof(int) * pp.perm.size());
-    q += perm_b;
-    PatDesc* h_ppats = (PatDesc*)q;
-    for (int k = 0; k < n_sel; ++k)
-      for (int c = 0; c < kPairingCands; ++c) {
-        PatDesc d = pp.pats[k * kPairingCands + c];
-        const PatDesc& m = h_pats[pp.sel[k]];
-        d.src_off = m.src_off;
-        d.idx_off = m.idx_off;
-        d.ld = m.ld;
-        h_ppats[k * kPairingCands + c] = d;
-      }
-    q += ppats_b;
-    memcpy(q, pp.items.data(), sizeof(WorkItem) * n_pitems);
-    q += pitems_b;
-    memcpy(q, pp.perm_off.data(), sizeof(int) * n_probe);
-    q += pperm_b;
-    int* h_mperm = (int*)q;
-    for (int b = 0; b < batch; ++b) h_mperm[b] = -1;  // the probe's choice replaces these on the device
-    q += mperm_b;
-    memcpy(q, pp.sel.data(), sizeof(int) * n_sel);
-  }
-  const size_t chunk_at = probe_at + probe_up_b;
-  if (n_chunks) {
-    memcpy(hs + chunk_at, chunk_off.data(), sizeof(int) * (batch + 1));
-    memcpy(hs + chunk_at + choff_b, chunk_pat.data(), sizeof(int) * n_chunks);
-  }
+  const size_t dev_b = data_b + parts_b + ctr_b + status_b + pstatus_b + outs_b + a32_b + pt_b + pparts_b + chparts_b + mperm_b + droute_b;
+  const size_t own_up_b = pe ? 0 : U.up_b;
 
   void* dmem = nullptr;
-  cudaError_t e = scratch_alloc(&dmem, total_b, st);
+  cudaError_t e = scratch_alloc(&dmem, own_up_b + dev_b, st);
   if (e != cudaSuccess) {
     pinned_release(slot, st);
+    if (!hit && pe) plan_uploaded(pe, false);
+    plan_release(pe);
     cudaGetLastError();
-    return fail(GBS_ENOMEM, "device scratch of %zu bytes: %s", total_b, cudaGetErrorString(e));
+    return fail(GBS_ENOMEM, "device scratch of %zu bytes: %s", own_up_b + dev_b, cudaGetErrorString(e));
   }
-  unsigned char* dm = (unsigned char*)dmem;
-  PatDesc* d_pats = (PatDesc*)dm;
-  WorkItem* d_items = (WorkItem*)(dm + pats_b);
-  const int* d_idx = idx_b ? (const int*)(dm + pats_b + items_b) : a.idx;
-  const double* d_src = src_b ? (const double*)(dm + pats_b + items_b + idx_b) : a.src;
-  Partial* d_parts = (Partial*)(dm + up_b);
-  int* d_ctr = (int*)(dm + up_b + parts_b);
-  int* d_status = (int*)(dm + up_b + parts_b + ctr_b);
-  double* d_outs = outs_b ? (double*)(dm + up_b + parts_b + ctr_b + status_b + pstatus_b) : nullptr;
-  float* d_a32 = a32_b ? (float*)(dm + up_b + parts_b + ctr_b + status_b + pstatus_b + outs_b) : nullptr;
-  const int64_t* d_ptoff = ptoff_b ? (const int64_t*)(dm + pats_b + items_b + idx_b + src_b) : nullptr;
-  // device-only block: parts | ctr | status | pstatus | outs | a32 | pt | pparts
-  double* d_pt = pt_b ? (double*)(dm + up_b + parts_b + ctr_b + status_b + pstatus_b + outs_b + a32_b) : nullptr;
-  const int* d_perm = n_sel ? (const int*)(dm + probe_at) : nullptr;
-  const PatDesc* d_ppats = n_sel ? (const PatDesc*)(dm + probe_at + perm_b) : nullptr;
-  const WorkItem* d_pitems = n_sel ? (const WorkItem*)(dm + probe_at + perm_b + ppats_b) : nullptr;
-  const int* d_pperm = n_sel ? (const int*)(dm + probe_at + perm_b + ppats_b + pitems_b) : nullptr;
-  int* d_mperm = n_sel ? (int*)(dm + probe_at + perm_b + ppats_b + pitems_b + pperm_b) : nullptr;
-  const int* d_selpat = n_sel ? (const int*)(dm + probe_at + perm_b + ppats_b + pitems_b + pperm_b + mperm_b) : nullptr;
-  int* d_pstatus = n_sel ? (int*)(dm + up_b + parts_b + ctr_b + status_b) : nullptr;
-  Partial* d_pparts = n_sel ? (Partial*)(dm + up_b + parts_b + ctr_b + status_b + pstatus_b + outs_b + a32_b + pt_b) : nullptr;
-  const int* d_choff = n_chunks ? (const int*)(dm + chunk_at) : nullptr;
-  const int* d_chpat = n_chunks ? (const int*)(dm + chunk_at + choff_b) : nullptr;
-  Partial* d_chparts =
-      n_chunks ? (Partial*)(dm + up_b + parts_b + ctr_b + status_b + pstatus_b + outs_b + a32_b + pt_b + pparts_b)
-               : nullptr;
-  unsigned char* droute = dm + (total_b - droute_b);
-  int* d_rephalf = dev_rep_cap ? (int*)droute : nullptr;
-  int* d_repend = dev_rep_cap ? (int*)(droute + al(sizeof(int) * batch)) : nullptr;
-  Partial* d_repparts = dev_rep_cap ? (Partial*)(droute + 2 * al(sizeof(int) * batch)) : nullptr;
+  unsigned char* up = pe ? (unsigned char*)pe->d_up : (unsigned char*)dmem;
+  unsigned char* dv = (unsigned char*)dmem + own_up_b;
+  PatDesc* d_pats = (PatDesc*)up;
+  WorkItem* d_items = (WorkItem*)(up + U.pats_b);
+  const int* d_idx = (data_b && a.mode == BatchArgs::PROB) ? (const int*)dv : a.idx;
+  const double* d_src = (data_b && a.mode == BatchArgs::HAFNIAN) ? (const double*)dv : a.src;
+  const int64_t* d_ptoff = U.ptoff_b ? (const int64_t*)(up + U.pats_b + U.items_b) : nullptr;
+  const int* d_perm = n_sel ? (const int*)(up + U.probe_at) : nullptr;
+  const PatDesc* d_ppats = n_sel ? (const PatDesc*)(up + U.probe_at + U.perm_b) : nullptr;
+  const WorkItem* d_pitems = n_sel ? (const WorkItem*)(up + U.probe_at + U.perm_b + U.ppats_b) : nullptr;
+  const int* d_pperm = n_sel ? (const int*)(up + U.probe_at + U.perm_b + U.ppats_b + U.pitems_b) : nullptr;
+  const int* d_selpat = n_sel ? (const int*)(up + U.probe_at + U.perm_b + U.ppats_b + U.pitems_b + U.pperm_b) : nullptr;
+  const int* d_choff = n_chunks ? (const int*)(up + U.chunk_at) : nullptr;
+  const int* d_chpat = n_chunks ? (const int*)(up + U.chunk_at + U.choff_b) : nullptr;
+  size_t o = data_b;
+  Partial* d_parts = (Partial*)(dv + o);
+  o += parts_b;
+  int* d_ctr = (int*)(dv + o);
+  o += ctr_b;
+  int* d_status = (int*)(dv + o);
+  o += status_b;
+  int* d_pstatus = n_sel ? (int*)(dv + o) : nullptr;
+  o += pstatus_b;
+  double* d_outs = outs_b ? (double*)(dv + o) : nullptr;
+  o += outs_b;
+  float* d_a32 = a32_b ? (float*)(dv + o) : nullptr;
+  o += a32_b;
+  double* d_pt = pt_b ? (double*)(dv + o) : nullptr;
+  o += pt_b;
+  Partial* d_pparts = n_sel ? (Partial*)(dv + o) : nullptr;
+  o += pparts_b;
+  Partial* d_chparts = n_chunks ? (Partial*)(dv + o) : nullptr;
+  o += chparts_b;
+  int* d_mperm = n_sel ? (int*)(dv + o) : nullptr;
+  o += mperm_b;
+  int* d_rephalf = dev_rep_cap ? (int*)(dv + o) : nullptr;
+  int* d_repend = dev_rep_cap ? (int*)(dv + o + al(sizeof(int) * batch)) : nullptr;
+  Partial* d_repparts = dev_rep_cap ? (Partial*)(dv + o + 2 * al(sizeof(int) * batch)) : nullptr;
 
+  HafLaunch L;
+  memset(&L, 0, sizeof(L));
   int ret = GBS_OK;
   do {
-    e = cudaMemcpyAsync(dm, hs, up_b, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) { ret = cuda_fail(e, "upload"); break; }
+    if (!hit) {
+      e = cudaMemcpyAsync(up, hs, U.up_b, cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) { ret = cuda_fail(e, "upload"); break; }
+      if (pe && (e = cudaEventRecord(pe->ready, st)) != cudaSuccess) { ret = cuda_fail(e, "plan event"); break; }
+    } else {
+      // the kept block was uploaded on some stream: order this one after it
+      e = cudaStreamWaitEvent(st, pe->ready, 0);
+      if (e != cudaSuccess) { ret = cuda_fail(e, "plan wait"); break; }
+    }
+    if (data_b) {
+      e = cudaMemcpyAsync(dv, hdata, data_b, cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) { ret = cuda_fail(e, "input upload"); break; }
+    }
     e = cudaMemsetAsync(d_ctr, 0, ctr_b + status_b + pstatus_b, st);
     if (e != cudaSuccess) { ret = cuda_fail(e, "memset"); break; }
+    if (d_mperm) {  // -1: the default ordering until the probe's choice replaces it
+      e = cudaMemsetAsync(d_mperm, 0xff, sizeof(int) * batch, st);
+      if (e != cudaSuccess) { ret = cuda_fail(e, "memset"); break; }
+    }
     if (d_a32) {
       e = launch_to_float(d_src, d_a32, 2 * src_elems, st);
       if (e != cudaSuccess) { ret = cuda_fail(e, "float copy"); break; }
     }
-    if (n_items > 0 || n_rep > 0) {
+    if (n_items > 0) {
       L.src = (a.mode == BatchArgs::HAFNIAN) ? d_src : a.B;
       L.src32 = (a.precision == GBS_MIXED) ? ((a.mode == BatchArgs::HAFNIAN) ? d_a32 : a.B32) : nullptr;
       L.idx = (a.mode == BatchArgs::PROB) ? d_idx : nullptr;
       L.pats = d_pats;
       L.items = d_items;
       L.n_items = (int)n_items;
-      L.m_bound = (a.mode == BatchArgs::PROB && idx_dev) ? a.m : 0;
+      L.m_bound = (a.mode == BatchArgs::PROB) ? a.m : 0;
       L.counter = d_ctr;
       L.status = d_status;
       L.parts = d_parts;
@@ -930,20 +1068,6 @@ int run_batch(const BatchArgs& a) {
         e = launch_haf_subsets(L, a.precision, blocks, cfg.warps_per_block, st);
         if (e != cudaSuccess) { ret = cuda_fail(e, "subset kernel launch"); break; }
       }
-      if (n_rep > 0) {
-        RepLaunch R;
-        R.B = a.B;
-        R.idx = d_idx;
-        R.pats = d_pats;
-        R.items = (const WorkItem*)(dm + rep_at);
-        R.n_items = (int)n_rep;
-        R.m_bound = L.m_bound;
-        R.counter = d_ctr + 48;
-        R.status = d_status;
-        R.parts = d_parts;
-        e = launch_haf_repeated(R, st);
-        if (e != cudaSuccess) { ret = cuda_fail(e, "repeated-row kernel launch"); break; }
-      }
       if (dev_rep_cap) {
         // the patterns the device chose for the repeated-row sum (the item
         // count is read on the device; the grid covers the reservation)
@@ -951,7 +1075,6 @@ int run_batch(const BatchArgs& a) {
         R.B = a.B;
         R.idx = d_idx;
         R.pats = d_pats;
-        R.items = nullptr;
         R.n_items = (int)dev_rep_cap;
         R.n_items_dev = d_ctr + 56;
         R.m_bound = L.m_bound;
@@ -966,7 +1089,7 @@ int run_batch(const BatchArgs& a) {
       }
       if (timed) cudaEventRecord(g_time_stop, st);
     }
-    if (n_chunks && n_items + n_rep > 0) {
+    if (n_chunks && n_items > 0) {
       ChunkLaunch C;
       C.pats = d_pats;
       C.parts = d_parts;
@@ -981,7 +1104,7 @@ int run_batch(const BatchArgs& a) {
     memset(&F, 0, sizeof(F));
     F.pats = d_pats;
     F.parts = d_parts;
-    if (n_chunks && n_items + n_rep > 0) {
+    if (n_chunks && n_items > 0) {
       F.chunk_parts = d_chparts;
       F.chunk_off = d_choff;
     }
@@ -1027,6 +1150,8 @@ int run_batch(const BatchArgs& a) {
     }
   } while (0);
   pinned_release(slot, st);
+  if (!hit && pe) plan_uploaded(pe, ret == GBS_OK);
+  plan_release(pe);
   e = scratch_free(dmem, st);
   if (e != cudaSuccess && ret == GBS_OK) ret = cuda_fail(e, "scratch free");
   if (ret == GBS_OK && out_host) {
@@ -1044,7 +1169,7 @@ int order_probe_launch(const gbs_kernel* k, const int* const* lists, const int* 
   out->n_lists = count;
   out->n.assign(n, n + count);
   PairingPlan pp;
-  plan_pairing(n, count, GBS_MIXED, cfg.warp_bytes, stage_h, nullptr, &pp);
+  plan_pairing(n, count, GBS_MIXED, cfg.warp_bytes, stage_h, &pp);
   out->perm = pp.perm;
   out->sel = pp.sel;
   const int n_sel = (int)pp.sel.size();
@@ -1376,6 +1501,11 @@ extern "C" int gbs_set_timing_events(void* start, void* stop) {
   g_time_start = (cudaEvent_t)start;
   g_time_stop = (cudaEvent_t)stop;
   return GBS_OK;
+}
+
+extern "C" int gbs_clear_plans(void) {
+  clear_error();
+  return clear_plans();
 }
 
 extern "C" const char* gbs_last_error(void) { return t_err.c_str(); }

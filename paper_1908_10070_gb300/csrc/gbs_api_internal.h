@@ -81,23 +81,18 @@ constexpr int kWholeMaxN = 24;
 // item ranges and the items (in schedule order) into caller memory.
 class Planner {
  public:
-  // rep_half (may be null): per matrix, the number of repeated-row terms it
-  // sums (ceil(T / 2)), or 0 for the subset-sum route; those matrices get
-  // repeated-row items (kRepTermsPerItem terms each) instead of subset items.
   // whole_reserve (0 = never): of an order n <= kWholeMaxN with at least
   // 2 * whole_reserve matrices, all but whole_reserve get one item each that
   // covers all their subsets (sizes staged and reduced together); the
   // remaining ones keep one item per size and rank range, which fill the tail
   // of the schedule (whole items go first, as the largest).
   void init(const int* n, int batch, int precision, int warp_bytes, const int* rounds_for_n,
-            const int* rep_half = nullptr, int64_t whole_reserve = 0);
-  void fill(PatDesc* pats, WorkItem* items, WorkItem* rep_items = nullptr);
-  int64_t rep_total() const { return rep_total_; }
+            int64_t whole_reserve = 0);
+  void fill(PatDesc* pats, WorkItem* items);
   int64_t total() const { return total_; }
   // work items of one matrix of order v (0 for odd v or v < 2)
   // work items (= partial slots) of matrix b
   int items_for(int b) const {
-    if (rep_half_ && rep_half_[b] > 0) return (rep_half_[b] + kRepTermsPerItem - 1) / kRepTermsPerItem;
     if (!whole_.empty() && whole_[b]) return 1;
     const int v = n_[b];
     return (v >= 2 && !(v & 1)) ? (int)tmpl_[v].size() : 0;
@@ -106,10 +101,8 @@ class Planner {
  private:
   static constexpr int kKeys = (kMaxN / 2 + 1) * 65;
   const int* n_ = nullptr;
-  const int* rep_half_ = nullptr;
   int batch_ = 0;
   int64_t total_ = 0;
-  int64_t rep_total_ = 0;
   int npat_[kMaxN + 1];
   int64_t nwhole_[kMaxN + 1];
   std::vector<char> whole_;  // per matrix: one whole-matrix item

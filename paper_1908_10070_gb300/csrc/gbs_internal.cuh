@@ -224,24 +224,22 @@ struct PairingSelect {
 // B_v the d x d submatrix of B on the distinct modes (the moment-extraction
 // identity of Kan, 2008). Terms are numbered in mixed radix (digit j = nu_j,
 // radix c_j + 1); term t and T - 1 - t (nu and c - nu) are equal, so only
-// t < ceil(T / 2) is summed, T = prod (c_j + 1). A work item is a run
-// [rank0, rank0 + count) of term numbers of one matrix; its partial sum goes to
-// parts[part] like a subset-sum item's.
+// t < ceil(T / 2) is summed, T = prod (c_j + 1). A work item is a run of
+// kRepTermsPerItem term numbers of one matrix (the last one shorter).
 constexpr int kRepMaxDistinct = 16;
 constexpr int kRepTermsPerItem = 1024;
 struct RepLaunch {
   const double* B;         // interleaved complex, m x m, row stride ld (the PatDesc's)
   const int* idx;
   const PatDesc* pats;
-  const WorkItem* items;
-  int n_items;
+  int n_items;             // grid coverage (the reservation); *n_items_dev items run
   int m_bound;             // index lists must be < m_bound (0 = no check)
   int* counter;            // work-queue head, zero before launch
   int* status;             // per-pattern flag, set to 1 on an out-of-range index
   Partial* parts;
-  // Route choice on the device (items null): item v of the *n_items_dev items
-  // is term chunk v - (rep_end[b] - chunks_b) of the pattern b whose partial
-  // range [rep_end[b] - chunks_b, rep_end[b]) holds v, chunks_b =
+  // Item v of the *n_items_dev items (written by route_plan_kernel) is term
+  // chunk v - (rep_end[b] - chunks_b) of the pattern b whose partial range
+  // [rep_end[b] - chunks_b, rep_end[b]) holds v, chunks_b =
   // ceil(rep_half[b] / kRepTermsPerItem); its partial goes to parts[v].
   const int* rep_half = nullptr;
   const int* rep_end = nullptr;
@@ -249,10 +247,10 @@ struct RepLaunch {
   int batch = 0;
 };
 
-// Route choice on the device, for FP64 probabilities of index lists held in
-// device memory (the host cannot read them without a synchronisation). One
-// warp per pattern finds its distinct modes and multiplicities and applies the
-// host's rule (rep_half_terms in api.cu): the repeated-row sum when the
+// Route choice on the device, for FP64 probabilities (index lists from the
+// host are copied to the device first, so one rule serves both). One warp per
+// pattern finds its distinct modes and multiplicities and applies the cost
+// rule: the repeated-row sum when the
 // pattern has a repeated mode, at most d_max[n] distinct modes, T <= 2^30 and
 // 4 ceil(T / 2) (d^2 + 3d + 60) < subset_cost[n]. The last block to finish
 // then assigns partial ranges in pattern order: a pattern keeps the route

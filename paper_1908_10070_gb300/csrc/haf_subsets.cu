@@ -1207,42 +1207,38 @@ __global__ void __launch_bounds__(128) haf_repeated_kernel(const RepLaunch R) {
   const int lane = threadIdx.x & 31;
   RepWarp& W = ws[threadIdx.x >> 5];
   const double2* src2 = reinterpret_cast<const double2*>(R.B);
-  const int n_items = R.n_items_dev ? *R.n_items_dev : R.n_items;
+  const int n_items = min(*R.n_items_dev, R.n_items);
   for (;;) {
     int it = 0;
     if (lane == 0) it = atomicAdd(R.counter, 1);
     it = __shfl_sync(FULL, it, 0);
     if (it >= n_items) break;
     WorkItem w;
-    if (R.items != nullptr) {
-      w = R.items[it];
-    } else {
-      // route choice on the device: the pattern whose partial range holds
-      // slot it (the smallest b with rep_end[b] > it), and its chunk
-      int lo = 0, hi = R.batch - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (R.rep_end[mid] > it) hi = mid;
-        else lo = mid + 1;
-      }
-      const int half = R.rep_half[lo];
-      const int chunks = (half + kRepTermsPerItem - 1) / kRepTermsPerItem;
-      const int c = it - (R.rep_end[lo] - chunks);
-      w.pat = lo;
-      w.s = 0;
-      w.rank0 = c * kRepTermsPerItem;
-      w.count = min(kRepTermsPerItem, half - w.rank0);
-      w.part = it;
-      w.stride = 1;
-      w.s_last = 0;
-      w.aux = 0;
-      if (half <= 0 || c < 0 || c >= chunks) {  // never for a consistent plan
-        if (lane == 0) R.status[lo] = 1;
-        const Comp<double> z = {0.0, 0.0};
-        store_warp_partial(z, z, 0.0, lane, R.parts + it);
-        __syncwarp();
-        continue;
-      }
+    // route choice on the device: the pattern whose partial range holds
+    // slot it (the smallest b with rep_end[b] > it), and its chunk
+    int lo = 0, hi = R.batch - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (R.rep_end[mid] > it) hi = mid;
+      else lo = mid + 1;
+    }
+    const int half = R.rep_half[lo];
+    const int chunks = (half + kRepTermsPerItem - 1) / kRepTermsPerItem;
+    const int c = it - (R.rep_end[lo] - chunks);
+    w.pat = lo;
+    w.s = 0;
+    w.rank0 = c * kRepTermsPerItem;
+    w.count = min(kRepTermsPerItem, half - w.rank0);
+    w.part = it;
+    w.stride = 1;
+    w.s_last = 0;
+    w.aux = 0;
+    if (half <= 0 || c < 0 || c >= chunks) {  // never for a consistent plan
+      if (lane == 0) R.status[lo] = 1;
+      const Comp<double> z = {0.0, 0.0};
+      store_warp_partial(z, z, 0.0, lane, R.parts + it);
+      __syncwarp();
+      continue;
     }
     const PatDesc d = R.pats[w.pat];
     const int n = d.n, h = n >> 1;
@@ -1290,7 +1286,7 @@ __global__ void __launch_bounds__(128) haf_repeated_kernel(const RepLaunch R) {
 }
 
 // Route choice on the device (see RoutePlan): one warp per pattern decides
-// between the subset sum and the repeated-row sum by the host's rule, then the
+// between the subset sum and the repeated-row sum by the cost rule, then the
 // last block to finish assigns each repeated-row pattern its partial range in
 // pattern order (a block-wide prefix sum over tiles of the batch).
 __global__ void __launch_bounds__(256) route_plan_kernel(const RoutePlan R) {
@@ -1380,8 +1376,9 @@ cudaError_t launch_route_plan(const RoutePlan& R, cudaStream_t st) {
 }
 
 cudaError_t launch_haf_repeated(const RepLaunch& R, cudaStream_t st) {
-  // with the item count on the device, n_items is its upper bound (the grid)
+  // the item count is on the device; n_items is its upper bound (the grid)
   if (R.n_items <= 0) return cudaSuccess;
+  if (R.n_items_dev == nullptr || R.rep_half == nullptr || R.rep_end == nullptr) return cudaErrorInvalidValue;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -178,6 +178,7 @@ struct gbs_server {
   // never holds up the server thread, which keeps mu while it admits, builds
   // and completes steps.
   std::mutex rmu;
+  std::condition_variable rcv;                 // a result was added to done
   std::unordered_set<int64_t> pending;         // under rmu
   std::unordered_map<int64_t, Result> done;   // under rmu
   int64_t next_ticket = 1;
@@ -493,6 +494,7 @@ void fail_tickets(gbs_server* s, const std::vector<Request>& reqs, int rc) {
     s->done[q.ticket] = r;
     s->pending.erase(q.ticket);
   }
+  s->rcv.notify_all();
 }
 
 // Ordering probe (lock held): collect a finished probe launch, whose requests
@@ -681,6 +683,7 @@ void complete(gbs_server* s, Stage& g) {
     sl.used = false;
     sl.items.clear();
   }
+  s->rcv.notify_all();
   g.fin.clear();
   g.busy = false;
   s->last_done_step = std::max(s->last_done_step, g.id);
@@ -706,6 +709,7 @@ void fail_all(gbs_server* s, int rc) {
     s->done[t] = r;
   }
   s->pending.clear();
+  s->rcv.notify_all();
   s->queue.clear();
   s->probe_wait.clear();
   s->probing.clear();
@@ -1024,6 +1028,7 @@ extern "C" int gbs_serve_submit(gbs_server* s, const int* idx, int n, int precis
     r.err = 0.0;
     std::lock_guard<std::mutex> rl(s->rmu);
     s->done[t] = r;
+    s->rcv.notify_all();
     return GBS_OK;
   }
   if ((int)s->queue.size() >= s->o.queue_capacity) return fail(GBS_EAGAIN, "queue full");
@@ -1086,6 +1091,7 @@ extern "C" int gbs_serve_cancel(gbs_server* s, int64_t ticket) {
   s->done[ticket] = r;
   s->pending.erase(ticket);
   s->stats.cancelled++;
+  s->rcv.notify_all();
   s->cv.notify_all();
   return GBS_OK;
 }
@@ -1114,6 +1120,35 @@ extern "C" int gbs_serve_poll(gbs_server* s, int64_t ticket, double* p, double* 
   }
   if (err_est) *err_est = r.err;
   return 0;
+}
+
+extern "C" int gbs_serve_wait_any(gbs_server* s, double timeout_s, int max, int64_t* tickets, double* p,
+                                  double* haf_ri, double* err_est, int* rc, int* count) {
+  clear_error();
+  if (!s || !tickets || !count || max < 0 || !(timeout_s >= 0.0)) return fail(GBS_EINVAL, "invalid argument");
+  *count = 0;
+  std::unique_lock<std::mutex> lk(s->rmu);
+  if (s->done.empty() && !s->pending.empty() && timeout_s > 0.0) {
+    const auto until = std::chrono::steady_clock::now() +
+                       std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                           std::chrono::duration<double>(std::min(timeout_s, 1e6)));
+    s->rcv.wait_until(lk, until, [s] { return !s->done.empty() || s->pending.empty(); });
+  }
+  int k = 0;
+  for (auto it = s->done.begin(); it != s->done.end() && k < max; ++k) {
+    const Result& r = it->second;
+    tickets[k] = it->first;
+    if (p) p[k] = r.p;
+    if (haf_ri) {
+      haf_ri[2 * k] = r.hr;
+      haf_ri[2 * k + 1] = r.hi;
+    }
+    if (err_est) err_est[k] = r.err;
+    if (rc) rc[k] = r.rc;
+    it = s->done.erase(it);
+  }
+  *count = k;
+  return GBS_OK;
 }
 
 extern "C" int gbs_serve_stats(gbs_server* s, gbs_serve_stats_t* out) {

@@ -407,3 +407,46 @@ def test_serving_memory_budget_failures(gbs, kern):
     _, h_ref = batch_ref(gbs, K, small, gbs.FP64)
     for (p, h, e), hr in zip(res, h_ref):
         assert abs(h - hr) <= FP64_TOL * abs(hr)
+
+
+def test_serving_completion_queue(gbs, kern):
+    """gbs_serve_wait_any returns every finished request once, in any order,
+    with the same bits as gbs_serve_poll gives for the same request (a result
+    does not depend on the mix); a cancelled request comes back with
+    GBS_ECANCELED and NaN outputs; with nothing pending it returns at once."""
+    K, m = kern
+    pats = requests(m, 120, 33, n_values=range(2, 25))
+    srv = gbs.Server(K, subsets_per_step=256)
+    try:
+        alone = {i: wait_all(srv, [srv.submit(pats[i])])[0] for i in (0, 7, 50, 119)}
+        tickets = [srv.submit(x, gbs.FP64 if i % 2 == 0 else gbs.MIXED) for i, x in enumerate(pats)]
+        assert srv.cancel(tickets[5]) in (0, 1)
+        got = {}
+        t0 = time.time()
+        while len(got) < len(tickets):
+            tk, p, h, e, rc = srv.wait_any(0.5, max_results=16)
+            assert len(tk) <= 16
+            for j in range(len(tk)):
+                assert int(tk[j]) not in got
+                got[int(tk[j])] = (p[j], h[j], e[j], rc[j])
+            assert time.time() - t0 < 60.0, "serving did not finish"
+        t1 = time.perf_counter()
+        empty = srv.wait_any(5.0)
+        assert len(empty[0]) == 0 and time.perf_counter() - t1 < 1.0
+        with pytest.raises(gbs.GbsError) as ei:
+            srv.poll(tickets[3])  # collected by wait_any
+        assert ei.value.code == -7
+    finally:
+        srv.destroy()
+    assert set(got) == set(tickets)
+    p5, h5, e5, rc5 = got[tickets[5]]
+    assert rc5 in (0, -8) and (rc5 == 0 or np.isnan(p5))
+    for i, (p, h, e) in alone.items():
+        if i % 2 == 0:  # FP64 in the mix, as alone
+            q = got[tickets[i]]
+            assert q[3] == 0 and q[0] == p and q[1] == h, (i, q, p, h)
+    p_ref, h_ref = batch_ref(gbs, K, pats, gbs.FP64)
+    for i, t in enumerate(tickets):
+        if i == 5 or i % 2:
+            continue
+        assert got[t][3] == 0 and abs(got[t][1] - h_ref[i]) <= FP64_TOL * max(abs(h_ref[i]), 1e-300)

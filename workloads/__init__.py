@@ -153,12 +153,13 @@ def workload(name: str):
     return U, r, pats
 
 
-def serving_requests(count: int, seed: int = 3):
+def serving_requests(count: int, seed: int = 3, rate_hz: float = None):
     """Request stream of the serving workload: (arrival_s, index list) pairs,
-    n ~ Uniform{12..26}, collision-free, Poisson arrivals at 2000 req/s."""
+    n ~ Uniform{12..26}, collision-free, Poisson arrivals at 2000 req/s (or
+    rate_hz; the same lists in the same order at every rate)."""
     w = WORKLOADS["serving_m256"]
     rng = np.random.default_rng(seed + 300)
-    t = poisson_arrivals(w["rate_hz"], count, seed + 400)
+    t = poisson_arrivals(rate_hz or w["rate_hz"], count, seed + 400)
     reqs = []
     for i in range(count):
         n = int(rng.integers(12, 27))
