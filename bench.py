@@ -243,9 +243,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="arithmetic of the headline line (mixed: FP32 terms, compensated sums)")
+    ap.add_argument("--profile-workload", default=None, choices=["batched_m64_n16", "mixed_m144", "large_m900"],
+                    help="no bench line: run that workload's batch --warmup + --steps times in the given "
+                         "precision and print its mean time (the command profiler captures run)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.profile_workload:
+        return profile_workload(args)
 
     import torch
     import paper_1908_10070_gb300 as gbs
@@ -275,7 +280,7 @@ def main():
     prec = gbs.FP64 if args.precision == "fp64" else gbs.MIXED
 
     def step():
-        gbs.prob_batch(K, d_idx, n, offs, prec, p_out=p, logp_out=lp, haf_out=hf, err_out=er)
+        gbs.prob_batch(K, d_idx, n, offs, prec, stream=stream, p_out=p, logp_out=lp, haf_out=hf, err_out=er)
 
     # launch shape for n = 16 from the library's autotuner (untimed)
     tuned_rounds = gbs.autotune(16, prec)
@@ -373,7 +378,7 @@ def main():
         dist.destroy_process_group()
 
 
-def timed_batch(gbs, torch, K, pats, precision, reps=3):
+def timed_batch(gbs, torch, K, pats, precision, reps=3, warm=1):
     idx, n, offs = gbs.pack_patterns(pats)
     b = len(pats)
     d_idx = torch.from_numpy(idx).cuda()
@@ -383,7 +388,8 @@ def timed_batch(gbs, torch, K, pats, precision, reps=3):
     ks, ke = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ks.record()
     ke.record()
-    gbs.prob_batch(K, d_idx, n, offs, precision, p_out=p, haf_out=hf, err_out=er)
+    for _ in range(warm):
+        gbs.prob_batch(K, d_idx, n, offs, precision, p_out=p, haf_out=hf, err_out=er)
     torch.cuda.synchronize()
     ts, tk = [], []
     for _ in range(reps):
@@ -460,6 +466,25 @@ def oracle_rate(pats, U, r, target_s=6.0):
             "sample": "%d patterns (the workload's %d, in order, cycled), FP64 subset sum, %.1f s"
                       % (k2, len(pats), dt2),
             "single_core_value": k1 / dt1, "cpu": host_cpu()}
+
+
+def profile_workload(args):
+    """One workload's batch, device inputs, repeated: a small, self-contained
+    command for profiler captures (-s skips the warm-up launches)."""
+    import torch
+    import paper_1908_10070_gb300 as gbs
+
+    U, r, pats = W.workload(args.profile_workload)
+    prec = gbs.FP64 if args.precision == "fp64" else gbs.MIXED
+    K = gbs.build_kernel(U, r)
+    # the launch shapes the bench uses (the tuner launches the subset kernel
+    # 4 x 5 times per block shape that fits: 120 at n = 16, 40 at n = 28, 30)
+    tuned = {"batched_m64_n16": (16,), "mixed_m144": tuple(range(8, 25, 2)), "large_m900": (28, 30)}
+    for nn in tuned[args.profile_workload]:
+        gbs.autotune(nn, prec)
+    t = timed_batch(gbs, torch, K, pats, prec, reps=max(1, args.steps), warm=max(0, args.warmup))[0]
+    print(json.dumps({"workload": args.profile_workload, "precision": args.precision, "patterns": len(pats),
+                      "warmup": args.warmup, "steps": args.steps, "ms_per_batch": t}))
 
 
 def extras(gbs, torch, measured_peak):
@@ -721,7 +746,7 @@ def sustainable(row):
             and row["median_last_quarter_ms"] <= 2.0 * row["median_first_quarter_ms"] + 1.0)
 
 
-def saturation(gbs, K, dur_s=1.0, max_levels=9):
+def saturation(gbs, K, dur_s=1.0, max_levels=12):
     """Rising Poisson rates (x1.5 from 1000 req/s, about dur_s of requests
     each) until the stream is no longer sustained; the largest sustained rate
     for the FP64 server, the mixed server and plain per-pattern calls."""

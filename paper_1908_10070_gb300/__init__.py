@@ -106,15 +106,16 @@ def _check(rc):
 
 
 def _ptr(x):
-    """Address of a torch tensor / numpy array / None."""
+    """Address (int, or None) of a torch tensor / numpy array / None; the
+    c_void_p arguments take plain ints."""
     if x is None:
         return None
     if hasattr(x, "data_ptr"):
-        return ctypes.c_void_p(x.data_ptr())
+        return x.data_ptr() or None
     if isinstance(x, np.ndarray):
         if not x.flags["C_CONTIGUOUS"]:
             raise ValueError("numpy array must be C-contiguous")
-        return ctypes.c_void_p(x.ctypes.data)
+        return x.ctypes.data or None
     raise TypeError("unsupported buffer type %r" % type(x))
 
 
@@ -128,8 +129,8 @@ def _stream(stream):
             pass
         return None
     if hasattr(stream, "cuda_stream"):
-        return ctypes.c_void_p(stream.cuda_stream)
-    return ctypes.c_void_p(int(stream))
+        return stream.cuda_stream or None
+    return int(stream) or None
 
 
 def pack_patterns(patterns):
@@ -351,7 +352,8 @@ class Server:
     def cancel(self, ticket) -> int:
         """0: cancelled (its poll raises GBS_ECANCELED); 1: already finished."""
         rc = lib().gbs_serve_cancel(self.handle, int(ticket))
-        _check(rc)
+        if rc != 1:
+            _check(rc)
         return rc
 
     def stats(self) -> dict:

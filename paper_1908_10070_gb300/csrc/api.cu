@@ -198,11 +198,32 @@ TuneCfg default_cfg(int precision, int n) {
   return c;
 }
 
+// default_cfg per (precision, n), computed once (g_tune_mu held)
+static const TuneCfg& default_cfg_cached(int precision, int n) {
+  static TuneCfg table[2][kMaxN + 1];
+  static bool ready[2] = {false, false};
+  const int p = precision == GBS_FP64 ? 0 : 1;
+  if (!ready[p]) {
+    for (int v = 0; v <= kMaxN; ++v) table[p][v] = default_cfg(precision, v);
+    ready[p] = true;
+  }
+  return table[p][n < 0 ? 0 : (n > kMaxN ? kMaxN : n)];
+}
+
 TuneCfg get_cfg(int precision, int n) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto it = g_tuned.find(std::make_pair(precision, n));
   if (it != g_tuned.end()) return it->second;
-  return default_cfg(precision, n);
+  return default_cfg_cached(precision, n);
+}
+
+// Rounds per item for every order 0..kMaxN (one lock for all of them).
+static void get_rounds(int precision, int* rounds) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (int v = 0; v <= kMaxN; ++v) {
+    auto it = g_tuned.find(std::make_pair(precision, v));
+    rounds[v] = (it != g_tuned.end()) ? it->second.rounds : default_cfg_cached(precision, v).rounds;
+  }
 }
 
 void set_cfg(int precision, int n, const TuneCfg& c) {
@@ -639,30 +660,30 @@ int run_batch(const BatchArgs& a) {
   if (a.precision != GBS_FP64 && a.precision != GBS_MIXED)
     return fail(GBS_EINVAL, "precision must be GBS_FP64 or GBS_MIXED");
   BatchLayout U;
+  // checks, the largest order and the extent of the inputs (elements)
+  const bool hmode = (a.mode == BatchArgs::HAFNIAN);
+  int64_t elems = 0;
   for (int b = 0; b < batch; ++b) {
-    if (a.n[b] < 0) return fail(GBS_EINVAL, "n[%d] = %d is negative", b, a.n[b]);
-    if (a.n[b] > GBS_MAX_N) return fail(GBS_ERANGE, "n[%d] = %d exceeds GBS_MAX_N", b, a.n[b]);
+    const int v = a.n[b];
+    if (v < 0) return fail(GBS_EINVAL, "n[%d] = %d is negative", b, v);
+    if (v > GBS_MAX_N) return fail(GBS_ERANGE, "n[%d] = %d exceeds GBS_MAX_N", b, v);
     if (a.offs[b] < 0) return fail(GBS_EINVAL, "offs[%d] is negative", b);
-    U.maxn = std::max(U.maxn, a.n[b]);
+    U.maxn = std::max(U.maxn, v);
+    elems = std::max<int64_t>(elems, a.offs[b] + (hmode ? (int64_t)v * v : (int64_t)v));
   }
+  (hmode ? U.src_elems : U.idx_elems) = elems;
   const int maxn = U.maxn;
   // launch shape from the largest n (it dominates the cost); rounds per n
   U.cfg = a.cfg_override ? *a.cfg_override : get_cfg(a.precision, maxn);
   const TuneCfg& cfg = U.cfg;
   int rounds_for_n[kMaxN + 1];
-  for (int v = 0; v <= kMaxN; ++v)
-    rounds_for_n[v] = a.cfg_override ? a.cfg_override->rounds : get_cfg(a.precision, v).rounds;
-  if (!shape_fits(a.precision, cfg.warp_bytes, maxn))
-    return fail(GBS_EINVAL, "warp_bytes %d too small for n = %d", cfg.warp_bytes, maxn);
+  if (a.cfg_override)
+    for (int v = 0; v <= kMaxN; ++v) rounds_for_n[v] = a.cfg_override->rounds;
+  else
+    get_rounds(a.precision, rounds_for_n);
   const bool src_dev = (a.mode == BatchArgs::HAFNIAN) ? is_device_ptr(a.src) : true;
   const bool idx_dev = (a.mode == BatchArgs::PROB) ? is_device_ptr(a.idx) : true;
-  // sizes of the inputs; host inputs are checked and staged on every call
-  for (int b = 0; b < batch; ++b) {
-    if (a.mode == BatchArgs::HAFNIAN)
-      U.src_elems = std::max<int64_t>(U.src_elems, a.offs[b] + (int64_t)a.n[b] * a.n[b]);
-    else
-      U.idx_elems = std::max<int64_t>(U.idx_elems, a.offs[b] + a.n[b]);
-  }
+  // host inputs are checked and staged on every call
   if (a.mode == BatchArgs::HAFNIAN && U.src_elems > 0 && a.src == nullptr)
     return fail(GBS_EINVAL, "A_ri is null");
   if (a.mode == BatchArgs::PROB && U.idx_elems > 0 && a.idx == nullptr)
@@ -722,6 +743,9 @@ int run_batch(const BatchArgs& a) {
   int slot = -1;
   unsigned char* hs = nullptr;
   if (!hit) {
+    // (a kept plan's shape was checked when it was made)
+    if (!shape_fits(a.precision, cfg.warp_bytes, maxn))
+      return fail(GBS_EINVAL, "warp_bytes %d too small for n = %d", cfg.warp_bytes, maxn);
     Planner plan;
     // a few items per resident warp balance the load over all SMs; whole-matrix
     // items for all but a reserve of an order, whose per-size items fill the
@@ -1018,6 +1042,7 @@ int run_batch(const BatchArgs& a) {
         RP.rep_end = d_repend;
         RP.rep_total = d_ctr + 56;
         RP.blocks_done = (unsigned*)(d_ctr + 57);
+        RP.n_chosen = d_ctr + 59;
         e = launch_route_plan(RP, st);
         if (e != cudaSuccess) { ret = cuda_fail(e, "route choice launch"); break; }
         L.skip = d_rephalf;

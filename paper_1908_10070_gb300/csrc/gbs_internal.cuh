@@ -268,6 +268,7 @@ struct RoutePlan {
   int* rep_end;            // out, per pattern: end of its partial range (non-decreasing)
   int* rep_total;          // out: partial slots used (the repeated-row item count)
   unsigned* blocks_done;   // zero before launch
+  int* n_chosen;           // zero before launch: patterns given the repeated-row sum
 };
 
 // Defined in haf_subsets.cu

@@ -878,8 +878,8 @@ __global__ void chunk_sum_kernel(const ChunkLaunch C) {
 
 // One warp per pattern adds its item partials (or, after chunk_sum_kernel,
 // the chunk sums) and forms prod_j s_j! (each lane counts the earlier
-// occurrences of its index; the c-th occurrence of a mode contributes a
-// factor c). The sums go to shared memory and warp 0 finishes the block's
+// occurrences of its index among the other lanes' indices; the c-th
+// occurrence of a mode contributes a factor c). The sums go to shared memory and warp 0 finishes the block's
 // patterns one per lane (hypot, log, exp): that scalar tail costs one warp
 // instruction per block instead of one per pattern.
 constexpr int kFinWarps = 16;  // most warps in a finalisation block
@@ -890,8 +890,13 @@ __global__ void __launch_bounds__(kFinWarps * 32) finalize_kernel(const Finalize
   const int wpb = blockDim.x >> 5;
   const bool want_p = F.p_out || F.logp_out || F.err_out;
   const int batch = F.batch_dev ? *F.batch_dev : F.batch;
-  for (int base = blockIdx.x * wpb; base < batch; base += gridDim.x * wpb) {
-    const int b = base + warp;
+  // pattern of warp w in round `base`: base + w * gridDim.x + blockIdx.x, so
+  // that consecutive patterns (alike in their partial counts, which the batch
+  // order groups) fall into different blocks and SMs: the FP64 additions of
+  // patterns with many partials then spread over the device
+  const int nb = gridDim.x;
+  for (int base = 0; base < batch; base += nb * wpb) {
+    const int b = base + warp * nb + blockIdx.x;
     if (b < batch) {  // uniform over the warp
       const int pb = F.sel ? F.sel[b] : b;
       const PatDesc d = F.pats[pb];
@@ -913,11 +918,16 @@ __global__ void __launch_bounds__(kFinWarps * 32) finalize_kernel(const Finalize
       }
       // odd n: no perfect matching, Haf = 0 (Sec. 3.1: P_n = 0 for odd n)
       double fac = 1.0;
-      if (want_p && d.idx_off >= 0 && lane < n) {
-        const int xi = F.idx[d.idx_off + lane];
+      if (want_p && d.idx_off >= 0) {  // uniform over the warp
+        // one load per lane; the earlier occurrences come by shuffles
+        const int xi = (lane < n) ? F.idx[d.idx_off + lane] : -1 - lane;
         int c = 1;
-        for (int q = 0; q < lane; ++q) c += (F.idx[d.idx_off + q] == xi);
-        fac = (double)c;
+#pragma unroll
+        for (int q = 0; q < 31; ++q) {
+          const int v = __shfl_sync(FULL, xi, q);
+          c += (q < lane && v == xi) ? 1 : 0;
+        }
+        if (lane < n) fac = (double)c;
       }
       for (int off = 16; off > 0; off >>= 1) fac *= __shfl_xor_sync(FULL, fac, off);
       if (lane == 0) {
@@ -930,14 +940,18 @@ __global__ void __launch_bounds__(kFinWarps * 32) finalize_kernel(const Finalize
       }
     }
     __syncthreads();
-    if (warp == 0 && lane < wpb && base + lane < batch) {
-      const int bo = base + lane;
+    if (warp == 0 && lane < wpb && base + lane * nb + blockIdx.x < batch) {
+      const int bo = base + lane * nb + blockIdx.x;
       const int pb = F.sel ? F.sel[bo] : bo;
       const int n = F.pats[pb].n;
       const bool bad = F.status != nullptr && F.status[pb] != 0;
       const double hr = sv[0][lane] + sv[1][lane], hi = sv[2][lane] + sv[3][lane];
       const double K = sv[4][lane];
-      const double mod = hypot(hr, hi);
+      // |Haf| by a plain square root unless the squares could leave the
+      // normal range (hypot's scaling costs FP64 instructions on this part)
+      const double ar = fabs(hr), ai = fabs(hi);
+      const double big = fmax(ar, ai);
+      const double mod = (big < 0x1p500 && big > 0x1p-500) ? sqrt(hr * hr + hi * hi) : hypot(hr, hi);
       const double kappa = (mod > 0.0) ? K / mod : (K > 0.0 ? INFINITY : 0.0);
       const double nan = __longlong_as_double(0x7ff8000000000000ll);
       if (F.haf_out) {
@@ -947,8 +961,12 @@ __global__ void __launch_bounds__(kFinWarps * 32) finalize_kernel(const Finalize
       if (F.kappa_out) F.kappa_out[bo] = bad ? nan : kappa;
       if (want_p) {
         const double L = F.log_norm ? *F.log_norm : 0.0;
-        const double lf = log(sv[5][lane]);  // sum_j log s_j!
-        const double logp = (mod > 0.0) ? 2.0 * log(mod) - lf - L : -INFINITY;
+        // log p = log(|Haf|^2 / prod_j s_j!) - L: one logarithm while
+        // |Haf|^2 / prod s_j! is a normal number (else two)
+        const double q = (mod / sv[5][lane]) * mod;
+        const double logp = (mod > 0.0) ? ((q >= 0x1p-1022 && q <= 0x1p1023) ? log(q) - L
+                                                                          : 2.0 * log(mod) - log(sv[5][lane]) - L)
+                                        : -INFINITY;
         if (F.p_out) F.p_out[bo] = bad ? nan : ((mod > 0.0) ? exp(logp) : 0.0);
         if (F.logp_out) F.logp_out[bo] = bad ? nan : logp;
         if (F.err_out) F.err_out[bo] = bad ? nan : err_estimate(F.precision, n, kappa);
@@ -1198,16 +1216,23 @@ __device__ __forceinline__ void rep_terms(RepWarp& W, const int (*binom)[kMaxN +
 __global__ void __launch_bounds__(128) haf_repeated_kernel(const RepLaunch R) {
   __shared__ RepWarp ws[4];
   __shared__ int binom[kMaxN + 1][kMaxN + 1];
-  if (threadIdx.x == 0)
-    for (int a = 0; a <= kMaxN; ++a)
-      for (int b = 0; b <= kMaxN; ++b)
-        binom[a][b] = (b == 0) ? 1 : (a == 0 ? 0 : binom[a - 1][b - 1] + binom[a - 1][b]);
+  // the grid covers the reservation; with no item (no bunched pattern) every
+  // block leaves before building its table (uniform over the block)
+  const int n_items = min(*R.n_items_dev, R.n_items);
+  if (n_items <= 0) return;
+  if (threadIdx.x <= kMaxN) {  // row a = threadIdx.x: C(a, b) = C(a, b-1) (a-b+1) / b
+    const int a = threadIdx.x;
+    long long c = 1;
+    for (int b = 0; b <= kMaxN; ++b) {
+      binom[a][b] = (b <= a) ? (int)c : 0;
+      if (b < a) c = c * (a - b) / (b + 1);
+    }
+  }
   __syncthreads();
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   RepWarp& W = ws[threadIdx.x >> 5];
   const double2* src2 = reinterpret_cast<const double2*>(R.B);
-  const int n_items = min(*R.n_items_dev, R.n_items);
   for (;;) {
     int it = 0;
     if (lane == 0) it = atomicAdd(R.counter, 1);
@@ -1320,7 +1345,10 @@ __global__ void __launch_bounds__(256) route_plan_kernel(const RoutePlan R) {
         }
       }
     }
-    if (lane == 0) R.rep_half[b] = half;
+    if (lane == 0) {
+      R.rep_half[b] = half;
+      if (half > 0) atomicAdd(R.n_chosen, 1);
+    }
   }
   __shared__ int s_last, s_total;
   __shared__ long long s_warp[8], s_base;
@@ -1330,6 +1358,10 @@ __global__ void __launch_bounds__(256) route_plan_kernel(const RoutePlan R) {
   __syncthreads();
   if (!s_last) return;
   __threadfence();
+  if (__ldcg(R.n_chosen) == 0) {  // every pattern keeps the subset sum: no ranges to assign
+    if (threadIdx.x == 0) *R.rep_total = 0;
+    return;
+  }
   if (threadIdx.x == 0) {
     s_base = 0;
     s_total = 0;
