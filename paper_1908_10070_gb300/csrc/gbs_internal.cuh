@@ -108,24 +108,33 @@ __host__ __device__ inline int64_t pair_terms_elems(int n) {
 }
 
 // Per-warp staging of finished subsets' power traces (32 slots of stage_h
-// complex doubles plus 32 sign flags; the FP32 path's traces are staged in
-// double too); the exponential series then runs in FP64 with one subset per
-// lane. Slots are stage_stride(stage_h) entries apart, an odd number of
-// 16-byte entries, so that the eight lanes of a quarter-warp reading entry k of
-// their own slots touch eight different bank groups (at an even stride such as
-// 8 entries they all hit the same four banks).
+// complex values of the path's own type, plus 32 sign flags); the exponential
+// series then runs in FP64 with one subset per lane, the FP32 path's traces
+// converted there, all 32 lanes at once (a conversion to double runs on the
+// FP64 pipe, whose warp instructions cost the same with one active lane).
+// Slots are stage_stride(stage_h) entries apart, an odd number, so that the
+// lanes reading entry k of their own slots touch different bank groups (at an
+// even stride such as 8 entries they all hit the same few banks).
+// Matrices of order 2 stage_h >= 2 kStageHalfFrom stage 16 subsets at a time
+// instead of 32: their lane groups are large (one or two per warp for the
+// orders that dominate) and the shared memory saved holds more warps per SM,
+// while the series of their small subsets runs on half the lanes.
+constexpr int kStageHalfFrom = 13;
+__host__ __device__ inline int stage_slots(int stage_h) { return stage_h >= kStageHalfFrom ? 16 : 32; }
 __host__ __device__ inline int stage_stride(int stage_h) { return stage_h | 1; }
-__host__ __device__ inline int stage_bytes(int stage_h) {
-  return (32 * stage_stride(stage_h) * 16 + 32 * 4 + 15) & ~15;
+__host__ __device__ inline int stage_bytes(int stage_h, int cbytes) {
+  const int slots = stage_slots(stage_h);
+  return (slots * stage_stride(stage_h) * cbytes + slots * 4 + 15) & ~15;
 }
 
 // Lane-group size L (a power of two) for subsets of order N of a matrix of
 // order 2h: the smallest L whose 32/L groups fit the warp's bytes left after
-// the header and the staging area; 0 if none does.
+// the header and the staging area, and no more groups than staging slots; 0
+// if none does.
 __host__ __device__ inline int lanes_for(int N, int h, int warp_bytes, int stage_h, int cbytes) {
-  const int avail = warp_bytes - kWarpHeaderBytes - stage_bytes(stage_h);
+  const int avail = warp_bytes - kWarpHeaderBytes - stage_bytes(stage_h, cbytes);
   const int gb = group_bytes(N, h, cbytes);
-  for (int L = 1; L <= 32; L <<= 1)
+  for (int L = 32 / stage_slots(stage_h); L <= 32; L <<= 1)
     if ((32 / L) * gb <= avail) return L;
   return 0;
 }

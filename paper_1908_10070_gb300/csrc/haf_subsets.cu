@@ -500,11 +500,12 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
   const int n_items = P.n_items_dev ? *P.n_items_dev : P.n_items;
   unsigned char* wbase = smem + (size_t)warp * P.warp_bytes;
   int* xs = reinterpret_cast<int*>(wbase);
-  // staging: the power traces of up to 32 finished subsets, their signs and orders
-  double2* stP = reinterpret_cast<double2*>(wbase + kWarpHeaderBytes);
+  // staging: the power traces of up to `slots` finished subsets, their signs and orders
+  C* stP = reinterpret_cast<C*>(wbase + kWarpHeaderBytes);
   const int sts = stage_stride(P.stage_h);  // entries between two subsets' slots
-  int* stF = reinterpret_cast<int*>(stP + 32 * sts);
-  unsigned char* gbase = wbase + kWarpHeaderBytes + stage_bytes(P.stage_h);
+  const int slots = stage_slots(P.stage_h);  // subsets staged at most
+  int* stF = reinterpret_cast<int*>(stP + slots * sts);
+  unsigned char* gbase = wbase + kWarpHeaderBytes + stage_bytes(P.stage_h, cb);
   const double2* src2 = reinterpret_cast<const double2*>(P.src);
 
   for (;;) {
@@ -585,7 +586,18 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
     // compensated accumulation
     auto flush = [&]() {
       if (lane < staged) {
-        double2* pq = stP + lane * sts;
+        // the subset's traces in FP64: the staged ones (FP64 path), or a
+        // converted copy of the staged floats
+        double2 pconv[sizeof(T) == 8 ? 1 : kMaxH];
+        double2* pq;
+        if constexpr (sizeof(T) == 8) {
+          pq = stP + lane * sts;
+        } else {
+          const C* ps = stP + lane * sts;
+#pragma unroll 1
+          for (int k = 0; k < h; ++k) pconv[k] = make_double2((double)ps[k].x, (double)ps[k].y);
+          pq = pconv;
+        }
         const int sv = stF[lane];
         const int Nl = sv < 0 ? -sv : sv;  // traces taken directly (the subset's order N when < h)
         // the loops run exact trip counts (not unrolled to the largest
@@ -656,7 +668,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
     const int rounds = (count + G - 1) / G;
 
     for (int rd = 0; rd < rounds; ++rd) {
-      if (staged + G > 32) flush();  // only when the group count changed between sizes
+      if (staged + G > slots) flush();  // only when the group count changed between sizes
       const int jsub = rd * G + g;
       const bool active = jsub < count;
       // -- unrank the subset (colex): rank = sum_i C(c_i, i), c_1 < ... < c_s;
@@ -713,7 +725,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
       //    time (one waits in registers for the next)
       C pend_v = mk<T>(T(0), T(0));
       int pend_k = 0;  // 0: none waiting
-      double2* const strow = stP + (staged + g) * sts;
+      C* const strow = stP + (staged + g) * sts;
       for (int o = 0; o < kMaxOps; ++o) {
         const SchedOp op = c_sched[hs][o];
         if (op.kind == kEnd) break;
@@ -739,14 +751,14 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
                    : (op.a == op.b) ? tr2sq_full(buf + op.a * NP, N, l, L)
                                     : tr2_full(buf + op.a * NP, buf + op.b * NP, N, l, L);
           if (L == 1) {
-            strow[op.k - 1] = make_double2(part.x, part.y);
+            strow[op.k - 1] = part;
           } else if (pend_k == 0) {
             pend_v = part;
             pend_k = op.k;
           } else {
             const C t = group_sum2<T>(pend_v, part, l, L);
-            if (l == 0) strow[pend_k - 1] = make_double2(t.x, t.y);
-            if (l == (L >> 1)) strow[op.k - 1] = make_double2(t.x, t.y);
+            if (l == 0) strow[pend_k - 1] = t;
+            if (l == (L >> 1)) strow[op.k - 1] = t;
             pend_k = 0;
           }
         }
@@ -754,15 +766,15 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
       }
       if (pend_k != 0) {  // uniform over the warp
         const C t = group_sum<T>(pend_v, L);
-        if (l == 0) strow[pend_k - 1] = make_double2(t.x, t.y);
+        if (l == 0) strow[pend_k - 1] = t;
       }
       // sign (-1)^{h-s} times the number of traces taken directly (< h: the
       // series step extends them; 0: no subset in this slot)
       if (l == 0) stF[staged + g] = active ? (((h - s) & 1) ? -hs : hs) : 0;
       staged += G;
       __syncwarp();
-      // -- once 32 subsets are staged, or the item ends
-      if (staged == 32 || (rd == rounds - 1 && s == s_last)) flush();
+      // -- once the staging slots are full, or the item ends
+      if (staged == slots || (rd == rounds - 1 && s == s_last)) flush();
     }
    }
 
