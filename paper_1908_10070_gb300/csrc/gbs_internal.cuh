@@ -111,7 +111,8 @@ __host__ __device__ inline int64_t pair_terms_elems(int n) {
 // complex values of the path's own type, plus 32 sign flags); the exponential
 // series then runs in FP64 with one subset per lane, the FP32 path's traces
 // converted there, all 32 lanes at once (a conversion to double runs on the
-// FP64 pipe, whose warp instructions cost the same with one active lane).
+// FP64 pipe, whose warp instructions cost the same with one active lane),
+// into the lane groups' region, which no subset uses between rounds.
 // Slots are stage_stride(stage_h) entries apart, an odd number, so that the
 // lanes reading entry k of their own slots touch different bank groups (at an
 // even stride such as 8 entries they all hit the same few banks).
@@ -133,6 +134,9 @@ __host__ __device__ inline int stage_bytes(int stage_h, int cbytes) {
 // if none does.
 __host__ __device__ inline int lanes_for(int N, int h, int warp_bytes, int stage_h, int cbytes) {
   const int avail = warp_bytes - kWarpHeaderBytes - stage_bytes(stage_h, cbytes);
+  // the FP32 path's series converts the staged traces to double in the lane
+  // groups' region (free between rounds): it must hold every slot in double
+  if (cbytes == 8 && avail < stage_slots(stage_h) * stage_stride(stage_h) * 16) return 0;
   const int gb = group_bytes(N, h, cbytes);
   for (int L = 32 / stage_slots(stage_h); L <= 32; L <<= 1)
     if ((32 / L) * gb <= avail) return L;

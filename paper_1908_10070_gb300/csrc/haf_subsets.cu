@@ -586,17 +586,17 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
     // compensated accumulation
     auto flush = [&]() {
       if (lane < staged) {
-        // the subset's traces in FP64: the staged ones (FP64 path), or a
-        // converted copy of the staged floats
-        double2 pconv[sizeof(T) == 8 ? 1 : kMaxH];
+        // the subset's traces in FP64: the staged ones (FP64 path), or the
+        // staged floats converted into the lane groups' region (free between
+        // rounds; the host's shape check keeps room for every slot there)
         double2* pq;
         if constexpr (sizeof(T) == 8) {
           pq = stP + lane * sts;
         } else {
           const C* ps = stP + lane * sts;
+          pq = reinterpret_cast<double2*>(gbase) + lane * sts;
 #pragma unroll 1
-          for (int k = 0; k < h; ++k) pconv[k] = make_double2((double)ps[k].x, (double)ps[k].y);
-          pq = pconv;
+          for (int k = 0; k < h; ++k) pq[k] = make_double2((double)ps[k].x, (double)ps[k].y);
         }
         const int sv = stF[lane];
         const int Nl = sv < 0 ? -sv : sv;  // traces taken directly (the subset's order N when < h)
