@@ -724,3 +724,28 @@ def test_autotune_shape_fits_and_agrees(gbs, n_):
     assert np.all(rel(after, before) <= FP64_TOL)
     assert np.all(rel(after, ref[sel]) <= FP64_TOL) and np.all(rel(before, ref[sel]) <= FP64_TOL)
     assert np.all(rel(after, ref[sel]) <= er)
+
+
+def test_float_probe_picks_the_fp64_probes_ordering(gbs):
+    """At n >= 26 gbs_prob_batch ranks the 16 candidate orderings with the
+    float kernel over the kernel's float copy of B, gbs_hafnian_batch with the
+    FP64 kernel over the explicit matrices B_x. Both read the same entries and
+    then run the same FP64 subset sum, so where they choose the same ordering
+    they give the same Hafnian and the same cancellation ratio kappa: checked
+    on n = 28 and n = 30 instances of the large batch (the gbs_autotune runs
+    at n = 28 cover the probe under an explicit launch shape)."""
+    U, r, pats = W.workload("large_m900")
+    m = U.shape[0]
+    K = kernel_for(gbs, U, r)
+    sel = [0, 1, 2, 3, 64, 65]
+    xs = [pats[i] for i in sel]
+    _, _, hp, ep = run_prob(gbs, K, xs, 0)
+    Bg = torch.zeros(2 * m * m, dtype=torch.float64, device="cuda")
+    K.copy_B(Bg)
+    torch.cuda.synchronize()
+    B = Bg.cpu().numpy().view(np.complex128).reshape(m, m)
+    hh, kh = run_haf(gbs, [B[np.ix_(x, x)] for x in xs], 0)
+    n = np.array([len(x) for x in xs], dtype=float)
+    kp = ep / (n * 2.0 ** -53)  # err_est = n u kappa
+    assert np.all(np.abs(kp / kh - 1.0) <= 1e-12), (kp, kh)
+    assert np.all(rel(hp, hh) <= 1e-14), (hp, hh)
