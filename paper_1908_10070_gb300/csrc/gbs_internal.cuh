@@ -83,11 +83,13 @@ __host__ __device__ inline int sched_nbuf(int hs) { return (int)((0x496b7236da44
 // half photon number h) with complex elements of `cbytes` bytes: the
 // matrices its schedule row holds at once (FP64: packed upper triangles of
 // N(N+1)/2 entries; FP32: full N x N tiles, whose rows the products read as
-// float4 pairs), N row indices and, for FP64, the N/2 pair numbers of the
-// subset.
-__host__ __device__ inline int group_bytes(int N, int h, int cbytes) {
+// float4 pairs), with `spare` one more tile (FP32: the next subset's A_S is
+// copied into it while the current one's products run), N row indices and,
+// for FP64, the N/2 pair numbers of the subset.
+__host__ __device__ inline int group_bytes(int N, int h, int cbytes, bool spare = false) {
   const int P = (cbytes == 16) ? N * (N + 1) / 2 : N * N;
-  const int bytes = sched_nbuf(sched_row(N, h, cbytes)) * P * cbytes + N * 4 + (cbytes == 16 ? N * 2 : 0);
+  const int mats = sched_nbuf(sched_row(N, h, cbytes)) + (spare ? 1 : 0);
+  const int bytes = mats * P * cbytes + N * 4 + (cbytes == 16 ? N * 2 : 0);
   return (bytes + 15) & ~15;
 }
 
@@ -111,8 +113,7 @@ __host__ __device__ inline int64_t pair_terms_elems(int n) {
 // complex values of the path's own type, plus 32 sign flags); the exponential
 // series then runs in FP64 with one subset per lane, the FP32 path's traces
 // converted there, all 32 lanes at once (a conversion to double runs on the
-// FP64 pipe, whose warp instructions cost the same with one active lane),
-// into the lane groups' region, which no subset uses between rounds.
+// FP64 pipe, whose warp instructions cost the same with one active lane).
 // Slots are stage_stride(stage_h) entries apart, an odd number, so that the
 // lanes reading entry k of their own slots touch different bank groups (at an
 // even stride such as 8 entries they all hit the same few banks).
@@ -134,13 +135,21 @@ __host__ __device__ inline int stage_bytes(int stage_h, int cbytes) {
 // if none does.
 __host__ __device__ inline int lanes_for(int N, int h, int warp_bytes, int stage_h, int cbytes) {
   const int avail = warp_bytes - kWarpHeaderBytes - stage_bytes(stage_h, cbytes);
-  // the FP32 path's series converts the staged traces to double in the lane
-  // groups' region (free between rounds): it must hold every slot in double
-  if (cbytes == 8 && avail < stage_slots(stage_h) * stage_stride(stage_h) * 16) return 0;
   const int gb = group_bytes(N, h, cbytes);
   for (int L = 32 / stage_slots(stage_h); L <= 32; L <<= 1)
     if ((32 / L) * gb <= avail) return L;
   return 0;
+}
+
+// FP32 lane groups take the spare tile where the warp's shared memory holds
+// it for all 32/L groups at the size lanes_for chose without it (the group
+// count, which the host plans with, never changes).
+__host__ __device__ inline bool spare_tile(int N, int h, int warp_bytes, int stage_h, int cbytes) {
+  if (cbytes != 8) return false;
+  const int L = lanes_for(N, h, warp_bytes, stage_h, cbytes);
+  if (L == 0) return false;
+  const int avail = warp_bytes - kWarpHeaderBytes - stage_bytes(stage_h, cbytes);
+  return (32 / L) * group_bytes(N, h, cbytes, true) <= avail;
 }
 
 struct HafLaunch {

@@ -145,6 +145,17 @@ __constant__ SchedOp c_sched[kMaxH + 1][kMaxOps] = {
     {{kProd, 1, 0, 0}, {kTr1, 1, 0, 0}, {kTr1, 2, 1, 0}, {kTr2, 4, 1, 1}, {kProd, 2, 1, 0}, {kTr1, 3, 2, 0}, {kTr2, 6, 2, 2}, {kProd, 3, 2, 1}, {kTr1, 5, 3, 0}, {kTr2, 10, 3, 3}, {kProd, 0, 3, 1}, {kTr1, 7, 0, 0}, {kTr2, 9, 0, 1}, {kTr2, 12, 0, 3}, {kTr2, 14, 0, 0}, {kProd, 1, 3, 2}, {kTr1, 8, 1, 0}, {kTr2, 11, 1, 2}, {kTr2, 13, 1, 3}, {kTr2, 15, 1, 0}, {kTr2, 16, 1, 1}, {kEnd, 0, 0, 0}},  // h = 16
 };
 
+// Asynchronous 8-byte copy global -> shared (cp.async, bypassing registers);
+// zero = true writes zeros and reads nothing. Completed copies are visible to
+// the issuing thread after cp_async_wait_all, to the rest of the warp after a
+// __syncwarp that follows it.
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc, bool zero) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gsrc), "r"(zero ? 0 : 8) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // Position of entry (r, c) of a symmetric N x N matrix stored as its packed
 // upper triangle, rows in order: row r holds columns r..N-1.
 __device__ __forceinline__ int tri_off(int r, int N) { return r * N - ((r * (r - 1)) >> 1); }
@@ -587,16 +598,17 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
     auto flush = [&]() {
       if (lane < staged) {
         // the subset's traces in FP64: the staged ones (FP64 path), or the
-        // staged floats converted into the lane groups' region (free between
-        // rounds; the host's shape check keeps room for every slot there)
+        // staged floats converted into a per-lane array (the lane groups'
+        // region may be receiving the next subset's A_S)
+        double2 pconv[sizeof(T) == 8 ? 1 : kMaxH];
         double2* pq;
         if constexpr (sizeof(T) == 8) {
           pq = stP + lane * sts;
         } else {
           const C* ps = stP + lane * sts;
-          pq = reinterpret_cast<double2*>(gbase) + lane * sts;
 #pragma unroll 1
-          for (int k = 0; k < h; ++k) pq[k] = make_double2((double)ps[k].x, (double)ps[k].y);
+          for (int k = 0; k < h; ++k) pconv[k] = make_double2((double)ps[k].x, (double)ps[k].y);
+          pq = pconv;
         }
         const int sv = stF[lane];
         const int Nl = sv < 0 ? -sv : sv;  // traces taken directly (the subset's order N when < h)
@@ -659,67 +671,98 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
     const int L = lanes_for(N, h, P.warp_bytes, P.stage_h, cb);
     const int G = 32 / L;
     const int g = lane / L, l = lane - g * L;
-    C* buf = reinterpret_cast<C*>(gbase + (size_t)g * group_bytes(N, h, cb));
-    int* rowidx = reinterpret_cast<int*>(buf + sched_nbuf(sched_row(N, h, cb)) * NP);
+    // FP32 path on the float copy of B, where the spare tile fits: the next
+    // round's A_S is copied into it (cp.async) while this round's products
+    // run, and the two tiles take turns as R_1
+    const bool pf = (sizeof(T) == 4) && src32p != nullptr && spare_tile(N, h, P.warp_bytes, P.stage_h, cb);
+    C* buf = reinterpret_cast<C*>(gbase + (size_t)g * group_bytes(N, h, cb, pf));
+    const int nb = sched_nbuf(hs);  // matrices of the schedule row
+    int* rowidx = reinterpret_cast<int*>(buf + (nb + (pf ? 1 : 0)) * NP);
     int* pairs = rowidx + N;  // FP64: the subset's pair numbers, increasing
     const int count = whole ? tab.binom[h][s] : w.count;
     const int rank0 = whole ? 0 : w.rank0;
     const int stride = (!whole && w.stride > 1) ? w.stride : 1;
     const int rounds = (count + G - 1) / G;
 
+    // -- unrank subset jsub of round rdx (colex): rank = sum_i C(c_i, i),
+    //    c_1 < ... < c_s; every lane of the group walks all of it and keeps
+    //    its pair mask
+    auto unrank = [&](int rdx) -> unsigned {
+      const int js = rdx * G + g;
+      unsigned msk = 0;
+      int r = rank0 + (js < count ? js : 0) * stride;
+      int c = h - 1;
+      for (int i = s; i >= 1; --i) {
+        while (tab.binom[c][i] > r) --c;
+        r -= tab.binom[c][i];
+        const int t = i - 1;
+        if ((t % L) == l) {
+          rowidx[2 * t] = xs[2 * c];
+          rowidx[2 * t + 1] = xs[2 * c + 1];
+          if (sizeof(T) == 8) pairs[t] = c;
+        }
+        msk |= 1u << c;
+        --c;
+      }
+      return msk;
+    };
+
     for (int rd = 0; rd < rounds; ++rd) {
       if (staged + G > slots) flush();  // only when the group count changed between sizes
       const int jsub = rd * G + g;
       const bool active = jsub < count;
-      // -- unrank the subset (colex): rank = sum_i C(c_i, i), c_1 < ... < c_s;
-      //    every lane of the group walks all of it and keeps its pair mask
+      const int cur = (pf && (rd & 1)) ? nb : 0;  // the tile holding this round's R_1
       unsigned smask = 0;
-      {
-        int r = rank0 + (active ? jsub : 0) * stride;
-        int c = h - 1;
-        for (int i = s; i >= 1; --i) {
-          while (tab.binom[c][i] > r) --c;
-          r -= tab.binom[c][i];
-          const int t = i - 1;
-          if ((t % L) == l) {
-            rowidx[2 * t] = xs[2 * c];
-            rowidx[2 * t + 1] = xs[2 * c + 1];
-            if (sizeof(T) == 8) pairs[t] = c;
-          }
-          smask |= 1u << c;
-          --c;
-        }
-      }
-      __syncwarp();
-      // -- R_1 = A_S (packed upper triangle). Its diagonal is set to zero: no
-      //    perfect matching uses V(i, i), and a zero diagonal lowers the
-      //    cancellation of the signed sum (collision entries B(x_i, x_i) with
-      //    i != j are off the diagonal of B_x and are kept).
-      if (sizeof(T) == 8) {
-        int i = 0, j = l;
-        tri_advance(i, j, 0, N);
-        for (int e = l; e < NP; e += L) {
-          const double2 v = (i == j) ? make_double2(0.0, 0.0)
-                                     : __ldg(srcp + (int64_t)rowidx[i] * d.ld + rowidx[j]);
-          buf[e] = mk<T>((T)v.x, (T)v.y);
-          tri_advance(i, j, L, N);
-        }
-      } else if (src32p) {
-        for (int e = l; e < NP; e += L) {
-          const int i = e / N, j = e - i * N;
-          const float2 v = (i == j) ? make_float2(0.f, 0.f)
-                                    : __ldg(src32p + (int64_t)rowidx[i] * d.ld + rowidx[j]);
-          buf[e] = mk<T>((T)v.x, (T)v.y);
-        }
+      if (pf && rd > 0) {
+        cp_async_wait_all();  // this round's A_S, copied during the last round
+        __syncwarp();
       } else {
+        smask = unrank(rd);
+        __syncwarp();
+        // -- R_1 = A_S (packed upper triangle). Its diagonal is set to zero: no
+        //    perfect matching uses V(i, i), and a zero diagonal lowers the
+        //    cancellation of the signed sum (collision entries B(x_i, x_i) with
+        //    i != j are off the diagonal of B_x and are kept).
+        if (sizeof(T) == 8) {
+          int i = 0, j = l;
+          tri_advance(i, j, 0, N);
+          for (int e = l; e < NP; e += L) {
+            const double2 v = (i == j) ? make_double2(0.0, 0.0)
+                                       : __ldg(srcp + (int64_t)rowidx[i] * d.ld + rowidx[j]);
+            buf[e] = mk<T>((T)v.x, (T)v.y);
+            tri_advance(i, j, L, N);
+          }
+        } else if (src32p) {
+          for (int e = l; e < NP; e += L) {
+            const int i = e / N, j = e - i * N;
+            const float2 v = (i == j) ? make_float2(0.f, 0.f)
+                                      : __ldg(src32p + (int64_t)rowidx[i] * d.ld + rowidx[j]);
+            buf[e] = mk<T>((T)v.x, (T)v.y);
+          }
+        } else {
+          for (int e = l; e < NP; e += L) {
+            const int i = e / N, j = e - i * N;
+            const double2 v = (i == j) ? make_double2(0.0, 0.0)
+                                       : __ldg(srcp + (int64_t)rowidx[i] * d.ld + rowidx[j]);
+            buf[e] = mk<T>((T)v.x, (T)v.y);
+          }
+        }
+        __syncwarp();
+      }
+      if (pf && rd + 1 < rounds) {
+        // the next round's rows (this round's A_S is in place), then its A_S
+        // into the other tile, in flight during the products below
+        unrank(rd + 1);
+        __syncwarp();
+        C* nxt = buf + (cur == 0 ? nb : 0) * NP;
         for (int e = l; e < NP; e += L) {
           const int i = e / N, j = e - i * N;
-          const double2 v = (i == j) ? make_double2(0.0, 0.0)
-                                     : __ldg(srcp + (int64_t)rowidx[i] * d.ld + rowidx[j]);
-          buf[e] = mk<T>((T)v.x, (T)v.y);
+          cp_async8(nxt + e, src32p + (int64_t)rowidx[i] * d.ld + rowidx[j], i == j);
         }
+        cp_async_commit();
       }
-      __syncwarp();
+      // schedule matrix b lives in tile b, except R_1's (b = 0): tile cur
+      auto bp = [&](int b) -> C* { return buf + (b == 0 ? cur : b) * NP; };
       // -- power traces tr((X A_S)^k), k = 1..hs, by the schedule for hs; the
       //    lanes' partial traces are summed over the group two traces at a
       //    time (one waits in registers for the next)
@@ -733,23 +776,23 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
           if constexpr (sizeof(T) == 8) {
             if (ptp != nullptr && op.k == 1 && op.a == 0 && op.b == 0) {
               const int hl = pair_split_lo(h);
-              pair_sum(buf + NP, ptp, pairs, N, NP, pair_sums_width(h), n, (int)(smask & ((1u << hl) - 1)),
+              pair_sum(bp(1), ptp, pairs, N, NP, pair_sums_width(h), n, (int)(smask & ((1u << hl) - 1)),
                        (1 << hl) + (int)(smask >> hl), l, L);
             }
             else
-              sym_prod<T>(buf + op.k * NP, buf + op.a * NP, buf + op.b * NP, N, NP, l, L);
+              sym_prod<T>(bp(op.k), bp(op.a), bp(op.b), N, NP, l, L);
           } else
-            sym_prod_full(buf + op.k * NP, buf + op.a * NP, buf + op.b * NP, N, l, L);
+            sym_prod_full(bp(op.k), bp(op.a), bp(op.b), N, l, L);
         } else {
           C part;
           if constexpr (sizeof(T) == 8)
-            part = (op.kind == kTr1)  ? tr1_part<T>(buf + op.a * NP, N, l, L)
-                   : (op.a == op.b) ? tr2sq_part<T>(buf + op.a * NP, N, l, L)
-                                    : tr2_part<T>(buf + op.a * NP, buf + op.b * NP, N, NP, l, L);
+            part = (op.kind == kTr1)  ? tr1_part<T>(bp(op.a), N, l, L)
+                   : (op.a == op.b) ? tr2sq_part<T>(bp(op.a), N, l, L)
+                                    : tr2_part<T>(bp(op.a), bp(op.b), N, NP, l, L);
           else
-            part = (op.kind == kTr1)  ? tr1_full(buf + op.a * NP, N, l, L)
-                   : (op.a == op.b) ? tr2sq_full(buf + op.a * NP, N, l, L)
-                                    : tr2_full(buf + op.a * NP, buf + op.b * NP, N, l, L);
+            part = (op.kind == kTr1)  ? tr1_full(bp(op.a), N, l, L)
+                   : (op.a == op.b) ? tr2sq_full(bp(op.a), N, l, L)
+                                    : tr2_full(bp(op.a), bp(op.b), N, l, L);
           if (L == 1) {
             strow[op.k - 1] = part;
           } else if (pend_k == 0) {
