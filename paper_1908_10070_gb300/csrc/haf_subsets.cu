@@ -595,21 +595,8 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
     // the exponential series e_k = (1/(2k)) sum_j tr_j e_{k-j}, f = e_h, in
     // FP64 for both paths (one staged subset per lane), and the signed
     // compensated accumulation
-    auto flush = [&]() {
-      if (lane < staged) {
-        // the subset's traces in FP64: the staged ones (FP64 path), or the
-        // staged floats converted into a per-lane array (the lane groups'
-        // region may be receiving the next subset's A_S)
-        double2 pconv[sizeof(T) == 8 ? 1 : kMaxH];
-        double2* pq;
-        if constexpr (sizeof(T) == 8) {
-          pq = stP + lane * sts;
-        } else {
-          const C* ps = stP + lane * sts;
-#pragma unroll 1
-          for (int k = 0; k < h; ++k) pconv[k] = make_double2((double)ps[k].x, (double)ps[k].y);
-          pq = pconv;
-        }
+    // (pq: this lane's subset's traces in FP64)
+    auto series = [&](double2* pq) {
         const int sv = stF[lane];
         const int Nl = sv < 0 ? -sv : sv;  // traces taken directly (the subset's order N when < h)
         // the loops run exact trip counts (not unrolled to the largest
@@ -654,6 +641,30 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
           comp_add<double>(acc_re, sg > 0 ? f.x : -f.x);
           comp_add<double>(acc_im, sg > 0 ? f.y : -f.y);
           kap += fabs(f.x) + fabs(f.y);
+        }
+    };
+    // The FP32 path converts its staged traces into the lane groups' region
+    // when no copy is in flight there (region_free) and the region holds
+    // every slot in double, else into a per-lane array.
+    const bool conv_fits =
+        (sizeof(T) == 4) && (P.warp_bytes - kWarpHeaderBytes - stage_bytes(P.stage_h, cb) >= slots * sts * 16);
+    auto flush = [&](bool region_free) {
+      if (lane < staged) {
+        if constexpr (sizeof(T) == 8) {
+          series(stP + lane * sts);
+        } else {
+          const C* ps = stP + lane * sts;
+          if (region_free && conv_fits) {
+            double2* q = reinterpret_cast<double2*>(gbase) + lane * sts;
+#pragma unroll 1
+            for (int k = 0; k < h; ++k) q[k] = make_double2((double)ps[k].x, (double)ps[k].y);
+            series(q);
+          } else {
+            double2 pconv[kMaxH];
+#pragma unroll 1
+            for (int k = 0; k < h; ++k) pconv[k] = make_double2((double)ps[k].x, (double)ps[k].y);
+            series(pconv);
+          }
         }
       }
       staged = 0;
@@ -708,7 +719,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
     };
 
     for (int rd = 0; rd < rounds; ++rd) {
-      if (staged + G > slots) flush();  // only when the group count changed between sizes
+      if (staged + G > slots) flush(!(pf && rd > 0));  // only when the group count changed between sizes
       const int jsub = rd * G + g;
       const bool active = jsub < count;
       const int cur = (pf && (rd & 1)) ? nb : 0;  // the tile holding this round's R_1
@@ -817,7 +828,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
       staged += G;
       __syncwarp();
       // -- once the staging slots are full, or the item ends
-      if (staged == slots || (rd == rounds - 1 && s == s_last)) flush();
+      if (staged == slots || (rd == rounds - 1 && s == s_last)) flush(!(pf && rd + 1 < rounds));
     }
    }
 
