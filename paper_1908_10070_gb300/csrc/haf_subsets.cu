@@ -596,14 +596,13 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
     // FP64 for both paths (one staged subset per lane), and the signed
     // compensated accumulation
     // (pq: this lane's subset's traces in FP64)
-    auto series = [&](double2* pq) {
+    auto series = [&](double2* pq, double2* dk) {
         const int sv = stF[lane];
         const int Nl = sv < 0 ? -sv : sv;  // traces taken directly (the subset's order N when < h)
         // the loops run exact trip counts (not unrolled to the largest
         // order): terms past h or N would be issued predicated off and still
         // hold the FP64 pipe, whose warp instructions occupy it for many
         // cycles on this part
-        double2 dk[kMaxH];  // d_1..d_N, then e_1..e_{h-1}
         if (Nl > 0 && Nl < h) {
           // an order-N subset has traces 1..N only: det(I - xM) = sum_i d_i x^i
           // has degree N, so by Newton's identities d_k = -(1/k) sum_{i<=k}
@@ -646,24 +645,29 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
     // The FP32 path converts its staged traces into the lane groups' region
     // when no copy is in flight there (region_free) and the region holds
     // every slot in double, else into a per-lane array.
-    const bool conv_fits =
-        (sizeof(T) == 4) && (P.warp_bytes - kWarpHeaderBytes - stage_bytes(P.stage_h, cb) >= slots * sts * 16);
+    const int region = P.warp_bytes - kWarpHeaderBytes - stage_bytes(P.stage_h, cb);
+    const bool conv_fits = (sizeof(T) == 4) && region >= slots * sts * 16;
+    const bool conv2_fits = (sizeof(T) == 4) && region >= 2 * slots * sts * 16;
     auto flush = [&](bool region_free) {
       if (lane < staged) {
+        double2 dk[kMaxH];  // d_1..d_N, then e_1..e_{h-1}
         if constexpr (sizeof(T) == 8) {
-          series(stP + lane * sts);
+          series(stP + lane * sts, dk);
         } else {
           const C* ps = stP + lane * sts;
           if (region_free && conv_fits) {
             double2* q = reinterpret_cast<double2*>(gbase) + lane * sts;
 #pragma unroll 1
             for (int k = 0; k < h; ++k) q[k] = make_double2((double)ps[k].x, (double)ps[k].y);
-            series(q);
+            if (conv2_fits)  // the coefficients beside them
+              series(q, reinterpret_cast<double2*>(gbase) + (slots + lane) * sts);
+            else
+              series(q, dk);
           } else {
             double2 pconv[kMaxH];
 #pragma unroll 1
             for (int k = 0; k < h; ++k) pconv[k] = make_double2((double)ps[k].x, (double)ps[k].y);
-            series(pconv);
+            series(pconv, dk);
           }
         }
       }
