@@ -699,33 +699,51 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
     const int stride = (!whole && w.stride > 1) ? w.stride : 1;
     const int rounds = (count + G - 1) / G;
 
-    // -- unrank subset jsub of round rdx (colex): rank = sum_i C(c_i, i),
-    //    c_1 < ... < c_s; every lane of the group walks all of it and keeps
-    //    its pair mask
-    auto unrank = [&](int rdx) -> unsigned {
-      const int js = rdx * G + g;
+    // Group g takes the subsets numbered g * rounds .. g * rounds + rounds - 1
+    // of the item (those below count), one per round. A subset's pair mask
+    // comes from its colex rank, rank = sum_i C(c_i, i) over its pairs
+    // c_1 < ... < c_s (every lane of the group walks it); with stride 1 the
+    // next round's mask is the next larger one with s bits (consecutive colex
+    // ranks), which costs a few integer operations instead of the walk.
+    auto mask_of = [&](int js) -> unsigned {
       unsigned msk = 0;
       int r = rank0 + (js < count ? js : 0) * stride;
       int c = h - 1;
       for (int i = s; i >= 1; --i) {
         while (tab.binom[c][i] > r) --c;
         r -= tab.binom[c][i];
-        const int t = i - 1;
-        if ((t % L) == l) {
-          rowidx[2 * t] = xs[2 * c];
-          rowidx[2 * t + 1] = xs[2 * c + 1];
-          if (sizeof(T) == 8) pairs[t] = c;
-        }
         msk |= 1u << c;
         --c;
       }
       return msk;
     };
+    unsigned gmask = 0;  // the mask of the group's latest subset
+    // mask of round rdx's subset (rounds in order) and its rows: position t
+    // of the subset is its t-th pair in increasing order
+    auto unrank = [&](int rdx) -> unsigned {
+      const int js = g * rounds + rdx;
+      if (rdx == 0 || stride != 1) {
+        gmask = mask_of(js);
+      } else if (js < count) {
+        const unsigned u = gmask & (0u - gmask), v = gmask + u;
+        gmask = v + (((v ^ gmask) >> 2) >> (__ffs(u) - 1));
+      }  // (past count the group idles on its last subset)
+      unsigned m = gmask;
+      for (int t = 0; t < s; ++t) {
+        const int c = __ffs(m) - 1;
+        m &= m - 1;
+        if ((t & (L - 1)) == l) {
+          rowidx[2 * t] = xs[2 * c];
+          rowidx[2 * t + 1] = xs[2 * c + 1];
+          if (sizeof(T) == 8) pairs[t] = c;
+        }
+      }
+      return gmask;
+    };
 
     for (int rd = 0; rd < rounds; ++rd) {
       if (staged + G > slots) flush(!(pf && rd > 0));  // only when the group count changed between sizes
-      const int jsub = rd * G + g;
-      const bool active = jsub < count;
+      const bool active = g * rounds + rd < count;
       const int cur = (pf && (rd & 1)) ? nb : 0;  // the tile holding this round's R_1
       unsigned smask = 0;
       if (pf && rd > 0) {
