@@ -911,8 +911,13 @@ int run_batch(const BatchArgs& a) {
   const size_t ctr_b = 256;
   const size_t status_b = al(sizeof(int) * batch);
   const size_t pstatus_b = n_sel ? al(sizeof(int) * n_probe) : 0;  // zeroed with ctr and status
-  const bool out_host = (a.out0 && !is_device_ptr(a.out0)) || (a.out1 && !is_device_ptr(a.out1)) ||
-                        (a.out2 && !is_device_ptr(a.out2)) || (a.out3 && !is_device_ptr(a.out3));
+  // outputs in host memory (any of them sends all through device staging)
+  bool out_hmem[4];
+  {
+    const double* outs[4] = {a.out0, a.out1, a.out2, a.out3};
+    for (int i = 0; i < 4; ++i) out_hmem[i] = outs[i] != nullptr && !is_device_ptr(outs[i]);
+  }
+  const bool out_host = out_hmem[0] || out_hmem[1] || out_hmem[2] || out_hmem[3];
   const size_t outs_b = out_host ? al(sizeof(double) * 5 * batch) : 0;
   // FP32 path on explicit matrices: one rounded copy per call, gathered by the kernel
   const size_t a32_b = (a.mode == BatchArgs::HAFNIAN && a.precision == GBS_MIXED) ? al(8 * (size_t)src_elems) : 0;
@@ -976,6 +981,10 @@ int run_batch(const BatchArgs& a) {
   HafLaunch L;
   memset(&L, 0, sizeof(L));
   int ret = GBS_OK;
+  void* h_outs = nullptr;  // pinned copy of the output staging (host outputs)
+  int oslot = -1;
+  const size_t out_sz[4] = {sizeof(double) * batch, sizeof(double) * batch, 2 * sizeof(double) * batch,
+                            sizeof(double) * batch};
   do {
     if (!hit) {
       e = cudaMemcpyAsync(up, hs, U.up_b, cudaMemcpyHostToDevice, st);
@@ -1165,13 +1174,21 @@ int run_batch(const BatchArgs& a) {
     e = launch_finalize(F, st);
     if (e != cudaSuccess) { ret = cuda_fail(e, "finalize launch"); break; }
     if (out_host) {
-      const size_t sz[4] = {sizeof(double) * batch, sizeof(double) * batch, 2 * sizeof(double) * batch,
-                            sizeof(double) * batch};
+      // device outputs straight from the staging; host ones by one copy of
+      // the staging block into pinned memory, spread after the synchronisation
       for (int i = 0; i < 4 && ret == GBS_OK; ++i)
-        if (o[i]) {
-          e = cudaMemcpyAsync(o[i], dst[i], sz[i], cudaMemcpyDefault, st);
+        if (o[i] && !out_hmem[i]) {
+          e = cudaMemcpyAsync(o[i], dst[i], out_sz[i], cudaMemcpyDeviceToDevice, st);
           if (e != cudaSuccess) ret = cuda_fail(e, "result copy");
         }
+      if (ret != GBS_OK) break;
+      const int prc = pinned_acquire(sizeof(double) * 5 * batch, &h_outs, &oslot);
+      if (prc != GBS_OK) {
+        ret = prc;
+        break;
+      }
+      e = cudaMemcpyAsync(h_outs, d_outs, sizeof(double) * 5 * batch, cudaMemcpyDeviceToHost, st);
+      if (e != cudaSuccess) ret = cuda_fail(e, "result copy");
     }
   } while (0);
   pinned_release(slot, st);
@@ -1182,7 +1199,15 @@ int run_batch(const BatchArgs& a) {
   if (ret == GBS_OK && out_host) {
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) ret = cuda_fail(e, "stream synchronize");
+    if (ret == GBS_OK) {
+      const double* ho = (const double*)h_outs;
+      const size_t off[4] = {0, (size_t)batch, 2 * (size_t)batch, 4 * (size_t)batch};
+      double* o[4] = {a.out0, a.out1, a.out2, a.out3};
+      for (int i = 0; i < 4; ++i)
+        if (out_hmem[i]) memcpy(o[i], ho + off[i], out_sz[i]);
+    }
   }
+  if (oslot >= 0) pinned_release(oslot, st);
   return ret;
 }
 
