@@ -157,3 +157,22 @@ def test_kept_plan_hafnian_batch(gbs, precision):
         host = np.zeros(2 * len(n))
         gbs.hafnian_batch(flat, n, offs, precision, haf_out=host)
         assert np.array_equal(kept, host), rep
+
+
+def test_kept_plan_still_checks_host_lists(gbs):
+    """A host index list is range-checked on every call, also when the call's
+    shape has a kept plan (GBS_ERANGE, nothing launched); the next valid call
+    of that shape still gives the fresh plan's bits."""
+    m = 24
+    K = kernel(gbs, m, 4)
+    idx, n, offs = gbs.pack_patterns(mixed_batch(m, 9, count=40))
+    good = probs(gbs, K, idx, n, offs, 0, host=True)  # plans and keeps the shape
+    bad = idx.copy()
+    bad[int(offs[7])] = m  # one index past the last mode
+    with pytest.raises(gbs.GbsError) as ei:
+        probs(gbs, K, bad, n, offs, 0, host=True)
+    assert ei.value.code == -3
+    again = probs(gbs, K, idx, n, offs, 0, host=True)
+    assert np.array_equal(good[0], again[0]) and np.array_equal(good[1], again[1])
+    gbs.clear_plans()
+    gbs.clear_plans()  # nothing kept: still fine
