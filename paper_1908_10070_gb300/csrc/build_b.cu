@@ -36,7 +36,10 @@ __global__ void tanh_lognorm_kernel(const double* __restrict__ r, int m, double*
     if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *log_norm = part[0];
+  if (threadIdx.x == 0) {
+    log_norm[0] = part[0];
+    log_norm[1] = exp(-part[0]);  // the normaliser itself, 1 / prod cosh r_i
+  }
 }
 
 // Error-free transformations (Knuth's two-sum; the FMA-based exact product).

@@ -25,7 +25,7 @@ struct gbs_kernel {
   double* t = nullptr;      // tanh r_i, m doubles, device
   int r_uniform = 0;        // 1 if every r_i is the same
   double t_uniform = 0.0;   // tanh r when r_uniform
-  double* dscal = nullptr;  // [0] = sum_i log cosh r_i, device
+  double* dscal = nullptr;  // [0] = L = sum_i log cosh r_i, [1] = exp(-L), device
 };
 
 namespace gbs {

@@ -215,7 +215,7 @@ struct FinalizeLaunch {
   const int* status;
   int batch;
   int precision;
-  const double* log_norm;  // device scalar sum_i log cosh r_i, or null (Hafnians only)
+  const double* log_norm;  // device [L = sum_i log cosh r_i, exp(-L)], or null (Hafnians only)
   double* p_out;
   double* logp_out;
   double* haf_out;

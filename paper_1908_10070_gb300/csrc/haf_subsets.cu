@@ -973,6 +973,7 @@ __global__ void chunk_sum_kernel(const ChunkLaunch C) {
 constexpr int kFinWarps = 16;  // most warps in a finalisation block
 __global__ void __launch_bounds__(kFinWarps * 32) finalize_kernel(const FinalizeLaunch F) {
   __shared__ double sv[6][kFinWarps];  // re hi/lo, im hi/lo, sum |f|, prod s_j!
+  __shared__ int sbad[kFinWarps];     // status flag of the pattern
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int wpb = blockDim.x >> 5;
@@ -989,6 +990,9 @@ __global__ void __launch_bounds__(kFinWarps * 32) finalize_kernel(const Finalize
       const int pb = F.sel ? F.sel[b] : b;
       const PatDesc d = F.pats[pb];
       const int n = d.n;
+      // loads that do not depend on the partial sums go first
+      const int xi = (want_p && d.idx_off >= 0 && lane < n) ? F.idx[d.idx_off + lane] : -1 - lane;
+      const int bad = (lane == 0 && F.status != nullptr) ? F.status[pb] : 0;
       double rh = 0, rl = 0, ih = 0, il = 0, K = 0;
       if (!(n & 1) && n > 0) {
         const int rep = F.rep_half ? F.rep_half[pb] : 0;
@@ -1008,7 +1012,6 @@ __global__ void __launch_bounds__(kFinWarps * 32) finalize_kernel(const Finalize
       double fac = 1.0;
       if (want_p && d.idx_off >= 0) {  // uniform over the warp
         // one load per lane; the earlier occurrences come by shuffles
-        const int xi = (lane < n) ? F.idx[d.idx_off + lane] : -1 - lane;
         int c = 1;
 #pragma unroll
         for (int q = 0; q < 31; ++q) {
@@ -1025,6 +1028,7 @@ __global__ void __launch_bounds__(kFinWarps * 32) finalize_kernel(const Finalize
         sv[3][warp] = il;
         sv[4][warp] = K;
         sv[5][warp] = fac;
+        sbad[warp] = bad;
       }
     }
     __syncthreads();
@@ -1032,7 +1036,7 @@ __global__ void __launch_bounds__(kFinWarps * 32) finalize_kernel(const Finalize
       const int bo = base + lane * nb + blockIdx.x;
       const int pb = F.sel ? F.sel[bo] : bo;
       const int n = F.pats[pb].n;
-      const bool bad = F.status != nullptr && F.status[pb] != 0;
+      const bool bad = sbad[lane] != 0;
       const double hr = sv[0][lane] + sv[1][lane], hi = sv[2][lane] + sv[3][lane];
       const double K = sv[4][lane];
       // |Haf| by a plain square root unless the squares could leave the
@@ -1048,14 +1052,19 @@ __global__ void __launch_bounds__(kFinWarps * 32) finalize_kernel(const Finalize
       }
       if (F.kappa_out) F.kappa_out[bo] = bad ? nan : kappa;
       if (want_p) {
-        const double L = F.log_norm ? *F.log_norm : 0.0;
-        // log p = log(|Haf|^2 / prod_j s_j!) - L: one logarithm while
-        // |Haf|^2 / prod s_j! is a normal number (else two)
+        // p = q exp(-L), q = |Haf|^2 / prod_j s_j!, and log p = log q - L,
+        // with the normaliser exp(-L) precomputed; where q or exp(-L) leaves
+        // the normal range, p = exp(log p) with log p = 2 log|Haf| -
+        // log prod s_j! - L
+        const double L = F.log_norm ? F.log_norm[0] : 0.0;
+        const double eL = F.log_norm ? F.log_norm[1] : 1.0;
         const double q = (mod / sv[5][lane]) * mod;
-        const double logp = (mod > 0.0) ? ((q >= 0x1p-1022 && q <= 0x1p1023) ? log(q) - L
-                                                                          : 2.0 * log(mod) - log(sv[5][lane]) - L)
-                                        : -INFINITY;
-        if (F.p_out) F.p_out[bo] = bad ? nan : ((mod > 0.0) ? exp(logp) : 0.0);
+        const bool qn = q >= 0x1p-1022 && q <= 0x1p1023;
+        const bool direct = qn && eL >= 0x1p-1022;
+        double logp = -INFINITY;
+        if (mod > 0.0 && (F.logp_out || !direct))
+          logp = qn ? log(q) - L : 2.0 * log(mod) - log(sv[5][lane]) - L;
+        if (F.p_out) F.p_out[bo] = bad ? nan : ((mod > 0.0) ? (direct ? q * eL : exp(logp)) : 0.0);
         if (F.logp_out) F.logp_out[bo] = bad ? nan : logp;
         if (F.err_out) F.err_out[bo] = bad ? nan : err_estimate(F.precision, n, kappa);
       }
