@@ -306,6 +306,11 @@ cudaError_t launch_pair_terms(const HafLaunch& L, cudaStream_t st);
 int max_blocks_per_sm(int precision, int warps_per_block, int smem_bytes);
 // Kernel entry points, for CUDA graph kernel nodes (the serving loop).
 const void* haf_kernel_fn(int precision);
+// The pair-term kernel (argument: HafLaunch, 256 threads a block) and the grid
+// launch_pair_terms gives it; with n_items_dev set it returns at once when
+// that count is 0 (serving steps without a new request).
+const void* pair_terms_kernel_fn();
+int pair_terms_grid(const HafLaunch& L);
 const void* finalize_kernel_fn();
 cudaError_t prepare_haf_kernel(int precision, int smem_bytes);
 

@@ -1087,6 +1087,8 @@ __global__ void __launch_bounds__(256) pair_terms_kernel(const HafLaunch P) {
   __shared__ int tri[kMaxN + 1];
   const double2* src2 = reinterpret_cast<const double2*>(P.src);
   double2* pt2 = reinterpret_cast<double2*>(P.pt);
+  // a serving step with no new request reads its count here (0: nothing to do)
+  if (P.n_items_dev != nullptr && *P.n_items_dev == 0) return;
   const int nmax = 2 * P.stage_h;
   const int cpm = (nmax * (nmax + 1) / 2 + kPairChunk - 1) / kPairChunk;  // chunks per matrix
   const int64_t n_chunks = (int64_t)P.batch * cpm;
@@ -1527,10 +1529,7 @@ cudaError_t launch_pairing_select(const PairingSelect& S, cudaStream_t st) {
 cudaError_t launch_pair_terms(const HafLaunch& L, cudaStream_t st) {
   if (L.pt == nullptr || L.batch <= 0) return cudaSuccess;
   if (2 * L.stage_h > kMaxN) return cudaErrorInvalidValue;
-  const int nmax = 2 * L.stage_h;
-  const int64_t chunks = (int64_t)L.batch * ((nmax * (nmax + 1) / 2 + kPairChunk - 1) / kPairChunk);
-  const int blocks = (int)std::min<int64_t>(chunks, 16384);
-  pair_terms_kernel<<<blocks, 256, 0, st>>>(L);
+  pair_terms_kernel<<<pair_terms_grid(L), 256, 0, st>>>(L);
   return cudaGetLastError();
 }
 
@@ -1585,6 +1584,14 @@ int max_blocks_per_sm(int precision, int warps_per_block, int smem_bytes) {
     return 0;
   }
   return nb;
+}
+
+const void* pair_terms_kernel_fn() { return (const void*)pair_terms_kernel; }
+
+int pair_terms_grid(const HafLaunch& L) {
+  const int nmax = 2 * L.stage_h;
+  const int64_t chunks = (int64_t)L.batch * ((nmax * (nmax + 1) / 2 + kPairChunk - 1) / kPairChunk);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(chunks, 16384));
 }
 
 const void* haf_kernel_fn(int precision) {

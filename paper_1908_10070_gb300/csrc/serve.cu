@@ -119,9 +119,12 @@ struct Slot {
   bool finalize_sent = false;
   bool cancelled = false;  // its ticket is answered; the slot frees once no step in flight uses it
   int64_t last_step = 0;   // the last step that carried its items or its finalisation
+  int pt = -1;             // FP64: element offset of its pair sums in the pool (-1: none)
+  bool pt_ready = false;   // its pair sums are computed (by an earlier step)
 };
 
 constexpr int kStepCap = 65536;  // work items per precision per step
+constexpr size_t kPtPoolBytes = (size_t)256 << 20;  // FP64 pair-sum pool
 
 // The GPU's global nanosecond timer, for the step graph's start and end stamps.
 __global__ void stamp_kernel(unsigned long long* out) {
@@ -146,13 +149,15 @@ struct Stage {
   bool busy = false;
   int64_t id = 0;
   int n_items[2] = {0, 0};
+  int n_pt_new = 0;      // slots whose pair sums this step computes
   std::vector<int> fin;  // slots finalised in this step, in selection order
   std::chrono::steady_clock::time_point t_launch;
   // graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaGraphNode_t nd_t0 = nullptr, nd_t1 = nullptr, nd_pats = nullptr, nd_idx = nullptr, nd_hdr = nullptr, nd_ctr = nullptr,
-                  nd_k[2] = {nullptr, nullptr}, nd_sel = nullptr, nd_fin = nullptr, nd_res = nullptr,
+                  nd_k[2] = {nullptr, nullptr}, nd_pt = nullptr, nd_ptk = nullptr, nd_sel = nullptr,
+                  nd_fin = nullptr, nd_res = nullptr,
                   nd_done = nullptr, nd_ev = nullptr;
 };
 
@@ -189,10 +194,19 @@ struct gbs_server {
   // device tables
   PatDesc* d_pats = nullptr;
   int* d_idx = nullptr;
+  // FP64 pair sums (R_2 of every subset in one addition per entry, as in the
+  // batched path): every FP64 request of order >= 6 holds its pair sums in a
+  // pool (first fit, in complex elements) and is admitted only when they fit,
+  // so its result never depends on the load; the step tables give each
+  // slot's offset (-1: none) to the subset kernel and, for the slots whose
+  // pair sums the step computes first, to the pair-term kernel
+  double* d_pt = nullptr;
+  Arena pt_arena;
+  int64_t* d_pttab = nullptr;   // [0, S): all, [S, 2S): computed in this step
   Partial* d_parts = nullptr;
   std::vector<PatDesc> h_pats;
   std::vector<int> h_idx;
-  size_t off_pats = 0, off_idx = 0, off_items[2] = {0, 0}, off_sel = 0, off_hdr = 0, up_bytes = 0;
+  size_t off_pats = 0, off_idx = 0, off_items[2] = {0, 0}, off_sel = 0, off_hdr = 0, off_pt = 0, up_bytes = 0;
   Stage stage[2];
   // ordering probe of requests with n >= kPairingMinN (side stream)
   cudaStream_t st_probe = nullptr;
@@ -221,15 +235,19 @@ int64_t binom64(int a, int b) {
   return r;
 }
 
-// Work items of one request (slot index `si`), one lane-group round each,
-// largest subsets first so the longest items start earliest.
+// Work items of one request (slot index `si`), largest subsets first so the
+// longest items start earliest: one lane-group round each in FP64; in the
+// float kernel, whose rounds are short next to an item's fixed cost (series
+// flush and double-double reduction), up to 4 rounds where a round holds 8 or
+// more subsets and 2 where it holds 4 (at 78K req/s that kept the mixed
+// stream's p99 at 6 ms instead of 55; in FP64 it only raised latency).
 void request_items(const gbs_server* s, int si, int n, int prec, std::vector<WorkItem>& out) {
   out.clear();
   const int h = n / 2;
   const int cb = complex_bytes(prec);
-  const int R = 1;
   for (int sz = h; sz >= 1; --sz) {
     const int G = 32 / lanes_for(2 * sz, h, s->cfg[prec].warp_bytes, s->o.max_n / 2, cb);
+    const int R = (prec == GBS_FP64) ? 1 : (G >= 8 ? 4 : (G >= 4 ? 2 : 1));
     const int64_t cnt = binom64(h, sz), cap = (int64_t)G * R;
     for (int64_t r0 = 0; r0 < cnt; r0 += cap) {
       WorkItem w;
@@ -270,6 +288,27 @@ HafLaunch make_launch(gbs_server* s, Stage& g, int prec, bool graph) {
   L.parts = s->d_parts;
   L.warp_bytes = s->cfg[prec].warp_bytes;
   L.stage_h = s->o.max_n / 2;
+  if (prec == GBS_FP64 && s->d_pt != nullptr) {
+    L.pt = s->d_pt;
+    L.pt_off = s->d_pttab;
+  }
+  return L;
+}
+
+// Launch arguments of the pair-term kernel: the slots whose offsets the
+// step's second table gives (their first step); in the step graph it reads
+// their count from the step header and returns at once when it is 0.
+HafLaunch make_pt_launch(gbs_server* s, Stage& g, bool graph) {
+  HafLaunch L;
+  memset(&L, 0, sizeof(L));
+  L.src = s->k->B;
+  L.idx = s->d_idx;
+  L.pats = s->d_pats;
+  L.pt = s->d_pt;
+  L.pt_off = s->d_pttab + s->o.max_slots;
+  L.batch = s->o.max_slots;
+  L.stage_h = s->o.max_n / 2;
+  if (graph) L.n_items_dev = g.d_ctr + 6;
   return L;
 }
 
@@ -362,10 +401,30 @@ cudaError_t build_graph(gbs_server* s, Stage& g) {
   if (e != cudaSuccess) return e;
   prev = g.nd_ctr;
   nd = dep(deps);
-  e = cudaGraphAddMemcpyNode1D(&g.nd_hdr, g.graph, deps, nd, g.d_ctr + 2, g.h_up + s->off_hdr, sizeof(int) * 4,
+  e = cudaGraphAddMemcpyNode1D(&g.nd_hdr, g.graph, deps, nd, g.d_ctr + 2, g.h_up + s->off_hdr, sizeof(int) * 5,
                                cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return e;
   prev = g.nd_hdr;
+  if (s->d_pt != nullptr) {
+    nd = dep(deps);
+    e = cudaGraphAddMemcpyNode1D(&g.nd_pt, g.graph, deps, nd, s->d_pttab, g.h_up + s->off_pt,
+                                 sizeof(int64_t) * 2 * S, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    prev = g.nd_pt;
+    HafLaunch Lp = make_pt_launch(s, g, true);
+    void* args[1] = {&Lp};
+    cudaKernelNodeParams kp;
+    memset(&kp, 0, sizeof(kp));
+    kp.func = (void*)pair_terms_kernel_fn();
+    kp.gridDim = dim3(pair_terms_grid(Lp));
+    kp.blockDim = dim3(256);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    nd = dep(deps);
+    e = cudaGraphAddKernelNode(&g.nd_ptk, g.graph, deps, nd, &kp);
+    if (e != cudaSuccess) return e;
+    prev = g.nd_ptk;
+  }
   for (int p = 0; p < 2; ++p) {
     HafLaunch L = make_launch(s, g, p, true);
     void* args[1] = {&L};
@@ -443,6 +502,7 @@ cudaError_t launch_stage(gbs_server* s, Stage& g) {
     hdr[1] = g.n_items[1];
     hdr[2] = (int)g.fin.size();
     hdr[3] = (int)(g.id & 0x7fffffff);  // comes back in the completion word
+    hdr[4] = g.n_pt_new;
     note_max(s->stats.update_max_s, t0);
     t0 = std::chrono::steady_clock::now();
     e = cudaGraphLaunch(g.exec, s->st);
@@ -459,6 +519,14 @@ cudaError_t launch_stage(gbs_server* s, Stage& g) {
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(g.d_ctr, 0, 2 * sizeof(int), s->st);
     if (e != cudaSuccess) return e;
+    if (s->d_pt != nullptr) {
+      e = cudaMemcpyAsync(s->d_pttab, g.h_up + s->off_pt, sizeof(int64_t) * 2 * S, cudaMemcpyHostToDevice, s->st);
+      if (e != cudaSuccess) return e;
+      if (g.n_pt_new > 0) {
+        e = launch_pair_terms(make_pt_launch(s, g, false), s->st);
+        if (e != cudaSuccess) return e;
+      }
+    }
     for (int p = 0; p < 2; ++p) {
       if (g.n_items[p] == 0) continue;
       e = cudaMemcpyAsync(g.d_items[p], g.h_up + s->off_items[p], sizeof(WorkItem) * g.n_items[p],
@@ -601,6 +669,16 @@ void admit(gbs_server* s) {
       sl.items.clear();
       return;
     }
+    int pto = -1;
+    if (r.prec == GBS_FP64 && s->d_pt != nullptr && pair_terms_elems(r.n) > 0) {
+      pto = s->pt_arena.alloc((int)pair_terms_elems(r.n));
+      if (pto < 0) {  // wait for pair-sum room to free up
+        s->arena.release(base, (int)sl.items.size());
+        s->stats.alloc_waits++;
+        sl.items.clear();
+        return;
+      }
+    }
     for (size_t i = 0; i < sl.items.size(); ++i) sl.items[i].part = base + (int)i;
     sl.used = true;
     sl.ticket = r.ticket;
@@ -611,6 +689,8 @@ void admit(gbs_server* s) {
     sl.finalize_sent = false;
     sl.cancelled = false;
     sl.last_step = 0;
+    sl.pt = pto;
+    sl.pt_ready = false;
     PatDesc& d = s->h_pats[si];
     d.src_off = 0;
     d.idx_off = (int64_t)si * GBS_MAX_N;
@@ -634,11 +714,26 @@ bool build_step(gbs_server* s, Stage& g) {
   int* sel = (int*)(g.h_up + s->off_sel);
   const int quota = s->o.subsets_per_step;
   const int64_t id = s->step_id + 1;
+  // pair-sum offsets: every FP64 slot that has a region, and those whose pair
+  // sums this step computes before its subset kernel (their first items)
+  int64_t* pt_all = (int64_t*)(g.h_up + s->off_pt);
+  int64_t* pt_new = pt_all + S;
+  g.n_pt_new = 0;
+  for (int q = 0; q < S; ++q) {
+    const Slot& sl = s->slots[q];
+    pt_all[q] = (sl.used && sl.pt >= 0) ? (int64_t)sl.pt : -1;
+    pt_new[q] = -1;
+  }
   for (int q = 0; q < S; ++q) {
     const int si = (s->rr + q) % S;
     Slot& sl = s->slots[si];
     if (!sl.used || sl.finalize_sent || sl.cancelled) continue;
     sl.last_step = id;
+    if (sl.pt >= 0 && !sl.pt_ready && sl.next < sl.items.size()) {
+      pt_new[si] = pt_all[si];
+      sl.pt_ready = true;  // steps run in order on one stream
+      ++g.n_pt_new;
+    }
     int taken = 0;
     int& cnt = g.n_items[sl.prec];
     while (sl.next < sl.items.size() && taken < quota && cnt < kStepCap) {
@@ -657,6 +752,17 @@ bool build_step(gbs_server* s, Stage& g) {
   return g.n_items[0] > 0 || g.n_items[1] > 0 || !g.fin.empty();
 }
 
+// Return a slot's partial sums and pair-sum region (no step in flight uses them).
+void free_slot(gbs_server* s, Slot& sl) {
+  s->arena.release(sl.part_base, (int)sl.items.size());
+  if (sl.pt >= 0) s->pt_arena.release(sl.pt, (int)pair_terms_elems(sl.n));
+  sl.pt = -1;
+  sl.pt_ready = false;
+  sl.used = false;
+  sl.cancelled = false;
+  sl.items.clear();
+}
+
 // Publish the results of a completed stage and free its finished slots (lock held).
 void complete(gbs_server* s, Stage& g) {
   const int S = s->o.max_slots;
@@ -664,10 +770,7 @@ void complete(gbs_server* s, Stage& g) {
   for (size_t b = 0; b < g.fin.size(); ++b) {
     Slot& sl = s->slots[g.fin[b]];
     if (sl.cancelled) {  // answered at cancellation: drop the result
-      s->arena.release(sl.part_base, (int)sl.items.size());
-      sl.used = false;
-      sl.cancelled = false;
-      sl.items.clear();
+      free_slot(s, sl);
       continue;
     }
     Result r;
@@ -679,9 +782,7 @@ void complete(gbs_server* s, Stage& g) {
     r.err = err_estimate(sl.prec, sl.n, kappa);
     s->done[sl.ticket] = r;
     s->pending.erase(sl.ticket);
-    s->arena.release(sl.part_base, (int)sl.items.size());
-    sl.used = false;
-    sl.items.clear();
+    free_slot(s, sl);
   }
   s->rcv.notify_all();
   g.fin.clear();
@@ -692,12 +793,7 @@ void complete(gbs_server* s, Stage& g) {
 // Free the slots of cancelled requests that no step in flight uses (lock held).
 void reap_cancelled(gbs_server* s) {
   for (Slot& sl : s->slots)
-    if (sl.used && sl.cancelled && !sl.finalize_sent && sl.last_step <= s->last_done_step) {
-      s->arena.release(sl.part_base, (int)sl.items.size());
-      sl.used = false;
-      sl.cancelled = false;
-      sl.items.clear();
-    }
+    if (sl.used && sl.cancelled && !sl.finalize_sent && sl.last_step <= s->last_done_step) free_slot(s, sl);
 }
 
 void fail_all(gbs_server* s, int rc) {
@@ -715,6 +811,9 @@ void fail_all(gbs_server* s, int rc) {
   s->probing.clear();
   s->probe_cancelled.clear();
   for (auto& sl : s->slots) {
+    if (sl.pt >= 0) s->pt_arena.release(sl.pt, (int)pair_terms_elems(sl.n));
+    sl.pt = -1;
+    sl.pt_ready = false;
     sl.used = false;
     sl.cancelled = false;
   }
@@ -879,6 +978,8 @@ void destroy_resources(gbs_server* s) {
   if (s->d_pats) cudaFree(s->d_pats);
   if (s->d_idx) cudaFree(s->d_idx);
   if (s->d_parts) cudaFree(s->d_parts);
+  if (s->d_pt) cudaFree(s->d_pt);
+  if (s->d_pttab) cudaFree(s->d_pttab);
   if (s->st_probe) {
     cudaStreamSynchronize(s->st_probe);
     order_probe_release(&s->probe, s->st_probe);
@@ -949,6 +1050,19 @@ extern "C" int gbs_serve_create(const gbs_kernel* k, const gbs_serve_opts* opts,
       ret = fail(GBS_ENOMEM, "device buffers: %s", cudaGetErrorString(e));
       break;
     }
+    // FP64 pair-sum pool: kPtPoolBytes, or less when every slot holding a
+    // request of the largest even order the server accepts needs less
+    const int64_t pt_max = pair_terms_elems(s->o.max_n & ~1);
+    if (pt_max > 0) {
+      const int64_t elems = std::min<int64_t>((int64_t)S * pt_max, (int64_t)(kPtPoolBytes / 16));
+      if ((e = cudaMalloc(&s->d_pt, 16 * (size_t)elems)) != cudaSuccess ||
+          (e = cudaMalloc(&s->d_pttab, sizeof(int64_t) * 2 * S)) != cudaSuccess) {
+        cudaGetLastError();
+        ret = fail(GBS_ENOMEM, "pair-sum pool: %s", cudaGetErrorString(e));
+        break;
+      }
+      s->pt_arena.init((int)elems);
+    }
     s->h_pats.assign(S, PatDesc());
     memset(s->h_pats.data(), 0, sizeof(PatDesc) * S);
     s->h_idx.assign((size_t)GBS_MAX_N * S, 0);
@@ -960,7 +1074,8 @@ extern "C" int gbs_serve_create(const gbs_kernel* k, const gbs_serve_opts* opts,
     s->off_items[1] = s->off_items[0] + al(sizeof(WorkItem) * kStepCap);
     s->off_sel = s->off_items[1] + al(sizeof(WorkItem) * kStepCap);
     s->off_hdr = s->off_sel + al(sizeof(int) * S);
-    s->up_bytes = s->off_hdr + al(sizeof(int) * 4);
+    s->off_pt = s->off_hdr + al(sizeof(int) * 8);
+    s->up_bytes = s->off_pt + al(sizeof(int64_t) * 2 * S);
     for (int i = 0; i < 2 && ret == GBS_OK; ++i) {
       Stage& g = s->stage[i];
       if ((e = cudaMallocHost(&g.h_up, s->up_bytes)) != cudaSuccess ||
