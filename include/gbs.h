@@ -300,7 +300,10 @@ typedef struct gbs_serve_opts {
 /* Start a server for kernel matrix k: a host thread admits requests into
  * device slots as slots and memory free up, and runs steps that advance every
  * resident request's subset sum together; partial sums stay on the device
- * between steps. A request with n >= 26 is admitted once the ordering probe
+ * between steps. Beside mem_budget the server keeps a pool of up to 256 MB
+ * (less when max_slots requests of order max_n need less) for the pair sums
+ * of FP64 requests of order >= 6; such a request is admitted once its pair
+ * sums fit there. A request with n >= 26 is admitted once the ordering probe
  * of gbs_prob_batch has chosen its ordering (on a side stream, several
  * waiting requests per launch), so its subset sum cancels as little as in
  * the batched call. k must outlive the server. opts may be NULL. */
