@@ -35,7 +35,7 @@ import workloads as W  # noqa: E402
 # headline workload, from one ncu capture (profiles/haf_subsets_fp64_m64_n16.md).
 # Reported only while the kernel's sources are the ones the capture was taken
 # from; any change to them makes the figure stale and the bench reports null.
-NCU_TRAFFIC = {"sources_sha256": "29a2563f137a8b56a16e3d545430fa0de5e8f23fc55ed884074b30c6e164dd70", "bytes_per_launch": 373934336.0,
+NCU_TRAFFIC = {"sources_sha256": "62a5988a47950a43b132d705652589f68470a2b235539ff23a26636efbdc44be", "bytes_per_launch": 365940480.0,
                # executed FP64 flops per cycle (DFMA x 2 + DADD + DMUL) over the 608 peak
                "executed_fp64_frac": 0.880}
 KERNEL_SOURCES = ("paper_1908_10070_gb300/csrc/haf_subsets.cu", "paper_1908_10070_gb300/csrc/gbs_internal.cuh")
@@ -750,8 +750,8 @@ def sustainable(row):
             and row["median_last_quarter_ms"] <= 2.0 * row["median_first_quarter_ms"] + 1.0)
 
 
-def saturation(gbs, K, dur_s=1.0, max_levels=12):
-    """Rising Poisson rates (x1.5 from 1000 req/s, about dur_s of requests
+def saturation(gbs, K, dur_s=1.0, max_levels=24):
+    """Rising Poisson rates (x1.25 from 1000 req/s, about dur_s of requests
     each) until the stream is no longer sustained; the largest sustained rate
     for the FP64 server, the mixed server and plain per-pattern calls."""
     out = {"criterion": "served >= 0.95 x offered and last-quarter median latency <= "
@@ -772,7 +772,7 @@ def saturation(gbs, K, dur_s=1.0, max_levels=12):
             if not row["sustained"]:
                 break
             best = row
-            rate *= 1.5
+            rate *= 1.25
         out["levels"][name] = rows
         out[name + "_max_sustained_req_s"] = best["offered_req_s"] if best else None
         out[name + "_at_max"] = ({"p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"]} if best else None)
