@@ -585,6 +585,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
       if (po >= 0) ptp = reinterpret_cast<const double2*>(P.pt) + po;
     }
     int staged = 0;  // subsets whose traces wait in the staging area
+    int lanes_used = 1;  // the most subsets one flush of this item held (lanes with terms)
     const double2* srcp = src2 + d.src_off;
     const float2* src32p = P.src32 ? reinterpret_cast<const float2*>(P.src32) + d.src_off : nullptr;
 
@@ -671,6 +672,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
           }
         }
       }
+      lanes_used = max(lanes_used, staged);
       staged = 0;
       __syncwarp();
     };
@@ -855,9 +857,13 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? kMaxWarpsPerBlock * 32 : 512,
    }
 
     // warp reduction of the group accumulators (fixed butterfly: deterministic)
-    // in double-double
+    // in double-double, over the levels that reach the lanes holding terms
+    // (lanes past lanes_used hold exact zeros all item long; an item of one
+    // round of few large subsets then skips most of the FP64 additions)
     double rh = acc_re.hi, rl = acc_re.lo, ih = acc_im.hi, il = acc_im.lo, kp = kap;
-    for (int off = 16; off > 0; off >>= 1) {
+    int span = 1;
+    while (span < lanes_used) span <<= 1;
+    for (int off = span >> 1; off > 0; off >>= 1) {
       const double orh = __shfl_xor_sync(FULL, rh, off), orl = __shfl_xor_sync(FULL, rl, off);
       const double oih = __shfl_xor_sync(FULL, ih, off), oil = __shfl_xor_sync(FULL, il, off);
       kp += __shfl_xor_sync(FULL, kp, off);
