@@ -176,8 +176,8 @@ int gbs_prob_batch(const gbs_kernel* k, const int* idx, const int* n, const int6
                    int batch, int precision, void* stream, double* p_out, double* logp_out,
                    double* haf_ri_out, double* err_est_out);
 
-/* Frees every kept plan that no call is using (see gbs_prob_batch), after the
- * device has finished the work already issued (a device-wide synchronize).
+/* Frees every kept plan that no call is using (see gbs_prob_batch), each after
+ * its device has finished the work already issued (a device-wide synchronize).
  * The paper has no counterpart (memory management only). Returns GBS_OK, or
  * GBS_ECUDA if that synchronize reports an earlier asynchronous error. */
 int gbs_clear_plans(void);

@@ -570,6 +570,20 @@ static std::mutex g_plan_mu;
 static std::vector<PlanEntry*> g_plans;
 static uint64_t g_plan_clock = 0;
 
+// Free a kept plan's device memory once its device has finished every launch
+// that may read it (on any stream); the caller's current device is kept.
+static cudaError_t plan_free(PlanEntry* v) {
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (v->key.device != cur) cudaSetDevice(v->key.device);
+  const cudaError_t e = cudaDeviceSynchronize();
+  cudaFree(v->d_up);
+  if (v->ready) cudaEventDestroy(v->ready);
+  if (v->key.device != cur) cudaSetDevice(cur);
+  delete v;
+  return e;
+}
+
 static PlanEntry* plan_lookup(const PlanKey& key, const int* n, const int64_t* offs) {
   std::lock_guard<std::mutex> lk(g_plan_mu);
   for (PlanEntry* p : g_plans)
@@ -596,11 +610,7 @@ static PlanEntry* plan_insert(const PlanKey& key, const int* n, const int64_t* o
     if (victim < 0) return nullptr;
     PlanEntry* v = g_plans[victim];
     used -= v->lay.up_b;
-    // launches of earlier calls may still read it, on any stream
-    cudaDeviceSynchronize();
-    cudaFree(v->d_up);
-    if (v->ready) cudaEventDestroy(v->ready);
-    delete v;
+    plan_free(v);
     g_plans.erase(g_plans.begin() + victim);
   }
   PlanEntry* p = new (std::nothrow) PlanEntry();
@@ -637,16 +647,15 @@ static void plan_release(PlanEntry* p) {
 
 static int clear_plans() {
   std::lock_guard<std::mutex> lk(g_plan_mu);
-  cudaError_t e = cudaDeviceSynchronize();
+  cudaError_t e = cudaSuccess;
   for (size_t i = 0; i < g_plans.size();) {
     PlanEntry* v = g_plans[i];
     if (v->in_use) {
       ++i;
       continue;
     }
-    cudaFree(v->d_up);
-    if (v->ready) cudaEventDestroy(v->ready);
-    delete v;
+    const cudaError_t ev = plan_free(v);
+    if (e == cudaSuccess) e = ev;
     g_plans.erase(g_plans.begin() + i);
   }
   return e == cudaSuccess ? GBS_OK : cuda_fail(e, "synchronize before freeing kept plans");
