@@ -450,3 +450,28 @@ def test_serving_completion_queue(gbs, kern):
         if i == 5 or i % 2:
             continue
         assert got[t][3] == 0 and abs(got[t][1] - h_ref[i]) <= FP64_TOL * max(abs(h_ref[i]), 1e-300)
+
+
+def test_serving_pair_sum_pool_full(gbs, kern):
+    """FP64 requests keep their pair sums in a pool of 256 MB: 96 requests of
+    n = 32 (4.3 MB each) cannot all be resident, so admissions wait for pair-sum
+    room. Every request still completes, with the batched path's Hafnian
+    within 1e-10, and a request's bits do not depend on the crowd (alone ==
+    in the full pool)."""
+    K, m = kern
+    rng = np.random.default_rng(44)
+    pats = [np.sort(rng.choice(m, size=32, replace=False)).astype(np.int32) for _ in range(96)]
+    # a partial-sum budget large enough that the pair-sum pool binds first
+    # (about 60 requests of n = 32 fit in it)
+    srv = gbs.Server(K, mem_budget=1 << 30)
+    try:
+        alone = wait_all(srv, [srv.submit(pats[0])])[0]
+        res = wait_all(srv, [srv.submit(x) for x in pats], timeout=300.0)
+        st = srv.stats()
+    finally:
+        srv.destroy()
+    assert st["alloc_waits"] > 0  # some admissions waited for room
+    assert res[0][0] == alone[0] and res[0][1] == alone[1]
+    _, h_ref = batch_ref(gbs, K, pats[:12], gbs.FP64)
+    for r, hr in zip(res[:12], h_ref):
+        assert abs(r[1] - hr) <= FP64_TOL * abs(hr), (r[1], hr)
