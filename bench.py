@@ -653,7 +653,7 @@ def serve_stream(gbs, K, reqs, precision):
         for t in warm:
             while srv.poll(t) is None:
                 pass
-        lat, outstanding, i = [], {}, 0
+        lat, even, outstanding, i = [], [], {}, 0
         # the client is Python: keep its cyclic garbage collector from pausing
         # it mid-stream (a pause would count as latency of every request due
         # in it); the server is native code and unaffected either way
@@ -666,19 +666,23 @@ def serve_stream(gbs, K, reqs, precision):
                 tk = srv.submit(reqs[i][1], precision)
                 if tk < 0:
                     break
-                outstanding[tk] = reqs[i][0]
+                outstanding[tk] = (reqs[i][0], len(reqs[i][1]) % 2 == 0)
                 i += 1
             for tk in list(outstanding):
                 if srv.poll(tk) is not None:
-                    lat.append(time.perf_counter() - t0 - outstanding.pop(tk))
+                    arr, ev = outstanding.pop(tk)
+                    lat.append(time.perf_counter() - t0 - arr)
+                    even.append(ev)
         total = time.perf_counter() - t0
         st = srv.stats()
     finally:
         gc.enable()
         srv.destroy()
     lat = np.array(lat) * 1e3
+    le = lat[np.array(even, dtype=bool)]  # odd n is answered at submission (p = 0)
     return {"requests": len(reqs), "throughput_req_s": len(reqs) / total, "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "even_n_p50_ms": float(np.percentile(le, 50)), "even_n_p99_ms": float(np.percentile(le, 99)),
             # the server's own view: device steps, their mean and longest wall time
             # (launch to detected completion) and device time (CUDA events around
             # the step); a long wall tail over short device steps points at the host
@@ -826,8 +830,10 @@ def per_pattern_stream(gbs, K, reqs):
     finally:
         gc.enable()
     lat = np.array(lat) * 1e3
+    le = lat[np.array([len(x) % 2 == 0 for _, x in reqs], dtype=bool)]
     return {"requests": len(reqs), "throughput_req_s": len(reqs) / total, "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean())}
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "even_n_p50_ms": float(np.percentile(le, 50)), "even_n_p99_ms": float(np.percentile(le, 99))}
 
 
 def serving(gbs, torch, count: int = 20000):
