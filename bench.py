@@ -370,7 +370,9 @@ def main():
     }
     if rank == 0 and not args.no_cpu_baseline and world == 1 and prec == gbs.FP64:
         line["cpu_baseline"] = cpu_baseline(pats, U, r)
-    if rank == 0 and not args.quick:
+    # the other workloads, serving and the samplers: one-GPU runs only (a
+    # multi-rank run holds every GPU meanwhile)
+    if rank == 0 and not args.quick and world == 1:
         line["extra"] = extras(gbs, torch, measured_peak)
     if rank == 0:
         print(json.dumps(line), flush=True)
