@@ -613,7 +613,8 @@ def bunched(gbs, torch, reps=3):
 
 def sampler(gbs):
     """Appendix I brute-force sampler at the paper's check size (n = 4, m = 16,
-    400,000 draws) and Step 1 (P_n) at m = 36: wall time through the C ABI."""
+    400,000 draws), Step 1 (P_n) at m = 36, and Algorithm 1 chain samples of
+    12, 16 and 20 photons at m = n^2: wall time through the C ABI."""
     m, n = 16, 4
     K = gbs.build_kernel(W.haar_unitary(m, 16), np.full(m, 0.5))
     u = np.random.default_rng(2019).random(400000)
@@ -628,7 +629,7 @@ def sampler(gbs):
     t_pn = time.perf_counter() - t0
     # Algorithm 1 chain samples in the paper's m = n^2 setting (Sec. 3.5)
     chain = {}
-    for n_, reps in ((12, 3), (16, 1)):
+    for n_, reps in ((12, 5), (16, 5), (20, 3)):
         m_ = n_ * n_
         Kc = gbs.build_kernel(W.haar_unitary(m_, 40 + n_), np.full(m_, 0.8814))
         rng = np.random.default_rng(n_)

@@ -243,10 +243,11 @@ int gbs_sample_bruteforce(const gbs_kernel* k, int n, const double* uniforms, in
  * squeezing on every mode (the kernel's r must all be equal and > 0: the
  * theorem sums out the unsampled photons with the unitarity of W, which
  * B = U diag(tanh r_i) U^T lacks when the r_i differ). The sub-Hafnians of
- * every even subset of each prefix come from the batched FP64 path; the sums
- * over s, s', A, B, mu of Theorem 1 are regrouped by the multisets of modes
- * they involve (at most 3^k products per prefix) and run one thread per
- * multiset.
+ * the prefix's subsets that the sum reads come from the batched FP64 path;
+ * the sums over s, s', A, B, mu of Theorem 1 are regrouped by the set
+ * rho = [k] \ A (Per(S_{A,B}) = 0 unless A and B hold the same modes), and
+ * only the sizes of rho and s inside the theorem's ranges are formed (one
+ * thread per rho).
  *   x      batch * k mode indices in [0, m), prefix b at [b * k, (b + 1) * k),
  *          host or device (read before return).
  *   k      0..min(n, 20).  n  even, <= GBS_MAX_N.
@@ -258,8 +259,11 @@ int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int batch, int
 
 /* Algorithm 1 (Sec. 3.2): one ordered n-photon sample x_1..x_n by the chain
  * rule, x_k drawn from the m conditional weights q_n(x_1..x_{k-1}, l),
- * l = 0..m-1 (gbs_marginal_batch), by the inverse CDF in mode order with the
- * caller's uniform u_k. Identical squeezing only.
+ * l = 0..m-1 (the sum of gbs_marginal_batch), by the inverse CDF in mode
+ * order with the caller's uniform u_k. Identical squeezing only. The sampled
+ * prefix's sub-Hafnians stay on the device between steps (the
+ * exponential-space variant, Appendix D); those of the sets that hold the
+ * new photon come from them by expanding the Hafnian along its row.
  *   n         even, 0..20.
  *   uniforms  n numbers in [0, 1), HOST memory.
  *   x_out     n ints, HOST memory: the mode of each photon in draw order.

@@ -20,25 +20,26 @@
 // e' uses s; the theorem's B ranges over [k] \ a. Both are read with s', which
 // the brute-force marginal of Eq. marginal_definition confirms.)
 //
-// Evaluation order. The same sum, regrouped: W_T, and so Haf(W_T), depends
-// only on the multiset of modes x_T, and Per(S_{A,B}) only on the multisets
-// of A and B. Write alpha for the multiset of A (per distinct mode v of the
-// prefix, alpha_v of its m_v copies) and rho = prefix - alpha for what is
-// left. For fixed A and B the sums over s and s' separate, and each depends
-// on A (or B) only through alpha, so
-//   q_n = sum_alpha  prod_v alpha_v! (prod_v C(m_v, alpha_v))^2
-//         sum_{ja, jb} F(k, |alpha|, ja, jb) / f_n  G(rho, ja) conj(G(rho, jb)),
-//   G(rho, j) = sum_{sigma <= rho, |sigma| = j} prod_v C(rho_v, sigma_v)
-//               Haf(W_sigma) Haf(W_{rho - sigma})
-// (the binomials count the position sets with a given multiset). That is
-// at most 3^k products per prefix, where the nested sums of the theorem take
-// about 6^k; for a prefix without repeated modes the multisets are the
-// position sets themselves and every count is 1.
+// Evaluation order. The same sum, regrouped by rho = [k] \ A: Per(S_{A,B})
+// vanishes unless A and B hold the same multiset alpha of modes, and is then
+// prod_v alpha_v!; rho_A and rho_B then hold equal multisets too, so their
+// sub-Hafnians agree, and for fixed A the sum over s runs over s in rho_A:
+//   q_n = sum_rho w(rho) sum_{ja, jb} F(k, k - |rho|, ja, jb) / f_n G(rho, ja) conj(G(rho, jb)),
+//   G(rho, j) = sum_{sigma in rho, |sigma| = j} Haf(W_sigma) Haf(W_{rho \ sigma}),
+//   w(rho) = prod_v alpha_v! C(m_v, alpha_v)
+// (alpha_v = m_v - |rho cap positions of v|, m_v the multiplicity of mode v in
+// the prefix; C(m_v, alpha_v) counts the sets B with A's multiset; w = 1
+// without repeated modes, the Proposition). F is 0 outside the theorem's
+// ranges, and the kernel forms no term there: a rho takes part only if some
+// (ja, jb) is in range for mu = k - |rho|, and only the sizes ja in range are
+// enumerated. At k = n only rho = [k], s = [k] remains; summed over the n
+// steps of a 16-photon sample, about 29 thousand products per candidate mode
+// (3^k each when every size is formed).
 //
-// The sub-Hafnians Haf(W_T) for every even subset T of the prefix come from
-// the batched subset-sum path (Haf(B_T) = tanh(r)^{|T|/2} Haf(W_T)); the
-// regrouped sum runs one thread per rho, in fixed-order block and prefix
-// reductions.
+// The sub-Hafnians Haf(W_T) of the sizes read (Haf(B_T) = tanh(r)^{|T|/2}
+// Haf(W_T)) come from the batched subset-sum path in gbs_marginal_batch and
+// from the sampled prefix's cache in the chain sampler; the sum runs one
+// thread per rho, in fixed-order block and prefix reductions.
 #include <math.h>
 #include <string.h>
 
@@ -55,151 +56,193 @@ constexpr int kMargThreads = 256;
 
 __device__ double lgbinom(double x, double y) { return lgamma(x + 1.0) - lgamma(y + 1.0) - lgamma(x - y + 1.0); }
 
+// t^{-s/2} for s = 0..kMaxK photons (tanh r = t): the factor from Haf(B_T)
+// to Haf(W_T). Computed once per call on the host.
+struct SizeScale {
+  double s[kMaxK + 1];
+};
+
+SizeScale size_scale(double t) {
+  SizeScale sc;
+  for (int i = 0; i <= kMaxK; ++i) sc.s[i] = pow(t, -0.5 * i);
+  return sc;
+}
+
+// The ranges of Theorem 1: ja, jb (the even sizes of s and s') at least
+// max(0, 2k - n), and mu = |A| in [max(0, 3k - ja - jb - n), k - max(ja, jb)].
+// F vanishes outside them, so no term there is formed.
+__host__ __device__ __forceinline__ bool theorem_range(int k, int n, int mu, int ja, int jb) {
+  const int lo = 2 * k - n > 0 ? 2 * k - n : 0;
+  const int hi = ja > jb ? ja : jb;
+  return ja >= lo && jb >= lo && mu >= (3 * k - ja - jb - n > 0 ? 3 * k - ja - jb - n : 0) && mu <= k - hi;
+}
+
 // F(k, mu, ja, jb) / f_n for ja, jb in {0, 2, .., k}, mu in [0, k]; 0 outside
-// the ranges of Theorem 1.
-__global__ void fcoef_kernel(int k, int n, int m, double* __restrict__ F) {
+// the ranges above. Prefix length k = k0 + blockIdx.y, its table at
+// F + blockIdx.y * stride (index (ja/2 * (k/2+1) + jb/2) * (k+1) + mu).
+__global__ void fcoef_kernel(int k0, int n, int m, int64_t stride, double* __restrict__ F) {
+  const int k = k0 + (int)blockIdx.y;
+  double* Fk = F + blockIdx.y * stride;
   const int K2 = k / 2 + 1;
   const int total = K2 * K2 * (k + 1);
-  const int lo = max(0, 2 * k - n);
-  for (int q = threadIdx.x; q < total; q += blockDim.x) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
     const int ja = 2 * (q / (K2 * (k + 1)));
     const int jb = 2 * ((q / (k + 1)) % K2);
     const int mu = q % (k + 1);
     double v = 0.0;
-    if (ja >= lo && jb >= lo && mu >= max(0, 3 * k - ja - jb - n) && mu <= k - max(ja, jb)) {
+    if (theorem_range(k, n, mu, ja, jb)) {
       const double lf = lgamma((double)(n - k) + 1.0) +
                         lgbinom(0.5 * (n - k + mu + m) - 1.0, k - 0.5 * (ja + jb) + 0.5 * m - 1.0) -
                         lgamma((double)n + 1.0) - lgbinom(0.5 * (m + n) - 1.0, 0.5 * n);
       v = exp(lf);
     }
-    F[q] = v;
+    Fk[q] = v;
   }
 }
 
-__device__ __forceinline__ double binom_d(int a, int b) {
-  double r = 1.0;
-  for (int i = 1; i <= b; ++i) r = r * (double)(a - b + i) / (double)i;
-  return r;
+// Entries of one F table for prefixes of up to k photons.
+inline int64_t fcoef_stride(int k) { return (int64_t)(k / 2 + 1) * (k / 2 + 1) * (k + 1); }
+
+// The sets rho of the sum that have some (ja, jb) in range: those of the
+// even sizes c[0..ncls-1], C(k, c[i]) of each, numbered from start[i].
+struct RhoClasses {
+  int ncls = 0;
+  int c[kMaxK / 2 + 1];
+  int64_t start[kMaxK / 2 + 2];
+  __host__ __device__ int64_t total() const { return start[ncls]; }
+};
+
+// Calls f(sub) for every subset of rho (c = |rho| set bits) with t elements:
+// Gosper's successor over t-of-c index masks, each spread onto rho's bits.
+template <class Fn>
+__device__ __forceinline__ void for_subsets_of_size(int rho, int c, int t, Fn&& f) {
+  if (t < 0 || t > c) return;
+  unsigned u = (1u << t) - 1;
+  for (;;) {
+    int sub = 0;
+    for (unsigned uu = u, r = (unsigned)rho; uu; uu >>= 1) {
+      const unsigned low = r & (0u - r);
+      if (uu & 1u) sub |= (int)low;
+      r ^= low;
+    }
+    f(sub);
+    if (t == 0) return;
+    const unsigned lo = u & (0u - u), v = u + lo;
+    u = v + (((v ^ u) / lo) >> 2);
+    if (u >= (1u << c)) return;
+  }
 }
 
-// The regrouped Theorem 1 sum (see the top of this file). Blocks cover the
-// rho of one prefix (blockIdx.y = prefix, blockIdx.x = a run of kMargThreads
-// indices); each thread forms G(rho, .) for its rho and the quadratic form
-// with F, and the block writes the sum of its threads (fixed tree) to
-// part[prefix * gridDim.x + blockIdx.x].
-//   H: Haf(W_T) of every position set T (bitmask order, 0 for odd |T|), 2^k per prefix.
+// The Theorem 1 sum over position sets, one thread per rho = [k] \ A of a
+// size class in `rc` (thread i of class c: the rho of rank i among the
+// c-element sets in colex order). For the
+// sets A, B of one multiset alpha (Per(S_{A,B}) = prod_v alpha_v!, 0 for
+// different multisets), rho_A and rho_B have equal sub-Hafnians, so
+//   q_n = sum_rho w(rho) sum_{ja, jb} F(k, k - |rho|, ja, jb) / f_n G(rho, ja) conj(G(rho, jb)),
+//   G(rho, j) = sum_{sigma subset of rho, |sigma| = j} Haf(W_sigma) Haf(W_{rho \ sigma}),
+//   w(rho) = prod_v alpha_v! C(m_v, alpha_v),  alpha_v = m_v - |rho cap (positions of mode v)|
+// (m_v the multiplicity of mode v in the prefix; w = 1 without repeated
+// modes, the Proposition). Only the sizes ja with some jb in range are
+// enumerated, and by their complements when those are smaller.
+//   H: Haf(W_T) by position mask T (0 for odd |T|); T without position k-1
+//      reads Hlo + b * slo, T with it Hhi + b * shi at T minus that position.
 //   vmask, nv: per prefix, the position mask of each of its nv distinct modes.
-// A prefix without repeated modes (nv == k) indexes rho by position masks; otherwise
-// rho is a mixed-radix number over the distinct modes (digit v in [0, m_v]),
-// and a multiset reads the sub-Hafnian of its representative position set (the
-// first rho_v positions of each mode v).
-__global__ void __launch_bounds__(kMargThreads) marginal_terms_kernel(int k, int n, const double2* __restrict__ H,
-                                                                     const double* __restrict__ F,
+// Each block writes the sum of its threads (fixed tree) to
+// part[b * gridDim.x + blockIdx.x].
+__global__ void __launch_bounds__(kMargThreads) marginal_terms_kernel(int k, int n, RhoClasses rc,
+                                                                     const double2* __restrict__ Hlo,
+                                                                     int64_t slo, const double2* __restrict__ Hhi,
+                                                                     int64_t shi, const double* __restrict__ F,
                                                                      const int* __restrict__ vmask,
                                                                      const int* __restrict__ nv,
                                                                      double* __restrict__ part) {
   __shared__ double red[kMargThreads];
-  __shared__ int s_pm[kMaxK][kMaxK + 1];  // first c positions of mode v
-  __shared__ int s_mv[kMaxK], s_stride[kMaxK + 1];
+  __shared__ unsigned s_need[kMaxK + 1];  // per mu: bit a set if ja = 2a has some jb in range
+  __shared__ int s_mask[kMaxK], s_mult[kMaxK];
+  __shared__ int s_nrep;
+  __shared__ int s_binom[kMaxK + 1][kMaxK + 1];  // C(p, i)
   const int b = blockIdx.y;
-  const double2* Hb = H + ((int64_t)b << k);
-  const int nvals = nv[b];
-  const int* vm = vmask + (int64_t)b * kMaxK;
-  if (threadIdx.x == 0) {
-    int stride = 1;
-    for (int v = 0; v < nvals; ++v) {
-      const int mk = vm[v];
-      s_mv[v] = __popc(mk);
-      s_stride[v] = stride;
-      stride *= s_mv[v] + 1;
-      int acc = 0, rest = mk;
-      s_pm[v][0] = 0;
-      for (int c = 1; c <= s_mv[v]; ++c) {
-        acc |= rest & -rest;  // the next position of mode v
-        rest &= rest - 1;
-        s_pm[v][c] = acc;
-      }
+  if (threadIdx.x <= (unsigned)kMaxK) {  // row p of Pascal's triangle, exact in integers
+    const int p = threadIdx.x;
+    int64_t v = 1;
+    for (int i = 0; i <= kMaxK; ++i) {
+      s_binom[p][i] = i > p ? 0 : (int)v;
+      v = v * (p - i) / (i + 1);
     }
-    s_stride[nvals] = stride;
+  }
+  const int K2 = k / 2 + 1;
+  if (threadIdx.x <= (unsigned)k) {
+    const int mu = threadIdx.x;
+    unsigned need = 0;
+    for (int a = 0; a < K2; ++a)
+      for (int c = 0; c < K2; ++c)
+        if (theorem_range(k, n, mu, 2 * a, 2 * c)) need |= 1u << a;
+    s_need[mu] = need;
+  }
+  if (threadIdx.x == 0) {
+    // the repeated modes only (a mode seen once has weight 1 either way)
+    const int* vm = vmask + (int64_t)b * kMaxK;
+    int r = 0;
+    for (int v = 0; v < nv[b]; ++v)
+      if (__popc(vm[v]) > 1) {
+        s_mask[r] = vm[v];
+        s_mult[r] = __popc(vm[v]);
+        ++r;
+      }
+    s_nrep = r;
   }
   __syncthreads();
-  const int K2 = k / 2 + 1;
-  const int full = (1 << k) - 1;
+  const double2* lo = Hlo + b * slo;
+  const double2* hi = Hhi + b * shi;
+  const int half = k > 0 ? 1 << (k - 1) : 0;
+  auto haf = [&](int T) { return (T & half) ? hi[T ^ half] : lo[T]; };
   const int64_t idx = (int64_t)blockIdx.x * kMargThreads + threadIdx.x;
   double acc = 0.0;
-  const bool distinct = (nvals == k);
-  if (idx < (distinct ? (int64_t)1 << k : (int64_t)s_stride[nvals])) {
+  if (idx < rc.total()) {
+    int cls = 0;
+    while (idx >= rc.start[cls + 1]) ++cls;
+    const int c = rc.c[cls];
+    // colex unranking: rank = sum_i C(p_i, i) over the positions p_1 < .. < p_c
+    int rank = (int)(idx - rc.start[cls]), rho = 0;
+    for (int i = c, p = k - 1; i >= 1; --i) {
+      while (s_binom[p][i] > rank) --p;
+      rho |= 1 << p;
+      rank -= s_binom[p][i];
+      --p;
+    }
+    const unsigned need = s_need[k - c] & ((2u << (c >> 1)) - 1);
+    const int mu = k - c;
     double2 G[kMaxK / 2 + 1];
-    for (int j = 0; j < K2; ++j) G[j] = make_double2(0.0, 0.0);
-    int rsize;
-    double w;  // prod alpha_v! (prod C(m_v, alpha_v))^2
-    if (distinct) {
-      const int rho = (int)idx;
-      rsize = __popc(rho);
-      if (!(rsize & 1)) {
-        for (int sub = rho;; sub = (sub - 1) & rho) {
-          const int c = __popc(sub);
-          if (!(c & 1)) {
-            const double2 a = Hb[sub], e = Hb[rho ^ sub];
-            G[c >> 1].x += a.x * e.x - a.y * e.y;
-            G[c >> 1].y += a.x * e.y + a.y * e.x;
-          }
-          if (sub == 0) break;
-        }
-      }
-      w = 1.0;
-      (void)full;
-    } else {
-      int rho_d[kMaxK];
-      int rem = (int)idx;
-      rsize = 0;
-      w = 1.0;
-      for (int v = 0; v < nvals; ++v) {
-        rho_d[v] = rem % (s_mv[v] + 1);
-        rem /= s_mv[v] + 1;
-        rsize += rho_d[v];
-        const int a = s_mv[v] - rho_d[v];
-        const double cm = binom_d(s_mv[v], a);
-        double fa = 1.0;
-        for (int c = 2; c <= a; ++c) fa *= (double)c;
-        w *= fa * cm * cm;
-      }
-      if (!(rsize & 1)) {
-        // sigma <= rho in mixed radix (digit v in [0, rho_v])
-        int sg[kMaxK];
-        for (int v = 0; v < nvals; ++v) sg[v] = 0;
-        for (;;) {
-          int c = 0, ms = 0, mr = 0;
-          double cnt = 1.0;
-          for (int v = 0; v < nvals; ++v) {
-            c += sg[v];
-            ms |= s_pm[v][sg[v]];
-            mr |= s_pm[v][rho_d[v] - sg[v]];
-            cnt *= binom_d(rho_d[v], sg[v]);
-          }
-          if (!(c & 1)) {
-            const double2 a = Hb[ms], e = Hb[mr];
-            G[c >> 1].x = fma(cnt, a.x * e.x - a.y * e.y, G[c >> 1].x);
-            G[c >> 1].y = fma(cnt, a.x * e.y + a.y * e.x, G[c >> 1].y);
-          }
-          int v = 0;
-          while (v < nvals && sg[v] == rho_d[v]) sg[v++] = 0;
-          if (v == nvals) break;
-          ++sg[v];
-        }
+    for (int a = 0; a < K2; ++a) G[a] = make_double2(0.0, 0.0);
+    for (int a = 0; 2 * a <= c; ++a) {
+      if (!(need >> a & 1)) continue;
+      const int s = 2 * a;
+      const bool direct = s <= c - s;  // enumerate sigma, or its complement in rho
+      double gx = 0.0, gy = 0.0;
+      for_subsets_of_size(rho, c, direct ? s : c - s, [&](int sub) {
+        const int sg = direct ? sub : rho ^ sub;
+        const double2 h1 = haf(sg), h2 = haf(rho ^ sg);
+        gx = fma(h1.x, h2.x, fma(-h1.y, h2.y, gx));
+        gy = fma(h1.x, h2.y, fma(h1.y, h2.x, gy));
+      });
+      G[a] = make_double2(gx, gy);
+    }
+    double t = 0.0;
+    for (int a = 0; 2 * a <= c; ++a) {
+      if (!(need >> a & 1)) continue;
+      for (int e = 0; 2 * e <= c; ++e) {
+        if (!(need >> e & 1)) continue;
+        const double f = F[(a * K2 + e) * (k + 1) + mu];
+        if (f != 0.0) t = fma(f, G[a].x * G[e].x + G[a].y * G[e].y, t);
       }
     }
-    if (!(rsize & 1)) {
-      // the Hermitian form sum_{ja, jb} F(k, mu, ja, jb) G_ja conj(G_jb), mu = k - |rho|
-      const int mu = k - rsize;
-      double t = 0.0;
-      for (int a = 0; a < K2; ++a)
-        for (int c = 0; c < K2; ++c) {
-          const double f = F[(a * K2 + c) * (k + 1) + mu];
-          if (f != 0.0) t = fma(f, G[a].x * G[c].x + G[a].y * G[c].y, t);
-        }
-      acc = w * t;
+    int64_t w = 1;  // at most 20!, exact
+    for (int v = 0; v < s_nrep; ++v) {
+      const int mv = s_mult[v], al = mv - __popc(rho & s_mask[v]);
+      for (int i = 2; i <= al; ++i) w *= i;
+      w *= s_binom[mv][al];
     }
+    acc = (double)w * t;
   }
   red[threadIdx.x] = acc;
   __syncthreads();
@@ -222,17 +265,18 @@ __global__ void marginal_sum_kernel(const double* __restrict__ part, int nblk, i
   if (lane == 0) q_out[b] = s;
 }
 
-// H_W[b][T] = Haf(B_{x_T}) / t^{|T|/2} for even |T| (0 for odd |T|).
+// H_W[b][T] = Haf(B_{x_T}) / t^{|T|/2} for the sets with a Hafnian in the
+// list (slot >= 0), 0 for the rest (odd |T|, and sizes that no term reads).
 __global__ void rescale_kernel(const double* __restrict__ hafB, const int* __restrict__ slot, int count,
-                               int k, double t, double2* __restrict__ H, int batch) {
+                               int k, SizeScale scale, double2* __restrict__ H, int batch) {
   const int64_t total = (int64_t)batch << k;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
     const int T = (int)(q & ((1 << k) - 1));
     const int c = __popc(T);
     double2 v = make_double2(0.0, 0.0);
-    if (!(c & 1)) {
-      const int j = slot[q];
-      const double sc = pow(t, -0.5 * c);
+    const int j = slot[q];
+    if (j >= 0) {
+      const double sc = scale.s[c];
       v.x = hafB[2 * j] * sc;
       v.y = hafB[2 * j + 1] * sc;
     }
@@ -242,44 +286,123 @@ __global__ void rescale_kernel(const double* __restrict__ hafB, const int* __res
 
 // Exponential-space variant (Appendix D) for the chain sampler: the sampled
 // prefix's sub-Hafnians Haf(B_T) are kept in `cache` (index = position mask
-// over the prefix). For candidate l of step k (prefix x_1..x_{k-1}, l), T with
-// position k-1 reads the step's new value newv[l][T minus that position], the
-// rest the cache; H holds Haf(W_T) = Haf(B_T) / t^{|T|/2} (0 for odd |T|).
-__global__ void chain_table_kernel(const double2* __restrict__ cache, const double2* __restrict__ newv, int k,
-                                   double t, int m, double2* __restrict__ H) {
-  const int64_t total = (int64_t)m << k;
-  const int half = 1 << (k - 1);
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-    const int l = (int)(q >> k);
-    const int T = (int)(q & ((1 << k) - 1));
-    const int c = __popc(T);
-    double2 v = make_double2(0.0, 0.0);
-    if (!(c & 1)) {
-      const double2 h = (T & half) ? newv[(int64_t)l * half + (T & (half - 1))] : cache[T];
-      const double sc = pow(t, -0.5 * c);
-      v.x = h.x * sc;
-      v.y = h.y * sc;
-    }
-    H[q] = v;
+// over the prefix x_1..x_{k-1}). A set T that holds the new photon (position
+// k-1, mode l) needs no Hafnian of its own: expanding along that photon's row,
+//   Haf(B_T) = sum_{i in T'} B(l, x_i) Haf(B_{T' \ i}),   T' = T minus position k-1,
+// where every T' \ i is an even subset of the prefix, so its Hafnian is in the
+// cache. The terms are added in increasing position order.
+__device__ __forceinline__ double2 chain_expand(const double2* __restrict__ cache, const double2* __restrict__ Brow,
+                                                const int* __restrict__ xs, int Tp) {
+  double2 acc = make_double2(0.0, 0.0);
+  for (int rest = Tp; rest; rest &= rest - 1) {
+    const int i = __ffs(rest) - 1;
+    const double2 b = Brow[xs[i]], h = cache[Tp ^ (1 << i)];
+    acc.x = fma(b.x, h.x, fma(-b.y, h.y, acc.x));
+    acc.y = fma(b.x, h.y, fma(b.y, h.x, acc.y));
   }
+  return acc;
+}
+
+// The two halves of the sub-Hafnian table of step k, as Haf(W_T) =
+// Haf(B_T) / t^{|T|/2} (0 for odd |T|): Hp[T] for the sets T of the prefix
+// alone (shared by every candidate; written when Hp is not null), and
+// Hn[l][T'] for T' plus the new photon in mode l0 + l (the expansion above),
+// written for the sizes that `sizes` marks (bit s: s photons; no term reads
+// the others, which keep what they held). x holds the prefix's k-1 modes.
+__global__ void chain_table_kernel(const double2* __restrict__ cache, const double2* __restrict__ B,
+                                   const int* __restrict__ x, int k, SizeScale scale, int l0, int cnt, int m,
+                                   unsigned sizes, double2* __restrict__ Hp, double2* __restrict__ Hn) {
+  __shared__ int xs[kMaxK];
+  if ((int)threadIdx.x < k - 1) xs[threadIdx.x] = x[threadIdx.x];
+  __syncthreads();
+  const int half = 1 << (k - 1);
+  const int64_t total = (int64_t)(cnt + 1) * half;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int row = (int)(q >> (k - 1));
+    const int T = (int)(q & (half - 1));
+    if (row == 0) {
+      if (Hp) {
+        const int c = __popc(T);
+        const double2 h = cache[T];
+        const double sc = (c & 1) ? 0.0 : scale.s[c];
+        Hp[T] = make_double2(h.x * sc, h.y * sc);
+      }
+      continue;
+    }
+    const int s = __popc(T) + 1;
+    if (!(sizes >> s & 1u)) continue;  // never read
+    double2 v = make_double2(0.0, 0.0);
+    if (!(s & 1)) {
+      const double2 h = chain_expand(cache, B + (int64_t)(l0 + row - 1) * m, xs, T);
+      const double sc = scale.s[s];
+      v = make_double2(h.x * sc, h.y * sc);
+    }
+    Hn[q - half] = v;
+  }
+}
+
+// After the pick: cache[T' | 2^(k-1)] = Haf(B_{x_T' + x_k}) for every T' over
+// the first k-1 positions (the expansion above for mode x_k; 0 for even |T'|).
+__global__ void chain_cache_kernel(double2* __restrict__ cache, const double2* __restrict__ B,
+                                   const int* __restrict__ x, int k, int m) {
+  __shared__ int xs[kMaxK];
+  if ((int)threadIdx.x < k) xs[threadIdx.x] = x[threadIdx.x];
+  __syncthreads();
+  const int half = 1 << (k - 1);
+  const double2* Brow = B + (int64_t)xs[k - 1] * m;
+  for (int Tp = blockIdx.x * blockDim.x + threadIdx.x; Tp < half; Tp += gridDim.x * blockDim.x)
+    cache[half + Tp] = (__popc(Tp) & 1) ? chain_expand(cache, Brow, xs, Tp) : make_double2(0.0, 0.0);
 }
 
 // The regrouped sum for `batch` prefixes of length k: block sums into
 // part (batch * blocks doubles), then one total per prefix.
-cudaError_t launch_marginals(int k, int n, const double2* H, const double* F, const int* vmask, const int* nv,
-                             int batch, double* part, double* q_out, cudaStream_t st) {
-  const int nblk = (int)((((int64_t)1 << k) + kMargThreads - 1) / kMargThreads);
-  marginal_terms_kernel<<<dim3(nblk, batch), kMargThreads, 0, st>>>(k, n, H, F, vmask, nv, part);
+// The size classes of rho for prefix length k of n photons (see RhoClasses).
+RhoClasses rho_classes(int k, int n) {
+  RhoClasses rc;
+  rc.start[0] = 0;
+  for (int c = 0; c <= k; c += 2) {
+    bool any = false;
+    for (int ja = 0; ja <= c && !any; ja += 2)
+      for (int jb = 0; jb <= c && !any; jb += 2) any = theorem_range(k, n, k - c, ja, jb);
+    if (!any) continue;
+    int64_t cnt = 1;
+    for (int i = 1; i <= c; ++i) cnt = cnt * (k - c + i) / i;
+    rc.c[rc.ncls] = c;
+    rc.start[rc.ncls + 1] = rc.start[rc.ncls] + cnt;
+    ++rc.ncls;
+  }
+  return rc;
+}
+
+int marginal_blocks(int k, int n) {
+  return (int)std::max<int64_t>(1, (rho_classes(k, n).total() + kMargThreads - 1) / kMargThreads);
+}
+
+cudaError_t launch_marginals(int k, int n, const double2* Hlo, int64_t slo, const double2* Hhi, int64_t shi,
+                             const double* F, const int* vmask, const int* nv, int batch, double* part,
+                             double* q_out, cudaStream_t st) {
+  const RhoClasses rc = rho_classes(k, n);
+  const int nblk = marginal_blocks(k, n);
+  marginal_terms_kernel<<<dim3(nblk, batch), kMargThreads, 0, st>>>(k, n, rc, Hlo, slo, Hhi, shi, F, vmask, nv,
+                                                                     part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   marginal_sum_kernel<<<(batch + 7) / 8, 256, 0, st>>>(part, nblk, batch, q_out);
   return cudaGetLastError();
 }
 
-size_t marginal_part_bytes(int k, int batch) {
-  const int64_t nblk = (((int64_t)1 << k) + kMargThreads - 1) / kMargThreads;
-  return sizeof(double) * (size_t)(nblk * batch);
+// Bit s set if some term of the Theorem 1 sum at prefix length k reads a
+// sub-Hafnian of s photons (a sigma of a size in range, or its complement in rho).
+unsigned needed_sizes(int k, int n) {
+  unsigned sizes = 0;
+  for (int c = 0; c <= k; c += 2)
+    for (int ja = 0; ja <= c; ja += 2)
+      for (int jb = 0; jb <= c; jb += 2)
+        if (theorem_range(k, n, k - c, ja, jb)) sizes |= (1u << ja) | (1u << (c - ja));
+  return sizes;
 }
+
+size_t marginal_part_bytes(int k, int n, int batch) { return sizeof(double) * (size_t)marginal_blocks(k, n) * batch; }
 
 }  // namespace
 }  // namespace gbs
@@ -308,10 +431,12 @@ extern "C" int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int
   const int nsub = 1 << kk;
   std::vector<int> idx, nv_list, slot((size_t)batch * nsub, 0), vmask((size_t)batch * kMaxK, 0), nv(batch, 0);
   std::vector<int64_t> offs;
+  const unsigned sizes = needed_sizes(kk, n);  // the sub-Hafnian sizes that some term reads
   for (int b = 0; b < batch; ++b) {
     const int* xb = hx.data() + (size_t)b * kk;
     for (int T = 0; T < nsub; ++T) {
-      if (__builtin_popcount(T) & 1) continue;
+      slot[(size_t)b * nsub + T] = -1;
+      if (!(sizes >> __builtin_popcount(T) & 1u)) continue;
       slot[(size_t)b * nsub + T] = (int)nv_list.size();
       offs.push_back((int64_t)idx.size());
       int c = 0;
@@ -336,7 +461,7 @@ extern "C" int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int
   const size_t hafB_b = al(16 * (size_t)nh), H_b = al(16 * ((size_t)batch << kk)), slot_b = al(4 * slot.size());
   const size_t F_b = al(8 * (size_t)(kk / 2 + 1) * (kk / 2 + 1) * (kk + 1)), vm_b = al(4 * vmask.size()),
                nv_b = al(4 * (size_t)batch), q_b = al(8 * (size_t)batch);
-  const size_t part_b = al(marginal_part_bytes(kk, batch));
+  const size_t part_b = al(marginal_part_bytes(kk, n, batch));
   void* tmp = nullptr;
   cudaError_t e = scratch_alloc(&tmp, hafB_b + H_b + slot_b + F_b + vm_b + nv_b + q_b + part_b, st);
   if (e != cudaSuccess) return fail(GBS_ENOMEM, "marginal scratch: %s", cudaGetErrorString(e));
@@ -373,13 +498,15 @@ extern "C" int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int
       break;
     }
     rescale_kernel<<<std::min(4096, (int)((((int64_t)batch << kk) + 255) / 256)), 256, 0, st>>>(
-        d_hafB, d_slot, nh, kk, k->t_uniform, d_H, batch);
-    fcoef_kernel<<<1, 256, 0, st>>>(kk, n, k->m, d_F);
+        d_hafB, d_slot, nh, kk, size_scale(k->t_uniform), d_H, batch);
+    fcoef_kernel<<<dim3((int)((fcoef_stride(kk) + 255) / 256), 1), 256, 0, st>>>(kk, n, k->m, 0, d_F);
     double* qd = q_dev ? q_out : d_q;
-    const int nblk = (int)(marginal_part_bytes(kk, 1) / sizeof(double));
+    const int nblk = marginal_blocks(kk, n);
     for (int b0 = 0; b0 < batch && e == cudaSuccess; b0 += 65535)  // the grid's y extent
-      e = launch_marginals(kk, n, d_H + ((int64_t)b0 << kk), d_F, d_vm + (int64_t)b0 * kMaxK, d_nv + b0,
-                           std::min(65535, batch - b0), d_part + (int64_t)b0 * nblk, qd + b0, st);
+      e = launch_marginals(kk, n, d_H + ((int64_t)b0 << kk), (int64_t)1 << kk,
+                           d_H + ((int64_t)b0 << kk) + (kk > 0 ? (int64_t)1 << (kk - 1) : 0), (int64_t)1 << kk, d_F,
+                           d_vm + (int64_t)b0 * kMaxK, d_nv + b0, std::min(65535, batch - b0),
+                           d_part + (int64_t)b0 * nblk, qd + b0, st);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
       ret = cuda_fail(e, "marginal kernels");
@@ -401,49 +528,11 @@ extern "C" int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int
 // Algorithm 1: x_k drawn from the m conditional weights q_n(x_1..x_{k-1}, l),
 // l = 0..m-1, with the caller's uniform number u_k (inverse CDF in mode order).
 // The exponential-space variant of Appendix D: the sub-Hafnians of the sampled
-// prefix are kept on the device across steps, so step k computes only those
-// of subsets that hold the new photon (for each candidate l, the odd subsets
-// T' of positions 0..k-2 plus l), half of the step's table; the marginal
-// kernels then read the cache for the rest. Candidates are taken in chunks
-// of at most 2^22 new sub-Hafnians, so memory stays bounded at large k; the
-// chosen candidate's new sub-Hafnians are then computed once more for the
-// cache.
-namespace {
-
-// new sub-Hafnians of candidates [l0, l0 + cnt) at step kk into dst
-// (cnt * 2^(kk-1) entries, candidate-major)
-int chain_new_subhafnians(const gbs_kernel* k, const std::vector<int>& x, int kk, int l0, int cnt,
-                          cudaStream_t st, double2* dst) {
-  const int half = 1 << (kk - 1);
-  std::vector<int> idx, nvl;
-  std::vector<int64_t> offs;
-  idx.reserve((size_t)cnt * half * kk / 2 + 1);
-  for (int l = l0; l < l0 + cnt; ++l)
-    for (int T = 0; T < half; ++T) {
-      offs.push_back((int64_t)idx.size());
-      for (int i = 0; i < kk - 1; ++i)
-        if (T >> i & 1) idx.push_back(x[i]);
-      idx.push_back(l);
-      nvl.push_back(__builtin_popcount(T) + 1);
-    }
-  BatchArgs a;
-  a.mode = BatchArgs::PROB;
-  a.B = k->B;
-  a.B32 = k->B32;
-  a.m = k->m;
-  a.log_norm_dev = k->dscal;
-  a.idx = idx.data();
-  a.n = nvl.data();
-  a.offs = offs.data();
-  a.batch = cnt * half;
-  a.precision = GBS_FP64;
-  a.stream = st;
-  a.out2 = (double*)dst;
-  return run_batch(a);
-}
-
-}  // namespace
-
+// prefix are kept on the device across steps, and those of the sets that hold
+// the new photon come from them by the row expansion of chain_table_kernel
+// (at most k-1 products each, no Hafnian evaluation). Candidates are taken in
+// chunks of at most 2^23 table entries, so memory stays bounded at large k;
+// after the pick chain_cache_kernel adds the chosen mode's values to the cache.
 extern "C" int gbs_sample_chain(const gbs_kernel* k, int n, const double* uniforms, void* stream, int* x_out) {
   clear_error();
   if (!k || (n > 0 && (!uniforms || !x_out))) return fail(GBS_EINVAL, "null argument");
@@ -453,30 +542,34 @@ extern "C" int gbs_sample_chain(const gbs_kernel* k, int n, const double* unifor
   if (!(k->t_uniform > 0.0)) return fail(GBS_EINVAL, "marginals need r > 0");
   cudaStream_t st = (cudaStream_t)stream;
   const int m = k->m;
-  // candidates per pass at the last step (at most 2^22 new sub-Hafnians)
-  const int chunk_max = std::max(1, std::min(m, (1 << 22) >> (n - 1)));
+  // candidates per pass: at most 2^22 new table entries, and the grid's y extent
+  auto chunk_of = [m](int kk) { return std::max(1, std::min(std::min(m, 65535), (1 << 23) >> kk)); };
   auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
-  const size_t cache_b = al(16 * ((size_t)1 << n)), new_b = al(16 * ((size_t)chunk_max << (n - 1)));
-  const size_t H_b = al(16 * ((size_t)chunk_max << n)), F_b = al(8 * (size_t)(n / 2 + 1) * (n / 2 + 1) * (n + 1));
+  const size_t cache_b = al(16 * ((size_t)1 << n)), x_b = al(4 * (size_t)kMaxK);
+  size_t Hn_n = 0;
+  for (int kk = 1; kk <= n; ++kk) Hn_n = std::max(Hn_n, (size_t)chunk_of(kk) << (kk - 1));
+  const size_t Hp_b = al(16 * ((size_t)1 << (n - 1))), H_b = Hp_b + al(16 * Hn_n);
+  const int64_t fstride = fcoef_stride(n);  // one F table per prefix length 1..n
+  const size_t F_b = al(8 * (size_t)(n * fstride));
   const size_t vm_b = al(4 * (size_t)m * kMaxK), nv_b = al(4 * (size_t)m), q_b = al(8 * (size_t)m);
   size_t part_b = 0;
-  for (int kk = 1; kk <= n; ++kk) {
-    const int ch = std::max(1, std::min(m, (1 << 22) >> (kk - 1)));
-    part_b = std::max(part_b, al(marginal_part_bytes(kk, ch)));
-  }
+  for (int kk = 1; kk <= n; ++kk) part_b = std::max(part_b, al(marginal_part_bytes(kk, n, chunk_of(kk))));
   void* tmp = nullptr;
-  cudaError_t e = scratch_alloc(&tmp, cache_b + new_b + H_b + F_b + vm_b + nv_b + q_b + part_b, st);
+  cudaError_t e = scratch_alloc(&tmp, cache_b + x_b + H_b + F_b + vm_b + nv_b + q_b + part_b, st);
   if (e != cudaSuccess) return fail(GBS_ENOMEM, "chain scratch: %s", cudaGetErrorString(e));
   unsigned char* t = (unsigned char*)tmp;
   double2* d_cache = (double2*)t;
-  double2* d_new = (double2*)(t + cache_b);
-  double2* d_H = (double2*)(t + cache_b + new_b);
-  double* d_F = (double*)(t + cache_b + new_b + H_b);
-  int* d_vm = (int*)(t + cache_b + new_b + H_b + F_b);
-  int* d_nv = (int*)(t + cache_b + new_b + H_b + F_b + vm_b);
-  double* d_q = (double*)(t + cache_b + new_b + H_b + F_b + vm_b + nv_b);
-  double* d_part = (double*)(t + cache_b + new_b + H_b + F_b + vm_b + nv_b + q_b);
-  std::vector<int> x;
+  int* d_x = (int*)(t + cache_b);
+  double2* d_Hp = (double2*)(t + cache_b + x_b);
+  double2* d_Hn = (double2*)(t + cache_b + x_b + Hp_b);
+  double* d_F = (double*)(t + cache_b + x_b + H_b);
+  int* d_vm = (int*)(t + cache_b + x_b + H_b + F_b);
+  int* d_nv = (int*)(t + cache_b + x_b + H_b + F_b + vm_b);
+  double* d_q = (double*)(t + cache_b + x_b + H_b + F_b + vm_b + nv_b);
+  double* d_part = (double*)(t + cache_b + x_b + H_b + F_b + vm_b + nv_b + q_b);
+  const double2* B = (const double2*)k->B;
+  const SizeScale scale = size_scale(k->t_uniform);
+  int x[kMaxK];
   std::vector<double> w(m);
   std::vector<int> vmask((size_t)m * kMaxK), nvals(m);
   int ret = GBS_OK;
@@ -486,9 +579,9 @@ extern "C" int gbs_sample_chain(const gbs_kernel* k, int n, const double* unifor
       ret = cuda_fail(e, "cache init");
       break;
     }
+    fcoef_kernel<<<dim3((int)((fstride + 255) / 256), n), 256, 0, st>>>(1, n, m, fstride, d_F);
     for (int kk = 1; kk <= n && ret == GBS_OK; ++kk) {
-      const int half = 1 << (kk - 1);
-      const int chunk = std::max(1, std::min(m, (1 << 22) >> (kk - 1)));
+      const int chunk = chunk_of(kk);
       // per candidate: position masks of the distinct values (for Per(S_{A,B}))
       std::fill(vmask.begin(), vmask.end(), 0);
       for (int l = 0; l < m; ++l) {
@@ -511,21 +604,21 @@ extern "C" int gbs_sample_chain(const gbs_kernel* k, int n, const double* unifor
         ret = cuda_fail(e, "chain upload");
         break;
       }
-      fcoef_kernel<<<1, 256, 0, st>>>(kk, n, m, d_F);
-      for (int l0 = 0; l0 < m && ret == GBS_OK; l0 += chunk) {
+      const unsigned sizes = needed_sizes(kk, n);
+      const int half = 1 << (kk - 1);
+      for (int l0 = 0; l0 < m && e == cudaSuccess; l0 += chunk) {
         const int cnt = std::min(chunk, m - l0);
-        if ((ret = chain_new_subhafnians(k, x, kk, l0, cnt, st, d_new)) != GBS_OK) break;
-        chain_table_kernel<<<std::min(4096, (int)((((int64_t)cnt << kk) + 255) / 256)), 256, 0, st>>>(
-            d_cache, d_new, kk, k->t_uniform, cnt, d_H);
+        chain_table_kernel<<<std::min(4096, (int)((((int64_t)cnt + 1) * half + 255) / 256)), 256, 0, st>>>(
+            d_cache, B, d_x, kk, scale, l0, cnt, m, sizes, l0 == 0 ? d_Hp : nullptr, d_Hn);
         e = cudaGetLastError();
         if (e == cudaSuccess)
-          e = launch_marginals(kk, n, d_H, d_F, d_vm + (size_t)l0 * kMaxK, d_nv + l0, cnt, d_part, d_q + l0, st);
-        if (e != cudaSuccess) {
-          ret = cuda_fail(e, "chain kernels");
-          break;
-        }
+          e = launch_marginals(kk, n, d_Hp, 0, d_Hn, half, d_F + (kk - 1) * fstride, d_vm + (size_t)l0 * kMaxK, d_nv + l0, cnt, d_part,
+                               d_q + l0, st);
       }
-      if (ret != GBS_OK) break;
+      if (e != cudaSuccess) {
+        ret = cuda_fail(e, "chain kernels");
+        break;
+      }
       if ((e = cudaMemcpyAsync(w.data(), d_q, 8 * (size_t)m, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
           (e = cudaStreamSynchronize(st)) != cudaSuccess) {
         ret = cuda_fail(e, "chain weights");
@@ -543,19 +636,17 @@ extern "C" int gbs_sample_chain(const gbs_kernel* k, int n, const double* unifor
           break;
         }
       }
-      x.push_back(pick);
-      // keep the chosen candidate's new sub-Hafnians: masks with bit kk-1
+      x[kk - 1] = pick;
+      // the chosen mode's new sub-Hafnians (sets that hold position kk-1) into the cache
       if (kk < n) {
-        if (chunk >= m) {
-          e = cudaMemcpyAsync(d_cache + half, d_new + (size_t)pick * half, 16 * (size_t)half,
-                              cudaMemcpyDeviceToDevice, st);
-          if (e != cudaSuccess) {
-            ret = cuda_fail(e, "cache update");
-            break;
-          }
-        } else {
-          std::vector<int> xp(x.begin(), x.end() - 1);
-          if ((ret = chain_new_subhafnians(k, xp, kk, pick, 1, st, d_cache + half)) != GBS_OK) break;
+        if ((e = cudaMemcpyAsync(d_x, x, 4 * (size_t)kk, cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+          ret = cuda_fail(e, "prefix upload");
+          break;
+        }
+        chain_cache_kernel<<<std::min(1024, (half + 255) / 256), 256, 0, st>>>(d_cache, B, d_x, kk, m);
+        if ((e = cudaGetLastError()) != cudaSuccess) {
+          ret = cuda_fail(e, "cache update");
+          break;
         }
       }
     }

@@ -212,3 +212,24 @@ def test_chain_sampler_n12_matches_plain_chain(gbs):
             c = np.cumsum(w)
             x.append(int(min(np.searchsorted(c, u[k - 1] * c[-1], side="right"), m - 1)))
         assert list(got) == x, (list(got), x)
+
+
+@pytest.mark.parametrize("m,n,seed", [(40, 16, 11), (24, 20, 12)])
+def test_chain_sampler_long_matches_plain_chain(gbs, m, n, seed):
+    """16- and 20-photon chain samples (the paper's 18-20 photon regime, with
+    collisions at m = 24): the cached chain, whose new sub-Hafnians come from
+    the row expansion, picks the same modes as the chain that recomputes every
+    conditional weight with gbs_marginal_batch (batched subset sums)."""
+    U = W.haar_unitary(m, 900 + seed)
+    K = gbs.build_kernel(U, np.full(m, 0.8814))
+    rng = np.random.default_rng(seed)
+    for _ in range(2):
+        u = rng.random(n)
+        got = gbs.sample_chain(K, n, u)
+        x = []
+        for k in range(1, n + 1):
+            pre = np.array([x + [l] for l in range(m)], np.int32)
+            w = np.maximum(gbs.marginal_batch(K, pre, n), 0.0)
+            c = np.cumsum(w)
+            x.append(int(min(np.searchsorted(c, u[k - 1] * c[-1], side="right"), m - 1)))
+        assert list(got) == x, (list(got), x)
