@@ -243,7 +243,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="arithmetic of the headline line (mixed: FP32 terms, compensated sums)")
-    ap.add_argument("--profile-workload", default=None, choices=["batched_m64_n16", "mixed_m144", "large_m900"],
+    ap.add_argument("--profile-workload", default=None,
+                    choices=["batched_m64_n16", "mixed_m144", "large_m900", "chain_n16_m256", "chain_n20_m400"],
                     help="no bench line: run that workload's batch --warmup + --steps times in the given "
                          "precision and print its mean time (the command profiler captures run)")
     args = ap.parse_args()
@@ -480,6 +481,8 @@ def profile_workload(args):
     import torch
     import paper_1908_10070_gb300 as gbs
 
+    if args.profile_workload.startswith("chain_"):
+        return profile_chain(args, torch, gbs)
     U, r, pats = W.workload(args.profile_workload)
     prec = gbs.FP64 if args.precision == "fp64" else gbs.MIXED
     K = gbs.build_kernel(U, r)
@@ -491,6 +494,27 @@ def profile_workload(args):
     t = timed_batch(gbs, torch, K, pats, prec, reps=max(1, args.steps), warm=max(0, args.warmup), nvtx="timed")[0]
     print(json.dumps({"workload": args.profile_workload, "precision": args.precision, "patterns": len(pats),
                       "warmup": args.warmup, "steps": args.steps, "ms_per_batch": t}))
+
+
+def profile_chain(args, torch, gbs):
+    """Algorithm 1 chain samples (n photons, m = n^2 modes, r = 0.8814): the
+    warm-up samples, then the timed ones inside the NVTX range "timed"."""
+    n = int(args.profile_workload.split("_")[1][1:])
+    m = n * n
+    K = gbs.build_kernel(W.haar_unitary(m, 40 + n), np.full(m, 0.8814))
+    rng = np.random.default_rng(n)
+    for _ in range(max(0, args.warmup)):
+        gbs.sample_chain(K, n, rng.random(n))
+    torch.cuda.synchronize()
+    ts = []
+    torch.cuda.nvtx.range_push("timed")
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        gbs.sample_chain(K, n, rng.random(n))
+        ts.append(time.perf_counter() - t0)
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"workload": args.profile_workload, "warmup": args.warmup, "steps": len(ts),
+                      "ms_per_sample": 1e3 * float(np.median(ts))}))
 
 
 def extras(gbs, torch, measured_peak):

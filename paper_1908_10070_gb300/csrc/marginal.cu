@@ -104,21 +104,36 @@ __global__ void fcoef_kernel(int k0, int n, int m, int64_t stride, double* __res
 inline int64_t fcoef_stride(int k) { return (int64_t)(k / 2 + 1) * (k / 2 + 1) * (k + 1); }
 
 // The sets rho of the sum that have some (ja, jb) in range: those of the
-// even sizes c[0..ncls-1], C(k, c[i]) of each, numbered from start[i].
+// even sizes c[i], count[i] = C(k, c[i]) of each. A team of team[i] lanes
+// (a power of two up to 32) shares each such rho; class i takes the threads
+// from start[i], a multiple of 32, so a warp never mixes classes.
 struct RhoClasses {
   int ncls = 0;
   int c[kMaxK / 2 + 1];
+  int team[kMaxK / 2 + 1];
+  int64_t count[kMaxK / 2 + 1];
   int64_t start[kMaxK / 2 + 2];
   __host__ __device__ int64_t total() const { return start[ncls]; }
 };
 
-// Calls f(sub) for every subset of rho (c = |rho| set bits) with t elements:
-// Gosper's successor over t-of-c index masks, each spread onto rho's bits.
+constexpr int kTeamWork = 8;  // subsets per lane that size a team
+
+// Calls f(sub) for the subsets of rho (c = |rho| set bits) with t elements of
+// colex ranks lo .. lo + cnt - 1: the first by colex unranking (binom = C(p, i)),
+// the rest by Gosper's successor on the t-of-c index mask; each index mask is
+// spread onto rho's bits.
 template <class Fn>
-__device__ __forceinline__ void for_subsets_of_size(int rho, int c, int t, Fn&& f) {
-  if (t < 0 || t > c) return;
-  unsigned u = (1u << t) - 1;
-  for (;;) {
+__device__ __forceinline__ void for_subsets_range(int rho, int c, int t, int lo, int cnt,
+                                                  const int (*binom)[kMaxK + 1], Fn&& f) {
+  if (cnt <= 0) return;
+  unsigned u = 0;
+  for (int i = t, p = c - 1, rank = lo; i >= 1; --i) {
+    while (binom[p][i] > rank) --p;
+    u |= 1u << p;
+    rank -= binom[p][i];
+    --p;
+  }
+  for (int j = 0;;) {
     int sub = 0;
     for (unsigned uu = u, r = (unsigned)rho; uu; uu >>= 1) {
       const unsigned low = r & (0u - r);
@@ -126,17 +141,17 @@ __device__ __forceinline__ void for_subsets_of_size(int rho, int c, int t, Fn&& 
       r ^= low;
     }
     f(sub);
-    if (t == 0) return;
-    const unsigned lo = u & (0u - u), v = u + lo;
-    u = v + (((v ^ u) / lo) >> 2);
-    if (u >= (1u << c)) return;
+    if (++j == cnt) return;
+    const unsigned l = u & (0u - u), v = u + l;  // t >= 1 here: C(c, 0) = 1 subset
+    u = v + (((v ^ u) / l) >> 2);
   }
 }
 
-// The Theorem 1 sum over position sets, one thread per rho = [k] \ A of a
-// size class in `rc` (thread i of class c: the rho of rank i among the
-// c-element sets in colex order). For the
-// sets A, B of one multiset alpha (Per(S_{A,B}) = prod_v alpha_v!, 0 for
+// The Theorem 1 sum over position sets rho = [k] \ A of the size classes in
+// `rc`: team i of class c takes the rho of colex rank i among the c-element
+// sets; its lanes split each enumeration below into contiguous colex ranges
+// and add their partial sums in a fixed butterfly, and the first lane forms
+// the rho's term. For the sets A, B of one multiset alpha (Per(S_{A,B}) = prod_v alpha_v!, 0 for
 // different multisets), rho_A and rho_B have equal sub-Hafnians, so
 //   q_n = sum_rho w(rho) sum_{ja, jb} F(k, k - |rho|, ja, jb) / f_n G(rho, ja) conj(G(rho, jb)),
 //   G(rho, j) = sum_{sigma subset of rho, |sigma| = j} Haf(W_sigma) Haf(W_{rho \ sigma}),
@@ -198,51 +213,66 @@ __global__ void __launch_bounds__(kMargThreads) marginal_terms_kernel(int k, int
   auto haf = [&](int T) { return (T & half) ? hi[T ^ half] : lo[T]; };
   const int64_t idx = (int64_t)blockIdx.x * kMargThreads + threadIdx.x;
   double acc = 0.0;
-  if (idx < rc.total()) {
+  if (idx < rc.total()) {  // whole warps: every class spans a multiple of 32 threads
     int cls = 0;
     while (idx >= rc.start[cls + 1]) ++cls;
-    const int c = rc.c[cls];
+    const int c = rc.c[cls], T = rc.team[cls];
+    const int64_t local = idx - rc.start[cls];
+    const int64_t team = local / T;
+    const int member = (int)(local % T);
+    const bool real = team < rc.count[cls];  // the rest pad the class to whole warps
     // colex unranking: rank = sum_i C(p_i, i) over the positions p_1 < .. < p_c
-    int rank = (int)(idx - rc.start[cls]), rho = 0;
-    for (int i = c, p = k - 1; i >= 1; --i) {
-      while (s_binom[p][i] > rank) --p;
-      rho |= 1 << p;
-      rank -= s_binom[p][i];
-      --p;
-    }
+    int rho = 0;
+    if (real)
+      for (int i = c, p = k - 1, rank = (int)team; i >= 1; --i) {
+        while (s_binom[p][i] > rank) --p;
+        rho |= 1 << p;
+        rank -= s_binom[p][i];
+        --p;
+      }
     const unsigned need = s_need[k - c] & ((2u << (c >> 1)) - 1);
     const int mu = k - c;
     double2 G[kMaxK / 2 + 1];
     for (int a = 0; a < K2; ++a) G[a] = make_double2(0.0, 0.0);
     for (int a = 0; 2 * a <= c; ++a) {
-      if (!(need >> a & 1)) continue;
+      if (!(need >> a & 1)) continue;  // the same for the whole warp
       const int s = 2 * a;
       const bool direct = s <= c - s;  // enumerate sigma, or its complement in rho
+      const int t = direct ? s : c - s;
+      const int N = s_binom[c][t];
+      const int lo = (int)((int64_t)N * member / T), hi = (int)((int64_t)N * (member + 1) / T);
       double gx = 0.0, gy = 0.0;
-      for_subsets_of_size(rho, c, direct ? s : c - s, [&](int sub) {
-        const int sg = direct ? sub : rho ^ sub;
-        const double2 h1 = haf(sg), h2 = haf(rho ^ sg);
-        gx = fma(h1.x, h2.x, fma(-h1.y, h2.y, gx));
-        gy = fma(h1.x, h2.y, fma(h1.y, h2.x, gy));
-      });
+      if (real)
+        for_subsets_range(rho, c, t, lo, hi - lo, s_binom, [&](int sub) {
+          const int sg = direct ? sub : rho ^ sub;
+          const double2 h1 = haf(sg), h2 = haf(rho ^ sg);
+          gx = fma(h1.x, h2.x, fma(-h1.y, h2.y, gx));
+          gy = fma(h1.x, h2.y, fma(h1.y, h2.x, gy));
+        });
+      for (int off = T >> 1; off > 0; off >>= 1) {
+        gx += __shfl_xor_sync(0xffffffffu, gx, off);
+        gy += __shfl_xor_sync(0xffffffffu, gy, off);
+      }
       G[a] = make_double2(gx, gy);
     }
-    double t = 0.0;
-    for (int a = 0; 2 * a <= c; ++a) {
-      if (!(need >> a & 1)) continue;
-      for (int e = 0; 2 * e <= c; ++e) {
-        if (!(need >> e & 1)) continue;
-        const double f = F[(a * K2 + e) * (k + 1) + mu];
-        if (f != 0.0) t = fma(f, G[a].x * G[e].x + G[a].y * G[e].y, t);
+    if (real && member == 0) {
+      double t = 0.0;
+      for (int a = 0; 2 * a <= c; ++a) {
+        if (!(need >> a & 1)) continue;
+        for (int e = 0; 2 * e <= c; ++e) {
+          if (!(need >> e & 1)) continue;
+          const double f = F[(a * K2 + e) * (k + 1) + mu];
+          if (f != 0.0) t = fma(f, G[a].x * G[e].x + G[a].y * G[e].y, t);
+        }
       }
+      int64_t w = 1;  // at most 20!, exact
+      for (int v = 0; v < s_nrep; ++v) {
+        const int mv = s_mult[v], al = mv - __popc(rho & s_mask[v]);
+        for (int i = 2; i <= al; ++i) w *= i;
+        w *= s_binom[mv][al];
+      }
+      acc = (double)w * t;
     }
-    int64_t w = 1;  // at most 20!, exact
-    for (int v = 0; v < s_nrep; ++v) {
-      const int mv = s_mult[v], al = mv - __popc(rho & s_mask[v]);
-      for (int i = 2; i <= al; ++i) w *= i;
-      w *= s_binom[mv][al];
-    }
-    acc = (double)w * t;
   }
   red[threadIdx.x] = acc;
   __syncthreads();
@@ -358,18 +388,28 @@ __global__ void chain_cache_kernel(double2* __restrict__ cache, const double2* _
 // part (batch * blocks doubles), then one total per prefix.
 // The size classes of rho for prefix length k of n photons (see RhoClasses).
 RhoClasses rho_classes(int k, int n) {
+  auto binom = [](int a, int b) {
+    int64_t v = 1;
+    for (int i = 1; i <= b; ++i) v = v * (a - b + i) / i;
+    return v;
+  };
   RhoClasses rc;
   rc.start[0] = 0;
   for (int c = 0; c <= k; c += 2) {
-    bool any = false;
-    for (int ja = 0; ja <= c && !any; ja += 2)
+    int64_t work = 0;  // subsets one rho enumerates (the kernel's sizes ja in range)
+    for (int ja = 0; ja <= c; ja += 2) {
+      bool any = false;
       for (int jb = 0; jb <= c && !any; jb += 2) any = theorem_range(k, n, k - c, ja, jb);
-    if (!any) continue;
-    int64_t cnt = 1;
-    for (int i = 1; i <= c; ++i) cnt = cnt * (k - c + i) / i;
-    rc.c[rc.ncls] = c;
-    rc.start[rc.ncls + 1] = rc.start[rc.ncls] + cnt;
-    ++rc.ncls;
+      if (any) work += binom(c, std::min(ja, c - ja));
+    }
+    if (!work) continue;
+    int T = 1;
+    while (T < 32 && (int64_t)T * kTeamWork < work) T *= 2;
+    const int i = rc.ncls++;
+    rc.c[i] = c;
+    rc.team[i] = T;
+    rc.count[i] = binom(k, c);
+    rc.start[i + 1] = rc.start[i] + (rc.count[i] * T + 31) / 32 * 32;
   }
   return rc;
 }
