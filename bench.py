@@ -665,6 +665,17 @@ def sampler(gbs):
             gbs.sample_chain(Kc, n_, uu)
             ts.append(time.perf_counter() - t0)
         chain["n%d_m%d" % (n_, m_)] = {"s_per_sample": float(np.median(ts)), "samples": reps}
+    # independent samples advanced together (gbs_sample_chain_batch)
+    for n_, S in ((12, 1024), (16, 256), (20, 32)):
+        m_ = n_ * n_
+        Kc = gbs.build_kernel(W.haar_unitary(m_, 40 + n_), np.full(m_, 0.8814))
+        rng = np.random.default_rng(100 + n_)
+        gbs.sample_chain_batch(Kc, n_, rng.random((S, n_)))  # warm-up
+        uu = rng.random((S, n_))
+        t0 = time.perf_counter()
+        gbs.sample_chain_batch(Kc, n_, uu)
+        dt = time.perf_counter() - t0
+        chain["batch_n%d_m%d" % (n_, m_)] = {"samples": S, "s_per_batch": dt, "samples_per_s": S / dt}
     return {"bruteforce_n4_m16": {"configurations": 3876, "draws": len(u), "wall_ms": 1e3 * t_bf,
                                   "draws_per_s": len(u) / t_bf, "P_n": total},
             "photon_number_m36_nmax200_wall_ms": 1e3 * t_pn,

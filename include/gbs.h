@@ -270,6 +270,18 @@ int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int batch, int
  * Errors: GBS_EINVAL, GBS_ERANGE, GBS_ENOMEM, GBS_ECUDA. */
 int gbs_sample_chain(const gbs_kernel* k, int n, const double* uniforms, void* stream, int* x_out);
 
+/* `samples` independent chain samples (gbs_sample_chain each), advanced
+ * together: every step covers all samples' m candidates in the same launches,
+ * with one copy of the weights and one stream synchronisation per step.
+ * Sample s equals gbs_sample_chain with uniforms[s * n .. s * n + n - 1].
+ *   samples   >= 0; they go in groups of at most 2^28 / 2^n (their sub-Hafnian
+ *             caches, 2^n complex doubles each, stay within 4 GB).
+ *   uniforms  samples * n numbers in [0, 1), sample-major, HOST memory.
+ *   x_out     samples * n ints, HOST memory, sample-major.
+ * Errors: GBS_EINVAL, GBS_ERANGE, GBS_ENOMEM, GBS_ECUDA. */
+int gbs_sample_chain_batch(const gbs_kernel* k, int n, int samples, const double* uniforms, void* stream,
+                           int* x_out);
+
 /* One complete sample (Sec. 3, Steps 1-3): the photon number n drawn from
  * P_n of Eq. Eqdistribution restricted to n <= n_max and renormalised (inverse
  * CDF with uniforms[0]), then the n photons placed by gbs_sample_chain with

@@ -21,7 +21,7 @@ __all__ = [
     "FP64", "MIXED", "MAX_N", "GbsError", "lib", "build_kernel", "KernelMatrix",
     "hafnian_batch", "hafnian_batch_noalloc", "prob_batch", "autotune", "measure_fp64_peak", "Server", "serve_create", "pack_patterns",
     "pack_matrices", "last_error", "ERRORS", "photon_number_dist", "sample_bruteforce", "marginal_batch", "sample_chain",
-    "clear_plans",
+    "sample_chain_batch", "clear_plans",
 ]
 
 FP64 = 0
@@ -77,6 +77,7 @@ def lib():
             L.gbs_sample_bruteforce.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, vp, ip, dp]
             L.gbs_marginal_batch.argtypes = [vp, ip, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, dp]
             L.gbs_sample_chain.argtypes = [vp, ctypes.c_int, dp, vp, ip]
+            L.gbs_sample_chain_batch.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, vp, ip]
             L.gbs_sample.argtypes = [vp, ctypes.c_int, dp, vp, ctypes.POINTER(ctypes.c_int), ip]
             L.gbs_autotune.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int)]
             L.gbs_measure_fp64_peak.argtypes = [vp, dp]
@@ -273,6 +274,18 @@ def sample_chain(kernel: KernelMatrix, n: int, uniforms, stream=None) -> np.ndar
     x = np.zeros(max(n, 1), dtype=np.int32)
     _check(lib().gbs_sample_chain(kernel.handle, int(n), _ptr(u), _stream(stream), _ptr(x)))
     return x[:n]
+
+
+def sample_chain_batch(kernel: KernelMatrix, n: int, uniforms, stream=None) -> np.ndarray:
+    """Independent Algorithm 1 samples advanced together (gbs_sample_chain_batch).
+    uniforms: (samples, n) numbers in [0, 1). Returns (samples, n) modes."""
+    u = np.ascontiguousarray(uniforms, dtype=np.float64)
+    S = u.shape[0] if u.ndim == 2 else 0
+    if u.ndim != 2 or u.shape[1] != n:
+        raise ValueError("uniforms must have shape (samples, n)")
+    x = np.zeros((max(S, 1), max(n, 1)), dtype=np.int32)
+    _check(lib().gbs_sample_chain_batch(kernel.handle, int(n), int(S), _ptr(u), _stream(stream), _ptr(x)))
+    return x[:S, :n]
 
 
 def sample(kernel: KernelMatrix, n_max: int, uniforms, stream=None) -> np.ndarray:

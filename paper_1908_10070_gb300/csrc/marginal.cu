@@ -158,18 +158,20 @@ __device__ __forceinline__ void for_subsets_range(int rho, int c, int t, int lo,
 //   w(rho) = prod_v alpha_v! C(m_v, alpha_v),  alpha_v = m_v - |rho cap (positions of mode v)|
 // (m_v the multiplicity of mode v in the prefix; w = 1 without repeated
 // modes, the Proposition). Only the sizes ja with some jb in range are
-// enumerated, and by their complements when those are smaller.
-//   H: Haf(W_T) by position mask T (0 for odd |T|); T without position k-1
-//      reads Hlo + b * slo, T with it Hhi + b * shi at T minus that position.
-//   vmask, nv: per prefix, the position mask of each of its nv distinct modes.
+// enumerated, and by their complements when those are smaller; G(rho, j) =
+// G(rho, |rho| - j) (the same products), so each such pair is formed once.
+//   H: Haf(W_T) by position mask T (0 for odd |T|); for prefix b, T without
+//      position k-1 reads Hlo + ((lo_off + b) / lo_div) * slo, T with it
+//      Hhi + b * shi, at T minus that position.
+//   modes: the k modes of prefix b at modes + b * k (repeated modes give w).
 // Each block writes the sum of its threads (fixed tree) to
 // part[b * gridDim.x + blockIdx.x].
 __global__ void __launch_bounds__(kMargThreads) marginal_terms_kernel(int k, int n, RhoClasses rc,
                                                                      const double2* __restrict__ Hlo,
-                                                                     int64_t slo, const double2* __restrict__ Hhi,
+                                                                     int64_t slo, int64_t lo_off, int lo_div,
+                                                                     const double2* __restrict__ Hhi,
                                                                      int64_t shi, const double* __restrict__ F,
-                                                                     const int* __restrict__ vmask,
-                                                                     const int* __restrict__ nv,
+                                                                     const int* __restrict__ modes,
                                                                      double* __restrict__ part) {
   __shared__ double red[kMargThreads];
   __shared__ unsigned s_need[kMaxK + 1];  // per mu: bit a set if ja = 2a has some jb in range
@@ -195,19 +197,26 @@ __global__ void __launch_bounds__(kMargThreads) marginal_terms_kernel(int k, int
     s_need[mu] = need;
   }
   if (threadIdx.x == 0) {
-    // the repeated modes only (a mode seen once has weight 1 either way)
-    const int* vm = vmask + (int64_t)b * kMaxK;
+    // position masks of the repeated modes only (a mode seen once has weight 1 either way)
+    const int* xb = modes + (int64_t)b * k;
     int r = 0;
-    for (int v = 0; v < nv[b]; ++v)
-      if (__popc(vm[v]) > 1) {
-        s_mask[r] = vm[v];
-        s_mult[r] = __popc(vm[v]);
+    unsigned seen = 0;
+    for (int i = 0; i < k; ++i) {
+      if (seen >> i & 1u) continue;
+      int mask = 1 << i;
+      for (int j = i + 1; j < k; ++j)
+        if (xb[j] == xb[i]) mask |= 1 << j;
+      seen |= (unsigned)mask;
+      if (mask != (1 << i)) {
+        s_mask[r] = mask;
+        s_mult[r] = __popc(mask);
         ++r;
       }
+    }
     s_nrep = r;
   }
   __syncthreads();
-  const double2* lo = Hlo + b * slo;
+  const double2* lo = Hlo + ((lo_off + b) / lo_div) * slo;
   const double2* hi = Hhi + b * shi;
   const int half = k > 0 ? 1 << (k - 1) : 0;
   auto haf = [&](int T) { return (T & half) ? hi[T ^ half] : lo[T]; };
@@ -236,6 +245,11 @@ __global__ void __launch_bounds__(kMargThreads) marginal_terms_kernel(int k, int
     for (int a = 0; a < K2; ++a) G[a] = make_double2(0.0, 0.0);
     for (int a = 0; 2 * a <= c; ++a) {
       if (!(need >> a & 1)) continue;  // the same for the whole warp
+      const int a2 = (c >> 1) - a;     // G(rho, 2a) = G(rho, c - 2a)
+      if (a2 < a && (need >> a2 & 1)) {
+        G[a] = G[a2];
+        continue;
+      }
       const int s = 2 * a;
       const bool direct = s <= c - s;  // enumerate sigma, or its complement in rho
       const int t = direct ? s : c - s;
@@ -314,10 +328,11 @@ __global__ void rescale_kernel(const double* __restrict__ hafB, const int* __res
   }
 }
 
-// Exponential-space variant (Appendix D) for the chain sampler: the sampled
-// prefix's sub-Hafnians Haf(B_T) are kept in `cache` (index = position mask
-// over the prefix x_1..x_{k-1}). A set T that holds the new photon (position
-// k-1, mode l) needs no Hafnian of its own: expanding along that photon's row,
+// Exponential-space variant (Appendix D) for the chain sampler: each sample's
+// sampled prefix keeps its sub-Hafnians Haf(B_T) in a cache (index = position
+// mask over the prefix x_1..x_{k-1}). A set T that holds the new photon
+// (position k-1, mode l) needs no Hafnian of its own: expanding along that
+// photon's row,
 //   Haf(B_T) = sum_{i in T'} B(l, x_i) Haf(B_{T' \ i}),   T' = T minus position k-1,
 // where every T' \ i is an even subset of the prefix, so its Hafnian is in the
 // cache. The terms are added in increasing position order.
@@ -333,55 +348,72 @@ __device__ __forceinline__ double2 chain_expand(const double2* __restrict__ cach
   return acc;
 }
 
-// The two halves of the sub-Hafnian table of step k, as Haf(W_T) =
-// Haf(B_T) / t^{|T|/2} (0 for odd |T|): Hp[T] for the sets T of the prefix
-// alone (shared by every candidate; written when Hp is not null), and
-// Hn[l][T'] for T' plus the new photon in mode l0 + l (the expansion above),
-// written for the sizes that `sizes` marks (bit s: s photons; no term reads
-// the others, which keep what they held). x holds the prefix's k-1 modes.
-__global__ void chain_table_kernel(const double2* __restrict__ cache, const double2* __restrict__ B,
-                                   const int* __restrict__ x, int k, SizeScale scale, int l0, int cnt, int m,
-                                   unsigned sizes, double2* __restrict__ Hp, double2* __restrict__ Hn) {
-  __shared__ int xs[kMaxK];
-  if ((int)threadIdx.x < k - 1) xs[threadIdx.x] = x[threadIdx.x];
-  __syncthreads();
+// Hp[s][T] = Haf(W_T) = Haf(B_T) t^{-|T|/2} for the sets T of sample s's
+// prefix (k-1 positions; 0 for odd |T|): the half of step k's table that every
+// candidate shares. cache: `samples` caches of cstride entries.
+__global__ void chain_prefix_kernel(const double2* __restrict__ cache, int64_t cstride, int k, int samples,
+                                    SizeScale scale, double2* __restrict__ Hp) {
   const int half = 1 << (k - 1);
-  const int64_t total = (int64_t)(cnt + 1) * half;
+  const int64_t total = (int64_t)samples * half;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-    const int row = (int)(q >> (k - 1));
     const int T = (int)(q & (half - 1));
-    if (row == 0) {
-      if (Hp) {
-        const int c = __popc(T);
-        const double2 h = cache[T];
-        const double sc = (c & 1) ? 0.0 : scale.s[c];
-        Hp[T] = make_double2(h.x * sc, h.y * sc);
-      }
-      continue;
-    }
-    const int s = __popc(T) + 1;
-    if (!(sizes >> s & 1u)) continue;  // never read
-    double2 v = make_double2(0.0, 0.0);
-    if (!(s & 1)) {
-      const double2 h = chain_expand(cache, B + (int64_t)(l0 + row - 1) * m, xs, T);
-      const double sc = scale.s[s];
-      v = make_double2(h.x * sc, h.y * sc);
-    }
-    Hn[q - half] = v;
+    const int c = __popc(T);
+    const double2 h = cache[(q >> (k - 1)) * cstride + T];
+    const double sc = (c & 1) ? 0.0 : scale.s[c];
+    Hp[q] = make_double2(h.x * sc, h.y * sc);
   }
 }
 
-// After the pick: cache[T' | 2^(k-1)] = Haf(B_{x_T' + x_k}) for every T' over
-// the first k-1 positions (the expansion above for mode x_k; 0 for even |T'|).
-__global__ void chain_cache_kernel(double2* __restrict__ cache, const double2* __restrict__ B,
-                                   const int* __restrict__ x, int k, int m) {
-  __shared__ int xs[kMaxK];
-  if ((int)threadIdx.x < k) xs[threadIdx.x] = x[threadIdx.x];
-  __syncthreads();
+// The other half for candidates g0 .. g0 + cnt - 1 (candidate g: sample g / m,
+// mode g % m): Hn[b][T'] = Haf(W) of T' plus the new photon (the expansion
+// above), written for the sizes that `sizes` marks (bit s: s photons; no term
+// reads the others, which keep what they held). Also the candidate's k modes
+// (its sample's prefix, then its own mode) into modes[b * k ..].
+//   x: kMaxK sampled modes per sample.
+__global__ void chain_table_kernel(const double2* __restrict__ cache, int64_t cstride, const double2* __restrict__ B,
+                                   const int* __restrict__ x, int k, SizeScale scale, int64_t g0, int cnt, int m,
+                                   unsigned sizes, double2* __restrict__ Hn, int* __restrict__ modes) {
   const int half = 1 << (k - 1);
-  const double2* Brow = B + (int64_t)xs[k - 1] * m;
-  for (int Tp = blockIdx.x * blockDim.x + threadIdx.x; Tp < half; Tp += gridDim.x * blockDim.x)
-    cache[half + Tp] = (__popc(Tp) & 1) ? chain_expand(cache, Brow, xs, Tp) : make_double2(0.0, 0.0);
+  const int64_t total = (int64_t)cnt * half;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = q >> (k - 1);
+    const int T = (int)(q & (half - 1));
+    const int64_t g = g0 + b;
+    const int64_t smp = g / m;
+    const int l = (int)(g - smp * m);
+    const int* xs = x + smp * kMaxK;
+    if (T < k) modes[b * k + T] = T < k - 1 ? xs[T] : l;  // half >= k
+    const int s = __popc(T) + 1;
+    if (!(sizes >> s & 1u)) continue;
+    double2 v = make_double2(0.0, 0.0);
+    if (!(s & 1)) {
+      const double2 h = chain_expand(cache + smp * cstride, B + (int64_t)l * m, xs, T);
+      v = make_double2(h.x * scale.s[s], h.y * scale.s[s]);
+    }
+    Hn[q] = v;
+  }
+}
+
+// Every cache starts as Haf of the empty matrix, 1.
+__global__ void chain_init_kernel(double2* __restrict__ cache, int64_t cstride, int samples) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < samples; s += gridDim.x * blockDim.x)
+    cache[s * cstride] = make_double2(1.0, 0.0);
+}
+
+// After the picks: cache[s][T' | 2^(k-1)] = Haf(B) of T' plus x_k for every T'
+// over the first k-1 positions of sample s (the expansion above for the
+// sampled mode x_k; 0 for even |T'|).
+__global__ void chain_cache_kernel(double2* __restrict__ cache, int64_t cstride, const double2* __restrict__ B,
+                                   const int* __restrict__ x, int k, int m, int samples) {
+  const int half = 1 << (k - 1);
+  const int64_t total = (int64_t)samples * half;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t smp = q >> (k - 1);
+    const int Tp = (int)(q & (half - 1));
+    const int* xs = x + smp * kMaxK;
+    double2* c = cache + smp * cstride;
+    c[half + Tp] = (__popc(Tp) & 1) ? chain_expand(c, B + (int64_t)xs[k - 1] * m, xs, Tp) : make_double2(0.0, 0.0);
+  }
 }
 
 // The regrouped sum for `batch` prefixes of length k: block sums into
@@ -418,13 +450,13 @@ int marginal_blocks(int k, int n) {
   return (int)std::max<int64_t>(1, (rho_classes(k, n).total() + kMargThreads - 1) / kMargThreads);
 }
 
-cudaError_t launch_marginals(int k, int n, const double2* Hlo, int64_t slo, const double2* Hhi, int64_t shi,
-                             const double* F, const int* vmask, const int* nv, int batch, double* part,
-                             double* q_out, cudaStream_t st) {
+cudaError_t launch_marginals(int k, int n, const double2* Hlo, int64_t slo, int64_t lo_off, int lo_div,
+                             const double2* Hhi, int64_t shi, const double* F, const int* modes, int batch,
+                             double* part, double* q_out, cudaStream_t st) {
   const RhoClasses rc = rho_classes(k, n);
   const int nblk = marginal_blocks(k, n);
-  marginal_terms_kernel<<<dim3(nblk, batch), kMargThreads, 0, st>>>(k, n, rc, Hlo, slo, Hhi, shi, F, vmask, nv,
-                                                                     part);
+  marginal_terms_kernel<<<dim3(nblk, batch), kMargThreads, 0, st>>>(k, n, rc, Hlo, slo, lo_off, lo_div, Hhi, shi, F,
+                                                                     modes, part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   marginal_sum_kernel<<<(batch + 7) / 8, 256, 0, st>>>(part, nblk, batch, q_out);
@@ -469,7 +501,7 @@ extern "C" int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int
   for (size_t i = 0; i < (size_t)batch * kk; ++i)
     if (hx[i] < 0 || hx[i] >= k->m) return fail(GBS_ERANGE, "mode index %d outside [0, %d)", hx[i], k->m);
   const int nsub = 1 << kk;
-  std::vector<int> idx, nv_list, slot((size_t)batch * nsub, 0), vmask((size_t)batch * kMaxK, 0), nv(batch, 0);
+  std::vector<int> idx, nv_list, slot((size_t)batch * nsub, 0);
   std::vector<int64_t> offs;
   const unsigned sizes = needed_sizes(kk, n);  // the sub-Hafnian sizes that some term reads
   for (int b = 0; b < batch; ++b) {
@@ -487,33 +519,24 @@ extern "C" int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int
         }
       nv_list.push_back(c);
     }
-    // position masks of the distinct mode values (for Per(S_{A,B}))
-    for (int i = 0; i < kk; ++i) {
-      int v = 0;
-      while (v < nv[b] && xb[__builtin_ctz(vmask[(size_t)b * kMaxK + v])] != xb[i]) ++v;
-      if (v == nv[b]) nv[b]++;
-      vmask[(size_t)b * kMaxK + v] |= 1 << i;
-    }
   }
   if (idx.empty()) idx.push_back(0);
   const int nh = (int)nv_list.size();
   auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
   const size_t hafB_b = al(16 * (size_t)nh), H_b = al(16 * ((size_t)batch << kk)), slot_b = al(4 * slot.size());
-  const size_t F_b = al(8 * (size_t)(kk / 2 + 1) * (kk / 2 + 1) * (kk + 1)), vm_b = al(4 * vmask.size()),
-               nv_b = al(4 * (size_t)batch), q_b = al(8 * (size_t)batch);
+  const size_t F_b = al(8 * (size_t)fcoef_stride(kk)), x_b = al(4 * hx.size()), q_b = al(8 * (size_t)batch);
   const size_t part_b = al(marginal_part_bytes(kk, n, batch));
   void* tmp = nullptr;
-  cudaError_t e = scratch_alloc(&tmp, hafB_b + H_b + slot_b + F_b + vm_b + nv_b + q_b + part_b, st);
+  cudaError_t e = scratch_alloc(&tmp, hafB_b + H_b + slot_b + F_b + x_b + q_b + part_b, st);
   if (e != cudaSuccess) return fail(GBS_ENOMEM, "marginal scratch: %s", cudaGetErrorString(e));
   unsigned char* t = (unsigned char*)tmp;
   double* d_hafB = (double*)t;
   double2* d_H = (double2*)(t + hafB_b);
   int* d_slot = (int*)(t + hafB_b + H_b);
   double* d_F = (double*)(t + hafB_b + H_b + slot_b);
-  int* d_vm = (int*)(t + hafB_b + H_b + slot_b + F_b);
-  int* d_nv = (int*)(t + hafB_b + H_b + slot_b + F_b + vm_b);
-  double* d_q = (double*)(t + hafB_b + H_b + slot_b + F_b + vm_b + nv_b);
-  double* d_part = (double*)(t + hafB_b + H_b + slot_b + F_b + vm_b + nv_b + q_b);
+  int* d_x = (int*)(t + hafB_b + H_b + slot_b + F_b);
+  double* d_q = (double*)(t + hafB_b + H_b + slot_b + F_b + x_b);
+  double* d_part = (double*)(t + hafB_b + H_b + slot_b + F_b + x_b + q_b);
   const bool q_dev = is_device_ptr(q_out);
   int ret = GBS_OK;
   do {
@@ -532,8 +555,7 @@ extern "C" int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int
     a.out2 = d_hafB;
     if ((ret = run_batch(a)) != GBS_OK) break;
     if ((e = cudaMemcpyAsync(d_slot, slot.data(), 4 * slot.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(d_vm, vmask.data(), 4 * vmask.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(d_nv, nv.data(), 4 * (size_t)batch, cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+        (e = cudaMemcpyAsync(d_x, hx.data(), 4 * hx.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess) {
       ret = cuda_fail(e, "marginal upload");
       break;
     }
@@ -543,10 +565,10 @@ extern "C" int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int
     double* qd = q_dev ? q_out : d_q;
     const int nblk = marginal_blocks(kk, n);
     for (int b0 = 0; b0 < batch && e == cudaSuccess; b0 += 65535)  // the grid's y extent
-      e = launch_marginals(kk, n, d_H + ((int64_t)b0 << kk), (int64_t)1 << kk,
+      e = launch_marginals(kk, n, d_H + ((int64_t)b0 << kk), (int64_t)1 << kk, 0, 1,
                            d_H + ((int64_t)b0 << kk) + (kk > 0 ? (int64_t)1 << (kk - 1) : 0), (int64_t)1 << kk, d_F,
-                           d_vm + (int64_t)b0 * kMaxK, d_nv + b0, std::min(65535, batch - b0),
-                           d_part + (int64_t)b0 * nblk, qd + b0, st);
+                           d_x + (int64_t)b0 * kk, std::min(65535, batch - b0), d_part + (int64_t)b0 * nblk,
+                           qd + b0, st);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
       ret = cuda_fail(e, "marginal kernels");
@@ -565,136 +587,136 @@ extern "C" int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int
   return ret;
 }
 
-// Algorithm 1: x_k drawn from the m conditional weights q_n(x_1..x_{k-1}, l),
-// l = 0..m-1, with the caller's uniform number u_k (inverse CDF in mode order).
-// The exponential-space variant of Appendix D: the sub-Hafnians of the sampled
-// prefix are kept on the device across steps, and those of the sets that hold
-// the new photon come from them by the row expansion of chain_table_kernel
-// (at most k-1 products each, no Hafnian evaluation). Candidates are taken in
-// chunks of at most 2^23 table entries, so memory stays bounded at large k;
-// after the pick chain_cache_kernel adds the chosen mode's values to the cache.
-extern "C" int gbs_sample_chain(const gbs_kernel* k, int n, const double* uniforms, void* stream, int* x_out) {
+// Algorithm 1 for `samples` independent samples at once: x_k of each drawn
+// from its m conditional weights q_n(x_1..x_{k-1}, l), l = 0..m-1, with its
+// own uniform number (inverse CDF in mode order). The exponential-space
+// variant of Appendix D: each sample's prefix sub-Hafnians stay on the device
+// across steps, and those of the sets that hold the new photon come from them
+// by the row expansion of chain_table_kernel (at most k-1 products each, no
+// Hafnian evaluation). A step covers every sample's candidates in the same
+// launches, in chunks of at most 2^22 new table entries; one copy of the
+// weights and one synchronisation per step serve all samples. Samples go in
+// groups whose caches fit in 2^28 entries (4 GB).
+extern "C" int gbs_sample_chain_batch(const gbs_kernel* k, int n, int samples, const double* uniforms, void* stream,
+                                      int* x_out) {
   clear_error();
-  if (!k || (n > 0 && (!uniforms || !x_out))) return fail(GBS_EINVAL, "null argument");
+  if (!k || (n > 0 && samples > 0 && (!uniforms || !x_out))) return fail(GBS_EINVAL, "null argument");
+  if (samples < 0) return fail(GBS_EINVAL, "samples = %d is negative", samples);
   if (n < 0 || n > kMaxK || (n & 1)) return fail(GBS_ERANGE, "n = %d must be even and <= %d", n, kMaxK);
-  if (n == 0) return GBS_OK;
+  if (n == 0 || samples == 0) return GBS_OK;
   if (!k->r_uniform) return fail(GBS_EINVAL, "marginals need identical squeezing on every mode");
   if (!(k->t_uniform > 0.0)) return fail(GBS_EINVAL, "marginals need r > 0");
   cudaStream_t st = (cudaStream_t)stream;
   const int m = k->m;
+  const int group = std::min(samples, std::max(1, (1 << 28) >> n));
   // candidates per pass: at most 2^22 new table entries, and the grid's y extent
-  auto chunk_of = [m](int kk) { return std::max(1, std::min(std::min(m, 65535), (1 << 23) >> kk)); };
+  auto chunk_of = [&](int kk) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)group * m, 65535, (int64_t)1 << (23 - kk)}));
+  };
   auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
-  const size_t cache_b = al(16 * ((size_t)1 << n)), x_b = al(4 * (size_t)kMaxK);
-  size_t Hn_n = 0;
-  for (int kk = 1; kk <= n; ++kk) Hn_n = std::max(Hn_n, (size_t)chunk_of(kk) << (kk - 1));
-  const size_t Hp_b = al(16 * ((size_t)1 << (n - 1))), H_b = Hp_b + al(16 * Hn_n);
+  const int64_t cstride = (int64_t)1 << n;
+  size_t Hn_n = 0, part_n = 0, modes_n = 0;
+  for (int kk = 1; kk <= n; ++kk) {
+    Hn_n = std::max(Hn_n, (size_t)chunk_of(kk) << (kk - 1));
+    part_n = std::max(part_n, (size_t)marginal_blocks(kk, n) * chunk_of(kk));
+    modes_n = std::max(modes_n, (size_t)chunk_of(kk) * kk);
+  }
   const int64_t fstride = fcoef_stride(n);  // one F table per prefix length 1..n
-  const size_t F_b = al(8 * (size_t)(n * fstride));
-  const size_t vm_b = al(4 * (size_t)m * kMaxK), nv_b = al(4 * (size_t)m), q_b = al(8 * (size_t)m);
-  size_t part_b = 0;
-  for (int kk = 1; kk <= n; ++kk) part_b = std::max(part_b, al(marginal_part_bytes(kk, n, chunk_of(kk))));
+  const size_t cache_b = al(16 * (size_t)(group * cstride)), x_b = al(4 * (size_t)group * kMaxK);
+  const size_t Hp_b = al(16 * ((size_t)group << (n - 1))), Hn_b = al(16 * Hn_n), F_b = al(8 * (size_t)(n * fstride));
+  const size_t md_b = al(4 * modes_n), q_b = al(8 * (size_t)group * m), part_b = al(8 * part_n);
   void* tmp = nullptr;
-  cudaError_t e = scratch_alloc(&tmp, cache_b + x_b + H_b + F_b + vm_b + nv_b + q_b + part_b, st);
+  cudaError_t e = scratch_alloc(&tmp, cache_b + x_b + Hp_b + Hn_b + F_b + md_b + q_b + part_b, st);
   if (e != cudaSuccess) return fail(GBS_ENOMEM, "chain scratch: %s", cudaGetErrorString(e));
   unsigned char* t = (unsigned char*)tmp;
   double2* d_cache = (double2*)t;
-  int* d_x = (int*)(t + cache_b);
-  double2* d_Hp = (double2*)(t + cache_b + x_b);
-  double2* d_Hn = (double2*)(t + cache_b + x_b + Hp_b);
-  double* d_F = (double*)(t + cache_b + x_b + H_b);
-  int* d_vm = (int*)(t + cache_b + x_b + H_b + F_b);
-  int* d_nv = (int*)(t + cache_b + x_b + H_b + F_b + vm_b);
-  double* d_q = (double*)(t + cache_b + x_b + H_b + F_b + vm_b + nv_b);
-  double* d_part = (double*)(t + cache_b + x_b + H_b + F_b + vm_b + nv_b + q_b);
+  int* d_x = (int*)(t += cache_b);
+  double2* d_Hp = (double2*)(t += x_b);
+  double2* d_Hn = (double2*)(t += Hp_b);
+  double* d_F = (double*)(t += Hn_b);
+  int* d_modes = (int*)(t += F_b);
+  double* d_q = (double*)(t += md_b);
+  double* d_part = (double*)(t += q_b);
   const double2* B = (const double2*)k->B;
   const SizeScale scale = size_scale(k->t_uniform);
-  int x[kMaxK];
-  std::vector<double> w(m);
-  std::vector<int> vmask((size_t)m * kMaxK), nvals(m);
+  std::vector<int> hx((size_t)group * kMaxK);
+  std::vector<double> w((size_t)group * m);
   int ret = GBS_OK;
-  do {
-    const double2 one = make_double2(1.0, 0.0);  // Haf of the empty matrix
-    if ((e = cudaMemcpyAsync(d_cache, &one, 16, cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+  fcoef_kernel<<<dim3((int)((fstride + 255) / 256), n), 256, 0, st>>>(1, n, m, fstride, d_F);
+  for (int s0 = 0; s0 < samples && ret == GBS_OK; s0 += group) {
+    const int S = std::min(group, samples - s0);
+    chain_init_kernel<<<(S + 255) / 256, 256, 0, st>>>(d_cache, cstride, S);
+    if ((e = cudaGetLastError()) != cudaSuccess) {
       ret = cuda_fail(e, "cache init");
       break;
     }
-    fcoef_kernel<<<dim3((int)((fstride + 255) / 256), n), 256, 0, st>>>(1, n, m, fstride, d_F);
     for (int kk = 1; kk <= n && ret == GBS_OK; ++kk) {
-      const int chunk = chunk_of(kk);
-      // per candidate: position masks of the distinct values (for Per(S_{A,B}))
-      std::fill(vmask.begin(), vmask.end(), 0);
-      for (int l = 0; l < m; ++l) {
-        int nvv = 0;
-        for (int i = 0; i < kk; ++i) {
-          const int xi = (i < kk - 1) ? x[i] : l;
-          int v = 0;
-          while (v < nvv) {
-            const int p0 = __builtin_ctz(vmask[(size_t)l * kMaxK + v]);
-            if (((p0 < kk - 1) ? x[p0] : l) == xi) break;
-            ++v;
-          }
-          if (v == nvv) nvv++;
-          vmask[(size_t)l * kMaxK + v] |= 1 << i;
-        }
-        nvals[l] = nvv;
-      }
-      if ((e = cudaMemcpyAsync(d_vm, vmask.data(), 4 * vmask.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-          (e = cudaMemcpyAsync(d_nv, nvals.data(), 4 * (size_t)m, cudaMemcpyHostToDevice, st)) != cudaSuccess) {
-        ret = cuda_fail(e, "chain upload");
-        break;
-      }
-      const unsigned sizes = needed_sizes(kk, n);
       const int half = 1 << (kk - 1);
-      for (int l0 = 0; l0 < m && e == cudaSuccess; l0 += chunk) {
-        const int cnt = std::min(chunk, m - l0);
-        chain_table_kernel<<<std::min(4096, (int)((((int64_t)cnt + 1) * half + 255) / 256)), 256, 0, st>>>(
-            d_cache, B, d_x, kk, scale, l0, cnt, m, sizes, l0 == 0 ? d_Hp : nullptr, d_Hn);
+      const int chunk = chunk_of(kk);
+      const unsigned sizes = needed_sizes(kk, n);
+      const int64_t items = (int64_t)S * m;
+      chain_prefix_kernel<<<(int)std::min<int64_t>(4096, ((int64_t)S * half + 255) / 256), 256, 0, st>>>(
+          d_cache, cstride, kk, S, scale, d_Hp);
+      e = cudaGetLastError();
+      for (int64_t g0 = 0; g0 < items && e == cudaSuccess; g0 += chunk) {
+        const int cnt = (int)std::min<int64_t>(chunk, items - g0);
+        chain_table_kernel<<<(int)std::min<int64_t>(4096, ((int64_t)cnt * half + 255) / 256), 256, 0, st>>>(
+            d_cache, cstride, B, d_x, kk, scale, g0, cnt, m, sizes, d_Hn, d_modes);
         e = cudaGetLastError();
         if (e == cudaSuccess)
-          e = launch_marginals(kk, n, d_Hp, 0, d_Hn, half, d_F + (kk - 1) * fstride, d_vm + (size_t)l0 * kMaxK, d_nv + l0, cnt, d_part,
-                               d_q + l0, st);
+          e = launch_marginals(kk, n, d_Hp, half, g0, m, d_Hn, half, d_F + (kk - 1) * fstride, d_modes, cnt, d_part,
+                               d_q + g0, st);
       }
       if (e != cudaSuccess) {
         ret = cuda_fail(e, "chain kernels");
         break;
       }
-      if ((e = cudaMemcpyAsync(w.data(), d_q, 8 * (size_t)m, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      if ((e = cudaMemcpyAsync(w.data(), d_q, 8 * (size_t)items, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
           (e = cudaStreamSynchronize(st)) != cudaSuccess) {
         ret = cuda_fail(e, "chain weights");
         break;
       }
-      double tot = 0.0;
-      for (int l = 0; l < m; ++l) tot += std::max(w[l], 0.0);
-      const double target = uniforms[kk - 1] * tot;
-      double run = 0.0;
-      int pick = m - 1;
-      for (int l = 0; l < m; ++l) {
-        run += std::max(w[l], 0.0);
-        if (run > target) {
-          pick = l;
-          break;
+      for (int s = 0; s < S; ++s) {
+        const double* ws = w.data() + (size_t)s * m;
+        double tot = 0.0;
+        for (int l = 0; l < m; ++l) tot += std::max(ws[l], 0.0);
+        const double target = uniforms[(size_t)(s0 + s) * n + kk - 1] * tot;
+        double run = 0.0;
+        int pick = m - 1;
+        for (int l = 0; l < m; ++l) {
+          run += std::max(ws[l], 0.0);
+          if (run > target) {
+            pick = l;
+            break;
+          }
         }
+        hx[(size_t)s * kMaxK + kk - 1] = pick;
       }
-      x[kk - 1] = pick;
-      // the chosen mode's new sub-Hafnians (sets that hold position kk-1) into the cache
+      // the chosen modes' new sub-Hafnians (sets that hold position kk-1) into the caches
       if (kk < n) {
-        if ((e = cudaMemcpyAsync(d_x, x, 4 * (size_t)kk, cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+        if ((e = cudaMemcpyAsync(d_x, hx.data(), 4 * (size_t)S * kMaxK, cudaMemcpyHostToDevice, st)) != cudaSuccess) {
           ret = cuda_fail(e, "prefix upload");
           break;
         }
-        chain_cache_kernel<<<std::min(1024, (half + 255) / 256), 256, 0, st>>>(d_cache, B, d_x, kk, m);
+        chain_cache_kernel<<<(int)std::min<int64_t>(4096, ((int64_t)S * half + 255) / 256), 256, 0, st>>>(
+            d_cache, cstride, B, d_x, kk, m, S);
         if ((e = cudaGetLastError()) != cudaSuccess) {
           ret = cuda_fail(e, "cache update");
           break;
         }
       }
     }
-  } while (0);
+    if (ret == GBS_OK)
+      for (int s = 0; s < S; ++s)
+        for (int i = 0; i < n; ++i) x_out[(size_t)(s0 + s) * n + i] = hx[(size_t)s * kMaxK + i];
+  }
   scratch_free(tmp, st);
-  if (ret == GBS_OK)
-    for (int i = 0; i < n; ++i) x_out[i] = x[i];
   return ret;
+}
+
+// One sample: the batch of one.
+extern "C" int gbs_sample_chain(const gbs_kernel* k, int n, const double* uniforms, void* stream, int* x_out) {
+  return gbs_sample_chain_batch(k, n, 1, uniforms, stream, x_out);
 }
 
 // Steps 1-3 of Sec. 3: n from P_n (truncated at n_max, renormalised) by the

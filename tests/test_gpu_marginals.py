@@ -233,3 +233,17 @@ def test_chain_sampler_long_matches_plain_chain(gbs, m, n, seed):
             c = np.cumsum(w)
             x.append(int(min(np.searchsorted(c, u[k - 1] * c[-1], side="right"), m - 1)))
         assert list(got) == x, (list(got), x)
+
+
+@pytest.mark.parametrize("m,n,count", [(30, 12, 8), (6, 12, 6), (40, 16, 3)])
+def test_chain_batch_equals_single_samples(gbs, m, n, count):
+    """Samples advanced together (one launch sequence for all of them) equal
+    the same samples drawn one at a time, with and without collisions."""
+    U = W.haar_unitary(m, 700 + m + n)
+    K = gbs.build_kernel(U, np.full(m, 0.7))
+    u = np.random.default_rng(m + n).random((count, n))
+    got = gbs.sample_chain_batch(K, n, u)
+    assert got.shape == (count, n)
+    for s in range(count):
+        assert list(got[s]) == list(gbs.sample_chain(K, n, u[s])), s
+    assert gbs.sample_chain_batch(K, n, np.zeros((0, n))).shape == (0, n)
