@@ -104,10 +104,13 @@ __global__ void fcoef_kernel(int k0, int n, int m, int64_t stride, double* __res
 inline int64_t fcoef_stride(int k) { return (int64_t)(k / 2 + 1) * (k / 2 + 1) * (k + 1); }
 
 // The sets rho of the sum that have some (ja, jb) in range: those of the
-// even sizes c[i], count[i] = C(k, c[i]) of each. A team of team[i] lanes
+// even sizes c[i], count[i] of each. `part` selects them: 0 every such rho
+// (C(k, c) of size c), 1 those that hold position k-1 (C(k-1, c-1)), 2 those
+// that do not (C(k-1, c)). A team of team[i] lanes
 // (a power of two up to 32) shares each such rho; class i takes the threads
 // from start[i], a multiple of 32, so a warp never mixes classes.
 struct RhoClasses {
+  int part = 0;
   int ncls = 0;
   int c[kMaxK / 2 + 1];
   int team[kMaxK / 2 + 1];
@@ -116,7 +119,11 @@ struct RhoClasses {
   __host__ __device__ int64_t total() const { return start[ncls]; }
 };
 
-constexpr int kTeamWork = 8;  // subsets per lane that size a team
+// Subsets per lane that size a team: 8 when a launch has little work (its
+// longest team sets the time), up to 32 when the launch fills the GPU (the
+// FP64 pipe sets it, and fewer lanes per team need fewer butterfly adds).
+constexpr int kTeamWorkMin = 8, kTeamWorkMax = 32;
+constexpr int64_t kResidentLanes = 152 * 2048;
 
 // Calls f(sub) for the subsets of rho (c = |rho| set bits) with t elements of
 // colex ranks lo .. lo + cnt - 1: the first by colex unranking (binom = C(p, i)),
@@ -231,14 +238,18 @@ __global__ void __launch_bounds__(kMargThreads) marginal_terms_kernel(int k, int
     const int member = (int)(local % T);
     const bool real = team < rc.count[cls];  // the rest pad the class to whole warps
     // colex unranking: rank = sum_i C(p_i, i) over the positions p_1 < .. < p_c
+    // (over the first k-1 positions when rc.part selects by position k-1)
     int rho = 0;
-    if (real)
-      for (int i = c, p = k - 1, rank = (int)team; i >= 1; --i) {
+    if (real) {
+      const int bits = rc.part ? k - 1 : k, csub = rc.part == 1 ? c - 1 : c;
+      for (int i = csub, p = bits - 1, rank = (int)team; i >= 1; --i) {
         while (s_binom[p][i] > rank) --p;
         rho |= 1 << p;
         rank -= s_binom[p][i];
         --p;
       }
+      if (rc.part == 1) rho |= 1 << (k - 1);
+    }
     const unsigned need = s_need[k - c] & ((2u << (c >> 1)) - 1);
     const int mu = k - c;
     double2 G[kMaxK / 2 + 1];
@@ -270,13 +281,14 @@ __global__ void __launch_bounds__(kMargThreads) marginal_terms_kernel(int k, int
       G[a] = make_double2(gx, gy);
     }
     if (real && member == 0) {
+      // F is symmetric in (ja, jb): the diagonal once, each pair a < e twice
       double t = 0.0;
       for (int a = 0; 2 * a <= c; ++a) {
         if (!(need >> a & 1)) continue;
-        for (int e = 0; 2 * e <= c; ++e) {
+        for (int e = a; 2 * e <= c; ++e) {
           if (!(need >> e & 1)) continue;
           const double f = F[(a * K2 + e) * (k + 1) + mu];
-          if (f != 0.0) t = fma(f, G[a].x * G[e].x + G[a].y * G[e].y, t);
+          if (f != 0.0) t = fma(e == a ? f : 2.0 * f, G[a].x * G[e].x + G[a].y * G[e].y, t);
         }
       }
       int64_t w = 1;  // at most 20!, exact
@@ -348,49 +360,102 @@ __device__ __forceinline__ double2 chain_expand(const double2* __restrict__ cach
   return acc;
 }
 
+// The subsets of `bits` positions with the sizes t[i] (C(bits, t[i]) each,
+// numbered from start[i]): the table entries that some term reads.
+struct SubsetClasses {
+  int bits = 0, ncls = 0;
+  int t[kMaxK + 1];
+  int64_t start[kMaxK + 2];
+  __host__ __device__ int64_t total() const { return start[ncls]; }
+};
+
+// Entry r of the classes: its size class, then colex unranking of its rank
+// (rank = sum_i C(p_i, i) over the positions p_1 < .. < p_t).
+__device__ __forceinline__ int subset_of(const SubsetClasses& sc, int64_t r, const int (*binom)[kMaxK + 1]) {
+  int cls = 0;
+  while (r >= sc.start[cls + 1]) ++cls;
+  int rank = (int)(r - sc.start[cls]), mask = 0;
+  for (int i = sc.t[cls], p = sc.bits - 1; i >= 1; --i) {
+    while (binom[p][i] > rank) --p;
+    mask |= 1 << p;
+    rank -= binom[p][i];
+    --p;
+  }
+  return mask;
+}
+
+// C(p, i) for p, i <= kMaxK into a block's shared table (rows of Pascal's
+// triangle, exact in integers).
+__device__ __forceinline__ void fill_binom(int (*binom)[kMaxK + 1]) {
+  if (threadIdx.x <= (unsigned)kMaxK) {
+    const int p = threadIdx.x;
+    int64_t v = 1;
+    for (int i = 0; i <= kMaxK; ++i) {
+      binom[p][i] = i > p ? 0 : (int)v;
+      v = v * (p - i) / (i + 1);
+    }
+  }
+  __syncthreads();
+}
+
 // Hp[s][T] = Haf(W_T) = Haf(B_T) t^{-|T|/2} for the sets T of sample s's
-// prefix (k-1 positions; 0 for odd |T|): the half of step k's table that every
-// candidate shares. cache: `samples` caches of cstride entries.
-__global__ void chain_prefix_kernel(const double2* __restrict__ cache, int64_t cstride, int k, int samples,
-                                    SizeScale scale, double2* __restrict__ Hp) {
+// prefix (k-1 positions) in the classes `ent` (the sizes some term reads;
+// the other entries are not written): the half of step k's table that every
+// candidate shares. Also each sample's k modes for the sum over the sets
+// without position k-1: its prefix, then -1 (a mode of its own) into
+// pmodes[s * k ..]. cache: `samples` caches of cstride entries; x: kMaxK
+// sampled modes per sample.
+__global__ void chain_prefix_kernel(const double2* __restrict__ cache, int64_t cstride, const int* __restrict__ x,
+                                    int k, int samples, SubsetClasses ent, SizeScale scale, double2* __restrict__ Hp,
+                                    int* __restrict__ pmodes) {
+  __shared__ int s_binom[kMaxK + 1][kMaxK + 1];
+  fill_binom(s_binom);
   const int half = 1 << (k - 1);
-  const int64_t total = (int64_t)samples * half;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < (int64_t)samples * k;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t smp = q / k;
+    const int i = (int)(q - smp * k);
+    pmodes[q] = i < k - 1 ? x[smp * kMaxK + i] : -1;
+  }
+  const int64_t E = ent.total();
+  const int64_t total = (int64_t)samples * E;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-    const int T = (int)(q & (half - 1));
-    const int c = __popc(T);
-    const double2 h = cache[(q >> (k - 1)) * cstride + T];
-    const double sc = (c & 1) ? 0.0 : scale.s[c];
-    Hp[q] = make_double2(h.x * sc, h.y * sc);
+    const int64_t smp = q / E;
+    const int T = subset_of(ent, q - smp * E, s_binom);
+    const double2 h = cache[smp * cstride + T];
+    const double sc = scale.s[__popc(T)];
+    Hp[smp * half + T] = make_double2(h.x * sc, h.y * sc);
   }
 }
 
 // The other half for candidates g0 .. g0 + cnt - 1 (candidate g: sample g / m,
 // mode g % m): Hn[b][T'] = Haf(W) of T' plus the new photon (the expansion
-// above), written for the sizes that `sizes` marks (bit s: s photons; no term
-// reads the others, which keep what they held). Also the candidate's k modes
-// (its sample's prefix, then its own mode) into modes[b * k ..].
+// above), for the T' of the classes `ent` (T' of odd size whose set with the
+// new photon has a size some term reads; the other entries are not written).
+// Also the candidate's k modes (its sample's prefix, then its own mode) into
+// modes[b * k ..].
 //   x: kMaxK sampled modes per sample.
 __global__ void chain_table_kernel(const double2* __restrict__ cache, int64_t cstride, const double2* __restrict__ B,
-                                   const int* __restrict__ x, int k, SizeScale scale, int64_t g0, int cnt, int m,
-                                   unsigned sizes, double2* __restrict__ Hn, int* __restrict__ modes) {
+                                   const int* __restrict__ x, int k, SubsetClasses ent, SizeScale scale, int64_t g0,
+                                   int cnt, int m, double2* __restrict__ Hn, int* __restrict__ modes) {
+  __shared__ int s_binom[kMaxK + 1][kMaxK + 1];
+  fill_binom(s_binom);
   const int half = 1 << (k - 1);
-  const int64_t total = (int64_t)cnt * half;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = q >> (k - 1);
-    const int T = (int)(q & (half - 1));
-    const int64_t g = g0 + b;
-    const int64_t smp = g / m;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t first = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t q = first; q < (int64_t)cnt * k; q += stride) {
+    const int64_t b = q / k, g = g0 + b, smp = g / m;
+    const int i = (int)(q - b * k);
+    modes[q] = i < k - 1 ? x[smp * kMaxK + i] : (int)(g - smp * m);
+  }
+  const int64_t E = ent.total();
+  for (int64_t q = first; q < (int64_t)cnt * E; q += stride) {
+    const int64_t b = q / E, g = g0 + b, smp = g / m;
     const int l = (int)(g - smp * m);
-    const int* xs = x + smp * kMaxK;
-    if (T < k) modes[b * k + T] = T < k - 1 ? xs[T] : l;  // half >= k
-    const int s = __popc(T) + 1;
-    if (!(sizes >> s & 1u)) continue;
-    double2 v = make_double2(0.0, 0.0);
-    if (!(s & 1)) {
-      const double2 h = chain_expand(cache + smp * cstride, B + (int64_t)l * m, xs, T);
-      v = make_double2(h.x * scale.s[s], h.y * scale.s[s]);
-    }
-    Hn[q] = v;
+    const int T = subset_of(ent, q - b * E, s_binom);
+    const double2 h = chain_expand(cache + smp * cstride, B + (int64_t)l * m, x + smp * kMaxK, T);
+    const double sc = scale.s[__popc(T) + 1];
+    Hn[b * half + T] = make_double2(h.x * sc, h.y * sc);
   }
 }
 
@@ -419,42 +484,75 @@ __global__ void chain_cache_kernel(double2* __restrict__ cache, int64_t cstride,
 // The regrouped sum for `batch` prefixes of length k: block sums into
 // part (batch * blocks doubles), then one total per prefix.
 // The size classes of rho for prefix length k of n photons (see RhoClasses).
-RhoClasses rho_classes(int k, int n) {
-  auto binom = [](int a, int b) {
+// Subsets that one prefix's sum enumerates, per size class of rho (0 where
+// the class has no term in range).
+int64_t rho_work(int k, int n, int c) {
+  auto binom = [](int a, int b) -> int64_t {
+    if (b < 0 || b > a) return 0;
     int64_t v = 1;
     for (int i = 1; i <= b; ++i) v = v * (a - b + i) / i;
     return v;
   };
+  int64_t work = 0;
+  for (int ja = 0; ja <= c; ja += 2) {
+    bool any = false;
+    for (int jb = 0; jb <= c && !any; jb += 2) any = theorem_range(k, n, k - c, ja, jb);
+    const int a = ja / 2, a2 = c / 2 - a;  // G(rho, ja) = G(rho, c - ja), formed once
+    bool twin = false;
+    for (int jb = 0; jb <= c && !twin && a2 < a; jb += 2) twin = theorem_range(k, n, k - c, 2 * a2, jb);
+    if (any && !twin) work += binom(c, std::min(ja, c - ja));
+  }
+  return work;
+}
+
+int64_t rho_count(int k, int c, int part) {
+  auto binom = [](int a, int b) -> int64_t {
+    if (b < 0 || b > a) return 0;
+    int64_t v = 1;
+    for (int i = 1; i <= b; ++i) v = v * (a - b + i) / i;
+    return v;
+  };
+  return part == 0 ? binom(k, c) : part == 1 ? binom(k - 1, c - 1) : binom(k - 1, c);
+}
+
+// Subsets one launch enumerates per prefix.
+int64_t prefix_work(int k, int n, int part) {
+  int64_t w = 0;
+  for (int c = 0; c <= k; c += 2) w += rho_count(k, c, part) * rho_work(k, n, c);
+  return w;
+}
+
+// The classes for a launch over `batch` prefixes (batch 0: the widest teams,
+// an upper bound on the threads of any batch).
+RhoClasses rho_classes(int k, int n, int part, int64_t batch) {
+  const int64_t per_lane =
+      std::min<int64_t>(kTeamWorkMax, std::max<int64_t>(kTeamWorkMin, batch * prefix_work(k, n, part) / kResidentLanes));
   RhoClasses rc;
+  rc.part = part;
   rc.start[0] = 0;
   for (int c = 0; c <= k; c += 2) {
-    int64_t work = 0;  // subsets one rho enumerates (the kernel's sizes ja in range)
-    for (int ja = 0; ja <= c; ja += 2) {
-      bool any = false;
-      for (int jb = 0; jb <= c && !any; jb += 2) any = theorem_range(k, n, k - c, ja, jb);
-      if (any) work += binom(c, std::min(ja, c - ja));
-    }
-    if (!work) continue;
+    const int64_t work = rho_work(k, n, c), count = rho_count(k, c, part);
+    if (!work || !count) continue;
     int T = 1;
-    while (T < 32 && (int64_t)T * kTeamWork < work) T *= 2;
+    while (T < 32 && (int64_t)T * per_lane < work) T *= 2;
     const int i = rc.ncls++;
     rc.c[i] = c;
     rc.team[i] = T;
-    rc.count[i] = binom(k, c);
-    rc.start[i + 1] = rc.start[i] + (rc.count[i] * T + 31) / 32 * 32;
+    rc.count[i] = count;
+    rc.start[i + 1] = rc.start[i] + (count * T + 31) / 32 * 32;
   }
   return rc;
 }
 
-int marginal_blocks(int k, int n) {
-  return (int)std::max<int64_t>(1, (rho_classes(k, n).total() + kMargThreads - 1) / kMargThreads);
+int marginal_blocks(int k, int n, int part, int64_t batch) {
+  return (int)std::max<int64_t>(1, (rho_classes(k, n, part, batch).total() + kMargThreads - 1) / kMargThreads);
 }
 
 cudaError_t launch_marginals(int k, int n, const double2* Hlo, int64_t slo, int64_t lo_off, int lo_div,
                              const double2* Hhi, int64_t shi, const double* F, const int* modes, int batch,
-                             double* part, double* q_out, cudaStream_t st) {
-  const RhoClasses rc = rho_classes(k, n);
-  const int nblk = marginal_blocks(k, n);
+                             double* part, double* q_out, cudaStream_t st, int sel = 0) {
+  const RhoClasses rc = rho_classes(k, n, sel, batch);
+  const int nblk = marginal_blocks(k, n, sel, batch);
   marginal_terms_kernel<<<dim3(nblk, batch), kMargThreads, 0, st>>>(k, n, rc, Hlo, slo, lo_off, lo_div, Hhi, shi, F,
                                                                      modes, part);
   cudaError_t e = cudaGetLastError();
@@ -474,7 +572,27 @@ unsigned needed_sizes(int k, int n) {
   return sizes;
 }
 
-size_t marginal_part_bytes(int k, int n, int batch) { return sizeof(double) * (size_t)marginal_blocks(k, n) * batch; }
+// The subsets of `bits` positions of size s - shift for the sizes s marked in
+// `sizes` (bit s: s photons).
+SubsetClasses subset_classes(int bits, unsigned sizes, int shift) {
+  SubsetClasses sc;
+  sc.bits = bits;
+  sc.start[0] = 0;
+  for (int s = 0; s <= kMaxK; ++s) {
+    const int t = s - shift;
+    if (!(sizes >> s & 1u) || t < 0 || t > bits) continue;
+    int64_t cnt = 1;
+    for (int i = 1; i <= t; ++i) cnt = cnt * (bits - t + i) / i;
+    sc.t[sc.ncls] = t;
+    sc.start[sc.ncls + 1] = sc.start[sc.ncls] + cnt;
+    ++sc.ncls;
+  }
+  return sc;
+}
+
+size_t marginal_part_bytes(int k, int n, int batch) {
+  return sizeof(double) * (size_t)marginal_blocks(k, n, 0, 0) * batch;
+}
 
 }  // namespace
 }  // namespace gbs
@@ -563,7 +681,7 @@ extern "C" int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int
         d_hafB, d_slot, nh, kk, size_scale(k->t_uniform), d_H, batch);
     fcoef_kernel<<<dim3((int)((fcoef_stride(kk) + 255) / 256), 1), 256, 0, st>>>(kk, n, k->m, 0, d_F);
     double* qd = q_dev ? q_out : d_q;
-    const int nblk = marginal_blocks(kk, n);
+    const int nblk = marginal_blocks(kk, n, 0, 0);
     for (int b0 = 0; b0 < batch && e == cudaSuccess; b0 += 65535)  // the grid's y extent
       e = launch_marginals(kk, n, d_H + ((int64_t)b0 << kk), (int64_t)1 << kk, 0, 1,
                            d_H + ((int64_t)b0 << kk) + (kk > 0 ? (int64_t)1 << (kk - 1) : 0), (int64_t)1 << kk, d_F,
@@ -608,25 +726,27 @@ extern "C" int gbs_sample_chain_batch(const gbs_kernel* k, int n, int samples, c
   if (!(k->t_uniform > 0.0)) return fail(GBS_EINVAL, "marginals need r > 0");
   cudaStream_t st = (cudaStream_t)stream;
   const int m = k->m;
-  const int group = std::min(samples, std::max(1, (1 << 28) >> n));
-  // candidates per pass: at most 2^22 new table entries, and the grid's y extent
+  const int group = std::min({samples, std::max(1, (1 << 28) >> n), 65535});
+  // candidates per pass: at most 2^26 new table entries (1 GB), and the grid's y extent
   auto chunk_of = [&](int kk) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)group * m, 65535, (int64_t)1 << (23 - kk)}));
+    return (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)group * m, 65535, (int64_t)1 << (27 - kk)}));
   };
   auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
   const int64_t cstride = (int64_t)1 << n;
   size_t Hn_n = 0, part_n = 0, modes_n = 0;
   for (int kk = 1; kk <= n; ++kk) {
     Hn_n = std::max(Hn_n, (size_t)chunk_of(kk) << (kk - 1));
-    part_n = std::max(part_n, (size_t)marginal_blocks(kk, n) * chunk_of(kk));
+    part_n = std::max({part_n, (size_t)marginal_blocks(kk, n, 0, 0) * chunk_of(kk),
+                       (size_t)marginal_blocks(kk, n, 1, 0) * chunk_of(kk), (size_t)marginal_blocks(kk, n, 2, 0) * group});
     modes_n = std::max(modes_n, (size_t)chunk_of(kk) * kk);
   }
   const int64_t fstride = fcoef_stride(n);  // one F table per prefix length 1..n
   const size_t cache_b = al(16 * (size_t)(group * cstride)), x_b = al(4 * (size_t)group * kMaxK);
   const size_t Hp_b = al(16 * ((size_t)group << (n - 1))), Hn_b = al(16 * Hn_n), F_b = al(8 * (size_t)(n * fstride));
-  const size_t md_b = al(4 * modes_n), q_b = al(8 * (size_t)group * m), part_b = al(8 * part_n);
+  const size_t md_b = al(4 * modes_n), q_b = al(8 * (size_t)group * (m + 1)), part_b = al(8 * part_n);
+  const size_t pm_b = al(4 * (size_t)group * n);
   void* tmp = nullptr;
-  cudaError_t e = scratch_alloc(&tmp, cache_b + x_b + Hp_b + Hn_b + F_b + md_b + q_b + part_b, st);
+  cudaError_t e = scratch_alloc(&tmp, cache_b + x_b + Hp_b + Hn_b + F_b + md_b + q_b + part_b + pm_b, st);
   if (e != cudaSuccess) return fail(GBS_ENOMEM, "chain scratch: %s", cudaGetErrorString(e));
   unsigned char* t = (unsigned char*)tmp;
   double2* d_cache = (double2*)t;
@@ -637,10 +757,12 @@ extern "C" int gbs_sample_chain_batch(const gbs_kernel* k, int n, int samples, c
   int* d_modes = (int*)(t += F_b);
   double* d_q = (double*)(t += md_b);
   double* d_part = (double*)(t += q_b);
+  int* d_pmodes = (int*)(t += part_b);
+  double* d_s0 = d_q + (size_t)group * m;  // per sample: the sum over the sets without the new photon
   const double2* B = (const double2*)k->B;
   const SizeScale scale = size_scale(k->t_uniform);
   std::vector<int> hx((size_t)group * kMaxK);
-  std::vector<double> w((size_t)group * m);
+  std::vector<double> w((size_t)group * (m + 1));
   int ret = GBS_OK;
   fcoef_kernel<<<dim3((int)((fstride + 255) / 256), n), 256, 0, st>>>(1, n, m, fstride, d_F);
   for (int s0 = 0; s0 < samples && ret == GBS_OK; s0 += group) {
@@ -654,30 +776,47 @@ extern "C" int gbs_sample_chain_batch(const gbs_kernel* k, int n, int samples, c
       const int half = 1 << (kk - 1);
       const int chunk = chunk_of(kk);
       const unsigned sizes = needed_sizes(kk, n);
+      const SubsetClasses pre = subset_classes(kk - 1, sizes, 0), nw = subset_classes(kk - 1, sizes, 1);
       const int64_t items = (int64_t)S * m;
-      chain_prefix_kernel<<<(int)std::min<int64_t>(4096, ((int64_t)S * half + 255) / 256), 256, 0, st>>>(
-          d_cache, cstride, kk, S, scale, d_Hp);
+      chain_prefix_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>(4096, (S * std::max<int64_t>(kk, pre.total()) + 255) / 256)),
+                            256, 0, st>>>(d_cache, cstride, d_x, kk, S, pre, scale, d_Hp, d_pmodes);
       e = cudaGetLastError();
+      // On steps with much work, the sets without the new photon get one sum
+      // per sample (the candidates differ there only by the factor 1 + the
+      // multiplicity of their mode); on light steps the two extra launches
+      // would cost more than the work they save.
+      const bool split = items * prefix_work(kk, n, 0) >= ((int64_t)1 << 24);
+      if (e == cudaSuccess && split)
+        e = launch_marginals(kk, n, d_Hp, half, 0, 1, d_Hp, 0, d_F + (kk - 1) * fstride, d_pmodes, S, d_part, d_s0,
+                             st, 2);
       for (int64_t g0 = 0; g0 < items && e == cudaSuccess; g0 += chunk) {
         const int cnt = (int)std::min<int64_t>(chunk, items - g0);
-        chain_table_kernel<<<(int)std::min<int64_t>(4096, ((int64_t)cnt * half + 255) / 256), 256, 0, st>>>(
-            d_cache, cstride, B, d_x, kk, scale, g0, cnt, m, sizes, d_Hn, d_modes);
+        const int64_t work = std::max<int64_t>((int64_t)cnt * kk, cnt * nw.total());
+        chain_table_kernel<<<(int)std::min<int64_t>(4096, (work + 255) / 256), 256, 0, st>>>(
+            d_cache, cstride, B, d_x, kk, nw, scale, g0, cnt, m, d_Hn, d_modes);
         e = cudaGetLastError();
         if (e == cudaSuccess)
           e = launch_marginals(kk, n, d_Hp, half, g0, m, d_Hn, half, d_F + (kk - 1) * fstride, d_modes, cnt, d_part,
-                               d_q + g0, st);
+                               d_q + g0, st, split ? 1 : 0);
       }
       if (e != cudaSuccess) {
         ret = cuda_fail(e, "chain kernels");
         break;
       }
+      double* hs0 = w.data() + (size_t)group * m;
       if ((e = cudaMemcpyAsync(w.data(), d_q, 8 * (size_t)items, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+          (split && (e = cudaMemcpyAsync(hs0, d_s0, 8 * (size_t)S, cudaMemcpyDeviceToHost, st)) != cudaSuccess) ||
           (e = cudaStreamSynchronize(st)) != cudaSuccess) {
         ret = cuda_fail(e, "chain weights");
         break;
       }
       for (int s = 0; s < S; ++s) {
-        const double* ws = w.data() + (size_t)s * m;
+        double* ws = w.data() + (size_t)s * m;
+        // q(prefix, l) = (sets with the new photon) + (1 + multiplicity of l in the prefix) * s0
+        if (split) {
+          for (int l = 0; l < m; ++l) ws[l] += hs0[s];
+          for (int i = 0; i < kk - 1; ++i) ws[hx[(size_t)s * kMaxK + i]] += hs0[s];
+        }
         double tot = 0.0;
         for (int l = 0; l < m; ++l) tot += std::max(ws[l], 0.0);
         const double target = uniforms[(size_t)(s0 + s) * n + kk - 1] * tot;

@@ -235,10 +235,13 @@ def test_chain_sampler_long_matches_plain_chain(gbs, m, n, seed):
         assert list(got) == x, (list(got), x)
 
 
-@pytest.mark.parametrize("m,n,count", [(30, 12, 8), (6, 12, 6), (40, 16, 3)])
+@pytest.mark.parametrize("m,n,count", [(30, 12, 8), (6, 12, 6), (40, 16, 3), (40, 16, 64)])
 def test_chain_batch_equals_single_samples(gbs, m, n, count):
     """Samples advanced together (one launch sequence for all of them) equal
-    the same samples drawn one at a time, with and without collisions."""
+    the same samples drawn one at a time, with and without collisions. At 64
+    samples of 16 photons the middle steps are heavy enough that the sum over
+    the sets without the new photon is formed once per sample and shared by
+    its candidates; one at a time it is formed per candidate."""
     U = W.haar_unitary(m, 700 + m + n)
     K = gbs.build_kernel(U, np.full(m, 0.7))
     u = np.random.default_rng(m + n).random((count, n))
