@@ -250,3 +250,33 @@ def test_chain_batch_equals_single_samples(gbs, m, n, count):
     for s in range(count):
         assert list(got[s]) == list(gbs.sample_chain(K, n, u[s])), s
     assert gbs.sample_chain_batch(K, n, np.zeros((0, n))).shape == (0, n)
+
+
+def test_chain_batch_distribution(gbs, orc):
+    """40,000 batched Algorithm 1 samples at m = 6, n = 6 (all 462
+    configurations, collisions included) follow the oracle's p_n(s): total
+    variation within 1.5 times its expectation under exact sampling."""
+    m, n = 6, 6
+    U = W.haar_unitary(m, 606)
+    K = gbs.build_kernel(U, np.full(m, 0.7))
+    draws = 40000
+    x = gbs.sample_chain_batch(K, n, np.random.default_rng(66).random((draws, n)))
+    counts = {}
+    for row in x:
+        key = tuple(sorted(int(v) for v in row))
+        counts[key] = counts.get(key, 0) + 1
+    configs = W.all_patterns(m, n)
+    Wdd = orc.build_B_dd(U, np.ones(m))
+    h = orc.prob(U, np.zeros(m), configs, method="pm", Bdd=Wdd)["haf"]
+    pn = []
+    for c, hv in zip(configs, h):
+        s = W.pattern_to_counts(c, m)
+        Np = math.factorial(n) / np.prod([math.factorial(int(v)) for v in s])
+        pn.append(Np * abs(hv) ** 2 / f_n(m, n))
+    pn = np.array(pn)
+    assert len(configs) == 462 and abs(pn.sum() - 1.0) < 1e-10
+    assert sum(counts.values()) == draws and set(counts) <= {tuple(int(v) for v in c) for c in configs}
+    freq = np.array([counts.get(tuple(int(v) for v in c), 0) for c in configs]) / draws
+    tv = 0.5 * np.abs(freq - pn).sum()
+    expected = 0.5 * np.sqrt(2 / (np.pi * draws)) * np.sum(np.sqrt(pn * (1 - pn)))
+    assert tv <= 1.5 * expected, (tv, expected)
