@@ -260,10 +260,15 @@ int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int batch, int
 /* Algorithm 1 (Sec. 3.2): one ordered n-photon sample x_1..x_n by the chain
  * rule, x_k drawn from the m conditional weights q_n(x_1..x_{k-1}, l),
  * l = 0..m-1 (the sum of gbs_marginal_batch), by the inverse CDF in mode
- * order with the caller's uniform u_k. Identical squeezing only. The sampled
- * prefix's sub-Hafnians stay on the device between steps (the
- * exponential-space variant, Appendix D); those of the sets that hold the
- * new photon come from them by expanding the Hafnian along its row.
+ * order with the caller's uniform u_k: x_k is the first mode of positive
+ * weight whose running sum of weights exceeds u_k times their total. The
+ * running sums are formed on the device in a fixed order (32 contiguous runs
+ * of modes joined by a fixed scan), so x_k can differ from the pick of a
+ * left-to-right sum only when u_k times the total lies within rounding of a
+ * running sum. Identical squeezing only. The sampled prefix's sub-Hafnians
+ * stay on the device between steps (the exponential-space variant,
+ * Appendix D); those of the sets that hold the new photon come from them by
+ * expanding the Hafnian along its row.
  *   n         even, 0..20.
  *   uniforms  n numbers in [0, 1), HOST memory.
  *   x_out     n ints, HOST memory: the mode of each photon in draw order.
@@ -272,7 +277,8 @@ int gbs_sample_chain(const gbs_kernel* k, int n, const double* uniforms, void* s
 
 /* `samples` independent chain samples (gbs_sample_chain each), advanced
  * together: every step covers all samples' m candidates in the same launches,
- * with one copy of the weights and one stream synchronisation per step.
+ * and the modes are drawn on the device, so the call synchronises the stream
+ * once per group of samples.
  * Sample s equals gbs_sample_chain with uniforms[s * n .. s * n + n - 1].
  *   samples   >= 0; they go in groups of at most 2^28 / 2^n (their sub-Hafnian
  *             caches, 2^n complex doubles each, stay within 4 GB).

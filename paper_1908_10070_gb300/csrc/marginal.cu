@@ -459,6 +459,53 @@ __global__ void chain_table_kernel(const double2* __restrict__ cache, int64_t cs
   }
 }
 
+// Step k's draw for each sample (one warp per sample): the weights
+// w_l = max(q_l + f_l s0, 0), l = 0..m-1 (with the per-sample sum s0 over the
+// sets without the new photon, f_l = 1 + the multiplicity of l in the prefix;
+// without it, w_l = max(q_l, 0)), their running sums in mode order (each lane
+// a contiguous run of modes, the runs joined by a fixed warp scan), and x_k =
+// the first l of positive weight whose running sum exceeds u_k times the
+// total (m - 1 if there is none). u: n uniforms per sample.
+__global__ void chain_pick_kernel(const double* __restrict__ q, const double* __restrict__ s0,
+                                  const double* __restrict__ u, int n, int k, int m, int samples, int* __restrict__ x) {
+  const int lane = threadIdx.x & 31;
+  const int smp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (smp >= samples) return;  // the whole warp
+  const double* qs = q + (int64_t)smp * m;
+  int* xs = x + (int64_t)smp * kMaxK;
+  const double sv = s0 ? s0[smp] : 0.0;
+  auto weight = [&](int l) {
+    double f = 1.0;
+    if (s0)
+      for (int i = 0; i < k - 1; ++i) f += xs[i] == l ? 1.0 : 0.0;
+    return fmax(s0 ? fma(f, sv, qs[l]) : qs[l], 0.0);
+  };
+  const int per = (m + 31) / 32, lo = min(m, lane * per), hi = min(m, lo + per);
+  double part = 0.0;
+  for (int l = lo; l < hi; ++l) part += weight(l);
+  double inc = part;  // inclusive scan over the lanes, fixed order
+  for (int off = 1; off < 32; off <<= 1) {
+    const double v = __shfl_up_sync(0xffffffffu, inc, off);
+    if (lane >= off) inc += v;
+  }
+  const double tot = __shfl_sync(0xffffffffu, inc, 31);
+  double run = __shfl_up_sync(0xffffffffu, inc, 1);
+  if (lane == 0) run = 0.0;
+  const double target = u[(int64_t)smp * n + k - 1] * tot;
+  int found = m;
+  for (int l = lo; l < hi; ++l) {
+    const double w = weight(l);
+    run += w;
+    if (w > 0.0 && run > target) {
+      found = l;
+      break;
+    }
+  }
+  const unsigned ball = __ballot_sync(0xffffffffu, found < m);
+  const int pick = ball ? __shfl_sync(0xffffffffu, found, __ffs(ball) - 1) : m - 1;
+  if (lane == 0) xs[k - 1] = pick;
+}
+
 // Every cache starts as Haf of the empty matrix, 1.
 __global__ void chain_init_kernel(double2* __restrict__ cache, int64_t cstride, int samples) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < samples; s += gridDim.x * blockDim.x)
@@ -712,9 +759,10 @@ extern "C" int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int
 // across steps, and those of the sets that hold the new photon come from them
 // by the row expansion of chain_table_kernel (at most k-1 products each, no
 // Hafnian evaluation). A step covers every sample's candidates in the same
-// launches, in chunks of at most 2^22 new table entries; one copy of the
-// weights and one synchronisation per step serve all samples. Samples go in
-// groups whose caches fit in 2^28 entries (4 GB).
+// launches, in chunks of at most 2^26 new table entries, and chain_pick_kernel
+// draws every sample's mode on the device, so the steps run without a host
+// synchronisation; the modes come back once per group of samples. Groups
+// keep their caches within 2^28 entries (4 GB).
 extern "C" int gbs_sample_chain_batch(const gbs_kernel* k, int n, int samples, const double* uniforms, void* stream,
                                       int* x_out) {
   clear_error();
@@ -744,9 +792,9 @@ extern "C" int gbs_sample_chain_batch(const gbs_kernel* k, int n, int samples, c
   const size_t cache_b = al(16 * (size_t)(group * cstride)), x_b = al(4 * (size_t)group * kMaxK);
   const size_t Hp_b = al(16 * ((size_t)group << (n - 1))), Hn_b = al(16 * Hn_n), F_b = al(8 * (size_t)(n * fstride));
   const size_t md_b = al(4 * modes_n), q_b = al(8 * (size_t)group * (m + 1)), part_b = al(8 * part_n);
-  const size_t pm_b = al(4 * (size_t)group * n);
+  const size_t pm_b = al(4 * (size_t)group * n), u_b = al(8 * (size_t)group * n);
   void* tmp = nullptr;
-  cudaError_t e = scratch_alloc(&tmp, cache_b + x_b + Hp_b + Hn_b + F_b + md_b + q_b + part_b + pm_b, st);
+  cudaError_t e = scratch_alloc(&tmp, cache_b + x_b + Hp_b + Hn_b + F_b + md_b + q_b + part_b + pm_b + u_b, st);
   if (e != cudaSuccess) return fail(GBS_ENOMEM, "chain scratch: %s", cudaGetErrorString(e));
   unsigned char* t = (unsigned char*)tmp;
   double2* d_cache = (double2*)t;
@@ -758,18 +806,20 @@ extern "C" int gbs_sample_chain_batch(const gbs_kernel* k, int n, int samples, c
   double* d_q = (double*)(t += md_b);
   double* d_part = (double*)(t += q_b);
   int* d_pmodes = (int*)(t += part_b);
+  double* d_u = (double*)(t += pm_b);
   double* d_s0 = d_q + (size_t)group * m;  // per sample: the sum over the sets without the new photon
   const double2* B = (const double2*)k->B;
   const SizeScale scale = size_scale(k->t_uniform);
   std::vector<int> hx((size_t)group * kMaxK);
-  std::vector<double> w((size_t)group * (m + 1));
   int ret = GBS_OK;
   fcoef_kernel<<<dim3((int)((fstride + 255) / 256), n), 256, 0, st>>>(1, n, m, fstride, d_F);
   for (int s0 = 0; s0 < samples && ret == GBS_OK; s0 += group) {
     const int S = std::min(group, samples - s0);
     chain_init_kernel<<<(S + 255) / 256, 256, 0, st>>>(d_cache, cstride, S);
-    if ((e = cudaGetLastError()) != cudaSuccess) {
-      ret = cuda_fail(e, "cache init");
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d_u, uniforms + (size_t)s0 * n, 8 * (size_t)S * n, cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess) {
+      ret = cuda_fail(e, "chain setup");
       break;
     }
     for (int kk = 1; kk <= n && ret == GBS_OK; ++kk) {
@@ -803,40 +853,13 @@ extern "C" int gbs_sample_chain_batch(const gbs_kernel* k, int n, int samples, c
         ret = cuda_fail(e, "chain kernels");
         break;
       }
-      double* hs0 = w.data() + (size_t)group * m;
-      if ((e = cudaMemcpyAsync(w.data(), d_q, 8 * (size_t)items, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-          (split && (e = cudaMemcpyAsync(hs0, d_s0, 8 * (size_t)S, cudaMemcpyDeviceToHost, st)) != cudaSuccess) ||
-          (e = cudaStreamSynchronize(st)) != cudaSuccess) {
-        ret = cuda_fail(e, "chain weights");
+      chain_pick_kernel<<<(S + 7) / 8, 256, 0, st>>>(d_q, split ? d_s0 : nullptr, d_u, n, kk, m, S, d_x);
+      if ((e = cudaGetLastError()) != cudaSuccess) {
+        ret = cuda_fail(e, "chain pick");
         break;
-      }
-      for (int s = 0; s < S; ++s) {
-        double* ws = w.data() + (size_t)s * m;
-        // q(prefix, l) = (sets with the new photon) + (1 + multiplicity of l in the prefix) * s0
-        if (split) {
-          for (int l = 0; l < m; ++l) ws[l] += hs0[s];
-          for (int i = 0; i < kk - 1; ++i) ws[hx[(size_t)s * kMaxK + i]] += hs0[s];
-        }
-        double tot = 0.0;
-        for (int l = 0; l < m; ++l) tot += std::max(ws[l], 0.0);
-        const double target = uniforms[(size_t)(s0 + s) * n + kk - 1] * tot;
-        double run = 0.0;
-        int pick = m - 1;
-        for (int l = 0; l < m; ++l) {
-          run += std::max(ws[l], 0.0);
-          if (run > target) {
-            pick = l;
-            break;
-          }
-        }
-        hx[(size_t)s * kMaxK + kk - 1] = pick;
       }
       // the chosen modes' new sub-Hafnians (sets that hold position kk-1) into the caches
       if (kk < n) {
-        if ((e = cudaMemcpyAsync(d_x, hx.data(), 4 * (size_t)S * kMaxK, cudaMemcpyHostToDevice, st)) != cudaSuccess) {
-          ret = cuda_fail(e, "prefix upload");
-          break;
-        }
         chain_cache_kernel<<<(int)std::min<int64_t>(4096, ((int64_t)S * half + 255) / 256), 256, 0, st>>>(
             d_cache, cstride, B, d_x, kk, m, S);
         if ((e = cudaGetLastError()) != cudaSuccess) {
@@ -845,9 +868,14 @@ extern "C" int gbs_sample_chain_batch(const gbs_kernel* k, int n, int samples, c
         }
       }
     }
-    if (ret == GBS_OK)
-      for (int s = 0; s < S; ++s)
-        for (int i = 0; i < n; ++i) x_out[(size_t)(s0 + s) * n + i] = hx[(size_t)s * kMaxK + i];
+    if (ret != GBS_OK) break;
+    if ((e = cudaMemcpyAsync(hx.data(), d_x, 4 * (size_t)S * kMaxK, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+      ret = cuda_fail(e, "chain samples");
+      break;
+    }
+    for (int s = 0; s < S; ++s)
+      for (int i = 0; i < n; ++i) x_out[(size_t)(s0 + s) * n + i] = hx[(size_t)s * kMaxK + i];
   }
   scratch_free(tmp, st);
   return ret;
