@@ -38,8 +38,8 @@
 //
 // The sub-Hafnians Haf(W_T) of the sizes read (Haf(B_T) = tanh(r)^{|T|/2}
 // Haf(W_T)) come from the batched subset-sum path in gbs_marginal_batch and
-// from the sampled prefix's cache in the chain sampler; the sum runs one
-// thread per rho, in fixed-order block and prefix reductions.
+// from the sampled prefix's cache in the chain sampler; the sum runs a team
+// of lanes per rho, in fixed-order team, block and prefix reductions.
 #include <math.h>
 #include <string.h>
 
@@ -51,7 +51,7 @@
 namespace gbs {
 namespace {
 
-constexpr int kMaxK = 20;  // prefix length limit (the regrouped sum takes up to 3^k products)
+constexpr int kMaxK = 20;  // prefix length limit (position masks in an int; the sum's sets up to 2^k)
 constexpr int kMargThreads = 256;
 
 __device__ double lgbinom(double x, double y) { return lgamma(x + 1.0) - lgamma(y + 1.0) - lgamma(x - y + 1.0); }
