@@ -301,6 +301,18 @@ int gbs_sample_chain_batch(const gbs_kernel* k, int n, int samples, const double
 int gbs_sample(const gbs_kernel* k, int n_max, const double* uniforms, void* stream, int* n_out,
                int* x_out);
 
+/* `samples` complete samples (gbs_sample each): every sample draws its n from
+ * the truncated P_n, then the samples of each n go through
+ * gbs_sample_chain_batch together. Sample s equals gbs_sample with
+ * uniforms[s * (n_max + 1) .. s * (n_max + 1) + n_max].
+ *   uniforms  samples * (n_max + 1) numbers in [0, 1), sample-major, HOST.
+ *   n_out     samples ints, HOST: each sample's photon number.
+ *   x_out     samples * n_max ints, HOST, sample-major: x_1..x_n of sample s
+ *             at [s * n_max, s * n_max + n), -1 after them.
+ * Errors: GBS_EINVAL, GBS_ERANGE, GBS_ENOMEM, GBS_ECUDA. */
+int gbs_sample_batch(const gbs_kernel* k, int n_max, int samples, const double* uniforms, void* stream,
+                     int* n_out, int* x_out);
+
 /* ------------------------------------------------------------------------ */
 /* Serving: continuous batching of single-pattern probability requests      */
 /* ------------------------------------------------------------------------ */

@@ -21,7 +21,7 @@ __all__ = [
     "FP64", "MIXED", "MAX_N", "GbsError", "lib", "build_kernel", "KernelMatrix",
     "hafnian_batch", "hafnian_batch_noalloc", "prob_batch", "autotune", "measure_fp64_peak", "Server", "serve_create", "pack_patterns",
     "pack_matrices", "last_error", "ERRORS", "photon_number_dist", "sample_bruteforce", "marginal_batch", "sample_chain",
-    "sample_chain_batch", "clear_plans",
+    "sample_chain_batch", "sample", "sample_batch", "clear_plans",
 ]
 
 FP64 = 0
@@ -79,6 +79,7 @@ def lib():
             L.gbs_sample_chain.argtypes = [vp, ctypes.c_int, dp, vp, ip]
             L.gbs_sample_chain_batch.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, vp, ip]
             L.gbs_sample.argtypes = [vp, ctypes.c_int, dp, vp, ctypes.POINTER(ctypes.c_int), ip]
+            L.gbs_sample_batch.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp, vp, ip, ip]
             L.gbs_autotune.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int)]
             L.gbs_measure_fp64_peak.argtypes = [vp, dp]
             L.gbs_set_timing_events.argtypes = [vp, vp]
@@ -298,6 +299,19 @@ def sample(kernel: KernelMatrix, n_max: int, uniforms, stream=None) -> np.ndarra
     n = ctypes.c_int()
     _check(lib().gbs_sample(kernel.handle, int(n_max), _ptr(u), _stream(stream), ctypes.byref(n), _ptr(x)))
     return x[:n.value]
+
+
+def sample_batch(kernel: KernelMatrix, n_max: int, uniforms, stream=None):
+    """Complete samples at once (gbs_sample_batch). uniforms: (samples, n_max + 1)
+    numbers in [0, 1). Returns a list of each sample's x_1..x_n."""
+    u = np.ascontiguousarray(uniforms, dtype=np.float64)
+    if u.ndim != 2 or u.shape[1] != n_max + 1:
+        raise ValueError("uniforms must have shape (samples, n_max + 1)")
+    S = u.shape[0]
+    n = np.zeros(max(S, 1), dtype=np.int32)
+    x = np.zeros((max(S, 1), max(n_max, 1)), dtype=np.int32)
+    _check(lib().gbs_sample_batch(kernel.handle, int(n_max), int(S), _ptr(u), _stream(stream), _ptr(n), _ptr(x)))
+    return [x[s, :n[s]].copy() for s in range(S)]
 
 
 def measure_fp64_peak(stream=None) -> float:

@@ -886,6 +886,33 @@ extern "C" int gbs_sample_chain(const gbs_kernel* k, int n, const double* unifor
   return gbs_sample_chain_batch(k, n, 1, uniforms, stream, x_out);
 }
 
+namespace {
+
+// Step 1 of Sec. 3: n from P_n truncated at n_max (renormalised) by the inverse
+// CDF with the uniform u.
+int pick_photon_number(const std::vector<double>& Pn, int n_max, double tot, double u) {
+  const double target = u * tot;
+  double run = 0.0;
+  for (int v = 0; v <= n_max; v += 2) {
+    run += std::max(Pn[v], 0.0);
+    if (run > target) return v;
+  }
+  return n_max & ~1;
+}
+
+// P_n for n = 0..n_max and the total of its even entries (GBS_EINVAL if 0).
+int truncated_pn(const gbs_kernel* k, int n_max, void* stream, std::vector<double>& Pn, double& tot) {
+  Pn.assign((size_t)n_max + 1, 0.0);
+  const int rc = gbs_photon_number_dist(k, n_max, stream, Pn.data());
+  if (rc) return rc;
+  tot = 0.0;
+  for (int v = 0; v <= n_max; v += 2) tot += std::max(Pn[v], 0.0);
+  if (!(tot > 0.0)) return fail(GBS_EINVAL, "P_n vanishes for every n <= n_max");
+  return GBS_OK;
+}
+
+}  // namespace
+
 // Steps 1-3 of Sec. 3: n from P_n (truncated at n_max, renormalised) by the
 // inverse CDF with uniforms[0], then the chain rule for the n photons.
 extern "C" int gbs_sample(const gbs_kernel* k, int n_max, const double* uniforms, void* stream, int* n_out,
@@ -894,23 +921,48 @@ extern "C" int gbs_sample(const gbs_kernel* k, int n_max, const double* uniforms
   if (!k || !uniforms || !n_out || (n_max > 0 && !x_out)) return fail(GBS_EINVAL, "null argument");
   if (n_max < 0 || n_max > kMaxK) return fail(GBS_ERANGE, "n_max = %d outside [0, %d]", n_max, kMaxK);
   if (!k->r_uniform) return fail(GBS_EINVAL, "sampling needs identical squeezing on every mode");
-  std::vector<double> Pn((size_t)n_max + 1);
-  int rc = gbs_photon_number_dist(k, n_max, stream, Pn.data());
-  if (rc) return rc;
+  std::vector<double> Pn;
   double tot = 0.0;
-  for (int v = 0; v <= n_max; v += 2) tot += std::max(Pn[v], 0.0);
-  if (!(tot > 0.0)) return fail(GBS_EINVAL, "P_n vanishes for every n <= n_max");
-  const double target = uniforms[0] * tot;
-  double run = 0.0;
-  int n = n_max & ~1;
-  for (int v = 0; v <= n_max; v += 2) {
-    run += std::max(Pn[v], 0.0);
-    if (run > target) {
-      n = v;
-      break;
-    }
-  }
+  int rc = truncated_pn(k, n_max, stream, Pn, tot);
+  if (rc) return rc;
+  const int n = pick_photon_number(Pn, n_max, tot, uniforms[0]);
   *n_out = n;
   if (n == 0) return GBS_OK;
   return gbs_sample_chain(k, n, uniforms + 1, stream, x_out);
+}
+
+// gbs_sample for `samples` samples at once: each draws its n, then the samples
+// of each n run as one gbs_sample_chain_batch.
+extern "C" int gbs_sample_batch(const gbs_kernel* k, int n_max, int samples, const double* uniforms, void* stream,
+                                int* n_out, int* x_out) {
+  clear_error();
+  if (!k || (samples > 0 && (!uniforms || !n_out || (n_max > 0 && !x_out)))) return fail(GBS_EINVAL, "null argument");
+  if (samples < 0) return fail(GBS_EINVAL, "samples = %d is negative", samples);
+  if (n_max < 0 || n_max > kMaxK) return fail(GBS_ERANGE, "n_max = %d outside [0, %d]", n_max, kMaxK);
+  if (!k->r_uniform) return fail(GBS_EINVAL, "sampling needs identical squeezing on every mode");
+  if (samples == 0) return GBS_OK;
+  std::vector<double> Pn;
+  double tot = 0.0;
+  int rc = truncated_pn(k, n_max, stream, Pn, tot);
+  if (rc) return rc;
+  const size_t row = (size_t)n_max + 1;
+  std::vector<std::vector<int>> by_n((size_t)n_max + 1);
+  for (int s = 0; s < samples; ++s) {
+    const int n = pick_photon_number(Pn, n_max, tot, uniforms[s * row]);
+    n_out[s] = n;
+    by_n[n].push_back(s);
+    for (int i = 0; i < n_max; ++i) x_out[(size_t)s * n_max + i] = -1;
+  }
+  for (int n = 2; n <= n_max; n += 2) {
+    const std::vector<int>& idx = by_n[n];
+    if (idx.empty()) continue;
+    std::vector<double> u(idx.size() * n);
+    std::vector<int> x(idx.size() * n);
+    for (size_t j = 0; j < idx.size(); ++j)
+      for (int i = 0; i < n; ++i) u[j * n + i] = uniforms[idx[j] * row + 1 + i];
+    if ((rc = gbs_sample_chain_batch(k, n, (int)idx.size(), u.data(), stream, x.data())) != GBS_OK) return rc;
+    for (size_t j = 0; j < idx.size(); ++j)
+      for (int i = 0; i < n; ++i) x_out[(size_t)idx[j] * n_max + i] = x[j * n + i];
+  }
+  return GBS_OK;
 }

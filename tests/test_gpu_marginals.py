@@ -280,3 +280,19 @@ def test_chain_batch_distribution(gbs, orc):
     tv = 0.5 * np.abs(freq - pn).sum()
     expected = 0.5 * np.sqrt(2 / (np.pi * draws)) * np.sum(np.sqrt(pn * (1 - pn)))
     assert tv <= 1.5 * expected, (tv, expected)
+
+
+def test_sample_batch_equals_single_samples(gbs):
+    """gbs_sample_batch: each row equals gbs_sample with the same uniforms
+    (photon number from the truncated P_n, then the chain of that n, samples of
+    one n advanced together); empty batches and n = 0 rows work."""
+    m, r, n_max = 9, 0.9, 8
+    K = gbs.build_kernel(W.haar_unitary(m, 92), np.full(m, r))
+    u = np.random.default_rng(12).random((60, n_max + 1))
+    u[3, 0] = 0.0  # n = 0
+    got = gbs.sample_batch(K, n_max, u)
+    assert len(got) == 60 and len(got[3]) == 0
+    assert len({len(x) for x in got}) >= 3  # several photon numbers in one batch
+    for s in range(60):
+        assert np.array_equal(got[s], gbs.sample(K, n_max, u[s])), s
+    assert gbs.sample_batch(K, n_max, np.zeros((0, n_max + 1))) == []
