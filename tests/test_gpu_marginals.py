@@ -296,3 +296,25 @@ def test_sample_batch_equals_single_samples(gbs):
     for s in range(60):
         assert np.array_equal(got[s], gbs.sample(K, n_max, u[s])), s
     assert gbs.sample_batch(K, n_max, np.zeros((0, n_max + 1))) == []
+
+
+@pytest.mark.parametrize("m", [1, 2])
+def test_chain_sampler_one_and_two_modes(gbs, m):
+    """Every photon in one of one or two modes: the repeated-mode weights carry
+    the whole sum. One mode gives x = 0...0; two modes equal the plain chain."""
+    n = 10
+    U = W.haar_unitary(m, 5 + m)
+    K = gbs.build_kernel(U, np.full(m, 0.8))
+    u = np.random.default_rng(m).random((4, n))
+    got = gbs.sample_chain_batch(K, n, u)
+    if m == 1:
+        assert np.all(got == 0)
+        return
+    for s in range(4):
+        x = []
+        for k in range(1, n + 1):
+            pre = np.array([x + [l] for l in range(m)], np.int32)
+            w = np.maximum(gbs.marginal_batch(K, pre, n), 0.0)
+            c = np.cumsum(w)
+            x.append(int(min(np.searchsorted(c, u[s, k - 1] * c[-1], side="right"), m - 1)))
+        assert list(got[s]) == x, (list(got[s]), x)
