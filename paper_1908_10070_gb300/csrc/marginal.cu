@@ -172,14 +172,18 @@ __device__ __forceinline__ void for_subsets_range(int rho, int c, int t, int lo,
 //      Hhi + b * shi, at T minus that position.
 //   modes: the k modes of prefix b at modes + b * k (repeated modes give w).
 // Each block writes the sum of its threads (fixed tree) to
-// part[b * gridDim.x + blockIdx.x].
+// part[b * gridDim.x + blockIdx.x]; the last block of prefix b to finish
+// (counted in counters[b], which starts at 0 and is left at 0) writes
+// q_out[b], the block sums added in a fixed order.
 __global__ void __launch_bounds__(kMargThreads) marginal_terms_kernel(int k, int n, RhoClasses rc,
                                                                      const double2* __restrict__ Hlo,
                                                                      int64_t slo, int64_t lo_off, int lo_div,
                                                                      const double2* __restrict__ Hhi,
                                                                      int64_t shi, const double* __restrict__ F,
                                                                      const int* __restrict__ modes,
-                                                                     double* __restrict__ part) {
+                                                                     double* __restrict__ part,
+                                                                     unsigned* __restrict__ counters,
+                                                                     double* __restrict__ q_out) {
   __shared__ double red[kMargThreads];
   __shared__ unsigned s_need[kMaxK + 1];  // per mu: bit a set if ja = 2a has some jb in range
   __shared__ int s_mask[kMaxK], s_mult[kMaxK];
@@ -306,19 +310,25 @@ __global__ void __launch_bounds__(kMargThreads) marginal_terms_kernel(int k, int
     if ((int)threadIdx.x < s2) red[threadIdx.x] += red[threadIdx.x + s2];
     __syncthreads();
   }
-  if (threadIdx.x == 0) part[(int64_t)b * gridDim.x + blockIdx.x] = red[0];
-}
-
-// q_out[b] = sum of the prefix's block sums, in block order (one warp per
-// prefix: lane-strided, then a fixed butterfly).
-__global__ void marginal_sum_kernel(const double* __restrict__ part, int nblk, int batch, double* __restrict__ q_out) {
-  const int lane = threadIdx.x & 31;
-  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (b >= batch) return;
-  double s = 0.0;
-  for (int i = lane; i < nblk; i += 32) s += part[(int64_t)b * nblk + i];
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  if (lane == 0) q_out[b] = s;
+  __shared__ bool s_last;
+  if (threadIdx.x == 0) {
+    part[(int64_t)b * gridDim.x + blockIdx.x] = red[0];
+    __threadfence();  // the block sum before the count
+    s_last = atomicAdd(&counters[b], 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x < 32) {
+    // the prefix's last block: q_out[b] = the block sums in block order
+    // (lane-strided, then a fixed butterfly), and the counter back to 0
+    __threadfence();
+    double sum = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) sum += __ldcg(part + (int64_t)b * gridDim.x + i);
+    for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+    if (threadIdx.x == 0) {
+      q_out[b] = sum;
+      counters[b] = 0;
+    }
+  }
 }
 
 // H_W[b][T] = Haf(B_{x_T}) / t^{|T|/2} for the sets with a Hafnian in the
@@ -398,112 +408,54 @@ __device__ __forceinline__ void fill_binom(int (*binom)[kMaxK + 1]) {
   __syncthreads();
 }
 
-// Hp[s][T] = Haf(W_T) = Haf(B_T) t^{-|T|/2} for the sets T of sample s's
-// prefix (k-1 positions) in the classes `ent` (the sizes some term reads;
-// the other entries are not written): the half of step k's table that every
-// candidate shares. Also each sample's k modes for the sum over the sets
-// without position k-1: its prefix, then -1 (a mode of its own) into
-// pmodes[s * k ..]. cache: `samples` caches of cstride entries; x: kMaxK
-// sampled modes per sample.
-__global__ void chain_prefix_kernel(const double2* __restrict__ cache, int64_t cstride, const int* __restrict__ x,
-                                    int k, int samples, SubsetClasses ent, SizeScale scale, double2* __restrict__ Hp,
-                                    int* __restrict__ pmodes) {
-  __shared__ int s_binom[kMaxK + 1][kMaxK + 1];
-  fill_binom(s_binom);
-  const int half = 1 << (k - 1);
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < (int64_t)samples * k;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t smp = q / k;
-    const int i = (int)(q - smp * k);
-    pmodes[q] = i < k - 1 ? x[smp * kMaxK + i] : -1;
-  }
-  const int64_t E = ent.total();
-  const int64_t total = (int64_t)samples * E;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t smp = q / E;
-    const int T = subset_of(ent, q - smp * E, s_binom);
-    const double2 h = cache[smp * cstride + T];
-    const double sc = scale.s[__popc(T)];
-    Hp[smp * half + T] = make_double2(h.x * sc, h.y * sc);
-  }
-}
-
-// The other half for candidates g0 .. g0 + cnt - 1 (candidate g: sample g / m,
-// mode g % m): Hn[b][T'] = Haf(W) of T' plus the new photon (the expansion
-// above), for the T' of the classes `ent` (T' of odd size whose set with the
-// new photon has a size some term reads; the other entries are not written).
-// Also the candidate's k modes (its sample's prefix, then its own mode) into
-// modes[b * k ..].
-//   x: kMaxK sampled modes per sample.
+// Step k's table, in one launch. When `samples` > 0 (the first pass of a
+// step): Hp[s][T] = Haf(W_T) = Haf(B_T) t^{-|T|/2} for the sets T of sample s's
+// prefix (k-1 positions) in the classes `pre` (the sizes some term reads; the
+// others are not written), the half of the table that every candidate
+// shares, and each sample's k modes for the sum over the sets without
+// position k-1 (its prefix, then -1: a mode of its own) into pmodes[s * k ..].
+// For candidates g0 .. g0 + cnt - 1 (candidate g: sample g / m, mode g % m):
+// Hn[b][T'] = Haf(W) of T' plus the new photon (the expansion above), for the
+// T' of the classes `nw` (odd T' whose set with the new photon has a size some
+// term reads; the others are not written), and the candidate's k modes (its
+// sample's prefix, then its own mode) into modes[b * k ..].
+//   cache: caches of cstride entries; x: kMaxK sampled modes per sample.
 __global__ void chain_table_kernel(const double2* __restrict__ cache, int64_t cstride, const double2* __restrict__ B,
-                                   const int* __restrict__ x, int k, SubsetClasses ent, SizeScale scale, int64_t g0,
-                                   int cnt, int m, double2* __restrict__ Hn, int* __restrict__ modes) {
+                                   const int* __restrict__ x, int k, SubsetClasses pre, SubsetClasses nw,
+                                   SizeScale scale, int samples, int64_t g0, int cnt, int m, double2* __restrict__ Hp,
+                                   int* __restrict__ pmodes, double2* __restrict__ Hn, int* __restrict__ modes) {
   __shared__ int s_binom[kMaxK + 1][kMaxK + 1];
   fill_binom(s_binom);
   const int half = 1 << (k - 1);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t first = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t q = first; q < (int64_t)samples * k; q += stride) {
+    const int64_t smp = q / k;
+    const int i = (int)(q - smp * k);
+    pmodes[q] = i < k - 1 ? x[smp * kMaxK + i] : -1;
+  }
+  const int64_t Ep = pre.total();
+  for (int64_t q = first; q < (int64_t)samples * Ep; q += stride) {
+    const int64_t smp = q / Ep;
+    const int T = subset_of(pre, q - smp * Ep, s_binom);
+    const double2 h = cache[smp * cstride + T];
+    const double sc = scale.s[__popc(T)];
+    Hp[smp * half + T] = make_double2(h.x * sc, h.y * sc);
+  }
   for (int64_t q = first; q < (int64_t)cnt * k; q += stride) {
     const int64_t b = q / k, g = g0 + b, smp = g / m;
     const int i = (int)(q - b * k);
     modes[q] = i < k - 1 ? x[smp * kMaxK + i] : (int)(g - smp * m);
   }
-  const int64_t E = ent.total();
+  const int64_t E = nw.total();
   for (int64_t q = first; q < (int64_t)cnt * E; q += stride) {
     const int64_t b = q / E, g = g0 + b, smp = g / m;
     const int l = (int)(g - smp * m);
-    const int T = subset_of(ent, q - b * E, s_binom);
+    const int T = subset_of(nw, q - b * E, s_binom);
     const double2 h = chain_expand(cache + smp * cstride, B + (int64_t)l * m, x + smp * kMaxK, T);
     const double sc = scale.s[__popc(T) + 1];
     Hn[b * half + T] = make_double2(h.x * sc, h.y * sc);
   }
-}
-
-// Step k's draw for each sample (one warp per sample): the weights
-// w_l = max(q_l + f_l s0, 0), l = 0..m-1 (with the per-sample sum s0 over the
-// sets without the new photon, f_l = 1 + the multiplicity of l in the prefix;
-// without it, w_l = max(q_l, 0)), their running sums in mode order (each lane
-// a contiguous run of modes, the runs joined by a fixed warp scan), and x_k =
-// the first l of positive weight whose running sum exceeds u_k times the
-// total (m - 1 if there is none). u: n uniforms per sample.
-__global__ void chain_pick_kernel(const double* __restrict__ q, const double* __restrict__ s0,
-                                  const double* __restrict__ u, int n, int k, int m, int samples, int* __restrict__ x) {
-  const int lane = threadIdx.x & 31;
-  const int smp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (smp >= samples) return;  // the whole warp
-  const double* qs = q + (int64_t)smp * m;
-  int* xs = x + (int64_t)smp * kMaxK;
-  const double sv = s0 ? s0[smp] : 0.0;
-  auto weight = [&](int l) {
-    double f = 1.0;
-    if (s0)
-      for (int i = 0; i < k - 1; ++i) f += xs[i] == l ? 1.0 : 0.0;
-    return fmax(s0 ? fma(f, sv, qs[l]) : qs[l], 0.0);
-  };
-  const int per = (m + 31) / 32, lo = min(m, lane * per), hi = min(m, lo + per);
-  double part = 0.0;
-  for (int l = lo; l < hi; ++l) part += weight(l);
-  double inc = part;  // inclusive scan over the lanes, fixed order
-  for (int off = 1; off < 32; off <<= 1) {
-    const double v = __shfl_up_sync(0xffffffffu, inc, off);
-    if (lane >= off) inc += v;
-  }
-  const double tot = __shfl_sync(0xffffffffu, inc, 31);
-  double run = __shfl_up_sync(0xffffffffu, inc, 1);
-  if (lane == 0) run = 0.0;
-  const double target = u[(int64_t)smp * n + k - 1] * tot;
-  int found = m;
-  for (int l = lo; l < hi; ++l) {
-    const double w = weight(l);
-    run += w;
-    if (w > 0.0 && run > target) {
-      found = l;
-      break;
-    }
-  }
-  const unsigned ball = __ballot_sync(0xffffffffu, found < m);
-  const int pick = ball ? __shfl_sync(0xffffffffu, found, __ffs(ball) - 1) : m - 1;
-  if (lane == 0) xs[k - 1] = pick;
 }
 
 // Every cache starts as Haf of the empty matrix, 1.
@@ -512,25 +464,70 @@ __global__ void chain_init_kernel(double2* __restrict__ cache, int64_t cstride, 
     cache[s * cstride] = make_double2(1.0, 0.0);
 }
 
-// After the picks: cache[s][T' | 2^(k-1)] = Haf(B) of T' plus x_k for every T'
-// over the first k-1 positions of sample s (the expansion above for the
-// sampled mode x_k; 0 for even |T'|).
-__global__ void chain_cache_kernel(double2* __restrict__ cache, int64_t cstride, const double2* __restrict__ B,
-                                   const int* __restrict__ x, int k, int m, int samples) {
-  const int half = 1 << (k - 1);
-  const int64_t total = (int64_t)samples * half;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t smp = q >> (k - 1);
-    const int Tp = (int)(q & (half - 1));
-    const int* xs = x + smp * kMaxK;
-    double2* c = cache + smp * cstride;
-    c[half + Tp] = (__popc(Tp) & 1) ? chain_expand(c, B + (int64_t)xs[k - 1] * m, xs, Tp) : make_double2(0.0, 0.0);
+// Step k's draw for sample blockIdx.y, then (k < n) its cache update; every
+// block of the sample draws (the same inputs give the same mode) and updates
+// its share of the cache. The draw, by warp 0: the weights
+// w_l = max(q_l + f_l s0, 0), l = 0..m-1 (with the per-sample sum s0 over the
+// sets without the new photon, f_l = 1 + the multiplicity of l in the prefix;
+// without it, w_l = max(q_l, 0)), their running sums in mode order (each lane
+// a contiguous run of modes, the runs joined by a fixed warp scan), and x_k =
+// the first l of positive weight whose running sum exceeds u_k times the total
+// (m - 1 if there is none); block 0 writes it. The update:
+// cache[T' | 2^(k-1)] = Haf(B) of T' plus x_k for every T' over the first k-1
+// positions (the expansion above; 0 for even |T'|).
+//   u: n uniforms per sample; x: kMaxK sampled modes per sample.
+__global__ void chain_pick_kernel(const double* __restrict__ q, const double* __restrict__ s0,
+                                  const double* __restrict__ u, int n, int k, int m, int* __restrict__ x,
+                                  double2* __restrict__ cache, int64_t cstride, const double2* __restrict__ B) {
+  __shared__ int s_pick;
+  const int smp = blockIdx.y;
+  const int* xs = x + (int64_t)smp * kMaxK;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const double* qs = q + (int64_t)smp * m;
+    const double sv = s0 ? s0[smp] : 0.0;
+    auto weight = [&](int l) {
+      if (!s0) return fmax(qs[l], 0.0);
+      int mult = 1;  // 1 + the multiplicity of l in the prefix
+      for (int i = 0; i < k - 1; ++i) mult += xs[i] == l;
+      return fmax(fma((double)mult, sv, qs[l]), 0.0);
+    };
+    const int per = (m + 31) / 32, lo = min(m, lane * per), hi = min(m, lo + per);
+    double part = 0.0;
+    for (int l = lo; l < hi; ++l) part += weight(l);
+    double inc = part;  // inclusive scan over the lanes, fixed order
+    for (int off = 1; off < 32; off <<= 1) {
+      const double v = __shfl_up_sync(0xffffffffu, inc, off);
+      if (lane >= off) inc += v;
+    }
+    const double tot = __shfl_sync(0xffffffffu, inc, 31);
+    double run = __shfl_up_sync(0xffffffffu, inc, 1);
+    if (lane == 0) run = 0.0;
+    const double target = u[(int64_t)smp * n + k - 1] * tot;
+    int found = m;
+    for (int l = lo; l < hi; ++l) {
+      const double w = weight(l);
+      run += w;
+      if (w > 0.0 && run > target) {
+        found = l;
+        break;
+      }
+    }
+    const unsigned ball = __ballot_sync(0xffffffffu, found < m);
+    const int first = __shfl_sync(0xffffffffu, found, ball ? __ffs(ball) - 1 : 0);
+    if (lane == 0) s_pick = ball ? first : m - 1;
   }
+  __syncthreads();
+  const int pick = s_pick;
+  if (blockIdx.x == 0 && threadIdx.x == 0) x[(int64_t)smp * kMaxK + k - 1] = pick;
+  if (k == n) return;
+  const int half = 1 << (k - 1);
+  double2* c = cache + (int64_t)smp * cstride;
+  const double2* Brow = B + (int64_t)pick * m;
+  for (int Tp = blockIdx.x * blockDim.x + threadIdx.x; Tp < half; Tp += gridDim.x * blockDim.x)
+    c[half + Tp] = (__popc(Tp) & 1) ? chain_expand(c, Brow, xs, Tp) : make_double2(0.0, 0.0);
 }
 
-// The regrouped sum for `batch` prefixes of length k: block sums into
-// part (batch * blocks doubles), then one total per prefix.
-// The size classes of rho for prefix length k of n photons (see RhoClasses).
 // Subsets that one prefix's sum enumerates, per size class of rho (0 where
 // the class has no term in range).
 int64_t rho_work(int k, int n, int c) {
@@ -595,16 +592,15 @@ int marginal_blocks(int k, int n, int part, int64_t batch) {
   return (int)std::max<int64_t>(1, (rho_classes(k, n, part, batch).total() + kMargThreads - 1) / kMargThreads);
 }
 
+// The sum for `batch` prefixes: q_out[b] for each (part: batch * blocks
+// doubles; counters: batch zeros, left at zero).
 cudaError_t launch_marginals(int k, int n, const double2* Hlo, int64_t slo, int64_t lo_off, int lo_div,
                              const double2* Hhi, int64_t shi, const double* F, const int* modes, int batch,
-                             double* part, double* q_out, cudaStream_t st, int sel = 0) {
+                             double* part, unsigned* counters, double* q_out, cudaStream_t st, int sel = 0) {
   const RhoClasses rc = rho_classes(k, n, sel, batch);
   const int nblk = marginal_blocks(k, n, sel, batch);
   marginal_terms_kernel<<<dim3(nblk, batch), kMargThreads, 0, st>>>(k, n, rc, Hlo, slo, lo_off, lo_div, Hhi, shi, F,
-                                                                     modes, part);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  marginal_sum_kernel<<<(batch + 7) / 8, 256, 0, st>>>(part, nblk, batch, q_out);
+                                                                     modes, part, counters, q_out);
   return cudaGetLastError();
 }
 
@@ -690,9 +686,9 @@ extern "C" int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int
   auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
   const size_t hafB_b = al(16 * (size_t)nh), H_b = al(16 * ((size_t)batch << kk)), slot_b = al(4 * slot.size());
   const size_t F_b = al(8 * (size_t)fcoef_stride(kk)), x_b = al(4 * hx.size()), q_b = al(8 * (size_t)batch);
-  const size_t part_b = al(marginal_part_bytes(kk, n, batch));
+  const size_t part_b = al(marginal_part_bytes(kk, n, batch)), cnt_b = al(4 * (size_t)std::min(batch, 65535));
   void* tmp = nullptr;
-  cudaError_t e = scratch_alloc(&tmp, hafB_b + H_b + slot_b + F_b + x_b + q_b + part_b, st);
+  cudaError_t e = scratch_alloc(&tmp, hafB_b + H_b + slot_b + F_b + x_b + q_b + part_b + cnt_b, st);
   if (e != cudaSuccess) return fail(GBS_ENOMEM, "marginal scratch: %s", cudaGetErrorString(e));
   unsigned char* t = (unsigned char*)tmp;
   double* d_hafB = (double*)t;
@@ -702,6 +698,7 @@ extern "C" int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int
   int* d_x = (int*)(t + hafB_b + H_b + slot_b + F_b);
   double* d_q = (double*)(t + hafB_b + H_b + slot_b + F_b + x_b);
   double* d_part = (double*)(t + hafB_b + H_b + slot_b + F_b + x_b + q_b);
+  unsigned* d_count = (unsigned*)(t + hafB_b + H_b + slot_b + F_b + x_b + q_b + part_b);
   const bool q_dev = is_device_ptr(q_out);
   int ret = GBS_OK;
   do {
@@ -720,7 +717,8 @@ extern "C" int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int
     a.out2 = d_hafB;
     if ((ret = run_batch(a)) != GBS_OK) break;
     if ((e = cudaMemcpyAsync(d_slot, slot.data(), 4 * slot.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(d_x, hx.data(), 4 * hx.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+        (e = cudaMemcpyAsync(d_x, hx.data(), 4 * hx.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(d_count, 0, cnt_b, st)) != cudaSuccess) {
       ret = cuda_fail(e, "marginal upload");
       break;
     }
@@ -733,7 +731,7 @@ extern "C" int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int
       e = launch_marginals(kk, n, d_H + ((int64_t)b0 << kk), (int64_t)1 << kk, 0, 1,
                            d_H + ((int64_t)b0 << kk) + (kk > 0 ? (int64_t)1 << (kk - 1) : 0), (int64_t)1 << kk, d_F,
                            d_x + (int64_t)b0 * kk, std::min(65535, batch - b0), d_part + (int64_t)b0 * nblk,
-                           qd + b0, st);
+                           d_count, qd + b0, st);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
       ret = cuda_fail(e, "marginal kernels");
@@ -793,8 +791,12 @@ extern "C" int gbs_sample_chain_batch(const gbs_kernel* k, int n, int samples, c
   const size_t Hp_b = al(16 * ((size_t)group << (n - 1))), Hn_b = al(16 * Hn_n), F_b = al(8 * (size_t)(n * fstride));
   const size_t md_b = al(4 * modes_n), q_b = al(8 * (size_t)group * (m + 1)), part_b = al(8 * part_n);
   const size_t pm_b = al(4 * (size_t)group * n), u_b = al(8 * (size_t)group * n);
+  size_t cnt_n = (size_t)group;
+  for (int kk = 1; kk <= n; ++kk) cnt_n = std::max(cnt_n, (size_t)chunk_of(kk));
+  const size_t cnt_b = al(4 * cnt_n);
   void* tmp = nullptr;
-  cudaError_t e = scratch_alloc(&tmp, cache_b + x_b + Hp_b + Hn_b + F_b + md_b + q_b + part_b + pm_b + u_b, st);
+  cudaError_t e =
+      scratch_alloc(&tmp, cache_b + x_b + Hp_b + Hn_b + F_b + md_b + q_b + part_b + pm_b + u_b + cnt_b, st);
   if (e != cudaSuccess) return fail(GBS_ENOMEM, "chain scratch: %s", cudaGetErrorString(e));
   unsigned char* t = (unsigned char*)tmp;
   double2* d_cache = (double2*)t;
@@ -807,12 +809,14 @@ extern "C" int gbs_sample_chain_batch(const gbs_kernel* k, int n, int samples, c
   double* d_part = (double*)(t += q_b);
   int* d_pmodes = (int*)(t += part_b);
   double* d_u = (double*)(t += pm_b);
+  unsigned* d_count = (unsigned*)(t += u_b);  // per prefix: blocks of the terms kernel done (left at 0)
   double* d_s0 = d_q + (size_t)group * m;  // per sample: the sum over the sets without the new photon
   const double2* B = (const double2*)k->B;
   const SizeScale scale = size_scale(k->t_uniform);
   std::vector<int> hx((size_t)group * kMaxK);
   int ret = GBS_OK;
   fcoef_kernel<<<dim3((int)((fstride + 255) / 256), n), 256, 0, st>>>(1, n, m, fstride, d_F);
+  if ((e = cudaMemsetAsync(d_count, 0, 4 * cnt_n, st)) != cudaSuccess) ret = cuda_fail(e, "chain counters");
   for (int s0 = 0; s0 < samples && ret == GBS_OK; s0 += group) {
     const int S = std::min(group, samples - s0);
     chain_init_kernel<<<(S + 255) / 256, 256, 0, st>>>(d_cache, cstride, S);
@@ -828,44 +832,38 @@ extern "C" int gbs_sample_chain_batch(const gbs_kernel* k, int n, int samples, c
       const unsigned sizes = needed_sizes(kk, n);
       const SubsetClasses pre = subset_classes(kk - 1, sizes, 0), nw = subset_classes(kk - 1, sizes, 1);
       const int64_t items = (int64_t)S * m;
-      chain_prefix_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>(4096, (S * std::max<int64_t>(kk, pre.total()) + 255) / 256)),
-                            256, 0, st>>>(d_cache, cstride, d_x, kk, S, pre, scale, d_Hp, d_pmodes);
-      e = cudaGetLastError();
       // On steps with much work, the sets without the new photon get one sum
       // per sample (the candidates differ there only by the factor 1 + the
-      // multiplicity of their mode); on light steps the two extra launches
-      // would cost more than the work they save.
+      // multiplicity of their mode); on light steps the extra launch would
+      // cost more than the work it saves.
       const bool split = items * prefix_work(kk, n, 0) >= ((int64_t)1 << 24);
-      if (e == cudaSuccess && split)
-        e = launch_marginals(kk, n, d_Hp, half, 0, 1, d_Hp, 0, d_F + (kk - 1) * fstride, d_pmodes, S, d_part, d_s0,
-                             st, 2);
+      e = cudaSuccess;
       for (int64_t g0 = 0; g0 < items && e == cudaSuccess; g0 += chunk) {
         const int cnt = (int)std::min<int64_t>(chunk, items - g0);
-        const int64_t work = std::max<int64_t>((int64_t)cnt * kk, cnt * nw.total());
-        chain_table_kernel<<<(int)std::min<int64_t>(4096, (work + 255) / 256), 256, 0, st>>>(
-            d_cache, cstride, B, d_x, kk, nw, scale, g0, cnt, m, d_Hn, d_modes);
+        const int Sp = g0 == 0 ? S : 0;  // the first pass also writes the prefix half
+        const int64_t work = std::max({(int64_t)cnt * kk, cnt * nw.total(), (int64_t)Sp * kk, Sp * pre.total()});
+        chain_table_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>(4096, (work + 255) / 256)), 256, 0, st>>>(
+            d_cache, cstride, B, d_x, kk, pre, nw, scale, Sp, g0, cnt, m, d_Hp, d_pmodes, d_Hn, d_modes);
         e = cudaGetLastError();
+        if (e == cudaSuccess && split && g0 == 0)
+          e = launch_marginals(kk, n, d_Hp, half, 0, 1, d_Hp, 0, d_F + (kk - 1) * fstride, d_pmodes, S, d_part,
+                               d_count, d_s0, st, 2);
         if (e == cudaSuccess)
           e = launch_marginals(kk, n, d_Hp, half, g0, m, d_Hn, half, d_F + (kk - 1) * fstride, d_modes, cnt, d_part,
-                               d_q + g0, st, split ? 1 : 0);
+                               d_count, d_q + g0, st, split ? 1 : 0);
       }
       if (e != cudaSuccess) {
         ret = cuda_fail(e, "chain kernels");
         break;
       }
-      chain_pick_kernel<<<(S + 7) / 8, 256, 0, st>>>(d_q, split ? d_s0 : nullptr, d_u, n, kk, m, S, d_x);
+      // the draws, then the chosen modes' new sub-Hafnians (sets that hold
+      // position kk-1) into the caches
+      const int nb = kk < n ? (int)std::max<int64_t>(1, std::min<int64_t>(64, (half + 1023) / 1024)) : 1;
+      chain_pick_kernel<<<dim3(nb, S), 256, 0, st>>>(d_q, split ? d_s0 : nullptr, d_u, n, kk, m, d_x, d_cache, cstride,
+                                                      B);
       if ((e = cudaGetLastError()) != cudaSuccess) {
-        ret = cuda_fail(e, "chain pick");
+        ret = cuda_fail(e, "chain draw");
         break;
-      }
-      // the chosen modes' new sub-Hafnians (sets that hold position kk-1) into the caches
-      if (kk < n) {
-        chain_cache_kernel<<<(int)std::min<int64_t>(4096, ((int64_t)S * half + 255) / 256), 256, 0, st>>>(
-            d_cache, cstride, B, d_x, kk, m, S);
-        if ((e = cudaGetLastError()) != cudaSuccess) {
-          ret = cuda_fail(e, "cache update");
-          break;
-        }
       }
     }
     if (ret != GBS_OK) break;
