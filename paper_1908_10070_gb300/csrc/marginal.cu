@@ -106,9 +106,11 @@ inline int64_t fcoef_stride(int k) { return (int64_t)(k / 2 + 1) * (k / 2 + 1) *
 // The sets rho of the sum that have some (ja, jb) in range: those of the
 // even sizes c[i], count[i] of each. `part` selects them: 0 every such rho
 // (C(k, c) of size c), 1 those that hold position k-1 (C(k-1, c-1)), 2 those
-// that do not (C(k-1, c)). A team of team[i] lanes
-// (a power of two up to 32) shares each such rho; class i takes the threads
-// from start[i], a multiple of 32, so a warp never mixes classes.
+// that do not (C(k-1, c)). A team of team[i] lanes (a power of two up to a
+// block, kMargThreads) shares each such rho; class i takes the threads from
+// start[i], a multiple of 32 (of a block when its teams span several warps),
+// so a warp never mixes classes and a block holds one class whenever that
+// class's teams need the block's barrier.
 struct RhoClasses {
   int part = 0;
   int ncls = 0;
@@ -189,6 +191,7 @@ __global__ void __launch_bounds__(kMargThreads) marginal_terms_kernel(int k, int
   __shared__ int s_mask[kMaxK], s_mult[kMaxK];
   __shared__ int s_nrep;
   __shared__ int s_binom[kMaxK + 1][kMaxK + 1];  // C(p, i)
+  __shared__ double2 s_team[kMargThreads / 32];   // per warp: its share of a team's sum
   const int b = blockIdx.y;
   if (threadIdx.x <= (unsigned)kMaxK) {  // row p of Pascal's triangle, exact in integers
     const int p = threadIdx.x;
@@ -259,7 +262,7 @@ __global__ void __launch_bounds__(kMargThreads) marginal_terms_kernel(int k, int
     double2 G[kMaxK / 2 + 1];
     for (int a = 0; a < K2; ++a) G[a] = make_double2(0.0, 0.0);
     for (int a = 0; 2 * a <= c; ++a) {
-      if (!(need >> a & 1)) continue;  // the same for the whole warp
+      if (!(need >> a & 1)) continue;  // the same for the whole warp (block, if T > 32)
       const int a2 = (c >> 1) - a;     // G(rho, 2a) = G(rho, c - 2a)
       if (a2 < a && (need >> a2 & 1)) {
         G[a] = G[a2];
@@ -278,9 +281,20 @@ __global__ void __launch_bounds__(kMargThreads) marginal_terms_kernel(int k, int
           gx = fma(h1.x, h2.x, fma(-h1.y, h2.y, gx));
           gy = fma(h1.x, h2.y, fma(h1.y, h2.x, gy));
         });
-      for (int off = T >> 1; off > 0; off >>= 1) {
+      for (int off = min(T, 32) >> 1; off > 0; off >>= 1) {
         gx += __shfl_xor_sync(0xffffffffu, gx, off);
         gy += __shfl_xor_sync(0xffffffffu, gy, off);
+      }
+      if (T > 32) {  // the team's warps: their sums in warp order (every thread of the block is here)
+        const int w = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0) s_team[w] = make_double2(gx, gy);
+        __syncthreads();
+        if (member == 0)
+          for (int v = w + 1; v < w + T / 32; ++v) {
+            gx += s_team[v].x;
+            gy += s_team[v].y;
+          }
+        __syncthreads();
       }
       G[a] = make_double2(gx, gy);
     }
@@ -574,16 +588,20 @@ RhoClasses rho_classes(int k, int n, int part, int64_t batch) {
   RhoClasses rc;
   rc.part = part;
   rc.start[0] = 0;
-  for (int c = 0; c <= k; c += 2) {
+  // the largest sets first: their teams run longest, so they start first and
+  // the short ones fill in behind them
+  for (int c = k & ~1; c >= 0; c -= 2) {
     const int64_t work = rho_work(k, n, c), count = rho_count(k, c, part);
     if (!work || !count) continue;
     int T = 1;
-    while (T < 32 && (int64_t)T * per_lane < work) T *= 2;
+    while (T < kMargThreads && (int64_t)T * per_lane < work) T *= 2;
     const int i = rc.ncls++;
+    const int64_t align = T > 32 ? kMargThreads : 32;  // teams of several warps own whole blocks
+    rc.start[i] = (rc.start[i] + align - 1) / align * align;
     rc.c[i] = c;
     rc.team[i] = T;
     rc.count[i] = count;
-    rc.start[i + 1] = rc.start[i] + (count * T + 31) / 32 * 32;
+    rc.start[i + 1] = rc.start[i] + (count * T + align - 1) / align * align;
   }
   return rc;
 }
@@ -591,6 +609,10 @@ RhoClasses rho_classes(int k, int n, int part, int64_t batch) {
 int marginal_blocks(int k, int n, int part, int64_t batch) {
   return (int)std::max<int64_t>(1, (rho_classes(k, n, part, batch).total() + kMargThreads - 1) / kMargThreads);
 }
+
+// At least marginal_blocks for any batch: the widest teams (batch 0), plus
+// the block alignment that narrower teams may add ahead of each class.
+int marginal_blocks_bound(int k, int n, int part) { return marginal_blocks(k, n, part, 0) + 2 * (kMaxK / 2 + 1); }
 
 // The sum for `batch` prefixes: q_out[b] for each (part: batch * blocks
 // doubles; counters: batch zeros, left at zero).
@@ -634,7 +656,7 @@ SubsetClasses subset_classes(int bits, unsigned sizes, int shift) {
 }
 
 size_t marginal_part_bytes(int k, int n, int batch) {
-  return sizeof(double) * (size_t)marginal_blocks(k, n, 0, 0) * batch;
+  return sizeof(double) * (size_t)marginal_blocks_bound(k, n, 0) * batch;
 }
 
 }  // namespace
@@ -726,7 +748,7 @@ extern "C" int gbs_marginal_batch(const gbs_kernel* k, const int* x, int kk, int
         d_hafB, d_slot, nh, kk, size_scale(k->t_uniform), d_H, batch);
     fcoef_kernel<<<dim3((int)((fcoef_stride(kk) + 255) / 256), 1), 256, 0, st>>>(kk, n, k->m, 0, d_F);
     double* qd = q_dev ? q_out : d_q;
-    const int nblk = marginal_blocks(kk, n, 0, 0);
+    const int nblk = marginal_blocks_bound(kk, n, 0);
     for (int b0 = 0; b0 < batch && e == cudaSuccess; b0 += 65535)  // the grid's y extent
       e = launch_marginals(kk, n, d_H + ((int64_t)b0 << kk), (int64_t)1 << kk, 0, 1,
                            d_H + ((int64_t)b0 << kk) + (kk > 0 ? (int64_t)1 << (kk - 1) : 0), (int64_t)1 << kk, d_F,
@@ -782,8 +804,9 @@ extern "C" int gbs_sample_chain_batch(const gbs_kernel* k, int n, int samples, c
   size_t Hn_n = 0, part_n = 0, modes_n = 0;
   for (int kk = 1; kk <= n; ++kk) {
     Hn_n = std::max(Hn_n, (size_t)chunk_of(kk) << (kk - 1));
-    part_n = std::max({part_n, (size_t)marginal_blocks(kk, n, 0, 0) * chunk_of(kk),
-                       (size_t)marginal_blocks(kk, n, 1, 0) * chunk_of(kk), (size_t)marginal_blocks(kk, n, 2, 0) * group});
+    part_n = std::max({part_n, (size_t)marginal_blocks_bound(kk, n, 0) * chunk_of(kk),
+                       (size_t)marginal_blocks_bound(kk, n, 1) * chunk_of(kk),
+                       (size_t)marginal_blocks_bound(kk, n, 2) * group});
     modes_n = std::max(modes_n, (size_t)chunk_of(kk) * kk);
   }
   const int64_t fstride = fcoef_stride(n);  // one F table per prefix length 1..n
