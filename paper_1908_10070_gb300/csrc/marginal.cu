@@ -122,9 +122,12 @@ struct RhoClasses {
 };
 
 // Subsets per lane that size a team: 8 when a launch has little work (its
-// longest team sets the time), up to 32 when the launch fills the GPU (the
-// FP64 pipe sets it, and fewer lanes per team need fewer butterfly adds).
-constexpr int kTeamWorkMin = 8, kTeamWorkMax = 32;
+// longest team sets the time), more when the launch fills the GPU (the FP64
+// pipe sets it, and fewer lanes per team need fewer butterfly adds): up to
+// 128 where a step's largest sets hold 1024 subsets or more (measured better
+// at 20 photons), else up to 32 (measured better at 12 and 16).
+constexpr int kTeamWorkMin = 8, kTeamWorkMax = 32, kTeamWorkMaxLarge = 128;
+constexpr int64_t kLargeSetWork = 1024;
 constexpr int64_t kResidentLanes = 152 * 2048;
 
 // Calls f(sub) for the subsets of rho (c = |rho| set bits) with t elements of
@@ -583,8 +586,12 @@ int64_t prefix_work(int k, int n, int part) {
 // The classes for a launch over `batch` prefixes (batch 0: the widest teams,
 // an upper bound on the threads of any batch).
 RhoClasses rho_classes(int k, int n, int part, int64_t batch) {
+  int64_t largest = 0;
+  for (int c = 0; c <= k; c += 2)
+    if (rho_count(k, c, part)) largest = std::max(largest, rho_work(k, n, c));
+  const int64_t cap = largest >= kLargeSetWork ? kTeamWorkMaxLarge : kTeamWorkMax;
   const int64_t per_lane =
-      std::min<int64_t>(kTeamWorkMax, std::max<int64_t>(kTeamWorkMin, batch * prefix_work(k, n, part) / kResidentLanes));
+      std::min<int64_t>(cap, std::max<int64_t>(kTeamWorkMin, batch * prefix_work(k, n, part) / kResidentLanes));
   RhoClasses rc;
   rc.part = part;
   rc.start[0] = 0;
