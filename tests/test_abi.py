@@ -58,3 +58,18 @@ def test_argument_errors_without_device():
     assert lib.gbs_serve_create(None, None, ctypes.byref(out)) == -1
     assert lib.gbs_serve_destroy(None) == 0
     assert lib.gbs_free_kernel(None) == 0
+
+
+def test_sampler_argument_errors_without_device():
+    """The sampler entry points check their arguments before any CUDA call."""
+    from paper_1908_10070_gb300 import build
+
+    lib = ctypes.CDLL(build.build())
+    lib.gbs_last_error.restype = ctypes.c_char_p
+    i = ctypes.c_int()
+    assert lib.gbs_sample_chain(None, 4, None, None, None) == -1
+    assert b"null" in lib.gbs_last_error()
+    assert lib.gbs_sample_chain_batch(None, 4, 2, None, None, None) == -1
+    assert lib.gbs_sample(None, 4, None, None, ctypes.byref(i), None) == -1
+    assert lib.gbs_sample_batch(None, 4, 2, None, None, None, None) == -1
+    assert lib.gbs_marginal_batch(None, None, 2, 1, 4, None, None) == -1
