@@ -54,6 +54,26 @@ namespace {
 constexpr int kMaxK = 20;  // prefix length limit (position masks in an int; the sum's sets up to 2^k)
 constexpr int kMargThreads = 256;
 
+// C(p, i) for p, i <= kMaxK (Pascal's rule, at compile time), in global
+// memory; blocks copy it (coalesced) into shared memory, where lanes index it
+// freely.
+struct BinomTable {
+  int v[kMaxK + 1][kMaxK + 1];
+};
+constexpr BinomTable make_binom_table() {
+  BinomTable t{};
+  for (int p = 0; p <= kMaxK; ++p)
+    for (int i = 0; i <= kMaxK; ++i) t.v[p][i] = i == 0 ? 1 : p == 0 ? 0 : t.v[p - 1][i - 1] + t.v[p - 1][i];
+  return t;
+}
+__device__ const BinomTable c_binom = make_binom_table();
+static_assert(make_binom_table().v[20][10] == 184756, "Pascal table");
+
+__device__ __forceinline__ void load_binom(int (*binom)[kMaxK + 1]) {
+  for (int q = threadIdx.x; q < (kMaxK + 1) * (kMaxK + 1); q += blockDim.x)
+    binom[q / (kMaxK + 1)][q % (kMaxK + 1)] = c_binom.v[q / (kMaxK + 1)][q % (kMaxK + 1)];
+}
+
 __device__ double lgbinom(double x, double y) { return lgamma(x + 1.0) - lgamma(y + 1.0) - lgamma(x - y + 1.0); }
 
 // t^{-s/2} for s = 0..kMaxK photons (tanh r = t): the factor from Haf(B_T)
@@ -114,6 +134,7 @@ inline int64_t fcoef_stride(int k) { return (int64_t)(k / 2 + 1) * (k / 2 + 1) *
 struct RhoClasses {
   int part = 0;
   int ncls = 0;
+  unsigned need[kMaxK + 1];  // per mu: bit a set if ja = 2a has some jb in range
   int c[kMaxK / 2 + 1];
   int team[kMaxK / 2 + 1];
   int64_t count[kMaxK / 2 + 1];
@@ -180,7 +201,7 @@ __device__ __forceinline__ void for_subsets_range(int rho, int c, int t, int lo,
 // part[b * gridDim.x + blockIdx.x]; the last block of prefix b to finish
 // (counted in counters[b], which starts at 0 and is left at 0) writes
 // q_out[b], the block sums added in a fixed order.
-__global__ void __launch_bounds__(kMargThreads) marginal_terms_kernel(int k, int n, RhoClasses rc,
+__global__ void __launch_bounds__(kMargThreads, 5) marginal_terms_kernel(int k, int n, RhoClasses rc,
                                                                      const double2* __restrict__ Hlo,
                                                                      int64_t slo, int64_t lo_off, int lo_div,
                                                                      const double2* __restrict__ Hhi,
@@ -188,32 +209,22 @@ __global__ void __launch_bounds__(kMargThreads) marginal_terms_kernel(int k, int
                                                                      const int* __restrict__ modes,
                                                                      double* __restrict__ part,
                                                                      unsigned* __restrict__ counters,
-                                                                     double* __restrict__ q_out) {
+                                                                     double* __restrict__ q_out, int batch,
+                                                                     int seg) {
+  constexpr int kSlots = kMargThreads / 32;      // prefixes per block at most (segments of 32 threads)
   __shared__ double red[kMargThreads];
-  __shared__ unsigned s_need[kMaxK + 1];  // per mu: bit a set if ja = 2a has some jb in range
-  __shared__ int s_mask[kMaxK], s_mult[kMaxK];
-  __shared__ int s_nrep;
+  __shared__ int s_mask[kSlots][kMaxK], s_mult[kSlots][kMaxK];
+  __shared__ int s_nrep[kSlots];
   __shared__ int s_binom[kMaxK + 1][kMaxK + 1];  // C(p, i)
   __shared__ double2 s_team[kMargThreads / 32];   // per warp: its share of a team's sum
-  const int b = blockIdx.y;
-  if (threadIdx.x <= (unsigned)kMaxK) {  // row p of Pascal's triangle, exact in integers
-    const int p = threadIdx.x;
-    int64_t v = 1;
-    for (int i = 0; i <= kMaxK; ++i) {
-      s_binom[p][i] = i > p ? 0 : (int)v;
-      v = v * (p - i) / (i + 1);
-    }
-  }
+  // seg < kMargThreads: the block holds kMargThreads / seg prefixes, seg threads each
+  // (gridDim.x == 1); else one prefix per blockIdx.y over gridDim.x blocks
+  const int slot = threadIdx.x / seg, lt = threadIdx.x % seg;
+  const int b = blockIdx.y * (kMargThreads / seg) + slot;
+  const bool live = b < batch;
+  load_binom(s_binom);
   const int K2 = k / 2 + 1;
-  if (threadIdx.x <= (unsigned)k) {
-    const int mu = threadIdx.x;
-    unsigned need = 0;
-    for (int a = 0; a < K2; ++a)
-      for (int c = 0; c < K2; ++c)
-        if (theorem_range(k, n, mu, 2 * a, 2 * c)) need |= 1u << a;
-    s_need[mu] = need;
-  }
-  if (threadIdx.x == 0) {
+  if (lt == 0 && live) {
     // position masks of the repeated modes only (a mode seen once has weight 1 either way)
     const int* xb = modes + (int64_t)b * k;
     int r = 0;
@@ -225,21 +236,21 @@ __global__ void __launch_bounds__(kMargThreads) marginal_terms_kernel(int k, int
         if (xb[j] == xb[i]) mask |= 1 << j;
       seen |= (unsigned)mask;
       if (mask != (1 << i)) {
-        s_mask[r] = mask;
-        s_mult[r] = __popc(mask);
+        s_mask[slot][r] = mask;
+        s_mult[slot][r] = __popc(mask);
         ++r;
       }
     }
-    s_nrep = r;
+    s_nrep[slot] = r;
   }
   __syncthreads();
   const double2* lo = Hlo + ((lo_off + b) / lo_div) * slo;
   const double2* hi = Hhi + b * shi;
   const int half = k > 0 ? 1 << (k - 1) : 0;
   auto haf = [&](int T) { return (T & half) ? hi[T ^ half] : lo[T]; };
-  const int64_t idx = (int64_t)blockIdx.x * kMargThreads + threadIdx.x;
+  const int64_t idx = (int64_t)blockIdx.x * kMargThreads + lt;
   double acc = 0.0;
-  if (idx < rc.total()) {  // whole warps: every class spans a multiple of 32 threads
+  if (live && idx < rc.total()) {  // whole warps: every class spans a multiple of 32 threads
     int cls = 0;
     while (idx >= rc.start[cls + 1]) ++cls;
     const int c = rc.c[cls], T = rc.team[cls];
@@ -260,7 +271,7 @@ __global__ void __launch_bounds__(kMargThreads) marginal_terms_kernel(int k, int
       }
       if (rc.part == 1) rho |= 1 << (k - 1);
     }
-    const unsigned need = s_need[k - c] & ((2u << (c >> 1)) - 1);
+    const unsigned need = rc.need[k - c] & ((2u << (c >> 1)) - 1);
     const int mu = k - c;
     double2 G[kMaxK / 2 + 1];
     for (int a = 0; a < K2; ++a) G[a] = make_double2(0.0, 0.0);
@@ -313,8 +324,8 @@ __global__ void __launch_bounds__(kMargThreads) marginal_terms_kernel(int k, int
         }
       }
       int64_t w = 1;  // at most 20!, exact
-      for (int v = 0; v < s_nrep; ++v) {
-        const int mv = s_mult[v], al = mv - __popc(rho & s_mask[v]);
+      for (int v = 0; v < s_nrep[slot]; ++v) {
+        const int mv = s_mult[slot][v], al = mv - __popc(rho & s_mask[slot][v]);
         for (int i = 2; i <= al; ++i) w *= i;
         w *= s_binom[mv][al];
       }
@@ -323,9 +334,13 @@ __global__ void __launch_bounds__(kMargThreads) marginal_terms_kernel(int k, int
   }
   red[threadIdx.x] = acc;
   __syncthreads();
-  for (int s2 = kMargThreads / 2; s2 > 0; s2 >>= 1) {
-    if ((int)threadIdx.x < s2) red[threadIdx.x] += red[threadIdx.x + s2];
+  for (int s2 = seg / 2; s2 > 0; s2 >>= 1) {  // a fixed tree per segment
+    if (lt < s2) red[threadIdx.x] += red[threadIdx.x + s2];
     __syncthreads();
+  }
+  if (gridDim.x == 1) {  // the prefix's whole sum is this segment's
+    if (lt == 0 && live) q_out[b] = red[threadIdx.x];
+    return;
   }
   __shared__ bool s_last;
   if (threadIdx.x == 0) {
@@ -411,17 +426,9 @@ __device__ __forceinline__ int subset_of(const SubsetClasses& sc, int64_t r, con
   return mask;
 }
 
-// C(p, i) for p, i <= kMaxK into a block's shared table (rows of Pascal's
-// triangle, exact in integers).
+// The Pascal table into a block's shared memory.
 __device__ __forceinline__ void fill_binom(int (*binom)[kMaxK + 1]) {
-  if (threadIdx.x <= (unsigned)kMaxK) {
-    const int p = threadIdx.x;
-    int64_t v = 1;
-    for (int i = 0; i <= kMaxK; ++i) {
-      binom[p][i] = i > p ? 0 : (int)v;
-      v = v * (p - i) / (i + 1);
-    }
-  }
+  load_binom(binom);
   __syncthreads();
 }
 
@@ -595,6 +602,13 @@ RhoClasses rho_classes(int k, int n, int part, int64_t batch) {
   RhoClasses rc;
   rc.part = part;
   rc.start[0] = 0;
+  for (int mu = 0; mu <= kMaxK; ++mu) {
+    unsigned need = 0;
+    for (int a = 0; mu <= k && a <= k / 2; ++a)
+      for (int e = 0; e <= k / 2; ++e)
+        if (theorem_range(k, n, mu, 2 * a, 2 * e)) need |= 1u << a;
+    rc.need[mu] = need;
+  }
   // the largest sets first: their teams run longest, so they start first and
   // the short ones fill in behind them
   for (int c = k & ~1; c >= 0; c -= 2) {
@@ -628,8 +642,12 @@ cudaError_t launch_marginals(int k, int n, const double2* Hlo, int64_t slo, int6
                              double* part, unsigned* counters, double* q_out, cudaStream_t st, int sel = 0) {
   const RhoClasses rc = rho_classes(k, n, sel, batch);
   const int nblk = marginal_blocks(k, n, sel, batch);
-  marginal_terms_kernel<<<dim3(nblk, batch), kMargThreads, 0, st>>>(k, n, rc, Hlo, slo, lo_off, lo_div, Hhi, shi, F,
-                                                                     modes, part, counters, q_out);
+  // a prefix whose sets need at most half a block shares the block with others
+  int seg = kMargThreads;
+  while (nblk == 1 && seg > 32 && rc.total() <= seg / 2) seg /= 2;
+  const int per = kMargThreads / seg;
+  marginal_terms_kernel<<<dim3(nblk, (batch + per - 1) / per), kMargThreads, 0, st>>>(
+      k, n, rc, Hlo, slo, lo_off, lo_div, Hhi, shi, F, modes, part, counters, q_out, batch, seg);
   return cudaGetLastError();
 }
 
