@@ -197,10 +197,14 @@ __device__ __forceinline__ void for_subsets_range(int rho, int c, int t, int lo,
 //      position k-1 reads Hlo + ((lo_off + b) / lo_div) * slo, T with it
 //      Hhi + b * shi, at T minus that position.
 //   modes: the k modes of prefix b at modes + b * k (repeated modes give w).
-// Each block writes the sum of its threads (fixed tree) to
-// part[b * gridDim.x + blockIdx.x]; the last block of prefix b to finish
+// With seg < kMargThreads (one block per prefix suffices, gridDim.x == 1),
+// a block holds kMargThreads / seg prefixes, seg threads each, and each
+// segment's fixed tree gives q_out[b]. Otherwise prefix b = blockIdx.y spans
+// gridDim.x blocks: each writes the sum of its threads (fixed tree) to
+// part[b * gridDim.x + blockIdx.x], and the last block of prefix b to finish
 // (counted in counters[b], which starts at 0 and is left at 0) writes
-// q_out[b], the block sums added in a fixed order.
+// q_out[b], the block sums added in a fixed order (a single block writes it
+// directly).
 __global__ void __launch_bounds__(kMargThreads, 5) marginal_terms_kernel(int k, int n, RhoClasses rc,
                                                                      const double2* __restrict__ Hlo,
                                                                      int64_t slo, int64_t lo_off, int lo_div,
