@@ -318,3 +318,27 @@ def test_chain_sampler_one_and_two_modes(gbs, m):
             c = np.cumsum(w)
             x.append(int(min(np.searchsorted(c, u[s, k - 1] * c[-1], side="right"), m - 1)))
         assert list(got[s]) == x, (list(got[s]), x)
+
+
+def test_marginal_batch_beyond_grid_extent(gbs):
+    """70,000 prefixes (more than one launch's 65,535): every one equals the
+    same prefix in a small batch, so the chunks and their counters are right."""
+    m, n = 12, 6
+    K = gbs.build_kernel(W.haar_unitary(m, 71), np.full(m, 0.7))
+    rng = np.random.default_rng(70)
+    base = rng.integers(0, m, size=(64, 2)).astype(np.int32)
+    ref = gbs.marginal_batch(K, base, n)
+    big = np.tile(base, (70000 // 64 + 1, 1))[:70000]
+    got = gbs.marginal_batch(K, big, n)
+    assert np.array_equal(got, ref[np.arange(70000) % 64])
+
+
+def test_chain_batch_across_sample_groups(gbs):
+    """300 samples of 20 photons span two groups (256 caches of 2^20 entries
+    fit in one): samples on both sides of the boundary equal single draws."""
+    m, n = 22, 20
+    K = gbs.build_kernel(W.haar_unitary(m, 72), np.full(m, 0.8))
+    u = np.random.default_rng(72).random((300, n))
+    got = gbs.sample_chain_batch(K, n, u)
+    for s in (0, 1, 255, 256, 257, 299):
+        assert list(got[s]) == list(gbs.sample_chain(K, n, u[s])), s
