@@ -342,3 +342,21 @@ def test_chain_batch_across_sample_groups(gbs):
     got = gbs.sample_chain_batch(K, n, u)
     for s in (0, 1, 255, 256, 257, 299):
         assert list(got[s]) == list(gbs.sample_chain(K, n, u[s])), s
+
+
+def test_chain_sampler_many_modes(gbs):
+    """m = 2000 modes, 6 photons: the draw's 32 lanes each scan 63 modes and a
+    step has 2000 candidates; samples equal the chain recomputed with
+    gbs_marginal_batch."""
+    m, n = 2000, 6
+    K = gbs.build_kernel(W.haar_unitary(m, 2000), np.full(m, 0.6))
+    u = np.random.default_rng(2000).random((3, n))
+    got = gbs.sample_chain_batch(K, n, u)
+    for s in range(3):
+        x = []
+        for k in range(1, n + 1):
+            pre = np.array([x + [l] for l in range(m)], np.int32)
+            w = np.maximum(gbs.marginal_batch(K, pre, n), 0.0)
+            c = np.cumsum(w)
+            x.append(int(min(np.searchsorted(c, u[s, k - 1] * c[-1], side="right"), m - 1)))
+        assert list(got[s]) == x, (list(got[s]), x)
