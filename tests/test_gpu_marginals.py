@@ -179,7 +179,7 @@ def brute_marginals_subset(orc, U, prefixes, n):
 @pytest.mark.parametrize("m,n,ks", [(3, 14, (12, 13, 14)), (14, 14, (12, 13)), (4, 16, (13, 14)), (2, 20, (18, 19, 20))])
 def test_marginals_long_prefixes_vs_definition(gbs, orc, m, n, ks):
     """Prefixes of 12 to 20 photons (beyond the nested sums' reach): with many
-    repeated modes (m = 2..4, the multiset form of the regrouped sum) and
+    repeated modes (m = 2..4, where the multiset weights w(rho) carry the sum) and
     without any (m = 14, one prefix of distinct modes), against the brute-force
     marginal of Eq. marginal_definition."""
     U = W.haar_unitary(m, 300 + m + n)
