@@ -73,6 +73,54 @@ def fp64_peak_tflops() -> float:
     return SMS * FP64_FLOP_PER_CLK_SM * SM_MHZ_MAX * 1e6 / 1e12
 
 
+def chain_sample_flops(n: int, m: int, samples: int) -> float:
+    """Algorithmic FP64 flops of `samples` Algorithm 1 samples of n photons over
+    m modes, as the library forms them (8 flops per complex multiply-add): per
+    step k, the Theorem 1 products Haf(W_sigma) Haf(W_{rho \\ sigma}) over the
+    sets rho and sizes |sigma| inside the theorem's ranges (one of each pair
+    G(rho, j) = G(rho, |rho| - j); the sets without the new photon once per
+    sample on steps of at least 2^24 subsets), the row expansions of the new
+    sub-Hafnians of the sizes read (|T'| products each), and the chosen mode's
+    cache update (|T'| products for each odd T' of the prefix)."""
+    from math import comb
+
+    def in_range(k, mu, ja, jb):
+        lo = max(0, 2 * k - n)
+        return ja >= lo and jb >= lo and max(0, 3 * k - ja - jb - n) <= mu <= k - max(ja, jb)
+
+    def rho_work(k, c):  # subsets one set rho of size c enumerates
+        w = 0
+        for ja in range(0, c + 1, 2):
+            a, a2 = ja // 2, c // 2 - ja // 2
+            used = any(in_range(k, k - c, ja, jb) for jb in range(0, c + 1, 2))
+            twin = a2 < a and any(in_range(k, k - c, 2 * a2, jb) for jb in range(0, c + 1, 2))
+            if used and not twin:
+                w += comb(c, min(ja, c - ja))
+        return w
+
+    def count(k, c, part):  # sets of size c: all, with position k-1, without it
+        if part == 0:
+            return comb(k, c)
+        if part == 1:
+            return comb(k - 1, c - 1) if c >= 1 else 0
+        return comb(k - 1, c)
+
+    macs = 0
+    items = samples * m
+    for k in range(1, n + 1):
+        work = {p: sum(count(k, c, p) * rho_work(k, c) for c in range(0, k + 1, 2)) for p in (0, 1, 2)}
+        if items * work[0] >= 1 << 24:
+            macs += items * work[1] + samples * work[2]
+        else:
+            macs += items * work[0]
+        sizes = {s for c in range(0, k + 1, 2) for ja in range(0, c + 1, 2) for jb in range(0, c + 1, 2)
+                 if in_range(k, k - c, ja, jb) for s in (ja, c - ja)}
+        macs += items * sum(comb(k - 1, s - 1) * (s - 1) for s in sizes if s >= 2 and s % 2 == 0)
+        if k < n:
+            macs += samples * sum(comb(k - 1, t) * t for t in range(1, k, 2))
+    return 8.0 * macs
+
+
 def fp32_peak_tflops() -> float:
     """FP32 peak from unit counts and clock: 152 SMs x 128 FFMA lanes (256 flop)/clk x 2.07 GHz."""
     return SMS * 256.0 * SM_MHZ_MAX * 1e6 / 1e12
@@ -569,7 +617,7 @@ def extras(gbs, torch, measured_peak):
     out["large_m900"]["cpu_baseline"]["sample"] += " (16 of the 64 n=28 patterns)"
     out["bunched_m8"] = bunched(gbs, torch)
     out["serving"] = serving(gbs, torch)
-    out["sampler"] = sampler(gbs)
+    out["sampler"] = sampler(gbs, measured_peak)
     return out
 
 
@@ -635,7 +683,7 @@ def bunched(gbs, torch, reps=3):
             "subset_sum_max_err_est": float(np.max(km.cpu().numpy() * 24 * 2.0 ** -53))}
 
 
-def sampler(gbs):
+def sampler(gbs, measured_peak=None):
     """Appendix I brute-force sampler at the paper's check size (n = 4, m = 16,
     400,000 draws), Step 1 (P_n) at m = 36, and Algorithm 1 chain samples of
     12, 16 and 20 photons at m = n^2: wall time through the C ABI."""
@@ -675,7 +723,13 @@ def sampler(gbs):
         t0 = time.perf_counter()
         gbs.sample_chain_batch(Kc, n_, uu)
         dt = time.perf_counter() - t0
-        chain["batch_n%d_m%d" % (n_, m_)] = {"samples": S, "s_per_batch": dt, "samples_per_s": S / dt}
+        fl = chain_sample_flops(n_, m_, S)
+        chain["batch_n%d_m%d" % (n_, m_)] = {
+            "samples": S, "s_per_batch": dt, "samples_per_s": S / dt,
+            "fp64_tflops": fl / dt / 1e12, "frac_of_fp64_peak": fl / dt / 1e12 / fp64_peak_tflops(),
+            "frac_of_measured_fp64_peak": (fl / dt / 1e12 / measured_peak) if measured_peak else None,
+            "work_note": "chain_sample_flops: the products, row expansions and cache updates the kernels form, "
+                         "8 flops per complex multiply-add; whole-call wall time"}
     return {"bruteforce_n4_m16": {"configurations": 3876, "draws": len(u), "wall_ms": 1e3 * t_bf,
                                   "draws_per_s": len(u) / t_bf, "P_n": total},
             "photon_number_m36_nmax200_wall_ms": 1e3 * t_pn,
