@@ -645,7 +645,7 @@ cudaError_t launch_marginals(int k, int n, const double2* Hlo, int64_t slo, int6
                              const double2* Hhi, int64_t shi, const double* F, const int* modes, int batch,
                              double* part, unsigned* counters, double* q_out, cudaStream_t st, int sel = 0) {
   const RhoClasses rc = rho_classes(k, n, sel, batch);
-  const int nblk = marginal_blocks(k, n, sel, batch);
+  const int nblk = (int)std::max<int64_t>(1, (rc.total() + kMargThreads - 1) / kMargThreads);
   // a prefix whose sets need at most half a block shares the block with others
   int seg = kMargThreads;
   while (nblk == 1 && seg > 32 && rc.total() <= seg / 2) seg /= 2;
