@@ -69,8 +69,9 @@ constexpr BinomTable make_binom_table() {
 __device__ const BinomTable c_binom = make_binom_table();
 static_assert(make_binom_table().v[20][10] == 184756, "Pascal table");
 
-__device__ __forceinline__ void load_binom(int (*binom)[kMaxK + 1]) {
-  for (int q = threadIdx.x; q < (kMaxK + 1) * (kMaxK + 1); q += blockDim.x)
+// Rows p <= rows of the table (a prefix of length k indexes p < k).
+__device__ __forceinline__ void load_binom(int (*binom)[kMaxK + 1], int rows) {
+  for (int q = threadIdx.x; q < (rows + 1) * (kMaxK + 1); q += blockDim.x)
     binom[q / (kMaxK + 1)][q % (kMaxK + 1)] = c_binom.v[q / (kMaxK + 1)][q % (kMaxK + 1)];
 }
 
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(kMargThreads, 5) marginal_terms_kernel(int k, 
   const int slot = threadIdx.x / seg, lt = threadIdx.x % seg;
   const int b = blockIdx.y * (kMargThreads / seg) + slot;
   const bool live = b < batch;
-  load_binom(s_binom);
+  load_binom(s_binom, k);
   const int K2 = k / 2 + 1;
   if (lt == 0 && live) {
     // position masks of the repeated modes only (a mode seen once has weight 1 either way)
@@ -431,8 +432,8 @@ __device__ __forceinline__ int subset_of(const SubsetClasses& sc, int64_t r, con
 }
 
 // The Pascal table into a block's shared memory.
-__device__ __forceinline__ void fill_binom(int (*binom)[kMaxK + 1]) {
-  load_binom(binom);
+__device__ __forceinline__ void fill_binom(int (*binom)[kMaxK + 1], int rows) {
+  load_binom(binom, rows);
   __syncthreads();
 }
 
@@ -453,7 +454,7 @@ __global__ void chain_table_kernel(const double2* __restrict__ cache, int64_t cs
                                    SizeScale scale, int samples, int64_t g0, int cnt, int m, double2* __restrict__ Hp,
                                    int* __restrict__ pmodes, double2* __restrict__ Hn, int* __restrict__ modes) {
   __shared__ int s_binom[kMaxK + 1][kMaxK + 1];
-  fill_binom(s_binom);
+  fill_binom(s_binom, k);
   const int half = 1 << (k - 1);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t first = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
