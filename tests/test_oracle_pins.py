@@ -372,3 +372,73 @@ def test_prob_order_and_diagonal_free(orc):
     k0 = orc.prob(U, r, pats)["kappa"]
     k1 = orc.prob(U, r, pats, zero_diag=True)["kappa"]
     assert np.all(k0 > 0) and np.all(k1 > 0) and not np.allclose(k0, k1)
+
+
+def _theorem1_position_sets(Wm, x, n, orc):
+    """Theorem 1 in the order the library sums it (over position sets rho =
+    [k] minus A, multiset weights prod alpha_v! C(m_v, alpha_v), only the sizes
+    inside the theorem's ranges), from the oracle's perfect-matching Hafnians."""
+    k, m = len(x), Wm.shape[0]
+
+    def haf(pos):
+        if not pos:
+            return 1.0
+        if len(pos) % 2:
+            return 0.0
+        sel = [x[i] for i in pos]
+        return orc.haf_pm(Wm[np.ix_(sel, sel)])
+
+    def lgb(a, b):
+        return math.lgamma(a + 1) - math.lgamma(b + 1) - math.lgamma(a - b + 1)
+
+    def in_range(mu, ja, jb):
+        lo = max(0, 2 * k - n)
+        return ja >= lo and jb >= lo and max(0, 3 * k - ja - jb - n) <= mu <= k - max(ja, jb)
+
+    def F(mu, ja, jb):  # F(k, mu, ja, jb) / f_n
+        if not in_range(mu, ja, jb):
+            return 0.0
+        return math.exp(math.lgamma(n - k + 1) + lgb(0.5 * (n - k + mu + m) - 1, k - 0.5 * (ja + jb) + 0.5 * m - 1)
+                        - math.lgamma(n + 1) - lgb(0.5 * (m + n) - 1, 0.5 * n))
+
+    mult = {}
+    for v in x:
+        mult[v] = mult.get(v, 0) + 1
+    q = 0.0
+    for c in range(0, k + 1, 2):
+        mu = k - c
+        need = [ja for ja in range(0, c + 1, 2) if any(in_range(mu, ja, jb) for jb in range(0, c + 1, 2))]
+        for rho in itertools.combinations(range(k), c):
+            G = {ja: sum(haf(list(s)) * haf([i for i in rho if i not in s]) for s in itertools.combinations(rho, ja))
+                 for ja in need}
+            form = sum(F(mu, a, b) * (G[a] * np.conj(G[b])).real for a in need for b in need)
+            w = 1.0
+            for v, mv in mult.items():
+                al = mv - sum(1 for i in rho if x[i] == v)
+                w *= math.factorial(al) * math.comb(mv, al)
+            q += w * form
+    return q
+
+
+@pytest.mark.parametrize("m,n", [(4, 4), (3, 6), (5, 6)])
+def test_theorem1_position_set_sum_equals_definition(orc, m, n):
+    """The reading of Theorem 1 the library computes (the sum over position sets
+    with multiset weights, terms outside the theorem's ranges never formed)
+    equals the brute-force marginal of Eq. marginal_definition, sum over the
+    completions of |Haf(W_x)|^2 / f_n, for prefixes with and without repeated
+    modes and every prefix length."""
+    U = W.haar_unitary(m, 808 + m + n)
+    Wm = U @ U.T
+    a = (m + n) / 2 - 1
+    f_n = math.factorial(n) * math.exp(math.lgamma(a + 1) - math.lgamma(n / 2 + 1) - math.lgamma(a - n / 2 + 1))
+    rng = np.random.default_rng(m * 10 + n)
+    for k in range(0, n + 1):
+        for trial in range(2):
+            x = [1] * k if trial == 0 else [int(v) for v in rng.integers(0, m, size=k)]
+            brute = 0.0
+            for comp in itertools.product(range(m), repeat=n - k):
+                y = x + list(comp)
+                brute += abs(orc.haf_pm(Wm[np.ix_(y, y)])) ** 2
+            brute /= f_n
+            got = _theorem1_position_sets(Wm, x, n, orc)
+            assert abs(got - brute) <= 1e-11 * abs(brute) + 1e-300, (m, n, x, got, brute)
