@@ -374,11 +374,14 @@ def test_prob_order_and_diagonal_free(orc):
     assert np.all(k0 > 0) and np.all(k1 > 0) and not np.allclose(k0, k1)
 
 
-def _theorem1_position_sets(Wm, x, n, orc):
+def _theorem1_position_sets(Wm, x, n, orc, part=0, weight_modes=None):
     """Theorem 1 in the order the library sums it (over position sets rho =
     [k] minus A, multiset weights prod alpha_v! C(m_v, alpha_v), only the sizes
-    inside the theorem's ranges), from the oracle's perfect-matching Hafnians."""
+    inside the theorem's ranges), from the oracle's perfect-matching Hafnians.
+    part 1 / 2 keeps only the sets rho with / without position k - 1;
+    weight_modes (default x) gives the modes the weights count."""
     k, m = len(x), Wm.shape[0]
+    wx = x if weight_modes is None else weight_modes
 
     def haf(pos):
         if not pos:
@@ -402,19 +405,21 @@ def _theorem1_position_sets(Wm, x, n, orc):
                         - math.lgamma(n + 1) - lgb(0.5 * (m + n) - 1, 0.5 * n))
 
     mult = {}
-    for v in x:
+    for v in wx:
         mult[v] = mult.get(v, 0) + 1
     q = 0.0
     for c in range(0, k + 1, 2):
         mu = k - c
         need = [ja for ja in range(0, c + 1, 2) if any(in_range(mu, ja, jb) for jb in range(0, c + 1, 2))]
         for rho in itertools.combinations(range(k), c):
+            if (part == 1 and k - 1 not in rho) or (part == 2 and k - 1 in rho):
+                continue
             G = {ja: sum(haf(list(s)) * haf([i for i in rho if i not in s]) for s in itertools.combinations(rho, ja))
                  for ja in need}
             form = sum(F(mu, a, b) * (G[a] * np.conj(G[b])).real for a in need for b in need)
             w = 1.0
             for v, mv in mult.items():
-                al = mv - sum(1 for i in rho if x[i] == v)
+                al = mv - sum(1 for i in rho if wx[i] == v)
                 w *= math.factorial(al) * math.comb(mv, al)
             q += w * form
     return q
@@ -442,3 +447,21 @@ def test_theorem1_position_set_sum_equals_definition(orc, m, n):
             brute /= f_n
             got = _theorem1_position_sets(Wm, x, n, orc)
             assert abs(got - brute) <= 1e-11 * abs(brute) + 1e-300, (m, n, x, got, brute)
+
+
+def test_theorem1_split_by_the_new_position(orc):
+    """The chain sampler's split of step k: for a candidate mode l after the
+    prefix x, q(x, l) = (the sets rho that hold position k - 1, weighted by
+    (x, l)) + (1 + multiplicity of l in x) * (the sets without it, weighted by
+    x and a mode of its own at k - 1), since (a+1)! C(m+1, a+1) = (m+1) a! C(m, a)."""
+    m, n = 4, 6
+    U = W.haar_unitary(m, 909)
+    Wm = U @ U.T
+    for x in ([2, 0], [1, 1, 3], [0, 0, 0, 2], [3]):
+        k = len(x) + 1
+        s0 = _theorem1_position_sets(Wm, x + [0], n, orc, part=2, weight_modes=x + [-1])
+        for l in range(m):
+            full = _theorem1_position_sets(Wm, x + [l], n, orc)
+            s1 = _theorem1_position_sets(Wm, x + [l], n, orc, part=1)
+            split = s1 + (1 + x.count(l)) * s0
+            assert abs(split - full) <= 1e-12 * abs(full) + 1e-300, (x, l, split, full, k)
