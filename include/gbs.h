@@ -247,7 +247,9 @@ int gbs_sample_bruteforce(const gbs_kernel* k, int n, const double* uniforms, in
  * the sums over s, s', A, B, mu of Theorem 1 are regrouped by the set
  * rho = [k] \ A (Per(S_{A,B}) = 0 unless A and B hold the same modes), and
  * only the sizes of rho and s inside the theorem's ranges are formed (a
- * team of lanes per rho; the result does not depend on the batch).
+ * team of lanes per rho, sized by the launch's work). Results are
+ * deterministic for a given batch; the same prefix in batches of different
+ * sizes can differ in the last bits (another split of its sums).
  *   x      batch * k mode indices in [0, m), prefix b at [b * k, (b + 1) * k),
  *          host or device (read before return).
  *   k      0..min(n, 20).  n  even, <= GBS_MAX_N.
